@@ -1,0 +1,302 @@
+"""Seeded synthetic unit cells for the periodic volume-integral-equation solver.
+
+This module only *generates inputs*: tetrahedral meshes of one a x b unit cell
+of a layered thin-film stack (optionally with embedded metal spheres) and the
+per-domain relative permittivities at a wavelength.  It holds none of the
+method's arithmetic (no basis functions, Green's functions, quadrature or
+linear algebra), so both the FP64 CPU oracle and the CUDA path consume it.
+
+Geometry follows the unit cell of the paper (Fig. 1, Sec. 2.3): a periodic
+a x b cell, stacked layers of thickness D1, D2, ... and metal particles inside
+the active layer.  The particles are spheres (not the paper's W x W x W cubes),
+the material models are synthetic Drude / Cauchy fits (the paper's measured
+P3HT:PCBM, PEDOT:PSS and Ag data are not available), and the mesh is a
+structured Kuhn (6-tetrahedra-per-hexahedron) split of a graded tensor grid,
+with seeded node jitter and nodes snapped to sphere surfaces.
+
+Conventions: lengths in nm; permittivities use the physics sign (Im > 0 is
+lossy); tetrahedra are positively oriented; periodic lateral faces match under
+translation by (a, 0, 0) and (0, b, 0).
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+import math
+
+import numpy as np
+
+__all__ = [
+    "Cell", "grid_1d", "kuhn_mesh", "slab_cell", "layered_cell",
+    "eps_ag_drude", "eps_active", "eps_buffer",
+    "config_slab", "config_plasmonic", "config_sweep_geometry", "small_cells",
+]
+
+
+@dataclasses.dataclass
+class Cell:
+    verts: np.ndarray          # [n_verts, 3] float64, nm
+    tets: np.ndarray           # [n_tets, 4] int32, positively oriented
+    tet_domain: np.ndarray     # [n_tets] int32 in 0..n_domains-1
+    n_domains: int
+    period_a: float
+    period_b: float
+    active_domain: int
+    domain_names: tuple
+    name: str = ""
+
+    @property
+    def n_tets(self) -> int:
+        return int(self.tets.shape[0])
+
+    def eps(self, lam_nm: float) -> np.ndarray:
+        """Per-domain permittivity at lam_nm from the synthetic models."""
+        table = {"ag": eps_ag_drude, "active": eps_active, "buffer": eps_buffer}
+        out = []
+        for nm in self.domain_names:
+            if nm in table:
+                out.append(complex(table[nm](lam_nm)))
+            else:  # a constant permittivity written as "const:re,im"
+                re, im = nm.split(":")[1].split(",")
+                out.append(complex(float(re), float(im)))
+        return np.array(out, dtype=np.complex128)
+
+
+# ----------------------------------------------------------------------------
+# synthetic material models (inputs, physics sign: Im eps > 0 is lossy)
+# ----------------------------------------------------------------------------
+_HC_EV_NM = 1239.841984  # h*c in eV*nm
+
+
+def eps_ag_drude(lam_nm):
+    """Silver, Drude fit: eps_inf 3.7, hbar*omega_p 9.1 eV, hbar*gamma 0.055 eV."""
+    w = _HC_EV_NM / np.asarray(lam_nm, dtype=np.float64)
+    return 3.7 - 9.1 ** 2 / (w * (w + 1j * 0.055))
+
+
+def eps_active(lam_nm):
+    """Organic active layer, Cauchy n plus a Gaussian absorption band near 500 nm."""
+    lam = np.asarray(lam_nm, dtype=np.float64)
+    n = 1.90 + 0.01925 / (lam * 1e-3) ** 2
+    k = 0.1515 * np.exp(-((lam - 500.0) / 120.0) ** 2)
+    return (n + 1j * k) ** 2
+
+
+def eps_buffer(lam_nm):
+    """Transparent-ish buffer / spacer layer, Cauchy n and constant k."""
+    lam = np.asarray(lam_nm, dtype=np.float64)
+    n = 1.52 + 0.0073 / (lam * 1e-3) ** 2
+    return (n + 1j * 0.0161) ** 2
+
+
+# ----------------------------------------------------------------------------
+# structured meshes
+# ----------------------------------------------------------------------------
+def grid_1d(lo, hi, breaks=(), fine_zones=(), h_fine=None, h_coarse=10.0):
+    """Graded 1D grid on [lo, hi] containing every break point exactly.
+
+    Segments between consecutive break points (zone edges included) are split
+    uniformly with spacing <= h_fine inside any fine zone, <= h_coarse outside.
+    """
+    pts = {float(lo), float(hi)}
+    for b in breaks:
+        if lo < b < hi:
+            pts.add(float(b))
+    for z0, z1 in fine_zones:
+        for b in (z0, z1):
+            if lo < b < hi:
+                pts.add(float(b))
+    pts = sorted(pts)
+    out = [pts[0]]
+    for p0, p1 in zip(pts[:-1], pts[1:]):
+        mid = 0.5 * (p0 + p1)
+        fine = any(z0 <= mid <= z1 for z0, z1 in fine_zones)
+        h = h_fine if (fine and h_fine) else h_coarse
+        n = max(1, int(math.ceil((p1 - p0) / h - 1e-9)))
+        out.extend(np.linspace(p0, p1, n + 1)[1:].tolist())
+    return np.array(out, dtype=np.float64)
+
+
+def kuhn_mesh(xs, ys, zs):
+    """Kuhn split of the tensor grid xs x ys x zs into 6 tetrahedra per hexahedron.
+
+    Every hexahedron is cut along its (0,0,0)-(1,1,1) diagonal into the six
+    path simplices; the split is translation invariant, so opposite lateral
+    faces of the cell carry identical triangulations.
+    """
+    nx, ny, nz = len(xs) - 1, len(ys) - 1, len(zs) - 1
+    X, Y, Z = np.meshgrid(xs, ys, zs, indexing="ij")
+    verts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+    def vid(i, j, k):
+        return (i * (ny + 1) + j) * (nz + 1) + k
+
+    I, J, K = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    I, J, K = I.ravel(), J.ravel(), K.ravel()
+    tets = []
+    for perm in itertools.permutations(range(3)):
+        off = np.zeros(3, dtype=np.int64)
+        path = [vid(I, J, K)]
+        for ax in perm:
+            off[ax] += 1
+            path.append(vid(I + off[0], J + off[1], K + off[2]))
+        tets.append(np.stack(path, axis=1))
+    tets = np.concatenate(tets, axis=0).astype(np.int64)
+    # order tets by hexahedron for locality
+    order = np.argsort(np.tile(np.arange(I.size), 6), kind="stable")
+    tets = tets[order]
+    tets = _orient(verts, tets)
+    return verts, tets.astype(np.int32)
+
+
+def _signed_volumes(verts, tets):
+    p = verts[tets]
+    return np.einsum("ij,ij->i", np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), p[:, 3] - p[:, 0]) / 6.0
+
+
+def _orient(verts, tets):
+    tets = tets.copy()
+    neg = _signed_volumes(verts, tets) < 0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    return tets
+
+
+def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=None,
+                 h_z=None, jitter=0.1, seed=0, snap=0.4, name="", active_domain=None,
+                 lateral_fine=True):
+    """Layered unit cell with optional spheres.
+
+    layers:  list of (thickness_nm, material_name) from bottom (z=0) to top.
+    spheres: list of (cx, cy, cz, radius, material_name); each sphere gets its
+             own domain, numbered after the layers.
+    The grid is graded to spacing h_fine inside the bounding box of each sphere
+    (plus half a fine cell), h_coarse elsewhere laterally, h_z (default
+    h_coarse) vertically outside fine zones.
+    """
+    rng = np.random.default_rng(seed)
+    zb = np.concatenate([[0.0], np.cumsum([t for t, _ in layers])])
+    fine_x, fine_y, fine_z = [], [], []
+    for cx, cy, cz, r, _ in spheres:
+        pad = 0.5 * (h_fine or h_coarse)
+        fine_x.append((cx - r - pad, cx + r + pad))
+        fine_y.append((cy - r - pad, cy + r + pad))
+        fine_z.append((cz - r - pad, cz + r + pad))
+    xs = grid_1d(0.0, period_a, (), fine_x if lateral_fine else (), h_fine, h_coarse)
+    ys = grid_1d(0.0, period_b, (), fine_y if lateral_fine else (), h_fine, h_coarse)
+    zs = grid_1d(0.0, zb[-1], zb[1:-1], fine_z, h_fine, h_z or h_coarse)
+    verts, tets = kuhn_mesh(xs, ys, zs)
+    v0 = verts.copy()
+    nxv, nyv, nzv = len(xs), len(ys), len(zs)
+    ii, jj, kk = np.meshgrid(np.arange(nxv), np.arange(nyv), np.arange(nzv), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    lateral = (ii == 0) | (ii == nxv - 1) | (jj == 0) | (jj == nyv - 1)
+    on_plane = np.isin(np.round(verts[:, 2], 9), np.round(zb, 9))
+    # local spacing per node (min of adjacent grid steps)
+    def _loc(g, idx):
+        d = np.diff(g)
+        left = np.where(idx > 0, d[np.clip(idx - 1, 0, len(d) - 1)], np.inf)
+        right = np.where(idx < len(g) - 1, d[np.clip(idx, 0, len(d) - 1)], np.inf)
+        return np.minimum(left, right)
+    hloc = np.minimum(np.minimum(_loc(xs, ii), _loc(ys, jj)), _loc(zs, kk))
+
+    snapped = np.zeros(len(verts), dtype=bool)
+    for cx, cy, cz, r, _ in spheres:
+        d = verts - np.array([cx, cy, cz])
+        dist = np.linalg.norm(d, axis=1)
+        near = (np.abs(dist - r) < snap * hloc) & ~lateral & ~on_plane & (dist > 0)
+        verts[near] = np.array([cx, cy, cz]) + d[near] * (r / dist[near])[:, None]
+        snapped |= near
+    # seeded jitter: free interior nodes in 3D, interface/top/bottom nodes in-plane
+    if jitter > 0:
+        free = ~lateral & ~snapped
+        dj = rng.uniform(-jitter, jitter, size=verts.shape) * hloc[:, None]
+        dj[on_plane, 2] = 0.0
+        # keep jittered nodes clear of sphere surfaces (no accidental straddling)
+        cand = verts + dj
+        for cx, cy, cz, r, _ in spheres:
+            d0 = np.linalg.norm(verts - np.array([cx, cy, cz]), axis=1)
+            d1 = np.linalg.norm(cand - np.array([cx, cy, cz]), axis=1)
+            free &= ~((d0 - r) * (d1 - r) <= 0) | (np.abs(d0 - r) > 1.5 * hloc)
+        verts[free] = cand[free]
+    # reject inverted / degenerate tets by undoing moves of their nodes
+    vol0 = _signed_volumes(v0, tets)
+    for _ in range(20):
+        vol = _signed_volumes(verts, tets)
+        bad = vol < 0.15 * vol0
+        if not bad.any():
+            break
+        nodes = np.unique(tets[bad])
+        verts[nodes] = v0[nodes]
+    vol = _signed_volumes(verts, tets)
+    assert (vol > 0).all(), "mesh generation produced an inverted tetrahedron"
+
+    cent = verts[tets].mean(axis=1)
+    dom = np.searchsorted(zb, cent[:, 2], side="right") - 1
+    dom = np.clip(dom, 0, len(layers) - 1).astype(np.int32)
+    names = [m for _, m in layers]
+    for s, (cx, cy, cz, r, m) in enumerate(spheres):
+        inside = np.linalg.norm(cent - np.array([cx, cy, cz]), axis=1) < r
+        dom[inside] = len(layers) + s
+        names.append(m)
+    if active_domain is None:
+        active_domain = names.index("active") if "active" in names else 0
+    return Cell(verts=verts, tets=tets.astype(np.int32), tet_domain=dom,
+                n_domains=len(names), period_a=float(period_a), period_b=float(period_b),
+                active_domain=int(active_domain), domain_names=tuple(names), name=name)
+
+
+def slab_cell(nx, ny, nz, a=200.0, b=200.0, d=40.0, eps=(4.0, 0.5), jitter=0.0, seed=0):
+    """Homogeneous slab of thickness d filling the a x b cell, uniform nx x ny x nz grid."""
+    xs = np.linspace(0.0, a, nx + 1)
+    ys = np.linspace(0.0, b, ny + 1)
+    zs = np.linspace(0.0, d, nz + 1)
+    verts, tets = kuhn_mesh(xs, ys, zs)
+    if jitter > 0:
+        rng = np.random.default_rng(seed)
+        h = min(a / nx, b / ny, d / nz)
+        interior = ((verts[:, 0] > 1e-9) & (verts[:, 0] < a - 1e-9)
+                    & (verts[:, 1] > 1e-9) & (verts[:, 1] < b - 1e-9))
+        dj = rng.uniform(-jitter, jitter, size=verts.shape) * h
+        planar = (np.abs(verts[:, 2]) < 1e-9) | (np.abs(verts[:, 2] - d) < 1e-9)
+        dj[planar, 2] = 0.0
+        verts = verts.copy()
+        verts[interior] += dj[interior]
+        assert (_signed_volumes(verts, tets) > 0).all()
+    name = "const:%r,%r" % (float(eps[0]), float(eps[1]))
+    return Cell(verts=verts, tets=tets, tet_domain=np.zeros(len(tets), np.int32), n_domains=1,
+                period_a=float(a), period_b=float(b), active_domain=0,
+                domain_names=(name,), name="slab_%dx%dx%d" % (nx, ny, nz))
+
+
+# ----------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------
+def config_slab():
+    """Homogeneous absorbing slab: period 200 nm, 40 nm thick, eps 4.0+0.5i, 6x6x2 hexahedra (432 tets)."""
+    return slab_cell(6, 6, 2, 200.0, 200.0, 40.0, (4.0, 0.5))
+
+
+def config_plasmonic(seed=2, h_coarse=20.0, h_fine=8.5, h_z=20.0):
+    """Plasmonic cell: period 200 nm, Ag sphere r=20 nm centred in a 100 nm active
+    layer over a 40 nm buffer (three material domains)."""
+    return layered_cell(200.0, 200.0, [(40.0, "buffer"), (100.0, "active")],
+                        spheres=[(100.0, 100.0, 90.0, 20.0, "ag")],
+                        h_coarse=h_coarse, h_fine=h_fine, h_z=h_z, jitter=0.1, seed=seed,
+                        name="plasmonic_200nm_r20")
+
+
+def config_sweep_geometry(seed=3):
+    """The plasmonic geometry at the coarser density used for wavelength x angle sweeps."""
+    return config_plasmonic(seed=seed, h_coarse=28.0, h_fine=11.0, h_z=28.0)
+
+
+def small_cells():
+    """Small cells the oracle finishes in seconds (parity cases)."""
+    return {
+        "slab_3x3x1": slab_cell(3, 3, 1, 200.0, 200.0, 40.0, (4.0, 0.5)),
+        "slab_4x3x2_jit": slab_cell(4, 3, 2, 180.0, 150.0, 40.0, (3.0, 0.8), jitter=0.12, seed=11),
+        "plasmonic_mini": layered_cell(120.0, 120.0, [(30.0, "buffer"), (50.0, "active")],
+                                       spheres=[(60.0, 60.0, 55.0, 15.0, "ag")],
+                                       h_coarse=40.0, h_fine=15.0, h_z=30.0, jitter=0.1, seed=5,
+                                       name="plasmonic_mini"),
+    }

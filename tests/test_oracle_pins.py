@@ -1,0 +1,292 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test fixes a part of the oracle to mathematics or closed forms it does not
+share code with: polynomial exactness of the quadrature rules, brute-force
+Duffy cubature of the 1/R potentials, independence of the Ewald sum from its
+splitting parameter plus agreement with the plain Floquet and windowed lattice
+sums of Eq. (3), transfer-matrix reflectance/transmittance/absorption of a
+homogeneous slab, reciprocity Z(k) = Z(-k)^T, the energy balance, and a planted
+sign error that must fail the slab test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import cellgen
+from closed_forms import tmm_rt
+from oracle import quadrature as qr
+from oracle.fill import Problem, assemble
+from oracle.greens import PeriodicGreen, spectral_direct, windowed_direct
+from oracle.potentials import tet_integrals, tri_integrals
+from oracle.topology import build_topology, KIND_HALF, KIND_PERIODIC
+from oracle import solve_cell
+
+
+# --------------------------------------------------------------------------- quadrature
+def _simplex_monomial(exps):
+    """Exact mean of prod l_i^e_i over a simplex of dimension len(exps)-1."""
+    dim = len(exps) - 1
+    num = math.factorial(dim) * np.prod([math.factorial(e) for e in exps])
+    return num / math.factorial(sum(exps) + dim)
+
+
+@pytest.mark.parametrize("rule,deg,nv", [(qr.tet_deg2, 2, 4), (qr.tet_deg5, 5, 4),
+                                         (qr.tri_deg2, 2, 3), (qr.tri_deg5, 5, 3)])
+def test_quadrature_exactness(rule, deg, nv):
+    pts, w = rule()
+    assert abs(w.sum() - 1) < 1e-14
+    assert np.all(w > 0)
+    import itertools
+    for total in range(deg + 1):
+        for exps in itertools.product(range(total + 1), repeat=nv):
+            if sum(exps) != total:
+                continue
+            q = np.sum(w * np.prod(pts ** np.array(exps), axis=1))
+            assert abs(q - _simplex_monomial(exps)) < 1e-13
+    # and not exact one degree higher (the rule is what it claims, no more)
+    exps = [deg + 1] + [0] * (nv - 1)
+    q = np.sum(w * pts[:, 0] ** (deg + 1))
+    assert abs(q - _simplex_monomial(exps)) > 1e-8
+
+
+# --------------------------------------------------------------------------- potentials
+def _gl(n):
+    """Composite Gauss-Legendre on [0, 1], geometrically graded towards both ends."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    half = np.concatenate([[0.0], 0.5 * np.logspace(-9, 0, 19)])
+    edges = np.unique(np.concatenate([half, 1.0 - half]))
+    xs, ws = [], []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        xs.append(lo + (hi - lo) * 0.5 * (x + 1))
+        ws.append((hi - lo) * 0.5 * w)
+    return np.concatenate(xs), np.concatenate(ws)
+
+
+def _brute_tri(r, tri, n=12):
+    """Duffy cubature with apex at the projection of r: integrand smooth in (u, v)."""
+    v0, v1, v2 = tri
+    nrm = np.cross(v1 - v0, v2 - v0)
+    nrm /= np.linalg.norm(nrm)
+    p = r - np.dot(r - v0, nrm) * nrm
+    u, wu = _gl(n)
+    inv = rr = 0.0
+    for A, B in ((v0, v1), (v1, v2), (v2, v0)):
+        J = np.dot(np.cross(A - p, B - p), nrm)          # signed twice-area
+        for vi, wv in zip(u, wu):
+            e = (1 - vi) * (A - p) + vi * (B - p)
+            x = p[None] + u[:, None] * e[None]
+            R = np.linalg.norm(x - r, axis=1)
+            inv += wv * np.sum(wu * u * J / R)
+            rr += wv * np.sum(wu * u * J * R)
+    return inv, rr
+
+
+def _brute_tet(r, tet, n=8):
+    """3D Duffy cubature with apex at r over the four signed sub-tetrahedra.
+
+    x = r + s (y - r), y = A + v (B - A) + v w (C - B) on face ABC:
+    dV = s^2 v [(A - r) . ((B - A) x (C - A))] ds dv dw, so 1/R and (x-r)/R are smooth.
+    """
+    u, wu = _gl(n)
+    V, W = np.meshgrid(u, u, indexing="ij")
+    WV = np.outer(wu, wu)
+    inv = 0.0
+    vec = np.zeros(3)
+    for i in range(4):
+        A, B, C = tet[[j for j in range(4) if j != i]]
+        sgn = np.sign(np.dot(np.cross(B - A, C - A), A - tet[i]))       # outward face
+        J0 = sgn * np.dot(np.cross(B - A, C - A), A - r)
+        y = A + V[..., None] * (B - A) + (V * W)[..., None] * (C - B)
+        d = y - r
+        nd = np.linalg.norm(d, axis=-1)
+        # int_0^1 s^2 / (s |d|) ds = 1/(2|d|);  int_0^1 s^2 ds = 1/3
+        inv += np.sum(WV * V * J0 / (2 * nd))
+        vec += np.sum((WV * V * J0 / 3.0)[..., None] * d / nd[..., None], axis=(0, 1))
+    return inv, vec
+
+
+def test_triangle_potentials_vs_cubature():
+    rng = np.random.default_rng(3)
+    tri = np.array([[0.0, 0, 0], [7.0, 1, 0.5], [2.0, 6, -1]])
+    pts = [tri.mean(0), tri.mean(0) + [0, 0, 3.0], tri[0] + [0.3, 0.2, 0.05],
+           np.array([20.0, -5, 4]), 0.5 * (tri[0] + tri[1]) + [0, 0, 0.8]]
+    nrm = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+    nrm /= np.linalg.norm(nrm)
+    pts.append(tri[0] + 0.4 * (tri[1] - tri[0]) + 0.3 * (tri[2] - tri[0]))   # in plane, inside
+    pts.append(tri[0] + 1.3 * (tri[1] - tri[0]) + 0.2 * (tri[2] - tri[0]))   # in plane, outside
+    pts += list(tri.mean(0) + rng.normal(size=(4, 3)) * 4)
+    for r in pts:
+        inv, rr = tri_integrals(r, tri)
+        binv, brr = _brute_tri(np.asarray(r, float), tri)
+        assert abs(inv - binv) < 1e-9 * abs(binv), (r, inv, binv)
+        assert abs(rr - brr) < 1e-9 * abs(brr), (r, rr, brr)
+
+
+def test_tet_potentials_vs_cubature():
+    rng = np.random.default_rng(4)
+    tet = np.array([[0.0, 0, 0], [6.0, 0.5, 0.2], [1.0, 5, 0.3], [0.5, 1, 4.0]])
+    pts = [tet.mean(0), tet.mean(0) + [0.5, -0.3, 0.2], np.array([9.0, 9, 9]),
+           0.5 * (tet[0] + tet[1]) + [0, 0, -0.7], tet[3] + [0.0, 0.0, 0.5]]
+    pts += list(tet.mean(0) + rng.normal(size=(4, 3)) * 3)
+    for r in pts:
+        inv, vec = tet_integrals(r, tet)
+        binv, bvec = _brute_tet(np.asarray(r, float), tet)
+        assert abs(inv - binv) < 2e-6 * abs(binv), (r, inv, binv)
+        # the vector integral cancels near the centroid: scale by |int 1/R| x diameter
+        scale = abs(binv) * np.max(np.linalg.norm(tet[:, None] - tet[None], axis=-1))
+        assert np.linalg.norm(vec - bvec) < 2e-6 * scale, (r, vec, bvec)
+
+
+# --------------------------------------------------------------------------- periodic Green
+K0 = 2 * np.pi / 500.0
+
+
+def _pgf_case():
+    th, ph, a, b = 0.5, 0.3, 200.0, 170.0
+    kx, ky = K0 * np.sin(th) * np.cos(ph), K0 * np.sin(th) * np.sin(ph)
+    rng = np.random.default_rng(1)
+    d = np.stack([rng.uniform(-a, a, 12), rng.uniform(-b, b, 12), rng.uniform(-60, 60, 12)], 1)
+    return kx, ky, a, b, d
+
+
+def test_ewald_independent_of_splitting():
+    kx, ky, a, b, d = _pgf_case()
+    g = PeriodicGreen(K0, kx, ky, a, b)
+    ref = g(d)
+    for f in (0.55, 1.9, 3.0):
+        alt = PeriodicGreen(K0, kx, ky, a, b, E=g.E * f)(d)
+        assert np.max(np.abs(alt - ref) / np.abs(ref)) < 1e-12
+
+
+def test_ewald_vs_floquet_series():
+    kx, ky, a, b, d = _pgf_case()
+    d[:, 2] = np.sign(d[:, 2]) * np.linspace(25, 90, len(d))
+    g = PeriodicGreen(K0, kx, ky, a, b)(d)
+    s = spectral_direct(d, K0, kx, ky, a, b, pq_max=45)
+    assert np.max(np.abs(g - s) / np.abs(s)) < 1e-12
+
+
+def test_ewald_vs_windowed_image_sum():
+    kx, ky, a, b, d = _pgf_case()
+    d = d[:3].copy()
+    d[0, 2] = 0.0
+    g = PeriodicGreen(K0, kx, ky, a, b)(d)
+    w = windowed_direct(d, K0, kx, ky, a, b, A=150 * a)
+    assert np.max(np.abs(g - w) / np.abs(w)) < 2e-5
+
+
+def test_ewald_bloch_and_free_space_limit():
+    kx, ky, a, b, d = _pgf_case()
+    g = PeriodicGreen(K0, kx, ky, a, b)
+    d2 = d.copy()
+    d2[:, 0] = -np.abs(d2[:, 0]) * 0.4
+    shifted = d2 + [a, 0, 0]
+    assert np.max(np.abs(g(shifted) - np.exp(-1j * kx * a) * g(d2)) / np.abs(g(d2))) < 1e-12
+    # a very large period: the image term of the cell dominates
+    A = 40123.0          # off the Rayleigh anomalies of the 500 nm wave
+    gl = PeriodicGreen(K0, 0.0, 0.0, A, A)
+    r = np.array([[3.0, 4.0, 12.0]])
+    R = 13.0
+    assert abs(gl(r)[0] - np.exp(-1j * K0 * R) / (4 * np.pi * R)) < 5e-3 * (1 / (4 * np.pi * R))
+
+
+def test_static_subtraction_continuous():
+    kx, ky, a, b, _ = _pgf_case()
+    g = PeriodicGreen(K0, kx, ky, a, b)
+    sub = np.zeros((1, len(g.images)), bool)
+    sub[0, g.image_index(0, 0)] = True
+    vals = [g(np.array([[r, 0.3 * r, -0.2 * r]]), subtract=sub)[0] for r in (1e-2, 1e-4, 1e-8, 0.0)]
+    assert abs(vals[0] - vals[3]) < 1e-4 * abs(vals[3])
+    assert abs(vals[2] - vals[3]) < 1e-9 * abs(vals[3])
+
+
+# --------------------------------------------------------------------------- topology
+def test_swg_topology_counts_and_flux():
+    cell = cellgen.config_slab()
+    topo = build_topology(cell)
+    assert topo["n"] == 936
+    assert np.sum(topo["kind"] == KIND_HALF) == 144
+    assert np.sum(topo["kind"] == KIND_PERIODIC) == 48
+    # unit normal flux: on T+ and T- the SWG component along the face normal is 1
+    P = topo["tet_verts"]
+    for n in range(0, topo["n"], 37):
+        tp, ip = topo["tp"][n], topo["ip"][n]
+        face = P[tp, [j for j in range(4) if j != ip]]
+        nrm = np.cross(face[1] - face[0], face[2] - face[0])
+        nrm /= np.linalg.norm(nrm)
+        if np.dot(nrm, face[0] - P[tp, ip]) < 0:
+            nrm = -nrm
+        x = face.mean(0)
+        fp = topo["area"][tp, ip] / (3 * topo["vol"][tp]) * (x - P[tp, ip])
+        assert abs(np.dot(fp, nrm) - 1) < 1e-12
+        if topo["tm"][n] >= 0:
+            tm, im = topo["tm"][n], topo["im"][n]
+            xm = x + topo["bshift"][n]
+            fm = -topo["area"][tm, im] / (3 * topo["vol"][tm]) * (xm - P[tm, im])
+            assert abs(np.dot(fm, nrm) - 1) < 1e-12
+            assert abs(topo["area"][tm, im] - topo["area"][tp, ip]) < 1e-9
+
+
+# --------------------------------------------------------------------------- physics pins
+@pytest.fixture(scope="module")
+def slab_runs():
+    out = {}
+    for nx, nz in ((3, 1), (6, 2)):
+        cell = cellgen.slab_cell(nx, nx, nz, 200.0, 200.0, 40.0, (4.0, 0.5))
+        out[(nx, nz)] = solve_cell(cell, 500.0, 0.0, 0.0)
+    return out
+
+
+def test_slab_matches_transfer_matrix(slab_runs):
+    R0, T0, A0 = tmm_rt([4 + 0.5j], [40.0], 500.0, 0.0, "TE")
+    fine, coarse = slab_runs[(6, 2)], slab_runs[(3, 1)]
+    for run in (fine, coarse):
+        assert run["residual"].max() < 1e-12
+        for p in range(2):
+            s = run["A"][p].sum() + run["R"][p] + run["T"][p]
+            assert abs(s - 1) < 1e-4
+    errA_f = abs(fine["A"][0, 0] - A0)
+    errA_c = abs(coarse["A"][0, 0] - A0)
+    assert errA_f < 0.005 and errA_f < errA_c
+    assert abs(fine["R"][0] - R0) < 0.01 and abs(fine["T"][0] - T0) < 0.01
+    # normal incidence: TE and TM are the same physical problem for a slab
+    assert abs(fine["A"][0, 0] - fine["A"][1, 0]) < 1e-9
+
+
+def test_slab_oblique_te_tm():
+    cell = cellgen.slab_cell(4, 4, 2, 200.0, 200.0, 40.0, (4.0, 0.5))
+    run = solve_cell(cell, 500.0, np.pi / 4, 0.0)
+    for p, pol in enumerate(("TE", "TM")):
+        R0, T0, A0 = tmm_rt([4 + 0.5j], [40.0], 500.0, np.pi / 4, pol)
+        assert abs(run["A"][p, 0] - A0) < 0.004
+        assert abs(run["R"][p] - R0) < 0.008
+        assert abs(run["A"][p, 0] + run["R"][p] + run["T"][p] - 1) < 1e-4
+
+
+def test_planted_surface_charge_sign_fails(monkeypatch):
+    """Surface charges only act when D has a normal component: oblique TM."""
+    from oracle import fill
+    cell = cellgen.slab_cell(3, 3, 1, 200.0, 200.0, 40.0, (4.0, 0.5))
+    R0, T0, A0 = tmm_rt([4 + 0.5j], [40.0], 500.0, np.pi / 4, "TM")
+    good = solve_cell(cell, 500.0, np.pi / 4, 0.0)
+    assert abs(good["T"][1] - T0) < 0.01 and abs(good["R"][1] - R0) < 0.01
+    monkeypatch.setattr(fill, "SURFACE_CHARGE_SIGN", -1.0)
+    bad = solve_cell(cell, 500.0, np.pi / 4, 0.0)
+    assert abs(bad["T"][1] - T0) > 0.2
+
+
+def test_reciprocity_single_material():
+    """Z(k_par) = Z(-k_par)^T for one material, exact to rounding.
+
+    Far pairs use symmetric product rules and near pairs average both
+    integration orders, so the discrete operator keeps the identity.
+    """
+    cell = cellgen.slab_cell(3, 2, 1, 150.0, 120.0, 30.0, (3.0, 0.7), jitter=0.1, seed=2)
+    topo = build_topology(cell)
+    th, ph = 0.6, 0.4
+    Zp, _ = assemble(Problem(topo, 480.0, th, ph, cell.eps(480.0)), with_rhs=False)
+    Zm, _ = assemble(Problem(topo, 480.0, th, ph + np.pi, cell.eps(480.0)), with_rhs=False)
+    scale = np.max(np.abs(Zp))
+    assert np.max(np.abs(Zp - Zm.T)) < 1e-12 * scale
+    assert np.max(np.abs(Zp - Zp.T)) > 1e-2 * scale          # oblique: not symmetric by itself
