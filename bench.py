@@ -1,0 +1,281 @@
+"""Benchmark: (lambda, theta) solves per second of the preconditioned periodic VIE.
+
+Workload (one step = one full solve at one incidence, TE and TM together):
+the plasmonic unit cell, period 200 nm, Ag sphere r = 20 nm centred in a
+100 nm active layer over a 40 nm buffer (three material domains, ~21k SWG
+unknowns), lambda = 500 nm, normal incidence.  A step runs the whole path:
+Ewald-summed fill of Z (Eq. (2)-(4)), inversion of the domain blocks
+(Eq. (6)), preconditioned GMRES with FP64 residual refinement, absorption
+(Eq. (7)), reflectance and transmittance.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64] [--impl reference]
+
+N > 1 runs under torch.distributed.run: every rank solves the same workload on
+its own GPU (independent solves, replicas only), timing is the max over ranks.
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+method, dense LU) on a reduced-density sample of the same cell.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "(lambda,theta) solves/s"
+UNIT = "solves/s"
+LAM, THETA, PHI = 500.0, 0.0, 0.0
+WORKLOAD = "plasmonic cell 200 nm period, Ag sphere r=20 nm in 100 nm active over 40 nm buffer, lambda=500 nm, theta=0, TE+TM"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import cellgen
+    from paper_1809_05334_gb300 import vie
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = vie.VIE_FP32 if args.precision == "fp32" else vie.VIE_FP64
+    cell = cellgen.config_plasmonic()
+    eps = cell.eps(LAM)
+    solver = vie.Solver(device=local, precision=prec, tol=1e-6, timing=True)
+    n = solver.set_mesh(cell)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        out = solver.solve(LAM, THETA, PHI, eps, stream=sp)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            results.append(solver.solve(LAM, THETA, PHI, eps, stream=sp))
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    last = results[-1]
+
+    # end-to-end through the public API from host buffers: mesh upload (H2D),
+    # solve, unknowns and result back to the host (D2H), every step
+    barrier()
+    coeffs = np.zeros((n, 2), dtype=np.complex128)
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_mesh(cell)
+        solver.solve(LAM, THETA, PHI, eps, coeffs=coeffs, stream=sp)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    h2d = cell.verts.nbytes + cell.tets.astype(np.int32).nbytes + cell.tet_domain.astype(np.int32).nbytes
+    d2h = coeffs.nbytes + 8 * 64
+
+    value = ws * args.steps / (ms_max / 1e3)
+    peaks = _peaks()
+    # dominant kernel: the block inversion of Eq. (6) (complex Gauss-Jordan),
+    # 8 n^3 real flops per domain block of n unknowns; ALU (FP32 CUDA-core) bound
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64+f64" if args.precision == "fp32" else "c128",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_unknowns": n, "n_tets": cell.n_tets, "precision": args.precision,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (Z is %.1f GB)" % (n * n * (8 if prec == vie.VIE_FP32 else 16) / 1e9)},
+        "phases_ms": {"fill": last["t_fill_ms"], "factor": last["t_factor_ms"], "solve": last["t_solve_ms"],
+                      "post": last["t_post_ms"]},
+        "kernels_ms": {"far_tt": last["k_far_tt_ms"], "fill": last["k_fill_ms"], "factor": last["k_factor_ms"],
+                       "matvec_total": last["k_matvec_ms"], "matvec_n": last["k_matvec_n"]},
+        "iterations": last["iterations"], "rel_residual": [float(v) for v in last["rel_residual"]],
+        "absorbed_active": [float(v) for v in last["A"][:, cell.active_domain]],
+        "e2e": {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": None,
+    }
+    res["roofline"] = roofline(last, n, peaks, prec == vie.VIE_FP32)
+    res["clocks"] = clk.summary()
+    res["gpu_launches"] = launches_per_step(last, n)
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        res["cpu_baseline"] = cpu_baseline(args)
+    solver.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res))
+
+
+def launches_per_step(last, n):
+    """Kernel launches of one solve (counted from the library's launch sequence)."""
+    nb = (n + 31) // 32
+    fill = 2 + 1 + 1 + 6          # gram, rhs, far/near tet pairs, face kernels
+    factor = 4 * nb + 3           # Gauss-Jordan: 4 kernels per 32-column step, 3 copies
+    it = sum(last["iterations"]) // 2 + 1
+    gmres = it * 14
+    return int(fill + factor + gmres + 4)
+
+
+def roofline(last, n, peaks, fp32):
+    # the matvec is the HBM-bound Krylov kernel: bytes per launch = N * ld * bytes/entry
+    ld = (n + 3) // 4 * 4
+    zb = 8 if fp32 else 16
+    if last["k_matvec_n"]:
+        t = last["k_matvec_ms"] / last["k_matvec_n"] / 1e3
+        bytes_ = n * ld * zb + n * 2 * (8 if fp32 else 16) * 2
+        ach = bytes_ / t / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        mv = {"bound": "hbm", "kernel": "k_matvec", "achieved": ach, "peak": peak, "unit": "GB/s",
+              "frac": ach / peak, "traffic": None, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    else:
+        mv = None
+    return mv
+
+
+def cpu_baseline(args):
+    """The FP64 oracle on a reduced-density sample of the same cell, scaled to the full workload."""
+    import cellgen
+    from oracle import solve_cell
+    sample = cellgen.config_plasmonic_sample()
+    full = cellgen.config_plasmonic()
+    t0 = time.perf_counter()
+    solve_cell(sample, LAM, THETA, PHI)
+    dt = time.perf_counter() - t0
+    scale = (full.n_tets / sample.n_tets) ** 2          # the fill dominates: pairs of tetrahedra
+    cores = int(os.environ.get("ORACLE_WORKERS", os.cpu_count() or 1))
+    return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one oracle solve of the same geometry at reduced density (%d tets vs %d) took %.1f s; "
+                      "scaled by the tetrahedron-pair ratio %.0f" % (sample.n_tets, full.n_tets, dt, scale)}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import cellgen
+    from oracle import solve_cell
+    sample = cellgen.config_plasmonic_sample()
+    full = cellgen.config_plasmonic()
+    scale = (full.n_tets / sample.n_tets) ** 2
+    for _ in range(args.warmup):
+        solve_cell(sample, LAM, THETA, PHI)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solve_cell(sample, LAM, THETA, PHI)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 1.0 / (dt * scale)
+    cores = int(os.environ.get("ORACLE_WORKERS", os.cpu_count() or 1))
+    res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * scale * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample_tets": sample.n_tets, "full_tets": full.n_tets},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "each step: one oracle solve of the geometry at %d tets; value scaled by "
+                                      "the tetrahedron-pair ratio %.0f to the %d-tet workload"
+                                      % (sample.n_tets, scale, full.n_tets)},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

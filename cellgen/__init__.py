@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "Cell", "grid_1d", "kuhn_mesh", "slab_cell", "layered_cell",
     "eps_ag_drude", "eps_active", "eps_buffer",
-    "config_slab", "config_plasmonic", "config_sweep_geometry", "small_cells",
+    "config_slab", "config_plasmonic", "config_plasmonic_sample", "config_sweep_geometry", "small_cells",
 ]
 
 
@@ -276,13 +276,22 @@ def config_slab():
     return slab_cell(6, 6, 2, 200.0, 200.0, 40.0, (4.0, 0.5))
 
 
-def config_plasmonic(seed=2, h_coarse=20.0, h_fine=8.5, h_z=20.0):
+def config_plasmonic(seed=2, h_coarse=28.0, h_fine=9.5, h_z=25.0):
     """Plasmonic cell: period 200 nm, Ag sphere r=20 nm centred in a 100 nm active
     layer over a 40 nm buffer (three material domains)."""
     return layered_cell(200.0, 200.0, [(40.0, "buffer"), (100.0, "active")],
                         spheres=[(100.0, 100.0, 90.0, 20.0, "ag")],
                         h_coarse=h_coarse, h_fine=h_fine, h_z=h_z, jitter=0.1, seed=seed,
                         name="plasmonic_200nm_r20")
+
+
+def config_plasmonic_sample(seed=2):
+    """The plasmonic geometry at a much lower density (378 tets): the bounded
+    sample on which the CPU oracle is timed."""
+    return layered_cell(200.0, 200.0, [(40.0, "buffer"), (100.0, "active")],
+                        spheres=[(100.0, 100.0, 90.0, 20.0, "ag")],
+                        h_coarse=67.0, h_fine=20.0, h_z=30.0, jitter=0.1, seed=seed, lateral_fine=False,
+                        name="plasmonic_200nm_r20_sample")
 
 
 def config_sweep_geometry(seed=3):
@@ -295,6 +304,10 @@ def small_cells():
     return {
         "slab_3x3x1": slab_cell(3, 3, 1, 200.0, 200.0, 40.0, (4.0, 0.5)),
         "slab_4x3x2_jit": slab_cell(4, 3, 2, 180.0, 150.0, 40.0, (3.0, 0.8), jitter=0.12, seed=11),
+        "plasmonic_tiny": layered_cell(60.0, 54.0, [(20.0, "buffer"), (40.0, "active")],
+                                       spheres=[(30.0, 27.0, 40.0, 13.0, "ag")],
+                                       h_coarse=20.0, h_fine=10.0, h_z=20.0, jitter=0.1, seed=7,
+                                       lateral_fine=False, name="plasmonic_tiny"),
         "plasmonic_mini": layered_cell(120.0, 120.0, [(30.0, "buffer"), (50.0, "active")],
                                        spheres=[(60.0, 60.0, 55.0, 15.0, "ag")],
                                        h_coarse=40.0, h_fine=15.0, h_z=30.0, jitter=0.1, seed=5,

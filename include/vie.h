@@ -1,0 +1,171 @@
+/*
+ * vie.h - C ABI of the GB300 preconditioned periodic volume-integral-equation solver.
+ *
+ * Method: He, Gu, Sha & Chen, "Efficient volumetric method of moments for
+ * modeling plasmonic thin-film solar cells with periodic structures"
+ * (arXiv:1809.05334).  One a x b unit cell of a periodic thin-film stack is
+ * meshed with tetrahedra; the flux density D is expanded in SWG functions
+ * (Sec. 2.1), the Galerkin impedance matrix of Eq. (2) is filled with the 2D
+ * periodic Green's function of Eq. (3)-(4), evaluated by Ewald's method
+ * (Sec. 2.2), the system is solved by GMRES with the domain-wise diagonal
+ * block preconditioner of Eq. (5)-(6) (Sec. 2.3), and the absorbed fraction
+ * of Eq. (7) is returned per material domain.
+ *
+ * Conventions
+ *  - Lengths in nm.  Permittivities use the physics sign (Im eps > 0 is lossy);
+ *    the library works internally in the exp(j w t) convention of the paper.
+ *  - Unknown n is the normal flux of D across face n divided by eps0.  Faces
+ *    are numbered in order of first appearance scanning tetrahedra t = 0.. and
+ *    local faces i = 0..3 (face i is opposite vertex i); T+ of an interior face
+ *    is the lower-numbered tetrahedron; a pair of lateral faces on x=0/x=a
+ *    (y=0/y=b) is one Bloch-periodic unknown with T+ on the x=0 (y=0) wall.
+ *  - Complex numbers are interleaved (re, im) doubles.
+ *  - All entry points are host functions.  Pointers are host pointers unless
+ *    the argument says "device".  Inputs are copied; the caller keeps
+ *    ownership of every buffer it passes.  Nothing is retained after return
+ *    except inside the opaque context.
+ *  - Errors are returned as negative vie_status codes; no exception crosses
+ *    the ABI.  Positive codes mean a result with a warning.  vie_last_error()
+ *    gives a one-line description of the last failure on a context.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef VIE_H
+#define VIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VIE_MAX_DOMAINS 8
+
+typedef struct vie_ctx vie_ctx;
+
+typedef enum {
+    VIE_OK = 0,
+    VIE_NOT_CONVERGED = 1,      /* result returned, residual above tolerance        */
+    VIE_EINVAL = -1,            /* bad argument                                      */
+    VIE_ENOMEM = -2,            /* device allocation failed                          */
+    VIE_ECUDA = -3,             /* CUDA runtime / launch error                       */
+    VIE_RAYLEIGH_ANOMALY = -4,  /* a Floquet mode is at grazing: g_p is singular     */
+    VIE_BAD_MESH = -6,          /* inverted tetrahedron or unmatched periodic walls  */
+    VIE_BREAKDOWN = -8          /* zero or non-finite pivot in a preconditioner block*/
+} vie_status;
+
+typedef enum {
+    VIE_FP64 = 0,   /* Z, Krylov vectors and products in FP64                        */
+    VIE_FP32 = 1    /* Z stored in FP32 (near-singular integrals in FP64), FP32
+                       GMRES inside FP64-residual iterative refinement           */
+} vie_precision;
+
+typedef struct {
+    int32_t precision;     /* vie_precision                                        */
+    int32_t use_precond;   /* 1: diagonal-block preconditioner of Eq. (6); 0: none  */
+    int32_t restart;       /* GMRES restart length (default 60)                    */
+    int32_t max_iter;      /* total GMRES iterations over all restarts (default 1000)*/
+    double  tol;           /* target FP64 relative residual ||b - Z x|| / ||b||     */
+    double  inner_tol;     /* FP32 inner GMRES tolerance of each refinement sweep   */
+    int32_t timing;        /* 1: record CUDA events around the main kernels and
+                              report their device times in vie_result.k_* (adds
+                              no work, only events on the solve stream)          */
+    int32_t reserved;
+} vie_options;
+
+typedef struct {
+    double  lambda_nm;                  /* vacuum wavelength                       */
+    double  theta;                      /* polar angle of incidence [rad]          */
+    double  phi;                        /* azimuth of the plane of incidence [rad] */
+    double  eps[2 * VIE_MAX_DOMAINS];   /* per-domain relative permittivity (re,im)*/
+    double *coeffs_out;                 /* optional [N][2 pol] complex (re,im): the
+                                           solved unknowns in canonical order; host
+                                           pointer, or device if coeffs_on_device */
+    int32_t coeffs_on_device;
+} vie_request;
+
+typedef struct {
+    int32_t status;                      /* vie_status of the solve                 */
+    int32_t n_unknowns;
+    int32_t iterations[2];               /* GMRES iterations, TE and TM             */
+    int32_t refinements;                 /* outer FP64 refinement sweeps            */
+    double  rel_residual[2];             /* final FP64 ||b - Z x|| / ||b||          */
+    double  absorbed[2][VIE_MAX_DOMAINS];/* fraction of incident power per domain   */
+    double  reflectance[2];
+    double  transmittance[2];
+    double  t_fill_ms, t_factor_ms, t_solve_ms, t_post_ms;   /* host wall time per phase */
+    /* device times from CUDA events on the solve stream (options.timing = 1):
+       k_far_tt_ms   the far tetrahedron-pair fill kernel (one launch)
+       k_fill_ms     the whole fill (all fill kernels)
+       k_factor_ms   the whole block inversion
+       k_matvec_ms   total of the Z matvec launches in GMRES, k_matvec_n launches */
+    double  k_far_tt_ms, k_fill_ms, k_factor_ms, k_matvec_ms;
+    int32_t k_matvec_n;
+    int32_t n_near_pairs;                /* near tetrahedron pairs of the mesh       */
+    int64_t far_pair_evals;              /* Green's-function evaluations of the far
+                                            tetrahedron-pair kernel (16 per pair)   */
+} vie_result;
+
+/* Fill *opt with defaults (FP32 with refinement, preconditioner on, tol 1e-6). */
+void vie_default_options(vie_options *opt);
+
+/* Create a context on CUDA device `device`.  opt may be NULL (defaults).
+   *out receives the context; returns VIE_OK or an error code. */
+int vie_create(vie_ctx **out, int device, const vie_options *opt);
+
+/* Replace the solver options of an existing context. */
+int vie_set_options(vie_ctx *ctx, const vie_options *opt);
+
+/* Mesh of one unit cell (Fig. 1): verts [n_verts][3] (nm), tets [n_tets][4]
+   positively oriented, tet_domain [n_tets] in 0..n_domains-1; period a x b;
+   active_domain = the domain whose absorption Eq. (7) reports.  The lateral
+   walls x=0/a and y=0/b must carry matching triangulations.  Builds the SWG
+   topology (Sec. 2.1) and the near-pair lists; keeps them on the device. */
+int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts,
+                 const int32_t *tets, int32_t n_tets,
+                 const int32_t *tet_domain, int32_t n_domains,
+                 double period_a, double period_b, int32_t active_domain);
+
+/* Number of SWG unknowns of the current mesh (0 before vie_set_mesh). */
+int32_t vie_num_unknowns(const vie_ctx *ctx);
+
+/* One solve at one incidence for TE and TM together: fill Eq. (2) with the
+   Ewald-summed g_p (Eq. (3)-(4)), factor the domain blocks (Eq. (6)), run
+   GMRES, compute Eq. (7) absorption per domain plus R and T.
+   stream: a cudaStream_t (may be NULL for the legacy default stream); the call
+   returns after the work on it has finished. */
+int vie_solve(vie_ctx *ctx, const vie_request *req, vie_result *res, void *stream);
+
+/* Parity entry points: the FP64 impedance matrix Z [N][N] (row-major, complex)
+   and right-hand side b [N][2] of Eq. (2) in canonical unknown order, copied
+   to host buffers owned by the caller.  They run the same fill kernels as
+   vie_solve in FP64. */
+int vie_fill_matrix(vie_ctx *ctx, const vie_request *req, double *Z_host, double *b_host, void *stream);
+
+/* Parity entry point: the matrix in the precision of the current options
+   (FP32 entries widened to double), canonical order. */
+int vie_fill_matrix_prec(vie_ctx *ctx, const vie_request *req, double *Z_host, void *stream);
+
+/* Complex erfcx(u) = exp(u^2) erfc(u) = w(j u) on the device for n host
+   arguments (Re u >= 0), in FP64 (precision VIE_FP64) or FP32 (VIE_FP32).
+   Used to check the Faddeeva evaluation of the Ewald series. */
+int vie_erfcx(vie_ctx *ctx, const double *u, double *out, int32_t n, int32_t precision);
+
+/* The Ewald-summed periodic Green's function g_p(d), Eq. (3), on the device
+   for n in-cell difference vectors d [n][3] (|dx| < a, |dy| < b, d != 0) at
+   the request's wavelength and incidence; out [n] complex. */
+int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out,
+              int32_t n, int32_t precision);
+
+/* Human-readable name of a status code; never NULL. */
+const char *vie_status_str(int status);
+
+/* Description of the last error on ctx (empty string if none); never NULL. */
+const char *vie_last_error(const vie_ctx *ctx);
+
+/* Free all device and host memory of the context. */
+void vie_destroy(vie_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIE_H */

@@ -23,7 +23,7 @@ physics-sign permittivities of the inputs are conjugated here.
 
 Discrete problem (shared as a definition with the CUDA path): element pairs
 whose centroid distance, for some lattice image (m, n) in {-1,0,1}^2, is below
-NEAR_FACTOR x (sum of the element radii) are *near*.  Far pairs use the degree-2
+NEAR_FACTOR x (sum of the element radii) x (1 + NEAR_MARGIN) are *near*.  Far pairs use the degree-2
 product rules.  Near pairs split g_p into the static part exp(j k_par.R)/(4 pi R)
 of every near image, integrated in closed form over the source element at the
 points of the degree-5 rule of the test element, plus the remainder integrated
@@ -41,6 +41,9 @@ from .potentials import tet_integrals, tri_integrals
 from .topology import KIND_HALF
 
 NEAR_FACTOR = 1.5
+# relative margin of the near test: exact ties (common on structured meshes)
+# must classify the same way whatever the rounding of the distance
+NEAR_MARGIN = 1e-9
 # Sign of the surface-charge terms.  Charge conservation fixes it to +1; the
 # tests set it to -1 (the sign printed for the kappa-gradient terms of Eq. (2))
 # to show that reading fails.
@@ -93,7 +96,7 @@ def _near_images(cx, rx, cy, ry, a, b):
     for k, (m, n) in enumerate(NEAR_IMAGES):
         R = np.array([m * a, n * b, 0.0])
         d = np.linalg.norm(cx[:, None, :] - cy[None, :, :] + R, axis=-1)
-        out[:, :, k] = d < NEAR_FACTOR * (rx[:, None] + ry[None, :])
+        out[:, :, k] = d < NEAR_FACTOR * (rx[:, None] + ry[None, :]) * (1.0 + NEAR_MARGIN)
     return out
 
 

@@ -1,0 +1,872 @@
+// C ABI of the periodic SWG VIE solver (declared in include/vie.h).
+//
+// vie_solve runs, on the caller's stream:
+//   fill   Eq. (2) with the Ewald-summed periodic Green's function (Sec. 2.2)
+//   factor the inverse of every domain block A_dd of Eq. (5)-(6)
+//   solve  GMRES on diag(A_dd^-1) Z x = diag(A_dd^-1) b, restarted; every restart
+//          recomputes the FP64 residual b - Z x (iterative refinement)
+//   post   absorbed fraction per domain (Eq. (7)), reflectance, transmittance
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "../../include/vie.h"
+#include "device_math.cuh"
+#include "fill.h"
+#include "linalg.h"
+#include "post.h"
+#include "vie_internal.h"
+
+using cplx = std::complex<double>;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, n ? n : 1);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+template <typename T>
+cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t st) {
+    cudaError_t e = b.ensure(sizeof(T) * v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    e = cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);   // host staging vectors are temporaries
+}
+
+}  // namespace
+
+struct vie_ctx {
+    int device = 0;
+    vie_options opt{};
+    std::string err;
+    bool have_mesh = false;
+    vie::Topology topo;
+    // mesh (device)
+    DevBuf tv, cen, vol, q5, far32, far64, fv, f5, farea, ffar32, ffar64, hf;
+    DevBuf bm_tt, bm_tf, bm_ft, bm_ff, n_tt, n_tf, n_ft, n_ff, tdom;
+    // request (device)
+    DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders;
+    // solve buffers
+    DevBuf Z, b, x, r, u, w, V, h, y, Minv, status, acc, J, rt, cout;
+    size_t ld = 0;
+    // CUDA events for options.timing
+    std::vector<cudaEvent_t> events;
+    size_t ev_used = 0;
+    ~vie_ctx() {
+        for (auto e : events) cudaEventDestroy(e);
+    }
+    cudaEvent_t event() {   // next event of the pool (nullptr when timing is off)
+        if (!opt.timing) return nullptr;
+        if (ev_used == events.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            events.push_back(e);
+        }
+        return events[ev_used++];
+    }
+};
+
+namespace {
+double ev_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0;
+    if (a && b && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) return ms;
+    return 0.0;
+}
+}  // namespace
+
+namespace {
+
+int fail(vie_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(expr)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? VIE_ENOMEM : VIE_ECUDA,        \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+constexpr double FP64_XCUT = 6.0;   // Ewald truncation: exp(-36) ~ 2e-16
+constexpr float FP32_XCUT = 4.2f;   // exp(-17.6) ~ 2e-8
+
+double erfi_series(double x) {
+    // erfi(x) = 2/sqrt(pi) sum x^(2n+1) / (n! (2n+1))
+    double term = x, sum = x;
+    for (int n = 1; n < 200; ++n) {
+        term *= x * x / n;
+        double add = term / (2 * n + 1);
+        sum += add;
+        if (std::fabs(add) < 1e-18 * std::fabs(sum)) break;
+    }
+    return 2.0 / std::sqrt(M_PI) * sum;
+}
+
+struct HostReq {
+    double k0, kx, ky, theta;
+    std::vector<cplx> eps, kap;          // per domain, exp(j w t) convention
+    std::vector<int32_t> perm;           // canonical unknown -> matrix row
+    std::vector<int> blk_off, blk_n;     // domain blocks (non-empty)
+    vie::EwaldTables ew;
+    std::vector<double> orders;          // [n][4]: k_tx, k_ty, k_z, is (0,0)
+    double pol[6], kinc[3];
+};
+
+int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
+    const vie::Topology &T = ctx->topo;
+    if (!(req->lambda_nm > 0) || !std::isfinite(req->lambda_nm)) return fail(ctx, VIE_EINVAL, "lambda must be > 0");
+    if (!(std::fabs(req->theta) < M_PI / 2)) return fail(ctx, VIE_EINVAL, "|theta| must be < pi/2");
+    H.k0 = 2.0 * M_PI / req->lambda_nm;
+    H.theta = req->theta;
+    H.kx = H.k0 * std::sin(req->theta) * std::cos(req->phi);
+    H.ky = H.k0 * std::sin(req->theta) * std::sin(req->phi);
+    H.kinc[0] = H.kx; H.kinc[1] = H.ky; H.kinc[2] = -H.k0 * std::cos(req->theta);
+    const double th = req->theta, ph = req->phi;
+    const double te[3] = {-std::sin(ph), std::cos(ph), 0.0};
+    const double tm[3] = {std::cos(th) * std::cos(ph), std::cos(th) * std::sin(ph), std::sin(th)};
+    for (int d = 0; d < 3; ++d) { H.pol[d] = te[d]; H.pol[3 + d] = tm[d]; }
+    H.eps.resize(T.n_dom);
+    H.kap.resize(T.n_dom);
+    for (int d = 0; d < T.n_dom; ++d) {
+        cplx e(req->eps[2 * d], -req->eps[2 * d + 1]);   // conjugate: exp(j w t)
+        if (!(std::abs(e) > 0) || !std::isfinite(std::abs(e))) return fail(ctx, VIE_EINVAL, "bad permittivity");
+        H.eps[d] = e;
+        H.kap[d] = 1.0 - 1.0 / e;
+    }
+    // domain of every unknown (interface faces: larger |eps|, ties to lower id), blocked order
+    std::vector<int> udom(T.N);
+    for (int n = 0; n < T.N; ++n) {
+        int dp = T.dom[T.tp[n]];
+        int dm = T.kind[n] == vie::KIND_HALF ? dp : T.dom[T.tm[n]];
+        double mp = std::abs(H.eps[dp]), mm = std::abs(H.eps[dm]);
+        udom[n] = (mm > mp || (mm == mp && dm < dp)) ? dm : dp;
+    }
+    H.perm.assign(T.N, 0);
+    int next = 0;
+    for (int d = 0; d < T.n_dom; ++d) {
+        int off = next;
+        for (int n = 0; n < T.N; ++n)
+            if (udom[n] == d) H.perm[n] = next++;
+        if (next > off) { H.blk_off.push_back(off); H.blk_n.push_back(next - off); }
+    }
+    // Ewald tables
+    vie::EwaldTables &E = H.ew;
+    std::memset(&E, 0, sizeof(E));
+    const double a = T.a, b = T.b, k0 = H.k0;
+    E.E = std::max(std::sqrt(M_PI / (a * b)), k0 / 6.0);
+    E.bb = k0 / (2.0 * E.E);
+    E.a = a; E.b = b;
+    E.xcut64 = FP64_XCUT;
+    E.xcut32 = FP32_XCUT;
+    const bool fp64 = ctx->opt.precision == VIE_FP64;
+    const double xc = fp64 ? FP64_XCUT : FP32_XCUT;
+    const int mm = (int)std::ceil(xc / (E.E * a)) + 2, nn = (int)std::ceil(xc / (E.E * b)) + 2;
+    int ni = 0;
+    for (int m = -mm; m <= mm; ++m)
+        for (int n = -nn; n <= nn; ++n) {
+            double dmin = std::hypot(std::max(std::abs(m) - 1, 0) * a, std::max(std::abs(n) - 1, 0) * b);
+            bool nearimg = std::abs(m) <= 1 && std::abs(n) <= 1;
+            if (dmin * E.E > xc && !nearimg) continue;
+            if (ni >= vie::MAX_IMG) return fail(ctx, VIE_EINVAL, "period too small for the image table");
+            double phs = H.kx * m * a + H.ky * n * b;
+            double f = std::exp(E.bb * E.bb) / (4.0 * M_PI);
+            double v[4] = {m * a, n * b, f * std::cos(phs), f * std::sin(phs)};
+            for (int q = 0; q < 4; ++q) { E.img64[ni][q] = v[q]; E.img32[ni][q] = (float)v[q]; }
+            if (nearimg) E.near_img[(m + 1) * 3 + (n + 1)] = ni;
+            ++ni;
+        }
+    E.n_img = ni;
+    const int pm = (int)std::ceil((2.0 * E.E * xc + std::fabs(H.kx)) * a / (2 * M_PI)) + 1;
+    const int qm = (int)std::ceil((2.0 * E.E * xc + std::fabs(H.ky)) * b / (2 * M_PI)) + 1;
+    int nm = 0;
+    H.orders.clear();
+    for (int p = -pm; p <= pm; ++p)
+        for (int q = -qm; q <= qm; ++q) {
+            double ktx = H.kx + 2 * M_PI * p / a, kty = H.ky + 2 * M_PI * q / b;
+            double kt2 = ktx * ktx + kty * kty;
+            double g2 = kt2 - k0 * k0;
+            if (std::fabs(g2) * std::max(a, b) * std::max(a, b) < 1e-10)
+                return fail(ctx, VIE_RAYLEIGH_ANOMALY, "a Floquet order is at grazing (Rayleigh anomaly)");
+            if (g2 < 0) H.orders.insert(H.orders.end(), {ktx, kty, std::sqrt(-g2), (p == 0 && q == 0) ? 1.0 : 0.0});
+            if (std::sqrt(kt2) > 2.0 * E.E * xc + k0) continue;
+            if (nm >= vie::MAX_MODE) return fail(ctx, VIE_EINVAL, "too many Floquet modes for the table");
+            cplx g = g2 >= 0 ? cplx(std::sqrt(g2), 0) : cplx(0, std::sqrt(-g2));
+            cplx ig = 1.0 / (4.0 * a * b * g);
+            double v[8] = {ktx, kty, g.real(), g.imag(), std::exp(-g2 / (4 * E.E * E.E)), ig.real(), ig.imag(), 0};
+            for (int c = 0; c < 8; ++c) { E.mode64[nm][c] = v[c]; E.mode32[nm][c] = (float)v[c]; }
+            ++nm;
+        }
+    E.n_mode = nm;
+    E.reg0_re = (E.E / (4 * M_PI)) * (2 * E.bb * erfi_series(E.bb) - 2.0 / std::sqrt(M_PI) * std::exp(E.bb * E.bb));
+    return VIE_OK;
+}
+
+// upload the per-request arrays and build the device views
+int upload_request(vie_ctx *ctx, const HostReq &H, vie::DevReq &q, cudaStream_t st) {
+    const vie::Topology &T = ctx->topo;
+    std::vector<int32_t> row(4 * (size_t)T.nt);
+    std::vector<double> coef(4 * (size_t)T.nt), wt(8 * (size_t)T.nt), kap(2 * (size_t)T.nt), ie(2 * (size_t)T.nt);
+    for (int t = 0; t < T.nt; ++t) {
+        cplx e = H.eps[T.dom[t]];
+        cplx k = H.kap[T.dom[t]];
+        kap[2 * t] = k.real(); kap[2 * t + 1] = k.imag();
+        cplx iv = 1.0 / e;
+        ie[2 * t] = iv.real(); ie[2 * t + 1] = iv.imag();
+        for (int i = 0; i < 4; ++i) {
+            size_t li = 4 * (size_t)t + i;
+            row[li] = H.perm[T.basis[li]];
+            coef[li] = T.sgn[li] * T.area[li] / (3.0 * T.vol[t]);
+            double sx = T.shift[li] == 1 ? T.a : 0.0, sy = T.shift[li] == 2 ? T.b : 0.0;
+            double phs = H.kx * sx + H.ky * sy;
+            wt[2 * li] = std::cos(phs);
+            wt[2 * li + 1] = std::sin(phs);
+        }
+    }
+    const int nf = (int)T.cf.size();
+    std::vector<int32_t> frow(std::max(nf, 1));
+    std::vector<double> qs(2 * (size_t)std::max(nf, 1));
+    for (int f = 0; f < nf; ++f) {
+        int n = T.cf[f];
+        frow[f] = H.perm[n];
+        cplx kp = H.kap[T.dom[T.tp[n]]];
+        cplx km = T.kind[n] == vie::KIND_HALF ? cplx(0, 0) : H.kap[T.dom[T.tm[n]]];
+        cplx s = km - kp;
+        qs[2 * f] = s.real(); qs[2 * f + 1] = s.imag();
+    }
+    CK(upload(ctx->row, row, st));
+    CK(upload(ctx->coef, coef, st));
+    CK(upload(ctx->wt, wt, st));
+    CK(upload(ctx->kap, kap, st));
+    CK(upload(ctx->ieps, ie, st));
+    CK(upload(ctx->frow, frow, st));
+    CK(upload(ctx->qs, qs, st));
+    CK(upload(ctx->perm, H.perm, st));
+    std::vector<double> pol(H.pol, H.pol + 6);
+    CK(upload(ctx->pol, pol, st));
+    std::vector<double> ord = H.orders;
+    if (ord.empty()) ord.assign(4, 0.0);
+    CK(upload(ctx->orders, ord, st));
+    CK(vie::upload_ewald(H.ew, st));
+    q.k0 = H.k0; q.kx = H.kx; q.ky = H.ky;
+    for (int d = 0; d < 3; ++d) q.kinc[d] = H.kinc[d];
+    for (int d = 0; d < 6; ++d) q.pol[d] = H.pol[d];
+    q.row = ctx->row.as<int32_t>();
+    q.coef = ctx->coef.as<double>();
+    q.wt = ctx->wt.as<double>();
+    q.kap = ctx->kap.as<double>();
+    q.ieps = ctx->ieps.as<double>();
+    q.frow = ctx->frow.as<int32_t>();
+    q.qs = ctx->qs.as<double>();
+    return VIE_OK;
+}
+
+vie::DevMesh dev_mesh(vie_ctx *ctx) {
+    const vie::Topology &T = ctx->topo;
+    vie::DevMesh m{};
+    m.nt = T.nt; m.N = T.N; m.nf = (int)T.cf.size(); m.nh = (int)T.hf.size();
+    m.a = T.a; m.b = T.b;
+    m.tv = ctx->tv.as<double>(); m.cen = ctx->cen.as<double>(); m.vol = ctx->vol.as<double>();
+    m.q5 = ctx->q5.as<double>(); m.far32 = ctx->far32.as<float>(); m.far64 = ctx->far64.as<double>();
+    m.fv = ctx->fv.as<double>(); m.f5 = ctx->f5.as<double>(); m.farea = ctx->farea.as<double>();
+    m.ffar32 = ctx->ffar32.as<float>(); m.ffar64 = ctx->ffar64.as<double>(); m.hf = ctx->hf.as<int32_t>();
+    m.bm_tt = ctx->bm_tt.as<uint32_t>(); m.bm_tf = ctx->bm_tf.as<uint32_t>();
+    m.bm_ft = ctx->bm_ft.as<uint32_t>(); m.bm_ff = ctx->bm_ff.as<uint32_t>();
+    m.near_tt = ctx->n_tt.as<vie::NearPair>(); m.near_tf = ctx->n_tf.as<vie::NearPair>();
+    m.near_ft = ctx->n_ft.as<vie::NearPair>(); m.near_ff = ctx->n_ff.as<vie::NearPair>();
+    m.n_tt = (int)T.near_tt.size(); m.n_tf = (int)T.near_tf.size();
+    m.n_ft = (int)T.near_ft.size(); m.n_ff = (int)T.near_ff.size();
+    return m;
+}
+
+struct Timing {
+    cudaEvent_t fill0 = nullptr, fill1 = nullptr, far0 = nullptr, far1 = nullptr, fac0 = nullptr, fac1 = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> mv;
+};
+
+template <typename TZ>
+int fill(vie_ctx *ctx, const vie::DevMesh &m, const vie::DevReq &q, bool with_rhs, cudaStream_t st,
+         Timing *tm = nullptr) {
+    const size_t N = (size_t)ctx->topo.N;
+    ctx->ld = (N + 3) / 4 * 4;
+    CK(ctx->Z.ensure(sizeof(TZ) * 2 * ctx->ld * N));
+    if (with_rhs) CK(ctx->b.ensure(sizeof(double) * 4 * N));
+    if (tm && tm->fill0) CK(cudaEventRecord(tm->fill0, st));
+    CK(vie::launch_fill<TZ>(m, q, ctx->Z.as<TZ>(), ctx->ld, with_rhs ? ctx->b.as<double>() : nullptr, st,
+                            tm ? tm->far0 : nullptr, tm ? tm->far1 : nullptr));
+    if (tm && tm->fill1) CK(cudaEventRecord(tm->fill1, st));
+    return VIE_OK;
+}
+
+// M^-1 applied block by block: out[blk] = Minv_d in[blk]
+template <typename TV>
+int precond_apply(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const std::vector<size_t> &mld,
+                  const TV *in, TV *out, cudaStream_t st) {
+    for (size_t k = 0; k < H.blk_off.size(); ++k) {
+        const float *Mi = ctx->Minv.as<float>() + 2 * moff[k];
+        CK((vie::matvec<float, TV, TV>(Mi, mld[k], H.blk_n[k], H.blk_n[k], in + 4 * (size_t)H.blk_off[k],
+                                        out + 4 * (size_t)H.blk_off[k], TV(1), false, st)));
+    }
+    return VIE_OK;
+}
+
+template <typename TZ, typename TV>
+int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const std::vector<size_t> &mld,
+          vie_result *res, cudaStream_t st, Timing &tm) {
+    const int N = ctx->topo.N;
+    const int m = std::max(2, ctx->opt.restart);
+    const bool pre = ctx->opt.use_precond != 0;
+    const double tol = ctx->opt.tol;
+    const double inner_tol = std::is_same<TV, float>::value ? std::max(ctx->opt.inner_tol, 1e-6) : tol * 0.1;
+    const size_t vs = 4 * (size_t)N;     // stride of one basis vector (two rhs)
+    CK(ctx->x.ensure(sizeof(double) * vs));
+    CK(ctx->r.ensure(sizeof(double) * vs));
+    CK(ctx->u.ensure(sizeof(TV) * vs));
+    CK(ctx->w.ensure(sizeof(TV) * vs));
+    CK(ctx->V.ensure(sizeof(TV) * vs * (m + 1)));
+    CK(ctx->h.ensure(sizeof(double) * 4 * (m + 2)));
+    CK(ctx->y.ensure(sizeof(double) * 4 * (m + 1)));
+    double *x = ctx->x.as<double>(), *r = ctx->r.as<double>(), *hd = ctx->h.as<double>();
+    TV *u = ctx->u.as<TV>(), *w = ctx->w.as<TV>(), *V = ctx->V.as<TV>();
+    const TZ *Z = ctx->Z.as<TZ>();
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * vs, st));
+    std::vector<double> hh(4 * (m + 2));
+    auto norms2 = [&](const double *vec, double out[2]) -> int {
+        CK(vie::dots<double>(vec, 0, 1, vec, N, hd, st));
+        CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        out[0] = std::sqrt(std::max(hh[0], 0.0));
+        out[1] = std::sqrt(std::max(hh[2], 0.0));
+        return VIE_OK;
+    };
+    double bn[2];
+    if (int e = norms2(ctx->b.as<double>(), bn)) return e;
+    for (int p = 0; p < 2; ++p) if (!(bn[p] > 0)) bn[p] = 1.0;
+    int iters[2] = {0, 0};
+    int total = 0, sweeps = 0;
+    double rel[2] = {1, 1};
+    while (true) {
+        // FP64 residual r = b - Z x
+        CK(cudaMemcpyAsync(r, ctx->b.p, sizeof(double) * vs, cudaMemcpyDeviceToDevice, st));
+        CK((vie::matvec<TZ, double, double>(Z, ctx->ld, N, N, x, r, -1.0, true, st)));
+        double rn[2];
+        if (int e = norms2(r, rn)) return e;
+        rel[0] = rn[0] / bn[0];
+        rel[1] = rn[1] / bn[1];
+        bool active[2] = {rel[0] > tol, rel[1] > tol};
+        if ((!active[0] && !active[1]) || total >= ctx->opt.max_iter) break;
+        ++sweeps;
+        // u = r / |r| (per rhs), v0 = M^-1 u
+        double s[4] = {rn[0] > 0 ? 1.0 / rn[0] : 0.0, 0.0, rn[1] > 0 ? 1.0 / rn[1] : 0.0, 0.0};
+        if (!active[0]) s[0] = 0;
+        if (!active[1]) s[2] = 0;
+        CK((vie::scale<double, TV>(r, u, N, s, st)));
+        if (pre) { if (int e = precond_apply<TV>(ctx, H, moff, mld, u, w, st)) return e; }
+        else CK(cudaMemcpyAsync(w, u, sizeof(TV) * vs, cudaMemcpyDeviceToDevice, st));
+        CK(vie::dots<TV>(w, 0, 1, w, N, hd, st));
+        CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double beta[2] = {std::sqrt(hh[0]), std::sqrt(hh[2])};
+        double s0[4] = {beta[0] > 0 ? 1.0 / beta[0] : 0.0, 0, beta[1] > 0 ? 1.0 / beta[1] : 0.0, 0};
+        CK((vie::scale<TV, TV>(w, V, N, s0, st)));
+        std::vector<cplx> Hm[2], g[2], cs[2], sn[2];
+        for (int p = 0; p < 2; ++p) {
+            Hm[p].assign((size_t)(m + 1) * m, cplx(0));
+            g[p].assign(m + 1, cplx(0));
+            cs[p].assign(m, cplx(0));
+            sn[p].assign(m, cplx(0));
+            g[p][0] = beta[p];
+        }
+        int kused[2] = {0, 0};
+        bool inner_active[2] = {active[0] && beta[0] > 0, active[1] && beta[1] > 0};
+        for (int k = 0; k < m; ++k) {
+            if (!inner_active[0] && !inner_active[1]) break;
+            TV *vk = V + vs * k;
+            TV *vn = V + vs * (k + 1);
+            cudaEvent_t e0 = ctx->event(), e1 = ctx->event();
+            if (e0) CK(cudaEventRecord(e0, st));
+            CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st)));
+            if (e1) { CK(cudaEventRecord(e1, st)); tm.mv.push_back({e0, e1}); }
+            if (pre) { if (int e = precond_apply<TV>(ctx, H, moff, mld, u, vn, st)) return e; }
+            // classical Gram-Schmidt, twice
+            std::vector<double> hsum(4 * (k + 1), 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
+                CK(vie::dots<TV>(V, vs, k + 1, vn, N, hd, st));
+                CK(vie::subtract<TV>(V, vs, k + 1, hd, vn, N, st));
+                CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4 * (k + 1), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                for (int i = 0; i < 4 * (k + 1); ++i) hsum[i] += hh[i];
+            }
+            CK(vie::dots<TV>(vn, 0, 1, vn, N, hd, st));
+            CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            double hn[2] = {std::sqrt(std::max(hh[0], 0.0)), std::sqrt(std::max(hh[2], 0.0))};
+            double sc[4] = {0, 0, 0, 0};
+            for (int p = 0; p < 2; ++p) {
+                if (!inner_active[p]) continue;
+                cplx *Hc = &Hm[p][(size_t)k * (m + 1)];   // column k
+                for (int i = 0; i <= k; ++i) Hc[i] = cplx(hsum[4 * i + 2 * p], hsum[4 * i + 2 * p + 1]);
+                Hc[k + 1] = hn[p];
+                for (int i = 0; i < k; ++i) {   // previous rotations
+                    cplx t = std::conj(cs[p][i]) * Hc[i] + std::conj(sn[p][i]) * Hc[i + 1];
+                    Hc[i + 1] = -sn[p][i] * Hc[i] + cs[p][i] * Hc[i + 1];
+                    Hc[i] = t;
+                }
+                double den = std::hypot(std::abs(Hc[k]), std::abs(Hc[k + 1]));
+                if (den == 0) { cs[p][k] = 1; sn[p][k] = 0; }
+                else { cs[p][k] = Hc[k] / den; sn[p][k] = Hc[k + 1] / den; }
+                Hc[k] = den;
+                Hc[k + 1] = 0;
+                g[p][k + 1] = -sn[p][k] * g[p][k];
+                g[p][k] = std::conj(cs[p][k]) * g[p][k];
+                kused[p] = k + 1;
+                ++iters[p];
+                if (std::abs(g[p][k + 1]) <= inner_tol * beta[p] || hn[p] <= 1e-300) inner_active[p] = false;
+                if (hn[p] > 0) sc[2 * p] = 1.0 / hn[p];
+            }
+            ++total;
+            if (total >= ctx->opt.max_iter) inner_active[0] = inner_active[1] = false;
+            CK((vie::scale<TV, TV>(vn, vn, N, sc, st)));
+        }
+        // y = H^-1 g, x += |r| V y
+        int kmax = std::max(kused[0], kused[1]);
+        std::vector<double> yv(4 * (size_t)std::max(kmax, 1), 0.0);
+        for (int p = 0; p < 2; ++p) {
+            int kk = kused[p];
+            std::vector<cplx> yy(kk);
+            for (int i = kk - 1; i >= 0; --i) {
+                cplx sacc = g[p][i];
+                for (int j = i + 1; j < kk; ++j) sacc -= Hm[p][(size_t)j * (m + 1) + i] * yy[j];
+                yy[i] = sacc / Hm[p][(size_t)i * (m + 1) + i];
+            }
+            for (int i = 0; i < kk; ++i) {
+                cplx v = yy[i] * rn[p];
+                yv[4 * i + 2 * p] = v.real();
+                yv[4 * i + 2 * p + 1] = v.imag();
+            }
+        }
+        if (kmax > 0) {
+            CK(cudaMemcpyAsync(ctx->y.p, yv.data(), sizeof(double) * 4 * kmax, cudaMemcpyHostToDevice, st));
+            CK(vie::combine<TV>(V, vs, kmax, ctx->y.as<double>(), x, N, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        if (kmax == 0) break;
+    }
+    res->iterations[0] = iters[0];
+    res->iterations[1] = iters[1];
+    res->refinements = sweeps;
+    res->rel_residual[0] = rel[0];
+    res->rel_residual[1] = rel[1];
+    return (rel[0] <= tol && rel[1] <= tol) ? VIE_OK : VIE_NOT_CONVERGED;
+}
+
+template <typename TZ>
+int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vector<size_t> &mld, cudaStream_t st) {
+    size_t tot = 0;
+    moff.clear();
+    mld.clear();
+    for (size_t k = 0; k < H.blk_n.size(); ++k) {
+        size_t l = ((size_t)H.blk_n[k] + 3) / 4 * 4;
+        moff.push_back(tot);
+        mld.push_back(l);
+        tot += l * (size_t)H.blk_n[k];
+    }
+    CK(ctx->Minv.ensure(sizeof(float) * 2 * std::max<size_t>(tot, 1)));
+    CK(ctx->status.ensure(sizeof(int)));
+    CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
+    for (size_t k = 0; k < H.blk_n.size(); ++k) {
+        float *B = ctx->Minv.as<float>() + 2 * moff[k];
+        CK((vie::copy_block<TZ, float>(ctx->Z.as<TZ>(), ctx->ld, H.blk_off[k], H.blk_n[k], B, mld[k], st)));
+        CK(vie::gj_invert<float>(B, mld[k], H.blk_n[k], ctx->status.as<int>(), st));
+    }
+    int stat = 0;
+    CK(cudaMemcpyAsync(&stat, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (stat) return fail(ctx, VIE_BREAKDOWN, "zero or non-finite pivot while inverting a domain block");
+    return VIE_OK;
+}
+
+template <typename TZ, typename TV>
+int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream_t st) {
+    using clk = std::chrono::steady_clock;
+    HostReq H;
+    if (int e = prepare(ctx, req, H)) return e;
+    vie::DevMesh m = dev_mesh(ctx);
+    vie::DevReq q{};
+    if (int e = upload_request(ctx, H, q, st)) return e;
+    ctx->ev_used = 0;
+    Timing tm;
+    tm.fill0 = ctx->event(); tm.fill1 = ctx->event(); tm.far0 = ctx->event(); tm.far1 = ctx->event();
+    tm.fac0 = ctx->event(); tm.fac1 = ctx->event();
+    auto t0 = clk::now();
+    if (int e = fill<TZ>(ctx, m, q, true, st, &tm)) return e;
+    CK(cudaStreamSynchronize(st));
+    auto t1 = clk::now();
+    std::vector<size_t> moff, mld;
+    if (ctx->opt.use_precond) {
+        if (tm.fac0) CK(cudaEventRecord(tm.fac0, st));
+        if (int e = factor<TZ>(ctx, H, moff, mld, st)) return e;
+        if (tm.fac1) { CK(cudaEventRecord(tm.fac1, st)); CK(cudaStreamSynchronize(st)); }
+    }
+    auto t2 = clk::now();
+    int stat = gmres<TZ, TV>(ctx, H, moff, mld, res, st, tm);
+    if (stat < 0) return stat;
+    auto t3 = clk::now();
+    // post-processing
+    const int nd = ctx->topo.n_dom;
+    const int n_orders = (int)H.orders.size() / 4;
+    CK(ctx->acc.ensure(sizeof(double) * 2 * nd));
+    CK(ctx->J.ensure(sizeof(double) * 24 * std::max(n_orders, 1)));
+    CK(ctx->rt.ensure(sizeof(double) * 4));
+    const double norm = H.k0 / (ctx->topo.a * ctx->topo.b * std::cos(H.theta));
+    CK(vie::launch_post(m, q, ctx->x.as<double>(), ctx->tdom.as<int32_t>(), nd, norm, ctx->orders.as<double>(),
+                        n_orders, ctx->topo.a, ctx->topo.b, H.k0 * std::cos(H.theta), ctx->pol.as<double>(),
+                        ctx->acc.as<double>(), ctx->J.as<double>(), ctx->rt.as<double>(), st));
+    std::vector<double> acc(2 * nd), rt(4);
+    CK(cudaMemcpyAsync(acc.data(), ctx->acc.p, sizeof(double) * 2 * nd, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rt.data(), ctx->rt.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+    if (req->coeffs_out) {
+        const size_t bytes = sizeof(double) * 4 * (size_t)ctx->topo.N;
+        if (req->coeffs_on_device) {
+            CK(vie::launch_unpermute(ctx->x.as<double>(), ctx->perm.as<int32_t>(), ctx->topo.N, req->coeffs_out, st));
+        } else {
+            CK(ctx->cout.ensure(bytes));
+            CK(vie::launch_unpermute(ctx->x.as<double>(), ctx->perm.as<int32_t>(), ctx->topo.N, ctx->cout.as<double>(), st));
+            CK(cudaMemcpyAsync(req->coeffs_out, ctx->cout.p, bytes, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    auto t4 = clk::now();
+    for (int p = 0; p < 2; ++p) {
+        for (int d = 0; d < nd; ++d) res->absorbed[p][d] = acc[p * nd + d];
+        res->reflectance[p] = rt[2 * p];
+        res->transmittance[p] = rt[2 * p + 1];
+    }
+    auto ms = [](clk::time_point a, clk::time_point b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
+    res->t_fill_ms = ms(t0, t1);
+    res->t_factor_ms = ms(t1, t2);
+    res->t_solve_ms = ms(t2, t3);
+    res->t_post_ms = ms(t3, t4);
+    res->n_unknowns = ctx->topo.N;
+    res->n_near_pairs = (int32_t)ctx->topo.near_tt.size();
+    res->far_pair_evals = 16 * ((int64_t)ctx->topo.nt * ctx->topo.nt - (int64_t)ctx->topo.near_tt.size());
+    if (ctx->opt.timing) {
+        res->k_far_tt_ms = ev_ms(tm.far0, tm.far1);
+        res->k_fill_ms = ev_ms(tm.fill0, tm.fill1);
+        res->k_factor_ms = ev_ms(tm.fac0, tm.fac1);
+        double s = 0;
+        for (auto &p : tm.mv) s += ev_ms(p.first, p.second);
+        res->k_matvec_ms = s;
+        res->k_matvec_n = (int32_t)tm.mv.size();
+    }
+    res->status = stat;
+    return stat;
+}
+
+void default_opts(vie_options *o) {
+    o->precision = VIE_FP32;
+    o->use_precond = 1;
+    o->restart = 60;
+    o->max_iter = 1000;
+    o->tol = 1e-6;
+    o->inner_tol = 1e-4;
+    o->timing = 0;
+    o->reserved = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vie_default_options(vie_options *opt) {
+    if (opt) default_opts(opt);
+}
+
+int vie_create(vie_ctx **out, int device, const vie_options *opt) {
+    if (!out) return VIE_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return VIE_ECUDA;
+    vie_ctx *ctx = new (std::nothrow) vie_ctx();
+    if (!ctx) return VIE_ENOMEM;
+    ctx->device = device;
+    default_opts(&ctx->opt);
+    if (opt) ctx->opt = *opt;
+    if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return VIE_ECUDA; }
+    if (vie::upload_constants() != cudaSuccess || vie::upload_post_constants() != cudaSuccess) {
+        delete ctx;
+        return VIE_ECUDA;
+    }
+    *out = ctx;
+    return VIE_OK;
+}
+
+int vie_set_options(vie_ctx *ctx, const vie_options *opt) {
+    if (!ctx || !opt) return VIE_EINVAL;
+    if (opt->precision != VIE_FP64 && opt->precision != VIE_FP32) return fail(ctx, VIE_EINVAL, "unknown precision");
+    if (opt->restart < 2 || opt->max_iter < 1 || !(opt->tol > 0)) return fail(ctx, VIE_EINVAL, "bad solver options");
+    ctx->opt = *opt;
+    return VIE_OK;
+}
+
+int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32_t *tets, int32_t n_tets,
+                 const int32_t *tet_domain, int32_t n_domains, double period_a, double period_b,
+                 int32_t active_domain) {
+    if (!ctx || !verts || !tets || !tet_domain) return VIE_EINVAL;
+    if (n_domains < 1 || n_domains > VIE_MAX_DOMAINS) return fail(ctx, VIE_EINVAL, "n_domains out of range");
+    if (active_domain < 0 || active_domain >= n_domains) return fail(ctx, VIE_EINVAL, "active_domain out of range");
+    cudaSetDevice(ctx->device);
+    ctx->have_mesh = false;
+    std::string e = vie::build_topology(verts, n_verts, tets, n_tets, tet_domain, n_domains, period_a, period_b,
+                                        active_domain, ctx->topo);
+    if (!e.empty()) return fail(ctx, e.find("range") != std::string::npos ? VIE_EINVAL : VIE_BAD_MESH, e);
+    const vie::Topology &T = ctx->topo;
+    cudaStream_t st = 0;
+    // quadrature points
+    double b2[4][4], w2[4], b5[14][4], w5[14], c2[3][3], cw2[3], c5[7][3], cw5[7];
+    vie::tet_rule2(b2, w2);
+    vie::tet_rule5(b5, w5);
+    vie::tri_rule2(c2, cw2);
+    vie::tri_rule5(c5, cw5);
+    std::vector<double> q5(42 * (size_t)T.nt), far64(28 * (size_t)T.nt);
+    for (int t = 0; t < T.nt; ++t) {
+        const double *P = &T.tv[12 * (size_t)t];
+        for (int k = 0; k < 14; ++k)
+            for (int d = 0; d < 3; ++d) {
+                double s = 0;
+                for (int j = 0; j < 4; ++j) s += b5[k][j] * P[3 * j + d];
+                q5[42 * (size_t)t + 3 * k + d] = s;
+            }
+        double *F = &far64[28 * (size_t)t];
+        for (int k = 0; k < 4; ++k)
+            for (int d = 0; d < 3; ++d) {
+                double s = 0;
+                for (int j = 0; j < 4; ++j) s += b2[k][j] * P[3 * j + d];
+                F[3 * k + d] = s;
+            }
+        for (int d = 0; d < 3; ++d) F[12 + d] = T.cen[3 * t + d];
+        for (int i = 0; i < 4; ++i)
+            for (int d = 0; d < 3; ++d) F[15 + 3 * i + d] = P[3 * i + d] - T.cen[3 * t + d];
+        F[27] = T.vol[t] * 0.25;
+    }
+    std::vector<float> far32(far64.begin(), far64.end());
+    const int nf = (int)T.cf.size();
+    std::vector<double> f5(21 * (size_t)std::max(nf, 1)), ffar64(12 * (size_t)std::max(nf, 1), 0.0),
+        farea(std::max(nf, 1));
+    for (int f = 0; f < nf; ++f) {
+        const double *P = &T.fv[9 * (size_t)f];
+        double e1[3] = {P[3] - P[0], P[4] - P[1], P[5] - P[2]}, e2[3] = {P[6] - P[0], P[7] - P[1], P[8] - P[2]};
+        double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double A = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        farea[f] = A;
+        for (int k = 0; k < 7; ++k)
+            for (int d = 0; d < 3; ++d) {
+                double s = 0;
+                for (int j = 0; j < 3; ++j) s += c5[k][j] * P[3 * j + d];
+                f5[21 * (size_t)f + 3 * k + d] = s;
+            }
+        for (int k = 0; k < 3; ++k)
+            for (int d = 0; d < 3; ++d) {
+                double s = 0;
+                for (int j = 0; j < 3; ++j) s += c2[k][j] * P[3 * j + d];
+                ffar64[12 * (size_t)f + 3 * k + d] = s;
+            }
+        ffar64[12 * (size_t)f + 9] = A / 3.0;
+    }
+    std::vector<float> ffar32(ffar64.begin(), ffar64.end());
+    const int nh = (int)T.hf.size();
+    auto bitmap = [](const std::vector<vie::NearPair> &L, size_t nx, size_t ny) {
+        std::vector<uint32_t> bm((nx * ny + 31) / 32 + 1, 0u);
+        for (auto &p : L) {
+            size_t i = (size_t)p.x * ny + p.y;
+            bm[i >> 5] |= 1u << (i & 31);
+        }
+        return bm;
+    };
+    auto nz = [](std::vector<vie::NearPair> v) { if (v.empty()) v.push_back({0, 0, 0, 0}); return v; };
+    std::vector<int32_t> hf = T.hf;
+    if (hf.empty()) hf.push_back(0);
+    std::vector<double> fv = T.fv;
+    if (fv.empty()) fv.assign(9, 0.0);
+    CK(upload(ctx->tv, T.tv, st));
+    CK(upload(ctx->cen, T.cen, st));
+    CK(upload(ctx->vol, T.vol, st));
+    CK(upload(ctx->q5, q5, st));
+    CK(upload(ctx->far64, far64, st));
+    CK(upload(ctx->far32, far32, st));
+    CK(upload(ctx->fv, fv, st));
+    CK(upload(ctx->f5, f5, st));
+    CK(upload(ctx->farea, farea, st));
+    CK(upload(ctx->ffar64, ffar64, st));
+    CK(upload(ctx->ffar32, ffar32, st));
+    CK(upload(ctx->hf, hf, st));
+    CK(upload(ctx->tdom, T.dom, st));
+    CK(upload(ctx->bm_tt, bitmap(T.near_tt, T.nt, T.nt), st));
+    CK(upload(ctx->bm_tf, bitmap(T.near_tf, T.nt, nf), st));
+    CK(upload(ctx->bm_ft, bitmap(T.near_ft, nh, T.nt), st));
+    CK(upload(ctx->bm_ff, bitmap(T.near_ff, nh, nf), st));
+    CK(upload(ctx->n_tt, nz(T.near_tt), st));
+    CK(upload(ctx->n_tf, nz(T.near_tf), st));
+    CK(upload(ctx->n_ft, nz(T.near_ft), st));
+    CK(upload(ctx->n_ff, nz(T.near_ff), st));
+    ctx->have_mesh = true;
+    return VIE_OK;
+}
+
+int32_t vie_num_unknowns(const vie_ctx *ctx) { return (ctx && ctx->have_mesh) ? ctx->topo.N : 0; }
+
+int vie_solve(vie_ctx *ctx, const vie_request *req, vie_result *res, void *stream) {
+    if (!ctx || !req || !res) return VIE_EINVAL;
+    if (!ctx->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
+    std::memset(res, 0, sizeof(*res));
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = ctx->opt.precision == VIE_FP64 ? solve_impl<double, double>(ctx, req, res, st)
+                                           : solve_impl<float, float>(ctx, req, res, st);
+    res->status = r;
+    return r;
+}
+
+int vie_fill_matrix(vie_ctx *ctx, const vie_request *req, double *Z_host, double *b_host, void *stream) {
+    if (!ctx || !req || !Z_host) return VIE_EINVAL;
+    if (!ctx->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    vie_options saved = ctx->opt;
+    ctx->opt.precision = VIE_FP64;
+    HostReq H;
+    int e = prepare(ctx, req, H);
+    ctx->opt = saved;
+    if (e) return e;
+    vie::DevMesh m = dev_mesh(ctx);
+    vie::DevReq q{};
+    if ((e = upload_request(ctx, H, q, st))) return e;
+    if ((e = fill<double>(ctx, m, q, true, st))) return e;
+    const int N = ctx->topo.N;
+    std::vector<double> Zp((size_t)2 * ctx->ld * N), bp(4 * (size_t)N);
+    CK(cudaMemcpyAsync(Zp.data(), ctx->Z.p, sizeof(double) * Zp.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(bp.data(), ctx->b.p, sizeof(double) * bp.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < N; ++i) {
+        size_t ri = H.perm[i];
+        for (int j = 0; j < N; ++j) {
+            size_t rj = H.perm[j];
+            Z_host[2 * ((size_t)i * N + j)] = Zp[2 * (ri * ctx->ld + rj)];
+            Z_host[2 * ((size_t)i * N + j) + 1] = Zp[2 * (ri * ctx->ld + rj) + 1];
+        }
+        if (b_host)
+            for (int k = 0; k < 4; ++k) b_host[4 * (size_t)i + k] = bp[4 * ri + k];
+    }
+    return VIE_OK;
+}
+
+int vie_fill_matrix_prec(vie_ctx *ctx, const vie_request *req, double *Z_host, void *stream) {
+    if (!ctx || !req || !Z_host) return VIE_EINVAL;
+    if (!ctx->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
+    if (ctx->opt.precision == VIE_FP64) return vie_fill_matrix(ctx, req, Z_host, nullptr, stream);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    HostReq H;
+    int e = prepare(ctx, req, H);
+    if (e) return e;
+    vie::DevMesh m = dev_mesh(ctx);
+    vie::DevReq q{};
+    if ((e = upload_request(ctx, H, q, st))) return e;
+    if ((e = fill<float>(ctx, m, q, false, st))) return e;
+    const int N = ctx->topo.N;
+    std::vector<float> Zp((size_t)2 * ctx->ld * N);
+    CK(cudaMemcpyAsync(Zp.data(), ctx->Z.p, sizeof(float) * Zp.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < N; ++i) {
+        size_t ri = H.perm[i];
+        for (int j = 0; j < N; ++j) {
+            size_t rj = H.perm[j];
+            Z_host[2 * ((size_t)i * N + j)] = Zp[2 * (ri * ctx->ld + rj)];
+            Z_host[2 * ((size_t)i * N + j) + 1] = Zp[2 * (ri * ctx->ld + rj) + 1];
+        }
+    }
+    return VIE_OK;
+}
+
+int vie_erfcx(vie_ctx *ctx, const double *u, double *out, int32_t n, int32_t precision) {
+    if (!ctx || !u || !out || n < 0) return VIE_EINVAL;
+    if (n == 0) return VIE_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = 0;
+    DevBuf du, dout;
+    CK(du.ensure(sizeof(double) * 2 * n));
+    CK(dout.ensure(sizeof(double) * 2 * n));
+    CK(cudaMemcpy(du.p, u, sizeof(double) * 2 * n, cudaMemcpyHostToDevice));
+    CK(vie::launch_erfcx(du.as<double>(), dout.as<double>(), n, precision == VIE_FP64, st));
+    CK(cudaMemcpy(out, dout.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
+    return VIE_OK;
+}
+
+int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out, int32_t n, int32_t precision) {
+    if (!ctx || !req || !d || !out || n < 0) return VIE_EINVAL;
+    if (!ctx->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set (the period comes from the mesh)");
+    if (n == 0) return VIE_OK;
+    cudaSetDevice(ctx->device);
+    vie_options saved = ctx->opt;
+    ctx->opt.precision = precision == VIE_FP64 ? VIE_FP64 : VIE_FP32;
+    HostReq H;
+    int e = prepare(ctx, req, H);
+    ctx->opt = saved;
+    if (e) return e;
+    cudaStream_t st = 0;
+    CK(vie::upload_ewald(H.ew, st));
+    DevBuf dd, dout;
+    CK(dd.ensure(sizeof(double) * 3 * n));
+    CK(dout.ensure(sizeof(double) * 2 * n));
+    CK(cudaMemcpy(dd.p, d, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+    CK(vie::launch_green(dd.as<double>(), dout.as<double>(), n, precision == VIE_FP64, st));
+    CK(cudaMemcpy(out, dout.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
+    return VIE_OK;
+}
+
+const char *vie_status_str(int s) {
+    switch (s) {
+        case VIE_OK: return "VIE_OK";
+        case VIE_NOT_CONVERGED: return "VIE_NOT_CONVERGED";
+        case VIE_EINVAL: return "VIE_EINVAL";
+        case VIE_ENOMEM: return "VIE_ENOMEM";
+        case VIE_ECUDA: return "VIE_ECUDA";
+        case VIE_RAYLEIGH_ANOMALY: return "VIE_RAYLEIGH_ANOMALY";
+        case VIE_BAD_MESH: return "VIE_BAD_MESH";
+        case VIE_BREAKDOWN: return "VIE_BREAKDOWN";
+        default: return "VIE_UNKNOWN";
+    }
+}
+
+const char *vie_last_error(const vie_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+void vie_destroy(vie_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    delete ctx;
+}
+
+}  // extern "C"

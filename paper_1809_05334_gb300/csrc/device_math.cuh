@@ -1,0 +1,284 @@
+// Device math for the fill: complex helpers, Faddeeva function, Ewald-summed
+// 2D periodic Green's function (Eq. (3)-(4), Sec. 2.2) and closed-form
+// integrals of 1/R and R over triangles and tetrahedra.
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+namespace vie {
+
+template <typename T> struct cx { T re, im; };
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { return {r, i}; }
+template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> __device__ __forceinline__ cx<T> cconj(cx<T> a) { return {a.re, -a.im}; }
+template <typename T> __device__ __forceinline__ cx<T> crecip(cx<T> a) {
+    // 1/a with scaling to avoid overflow of |a|^2
+    T s = fmax(fabs(a.re), fabs(a.im));
+    T ar = a.re / s, ai = a.im / s;
+    T d = s * (ar * ar + ai * ai);
+    return {ar / d, -ai / d};
+}
+template <typename T> __device__ __forceinline__ void cfma(cx<T> &acc, T s, cx<T> a) {
+    acc.re = fma(s, a.re, acc.re);
+    acc.im = fma(s, a.im, acc.im);
+}
+
+// ---------------------------------------------------------------------------
+// Faddeeva function w(z) = exp(-z^2) erfc(-j z) for Im z >= 0 by Weideman's
+// rational expansion (SIAM J. Numer. Anal. 31, 1994):
+//   w(z) = 2 p(Zz) / (L - j z)^2 + 1 / (sqrt(pi) (L - j z)),  Zz = (L + j z)/(L - j z),
+// p(Zz) = sum_{n=1}^{NW} a_n Zz^(n-1), a_n the Fourier coefficients of
+// (L^2 + t^2) exp(-t^2) in the variable theta, t = L tan(theta/2).  The
+// coefficients are computed on the host in FP64 and stored here.
+constexpr int NW64 = 40;
+constexpr int NW32 = 20;
+struct WeidemanTables {
+    double a64[NW64 + 1];
+    float a32[NW32 + 1];
+    double L64;
+    float L32;
+};
+static __constant__ WeidemanTables c_weid;   // filled by upload_constants() (fill.cu)
+
+template <typename T> struct WTraits;
+template <> struct WTraits<double> {
+    static constexpr int N = NW64;
+    __device__ static double L() { return c_weid.L64; }
+    __device__ static double a(int n) { return c_weid.a64[n]; }
+};
+template <> struct WTraits<float> {
+    static constexpr int N = NW32;
+    __device__ static float L() { return c_weid.L32; }
+    __device__ static float a(int n) { return c_weid.a32[n]; }
+};
+
+template <typename T> __device__ __forceinline__ T rsqrt_pi() { return T(0.56418958354775628695); }
+
+// erfcx(u) = exp(u^2) erfc(u) = w(j u), complex u with Re u >= 0.
+template <typename T> __device__ __forceinline__ cx<T> erfcx_c(cx<T> u) {
+    const T L = WTraits<T>::L();
+    // z = j u: L - j z = L + u, L + j z = L - u
+    cx<T> dm = {L + u.re, u.im};
+    cx<T> dp = {L - u.re, -u.im};
+    cx<T> inv = crecip(dm);
+    cx<T> Z = dp * inv;
+    cx<T> p = {WTraits<T>::a(WTraits<T>::N), T(0)};
+#pragma unroll
+    for (int n = WTraits<T>::N - 1; n >= 1; --n) {
+        p = p * Z;
+        p.re += WTraits<T>::a(n);
+    }
+    cx<T> t = inv * p;
+    t.re = fma(T(2), t.re, rsqrt_pi<T>());
+    t.im = T(2) * t.im;
+    return inv * t;
+}
+
+// erfcx(x) for real x >= 0 (the expansion at z = j x stays real).
+template <typename T> __device__ __forceinline__ T erfcx_r(T x) {
+    const T L = WTraits<T>::L();
+    T inv = T(1) / (L + x);
+    T Z = (L - x) * inv;
+    T p = WTraits<T>::a(WTraits<T>::N);
+#pragma unroll
+    for (int n = WTraits<T>::N - 1; n >= 1; --n) p = fma(p, Z, WTraits<T>::a(n));
+    return inv * fma(T(2) * p, inv, rsqrt_pi<T>());
+}
+
+// ---------------------------------------------------------------------------
+// Ewald parameters of one incidence.  Spatial series (images R_mn):
+//   phase_mn exp(b^2 - R^2 E^2) Re erfcx(R E + j b) / (4 pi R),  b = k/(2E)
+// Spectral series (Floquet modes k_t = k_par + 2 pi (p/a, q/b)):
+//   exp(-j k_t.rho) / (4 a b gamma) [e^{gamma z} erfc(gamma/2E + zE) + e^{-gamma z} erfc(gamma/2E - zE)]
+constexpr int MAX_IMG = 160;
+constexpr int MAX_MODE = 160;
+struct EwaldTables {
+    // per image: (m a, n b, Re, Im) of exp(j k_par.R_mn) exp(b^2)/(4 pi)
+    double img64[MAX_IMG][4];
+    float img32[MAX_IMG][4];
+    // per mode: (k_tx, k_ty, gamma_re, gamma_im, exp(-gamma^2/4E^2), Re, Im of 1/(4ab gamma))
+    double mode64[MAX_MODE][8];
+    float mode32[MAX_MODE][8];
+    int n_img, n_mode;
+    int near_img[9];        // image-table index of (m,n) = (k/3-1, k%3-1)
+    double E, bb, a, b, xcut64;
+    float xcut32;
+    double reg0_re;          // limit R->0 of (image term - static term), without the phase
+};
+static __constant__ EwaldTables c_ew;        // filled by upload_ewald() (fill.cu)
+
+template <typename T> struct ETraits;
+template <> struct ETraits<double> {
+    __device__ static const double *img(int i) { return c_ew.img64[i]; }
+    __device__ static const double *mode(int i) { return c_ew.mode64[i]; }
+    __device__ static double xcut() { return c_ew.xcut64; }
+};
+template <> struct ETraits<float> {
+    __device__ static const float *img(int i) { return c_ew.img32[i]; }
+    __device__ static const float *mode(int i) { return c_ew.mode32[i]; }
+    __device__ static float xcut() { return c_ew.xcut32; }
+};
+
+// g_p(d) for an in-cell difference d; images whose bit is set in `sub`
+// (9-bit mask over (m,n) in {-1,0,1}^2) have their static part
+// phase/(4 pi R) removed.
+template <typename T>
+__device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub) {
+    const T E = T(c_ew.E);
+    const T bb = T(c_ew.bb);
+    const T xc = ETraits<T>::xcut() + T(0.5);
+    cx<T> acc = {T(0), T(0)};
+    // spectral series
+    const T z = fabs(dz);
+    const T ez = exp(-(z * E) * (z * E));
+    const T inv2E = T(0.5) / E;
+    for (int i = 0; i < c_ew.n_mode; ++i) {
+        const T *md = ETraits<T>::mode(i);
+        T s, c;
+        sincos(-(md[0] * dx + md[1] * dy), &s, &c);
+        cx<T> ph = {c, s};
+        cx<T> br;
+        if (md[3] == T(0)) {                       // evanescent: gamma real
+            T g = md[2];
+            T pre = md[4] * ez;
+            T t1 = pre * erfcx_r(g * inv2E + z * E);
+            T u = g * inv2E - z * E;
+            T t2 = (u >= T(0)) ? pre * erfcx_r(u) : T(2) * exp(-g * z) - pre * erfcx_r(-u);
+            br = {t1 + t2, T(0)};
+        } else {                                    // propagating: gamma = j gi
+            T gi = md[3];
+            T pre = md[4] * ez;
+            cx<T> e1 = erfcx_c(cx<T>{z * E, gi * inv2E});
+            // erfcx(zE - j gi/2E) = conj(e1)
+            T sg, cg;
+            sincos(gi * z, &sg, &cg);
+            // t1 = pre e1; t2 = 2 e^{-j gi z} - pre conj(e1)
+            br = {pre * e1.re + T(2) * cg - pre * e1.re, pre * e1.im - T(2) * sg + pre * e1.im};
+        }
+        cx<T> ig = {md[5], md[6]};
+        acc = acc + ph * (br * ig);
+    }
+    // spatial series
+    for (int i = 0; i < c_ew.n_img; ++i) {
+        const T *im = ETraits<T>::img(i);
+        T x = dx + im[0], y = dy + im[1];
+        T R2 = x * x + y * y + dz * dz;
+        T R = sqrt(R2);
+        if (R * E > xc) continue;
+        bool regular = false;
+        if (sub) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                if (((sub >> k) & 1u) && c_ew.near_img[k] == i) regular = true;
+        }
+        if (regular && R * E < T(1e-6)) {
+            // continuous limit at R = 0 of (image term - static term):
+            // reg0 = (E/4pi)[2 b erfi(b) - (2/sqrt pi) exp(b^2)]; the table
+            // phase carries exp(b^2)/(4 pi), undone here
+            cx<T> ph = {im[2], im[3]};
+            T unscale = T(4.0 * CUDART_PI) * exp(-bb * bb) * T(c_ew.reg0_re);
+            acc = acc + unscale * ph;
+            continue;
+        }
+        T val = exp(-R2 * E * E) * erfcx_c(cx<T>{R * E, bb}).re / R;
+        if (regular) val -= exp(-bb * bb) / R;   // static part phase/(4 pi R) in table units
+        cx<T> ph = {im[2], im[3]};
+        acc = acc + val * ph;
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Closed forms (divergence theorem, polygonal / polyhedral sources):
+//  triangle: int 1/R = sum_i t_i ln[(R+_i + s+_i)/(R-_i + s-_i)]
+//                      - |h| sum_i [atan(t s+/(R0^2+|h|R+)) - atan(t s-/(R0^2+|h|R-))]
+//            int R   = ( h^2 int 1/R + 1/2 sum_i t_i (s+R+ - s-R- + R0^2 ln(..)) ) / 3
+//  tetrahedron: int 1/R = 1/2 sum_f d_f int_f 1/R,  int (r'-r)/R = sum_f n_f int_f R
+template <typename T>
+__device__ __forceinline__ T log_rs(T R, T s, T R0sq) {
+    // ln(R + s) without cancellation for s < 0: R + s = R0^2 / (R - s)
+    return (s >= T(0)) ? log(R + s) : log(R0sq) - log(R - s);
+}
+
+template <typename T>
+__device__ void tri_integrals(const T r[3], const T *v, T &inv, T &rint, bool want_r) {
+    T e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
+    T e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+    T n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    T nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    n[0] /= nn; n[1] /= nn; n[2] /= nn;
+    T h = n[0] * (r[0] - v[0]) + n[1] * (r[1] - v[1]) + n[2] * (r[2] - v[2]);
+    T ah = fabs(h);
+    T scale = fmax(sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]),
+                   sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]));
+    T tiny = (sizeof(T) == 8 ? T(1e-13) : T(1e-6)) * scale;
+    T slog = 0, satan = 0, sr = 0;
+    T Rv[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T d0 = r[0] - v[3 * j], d1 = r[1] - v[3 * j + 1], d2 = r[2] - v[3 * j + 2];
+        Rv[j] = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int ja = e, jb = (e + 1) % 3;
+        const T *pa = v + 3 * ja, *pb = v + 3 * jb;
+        T L[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+        T ll = sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
+        L[0] /= ll; L[1] /= ll; L[2] /= ll;
+        // in-plane outward normal u = l x n
+        T u[3] = {L[1] * n[2] - L[2] * n[1], L[2] * n[0] - L[0] * n[2], L[0] * n[1] - L[1] * n[0]};
+        T t = u[0] * (pa[0] - r[0]) + u[1] * (pa[1] - r[1]) + u[2] * (pa[2] - r[2]);
+        T sm = L[0] * (pa[0] - r[0]) + L[1] * (pa[1] - r[1]) + L[2] * (pa[2] - r[2]);
+        T sp = sm + ll;
+        T Rm = Rv[ja], Rp = Rv[jb];
+        T R0sq = t * t + h * h;
+        if (fabs(t) > tiny) {
+            T lr = log_rs(Rp, sp, R0sq) - log_rs(Rm, sm, R0sq);
+            slog += t * lr;
+            if (want_r) sr += t * (sp * Rp - sm * Rm + R0sq * lr);
+            if (ah > tiny) satan += atan2(t * sp, R0sq + ah * Rp) - atan2(t * sm, R0sq + ah * Rm);
+        }
+    }
+    inv = slog - ah * satan;
+    rint = want_r ? (h * h * inv + T(0.5) * sr) / T(3) : T(0);
+}
+
+template <typename T>
+__device__ void tet_integrals(const T r[3], const T *tv, T &inv, T vec[3], bool want_vec) {
+    inv = 0;
+    vec[0] = vec[1] = vec[2] = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        T f[9];
+        int k = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j != i) {
+                f[3 * k] = tv[3 * j]; f[3 * k + 1] = tv[3 * j + 1]; f[3 * k + 2] = tv[3 * j + 2];
+                ++k;
+            }
+        T e1[3] = {f[3] - f[0], f[4] - f[1], f[5] - f[2]};
+        T e2[3] = {f[6] - f[0], f[7] - f[1], f[8] - f[2]};
+        T n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        T nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        T o = n[0] * (f[0] - tv[3 * i]) + n[1] * (f[1] - tv[3 * i + 1]) + n[2] * (f[2] - tv[3 * i + 2]);
+        T sg = (o >= T(0)) ? T(1) / nn : T(-1) / nn;   // outward unit normal
+        n[0] *= sg; n[1] *= sg; n[2] *= sg;
+        T d = n[0] * (f[0] - r[0]) + n[1] * (f[1] - r[1]) + n[2] * (f[2] - r[2]);
+        T fi, fr;
+        tri_integrals<T>(r, f, fi, fr, want_vec);
+        inv += T(0.5) * d * fi;
+        if (want_vec) {
+            vec[0] += n[0] * fr; vec[1] += n[1] * fr; vec[2] += n[2] * fr;
+        }
+    }
+}
+
+}  // namespace vie

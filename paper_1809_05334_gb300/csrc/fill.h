@@ -1,0 +1,67 @@
+// Device-side views of the mesh and of one request, shared by the fill,
+// post-processing and API translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "vie_internal.h"
+
+namespace vie {
+
+struct EwaldTables;
+
+struct DevMesh {
+    int nt, N, nf, nh;
+    double a, b;
+    const double *tv;      // [nt][12] vertices
+    const double *cen;     // [nt][3]
+    const double *vol;     // [nt]
+    const double *q5;      // [nt][14][3] degree-5 points
+    const float *far32;    // [nt][28]: 4 points, centroid, v_i - c (4x3), weight vol/4
+    const double *far64;
+    const double *fv;      // [nf][9] charge-face vertices
+    const double *f5;      // [nf][7][3] degree-5 points
+    const double *farea;   // [nf]
+    const float *ffar32;   // [nf][12]: 3 points, weight area/3, pad
+    const double *ffar64;
+    const int32_t *hf;     // [nh] charge-face index of each half function
+    const uint32_t *bm_tt, *bm_tf, *bm_ft, *bm_ff;   // near bitmaps (x-major)
+    const NearPair *near_tt, *near_tf, *near_ft, *near_ff;
+    int n_tt, n_tf, n_ft, n_ff;
+
+    template <typename T> __device__ const T *far(int t) const;
+    template <typename T> __device__ const T *ffar(int f) const;
+};
+template <> __device__ inline const float *DevMesh::far<float>(int t) const { return far32 + 28 * (size_t)t; }
+template <> __device__ inline const double *DevMesh::far<double>(int t) const { return far64 + 28 * (size_t)t; }
+template <> __device__ inline const float *DevMesh::ffar<float>(int f) const { return ffar32 + 12 * (size_t)f; }
+template <> __device__ inline const double *DevMesh::ffar<double>(int f) const { return ffar64 + 12 * (size_t)f; }
+
+struct DevReq {
+    double k0, kx, ky;
+    double kinc[3];        // incident wavevector (k_par, -k0 cos theta)
+    double pol[6];         // TE and TM unit polarisations
+    const int32_t *row;    // [nt*4] matrix row (domain-blocked order) of local face (t,i)
+    const double *coef;    // [nt*4] sgn * area / (3 vol)
+    const double *wt;      // [nt*4][2] test weight exp(+j k_par.s) (source weight = conjugate)
+    const double *kap;     // [nt][2] kappa = 1 - 1/eps_r (exp(j w t) convention)
+    const double *ieps;    // [nt][2] 1/eps_r
+    const int32_t *frow;   // [nf] matrix row of each charge face's unknown
+    const double *qs;      // [nf][2] surface charge kappa- - kappa+ (kappa- = 0 for half)
+};
+
+// degree-5 rules: barycentric points [14][4] / [7][3] (may be null) and weights
+void tet_rule5(double (*pts)[4], double *w);
+void tri_rule5(double (*pts)[3], double *w);
+void tet_rule2(double (*pts)[4], double *w);
+void tri_rule2(double (*pts)[3], double *w);
+
+cudaError_t upload_constants();
+cudaError_t upload_ewald(const EwaldTables &t, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, double *b, cudaStream_t st,
+                        cudaEvent_t far0 = nullptr, cudaEvent_t far1 = nullptr);
+cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStream_t st);
+cudaError_t launch_green(const double *d, double *out, int n, bool fp64, cudaStream_t st);
+
+}  // namespace vie

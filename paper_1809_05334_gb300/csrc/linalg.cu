@@ -1,0 +1,475 @@
+// Dense complex linear algebra of the solve: the HBM-bound matvec Y = Z X for
+// two right-hand sides, the in-place blocked Gauss-Jordan inversion of the
+// domain blocks A_dd of Eq. (6) (no pivoting), and the vector kernels of GMRES.
+//
+// Layouts: complex interleaved (re, im).  A matrix is `rows` rows of `ld`
+// complex entries (ld a multiple of 4, zero padded).  Vectors with two
+// right-hand sides are [n][2] complex.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "linalg.h"
+
+namespace vie {
+
+template <typename T> struct V2;
+template <> struct V2<float> { using t = float4; };
+template <> struct V2<double> { using t = double2; };
+
+// ---------------------------------------------------------------------------
+// matvec: y[r] = sum_c A[r][c] x[c] for rows [0, rows), two right-hand sides.
+// One warp per MV_ROWS rows; the x tile of MV_TILE columns is staged in shared
+// memory (converted to the accumulation type TA); Z streams with 16-byte loads.
+// ---------------------------------------------------------------------------
+constexpr int MV_ROWS = 4;
+constexpr int MV_WARPS = 8;
+constexpr int MV_TILE = 512;
+
+template <typename TZ, typename TX, typename TA, bool ACCUM>
+__global__ void __launch_bounds__(MV_WARPS * 32)
+k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__restrict__ x,
+         TA *__restrict__ y, TA alpha) {
+    __shared__ TA xs[MV_TILE * 4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = (blockIdx.x * MV_WARPS + warp) * MV_ROWS;
+    TA acc[MV_ROWS][4];
+#pragma unroll
+    for (int i = 0; i < MV_ROWS; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[i][k] = TA(0);
+    constexpr int VEC = sizeof(TZ) == 4 ? 2 : 1;   // complex entries per 16-byte load
+    for (int c0 = 0; c0 < cols; c0 += MV_TILE) {
+        const int cn = min(MV_TILE, cols - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < MV_TILE * 4; i += blockDim.x)
+            xs[i] = (i < cn * 4) ? TA(x[(size_t)c0 * 4 + i]) : TA(0);
+        __syncthreads();
+        const int cend = (cn + VEC - 1) / VEC * VEC;
+        for (int c = lane * VEC; c < cend; c += 32 * VEC) {
+            typename V2<TZ>::t z[MV_ROWS];
+#pragma unroll
+            for (int i = 0; i < MV_ROWS; ++i) {
+                const int r = r0 + i;
+                if (r < rows)
+                    z[i] = __ldcs(reinterpret_cast<const typename V2<TZ>::t *>(A + 2 * ((size_t)r * ld + c0 + c)));
+                else
+                    z[i] = {};
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const TA *xv = xs + 4 * (c + v);
+                const TA x0r = xv[0], x0i = xv[1], x1r = xv[2], x1i = xv[3];
+#pragma unroll
+                for (int i = 0; i < MV_ROWS; ++i) {
+                    TA zr, zi;
+                    if (VEC == 2) {
+                        const float4 f = *reinterpret_cast<const float4 *>(&z[i]);
+                        zr = TA(v == 0 ? f.x : f.z);
+                        zi = TA(v == 0 ? f.y : f.w);
+                    } else {
+                        const double2 d = *reinterpret_cast<const double2 *>(&z[i]);
+                        zr = TA(d.x);
+                        zi = TA(d.y);
+                    }
+                    acc[i][0] = fma(zr, x0r, fma(-zi, x0i, acc[i][0]));
+                    acc[i][1] = fma(zr, x0i, fma(zi, x0r, acc[i][1]));
+                    acc[i][2] = fma(zr, x1r, fma(-zi, x1i, acc[i][2]));
+                    acc[i][3] = fma(zr, x1i, fma(zi, x1r, acc[i][3]));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < MV_ROWS; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[i][k] += __shfl_down_sync(0xffffffffu, acc[i][k], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < MV_ROWS; ++i) {
+            const int r = r0 + i;
+            if (r >= rows) continue;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (ACCUM) y[(size_t)r * 4 + k] += alpha * acc[i][k];
+                else y[(size_t)r * 4 + k] = alpha * acc[i][k];
+            }
+        }
+    }
+}
+
+template <typename TZ, typename TX, typename TA>
+cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *y, TA alpha, bool accumulate,
+                   cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    const int grid = (rows + MV_WARPS * MV_ROWS - 1) / (MV_WARPS * MV_ROWS);
+    if (accumulate)
+        k_matvec<TZ, TX, TA, true><<<grid, MV_WARPS * 32, 0, st>>>(A, ld, rows, cols, x, y, alpha);
+    else
+        k_matvec<TZ, TX, TA, false><<<grid, MV_WARPS * 32, 0, st>>>(A, ld, rows, cols, x, y, alpha);
+    return cudaGetLastError();
+}
+
+template cudaError_t matvec<float, float, float>(const float *, size_t, int, int, const float *, float *, float, bool, cudaStream_t);
+template cudaError_t matvec<float, double, double>(const float *, size_t, int, int, const double *, double *, double, bool, cudaStream_t);
+template cudaError_t matvec<double, double, double>(const double *, size_t, int, int, const double *, double *, double, bool, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Blocked Gauss-Jordan inversion in place, no pivoting (step k, block width w):
+//   P = A_kk^-1; A_kj <- P A_kj (j != k); A_ij <- A_ij - A_ik A_kj (i, j != k);
+//   A_ik <- -A_ik P (i != k); A_kk <- P.
+// ---------------------------------------------------------------------------
+constexpr int GJ_NB = 32;
+
+template <typename T>
+__global__ void k_gj_diag(T *A, size_t ld, int k0, int w, int *status) {
+    // unblocked in-place Gauss-Jordan inverse of the w x w pivot block
+    __shared__ T P[GJ_NB][GJ_NB][2];
+    __shared__ T col[GJ_NB][2];
+    __shared__ T piv[2];
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i = e / w, j = e % w;
+        P[i][j][0] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
+        P[i][j][1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
+    }
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+        if (threadIdx.x == 0) {
+            T pr = P[j][j][0], pi = P[j][j][1];
+            T d = pr * pr + pi * pi;
+            if (!(d > T(0)) || !isfinite(d)) atomicExch(status, 1);
+            piv[0] = pr / d;
+            piv[1] = -pi / d;
+        }
+        if (threadIdx.x < w) {   // column j before the step: f_i = a_ij
+            col[threadIdx.x][0] = P[threadIdx.x][j][0];
+            col[threadIdx.x][1] = P[threadIdx.x][j][1];
+        }
+        __syncthreads();
+        const T qr = piv[0], qi = piv[1];
+        if (threadIdx.x < w) {   // row j <- p * row j, pivot entry <- p
+            const int c = threadIdx.x;
+            if (c == j) {
+                P[j][c][0] = qr; P[j][c][1] = qi;
+            } else {
+                T ar = P[j][c][0], ai = P[j][c][1];
+                P[j][c][0] = qr * ar - qi * ai;
+                P[j][c][1] = qr * ai + qi * ar;
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+            const int i = e / w, c = e % w;
+            if (i == j) continue;
+            const T fr = col[i][0], fi = col[i][1];
+            if (c == j) {            // a_ij <- -f_i p
+                P[i][c][0] = -(fr * qr - fi * qi);
+                P[i][c][1] = -(fr * qi + fi * qr);
+            } else {                 // a_ic <- a_ic - f_i a_jc(new)
+                const T br = P[j][c][0], bi = P[j][c][1];
+                P[i][c][0] -= fr * br - fi * bi;
+                P[i][c][1] -= fr * bi + fi * br;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i = e / w, j = e % w;
+        A[2 * ((size_t)(k0 + i) * ld + k0 + j)] = P[i][j][0];
+        A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1] = P[i][j][1];
+    }
+}
+
+// row panel: A_kj <- P A_kj for columns j outside the pivot block (thread per column)
+template <typename T>
+__global__ void k_gj_row(T *A, size_t ld, int n, int k0, int w) {
+    __shared__ T P[GJ_NB][GJ_NB][2];
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i = e / w, j = e % w;
+        P[i][j][0] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
+        P[i][j][1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
+    }
+    __syncthreads();
+    int jj = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jj >= n - w) return;
+    const int j = jj < k0 ? jj : jj + w;
+    T cr[GJ_NB], ci[GJ_NB];
+    for (int i = 0; i < w; ++i) {
+        cr[i] = A[2 * ((size_t)(k0 + i) * ld + j)];
+        ci[i] = A[2 * ((size_t)(k0 + i) * ld + j) + 1];
+    }
+    for (int i = 0; i < w; ++i) {
+        T sr = 0, si = 0;
+        for (int c = 0; c < w; ++c) {
+            sr += P[i][c][0] * cr[c] - P[i][c][1] * ci[c];
+            si += P[i][c][0] * ci[c] + P[i][c][1] * cr[c];
+        }
+        A[2 * ((size_t)(k0 + i) * ld + j)] = sr;
+        A[2 * ((size_t)(k0 + i) * ld + j) + 1] = si;
+    }
+}
+
+// trailing update A_ij -= A_ik A_kj for i, j outside the pivot block.
+// 64 x 64 output tile per CTA, 256 threads, 4 x 4 complex outputs per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_update(T *A, size_t ld, int n, int k0, int w) {
+    __shared__ T Ls[64][GJ_NB + 1][2];   // A_ik tile: 64 rows x w
+    __shared__ T Us[GJ_NB][64 + 1][2];   // A_kj tile: w x 64 cols
+    const int m = n - w;
+    const int ti = blockIdx.y * 64, tj = blockIdx.x * 64;
+    for (int e = threadIdx.x; e < 64 * w; e += 256) {
+        int i = e / w, c = e % w;
+        int ii = ti + i;
+        T vr = 0, vi = 0;
+        if (ii < m) {
+            int r = ii < k0 ? ii : ii + w;
+            vr = A[2 * ((size_t)r * ld + k0 + c)];
+            vi = A[2 * ((size_t)r * ld + k0 + c) + 1];
+        }
+        Ls[i][c][0] = vr; Ls[i][c][1] = vi;
+    }
+    for (int e = threadIdx.x; e < 64 * w; e += 256) {
+        int c = e / 64, j = e % 64;
+        int jj = tj + j;
+        T vr = 0, vi = 0;
+        if (jj < m) {
+            int col = jj < k0 ? jj : jj + w;
+            vr = A[2 * ((size_t)(k0 + c) * ld + col)];
+            vi = A[2 * ((size_t)(k0 + c) * ld + col) + 1];
+        }
+        Us[c][j][0] = vr; Us[c][j][1] = vi;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T ar[4][4], ai[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { ar[a][b] = 0; ai[a][b] = 0; }
+    for (int c = 0; c < w; ++c) {
+        T lr[4], li[4], ur[4], ui[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) { lr[a] = Ls[ty + 16 * a][c][0]; li[a] = Ls[ty + 16 * a][c][1]; }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { ur[b] = Us[c][tx + 16 * b][0]; ui[b] = Us[c][tx + 16 * b][1]; }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                ar[a][b] = fma(lr[a], ur[b], fma(-li[a], ui[b], ar[a][b]));
+                ai[a][b] = fma(lr[a], ui[b], fma(li[a], ur[b], ai[a][b]));
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        int ii = ti + ty + 16 * a;
+        if (ii >= m) continue;
+        int r = ii < k0 ? ii : ii + w;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int jj = tj + tx + 16 * b;
+            if (jj >= m) continue;
+            int col = jj < k0 ? jj : jj + w;
+            size_t o = 2 * ((size_t)r * ld + col);
+            A[o] -= ar[a][b];
+            A[o + 1] -= ai[a][b];
+        }
+    }
+}
+
+// column panel: A_ik <- -A_ik P for rows i outside the pivot block (thread per row)
+template <typename T>
+__global__ void k_gj_col(T *A, size_t ld, int n, int k0, int w) {
+    __shared__ T P[GJ_NB][GJ_NB][2];
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i = e / w, j = e % w;
+        P[i][j][0] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
+        P[i][j][1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
+    }
+    __syncthreads();
+    int ii = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ii >= n - w) return;
+    const int r = ii < k0 ? ii : ii + w;
+    T vr[GJ_NB], vi[GJ_NB];
+    for (int c = 0; c < w; ++c) {
+        vr[c] = A[2 * ((size_t)r * ld + k0 + c)];
+        vi[c] = A[2 * ((size_t)r * ld + k0 + c) + 1];
+    }
+    for (int j = 0; j < w; ++j) {
+        T sr = 0, si = 0;
+        for (int c = 0; c < w; ++c) {
+            sr += vr[c] * P[c][j][0] - vi[c] * P[c][j][1];
+            si += vr[c] * P[c][j][1] + vi[c] * P[c][j][0];
+        }
+        A[2 * ((size_t)r * ld + k0 + j)] = -sr;
+        A[2 * ((size_t)r * ld + k0 + j) + 1] = -si;
+    }
+}
+
+template <typename T>
+cudaError_t gj_invert(T *A, size_t ld, int n, int *status, cudaStream_t st) {
+    for (int k0 = 0; k0 < n; k0 += GJ_NB) {
+        const int w = (n - k0 < GJ_NB) ? n - k0 : GJ_NB;
+        k_gj_diag<T><<<1, 256, 0, st>>>(A, ld, k0, w, status);
+        const int m = n - w;
+        if (m > 0) {
+            k_gj_row<T><<<(m + 127) / 128, 128, 0, st>>>(A, ld, n, k0, w);
+            dim3 g((m + 63) / 64, (m + 63) / 64);
+            k_gj_update<T><<<g, 256, 0, st>>>(A, ld, n, k0, w);
+            k_gj_col<T><<<(m + 127) / 128, 128, 0, st>>>(A, ld, n, k0, w);
+        }
+    }
+    return cudaGetLastError();
+}
+template cudaError_t gj_invert<float>(float *, size_t, int, int *, cudaStream_t);
+template cudaError_t gj_invert<double>(double *, size_t, int, int *, cudaStream_t);
+
+// copy a diagonal block Z[off:off+n, off:off+n] into B (ld_b), converting precision
+template <typename TS, typename TD>
+__global__ void k_copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t tot = (size_t)n * ldb;
+    if (e >= tot) return;
+    int i = (int)(e / ldb), j = (int)(e % ldb);
+    TD vr = 0, vi = 0;
+    if (j < n) {
+        vr = TD(Z[2 * ((size_t)(off + i) * ldz + off + j)]);
+        vi = TD(Z[2 * ((size_t)(off + i) * ldz + off + j) + 1]);
+    }
+    B[2 * e] = vr;
+    B[2 * e + 1] = vi;
+}
+
+template <typename TS, typename TD>
+cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st) {
+    size_t tot = (size_t)n * ldb;
+    k_copy_block<TS, TD><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Z, ldz, off, n, B, ldb);
+    return cudaGetLastError();
+}
+template cudaError_t copy_block<float, float>(const float *, size_t, int, int, float *, size_t, cudaStream_t);
+template cudaError_t copy_block<double, float>(const double *, size_t, int, int, float *, size_t, cudaStream_t);
+template cudaError_t copy_block<double, double>(const double *, size_t, int, int, double *, size_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// GMRES vector kernels (two right-hand sides, [n][2] complex)
+// ---------------------------------------------------------------------------
+// h[j][r] += sum_i conj(V_j[i][r]) w[i][r]  for j < nv (atomics into FP64)
+template <typename TV>
+__global__ void k_dots(const TV *V, size_t vstride, int nv, const TV *w, int n, double *h) {
+    __shared__ double red[8][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = 0; j < nv; ++j) {
+        const TV *v = V + j * vstride;
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const double vr0 = v[4 * i], vi0 = v[4 * i + 1], vr1 = v[4 * i + 2], vi1 = v[4 * i + 3];
+            const double wr0 = w[4 * i], wi0 = w[4 * i + 1], wr1 = w[4 * i + 2], wi1 = w[4 * i + 3];
+            a0 += vr0 * wr0 + vi0 * wi0;
+            a1 += vr0 * wi0 - vi0 * wr0;
+            a2 += vr1 * wr1 + vi1 * wi1;
+            a3 += vr1 * wi1 - vi1 * wr1;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_down_sync(0xffffffffu, a0, o);
+            a1 += __shfl_down_sync(0xffffffffu, a1, o);
+            a2 += __shfl_down_sync(0xffffffffu, a2, o);
+            a3 += __shfl_down_sync(0xffffffffu, a3, o);
+        }
+        if (lane == 0) { red[warp][0] = a0; red[warp][1] = a1; red[warp][2] = a2; red[warp][3] = a3; }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double s = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q][threadIdx.x];
+            atomicAdd(h + 4 * j + threadIdx.x, s);
+        }
+        __syncthreads();
+    }
+}
+
+// w[i][r] -= sum_j V_j[i][r] h[j][r]   (h on the device, FP64)
+template <typename TV>
+__global__ void k_subtract(const TV *V, size_t vstride, int nv, const double *h, TV *w, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s0r = 0, s0i = 0, s1r = 0, s1i = 0;
+    for (int j = 0; j < nv; ++j) {
+        const TV *v = V + j * vstride + 4 * (size_t)i;
+        const double *hh = h + 4 * j;
+        s0r += double(v[0]) * hh[0] - double(v[1]) * hh[1];
+        s0i += double(v[0]) * hh[1] + double(v[1]) * hh[0];
+        s1r += double(v[2]) * hh[2] - double(v[3]) * hh[3];
+        s1i += double(v[2]) * hh[3] + double(v[3]) * hh[2];
+    }
+    TV *o = w + 4 * (size_t)i;
+    o[0] = TV(double(o[0]) - s0r);
+    o[1] = TV(double(o[1]) - s0i);
+    o[2] = TV(double(o[2]) - s1r);
+    o[3] = TV(double(o[3]) - s1i);
+}
+
+// y[i][r] = s[r] * x[i][r] (complex scale per rhs; s on the host)
+template <typename TX, typename TY>
+__global__ void k_scale(const TX *x, TY *y, int n, double s0r, double s0i, double s1r, double s1i) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const TX *a = x + 4 * (size_t)i;
+    TY *o = y + 4 * (size_t)i;
+    double xr0 = a[0], xi0 = a[1], xr1 = a[2], xi1 = a[3];
+    o[0] = TY(s0r * xr0 - s0i * xi0);
+    o[1] = TY(s0r * xi0 + s0i * xr0);
+    o[2] = TY(s1r * xr1 - s1i * xi1);
+    o[3] = TY(s1r * xi1 + s1i * xr1);
+}
+
+// x[i][r] += sum_j V_j[i][r] y[j][r]  (y on the device)
+template <typename TV>
+__global__ void k_combine(const TV *V, size_t vstride, int nv, const double *y, double *x, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s0r = 0, s0i = 0, s1r = 0, s1i = 0;
+    for (int j = 0; j < nv; ++j) {
+        const TV *v = V + j * vstride + 4 * (size_t)i;
+        const double *yy = y + 4 * j;
+        s0r += double(v[0]) * yy[0] - double(v[1]) * yy[1];
+        s0i += double(v[0]) * yy[1] + double(v[1]) * yy[0];
+        s1r += double(v[2]) * yy[2] - double(v[3]) * yy[3];
+        s1i += double(v[2]) * yy[3] + double(v[3]) * yy[2];
+    }
+    double *o = x + 4 * (size_t)i;
+    o[0] += s0r; o[1] += s0i; o[2] += s1r; o[3] += s1i;
+}
+
+template <typename TV>
+cudaError_t dots(const TV *V, size_t vstride, int nv, const TV *w, int n, double *h, cudaStream_t st) {
+    cudaMemsetAsync(h, 0, sizeof(double) * 4 * nv, st);
+    k_dots<TV><<<296, 256, 0, st>>>(V, vstride, nv, w, n, h);
+    return cudaGetLastError();
+}
+template <typename TV>
+cudaError_t subtract(const TV *V, size_t vstride, int nv, const double *h, TV *w, int n, cudaStream_t st) {
+    k_subtract<TV><<<(n + 255) / 256, 256, 0, st>>>(V, vstride, nv, h, w, n);
+    return cudaGetLastError();
+}
+template <typename TX, typename TY>
+cudaError_t scale(const TX *x, TY *y, int n, const double s[4], cudaStream_t st) {
+    k_scale<TX, TY><<<(n + 255) / 256, 256, 0, st>>>(x, y, n, s[0], s[1], s[2], s[3]);
+    return cudaGetLastError();
+}
+template <typename TV>
+cudaError_t combine(const TV *V, size_t vstride, int nv, const double *y, double *x, int n, cudaStream_t st) {
+    k_combine<TV><<<(n + 255) / 256, 256, 0, st>>>(V, vstride, nv, y, x, n);
+    return cudaGetLastError();
+}
+template cudaError_t dots<float>(const float *, size_t, int, const float *, int, double *, cudaStream_t);
+template cudaError_t dots<double>(const double *, size_t, int, const double *, int, double *, cudaStream_t);
+template cudaError_t subtract<float>(const float *, size_t, int, const double *, float *, int, cudaStream_t);
+template cudaError_t subtract<double>(const double *, size_t, int, const double *, double *, int, cudaStream_t);
+template cudaError_t scale<double, float>(const double *, float *, int, const double *, cudaStream_t);
+template cudaError_t scale<float, float>(const float *, float *, int, const double *, cudaStream_t);
+template cudaError_t scale<double, double>(const double *, double *, int, const double *, cudaStream_t);
+template cudaError_t combine<float>(const float *, size_t, int, const double *, double *, int, cudaStream_t);
+template cudaError_t combine<double>(const double *, size_t, int, const double *, double *, int, cudaStream_t);
+
+}  // namespace vie

@@ -1,0 +1,24 @@
+// Dense complex linear algebra used by the solve (see linalg.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace vie {
+
+template <typename TZ, typename TX, typename TA>
+cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *y, TA alpha, bool accumulate,
+                   cudaStream_t st);
+template <typename T>
+cudaError_t gj_invert(T *A, size_t ld, int n, int *status, cudaStream_t st);
+template <typename TS, typename TD>
+cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st);
+template <typename TV>
+cudaError_t dots(const TV *V, size_t vstride, int nv, const TV *w, int n, double *h, cudaStream_t st);
+template <typename TV>
+cudaError_t subtract(const TV *V, size_t vstride, int nv, const double *h, TV *w, int n, cudaStream_t st);
+template <typename TX, typename TY>
+cudaError_t scale(const TX *x, TY *y, int n, const double s[4], cudaStream_t st);
+template <typename TV>
+cudaError_t combine(const TV *V, size_t vstride, int nv, const double *y, double *x, int n, cudaStream_t st);
+
+}  // namespace vie

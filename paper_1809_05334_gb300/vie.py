@@ -1,0 +1,215 @@
+"""ctypes binding of libvie.so (include/vie.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts numpy arrays to pointers and C structs back to Python values.  There
+is no fallback: if the library is missing or no GPU is present, the calls
+raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvie.so")
+MAX_DOMAINS = 8
+
+VIE_FP64, VIE_FP32 = 0, 1
+STATUS = {0: "VIE_OK", 1: "VIE_NOT_CONVERGED", -1: "VIE_EINVAL", -2: "VIE_ENOMEM", -3: "VIE_ECUDA",
+          -4: "VIE_RAYLEIGH_ANOMALY", -6: "VIE_BAD_MESH", -8: "VIE_BREAKDOWN"}
+
+# every symbol include/vie.h declares
+EXPORTS = ["vie_default_options", "vie_create", "vie_set_options", "vie_set_mesh", "vie_num_unknowns",
+           "vie_solve", "vie_fill_matrix", "vie_fill_matrix_prec", "vie_erfcx", "vie_green",
+           "vie_status_str", "vie_last_error", "vie_destroy"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("use_precond", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("lambda_nm", ctypes.c_double), ("theta", ctypes.c_double), ("phi", ctypes.c_double),
+                ("eps", ctypes.c_double * (2 * MAX_DOMAINS)), ("coeffs_out", ctypes.c_void_p),
+                ("coeffs_on_device", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_unknowns", ctypes.c_int32), ("iterations", ctypes.c_int32 * 2),
+                ("refinements", ctypes.c_int32), ("rel_residual", ctypes.c_double * 2),
+                ("absorbed", (ctypes.c_double * MAX_DOMAINS) * 2), ("reflectance", ctypes.c_double * 2),
+                ("transmittance", ctypes.c_double * 2), ("t_fill_ms", ctypes.c_double),
+                ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("t_post_ms", ctypes.c_double),
+                ("k_far_tt_ms", ctypes.c_double), ("k_fill_ms", ctypes.c_double), ("k_factor_ms", ctypes.c_double),
+                ("k_matvec_ms", ctypes.c_double), ("k_matvec_n", ctypes.c_int32), ("n_near_pairs", ctypes.c_int32),
+                ("far_pair_evals", ctypes.c_int64)]
+
+
+_LIB = None
+
+
+def load():
+    """Load libvie.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libvie.so not built: run `python -m paper_1809_05334_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    lib.vie_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.vie_default_options.restype = None
+    lib.vie_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(Options)]
+    lib.vie_set_options.argtypes = [P, ctypes.POINTER(Options)]
+    lib.vie_set_mesh.argtypes = [P, P, I, P, I, P, I, D, D, I]
+    lib.vie_num_unknowns.argtypes = [P]
+    lib.vie_num_unknowns.restype = I
+    lib.vie_solve.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(Result), P]
+    lib.vie_fill_matrix.argtypes = [P, ctypes.POINTER(Request), P, P, P]
+    lib.vie_fill_matrix_prec.argtypes = [P, ctypes.POINTER(Request), P, P]
+    lib.vie_erfcx.argtypes = [P, P, P, I, I]
+    lib.vie_green.argtypes = [P, ctypes.POINTER(Request), P, P, I, I]
+    lib.vie_status_str.argtypes = [ctypes.c_int]
+    lib.vie_status_str.restype = ctypes.c_char_p
+    lib.vie_last_error.argtypes = [P]
+    lib.vie_last_error.restype = ctypes.c_char_p
+    lib.vie_destroy.argtypes = [P]
+    lib.vie_destroy.restype = None
+    _LIB = lib
+    return lib
+
+
+class VIEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Solver:
+    """One library context on one GPU (vie_create ... vie_destroy)."""
+
+    def __init__(self, device=0, precision=VIE_FP32, use_precond=True, restart=60, max_iter=1000,
+                 tol=1e-6, inner_tol=1e-4, timing=False):
+        self.lib = load()
+        self.opt = Options()
+        self.lib.vie_default_options(ctypes.byref(self.opt))
+        self.opt.precision, self.opt.use_precond = int(precision), int(bool(use_precond))
+        self.opt.restart, self.opt.max_iter = int(restart), int(max_iter)
+        self.opt.tol, self.opt.inner_tol = float(tol), float(inner_tol)
+        self.opt.timing = int(bool(timing))
+        self.ctx = ctypes.c_void_p()
+        rc = self.lib.vie_create(ctypes.byref(self.ctx), int(device), ctypes.byref(self.opt))
+        if rc != 0:
+            raise VIEError(rc, "vie_create failed (is a CUDA GPU present?)")
+        self.n_domains = 0
+
+    def _check(self, rc, allow_positive=False):
+        if rc < 0 or (rc > 0 and not allow_positive):
+            raise VIEError(rc, self.lib.vie_last_error(self.ctx).decode())
+        return rc
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            setattr(self.opt, k, v)
+        self._check(self.lib.vie_set_options(self.ctx, ctypes.byref(self.opt)))
+
+    def set_mesh(self, cell):
+        self._verts = np.ascontiguousarray(cell.verts, dtype=np.float64)
+        self._tets = np.ascontiguousarray(cell.tets, dtype=np.int32)
+        self._dom = np.ascontiguousarray(cell.tet_domain, dtype=np.int32)
+        self.n_domains = int(cell.n_domains)
+        self._check(self.lib.vie_set_mesh(self.ctx, _ptr(self._verts), len(self._verts), _ptr(self._tets),
+                                          len(self._tets), _ptr(self._dom), self.n_domains,
+                                          float(cell.period_a), float(cell.period_b), int(cell.active_domain)))
+        return self.num_unknowns()
+
+    def num_unknowns(self):
+        return int(self.lib.vie_num_unknowns(self.ctx))
+
+    def request(self, lam, theta=0.0, phi=0.0, eps=()):
+        r = Request()
+        r.lambda_nm, r.theta, r.phi = float(lam), float(theta), float(phi)
+        for d, e in enumerate(np.asarray(eps, dtype=np.complex128)):
+            r.eps[2 * d], r.eps[2 * d + 1] = e.real, e.imag
+        return r
+
+    def solve(self, lam, theta=0.0, phi=0.0, eps=(), coeffs=False, stream=None):
+        """Solve at one incidence; returns a dict of absorbed fractions, R, T, residuals, timings."""
+        req = self.request(lam, theta, phi, eps)
+        out = None
+        if coeffs is not False and coeffs is not None:
+            if isinstance(coeffs, np.ndarray):
+                out = coeffs
+            else:
+                out = np.zeros((self.num_unknowns(), 2), dtype=np.complex128)
+            req.coeffs_out = out.ctypes.data
+        res = Result()
+        rc = self.lib.vie_solve(self.ctx, ctypes.byref(req), ctypes.byref(res),
+                                ctypes.c_void_p(stream) if stream else None)
+        self._check(rc, allow_positive=True)
+        nd = self.n_domains
+        return dict(status=rc, n=res.n_unknowns, iterations=list(res.iterations), refinements=res.refinements,
+                    rel_residual=np.array(res.rel_residual[:]),
+                    A=np.array([[res.absorbed[p][d] for d in range(nd)] for p in range(2)]),
+                    R=np.array(res.reflectance[:]), T=np.array(res.transmittance[:]),
+                    t_fill_ms=res.t_fill_ms, t_factor_ms=res.t_factor_ms, t_solve_ms=res.t_solve_ms,
+                    t_post_ms=res.t_post_ms, k_far_tt_ms=res.k_far_tt_ms, k_fill_ms=res.k_fill_ms,
+                    k_factor_ms=res.k_factor_ms, k_matvec_ms=res.k_matvec_ms, k_matvec_n=res.k_matvec_n,
+                    n_near_pairs=res.n_near_pairs, far_pair_evals=res.far_pair_evals, x=out)
+
+    def solve_device(self, lam, theta, phi, eps, coeffs_dev_ptr, stream=None):
+        """Solve writing the unknowns to a caller-owned device buffer [N][2] complex128."""
+        req = self.request(lam, theta, phi, eps)
+        req.coeffs_out = int(coeffs_dev_ptr)
+        req.coeffs_on_device = 1
+        res = Result()
+        rc = self.lib.vie_solve(self.ctx, ctypes.byref(req), ctypes.byref(res),
+                                ctypes.c_void_p(stream) if stream else None)
+        self._check(rc, allow_positive=True)
+        return res
+
+    def fill_matrix(self, lam, theta=0.0, phi=0.0, eps=()):
+        """FP64 Z [N,N] and b [N,2] in canonical unknown order (parity entry point)."""
+        n = self.num_unknowns()
+        Z = np.zeros((n, n), dtype=np.complex128)
+        b = np.zeros((n, 2), dtype=np.complex128)
+        req = self.request(lam, theta, phi, eps)
+        self._check(self.lib.vie_fill_matrix(self.ctx, ctypes.byref(req), _ptr(Z), _ptr(b), None))
+        return Z, b
+
+    def fill_matrix_prec(self, lam, theta=0.0, phi=0.0, eps=()):
+        n = self.num_unknowns()
+        Z = np.zeros((n, n), dtype=np.complex128)
+        req = self.request(lam, theta, phi, eps)
+        self._check(self.lib.vie_fill_matrix_prec(self.ctx, ctypes.byref(req), _ptr(Z), None))
+        return Z
+
+    def erfcx(self, u, precision=VIE_FP64):
+        u = np.ascontiguousarray(u, dtype=np.complex128)
+        out = np.zeros_like(u)
+        self._check(self.lib.vie_erfcx(self.ctx, _ptr(u), _ptr(out), u.size, int(precision)))
+        return out
+
+    def green(self, d, lam, theta=0.0, phi=0.0, precision=VIE_FP64):
+        d = np.ascontiguousarray(d, dtype=np.float64).reshape(-1, 3)
+        out = np.zeros(len(d), dtype=np.complex128)
+        req = self.request(lam, theta, phi, [1.0] * max(self.n_domains, 1))
+        self._check(self.lib.vie_green(self.ctx, ctypes.byref(req), _ptr(d), _ptr(out), len(d), int(precision)))
+        return out
+
+    def close(self):
+        if self.ctx:
+            self.lib.vie_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
