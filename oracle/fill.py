@@ -23,15 +23,17 @@ physics-sign permittivities of the inputs are conjugated here.
 
 Discrete problem (shared as a definition with the CUDA path): element pairs
 whose centroid distance, for some lattice image (m, n) in {-1,0,1}^2, is below
-NEAR_FACTOR x (sum of the element radii) x (1 + NEAR_MARGIN) are *near*.  Far pairs use the degree-2
-product rules.  Near pairs split g_p into the static part exp(j k_par.R)/(4 pi R)
-of every near image, integrated in closed form over the source element at the
-points of the degree-5 rule of the test element, plus the remainder integrated
-with the degree-2 product rules.  The static part is the average of the two
-integration orders (outer rule on the test element with the source in closed
-form, and outer rule on the source element with the test element in closed
-form), so the discrete operator keeps the reciprocity Z(k_par) = Z(-k_par)^T of
-the continuous one for a single material.
+NEAR_FACTOR x (sum of the element radii) x (1 + NEAR_MARGIN) are *near* in that
+image.  Far pairs use the degree-2 product rules.  Near pairs split g_p into
+the static part exp(j k_par.R)/(4 pi R) of every near image plus the remainder,
+which is integrated with the degree-2 product rules.  The static part of an
+image in which the two elements *touch* (share a vertex) is integrated in
+closed form over one element at the points of the degree-5 rule of the other,
+averaged over the two orders (outer rule on the test element, and outer rule
+on the source element); the static part of a near image in which they do not
+touch uses the degree-5 x degree-5 product rule.  Both choices are symmetric,
+so the discrete operator keeps the reciprocity Z(k_par) = Z(-k_par)^T of the
+continuous one for a single material.
 """
 import numpy as np
 
@@ -98,6 +100,13 @@ def _near_images(cx, rx, cy, ry, a, b):
         d = np.linalg.norm(cx[:, None, :] - cy[None, :, :] + R, axis=-1)
         out[:, :, k] = d < NEAR_FACTOR * (rx[:, None] + ry[None, :]) * (1.0 + NEAR_MARGIN)
     return out
+
+
+def _touch(vx, vy, R, a, b):
+    """Boolean [p]: element x shares a vertex with the image y - R of element y."""
+    tol = 1e-9 * max(a, b)
+    d = np.linalg.norm(vx[:, :, None, :] - (vy[:, None, :, :] - R), axis=-1)
+    return (d < tol).any(axis=(1, 2))
 
 
 def _pair_moments(green, X, wX, cX, Y, wY, cY, sub=None, vector=True):
@@ -173,6 +182,23 @@ def tet_tet_moments(prob, chunk=48):
             if not sel.any():
                 continue
             R = np.array([m * topo["a"], n * topo["b"], 0.0])
+            touch = _touch(P[I[sel]], P[J[sel]], R, topo["a"], topo["b"])
+            # non-touching near image: degree-5 x degree-5 product rule of the static part
+            nt_ = np.nonzero(sel)[0][~touch]
+            if len(nt_):
+                ph1 = np.exp(1j * (prob.kpar @ R)) / (4 * np.pi)
+                xr, yr = X5[I[nt_]], X5[J[nt_]]                       # [p,14,3]
+                Rv = np.linalg.norm(xr[:, :, None, :] - yr[:, None, :, :] + R, axis=-1)
+                Wp = W5[I[nt_]][:, :, None] * W5[J[nt_]][:, None, :] / Rv
+                rx5 = xr - cent[I[nt_]][:, None]
+                ry5 = yr - cent[J[nt_]][:, None]
+                s[nt_] += ph1 * Wp.sum(axis=(1, 2))
+                a_[nt_] += ph1 * np.einsum("ipq,ipd->id", Wp, rx5)
+                b_[nt_] += ph1 * np.einsum("ipq,iqd->id", Wp, ry5)
+                c_[nt_] += ph1 * np.einsum("ipq,ipd,iqd->i", Wp, rx5, ry5)
+            sel = np.nonzero(sel)[0][touch]
+            if not len(sel):
+                continue
             ph = 0.5 * np.exp(1j * (prob.kpar @ R)) / (4 * np.pi)    # half of each order
             ct, cs = cent[I[sel]], cent[J[sel]]
             # (i) outer over the test tet, closed form over the image source tet T' - R
@@ -240,6 +266,15 @@ def _scalar_moments(prob, X_el, X_cent, X_rad, X_kind, Y_el, Y_cent, Y_rad, Y_ki
             if not sel.any():
                 continue
             R = np.array([m * topo["a"], n * topo["b"], 0.0])
+            touch = _touch(X_el[Ii[sel]], Y_el[Jj[sel]], R, topo["a"], topo["b"])
+            nt_ = np.nonzero(sel)[0][~touch]
+            if len(nt_):   # non-touching: degree-5 x degree-5 product rule of the static part
+                ph1 = np.exp(1j * (prob.kpar @ R)) / (4 * np.pi)
+                Rv = np.linalg.norm(X5[Ii[nt_]][:, :, None, :] - Y5[Jj[nt_]][:, None, :, :] + R, axis=-1)
+                s[nt_] += ph1 * (W5[Ii[nt_]][:, :, None] * WY5[Jj[nt_]][:, None, :] / Rv).sum(axis=(1, 2))
+            sel = np.nonzero(sel)[0][touch]
+            if not len(sel):
+                continue
             ph = 0.5 * np.exp(1j * (prob.kpar @ R)) / (4 * np.pi)
             # (i) outer over X, closed form over the image of Y; (ii) the reverse
             for outer5, Wo, el, kind, shift in ((X5[Ii[sel]], W5[Ii[sel]], Y_el[Jj[sel]] - R, Y_kind, None),

@@ -64,10 +64,11 @@ struct vie_ctx {
     bool have_mesh = false;
     vie::Topology topo;
     // mesh (device)
-    DevBuf tv, cen, vol, q5, far32, far64, fv, f5, farea, ffar32, ffar64, hf;
+    DevBuf tv, cen, vol, q5, far32, far64, fv, f5, farea, ffar32, ffar64, hf, n32, n64, fn32, fn64, fcen;
     DevBuf bm_tt, bm_tf, bm_ft, bm_ff, n_tt, n_tf, n_ft, n_ff, tdom;
     // request (device)
-    DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders;
+    DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab;
+    double z_extent = 0;
     // solve buffers
     DevBuf Z, b, x, r, u, w, V, h, y, Minv, status, acc, J, rt, cout;
     size_t ld = 0;
@@ -222,6 +223,47 @@ int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
         }
     E.n_mode = nm;
     E.reg0_re = (E.E / (4 * M_PI)) * (2 * E.bb * erfi_series(E.bb) - 2.0 / std::sqrt(M_PI) * std::exp(E.bb * E.bb));
+    // tabulated FP32 path: same truncation as the FP32 series
+    {
+        const double xc32 = FP32_XCUT;
+        E.xs_max = (float)(xc32 + 0.5);
+        E.xs_inv_h = (float)(vie::NSPAT / (xc32 + 0.5));
+        const double zr = std::max(ctx->z_extent, 1e-6) * (1.0 + 1e-6);
+        E.z_max = (float)zr;
+        E.z_inv_h = (float)(vie::NZTAB / zr);
+        E.e_mb2 = (float)std::exp(-E.bb * E.bb);
+        E.Ef = (float)E.E;
+        E.kx = (float)H.kx; E.ky = (float)H.ky;
+        E.step_x = (float)(2 * M_PI / a); E.step_y = (float)(2 * M_PI / b);
+        const int P = (int)std::ceil((2.0 * E.E * xc32 + std::fabs(H.kx)) * a / (2 * M_PI)) + 1;
+        const int Q = (int)std::ceil((2.0 * E.E * xc32 + std::fabs(H.ky)) * b / (2 * M_PI)) + 1;
+        if ((2 * P + 1) * (2 * Q + 1) > vie::MAX_MODE) return fail(ctx, VIE_EINVAL, "too many Floquet modes for the table");
+        E.P = P; E.Q = Q;
+        int nt = 0;
+        std::vector<double> g2s;
+        for (int p = -P; p <= P; ++p)
+            for (int q = -Q; q <= Q; ++q) {
+                const int idx = (p + P) * (2 * Q + 1) + (q + Q);
+                const double ktx = H.kx + 2 * M_PI * p / a, kty = H.ky + 2 * M_PI * q / b;
+                const double kt2 = ktx * ktx + kty * kty;
+                if (std::sqrt(kt2) > 2.0 * E.E * xc32 + k0) { E.rect_tab[idx] = -1; continue; }
+                const double g2 = kt2 - k0 * k0;
+                int found = -1;
+                for (int j = 0; j < nt; ++j)
+                    if (std::fabs(g2s[j] - g2) <= 1e-12 * std::max(1e-6, std::fabs(g2))) { found = j; break; }
+                if (found < 0) {
+                    found = nt++;
+                    g2s.push_back(g2);
+                    cplx g = g2 >= 0 ? cplx(std::sqrt(g2), 0) : cplx(0, std::sqrt(-g2));
+                    cplx ig = 1.0 / (4.0 * a * b * g);
+                    E.tab_gamma[found][0] = g.real(); E.tab_gamma[found][1] = g.imag();
+                    E.tab_ig[found][0] = ig.real(); E.tab_ig[found][1] = ig.imag();
+                    E.tab_pre[found] = std::exp(-g2 / (4 * E.E * E.E));
+                }
+                E.rect_tab[idx] = found;
+            }
+        E.n_tab = nt;
+    }
     return VIE_OK;
 }
 
@@ -271,7 +313,17 @@ int upload_request(vie_ctx *ctx, const HostReq &H, vie::DevReq &q, cudaStream_t 
     if (ord.empty()) ord.assign(4, 0.0);
     CK(upload(ctx->orders, ord, st));
     CK(vie::upload_ewald(H.ew, st));
+    CK(ctx->stab.ensure(sizeof(float) * 4 * vie::NSPAT));
+    CK(ctx->ztab.ensure(sizeof(float2) * 4 * vie::NZTAB * std::max(H.ew.n_tab, 1)));
+    CK(vie::launch_build_tables(ctx->stab.as<float>(), ctx->ztab.as<float2>(), H.ew.n_tab, st));
+    q.stab = ctx->stab.as<float>();
+    q.ztab = ctx->ztab.as<float2>();
     q.k0 = H.k0; q.kx = H.kx; q.ky = H.ky;
+    for (int k = 0; k < 9; ++k) {
+        const double phs = H.kx * (k / 3 - 1) * ctx->topo.a + H.ky * (k % 3 - 1) * ctx->topo.b;
+        q.img_ph[2 * k] = std::cos(phs) / (4.0 * M_PI);
+        q.img_ph[2 * k + 1] = std::sin(phs) / (4.0 * M_PI);
+    }
     for (int d = 0; d < 3; ++d) q.kinc[d] = H.kinc[d];
     for (int d = 0; d < 6; ++d) q.pol[d] = H.pol[d];
     q.row = ctx->row.as<int32_t>();
@@ -293,6 +345,8 @@ vie::DevMesh dev_mesh(vie_ctx *ctx) {
     m.q5 = ctx->q5.as<double>(); m.far32 = ctx->far32.as<float>(); m.far64 = ctx->far64.as<double>();
     m.fv = ctx->fv.as<double>(); m.f5 = ctx->f5.as<double>(); m.farea = ctx->farea.as<double>();
     m.ffar32 = ctx->ffar32.as<float>(); m.ffar64 = ctx->ffar64.as<double>(); m.hf = ctx->hf.as<int32_t>();
+    m.n32 = ctx->n32.as<float>(); m.n64 = ctx->n64.as<double>();
+    m.fn32 = ctx->fn32.as<float>(); m.fn64 = ctx->fn64.as<double>(); m.fcen = ctx->fcen.as<double>();
     m.bm_tt = ctx->bm_tt.as<uint32_t>(); m.bm_tf = ctx->bm_tf.as<uint32_t>();
     m.bm_ft = ctx->bm_ft.as<uint32_t>(); m.bm_ff = ctx->bm_ff.as<uint32_t>();
     m.near_tt = ctx->n_tt.as<vie::NearPair>(); m.near_tf = ctx->n_tf.as<vie::NearPair>();
@@ -645,6 +699,11 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
     if (!e.empty()) return fail(ctx, e.find("range") != std::string::npos ? VIE_EINVAL : VIE_BAD_MESH, e);
     const vie::Topology &T = ctx->topo;
     cudaStream_t st = 0;
+    {
+        double zlo = 1e300, zhi = -1e300;
+        for (int v = 0; v < n_verts; ++v) { zlo = std::min(zlo, verts[3 * v + 2]); zhi = std::max(zhi, verts[3 * v + 2]); }
+        ctx->z_extent = zhi - zlo;
+    }
     // quadrature points
     double b2[4][4], w2[4], b5[14][4], w5[14], c2[3][3], cw2[3], c5[7][3], cw5[7];
     vie::tet_rule2(b2, w2);
@@ -673,6 +732,13 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
         F[27] = T.vol[t] * 0.25;
     }
     std::vector<float> far32(far64.begin(), far64.end());
+    std::vector<double> n64(56 * (size_t)T.nt);
+    for (int t = 0; t < T.nt; ++t)
+        for (int k = 0; k < 14; ++k) {
+            for (int d = 0; d < 3; ++d) n64[56 * (size_t)t + 4 * k + d] = q5[42 * (size_t)t + 3 * k + d] - T.cen[3 * t + d];
+            n64[56 * (size_t)t + 4 * k + 3] = T.vol[t] * w5[k];
+        }
+    std::vector<float> n32(n64.begin(), n64.end());
     const int nf = (int)T.cf.size();
     std::vector<double> f5(21 * (size_t)std::max(nf, 1)), ffar64(12 * (size_t)std::max(nf, 1), 0.0),
         farea(std::max(nf, 1));
@@ -697,6 +763,15 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
         ffar64[12 * (size_t)f + 9] = A / 3.0;
     }
     std::vector<float> ffar32(ffar64.begin(), ffar64.end());
+    std::vector<double> fn64(28 * (size_t)std::max(nf, 1), 0.0), fcen(3 * (size_t)std::max(nf, 1), 0.0);
+    for (int f = 0; f < nf; ++f) {
+        for (int d = 0; d < 3; ++d) fcen[3 * f + d] = T.fcen[3 * f + d];
+        for (int k = 0; k < 7; ++k) {
+            for (int d = 0; d < 3; ++d) fn64[28 * (size_t)f + 4 * k + d] = f5[21 * (size_t)f + 3 * k + d] - T.fcen[3 * f + d];
+            fn64[28 * (size_t)f + 4 * k + 3] = farea[f] * cw5[k];
+        }
+    }
+    std::vector<float> fn32(fn64.begin(), fn64.end());
     const int nh = (int)T.hf.size();
     auto bitmap = [](const std::vector<vie::NearPair> &L, size_t nx, size_t ny) {
         std::vector<uint32_t> bm((nx * ny + 31) / 32 + 1, 0u);
@@ -723,6 +798,11 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
     CK(upload(ctx->ffar64, ffar64, st));
     CK(upload(ctx->ffar32, ffar32, st));
     CK(upload(ctx->hf, hf, st));
+    CK(upload(ctx->n64, n64, st));
+    CK(upload(ctx->n32, n32, st));
+    CK(upload(ctx->fn64, fn64, st));
+    CK(upload(ctx->fn32, fn32, st));
+    CK(upload(ctx->fcen, fcen, st));
     CK(upload(ctx->tdom, T.dom, st));
     CK(upload(ctx->bm_tt, bitmap(T.near_tt, T.nt, T.nt), st));
     CK(upload(ctx->bm_tf, bitmap(T.near_tf, T.nt, nf), st));
@@ -831,18 +911,25 @@ int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out
     if (n == 0) return VIE_OK;
     cudaSetDevice(ctx->device);
     vie_options saved = ctx->opt;
+    const double saved_z = ctx->z_extent;
     ctx->opt.precision = precision == VIE_FP64 ? VIE_FP64 : VIE_FP32;
+    for (int i = 0; i < n; ++i) ctx->z_extent = std::max(ctx->z_extent, std::fabs(d[3 * i + 2]));   // table range
     HostReq H;
     int e = prepare(ctx, req, H);
     ctx->opt = saved;
+    ctx->z_extent = saved_z;
     if (e) return e;
     cudaStream_t st = 0;
     CK(vie::upload_ewald(H.ew, st));
+    CK(ctx->stab.ensure(sizeof(float) * 4 * vie::NSPAT));
+    CK(ctx->ztab.ensure(sizeof(float2) * 4 * vie::NZTAB * std::max(H.ew.n_tab, 1)));
+    CK(vie::launch_build_tables(ctx->stab.as<float>(), ctx->ztab.as<float2>(), H.ew.n_tab, st));
     DevBuf dd, dout;
     CK(dd.ensure(sizeof(double) * 3 * n));
     CK(dout.ensure(sizeof(double) * 2 * n));
     CK(cudaMemcpy(dd.p, d, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
-    CK(vie::launch_green(dd.as<double>(), dout.as<double>(), n, precision == VIE_FP64, st));
+    CK(vie::launch_green(dd.as<double>(), dout.as<double>(), n, precision == VIE_FP64, ctx->stab.as<float>(),
+                         ctx->ztab.as<float2>(), st));
     CK(cudaMemcpy(out, dout.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
     return VIE_OK;
 }

@@ -110,7 +110,18 @@ struct EwaldTables {
     double E, bb, a, b, xcut64;
     float xcut32;
     double reg0_re;          // limit R->0 of (image term - static term), without the phase
+    // tabulated FP32 evaluation (see green_tab): spatial kernel F(x) on [0, xs_max],
+    // spectral G_g(z) per distinct gamma on [0, z_max], piecewise cubic Hermite
+    float xs_max, xs_inv_h, z_max, z_inv_h, e_mb2, Ef;
+    float kx, ky, step_x, step_y;   // k_t,pq = (kx + p step_x, ky + q step_y)
+    int P, Q, n_tab;
+    int rect_tab[MAX_MODE];  // table of rectangle entry (p+P)(2Q+1)+(q+Q), -1 outside the cut
+    double tab_gamma[MAX_MODE][2];   // gamma of each table
+    double tab_ig[MAX_MODE][2];      // 1/(4ab gamma) of each table
+    double tab_pre[MAX_MODE];        // exp(-gamma^2/4E^2)
 };
+constexpr int NSPAT = 512;    // spatial intervals
+constexpr int NZTAB = 256;    // spectral intervals
 static __constant__ EwaldTables c_ew;        // filled by upload_ewald() (fill.cu)
 
 template <typename T> struct ETraits;
@@ -190,6 +201,80 @@ __device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub) {
         if (regular) val -= exp(-bb * bb) / R;   // static part phase/(4 pi R) in table units
         cx<T> ph = {im[2], im[3]};
         acc = acc + val * ph;
+    }
+    return acc;
+}
+
+// FP32 g_p from per-request tables (same series, same truncation as green_p):
+//  spectral: sum_pq exp(-j k_t,pq . rho) G_pq(|z|), G = [e^{gz}erfc(..) + e^{-gz}erfc(..)]/(4ab g)
+//            tabulated per distinct gamma; phases by recurrence over the (p, q) rectangle
+//  spatial:  phase_mn exp(b^2)/(4 pi) F(R E)/R with F(x) = exp(-x^2) Re erfcx(x + j b);
+//            the regularised near image uses (F(RE) - F(0))/R, formed without
+//            cancellation in the first interval
+// stab: [NSPAT][4] cubic coefficients (shared memory); ztab: [n_tab][NZTAB][4] complex
+__device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, unsigned sub, const float *stab,
+                                               const float2 *__restrict__ ztab) {
+    cx<float> acc = {0.f, 0.f};
+    const float z = fabsf(dz);
+    float zu = fminf(z * c_ew.z_inv_h, float(NZTAB));
+    int iz = min((int)zu, NZTAB - 1);
+    const float u = zu - iz;
+    const int P = c_ew.P, Q = c_ew.Q, nq = 2 * Q + 1;
+    float s, c;
+    sincospif(-(c_ew.kx - P * c_ew.step_x) * dx * 0.31830988618f, &s, &c);
+    cx<float> ex = {c, s};
+    sincospif(-c_ew.step_x * dx * 0.31830988618f, &s, &c);
+    const cx<float> sx = {c, s};
+    sincospif(-(c_ew.ky - Q * c_ew.step_y) * dy * 0.31830988618f, &s, &c);
+    cx<float> ey0 = {c, s};
+    sincospif(-c_ew.step_y * dy * 0.31830988618f, &s, &c);
+    const cx<float> sy = {c, s};
+    for (int p = 0; p <= 2 * P; ++p) {
+        cx<float> inner = {0.f, 0.f};
+        cx<float> ey = ey0;
+        for (int q = 0; q < nq; ++q) {
+            const int tb = c_ew.rect_tab[p * nq + q];
+            if (tb >= 0) {
+                const float2 *cf = ztab + ((size_t)tb * NZTAB + iz) * 4;
+                const float2 c0 = __ldg(cf), c1 = __ldg(cf + 1), c2 = __ldg(cf + 2), c3 = __ldg(cf + 3);
+                cx<float> g = {fmaf(u, fmaf(u, fmaf(u, c3.x, c2.x), c1.x), c0.x),
+                               fmaf(u, fmaf(u, fmaf(u, c3.y, c2.y), c1.y), c0.y)};
+                inner = inner + ey * g;
+            }
+            ey = ey * sy;
+        }
+        acc = acc + ex * inner;
+        ex = ex * sx;
+    }
+    const float E = c_ew.Ef;
+    const float xmax = c_ew.xs_max, ih = c_ew.xs_inv_h;
+    for (int i = 0; i < c_ew.n_img; ++i) {
+        const float *im = c_ew.img32[i];
+        const float x = dx + im[0], y = dy + im[1];
+        const float R = sqrtf(x * x + y * y + dz * dz);
+        const float xr = R * E;
+        if (xr > xmax) continue;
+        bool regular = false;
+        if (sub) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                if (((sub >> k) & 1u) && c_ew.near_img[k] == i) regular = true;
+        }
+        const float xu = xr * ih;
+        const int ix = min((int)xu, NSPAT - 1);
+        const float v = xu - ix;
+        const float *cs = stab + 4 * ix;
+        float val;
+        if (regular) {
+            if (ix == 0)   // (F(x) - F(0))/R = E (c1 + v (c2 + v c3)) / h
+                val = E * ih * fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]);
+            else
+                val = (fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) - c_ew.e_mb2) / R;
+        } else {
+            val = fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) / R;
+        }
+        acc.re = fmaf(val, im[2], acc.re);
+        acc.im = fmaf(val, im[3], acc.im);
     }
     return acc;
 }

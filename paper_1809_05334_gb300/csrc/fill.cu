@@ -68,6 +68,105 @@ cudaError_t upload_ewald(const EwaldTables &t, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
+// per-request tables of the FP32 path (built in FP64 from the Ewald series):
+// cubic Hermite coefficients per interval, in the local variable u in [0, 1)
+// ---------------------------------------------------------------------------
+__device__ void hermite(double f0, double d0, double f1, double d1, double h, double c[4]) {
+    c[0] = f0;
+    c[1] = h * d0;
+    c[2] = 3.0 * (f1 - f0) - h * (2.0 * d0 + d1);
+    c[3] = 2.0 * (f0 - f1) + h * (d0 + d1);
+}
+
+__device__ void spatial_node(double x, double &F, double &dF) {
+    // F(x) = exp(-x^2) Re erfcx(x + j b),  F'(x) = -exp(-x^2) (2 b Im erfcx(x + j b) + 2/sqrt(pi))
+    const double b = c_ew.bb;
+    cx<double> w = erfcx_c<double>(cx<double>{x, b});
+    const double g = exp(-x * x);
+    F = g * w.re;
+    dF = -g * (2.0 * b * w.im + 2.0 * rsqrt_pi<double>());
+}
+
+__device__ void spectral_node(int tb, double z, cx<double> &G, cx<double> &dG) {
+    // G(z) = (t1 + t2)/(4ab gamma), G'(z) = gamma (t1 - t2)/(4ab gamma)
+    const double E = c_ew.E;
+    const cx<double> g = {c_ew.tab_gamma[tb][0], c_ew.tab_gamma[tb][1]};
+    const cx<double> ig = {c_ew.tab_ig[tb][0], c_ew.tab_ig[tb][1]};
+    const double pre = c_ew.tab_pre[tb] * exp(-(z * E) * (z * E));
+    cx<double> t1, t2;
+    if (g.im == 0.0) {
+        const double gr = g.re;
+        t1 = {pre * erfcx_r<double>(gr / (2 * E) + z * E), 0.0};
+        const double u = gr / (2 * E) - z * E;
+        t2 = {(u >= 0) ? pre * erfcx_r<double>(u) : 2.0 * exp(-gr * z) - pre * erfcx_r<double>(-u), 0.0};
+    } else {
+        const double gi = g.im;
+        cx<double> e1 = erfcx_c<double>(cx<double>{z * E, gi / (2 * E)});
+        double sg, cg;
+        sincos(gi * z, &sg, &cg);
+        t1 = pre * e1;
+        t2 = cx<double>{2.0 * cg - pre * e1.re, -2.0 * sg + pre * e1.im};
+    }
+    G = (t1 + t2) * ig;
+    dG = (g * (t1 - t2)) * ig;
+}
+
+__global__ void k_build_tables(float *stab, float2 *ztab, int n_tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NSPAT) {
+        const double h = double(c_ew.xs_max) / NSPAT;
+        double F0, D0, F1, D1, c[4];
+        spatial_node(i * h, F0, D0);
+        spatial_node((i + 1) * h, F1, D1);
+        hermite(F0, D0, F1, D1, h, c);
+        for (int k = 0; k < 4; ++k) stab[4 * i + k] = float(c[k]);
+        return;
+    }
+    const int j = i - NSPAT;
+    const int tb = j / NZTAB, iz = j % NZTAB;
+    if (tb >= n_tab) return;
+    const double h = double(c_ew.z_max) / NZTAB;
+    cx<double> G0, D0, G1, D1;
+    spectral_node(tb, iz * h, G0, D0);
+    spectral_node(tb, (iz + 1) * h, G1, D1);
+    double cr[4], ci[4];
+    hermite(G0.re, D0.re, G1.re, D1.re, h, cr);
+    hermite(G0.im, D0.im, G1.im, D1.im, h, ci);
+    for (int k = 0; k < 4; ++k) ztab[((size_t)tb * NZTAB + iz) * 4 + k] = make_float2(float(cr[k]), float(ci[k]));
+}
+
+cudaError_t launch_build_tables(float *stab, float2 *ztab, int n_tab, cudaStream_t st) {
+    const int n = NSPAT + n_tab * NZTAB;
+    k_build_tables<<<(n + 127) / 128, 128, 0, st>>>(stab, ztab, n_tab);
+    return cudaGetLastError();
+}
+
+// g_p for the fill kernels: FP64 by the Ewald series, FP32 from the tables
+template <typename T> struct Green;
+template <> struct Green<double> {
+    __device__ static cx<double> eval(double dx, double dy, double dz, unsigned sub, const float *, const float2 *) {
+        return green_p<double>(dx, dy, dz, sub);
+    }
+};
+template <> struct Green<float> {
+    __device__ static cx<float> eval(float dx, float dy, float dz, unsigned sub, const float *stab,
+                                     const float2 *ztab) {
+        return green_tab(dx, dy, dz, sub, stab, ztab);
+    }
+};
+
+// stage the spatial table in shared memory (FP32 path only)
+template <typename T>
+__device__ __forceinline__ const float *stage_stab(const DevReq &q, float *smem) {
+    if (sizeof(T) == 8) return nullptr;
+    for (int i = threadIdx.x; i < 4 * NSPAT; i += blockDim.x) smem[i] = q.stab[i];
+    __syncthreads();
+    return smem;
+}
+
+template <typename T> constexpr size_t stab_bytes() { return sizeof(T) == 4 ? 4 * NSPAT * sizeof(float) : 0; }
+
+// ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
 template <typename T> struct Mom {
@@ -122,6 +221,8 @@ __device__ void scatter_tt(const DevMesh &m, const DevReq &q, T *Z, size_t N, in
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(128) k_far_tt(DevMesh m, DevReq q, T *Z, size_t N) {
+    extern __shared__ float smem_tab[];
+    const float *stab = stage_stab<T>(q, smem_tab);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = blockIdx.y;
     if (s >= m.nt) return;
@@ -137,7 +238,7 @@ __global__ void __launch_bounds__(128) k_far_tt(DevMesh m, DevReq q, T *Z, size_
         for (int b = 0; b < 4; ++b) {
             const T yb[3] = {fs[3 * b], fs[3 * b + 1], fs[3 * b + 2]};
             const T rb[3] = {yb[0] - fs[12], yb[1] - fs[13], yb[2] - fs[14]};
-            cx<T> g = green_p<T>(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], 0u);
+            cx<T> g = Green<T>::eval(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], 0u, stab, q.ztab);
             g = wgt * g;
             mo.S = mo.S + g;
             for (int d = 0; d < 3; ++d) {
@@ -196,34 +297,60 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename T>
 __global__ void __launch_bounds__(128) k_near_tt(DevMesh m, DevReq q, T *Z, size_t N,
                                                  const NearPair *list, int n) {
+    extern __shared__ float smem_tab[];
+    const float *stab = stage_stab<T>(q, smem_tab);
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= n) return;
     const NearPair pr = list[wid];
     const int t = pr.x, s = pr.y;
-    Mom<double> acc;
-    acc.zero();
-    if (lane < 28) {
-        const bool oi = lane < 14;
-        const int qi = oi ? lane : lane - 14;
-        const int self = oi ? t : s, other = oi ? s : t;
-        const double *r5 = m.q5 + (size_t)self * 42 + 3 * qi;
-        const double w = m.vol[self] * c_w5tet[qi];
-        for (int k = 0; k < 9; ++k) {
-            if (!((pr.mask >> k) & 1u)) continue;
-            const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
-            double sp, cp;
-            sincos(q.kx * R[0] + q.ky * R[1], &sp, &cp);
-            const double f = 0.5 / (4.0 * M_PI);
-            cx<double> ph = {f * cp, f * sp};
-            // order (i): source image y - R; order (ii): test image x + R
-            const double sg = oi ? -1.0 : 1.0;
-            if ((pr.touch >> k) & 1u)
-                static_tt_term<double>(r5, w, m.tv + 12 * (size_t)other, R, sg, m.cen + 3 * self,
-                                       m.cen + 3 * other, oi, ph, acc);
-            else
-                static_tt_term<T>(r5, w, m.tv + 12 * (size_t)other, R, sg, m.cen + 3 * self,
-                                  m.cen + 3 * other, oi, ph, acc);
+    Mom<double> accd;        // closed forms of touching images (FP64)
+    accd.zero();
+    Mom<T> acct;             // product-rule static parts and the smooth remainder (T)
+    acct.zero();
+    const double *ct = m.cen + 3 * (size_t)t, *cs = m.cen + 3 * (size_t)s;
+    for (int k = 0; k < 9; ++k) {
+        if (!((pr.mask >> k) & 1u)) continue;
+        const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
+        const cx<double> ph = {q.img_ph[2 * k], q.img_ph[2 * k + 1]};   // exp(j k_par.R)/(4 pi)
+        if ((pr.touch >> k) & 1u) {
+            // touching: closed form over one element at the degree-5 points of the
+            // other, both orders averaged (lanes 0..13: order (i), 14..27: order (ii))
+            if (lane < 28) {
+                const bool oi = lane < 14;
+                const int qi = oi ? lane : lane - 14;
+                const int self = oi ? t : s, other = oi ? s : t;
+                const double *r5 = m.q5 + (size_t)self * 42 + 3 * qi;
+                const double w = m.vol[self] * c_w5tet[qi];
+                const cx<double> hph = {0.5 * ph.re, 0.5 * ph.im};
+                static_tt_term<double>(r5, w, m.tv + 12 * (size_t)other, R, oi ? -1.0 : 1.0, m.cen + 3 * self,
+                                       m.cen + 3 * other, oi, hph, accd);
+            }
+        } else {
+            // near but not touching: degree-5 x degree-5 product rule of 1/(4 pi R),
+            // points relative to their centroids in T, centroid offset formed in FP64
+            const T *nx = m.nrel<T>(t), *ny = m.nrel<T>(s);
+            const T dc[3] = {T(ct[0] - cs[0] + R[0]), T(ct[1] - cs[1] + R[1]), T(ct[2] - cs[2])};
+            T s0 = 0, sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0}, sC = 0;
+            for (int p = lane; p < 196; p += 32) {
+                const int a = p / 14, b = p % 14;
+                const T *xa = nx + 4 * a, *yb = ny + 4 * b;
+                const T dx = xa[0] - yb[0] + dc[0], dy = xa[1] - yb[1] + dc[1], dz = xa[2] - yb[2] + dc[2];
+                const T f = xa[3] * yb[3] / sqrt(dx * dx + dy * dy + dz * dz);
+                s0 += f;
+                for (int d = 0; d < 3; ++d) {
+                    sA[d] += f * xa[d];
+                    sB[d] += f * yb[d];
+                }
+                sC += f * (xa[0] * yb[0] + xa[1] * yb[1] + xa[2] * yb[2]);
+            }
+            const cx<T> pt = {T(ph.re), T(ph.im)};
+            acct.S = acct.S + s0 * pt;
+            acct.C = acct.C + sC * pt;
+            for (int d = 0; d < 3; ++d) {
+                acct.A[d] = acct.A[d] + sA[d] * pt;
+                acct.B[d] = acct.B[d] + sB[d] * pt;
+            }
         }
     }
     if (lane < 16) {
@@ -232,24 +359,25 @@ __global__ void __launch_bounds__(128) k_near_tt(DevMesh m, DevReq q, T *Z, size
         const int a = lane >> 2, b = lane & 3;
         const T xa[3] = {ft[3 * a], ft[3 * a + 1], ft[3 * a + 2]};
         const T yb[3] = {fs[3 * b], fs[3 * b + 1], fs[3 * b + 2]};
-        cx<T> g = green_p<T>(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], pr.mask);
-        const double wg = double(ft[27]) * double(fs[27]);
-        cx<double> gd = {wg * double(g.re), wg * double(g.im)};
-        double ra[3], rb[3];
+        cx<T> g = Green<T>::eval(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], pr.mask, stab, q.ztab);
+        g = (ft[27] * fs[27]) * g;
+        T ra[3], rb[3];
         for (int d = 0; d < 3; ++d) {
-            ra[d] = double(xa[d]) - double(ft[12 + d]);
-            rb[d] = double(yb[d]) - double(fs[12 + d]);
+            ra[d] = xa[d] - ft[12 + d];
+            rb[d] = yb[d] - fs[12 + d];
         }
-        acc.S = acc.S + gd;
+        acct.S = acct.S + g;
         for (int d = 0; d < 3; ++d) {
-            acc.A[d] = acc.A[d] + ra[d] * gd;
-            acc.B[d] = acc.B[d] + rb[d] * gd;
+            acct.A[d] = acct.A[d] + ra[d] * g;
+            acct.B[d] = acct.B[d] + rb[d] * g;
         }
-        acc.C = acc.C + (ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2]) * gd;
+        acct.C = acct.C + (ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2]) * g;
     }
-    double v[16] = {acc.S.re, acc.S.im, acc.C.re, acc.C.im,
-                    acc.A[0].re, acc.A[0].im, acc.A[1].re, acc.A[1].im, acc.A[2].re, acc.A[2].im,
-                    acc.B[0].re, acc.B[0].im, acc.B[1].re, acc.B[1].im, acc.B[2].re, acc.B[2].im};
+    double v[16] = {accd.S.re + acct.S.re, accd.S.im + acct.S.im, accd.C.re + acct.C.re, accd.C.im + acct.C.im,
+                    accd.A[0].re + acct.A[0].re, accd.A[0].im + acct.A[0].im, accd.A[1].re + acct.A[1].re,
+                    accd.A[1].im + acct.A[1].im, accd.A[2].re + acct.A[2].re, accd.A[2].im + acct.A[2].im,
+                    accd.B[0].re + acct.B[0].re, accd.B[0].im + acct.B[0].im, accd.B[1].re + acct.B[1].re,
+                    accd.B[1].im + acct.B[1].im, accd.B[2].re + acct.B[2].re, accd.B[2].im + acct.B[2].im};
     for (int i = 0; i < 16; ++i) v[i] = warp_sum(v[i]);
     if (lane == 0) {
         Mom<T> mo;
@@ -311,6 +439,8 @@ __device__ __forceinline__ const T *far_el(const DevMesh &m, int e) {
 template <typename T, int PK>
 __global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, DevReq q, T *Z, size_t N, int nx, int ny,
                                                     const uint32_t *bm) {
+    extern __shared__ float smem_tab[];
+    const float *stab = stage_stab<T>(q, smem_tab);
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     const int x = blockIdx.y;
     if (y >= ny) return;
@@ -324,7 +454,8 @@ __global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, DevReq q, T *Z, s
     cx<T> S = {0, 0};
     for (int a = 0; a < qx; ++a)
         for (int b = 0; b < qy; ++b) {
-            cx<T> g = green_p<T>(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1], fx[3 * a + 2] - fy[3 * b + 2], 0u);
+            cx<T> g = Green<T>::eval(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1], fx[3 * a + 2] - fy[3 * b + 2],
+                                     0u, stab, q.ztab);
             S = S + g;
         }
     S = wgt * S;
@@ -353,6 +484,8 @@ __device__ double static_scalar(const double *r5, bool other_tet, const double *
 template <typename T, int PK>
 __global__ void __launch_bounds__(128) k_near_scalar(DevMesh m, DevReq q, T *Z, size_t N,
                                                      const NearPair *list, int n) {
+    extern __shared__ float smem_tab[];
+    const float *stab = stage_stab<T>(q, smem_tab);
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= n) return;
@@ -362,29 +495,45 @@ __global__ void __launch_bounds__(128) k_near_scalar(DevMesh m, DevReq q, T *Z, 
     // face elements are addressed through the charge-face index
     const int xf = XT ? x : m.hf[x];
     const int yf = y;
-    const int nqx = XT ? 14 : 7, nqy = YT ? 14 : 7;
-    cx<double> acc = {0, 0};
-    if (lane < nqx + nqy) {
-        const bool oi = lane < nqx;
-        const int qi = oi ? lane : lane - nqx;
-        const bool self_tet = oi ? XT : YT;
-        const int self = oi ? (XT ? x : xf) : (YT ? y : yf);
-        const bool other_tet = oi ? YT : XT;
-        const int other = oi ? (YT ? y : yf) : (XT ? x : xf);
-        const double *r5 = self_tet ? m.q5 + (size_t)self * 42 + 3 * qi : m.f5 + (size_t)self * 21 + 3 * qi;
-        const double w = self_tet ? m.vol[self] * c_w5tet[qi] : m.farea[self] * c_w5tri[qi];
-        const double *vo = other_tet ? m.tv + 12 * (size_t)other : m.fv + 9 * (size_t)other;
-        for (int k = 0; k < 9; ++k) {
-            if (!((pr.mask >> k) & 1u)) continue;
-            const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
-            double sp, cp;
-            sincos(q.kx * R[0] + q.ky * R[1], &sp, &cp);
-            const double f = 0.5 * w / (4.0 * M_PI);
-            const double sg = oi ? -1.0 : 1.0;
-            double I = ((pr.touch >> k) & 1u) ? static_scalar<double>(r5, other_tet, vo, R, sg)
-                                              : static_scalar<T>(r5, other_tet, vo, R, sg);
-            acc.re += f * cp * I;
-            acc.im += f * sp * I;
+    constexpr int nqx = XT ? 14 : 7, nqy = YT ? 14 : 7;
+    const double *x5 = XT ? m.q5 + (size_t)xf * 42 : m.f5 + (size_t)xf * 21;
+    const double *y5 = YT ? m.q5 + (size_t)yf * 42 : m.f5 + (size_t)yf * 21;
+    const double mx = XT ? m.vol[xf] : m.farea[xf];
+    const double my = YT ? m.vol[yf] : m.farea[yf];
+    cx<double> accd = {0, 0};
+    cx<T> acct = {0, 0};
+    for (int k = 0; k < 9; ++k) {
+        if (!((pr.mask >> k) & 1u)) continue;
+        const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
+        const cx<double> ph = {q.img_ph[2 * k], q.img_ph[2 * k + 1]};
+        if ((pr.touch >> k) & 1u) {
+            if (lane < nqx + nqy) {
+                const bool oi = lane < nqx;
+                const int qi = oi ? lane : lane - nqx;
+                const bool self_tet = oi ? XT : YT;
+                const bool other_tet = oi ? YT : XT;
+                const int other = oi ? yf : xf;
+                const double *r5 = (oi ? x5 : y5) + 3 * qi;
+                const double w = (oi ? mx : my) * (self_tet ? c_w5tet[qi] : c_w5tri[qi]);
+                const double *vo = other_tet ? m.tv + 12 * (size_t)other : m.fv + 9 * (size_t)other;
+                const double I = static_scalar<double>(r5, other_tet, vo, R, oi ? -1.0 : 1.0);
+                accd.re += 0.5 * w * ph.re * I;
+                accd.im += 0.5 * w * ph.im * I;
+            }
+        } else {
+            const T *nx = XT ? m.nrel<T>(xf) : m.fnrel<T>(xf);
+            const T *ny = YT ? m.nrel<T>(yf) : m.fnrel<T>(yf);
+            const double *cxp = XT ? m.cen + 3 * (size_t)xf : m.fcen + 3 * (size_t)xf;
+            const double *cyp = YT ? m.cen + 3 * (size_t)yf : m.fcen + 3 * (size_t)yf;
+            const T dc[3] = {T(cxp[0] - cyp[0] + R[0]), T(cxp[1] - cyp[1] + R[1]), T(cxp[2] - cyp[2])};
+            T s0 = 0;
+            for (int p = lane; p < nqx * nqy; p += 32) {
+                const int a = p / nqy, b = p % nqy;
+                const T *xa = nx + 4 * a, *yb = ny + 4 * b;
+                const T dx = xa[0] - yb[0] + dc[0], dy = xa[1] - yb[1] + dc[1], dz = xa[2] - yb[2] + dc[2];
+                s0 += xa[3] * yb[3] / sqrt(dx * dx + dy * dy + dz * dz);
+            }
+            acct = acct + s0 * cx<T>{T(ph.re), T(ph.im)};
         }
     }
     const int qx = XT ? 4 : 3, qy = YT ? 4 : 3;
@@ -392,12 +541,11 @@ __global__ void __launch_bounds__(128) k_near_scalar(DevMesh m, DevReq q, T *Z, 
         const T *fx = far_el<T, XT>(m, xf);
         const T *fy = far_el<T, YT>(m, yf);
         const int a = lane / qy, b = lane % qy;
-        cx<T> g = green_p<T>(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1], fx[3 * a + 2] - fy[3 * b + 2], pr.mask);
-        const double wg = double(fx[XT ? 27 : 9]) * double(fy[YT ? 27 : 9]);
-        acc.re += wg * double(g.re);
-        acc.im += wg * double(g.im);
+        cx<T> g = Green<T>::eval(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1], fx[3 * a + 2] - fy[3 * b + 2],
+                                 pr.mask, stab, q.ztab);
+        acct = acct + (fx[XT ? 27 : 9] * fy[YT ? 27 : 9]) * g;
     }
-    double sr = warp_sum(acc.re), si = warp_sum(acc.im);
+    double sr = warp_sum(accd.re + double(acct.re)), si = warp_sum(accd.im + double(acct.im));
     if (lane == 0) scatter_scalar<T, PK>(m, q, Z, N, x, y, cx<T>{T(sr), T(si)});
 }
 
@@ -472,10 +620,10 @@ __global__ void k_erfcx(const double *u, double *out, int n) {
 }
 
 template <typename T>
-__global__ void k_green(const double *d, double *out, int n) {
+__global__ void k_green(const double *d, double *out, int n, const float *stab, const float2 *ztab) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    cx<T> r = green_p<T>(T(d[3 * i]), T(d[3 * i + 1]), T(d[3 * i + 2]), 0u);
+    cx<T> r = Green<T>::eval(T(d[3 * i]), T(d[3 * i + 1]), T(d[3 * i + 2]), 0u, stab, ztab);
     out[2 * i] = double(r.re);
     out[2 * i + 1] = double(r.im);
 }
@@ -494,18 +642,19 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
     k_gram<T><<<(m.nt + 127) / 128, blk, 0, st>>>(m, q, Z, N);
     if (b) k_rhs<<<(m.nt + 127) / 128, blk, 0, st>>>(m, q, b);
     if (far0) cudaEventRecord(far0, st);
-    k_far_tt<T><<<dim3((m.nt + 127) / 128, m.nt), blk, 0, st>>>(m, q, Z, N);
+    const size_t sm = stab_bytes<T>();
+    k_far_tt<T><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N);
     if (far1) cudaEventRecord(far1, st);
-    if (m.n_tt) k_near_tt<T><<<(m.n_tt * 32 + 127) / 128, blk, 0, st>>>(m, q, Z, N, m.near_tt, m.n_tt);
+    if (m.n_tt) k_near_tt<T><<<(m.n_tt * 32 + 127) / 128, blk, sm, st>>>(m, q, Z, N, m.near_tt, m.n_tt);
     if (m.nf) {
-        k_far_scalar<T, PK_TF><<<dim3((m.nf + 127) / 128, m.nt), blk, 0, st>>>(m, q, Z, N, m.nt, m.nf, m.bm_tf);
-        if (m.n_tf) k_near_scalar<T, PK_TF><<<(m.n_tf * 32 + 127) / 128, blk, 0, st>>>(m, q, Z, N, m.near_tf, m.n_tf);
+        k_far_scalar<T, PK_TF><<<dim3((m.nf + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N, m.nt, m.nf, m.bm_tf);
+        if (m.n_tf) k_near_scalar<T, PK_TF><<<(m.n_tf * 32 + 127) / 128, blk, sm, st>>>(m, q, Z, N, m.near_tf, m.n_tf);
     }
     if (m.nh) {
-        k_far_scalar<T, PK_FT><<<dim3((m.nt + 127) / 128, m.nh), blk, 0, st>>>(m, q, Z, N, m.nh, m.nt, m.bm_ft);
-        if (m.n_ft) k_near_scalar<T, PK_FT><<<(m.n_ft * 32 + 127) / 128, blk, 0, st>>>(m, q, Z, N, m.near_ft, m.n_ft);
-        k_far_scalar<T, PK_FF><<<dim3((m.nf + 127) / 128, m.nh), blk, 0, st>>>(m, q, Z, N, m.nh, m.nf, m.bm_ff);
-        if (m.n_ff) k_near_scalar<T, PK_FF><<<(m.n_ff * 32 + 127) / 128, blk, 0, st>>>(m, q, Z, N, m.near_ff, m.n_ff);
+        k_far_scalar<T, PK_FT><<<dim3((m.nt + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nt, m.bm_ft);
+        if (m.n_ft) k_near_scalar<T, PK_FT><<<(m.n_ft * 32 + 127) / 128, blk, sm, st>>>(m, q, Z, N, m.near_ft, m.n_ft);
+        k_far_scalar<T, PK_FF><<<dim3((m.nf + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nf, m.bm_ff);
+        if (m.n_ff) k_near_scalar<T, PK_FF><<<(m.n_ff * 32 + 127) / 128, blk, sm, st>>>(m, q, Z, N, m.near_ff, m.n_ff);
     }
     return cudaGetLastError();
 }
@@ -521,9 +670,10 @@ cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_green(const double *d, double *out, int n, bool fp64, cudaStream_t st) {
-    if (fp64) k_green<double><<<(n + 127) / 128, 128, 0, st>>>(d, out, n);
-    else k_green<float><<<(n + 127) / 128, 128, 0, st>>>(d, out, n);
+cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const float *stab, const float2 *ztab,
+                         cudaStream_t st) {
+    if (fp64) k_green<double><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab);
+    else k_green<float><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab);
     return cudaGetLastError();
 }
 

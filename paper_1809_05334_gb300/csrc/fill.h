@@ -17,6 +17,11 @@ struct DevMesh {
     const double *cen;     // [nt][3]
     const double *vol;     // [nt]
     const double *q5;      // [nt][14][3] degree-5 points
+    const float *n32;      // [nt][14][4]: degree-5 point minus centroid, vol * weight
+    const double *n64;
+    const float *fn32;     // [nf][7][4]: degree-5 point minus face centroid, area * weight
+    const double *fn64;
+    const double *fcen;    // [nf][3] charge-face centroids
     const float *far32;    // [nt][28]: 4 points, centroid, v_i - c (4x3), weight vol/4
     const double *far64;
     const double *fv;      // [nf][9] charge-face vertices
@@ -31,11 +36,17 @@ struct DevMesh {
 
     template <typename T> __device__ const T *far(int t) const;
     template <typename T> __device__ const T *ffar(int f) const;
+    template <typename T> __device__ const T *nrel(int t) const;
+    template <typename T> __device__ const T *fnrel(int f) const;
 };
 template <> __device__ inline const float *DevMesh::far<float>(int t) const { return far32 + 28 * (size_t)t; }
 template <> __device__ inline const double *DevMesh::far<double>(int t) const { return far64 + 28 * (size_t)t; }
 template <> __device__ inline const float *DevMesh::ffar<float>(int f) const { return ffar32 + 12 * (size_t)f; }
 template <> __device__ inline const double *DevMesh::ffar<double>(int f) const { return ffar64 + 12 * (size_t)f; }
+template <> __device__ inline const float *DevMesh::nrel<float>(int t) const { return n32 + 56 * (size_t)t; }
+template <> __device__ inline const double *DevMesh::nrel<double>(int t) const { return n64 + 56 * (size_t)t; }
+template <> __device__ inline const float *DevMesh::fnrel<float>(int f) const { return fn32 + 28 * (size_t)f; }
+template <> __device__ inline const double *DevMesh::fnrel<double>(int f) const { return fn64 + 28 * (size_t)f; }
 
 struct DevReq {
     double k0, kx, ky;
@@ -48,6 +59,9 @@ struct DevReq {
     const double *ieps;    // [nt][2] 1/eps_r
     const int32_t *frow;   // [nf] matrix row of each charge face's unknown
     const double *qs;      // [nf][2] surface charge kappa- - kappa+ (kappa- = 0 for half)
+    double img_ph[18];     // exp(j k_par.R_k)/(4 pi) of the near images k = 0..8
+    const float *stab;     // FP32 tables of the Ewald series (built per request)
+    const float2 *ztab;
 };
 
 // degree-5 rules: barycentric points [14][4] / [7][3] (may be null) and weights
@@ -62,6 +76,8 @@ template <typename T>
 cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, double *b, cudaStream_t st,
                         cudaEvent_t far0 = nullptr, cudaEvent_t far1 = nullptr);
 cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStream_t st);
-cudaError_t launch_green(const double *d, double *out, int n, bool fp64, cudaStream_t st);
+cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const float *stab, const float2 *ztab,
+                         cudaStream_t st);
+cudaError_t launch_build_tables(float *stab, float2 *ztab, int n_tab, cudaStream_t st);
 
 }  // namespace vie
