@@ -101,7 +101,7 @@ typedef struct {
     double  k_far_tt_ms, k_fill_ms, k_factor_ms, k_matvec_ms;
     int32_t k_matvec_n;
     int32_t n_near_pairs;                /* near tetrahedron pairs of the mesh       */
-    int64_t far_pair_evals;              /* Green's-function evaluations of the far
+    int64_t far_pair_evals;              /* Green's-function evaluations of the
                                             tetrahedron-pair kernel (16 per pair)   */
 } vie_result;
 

@@ -65,7 +65,8 @@ struct vie_ctx {
     vie::Topology topo;
     // mesh (device)
     DevBuf tv, cen, vol, q5, far32, far64, fv, f5, farea, ffar32, ffar64, hf, n32, n64, fn32, fn64, fcen;
-    DevBuf bm_tt, bm_tf, bm_ft, bm_ff, n_tt, n_tf, n_ft, n_ff, tdom;
+    DevBuf mk[4], pr[4], to[4], tdom;
+    int npr[4] = {0, 0, 0, 0}, nto[4] = {0, 0, 0, 0};
     // request (device)
     DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab;
     double z_extent = 0;
@@ -347,12 +348,14 @@ vie::DevMesh dev_mesh(vie_ctx *ctx) {
     m.ffar32 = ctx->ffar32.as<float>(); m.ffar64 = ctx->ffar64.as<double>(); m.hf = ctx->hf.as<int32_t>();
     m.n32 = ctx->n32.as<float>(); m.n64 = ctx->n64.as<double>();
     m.fn32 = ctx->fn32.as<float>(); m.fn64 = ctx->fn64.as<double>(); m.fcen = ctx->fcen.as<double>();
-    m.bm_tt = ctx->bm_tt.as<uint32_t>(); m.bm_tf = ctx->bm_tf.as<uint32_t>();
-    m.bm_ft = ctx->bm_ft.as<uint32_t>(); m.bm_ff = ctx->bm_ff.as<uint32_t>();
-    m.near_tt = ctx->n_tt.as<vie::NearPair>(); m.near_tf = ctx->n_tf.as<vie::NearPair>();
-    m.near_ft = ctx->n_ft.as<vie::NearPair>(); m.near_ff = ctx->n_ff.as<vie::NearPair>();
-    m.n_tt = (int)T.near_tt.size(); m.n_tf = (int)T.near_tf.size();
-    m.n_ft = (int)T.near_ft.size(); m.n_ff = (int)T.near_ff.size();
+    m.mk_tt = ctx->mk[0].as<uint16_t>(); m.mk_tf = ctx->mk[1].as<uint16_t>();
+    m.mk_ft = ctx->mk[2].as<uint16_t>(); m.mk_ff = ctx->mk[3].as<uint16_t>();
+    for (int i = 0; i < 4; ++i) {
+        m.pr[i] = ctx->pr[i].as<vie::NearEntry>();
+        m.to[i] = ctx->to[i].as<vie::NearEntry>();
+        m.npr[i] = ctx->npr[i];
+        m.nto[i] = ctx->nto[i];
+    }
     return m;
 }
 
@@ -626,7 +629,7 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     res->t_post_ms = ms(t3, t4);
     res->n_unknowns = ctx->topo.N;
     res->n_near_pairs = (int32_t)ctx->topo.near_tt.size();
-    res->far_pair_evals = 16 * ((int64_t)ctx->topo.nt * ctx->topo.nt - (int64_t)ctx->topo.near_tt.size());
+    res->far_pair_evals = 16 * (int64_t)ctx->topo.nt * ctx->topo.nt;
     if (ctx->opt.timing) {
         res->k_far_tt_ms = ev_ms(tm.far0, tm.far1);
         res->k_fill_ms = ev_ms(tm.fill0, tm.fill1);
@@ -773,15 +776,19 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
     }
     std::vector<float> fn32(fn64.begin(), fn64.end());
     const int nh = (int)T.hf.size();
-    auto bitmap = [](const std::vector<vie::NearPair> &L, size_t nx, size_t ny) {
-        std::vector<uint32_t> bm((nx * ny + 31) / 32 + 1, 0u);
-        for (auto &p : L) {
-            size_t i = (size_t)p.x * ny + p.y;
-            bm[i >> 5] |= 1u << (i & 31);
-        }
-        return bm;
+    // dense near-image masks and the (pair, image) entry lists
+    auto masks = [](const std::vector<vie::NearPair> &L, size_t nx, size_t ny) {
+        std::vector<uint16_t> mk(std::max<size_t>(nx * ny, 1), 0);
+        for (auto &p : L) mk[(size_t)p.x * ny + p.y] = p.mask;
+        return mk;
     };
-    auto nz = [](std::vector<vie::NearPair> v) { if (v.empty()) v.push_back({0, 0, 0, 0}); return v; };
+    auto entries = [](const std::vector<vie::NearPair> &L, bool touching) {
+        std::vector<vie::NearEntry> out;
+        for (auto &p : L)
+            for (int k = 0; k < 9; ++k)
+                if (((p.mask >> k) & 1u) && (((p.touch >> k) & 1u) != 0) == touching) out.push_back({p.x, p.y, k, 0});
+        return out;
+    };
     std::vector<int32_t> hf = T.hf;
     if (hf.empty()) hf.push_back(0);
     std::vector<double> fv = T.fv;
@@ -804,14 +811,19 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
     CK(upload(ctx->fn32, fn32, st));
     CK(upload(ctx->fcen, fcen, st));
     CK(upload(ctx->tdom, T.dom, st));
-    CK(upload(ctx->bm_tt, bitmap(T.near_tt, T.nt, T.nt), st));
-    CK(upload(ctx->bm_tf, bitmap(T.near_tf, T.nt, nf), st));
-    CK(upload(ctx->bm_ft, bitmap(T.near_ft, nh, T.nt), st));
-    CK(upload(ctx->bm_ff, bitmap(T.near_ff, nh, nf), st));
-    CK(upload(ctx->n_tt, nz(T.near_tt), st));
-    CK(upload(ctx->n_tf, nz(T.near_tf), st));
-    CK(upload(ctx->n_ft, nz(T.near_ft), st));
-    CK(upload(ctx->n_ff, nz(T.near_ff), st));
+    const std::vector<vie::NearPair> *lists[4] = {&T.near_tt, &T.near_tf, &T.near_ft, &T.near_ff};
+    const size_t dims[4][2] = {{(size_t)T.nt, (size_t)T.nt}, {(size_t)T.nt, (size_t)nf}, {(size_t)nh, (size_t)T.nt},
+                               {(size_t)nh, (size_t)nf}};
+    for (int i = 0; i < 4; ++i) {
+        CK(upload(ctx->mk[i], masks(*lists[i], dims[i][0], dims[i][1]), st));
+        auto p = entries(*lists[i], false), q = entries(*lists[i], true);
+        ctx->npr[i] = (int)p.size();
+        ctx->nto[i] = (int)q.size();
+        if (p.empty()) p.push_back({0, 0, 0, 0});
+        if (q.empty()) q.push_back({0, 0, 0, 0});
+        CK(upload(ctx->pr[i], p, st));
+        CK(upload(ctx->to[i], q, st));
+    }
     ctx->have_mesh = true;
     return VIE_OK;
 }

@@ -16,8 +16,10 @@
 //              forms run in FP64 when the elements touch, in T otherwise.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "device_math.cuh"
@@ -183,8 +185,6 @@ __device__ __forceinline__ void atomic_add_c(T *Z, size_t idx, cx<T> v) {
     atomicAdd(Z + 2 * idx + 1, v.im);
 }
 
-__device__ __forceinline__ bool bit_set(const uint32_t *bm, size_t i) { return (bm[i >> 5] >> (i & 31)) & 1u; }
-
 __device__ __forceinline__ cx<double> ld2(const double *p) { return {p[0], p[1]}; }
 
 // scatter the 16 face-pair contributions of one tetrahedron pair
@@ -217,7 +217,8 @@ __device__ void scatter_tt(const DevMesh &m, const DevReq &q, T *Z, size_t N, in
 }
 
 // ---------------------------------------------------------------------------
-// far tetrahedron pairs
+// all tetrahedron pairs: degree-2 product rule of g_p; for the near images of a
+// pair the static part is removed here and integrated by k_pr_tt / k_touch_tt
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(128) k_far_tt(DevMesh m, DevReq q, T *Z, size_t N) {
@@ -226,7 +227,8 @@ __global__ void __launch_bounds__(128) k_far_tt(DevMesh m, DevReq q, T *Z, size_
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = blockIdx.y;
     if (s >= m.nt) return;
-    if (bit_set(m.bm_tt, (size_t)t * m.nt + s)) return;
+    // near images of this pair: their static part is integrated separately
+    const unsigned sub = m.mk_tt[(size_t)t * m.nt + s];
     const T *ft = m.far<T>(t);
     const T *fs = m.far<T>(s);
     Mom<T> mo;
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(128) k_far_tt(DevMesh m, DevReq q, T *Z, size_
         for (int b = 0; b < 4; ++b) {
             const T yb[3] = {fs[3 * b], fs[3 * b + 1], fs[3 * b + 2]};
             const T rb[3] = {yb[0] - fs[12], yb[1] - fs[13], yb[2] - fs[14]};
-            cx<T> g = Green<T>::eval(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], 0u, stab, q.ztab);
+            cx<T> g = Green<T>::eval(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab);
             g = wgt * g;
             mo.S = mo.S + g;
             for (int d = 0; d < 3; ++d) {
@@ -294,90 +296,78 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// near image of a pair, elements not touching: degree-5 x degree-5 product
+// rule of exp(j k_par.R)/(4 pi R), one thread per (pair, image)
 template <typename T>
-__global__ void __launch_bounds__(128) k_near_tt(DevMesh m, DevReq q, T *Z, size_t N,
-                                                 const NearPair *list, int n) {
-    extern __shared__ float smem_tab[];
-    const float *stab = stage_stab<T>(q, smem_tab);
+__global__ void __launch_bounds__(128) k_pr_tt(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list, int n) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const NearEntry en = list[e];
+    const int t = en.x, s = en.y, k = en.k;
+    const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
+    const double *ct = m.cen + 3 * (size_t)t, *cs = m.cen + 3 * (size_t)s;
+    const T *nx = m.nrel<T>(t), *ny = m.nrel<T>(s);
+    const T dc[3] = {T(ct[0] - cs[0] + R[0]), T(ct[1] - cs[1] + R[1]), T(ct[2] - cs[2])};
+    T s0 = 0, sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0}, sC = 0;
+    for (int a = 0; a < 14; ++a) {
+        const T xa[4] = {nx[4 * a], nx[4 * a + 1], nx[4 * a + 2], nx[4 * a + 3]};
+        T f0 = 0, fb[3] = {0, 0, 0};
+        for (int b = 0; b < 14; ++b) {
+            const T *yb = ny + 4 * b;
+            const T dx = xa[0] - yb[0] + dc[0], dy = xa[1] - yb[1] + dc[1], dz = xa[2] - yb[2] + dc[2];
+            const T f = yb[3] / sqrt(dx * dx + dy * dy + dz * dz);
+            f0 += f;
+            fb[0] += f * yb[0];
+            fb[1] += f * yb[1];
+            fb[2] += f * yb[2];
+        }
+        f0 *= xa[3];
+        for (int d = 0; d < 3; ++d) fb[d] *= xa[3];
+        s0 += f0;
+        for (int d = 0; d < 3; ++d) {
+            sA[d] += f0 * xa[d];
+            sB[d] += fb[d];
+        }
+        sC += xa[0] * fb[0] + xa[1] * fb[1] + xa[2] * fb[2];
+    }
+    const cx<T> pt = {T(q.img_ph[2 * k]), T(q.img_ph[2 * k + 1])};
+    Mom<T> mo;
+    mo.S = s0 * pt;
+    mo.C = sC * pt;
+    for (int d = 0; d < 3; ++d) {
+        mo.A[d] = sA[d] * pt;
+        mo.B[d] = sB[d] * pt;
+    }
+    scatter_tt<T>(m, q, Z, N, t, s, mo);
+}
+
+// near image of a pair whose elements touch: closed form over one element at
+// the degree-5 points of the other, both orders averaged, in FP64; one warp per
+// (pair, image), lanes 0..13 order (i), 14..27 order (ii)
+template <typename T>
+__global__ void __launch_bounds__(128) k_touch_tt(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list,
+                                                  int n) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= n) return;
-    const NearPair pr = list[wid];
-    const int t = pr.x, s = pr.y;
-    Mom<double> accd;        // closed forms of touching images (FP64)
-    accd.zero();
-    Mom<T> acct;             // product-rule static parts and the smooth remainder (T)
-    acct.zero();
-    const double *ct = m.cen + 3 * (size_t)t, *cs = m.cen + 3 * (size_t)s;
-    for (int k = 0; k < 9; ++k) {
-        if (!((pr.mask >> k) & 1u)) continue;
+    const NearEntry en = list[wid];
+    const int t = en.x, s = en.y, k = en.k;
+    Mom<double> acc;
+    acc.zero();
+    if (lane < 28) {
         const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
-        const cx<double> ph = {q.img_ph[2 * k], q.img_ph[2 * k + 1]};   // exp(j k_par.R)/(4 pi)
-        if ((pr.touch >> k) & 1u) {
-            // touching: closed form over one element at the degree-5 points of the
-            // other, both orders averaged (lanes 0..13: order (i), 14..27: order (ii))
-            if (lane < 28) {
-                const bool oi = lane < 14;
-                const int qi = oi ? lane : lane - 14;
-                const int self = oi ? t : s, other = oi ? s : t;
-                const double *r5 = m.q5 + (size_t)self * 42 + 3 * qi;
-                const double w = m.vol[self] * c_w5tet[qi];
-                const cx<double> hph = {0.5 * ph.re, 0.5 * ph.im};
-                static_tt_term<double>(r5, w, m.tv + 12 * (size_t)other, R, oi ? -1.0 : 1.0, m.cen + 3 * self,
-                                       m.cen + 3 * other, oi, hph, accd);
-            }
-        } else {
-            // near but not touching: degree-5 x degree-5 product rule of 1/(4 pi R),
-            // points relative to their centroids in T, centroid offset formed in FP64
-            const T *nx = m.nrel<T>(t), *ny = m.nrel<T>(s);
-            const T dc[3] = {T(ct[0] - cs[0] + R[0]), T(ct[1] - cs[1] + R[1]), T(ct[2] - cs[2])};
-            T s0 = 0, sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0}, sC = 0;
-            for (int p = lane; p < 196; p += 32) {
-                const int a = p / 14, b = p % 14;
-                const T *xa = nx + 4 * a, *yb = ny + 4 * b;
-                const T dx = xa[0] - yb[0] + dc[0], dy = xa[1] - yb[1] + dc[1], dz = xa[2] - yb[2] + dc[2];
-                const T f = xa[3] * yb[3] / sqrt(dx * dx + dy * dy + dz * dz);
-                s0 += f;
-                for (int d = 0; d < 3; ++d) {
-                    sA[d] += f * xa[d];
-                    sB[d] += f * yb[d];
-                }
-                sC += f * (xa[0] * yb[0] + xa[1] * yb[1] + xa[2] * yb[2]);
-            }
-            const cx<T> pt = {T(ph.re), T(ph.im)};
-            acct.S = acct.S + s0 * pt;
-            acct.C = acct.C + sC * pt;
-            for (int d = 0; d < 3; ++d) {
-                acct.A[d] = acct.A[d] + sA[d] * pt;
-                acct.B[d] = acct.B[d] + sB[d] * pt;
-            }
-        }
+        const cx<double> hph = {0.5 * q.img_ph[2 * k], 0.5 * q.img_ph[2 * k + 1]};
+        const bool oi = lane < 14;
+        const int qi = oi ? lane : lane - 14;
+        const int self = oi ? t : s, other = oi ? s : t;
+        const double *r5 = m.q5 + (size_t)self * 42 + 3 * qi;
+        const double w = m.vol[self] * c_w5tet[qi];
+        static_tt_term<double>(r5, w, m.tv + 12 * (size_t)other, R, oi ? -1.0 : 1.0, m.cen + 3 * self,
+                               m.cen + 3 * other, oi, hph, acc);
     }
-    if (lane < 16) {
-        const T *ft = m.far<T>(t);
-        const T *fs = m.far<T>(s);
-        const int a = lane >> 2, b = lane & 3;
-        const T xa[3] = {ft[3 * a], ft[3 * a + 1], ft[3 * a + 2]};
-        const T yb[3] = {fs[3 * b], fs[3 * b + 1], fs[3 * b + 2]};
-        cx<T> g = Green<T>::eval(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], pr.mask, stab, q.ztab);
-        g = (ft[27] * fs[27]) * g;
-        T ra[3], rb[3];
-        for (int d = 0; d < 3; ++d) {
-            ra[d] = xa[d] - ft[12 + d];
-            rb[d] = yb[d] - fs[12 + d];
-        }
-        acct.S = acct.S + g;
-        for (int d = 0; d < 3; ++d) {
-            acct.A[d] = acct.A[d] + ra[d] * g;
-            acct.B[d] = acct.B[d] + rb[d] * g;
-        }
-        acct.C = acct.C + (ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2]) * g;
-    }
-    double v[16] = {accd.S.re + acct.S.re, accd.S.im + acct.S.im, accd.C.re + acct.C.re, accd.C.im + acct.C.im,
-                    accd.A[0].re + acct.A[0].re, accd.A[0].im + acct.A[0].im, accd.A[1].re + acct.A[1].re,
-                    accd.A[1].im + acct.A[1].im, accd.A[2].re + acct.A[2].re, accd.A[2].im + acct.A[2].im,
-                    accd.B[0].re + acct.B[0].re, accd.B[0].im + acct.B[0].im, accd.B[1].re + acct.B[1].re,
-                    accd.B[1].im + acct.B[1].im, accd.B[2].re + acct.B[2].re, accd.B[2].im + acct.B[2].im};
+    double v[16] = {acc.S.re, acc.S.im, acc.C.re, acc.C.im, acc.A[0].re, acc.A[0].im, acc.A[1].re, acc.A[1].im,
+                    acc.A[2].re, acc.A[2].im, acc.B[0].re, acc.B[0].im, acc.B[1].re, acc.B[1].im, acc.B[2].re,
+                    acc.B[2].im};
     for (int i = 0; i < 16; ++i) v[i] = warp_sum(v[i]);
     if (lane == 0) {
         Mom<T> mo;
@@ -438,13 +428,13 @@ __device__ __forceinline__ const T *far_el(const DevMesh &m, int e) {
 
 template <typename T, int PK>
 __global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, DevReq q, T *Z, size_t N, int nx, int ny,
-                                                    const uint32_t *bm) {
+                                                    const uint16_t *mk) {
     extern __shared__ float smem_tab[];
     const float *stab = stage_stab<T>(q, smem_tab);
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     const int x = blockIdx.y;
     if (y >= ny) return;
-    if (bit_set(bm, (size_t)x * ny + y)) return;
+    const unsigned sub = mk[(size_t)x * ny + y];
     constexpr bool XT = PKTraits<PK>::xtet, YT = PKTraits<PK>::ytet;
     // a test face is addressed by its half-function index; geometry by charge-face index
     const T *fx = far_el<T, XT>(m, XT ? x : m.hf[x]);
@@ -455,7 +445,7 @@ __global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, DevReq q, T *Z, s
     for (int a = 0; a < qx; ++a)
         for (int b = 0; b < qy; ++b) {
             cx<T> g = Green<T>::eval(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1], fx[3 * a + 2] - fy[3 * b + 2],
-                                     0u, stab, q.ztab);
+                                     sub, stab, q.ztab);
             S = S + g;
         }
     S = wgt * S;
@@ -482,17 +472,44 @@ __device__ double static_scalar(const double *r5, bool other_tet, const double *
 }
 
 template <typename T, int PK>
-__global__ void __launch_bounds__(128) k_near_scalar(DevMesh m, DevReq q, T *Z, size_t N,
-                                                     const NearPair *list, int n) {
-    extern __shared__ float smem_tab[];
-    const float *stab = stage_stab<T>(q, smem_tab);
+__global__ void __launch_bounds__(128) k_pr_scalar(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list,
+                                                   int n) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    constexpr bool XT = PKTraits<PK>::xtet, YT = PKTraits<PK>::ytet;
+    const NearEntry en = list[e];
+    const int x = en.x, y = en.y, k = en.k;
+    const int xf = XT ? x : m.hf[x];
+    constexpr int nqx = XT ? 14 : 7, nqy = YT ? 14 : 7;
+    const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
+    const T *nx = XT ? m.nrel<T>(xf) : m.fnrel<T>(xf);
+    const T *ny = YT ? m.nrel<T>(y) : m.fnrel<T>(y);
+    const double *cxp = XT ? m.cen + 3 * (size_t)xf : m.fcen + 3 * (size_t)xf;
+    const double *cyp = YT ? m.cen + 3 * (size_t)y : m.fcen + 3 * (size_t)y;
+    const T dc[3] = {T(cxp[0] - cyp[0] + R[0]), T(cxp[1] - cyp[1] + R[1]), T(cxp[2] - cyp[2])};
+    T s0 = 0;
+    for (int a = 0; a < nqx; ++a) {
+        const T *xa = nx + 4 * a;
+        T f0 = 0;
+        for (int b = 0; b < nqy; ++b) {
+            const T *yb = ny + 4 * b;
+            const T dx = xa[0] - yb[0] + dc[0], dy = xa[1] - yb[1] + dc[1], dz = xa[2] - yb[2] + dc[2];
+            f0 += yb[3] / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        s0 += xa[3] * f0;
+    }
+    scatter_scalar<T, PK>(m, q, Z, N, x, y, s0 * cx<T>{T(q.img_ph[2 * k]), T(q.img_ph[2 * k + 1])});
+}
+
+template <typename T, int PK>
+__global__ void __launch_bounds__(128) k_touch_scalar(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list,
+                                                      int n) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= n) return;
     constexpr bool XT = PKTraits<PK>::xtet, YT = PKTraits<PK>::ytet;
-    const NearPair pr = list[wid];
-    const int x = pr.x, y = pr.y;
-    // face elements are addressed through the charge-face index
+    const NearEntry en = list[wid];
+    const int x = en.x, y = en.y, k = en.k;
     const int xf = XT ? x : m.hf[x];
     const int yf = y;
     constexpr int nqx = XT ? 14 : 7, nqy = YT ? 14 : 7;
@@ -500,52 +517,22 @@ __global__ void __launch_bounds__(128) k_near_scalar(DevMesh m, DevReq q, T *Z, 
     const double *y5 = YT ? m.q5 + (size_t)yf * 42 : m.f5 + (size_t)yf * 21;
     const double mx = XT ? m.vol[xf] : m.farea[xf];
     const double my = YT ? m.vol[yf] : m.farea[yf];
-    cx<double> accd = {0, 0};
-    cx<T> acct = {0, 0};
-    for (int k = 0; k < 9; ++k) {
-        if (!((pr.mask >> k) & 1u)) continue;
+    cx<double> acc = {0, 0};
+    if (lane < nqx + nqy) {
         const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
-        const cx<double> ph = {q.img_ph[2 * k], q.img_ph[2 * k + 1]};
-        if ((pr.touch >> k) & 1u) {
-            if (lane < nqx + nqy) {
-                const bool oi = lane < nqx;
-                const int qi = oi ? lane : lane - nqx;
-                const bool self_tet = oi ? XT : YT;
-                const bool other_tet = oi ? YT : XT;
-                const int other = oi ? yf : xf;
-                const double *r5 = (oi ? x5 : y5) + 3 * qi;
-                const double w = (oi ? mx : my) * (self_tet ? c_w5tet[qi] : c_w5tri[qi]);
-                const double *vo = other_tet ? m.tv + 12 * (size_t)other : m.fv + 9 * (size_t)other;
-                const double I = static_scalar<double>(r5, other_tet, vo, R, oi ? -1.0 : 1.0);
-                accd.re += 0.5 * w * ph.re * I;
-                accd.im += 0.5 * w * ph.im * I;
-            }
-        } else {
-            const T *nx = XT ? m.nrel<T>(xf) : m.fnrel<T>(xf);
-            const T *ny = YT ? m.nrel<T>(yf) : m.fnrel<T>(yf);
-            const double *cxp = XT ? m.cen + 3 * (size_t)xf : m.fcen + 3 * (size_t)xf;
-            const double *cyp = YT ? m.cen + 3 * (size_t)yf : m.fcen + 3 * (size_t)yf;
-            const T dc[3] = {T(cxp[0] - cyp[0] + R[0]), T(cxp[1] - cyp[1] + R[1]), T(cxp[2] - cyp[2])};
-            T s0 = 0;
-            for (int p = lane; p < nqx * nqy; p += 32) {
-                const int a = p / nqy, b = p % nqy;
-                const T *xa = nx + 4 * a, *yb = ny + 4 * b;
-                const T dx = xa[0] - yb[0] + dc[0], dy = xa[1] - yb[1] + dc[1], dz = xa[2] - yb[2] + dc[2];
-                s0 += xa[3] * yb[3] / sqrt(dx * dx + dy * dy + dz * dz);
-            }
-            acct = acct + s0 * cx<T>{T(ph.re), T(ph.im)};
-        }
+        const bool oi = lane < nqx;
+        const int qi = oi ? lane : lane - nqx;
+        const bool self_tet = oi ? XT : YT;
+        const bool other_tet = oi ? YT : XT;
+        const int other = oi ? yf : xf;
+        const double *r5 = (oi ? x5 : y5) + 3 * qi;
+        const double w = (oi ? mx : my) * (self_tet ? c_w5tet[qi] : c_w5tri[qi]);
+        const double *vo = other_tet ? m.tv + 12 * (size_t)other : m.fv + 9 * (size_t)other;
+        const double I = static_scalar<double>(r5, other_tet, vo, R, oi ? -1.0 : 1.0);
+        acc.re = 0.5 * w * q.img_ph[2 * k] * I;
+        acc.im = 0.5 * w * q.img_ph[2 * k + 1] * I;
     }
-    const int qx = XT ? 4 : 3, qy = YT ? 4 : 3;
-    if (lane < qx * qy) {
-        const T *fx = far_el<T, XT>(m, xf);
-        const T *fy = far_el<T, YT>(m, yf);
-        const int a = lane / qy, b = lane % qy;
-        cx<T> g = Green<T>::eval(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1], fx[3 * a + 2] - fy[3 * b + 2],
-                                 pr.mask, stab, q.ztab);
-        acct = acct + (fx[XT ? 27 : 9] * fy[YT ? 27 : 9]) * g;
-    }
-    double sr = warp_sum(accd.re + double(acct.re)), si = warp_sum(accd.im + double(acct.im));
+    const double sr = warp_sum(acc.re), si = warp_sum(acc.im);
     if (lane == 0) scatter_scalar<T, PK>(m, q, Z, N, x, y, cx<T>{T(sr), T(si)});
 }
 
@@ -641,20 +628,26 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
     dim3 blk(128);
     k_gram<T><<<(m.nt + 127) / 128, blk, 0, st>>>(m, q, Z, N);
     if (b) k_rhs<<<(m.nt + 127) / 128, blk, 0, st>>>(m, q, b);
-    if (far0) cudaEventRecord(far0, st);
     const size_t sm = stab_bytes<T>();
+    if (far0) cudaEventRecord(far0, st);
     k_far_tt<T><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N);
     if (far1) cudaEventRecord(far1, st);
-    if (m.n_tt) k_near_tt<T><<<(m.n_tt * 32 + 127) / 128, blk, sm, st>>>(m, q, Z, N, m.near_tt, m.n_tt);
+    auto grid1 = [](int n) { return (unsigned)((n + 127) / 128); };
+    auto gridw = [](int n) { return (unsigned)(((size_t)n * 32 + 127) / 128); };
+    if (m.npr[0]) k_pr_tt<T><<<grid1(m.npr[0]), blk, 0, st>>>(m, q, Z, N, m.pr[0], m.npr[0]);
+    if (m.nto[0]) k_touch_tt<T><<<gridw(m.nto[0]), blk, 0, st>>>(m, q, Z, N, m.to[0], m.nto[0]);
     if (m.nf) {
-        k_far_scalar<T, PK_TF><<<dim3((m.nf + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N, m.nt, m.nf, m.bm_tf);
-        if (m.n_tf) k_near_scalar<T, PK_TF><<<(m.n_tf * 32 + 127) / 128, blk, sm, st>>>(m, q, Z, N, m.near_tf, m.n_tf);
+        k_far_scalar<T, PK_TF><<<dim3((m.nf + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N, m.nt, m.nf, m.mk_tf);
+        if (m.npr[1]) k_pr_scalar<T, PK_TF><<<grid1(m.npr[1]), blk, 0, st>>>(m, q, Z, N, m.pr[1], m.npr[1]);
+        if (m.nto[1]) k_touch_scalar<T, PK_TF><<<gridw(m.nto[1]), blk, 0, st>>>(m, q, Z, N, m.to[1], m.nto[1]);
     }
     if (m.nh) {
-        k_far_scalar<T, PK_FT><<<dim3((m.nt + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nt, m.bm_ft);
-        if (m.n_ft) k_near_scalar<T, PK_FT><<<(m.n_ft * 32 + 127) / 128, blk, sm, st>>>(m, q, Z, N, m.near_ft, m.n_ft);
-        k_far_scalar<T, PK_FF><<<dim3((m.nf + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nf, m.bm_ff);
-        if (m.n_ff) k_near_scalar<T, PK_FF><<<(m.n_ff * 32 + 127) / 128, blk, sm, st>>>(m, q, Z, N, m.near_ff, m.n_ff);
+        k_far_scalar<T, PK_FT><<<dim3((m.nt + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nt, m.mk_ft);
+        if (m.npr[2]) k_pr_scalar<T, PK_FT><<<grid1(m.npr[2]), blk, 0, st>>>(m, q, Z, N, m.pr[2], m.npr[2]);
+        if (m.nto[2]) k_touch_scalar<T, PK_FT><<<gridw(m.nto[2]), blk, 0, st>>>(m, q, Z, N, m.to[2], m.nto[2]);
+        k_far_scalar<T, PK_FF><<<dim3((m.nf + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nf, m.mk_ff);
+        if (m.npr[3]) k_pr_scalar<T, PK_FF><<<grid1(m.npr[3]), blk, 0, st>>>(m, q, Z, N, m.pr[3], m.npr[3]);
+        if (m.nto[3]) k_touch_scalar<T, PK_FF><<<gridw(m.nto[3]), blk, 0, st>>>(m, q, Z, N, m.to[3], m.nto[3]);
     }
     return cudaGetLastError();
 }

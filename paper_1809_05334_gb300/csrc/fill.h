@@ -10,6 +10,11 @@ namespace vie {
 
 struct EwaldTables;
 
+// one near image k (= 3(m+1) + (n+1)) of the element pair (x, y)
+struct NearEntry {
+    int32_t x, y, k, pad;
+};
+
 struct DevMesh {
     int nt, N, nf, nh;
     double a, b;
@@ -30,9 +35,12 @@ struct DevMesh {
     const float *ffar32;   // [nf][12]: 3 points, weight area/3, pad
     const double *ffar64;
     const int32_t *hf;     // [nh] charge-face index of each half function
-    const uint32_t *bm_tt, *bm_tf, *bm_ft, *bm_ff;   // near bitmaps (x-major)
-    const NearPair *near_tt, *near_tf, *near_ft, *near_ff;
-    int n_tt, n_tf, n_ft, n_ff;
+    // per pair of elements (x-major): 9-bit mask of the near images
+    const uint16_t *mk_tt, *mk_tf, *mk_ft, *mk_ff;
+    // near (pair, image) entries, kinds 0 tet-tet, 1 tet-face, 2 face-tet, 3 face-face:
+    // pr = elements not touching (product rule), to = touching (closed forms)
+    const NearEntry *pr[4], *to[4];
+    int npr[4], nto[4];
 
     template <typename T> __device__ const T *far(int t) const;
     template <typename T> __device__ const T *ffar(int f) const;
