@@ -156,6 +156,32 @@ int vie_erfcx(vie_ctx *ctx, const double *u, double *out, int32_t n, int32_t pre
 int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out,
               int32_t n, int32_t precision);
 
+/* Allocation-free g_p(d): the same Ewald evaluation as vie_green, for callers
+   that cannot allocate device memory while they run (a host framework that
+   owns all of HBM through its own pool and forbids cudaMalloc/cudaFree after
+   start-up, or code that must not let an allocation synchronise the device).
+   The paper has no counterpart; this is a deployment entry point.
+   Arguments: incidence (lambda_nm, theta, phi) as in vie_request; lattice
+   periods period_a, period_b (nm); z_extent >= the largest |dz| that will be
+   evaluated (the FP32 tables cover |dz| in [0, z_extent]); d_dev [n][3] and
+   out_dev [n] complex (re,im) are DEVICE buffers owned by the caller, with the
+   same in-cell restriction as vie_green; precision VIE_FP64 or VIE_FP32;
+   stream a cudaStream_t (NULL: legacy default stream).  Needs no context.
+   Scratch: the FP32 interpolation tables live in a file-scope device array of
+   about 0.8 MB that every GPU loading this library keeps until the process
+   exits; requests needing more than 96 distinct Floquet decay constants are
+   rejected with VIE_EINVAL.  The tables are rebuilt completely by each call,
+   so nothing has to start at zero.  All calls share that array and the
+   library's constant tables: calls whose work overlaps on the GPU race.
+   The first call on a device does a one-time set-up (constant upload and the
+   device address of the array); make that first call before any stream
+   capture.  The call only enqueues work: out_dev is valid once the stream has
+   completed it.  Calls no cudaMalloc, cudaFree or allocating library routine.
+   Returns VIE_OK, VIE_EINVAL, VIE_RAYLEIGH_ANOMALY or VIE_ECUDA. */
+int vie_green_noalloc(double lambda_nm, double theta, double phi, double period_a, double period_b,
+                      double z_extent, const double *d_dev, double *out_dev, int32_t n,
+                      int32_t precision, void *stream);
+
 /* Human-readable name of a status code; never NULL. */
 const char *vie_status_str(int status);
 

@@ -671,3 +671,169 @@ cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const f
 }
 
 }  // namespace vie
+
+// ===========================================================================
+// Allocation-free evaluation of the periodic Green's function.
+//
+// Some callers cannot allocate device memory while they run: a host framework
+// that reserves all of HBM up front through its own pool and forbids
+// cudaMalloc/cudaFree afterwards (a long-running serving process, for
+// example), or code that must not let an allocation synchronise the device.
+// vie_green_noalloc serves them: the caller passes device buffers for the
+// inputs and outputs, and the only scratch -- the FP32 interpolation tables of
+// the Ewald series -- lives in the file-scope array below, which every GPU
+// that loads this library holds until the process exits.
+// ===========================================================================
+#include "../../include/vie.h"
+
+namespace vie {
+
+constexpr int NOALLOC_MAX_TAB = 96;   // distinct Floquet decay constants the scratch can hold
+constexpr size_t NOALLOC_FLOAT2 = 2 * NSPAT + (size_t)NOALLOC_MAX_TAB * NZTAB * 4;
+// spatial table (4*NSPAT floats) followed by the spectral tables (float2): 786 KB + 8 KB
+static __device__ __align__(256) float2 g_noalloc_scratch[NOALLOC_FLOAT2];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+float2 *g_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
+bool g_ready[NOALLOC_MAX_DEVICES] = {};
+
+// Ewald parameters and tables of one incidence (FP64 and tabulated FP32 paths),
+// the same series and truncations as the solver's.
+int noalloc_tables(double lambda, double theta, double phi, double a, double b, double z_extent, bool fp64,
+                   EwaldTables &E) {
+    const double k0 = 2.0 * M_PI / lambda;
+    const double kx = k0 * std::sin(theta) * std::cos(phi), ky = k0 * std::sin(theta) * std::sin(phi);
+    std::memset(&E, 0, sizeof(E));
+    E.E = std::max(std::sqrt(M_PI / (a * b)), k0 / 6.0);
+    E.bb = k0 / (2.0 * E.E);
+    E.a = a;
+    E.b = b;
+    E.xcut64 = 6.0;
+    E.xcut32 = 4.2f;
+    const double xc = fp64 ? 6.0 : 4.2;
+    const int mm = (int)std::ceil(xc / (E.E * a)) + 2, nn = (int)std::ceil(xc / (E.E * b)) + 2;
+    int ni = 0;
+    for (int m = -mm; m <= mm; ++m)
+        for (int n = -nn; n <= nn; ++n) {
+            const double dmin = std::hypot(std::max(std::abs(m) - 1, 0) * a, std::max(std::abs(n) - 1, 0) * b);
+            const bool nearimg = std::abs(m) <= 1 && std::abs(n) <= 1;
+            if (dmin * E.E > xc && !nearimg) continue;
+            if (ni >= MAX_IMG) return VIE_EINVAL;
+            const double phs = kx * m * a + ky * n * b, f = std::exp(E.bb * E.bb) / (4.0 * M_PI);
+            const double v[4] = {m * a, n * b, f * std::cos(phs), f * std::sin(phs)};
+            for (int q = 0; q < 4; ++q) { E.img64[ni][q] = v[q]; E.img32[ni][q] = (float)v[q]; }
+            if (nearimg) E.near_img[(m + 1) * 3 + (n + 1)] = ni;
+            ++ni;
+        }
+    E.n_img = ni;
+    const int pm = (int)std::ceil((2.0 * E.E * xc + std::fabs(kx)) * a / (2 * M_PI)) + 1;
+    const int qm = (int)std::ceil((2.0 * E.E * xc + std::fabs(ky)) * b / (2 * M_PI)) + 1;
+    int nm = 0;
+    for (int p = -pm; p <= pm; ++p)
+        for (int q = -qm; q <= qm; ++q) {
+            const double ktx = kx + 2 * M_PI * p / a, kty = ky + 2 * M_PI * q / b;
+            const double kt2 = ktx * ktx + kty * kty, g2 = kt2 - k0 * k0;
+            if (std::fabs(g2) * std::max(a, b) * std::max(a, b) < 1e-10) return VIE_RAYLEIGH_ANOMALY;
+            if (std::sqrt(kt2) > 2.0 * E.E * xc + k0) continue;
+            if (nm >= MAX_MODE) return VIE_EINVAL;
+            const double gr = g2 >= 0 ? std::sqrt(g2) : 0.0, gi = g2 >= 0 ? 0.0 : std::sqrt(-g2);
+            // 1/(4 a b gamma)
+            const double ir = gr / (4.0 * a * b * (gr * gr + gi * gi)), ii = -gi / (4.0 * a * b * (gr * gr + gi * gi));
+            const double w8[8] = {ktx, kty, gr, gi, std::exp(-g2 / (4 * E.E * E.E)), ir, ii, 0};
+            for (int c = 0; c < 8; ++c) { E.mode64[nm][c] = w8[c]; E.mode32[nm][c] = (float)w8[c]; }
+            ++nm;
+        }
+    E.n_mode = nm;
+    {   // erfi(b) by its series, for the limit of the regularised image term
+        double term = E.bb, sum = E.bb;
+        for (int n = 1; n < 200; ++n) {
+            term *= E.bb * E.bb / n;
+            const double add = term / (2 * n + 1);
+            sum += add;
+            if (std::fabs(add) < 1e-18 * std::fabs(sum)) break;
+        }
+        const double erfi = 2.0 / std::sqrt(M_PI) * sum;
+        E.reg0_re = (E.E / (4 * M_PI)) * (2 * E.bb * erfi - 2.0 / std::sqrt(M_PI) * std::exp(E.bb * E.bb));
+    }
+    const double xc32 = 4.2, zr = std::max(z_extent, 1e-6) * (1.0 + 1e-6);
+    E.xs_max = (float)(xc32 + 0.5);
+    E.xs_inv_h = (float)(NSPAT / (xc32 + 0.5));
+    E.z_max = (float)zr;
+    E.z_inv_h = (float)(NZTAB / zr);
+    E.e_mb2 = (float)std::exp(-E.bb * E.bb);
+    E.Ef = (float)E.E;
+    E.kx = (float)kx;
+    E.ky = (float)ky;
+    E.step_x = (float)(2 * M_PI / a);
+    E.step_y = (float)(2 * M_PI / b);
+    const int P = (int)std::ceil((2.0 * E.E * xc32 + std::fabs(kx)) * a / (2 * M_PI)) + 1;
+    const int Q = (int)std::ceil((2.0 * E.E * xc32 + std::fabs(ky)) * b / (2 * M_PI)) + 1;
+    if ((2 * P + 1) * (2 * Q + 1) > MAX_MODE) return VIE_EINVAL;
+    E.P = P;
+    E.Q = Q;
+    int nt = 0;
+    double g2s[MAX_MODE];
+    for (int p = -P; p <= P; ++p)
+        for (int q = -Q; q <= Q; ++q) {
+            const int idx = (p + P) * (2 * Q + 1) + (q + Q);
+            const double ktx = kx + 2 * M_PI * p / a, kty = ky + 2 * M_PI * q / b;
+            const double kt2 = ktx * ktx + kty * kty;
+            if (std::sqrt(kt2) > 2.0 * E.E * xc32 + k0) { E.rect_tab[idx] = -1; continue; }
+            const double g2 = kt2 - k0 * k0;
+            int found = -1;
+            for (int j = 0; j < nt; ++j)
+                if (std::fabs(g2s[j] - g2) <= 1e-12 * std::max(1e-6, std::fabs(g2))) { found = j; break; }
+            if (found < 0) {
+                found = nt++;
+                g2s[found] = g2;
+                const double gr = g2 >= 0 ? std::sqrt(g2) : 0.0, gi = g2 >= 0 ? 0.0 : std::sqrt(-g2);
+                E.tab_gamma[found][0] = gr;
+                E.tab_gamma[found][1] = gi;
+                E.tab_ig[found][0] = gr / (4.0 * a * b * (gr * gr + gi * gi));
+                E.tab_ig[found][1] = -gi / (4.0 * a * b * (gr * gr + gi * gi));
+                E.tab_pre[found] = std::exp(-g2 / (4 * E.E * E.E));
+            }
+            E.rect_tab[idx] = found;
+        }
+    E.n_tab = nt;
+    return VIE_OK;
+}
+
+}  // namespace
+}  // namespace vie
+
+extern "C" int vie_green_noalloc(double lambda_nm, double theta, double phi, double period_a, double period_b,
+                                 double z_extent, const double *d_dev, double *out_dev, int32_t n,
+                                 int32_t precision, void *stream) {
+    using namespace vie;
+    if (n < 0 || (n > 0 && (!d_dev || !out_dev))) return VIE_EINVAL;
+    if (!(lambda_nm > 0) || !(period_a > 0) || !(period_b > 0) || !(std::fabs(theta) < M_PI / 2) ||
+        !(z_extent >= 0) || !std::isfinite(lambda_nm + period_a + period_b + z_extent))
+        return VIE_EINVAL;
+    if (precision != VIE_FP64 && precision != VIE_FP32) return VIE_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return VIE_ECUDA;
+    if (!g_ready[dev]) {
+        // one-time set-up on this device (the device is current): Weideman
+        // constants and the device address of the scratch array
+        if (upload_constants() != cudaSuccess) return VIE_ECUDA;
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VIE_ECUDA;
+        g_scratch_ptr[dev] = static_cast<float2 *>(p);
+        g_ready[dev] = true;
+    }
+    if (n == 0) return VIE_OK;
+    static thread_local EwaldTables tabs;
+    const int rc = noalloc_tables(lambda_nm, theta, phi, period_a, period_b, z_extent, precision == VIE_FP64, tabs);
+    if (rc != VIE_OK) return rc;
+    if (precision == VIE_FP32 && tabs.n_tab > NOALLOC_MAX_TAB) return VIE_EINVAL;   // scratch too small
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (upload_ewald(tabs, st) != cudaSuccess) return VIE_ECUDA;
+    float *stab = reinterpret_cast<float *>(g_scratch_ptr[dev]);
+    float2 *ztab = g_scratch_ptr[dev] + 2 * NSPAT;
+    if (precision == VIE_FP32 && launch_build_tables(stab, ztab, tabs.n_tab, st) != cudaSuccess) return VIE_ECUDA;
+    if (launch_green(d_dev, out_dev, n, precision == VIE_FP64, stab, ztab, st) != cudaSuccess) return VIE_ECUDA;
+    return VIE_OK;
+}

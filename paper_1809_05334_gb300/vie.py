@@ -21,7 +21,7 @@ STATUS = {0: "VIE_OK", 1: "VIE_NOT_CONVERGED", -1: "VIE_EINVAL", -2: "VIE_ENOMEM
 # every symbol include/vie.h declares
 EXPORTS = ["vie_default_options", "vie_create", "vie_set_options", "vie_set_mesh", "vie_num_unknowns",
            "vie_solve", "vie_fill_matrix", "vie_fill_matrix_prec", "vie_erfcx", "vie_green",
-           "vie_status_str", "vie_last_error", "vie_destroy"]
+           "vie_status_str", "vie_last_error", "vie_destroy", "vie_green_noalloc"]
 
 
 class Options(ctypes.Structure):
@@ -77,6 +77,7 @@ def load():
     lib.vie_last_error.restype = ctypes.c_char_p
     lib.vie_destroy.argtypes = [P]
     lib.vie_destroy.restype = None
+    lib.vie_green_noalloc.argtypes = [D, D, D, D, D, D, P, P, I, I, P]
     _LIB = lib
     return lib
 
