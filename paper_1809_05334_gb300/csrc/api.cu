@@ -557,7 +557,7 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
     for (size_t k = 0; k < H.blk_n.size(); ++k) {
         float *B = ctx->Minv.as<float>() + 2 * moff[k];
         CK((vie::copy_block<TZ, float>(ctx->Z.as<TZ>(), ctx->ld, H.blk_off[k], H.blk_n[k], B, mld[k], st)));
-        CK(vie::gj_invert<float>(B, mld[k], H.blk_n[k], ctx->status.as<int>(), st));
+        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), st));
     }
     int stat = 0;
     CK(cudaMemcpyAsync(&stat, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));

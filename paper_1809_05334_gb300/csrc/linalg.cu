@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "linalg.h"
+#include "tc_gemm.cuh"
 
 namespace vie {
 
@@ -325,6 +326,164 @@ cudaError_t gj_invert(T *A, size_t ld, int n, int *status, cudaStream_t st) {
 }
 template cudaError_t gj_invert<float>(float *, size_t, int, int *, cudaStream_t);
 template cudaError_t gj_invert<double>(double *, size_t, int, int *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Gauss-Jordan with 64-wide pivot blocks and the tensor-core trailing update
+// (FP32 matrix, TF32 products with FP32 accumulation).
+// ---------------------------------------------------------------------------
+constexpr int GJ_W = 128;     // pivot block width (the K of the tensor-core update)
+constexpr int GJ_PL = 32;     // panel lines per CTA in the row / column panel kernels
+
+__global__ void __launch_bounds__(512) k_gj_diag_w(float *A, size_t ld, int k0, int w, int *status) {
+    // unblocked in-place Gauss-Jordan inverse of the w x w (w <= GJ_W) pivot block
+    extern __shared__ float dsm[];
+    float *P = dsm;                      // [w][w][2], row stride 2w
+    float *col = dsm + 2 * GJ_W * GJ_W;  // [w][2]
+    float *piv = col + 2 * GJ_W;         // [2]
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i = e / w, j = e % w;
+        P[2 * (i * w + j)] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
+        P[2 * (i * w + j) + 1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
+    }
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+        if (threadIdx.x == 0) {
+            float pr = P[2 * (j * w + j)], pi = P[2 * (j * w + j) + 1];
+            float d = pr * pr + pi * pi;
+            if (!(d > 0.f) || !isfinite(d)) atomicExch(status, 1);
+            piv[0] = pr / d;
+            piv[1] = -pi / d;
+        }
+        if (threadIdx.x < w) {
+            col[2 * threadIdx.x] = P[2 * (threadIdx.x * w + j)];
+            col[2 * threadIdx.x + 1] = P[2 * (threadIdx.x * w + j) + 1];
+        }
+        __syncthreads();
+        const float qr = piv[0], qi = piv[1];
+        if (threadIdx.x < w) {   // row j <- p * row j, pivot entry <- p
+            const int c = threadIdx.x;
+            if (c == j) {
+                P[2 * (j * w + c)] = qr; P[2 * (j * w + c) + 1] = qi;
+            } else {
+                float ar = P[2 * (j * w + c)], ai = P[2 * (j * w + c) + 1];
+                P[2 * (j * w + c)] = qr * ar - qi * ai;
+                P[2 * (j * w + c) + 1] = qr * ai + qi * ar;
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+            const int i = e / w, c = e % w;
+            if (i == j) continue;
+            const float fr = col[2 * i], fi = col[2 * i + 1];
+            if (c == j) {            // a_ij <- -f_i p
+                P[2 * (i * w + c)] = -(fr * qr - fi * qi);
+                P[2 * (i * w + c) + 1] = -(fr * qi + fi * qr);
+            } else {                 // a_ic <- a_ic - f_i a_jc(new)
+                const float br = P[2 * (j * w + c)], bi = P[2 * (j * w + c) + 1];
+                P[2 * (i * w + c)] -= fr * br - fi * bi;
+                P[2 * (i * w + c) + 1] -= fr * bi + fi * br;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i = e / w, j = e % w;
+        A[2 * ((size_t)(k0 + i) * ld + k0 + j)] = P[2 * (i * w + j)];
+        A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1] = P[2 * (i * w + j) + 1];
+    }
+}
+
+// row panel (ROW): A[k0+i][c] <- sum_q P[i][q] A[k0+q][c]  for GJ_PL columns c per CTA
+// column panel   : A[r][k0+j] <- -sum_q A[r][k0+q] P[q][j] for GJ_PL rows r per CTA
+// (columns / rows outside the pivot block; P = the inverted pivot block)
+template <bool ROW>
+__global__ void __launch_bounds__(256) k_gj_panel(float *A, size_t ld, int n, int k0, int w) {
+    extern __shared__ float pan_smem[];
+    float *P = pan_smem;                          // [w][w][2]
+    float *Tt = pan_smem + 2 * GJ_W * GJ_W;       // [GJ_PL][w + 1][2]: line l, pivot index q
+    const int tw = w + 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i = e / w, j = e % w;
+        P[2 * (i * w + j)] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
+        P[2 * (i * w + j) + 1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
+    }
+    const int m = n - w;
+    const int base = blockIdx.x * GJ_PL;
+    for (int e = threadIdx.x; e < GJ_PL * w; e += blockDim.x) {
+        float vr = 0.f, vi = 0.f;
+        int l, q;
+        if (ROW) {   // coalesced along the row of pivot index q
+            q = e / GJ_PL; l = e % GJ_PL;
+            const int jj = base + l;
+            if (jj < m) {
+                const int c = jj < k0 ? jj : jj + w;
+                vr = A[2 * ((size_t)(k0 + q) * ld + c)];
+                vi = A[2 * ((size_t)(k0 + q) * ld + c) + 1];
+            }
+        } else {     // coalesced along the row segment of line l
+            l = e / w; q = e % w;
+            const int jj = base + l;
+            if (jj < m) {
+                const int r = jj < k0 ? jj : jj + w;
+                vr = A[2 * ((size_t)r * ld + k0 + q)];
+                vi = A[2 * ((size_t)r * ld + k0 + q) + 1];
+            }
+        }
+        Tt[2 * (l * tw + q)] = vr;
+        Tt[2 * (l * tw + q) + 1] = vi;
+    }
+    __syncthreads();
+    // thread: line l = tid % GJ_PL, outputs o = tid / GJ_PL + 8 t
+    const int l = threadIdx.x % GJ_PL;
+    const int jj = base + l;
+    for (int o = threadIdx.x / GJ_PL; o < w; o += blockDim.x / GJ_PL) {
+        float sr = 0.f, si = 0.f;
+        for (int q = 0; q < w; ++q) {
+            const float tr = Tt[2 * (l * tw + q)], ti = Tt[2 * (l * tw + q) + 1];
+            // ROW: P[o][q] * T[q];  COL: T[q] * P[q][o]
+            const float pr = ROW ? P[2 * (o * w + q)] : P[2 * (q * w + o)];
+            const float pi = ROW ? P[2 * (o * w + q) + 1] : P[2 * (q * w + o) + 1];
+            sr = fmaf(pr, tr, fmaf(-pi, ti, sr));
+            si = fmaf(pr, ti, fmaf(pi, tr, si));
+        }
+        if (jj < m) {
+            if (ROW) {
+                const int c = jj < k0 ? jj : jj + w;
+                A[2 * ((size_t)(k0 + o) * ld + c)] = sr;
+                A[2 * ((size_t)(k0 + o) * ld + c) + 1] = si;
+            } else {
+                const int r = jj < k0 ? jj : jj + w;
+                A[2 * ((size_t)r * ld + k0 + o)] = -sr;
+                A[2 * ((size_t)r * ld + k0 + o) + 1] = -si;
+            }
+        }
+    }
+}
+
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t st) {
+    const int dsz = (2 * GJ_W * GJ_W + 2 * GJ_W + 2) * (int)sizeof(float);
+    const int psz = (2 * GJ_W * GJ_W + 2 * GJ_PL * (GJ_W + 1)) * (int)sizeof(float);
+    {   // opt in to the large dynamic shared memory (per device, cheap to repeat)
+        cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_diag_w, cudaFuncAttributeMaxDynamicSharedMemorySize, dsz);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, psz);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_panel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, psz);
+        if (e != cudaSuccess) return e;
+    }
+    for (int k0 = 0; k0 < n; k0 += GJ_W) {
+        const int w = (n - k0 < GJ_W) ? n - k0 : GJ_W;
+        k_gj_diag_w<<<1, 512, dsz, st>>>(A, ld, k0, w, status);
+        const int m = n - w;
+        if (m > 0) {
+            const int nb = (m + GJ_PL - 1) / GJ_PL;
+            k_gj_panel<true><<<nb, 256, psz, st>>>(A, ld, n, k0, w);
+            dim3 g((m + TC_TN - 1) / TC_TN, (m + TC_TM - 1) / TC_TM);
+            k_tc_update<<<g, TC_THREADS, TC_SMEM, st>>>(A, ld, m, k0, w, w, status);
+            k_gj_panel<false><<<nb, 256, psz, st>>>(A, ld, n, k0, w);
+        }
+    }
+    return cudaGetLastError();
+}
 
 // copy a diagonal block Z[off:off+n, off:off+n] into B (ld_b), converting precision
 template <typename TS, typename TD>

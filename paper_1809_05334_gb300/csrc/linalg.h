@@ -10,6 +10,8 @@ cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *
                    cudaStream_t st);
 template <typename T>
 cudaError_t gj_invert(T *A, size_t ld, int n, int *status, cudaStream_t st);
+// the same inversion with 64-wide pivot blocks and the tcgen05 (TF32) trailing update
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t st);
 template <typename TS, typename TD>
 cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st);
 template <typename TV>
