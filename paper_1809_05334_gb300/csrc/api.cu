@@ -14,7 +14,9 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
+#include <tuple>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -65,7 +67,7 @@ struct vie_ctx {
     vie::Topology topo;
     // mesh (device)
     DevBuf tv, cen, vol, q5, far32, far64, fv, f5, farea, ffar32, ffar64, hf, n32, n64, fn32, fn64, fcen;
-    DevBuf mk[4], pr[4], to[4], tdom;
+    DevBuf mk[4], pr[4], to[4], tdom, tpart, thalf;
     int npr[4] = {0, 0, 0, 0}, nto[4] = {0, 0, 0, 0};
     // request (device)
     DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab;
@@ -350,6 +352,8 @@ vie::DevMesh dev_mesh(vie_ctx *ctx) {
     m.fn32 = ctx->fn32.as<float>(); m.fn64 = ctx->fn64.as<double>(); m.fcen = ctx->fcen.as<double>();
     m.mk_tt = ctx->mk[0].as<uint16_t>(); m.mk_tf = ctx->mk[1].as<uint16_t>();
     m.mk_ft = ctx->mk[2].as<uint16_t>(); m.mk_ff = ctx->mk[3].as<uint16_t>();
+    m.touch_partner = ctx->tpart.as<int32_t>();
+    m.touch_half = ctx->thalf.as<double>();
     for (int i = 0; i < 4; ++i) {
         m.pr[i] = ctx->pr[i].as<vie::NearEntry>();
         m.to[i] = ctx->to[i].as<vie::NearEntry>();
@@ -823,6 +827,18 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
         if (q.empty()) q.push_back({0, 0, 0, 0});
         CK(upload(ctx->pr[i], p, st));
         CK(upload(ctx->to[i], q, st));
+        if (i == 0) {   // partner (y, x, 8-k) of every touching tetrahedron entry
+            std::map<std::tuple<int, int, int>, int> idx;
+            for (int e = 0; e < ctx->nto[0]; ++e) idx[std::make_tuple(q[e].x, q[e].y, q[e].k)] = e;
+            std::vector<int32_t> part(std::max(ctx->nto[0], 1), 0);
+            for (int e = 0; e < ctx->nto[0]; ++e) {
+                auto it = idx.find(std::make_tuple(q[e].y, q[e].x, 8 - q[e].k));
+                if (it == idx.end()) return fail(ctx, VIE_BAD_MESH, "near-pair lists are not symmetric");
+                part[e] = it->second;
+            }
+            CK(upload(ctx->tpart, part, st));
+            CK(ctx->thalf.ensure(sizeof(double) * 8 * std::max(ctx->nto[0], 1)));
+        }
     }
     ctx->have_mesh = true;
     return VIE_OK;

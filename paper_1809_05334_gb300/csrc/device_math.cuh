@@ -286,13 +286,13 @@ __device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, uns
 //            int R   = ( h^2 int 1/R + 1/2 sum_i t_i (s+R+ - s-R- + R0^2 ln(..)) ) / 3
 //  tetrahedron: int 1/R = 1/2 sum_f d_f int_f 1/R,  int (r'-r)/R = sum_f n_f int_f R
 template <typename T>
-__device__ __forceinline__ T log_rs(T R, T s, T R0sq) {
+__host__ __device__ __forceinline__ T log_rs(T R, T s, T R0sq) {
     // ln(R + s) without cancellation for s < 0: R + s = R0^2 / (R - s)
     return (s >= T(0)) ? log(R + s) : log(R0sq) - log(R - s);
 }
 
 template <typename T>
-__device__ void tri_integrals(const T r[3], const T *v, T &inv, T &rint, bool want_r) {
+__host__ __device__ void tri_integrals(const T r[3], const T *v, T &inv, T &rint, bool want_r) {
     T e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
     T e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
     T n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
@@ -336,7 +336,7 @@ __device__ void tri_integrals(const T r[3], const T *v, T &inv, T &rint, bool wa
 }
 
 template <typename T>
-__device__ void tet_integrals(const T r[3], const T *tv, T &inv, T vec[3], bool want_vec) {
+__host__ __device__ void tet_integrals(const T r[3], const T *tv, T &inv, T vec[3], bool want_vec) {
     inv = 0;
     vec[0] = vec[1] = vec[2] = 0;
 #pragma unroll
@@ -363,6 +363,91 @@ __device__ void tet_integrals(const T r[3], const T *tv, T &inv, T vec[3], bool 
         if (want_vec) {
             vec[0] += n[0] * fr; vec[1] += n[1] * fr; vec[2] += n[2] * fr;
         }
+    }
+}
+
+// The same tetrahedron closed forms with the per-edge quantities shared by the
+// two faces of each edge: 4 vertex distances, 6 edge logarithms
+// ln[(R_b + s_b)/(R_a + s_a)] (orientation independent) and one combined
+// arctangent per (face, edge): atan2(t s_b, R0^2+|h|R_b) - atan2(t s_a, R0^2+|h|R_a)
+// = atan2(y_b x_a - x_b y_a, x_a x_b + y_a y_b) (both angles lie in (-pi/2, pi/2)).
+// tv holds the vertices relative to the observer (the observer is the origin).
+__host__ __device__ inline void tet_integrals_shared(const double *tv, double &inv, double vec[3]) {
+    constexpr int EA[6] = {0, 0, 0, 1, 1, 2}, EB[6] = {1, 2, 3, 2, 3, 3};
+    // edges of face f (opposite vertex f) in the face's vertex order, and the face's third vertex per edge
+    constexpr int FE[4][3] = {{3, 5, 4}, {1, 5, 2}, {0, 4, 2}, {0, 3, 1}};
+    constexpr int FC[4][3] = {{3, 1, 2}, {3, 0, 2}, {3, 0, 1}, {2, 0, 1}};
+    double Rv[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Rv[v] = sqrt(tv[3 * v] * tv[3 * v] + tv[3 * v + 1] * tv[3 * v + 1] + tv[3 * v + 2] * tv[3 * v + 2]);
+    double scale = 0;
+    double L[6], lh[6][3], sa[6], sb[6], sR[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const double *pa = tv + 3 * EA[e], *pb = tv + 3 * EB[e];
+        double d[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+        const double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        scale = fmax(scale, len);
+        for (int q = 0; q < 3; ++q) lh[e][q] = d[q] / len;
+        sa[e] = lh[e][0] * pa[0] + lh[e][1] * pa[1] + lh[e][2] * pa[2];   // along the edge, observer at 0
+        sb[e] = sa[e] + len;
+        const double c0 = pa[1] * lh[e][2] - pa[2] * lh[e][1], c1 = pa[2] * lh[e][0] - pa[0] * lh[e][2],
+                     c2 = pa[0] * lh[e][1] - pa[1] * lh[e][0];
+        const double d2 = c0 * c0 + c1 * c1 + c2 * c2;   // squared distance to the edge line
+        const double Ra = Rv[EA[e]], Rb = Rv[EB[e]];
+        // ln[(Rb + sb)/(Ra + sa)] with R + s = d2/(R - s) for s < 0
+        double lv;
+        if (sa[e] >= 0) lv = log((Rb + sb[e]) / (Ra + sa[e]));
+        else if (sb[e] <= 0) lv = log((Ra - sa[e]) / (Rb - sb[e]));
+        else lv = (d2 > 0) ? log((Rb + sb[e]) * (Ra - sa[e]) / d2) : 0.0;
+        L[e] = lv;
+        sR[e] = sb[e] * Rb - sa[e] * Ra;
+    }
+    const double tiny = 1e-13 * scale;
+    inv = 0;
+    vec[0] = vec[1] = vec[2] = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        // face opposite vertex f; outward normal
+        const int fv[3] = {f == 0 ? 1 : 0, f <= 1 ? 2 : 1, f <= 2 ? 3 : 2};
+        const double *p0 = tv + 3 * fv[0], *p1 = tv + 3 * fv[1], *p2 = tv + 3 * fv[2];
+        const double e1[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+        const double e2[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        const double o = n[0] * (p0[0] - tv[3 * f]) + n[1] * (p0[1] - tv[3 * f + 1]) + n[2] * (p0[2] - tv[3 * f + 2]);
+        const double sg = (o >= 0) ? 1.0 / nn : -1.0 / nn;
+        n[0] *= sg; n[1] *= sg; n[2] *= sg;
+        const double dfc = n[0] * p0[0] + n[1] * p0[1] + n[2] * p0[2];   // n.(p0 - r): signed distance
+        const double h = -dfc, ah = fabs(h);
+        double slog = 0, satan = 0, sr = 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int e = FE[f][q];
+            // in-plane outward normal of the edge: u = l x n, its sign fixed by
+            // pointing away from the face's third vertex
+            const double *pc = tv + 3 * FC[f][q];
+            double u[3] = {lh[e][1] * n[2] - lh[e][2] * n[1], lh[e][2] * n[0] - lh[e][0] * n[2],
+                           lh[e][0] * n[1] - lh[e][1] * n[0]};
+            const double *pa = tv + 3 * EA[e];
+            if (u[0] * (pa[0] - pc[0]) + u[1] * (pa[1] - pc[1]) + u[2] * (pa[2] - pc[2]) < 0) {
+                u[0] = -u[0]; u[1] = -u[1]; u[2] = -u[2];
+            }
+            const double t = u[0] * pa[0] + u[1] * pa[1] + u[2] * pa[2];
+            if (fabs(t) <= tiny) continue;
+            const double R0sq = t * t + h * h;
+            slog += t * L[e];
+            sr += t * (sR[e] + R0sq * L[e]);
+            if (ah > tiny) {
+                const double xa = R0sq + ah * Rv[EA[e]], ya = t * sa[e];
+                const double xb = R0sq + ah * Rv[EB[e]], yb = t * sb[e];
+                satan += atan2(yb * xa - xb * ya, xa * xb + ya * yb);
+            }
+        }
+        const double fi = slog - ah * satan;
+        const double fr = (h * h * fi + 0.5 * sr) / 3.0;
+        inv += 0.5 * dfc * fi;
+        vec[0] += n[0] * fr; vec[1] += n[1] * fr; vec[2] += n[2] * fr;
     }
 }
 

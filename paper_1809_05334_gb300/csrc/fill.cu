@@ -381,6 +381,74 @@ __global__ void __launch_bounds__(128) k_touch_tt(DevMesh m, DevReq q, T *Z, siz
     }
 }
 
+// Touching images, exploiting the symmetry of the two integration orders:
+// order (ii) of the entry (t, s, k) is order (i) of its partner (s, t, 8-k)
+// with the test and source polynomial moments exchanged.  k_touch_half
+// computes order (i) of every entry once (phase-free real moments, FP64;
+// half a warp per entry, lane q = degree-5 point q of the test element);
+// k_touch_combine averages each entry with its partner and scatters.
+__global__ void __launch_bounds__(128) k_touch_half(DevMesh m, const NearEntry *list, int n, double *out) {
+    const int e = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 2 + ((threadIdx.x >> 4) & 1);
+    const int hl = threadIdx.x & 15;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (e < n && hl < 14) {
+        const NearEntry en = list[e];
+        const int t = en.x, s = en.y, k = en.k;
+        const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
+        const double *r5 = m.q5 + (size_t)t * 42 + 3 * hl;
+        const double w = m.vol[t] * c_w5tet[hl];
+        const double *src = m.tv + 12 * (size_t)s;
+        const double *ct = m.cen + 3 * (size_t)t, *cs = m.cen + 3 * (size_t)s;
+        double rel[12];
+        for (int j = 0; j < 4; ++j)
+            for (int d = 0; d < 3; ++d) rel[3 * j + d] = (src[3 * j + d] - R[d]) - r5[d];
+        double I, vec[3];
+        tet_integrals_shared(rel, I, vec);
+        double f[3], rho[3];
+        for (int d = 0; d < 3; ++d) {
+            f[d] = vec[d] + (r5[d] - (cs[d] - R[d])) * I;   // int (r' - c_s)/R over the image source
+            rho[d] = r5[d] - ct[d];
+        }
+        acc[0] = w * I;
+        for (int d = 0; d < 3; ++d) {
+            acc[1 + d] = w * rho[d] * I;   // test polynomial
+            acc[4 + d] = w * f[d];         // source polynomial
+        }
+        acc[7] = w * (rho[0] * f[0] + rho[1] * f[1] + rho[2] * f[2]);
+    }
+    for (int i = 0; i < 8; ++i)
+        for (int o = 8; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o, 16);
+    if (e < n && hl == 0)
+        for (int i = 0; i < 8; ++i) out[8 * (size_t)e + i] = acc[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_touch_combine(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list,
+                                                       const int32_t *partner, const double *half, int n) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const NearEntry en = list[e];
+    const double *a = half + 8 * (size_t)e;
+    const double *b = half + 8 * (size_t)partner[e];
+    const double pr = 0.5 * q.img_ph[2 * en.k], pi = 0.5 * q.img_ph[2 * en.k + 1];
+    // moments of this entry: S and C symmetric, test/source polynomials exchanged in the partner
+    double v[8];
+    v[0] = a[0] + b[0];
+    for (int d = 0; d < 3; ++d) {
+        v[1 + d] = a[1 + d] + b[4 + d];
+        v[4 + d] = a[4 + d] + b[1 + d];
+    }
+    v[7] = a[7] + b[7];
+    Mom<T> mo;
+    mo.S = {T(pr * v[0]), T(pi * v[0])};
+    mo.C = {T(pr * v[7]), T(pi * v[7])};
+    for (int d = 0; d < 3; ++d) {
+        mo.A[d] = {T(pr * v[1 + d]), T(pi * v[1 + d])};
+        mo.B[d] = {T(pr * v[4 + d]), T(pi * v[4 + d])};
+    }
+    scatter_tt<T>(m, q, Z, N, en.x, en.y, mo);
+}
+
 // ---------------------------------------------------------------------------
 // scalar element pairs involving charge faces:
 //   TF: test tet t, source charge face f   -> Z[row(t,i), frow(f)] += wt 3c qs_f S
@@ -635,7 +703,12 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
     auto grid1 = [](int n) { return (unsigned)((n + 127) / 128); };
     auto gridw = [](int n) { return (unsigned)(((size_t)n * 32 + 127) / 128); };
     if (m.npr[0]) k_pr_tt<T><<<grid1(m.npr[0]), blk, 0, st>>>(m, q, Z, N, m.pr[0], m.npr[0]);
-    if (m.nto[0]) k_touch_tt<T><<<gridw(m.nto[0]), blk, 0, st>>>(m, q, Z, N, m.to[0], m.nto[0]);
+    if (m.nto[0]) {
+        k_touch_half<<<(unsigned)(((size_t)(m.nto[0] + 1) / 2 * 32 + 127) / 128), blk, 0, st>>>(m, m.to[0], m.nto[0],
+                                                                                              m.touch_half);
+        k_touch_combine<T><<<grid1(m.nto[0]), blk, 0, st>>>(m, q, Z, N, m.to[0], m.touch_partner, m.touch_half,
+                                                            m.nto[0]);
+    }
     if (m.nf) {
         k_far_scalar<T, PK_TF><<<dim3((m.nf + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N, m.nt, m.nf, m.mk_tf);
         if (m.npr[1]) k_pr_scalar<T, PK_TF><<<grid1(m.npr[1]), blk, 0, st>>>(m, q, Z, N, m.pr[1], m.npr[1]);

@@ -41,6 +41,8 @@ struct DevMesh {
     // pr = elements not touching (product rule), to = touching (closed forms)
     const NearEntry *pr[4], *to[4];
     int npr[4], nto[4];
+    const int32_t *touch_partner;   // [nto[0]] index of the entry (y, x, 8-k)
+    double *touch_half;             // [nto[0]][8] scratch: one integration order per entry
 
     template <typename T> __device__ const T *far(int t) const;
     template <typename T> __device__ const T *ffar(int f) const;

@@ -113,6 +113,71 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float *__restrict__ C,
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
 
+    // per-thread registers of one chunk: A items (row, k pair) and B items (column, k pair)
+    constexpr int NA = TC_TM * 8 / TC_THREADS, NB = TC_TN * 8 / TC_THREADS;   // 4 and 4
+    float4 ra[NA];
+    float4 rb[NB];   // (Re B[k], Im B[k], Re B[k+1], Im B[k+1]) of one column
+    auto load_chunk = [&](int c) {
+        const int kc0 = c * (TC_CHUNK / 2);
+        const int kcn = min(TC_CHUNK / 2, K - kc0);
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+            const int e = tid + u * TC_THREADS;
+            const int i = e >> 3, f = e & 7;
+            const int ii = ti + i;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ii < m && 2 * f < kcn) {
+                const int r = ii < k0 ? ii : ii + w;
+                const float *src = C + 2 * ((size_t)r * ld + k0 + kc0 + 2 * f);
+                if (2 * f + 1 < kcn) v = __ldcg(reinterpret_cast<const float4 *>(src));
+                else v = make_float4(__ldcg(src), __ldcg(src + 1), 0.f, 0.f);
+            }
+            ra[u] = v;
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int e = tid + u * TC_THREADS;
+            const int j = e % TC_TN, kp = e / TC_TN;
+            const int jj = tj + j;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (jj < m && 2 * kp < kcn) {
+                const int cc = jj < k0 ? jj : jj + w;
+                const float2 u0 = __ldcg(reinterpret_cast<const float2 *>(C + 2 * ((size_t)(k0 + kc0 + 2 * kp) * ld + cc)));
+                v.x = u0.x;
+                v.y = u0.y;
+                if (2 * kp + 1 < kcn) {
+                    const float2 u1 =
+                        __ldcg(reinterpret_cast<const float2 *>(C + 2 * ((size_t)(k0 + kc0 + 2 * kp + 1) * ld + cc)));
+                    v.z = u1.x;
+                    v.w = u1.y;
+                }
+            }
+            rb[u] = v;
+        }
+    };
+    auto store_chunk = [&](uint8_t *a_st, uint8_t *b_st) {
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+            const int e = tid + u * TC_THREADS;
+            const int i = e >> 3, f = e & 7;
+            const float4 v = ra[u];
+            *reinterpret_cast<float4 *>(a_st + sw128(i, 4 * f)) =
+                make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int e = tid + u * TC_THREADS;
+            const int j = e % TC_TN, kp = e / TC_TN;
+            const float4 v = rb[u];
+            // real column 2j (Re C): [Re B, -Im B]; column 2j+1 (Im C): [Im B, Re B]
+            *reinterpret_cast<float4 *>(b_st + sw128(2 * j, 4 * kp)) =
+                make_float4(to_tf32(v.x), to_tf32(-v.y), to_tf32(v.z), to_tf32(-v.w));
+            *reinterpret_cast<float4 *>(b_st + sw128(2 * j + 1, 4 * kp)) =
+                make_float4(to_tf32(v.y), to_tf32(v.x), to_tf32(v.w), to_tf32(v.z));
+        }
+    };
+
+    load_chunk(0);
     for (int c = 0; c < nch; ++c) {
         const int st = c % TC_STAGES;
         uint8_t *a_st = sA + st * TC_A_CHUNK_BYTES;
@@ -122,49 +187,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float *__restrict__ C,
             ok = __syncthreads_and(done) && ok;
             if (!ok) break;
         }
-        const int kc0 = c * (TC_CHUNK / 2);                 // first complex k of the chunk
-        const int kcn = min(TC_CHUNK / 2, K - kc0);         // complex k in the chunk
-        // A: 128 rows x 16 complex k; thread -> (row, k pair)
-        for (int e = tid; e < TC_TM * 8; e += TC_THREADS) {
-            const int i = e >> 3, f = e & 7;
-            const int ii = ti + i;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (ii < m && 2 * f < kcn) {
-                const int r = ii < k0 ? ii : ii + w;
-                const float *src = C + 2 * ((size_t)r * ld + k0 + kc0 + 2 * f);
-                if (2 * f + 1 < kcn) v = *reinterpret_cast<const float4 *>(src);
-                else v = make_float4(src[0], src[1], 0.f, 0.f);
-            }
-            *reinterpret_cast<float4 *>(a_st + sw128(i, 4 * f)) =
-                make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
-        }
-        // B: 16 complex k rows x 128 columns -> 256 real columns; thread -> (column, k pair)
-        for (int e = tid; e < TC_TN * 8; e += TC_THREADS) {
-            const int j = e % TC_TN, kp = e / TC_TN;
-            const int jj = tj + j;
-            float b0r = 0.f, b0i = 0.f, b1r = 0.f, b1i = 0.f;
-            if (jj < m && 2 * kp < kcn) {
-                const int cc = jj < k0 ? jj : jj + w;
-                const float2 u0 = *reinterpret_cast<const float2 *>(C + 2 * ((size_t)(k0 + kc0 + 2 * kp) * ld + cc));
-                b0r = u0.x; b0i = u0.y;
-                if (2 * kp + 1 < kcn) {
-                    const float2 u1 =
-                        *reinterpret_cast<const float2 *>(C + 2 * ((size_t)(k0 + kc0 + 2 * kp + 1) * ld + cc));
-                    b1r = u1.x; b1i = u1.y;
-                }
-            }
-            // real column 2j (Re C): [Re B, -Im B]; column 2j+1 (Im C): [Im B, Re B]
-            *reinterpret_cast<float4 *>(b_st + sw128(2 * j, 4 * kp)) =
-                make_float4(to_tf32(b0r), to_tf32(-b0i), to_tf32(b1r), to_tf32(-b1i));
-            *reinterpret_cast<float4 *>(b_st + sw128(2 * j + 1, 4 * kp)) =
-                make_float4(to_tf32(b0i), to_tf32(b0r), to_tf32(b1i), to_tf32(b1r));
-        }
+        store_chunk(a_st, b_st);
+        if (c + 1 < nch) load_chunk(c + 1);   // next chunk's loads overlap this chunk's MMAs
         // make the generic-proxy shared stores visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
+            const int kcn = min(TC_CHUNK / 2, K - c * (TC_CHUNK / 2));
             const int steps = (2 * kcn + 7) / 8;
             for (int s2 = 0; s2 < steps; ++s2) {
                 const uint64_t da = make_desc(smem_u32(a_st) + s2 * 32), db = make_desc(smem_u32(b_st) + s2 * 32);
