@@ -103,6 +103,12 @@ typedef struct {
     int32_t n_near_pairs;                /* near tetrahedron pairs of the mesh       */
     int64_t far_pair_evals;              /* Green's-function evaluations of the
                                             tetrahedron-pair kernel (16 per pair)   */
+    int64_t h2d_bytes, d2h_bytes;        /* host<->device bytes this solve copied    */
+    /* tensor-core update of the block inversion (options.timing = 1): total
+       device time of its k_tc_n launches and their algorithmic bytes (the
+       read-modify-write of the trailing matrix plus one read of the panels) */
+    double  k_tc_ms, k_tc_bytes;
+    int32_t k_tc_n, reserved2;
 } vie_result;
 
 /* Fill *opt with defaults (FP32 with refinement, preconditioner on, tol 1e-6). */

@@ -48,8 +48,11 @@ struct DevBuf {
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
 
+thread_local int64_t *g_h2d_counter = nullptr;   // bytes counter of the solve in progress (host thread local use)
+
 template <typename T>
 cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t st) {
+    if (g_h2d_counter) *g_h2d_counter += (int64_t)(sizeof(T) * v.size());
     cudaError_t e = b.ensure(sizeof(T) * v.size());
     if (e != cudaSuccess || v.empty()) return e;
     e = cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
@@ -75,6 +78,7 @@ struct vie_ctx {
     // solve buffers
     DevBuf Z, b, x, r, u, w, V, h, y, Minv, status, acc, J, rt, cout;
     size_t ld = 0;
+    int64_t h2d = 0, d2h = 0;   // bytes copied by the current solve
     // CUDA events for options.timing
     std::vector<cudaEvent_t> events;
     size_t ev_used = 0;
@@ -366,6 +370,7 @@ vie::DevMesh dev_mesh(vie_ctx *ctx) {
 struct Timing {
     cudaEvent_t fill0 = nullptr, fill1 = nullptr, far0 = nullptr, far1 = nullptr, fac0 = nullptr, fac1 = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> mv;
+    vie::KernelTimer tc;
 };
 
 template <typename TZ>
@@ -418,6 +423,7 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
     auto norms2 = [&](const double *vec, double out[2]) -> int {
         CK(vie::dots<double>(vec, 0, 1, vec, N, hd, st));
         CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+        ctx->d2h += sizeof(double) * 4;
         CK(cudaStreamSynchronize(st));
         out[0] = std::sqrt(std::max(hh[0], 0.0));
         out[1] = std::sqrt(std::max(hh[2], 0.0));
@@ -448,6 +454,7 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
         if (pre) { if (int e = precond_apply<TV>(ctx, H, moff, mld, u, w, st)) return e; }
         else CK(cudaMemcpyAsync(w, u, sizeof(TV) * vs, cudaMemcpyDeviceToDevice, st));
         CK(vie::dots<TV>(w, 0, 1, w, N, hd, st));
+        ctx->d2h += sizeof(double) * 4;
         CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         double beta[2] = {std::sqrt(hh[0]), std::sqrt(hh[2])};
@@ -478,10 +485,12 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
                 CK(vie::dots<TV>(V, vs, k + 1, vn, N, hd, st));
                 CK(vie::subtract<TV>(V, vs, k + 1, hd, vn, N, st));
                 CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4 * (k + 1), cudaMemcpyDeviceToHost, st));
+                ctx->d2h += sizeof(double) * 4 * (k + 1);
                 CK(cudaStreamSynchronize(st));
                 for (int i = 0; i < 4 * (k + 1); ++i) hsum[i] += hh[i];
             }
             CK(vie::dots<TV>(vn, 0, 1, vn, N, hd, st));
+            ctx->d2h += sizeof(double) * 4;
             CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             double hn[2] = {std::sqrt(std::max(hh[0], 0.0)), std::sqrt(std::max(hh[2], 0.0))};
@@ -531,6 +540,7 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
         }
         if (kmax > 0) {
             CK(cudaMemcpyAsync(ctx->y.p, yv.data(), sizeof(double) * 4 * kmax, cudaMemcpyHostToDevice, st));
+            ctx->h2d += sizeof(double) * 4 * kmax;
             CK(vie::combine<TV>(V, vs, kmax, ctx->y.as<double>(), x, N, st));
             CK(cudaStreamSynchronize(st));
         }
@@ -544,8 +554,11 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
     return (rel[0] <= tol && rel[1] <= tol) ? VIE_OK : VIE_NOT_CONVERGED;
 }
 
+cudaEvent_t pool_event(void *c) { return static_cast<vie_ctx *>(c)->event(); }
+
 template <typename TZ>
-int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vector<size_t> &mld, cudaStream_t st) {
+int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vector<size_t> &mld, cudaStream_t st,
+           vie::KernelTimer *kt) {
     size_t tot = 0;
     moff.clear();
     mld.clear();
@@ -561,9 +574,10 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
     for (size_t k = 0; k < H.blk_n.size(); ++k) {
         float *B = ctx->Minv.as<float>() + 2 * moff[k];
         CK((vie::copy_block<TZ, float>(ctx->Z.as<TZ>(), ctx->ld, H.blk_off[k], H.blk_n[k], B, mld[k], st)));
-        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), st));
+        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), st, kt));
     }
     int stat = 0;
+    ctx->d2h += sizeof(int);
     CK(cudaMemcpyAsync(&stat, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (stat) return fail(ctx, VIE_BREAKDOWN, "zero or non-finite pivot while inverting a domain block");
@@ -577,7 +591,12 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     if (int e = prepare(ctx, req, H)) return e;
     vie::DevMesh m = dev_mesh(ctx);
     vie::DevReq q{};
-    if (int e = upload_request(ctx, H, q, st)) return e;
+    ctx->h2d = (int64_t)sizeof(vie::EwaldTables);   // the constant-memory upload of the request
+    ctx->d2h = 0;
+    g_h2d_counter = &ctx->h2d;
+    int ur = upload_request(ctx, H, q, st);
+    g_h2d_counter = nullptr;
+    if (ur) return ur;
     ctx->ev_used = 0;
     Timing tm;
     tm.fill0 = ctx->event(); tm.fill1 = ctx->event(); tm.far0 = ctx->event(); tm.far1 = ctx->event();
@@ -589,7 +608,8 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     std::vector<size_t> moff, mld;
     if (ctx->opt.use_precond) {
         if (tm.fac0) CK(cudaEventRecord(tm.fac0, st));
-        if (int e = factor<TZ>(ctx, H, moff, mld, st)) return e;
+        if (ctx->opt.timing) { tm.tc.alloc = pool_event; tm.tc.pool = ctx; }
+        if (int e = factor<TZ>(ctx, H, moff, mld, st, ctx->opt.timing ? &tm.tc : nullptr)) return e;
         if (tm.fac1) { CK(cudaEventRecord(tm.fac1, st)); CK(cudaStreamSynchronize(st)); }
     }
     auto t2 = clk::now();
@@ -609,6 +629,7 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     std::vector<double> acc(2 * nd), rt(4);
     CK(cudaMemcpyAsync(acc.data(), ctx->acc.p, sizeof(double) * 2 * nd, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(rt.data(), ctx->rt.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+    ctx->d2h += sizeof(double) * (2 * nd + 4);
     if (req->coeffs_out) {
         const size_t bytes = sizeof(double) * 4 * (size_t)ctx->topo.N;
         if (req->coeffs_on_device) {
@@ -617,6 +638,7 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
             CK(ctx->cout.ensure(bytes));
             CK(vie::launch_unpermute(ctx->x.as<double>(), ctx->perm.as<int32_t>(), ctx->topo.N, ctx->cout.as<double>(), st));
             CK(cudaMemcpyAsync(req->coeffs_out, ctx->cout.p, bytes, cudaMemcpyDeviceToHost, st));
+            ctx->d2h += bytes;
         }
     }
     CK(cudaStreamSynchronize(st));
@@ -633,6 +655,8 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     res->t_post_ms = ms(t3, t4);
     res->n_unknowns = ctx->topo.N;
     res->n_near_pairs = (int32_t)ctx->topo.near_tt.size();
+    res->h2d_bytes = ctx->h2d;
+    res->d2h_bytes = ctx->d2h;
     res->far_pair_evals = 16 * (int64_t)ctx->topo.nt * ctx->topo.nt;
     if (ctx->opt.timing) {
         res->k_far_tt_ms = ev_ms(tm.far0, tm.far1);
@@ -642,6 +666,14 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
         for (auto &p : tm.mv) s += ev_ms(p.first, p.second);
         res->k_matvec_ms = s;
         res->k_matvec_n = (int32_t)tm.mv.size();
+        double ts = 0, tb = 0;
+        for (size_t i = 0; i < tm.tc.ev.size(); ++i) {
+            ts += ev_ms(tm.tc.ev[i].first, tm.tc.ev[i].second);
+            tb += tm.tc.work[i];
+        }
+        res->k_tc_ms = ts;
+        res->k_tc_bytes = tb;
+        res->k_tc_n = (int32_t)tm.tc.ev.size();
     }
     res->status = stat;
     return stat;

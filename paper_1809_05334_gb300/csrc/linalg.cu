@@ -25,12 +25,13 @@ template <> struct V2<double> { using t = double2; };
 // ---------------------------------------------------------------------------
 constexpr int MV_ROWS = 4;
 constexpr int MV_WARPS = 8;
-constexpr int MV_TILE = 512;
+template <typename TA> __host__ __device__ constexpr int mv_tile() { return 512; }   // x tile of 512 columns
 
 template <typename TZ, typename TX, typename TA, bool ACCUM>
 __global__ void __launch_bounds__(MV_WARPS * 32)
 k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__restrict__ x,
          TA *__restrict__ y, TA alpha) {
+    constexpr int MV_TILE = mv_tile<TA>();
     __shared__ TA xs[MV_TILE * 4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = (blockIdx.x * MV_WARPS + warp) * MV_ROWS;
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(256) k_gj_panel(float *A, size_t ld, int n, in
     }
 }
 
-cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t st) {
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t st, KernelTimer *kt) {
     const int dsz = (2 * GJ_W * GJ_W + 2 * GJ_W + 2) * (int)sizeof(float);
     const int psz = (2 * GJ_W * GJ_W + 2 * GJ_PL * (GJ_W + 1)) * (int)sizeof(float);
     {   // opt in to the large dynamic shared memory (per device, cheap to repeat)
@@ -478,7 +479,15 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t s
             const int nb = (m + GJ_PL - 1) / GJ_PL;
             k_gj_panel<true><<<nb, 256, psz, st>>>(A, ld, n, k0, w);
             dim3 g((m + TC_TN - 1) / TC_TN, (m + TC_TM - 1) / TC_TM);
+            cudaEvent_t e0 = kt ? kt->next() : nullptr, e1 = kt ? kt->next() : nullptr;
+            if (e0) cudaEventRecord(e0, st);
             k_tc_update<<<g, TC_THREADS, TC_SMEM, st>>>(A, ld, m, k0, w, w, status);
+            if (e1) {
+                cudaEventRecord(e1, st);
+                // algorithmic bytes: read-modify-write of the m x m trailing matrix and one
+                // read of the two m x w panels (complex FP32)
+                kt->add(e0, e1, 16.0 * m * (double)m + 16.0 * m * (double)w);
+            }
             k_gj_panel<false><<<nb, 256, psz, st>>>(A, ld, n, k0, w);
         }
     }

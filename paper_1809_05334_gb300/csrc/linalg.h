@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstddef>
+#include <utility>
+#include <vector>
 
 namespace vie {
 
@@ -10,8 +12,17 @@ cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *
                    cudaStream_t st);
 template <typename T>
 cudaError_t gj_invert(T *A, size_t ld, int n, int *status, cudaStream_t st);
-// the same inversion with 64-wide pivot blocks and the tcgen05 (TF32) trailing update
-cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t st);
+// CUDA-event timing of selected launches (optional)
+struct KernelTimer {
+    cudaEvent_t (*alloc)(void *) = nullptr;   // returns the next event of the caller's pool
+    void *pool = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    std::vector<double> work;
+    cudaEvent_t next() { return alloc ? alloc(pool) : nullptr; }
+    void add(cudaEvent_t a, cudaEvent_t b, double w) { ev.push_back({a, b}); work.push_back(w); }
+};
+// the same inversion with 128-wide pivot blocks and the tcgen05 (TF32) trailing update
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t st, KernelTimer *kt = nullptr);
 template <typename TS, typename TD>
 cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st);
 template <typename TV>

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float *__restrict__ C,
                 const int jj = tj + c0 / 2 + 2 * p2;
                 const int cc = jj < k0 ? jj : jj + w;
                 vec[p2] = (jj + 1 < m) && !(jj < k0 && jj + 1 >= k0) && (cc & 1) == 0;
-                if (vec[p2]) old[p2] = *reinterpret_cast<const float4 *>(C + 2 * ((size_t)r * ld + cc));
+                if (vec[p2]) old[p2] = __ldcs(reinterpret_cast<const float4 *>(C + 2 * ((size_t)r * ld + cc)));
             }
 #pragma unroll
             for (int p2 = 0; p2 < 8; ++p2) {
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float *__restrict__ C,
                     const int cc = jj < k0 ? jj : jj + w;
                     float4 o = old[p2];
                     o.x -= a0; o.y -= a1; o.z -= a2; o.w -= a3;
-                    *reinterpret_cast<float4 *>(C + 2 * ((size_t)r * ld + cc)) = o;
+                    __stcs(reinterpret_cast<float4 *>(C + 2 * ((size_t)r * ld + cc)), o);   // streaming: keep the panels in L2
                 } else {
                     for (int h = 0; h < 2; ++h) {
                         const int j2 = jj + h;
