@@ -31,7 +31,19 @@ sys.path.insert(0, ROOT)
 METRIC = "(lambda,theta) solves/s"
 UNIT = "solves/s"
 LAM, THETA, PHI = 500.0, 0.0, 0.0
-WORKLOAD = "plasmonic cell 200 nm period, Ag sphere r=20 nm in 100 nm active over 40 nm buffer, lambda=500 nm, theta=0, TE+TM"
+WORKLOADS = {
+    "plasmonic": ("config_plasmonic",
+                  "plasmonic cell 200 nm period, Ag sphere r=20 nm in 100 nm active over 40 nm buffer, "
+                  "~21k unknowns, lambda=500 nm, theta=0, TE+TM"),
+    # the same geometry at the sweep density (~8.9k unknowns): a smaller case for profiling
+    "sweep_cell": ("config_sweep_geometry",
+                   "plasmonic cell 200 nm period at sweep density (~8.9k unknowns), lambda=500 nm, theta=0, TE+TM"),
+}
+
+
+def _cell(name):
+    import cellgen
+    return getattr(cellgen, WORKLOADS[name][0])()
 
 
 def _peaks():
@@ -108,7 +120,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = vie.VIE_FP32 if args.precision == "fp32" else vie.VIE_FP64
-    cell = cellgen.config_plasmonic()
+    cell = _cell(args.workload)
     eps = cell.eps(LAM)
     solver = vie.Solver(device=local, precision=prec, tol=1e-6, timing=True)
     n = solver.set_mesh(cell)
@@ -169,7 +181,7 @@ def run_ours(args):
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64+f64" if args.precision == "fp32" else "c128",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_unknowns": n, "n_tets": cell.n_tets, "precision": args.precision,
+        "config": {"workload": WORKLOADS[args.workload][1], "n_unknowns": n, "n_tets": cell.n_tets, "precision": args.precision,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (Z is %.1f GB)" % (n * n * (8 if prec == vie.VIE_FP32 else 16) / 1e9)},
         "phases_ms": {"fill": last["t_fill_ms"], "factor": last["t_factor_ms"], "solve": last["t_solve_ms"],
@@ -185,7 +197,8 @@ def run_ours(args):
     }
     res["roofline"], res["rooflines"] = roofline(last, n, peaks, prec == vie.VIE_FP32)
     res["clocks"] = clk.summary()
-    res["gpu_launches"] = launches_per_step(last, n)
+    # kernels launched inside the timed region, counted by the library at each launch site
+    res["gpu_launches"] = int(sum(r["n_launches"] for r in results))
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         res["cpu_baseline"] = cpu_baseline(args)
     solver.close()
@@ -194,16 +207,6 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res))
-
-
-def launches_per_step(last, n):
-    """Kernel launches of one solve (counted from the library's launch sequence)."""
-    nb = (n + 31) // 32
-    fill = 2 + 1 + 1 + 6          # gram, rhs, far/near tet pairs, face kernels
-    factor = 4 * nb + 3           # Gauss-Jordan: 4 kernels per 32-column step, 3 copies
-    it = sum(last["iterations"]) // 2 + 1
-    gmres = it * 14
-    return int(fill + factor + gmres + 4)
 
 
 def roofline(last, n, peaks, fp32):
@@ -276,7 +279,7 @@ def run_reference(args):
     res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt * scale * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sample_tets": sample.n_tets, "full_tets": full.n_tets},
+           "config": {"workload": WORKLOADS["plasmonic"][1], "sample_tets": sample.n_tets, "full_tets": full.n_tets},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": "each step: one oracle solve of the geometry at %d tets; value scaled by "
                                       "the tetrahedron-pair ratio %.0f to the %d-tet workload"
@@ -293,6 +296,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="plasmonic", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -108,7 +108,8 @@ typedef struct {
        device time of its k_tc_n launches and their algorithmic bytes (the
        read-modify-write of the trailing matrix plus one read of the panels) */
     double  k_tc_ms, k_tc_bytes;
-    int32_t k_tc_n, reserved2;
+    int32_t k_tc_n;
+    int32_t n_launches;                  /* CUDA kernels this call launched          */
 } vie_result;
 
 /* Fill *opt with defaults (FP32 with refinement, preconditioner on, tol 1e-6). */
@@ -173,9 +174,9 @@ int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out
    out_dev [n] complex (re,im) are DEVICE buffers owned by the caller, with the
    same in-cell restriction as vie_green; precision VIE_FP64 or VIE_FP32;
    stream a cudaStream_t (NULL: legacy default stream).  Needs no context.
-   Scratch: the FP32 interpolation tables live in a file-scope device array of
-   about 0.8 MB that every GPU loading this library keeps until the process
-   exits; requests needing more than 96 distinct Floquet decay constants are
+   Scratch: the Ewald parameter block and the FP32 interpolation tables live
+   in a file-scope device array of about 0.85 MB that every GPU loading this
+   library keeps until the process exits; requests needing more than 96 distinct Floquet decay constants are
    rejected with VIE_EINVAL.  The tables are rebuilt completely by each call,
    so nothing has to start at zero.  All calls share that array and the
    library's constant tables: calls whose work overlaps on the GPU race.

@@ -30,6 +30,10 @@
 
 using cplx = std::complex<double>;
 
+namespace vie {
+thread_local int64_t g_launches = 0;
+}
+
 namespace {
 
 struct DevBuf {
@@ -73,7 +77,7 @@ struct vie_ctx {
     DevBuf mk[4], pr[4], to[4], tdom, tpart, thalf;
     int npr[4] = {0, 0, 0, 0}, nto[4] = {0, 0, 0, 0};
     // request (device)
-    DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab;
+    DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab, ew;
     double z_extent = 0;
     // solve buffers
     DevBuf Z, b, x, r, u, w, V, h, y, Minv, status, acc, J, rt, cout;
@@ -319,12 +323,17 @@ int upload_request(vie_ctx *ctx, const HostReq &H, vie::DevReq &q, cudaStream_t 
     std::vector<double> ord = H.orders;
     if (ord.empty()) ord.assign(4, 0.0);
     CK(upload(ctx->orders, ord, st));
-    CK(vie::upload_ewald(H.ew, st));
+    CK(ctx->ew.ensure(sizeof(vie::EwaldTables)));
+    CK(vie::upload_ewald(ctx->ew.as<vie::EwaldTables>(), H.ew, st));
+    if (g_h2d_counter) *g_h2d_counter += (int64_t)sizeof(vie::EwaldTables);
     CK(ctx->stab.ensure(sizeof(float) * 4 * vie::NSPAT));
     CK(ctx->ztab.ensure(sizeof(float2) * 4 * vie::NZTAB * std::max(H.ew.n_tab, 1)));
-    CK(vie::launch_build_tables(ctx->stab.as<float>(), ctx->ztab.as<float2>(), H.ew.n_tab, st));
+    CK(vie::launch_build_tables(ctx->ew.as<vie::EwaldTables>(), ctx->stab.as<float>(), ctx->ztab.as<float2>(),
+                                H.ew.n_tab, st));
     q.stab = ctx->stab.as<float>();
     q.ztab = ctx->ztab.as<float2>();
+    q.ew = ctx->ew.as<vie::EwaldTables>();
+    q.ef = vie::make_ewald_f32(H.ew);
     q.k0 = H.k0; q.kx = H.kx; q.ky = H.ky;
     for (int k = 0; k < 9; ++k) {
         const double phs = H.kx * (k / 3 - 1) * ctx->topo.a + H.ky * (k % 3 - 1) * ctx->topo.b;
@@ -591,7 +600,8 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     if (int e = prepare(ctx, req, H)) return e;
     vie::DevMesh m = dev_mesh(ctx);
     vie::DevReq q{};
-    ctx->h2d = (int64_t)sizeof(vie::EwaldTables);   // the constant-memory upload of the request
+    const int64_t launches0 = vie::g_launches;
+    ctx->h2d = 0;
     ctx->d2h = 0;
     g_h2d_counter = &ctx->h2d;
     int ur = upload_request(ctx, H, q, st);
@@ -658,6 +668,7 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     res->h2d_bytes = ctx->h2d;
     res->d2h_bytes = ctx->d2h;
     res->far_pair_evals = 16 * (int64_t)ctx->topo.nt * ctx->topo.nt;
+    res->n_launches = (int32_t)(vie::g_launches - launches0);
     if (ctx->opt.timing) {
         res->k_far_tt_ms = ev_ms(tm.far0, tm.far1);
         res->k_fill_ms = ev_ms(tm.fill0, tm.fill1);
@@ -980,16 +991,18 @@ int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out
     ctx->z_extent = saved_z;
     if (e) return e;
     cudaStream_t st = 0;
-    CK(vie::upload_ewald(H.ew, st));
+    CK(ctx->ew.ensure(sizeof(vie::EwaldTables)));
+    CK(vie::upload_ewald(ctx->ew.as<vie::EwaldTables>(), H.ew, st));
     CK(ctx->stab.ensure(sizeof(float) * 4 * vie::NSPAT));
     CK(ctx->ztab.ensure(sizeof(float2) * 4 * vie::NZTAB * std::max(H.ew.n_tab, 1)));
-    CK(vie::launch_build_tables(ctx->stab.as<float>(), ctx->ztab.as<float2>(), H.ew.n_tab, st));
+    CK(vie::launch_build_tables(ctx->ew.as<vie::EwaldTables>(), ctx->stab.as<float>(), ctx->ztab.as<float2>(),
+                                H.ew.n_tab, st));
     DevBuf dd, dout;
     CK(dd.ensure(sizeof(double) * 3 * n));
     CK(dout.ensure(sizeof(double) * 2 * n));
     CK(cudaMemcpy(dd.p, d, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
     CK(vie::launch_green(dd.as<double>(), dout.as<double>(), n, precision == VIE_FP64, ctx->stab.as<float>(),
-                         ctx->ztab.as<float2>(), st));
+                         ctx->ztab.as<float2>(), ctx->ew.as<vie::EwaldTables>(), vie::make_ewald_f32(H.ew), st));
     CK(cudaMemcpy(out, dout.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
     return VIE_OK;
 }

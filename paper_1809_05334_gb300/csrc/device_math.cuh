@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include "ewald_params.h"
+
 namespace vie {
 
 template <typename T> struct cx { T re, im; };
@@ -91,66 +93,35 @@ template <typename T> __device__ __forceinline__ T erfcx_r(T x) {
     return inv * fma(T(2) * p, inv, rsqrt_pi<T>());
 }
 
-// ---------------------------------------------------------------------------
-// Ewald parameters of one incidence.  Spatial series (images R_mn):
-//   phase_mn exp(b^2 - R^2 E^2) Re erfcx(R E + j b) / (4 pi R),  b = k/(2E)
-// Spectral series (Floquet modes k_t = k_par + 2 pi (p/a, q/b)):
-//   exp(-j k_t.rho) / (4 a b gamma) [e^{gamma z} erfc(gamma/2E + zE) + e^{-gamma z} erfc(gamma/2E - zE)]
-constexpr int MAX_IMG = 160;
-constexpr int MAX_MODE = 160;
-struct EwaldTables {
-    // per image: (m a, n b, Re, Im) of exp(j k_par.R_mn) exp(b^2)/(4 pi)
-    double img64[MAX_IMG][4];
-    float img32[MAX_IMG][4];
-    // per mode: (k_tx, k_ty, gamma_re, gamma_im, exp(-gamma^2/4E^2), Re, Im of 1/(4ab gamma))
-    double mode64[MAX_MODE][8];
-    float mode32[MAX_MODE][8];
-    int n_img, n_mode;
-    int near_img[9];        // image-table index of (m,n) = (k/3-1, k%3-1)
-    double E, bb, a, b, xcut64;
-    float xcut32;
-    double reg0_re;          // limit R->0 of (image term - static term), without the phase
-    // tabulated FP32 evaluation (see green_tab): spatial kernel F(x) on [0, xs_max],
-    // spectral G_g(z) per distinct gamma on [0, z_max], piecewise cubic Hermite
-    float xs_max, xs_inv_h, z_max, z_inv_h, e_mb2, Ef;
-    float kx, ky, step_x, step_y;   // k_t,pq = (kx + p step_x, ky + q step_y)
-    int P, Q, n_tab;
-    int rect_tab[MAX_MODE];  // table of rectangle entry (p+P)(2Q+1)+(q+Q), -1 outside the cut
-    double tab_gamma[MAX_MODE][2];   // gamma of each table
-    double tab_ig[MAX_MODE][2];      // 1/(4ab gamma) of each table
-    double tab_pre[MAX_MODE];        // exp(-gamma^2/4E^2)
-};
-constexpr int NSPAT = 512;    // spatial intervals
-constexpr int NZTAB = 256;    // spectral intervals
-static __constant__ EwaldTables c_ew;        // filled by upload_ewald() (fill.cu)
+// Ewald parameter blocks (EwaldTables, EwaldF32): ewald_params.h
 
 template <typename T> struct ETraits;
 template <> struct ETraits<double> {
-    __device__ static const double *img(int i) { return c_ew.img64[i]; }
-    __device__ static const double *mode(int i) { return c_ew.mode64[i]; }
-    __device__ static double xcut() { return c_ew.xcut64; }
+    __device__ static const double *img(const EwaldTables *ew, int i) { return ew->img64[i]; }
+    __device__ static const double *mode(const EwaldTables *ew, int i) { return ew->mode64[i]; }
+    __device__ static double xcut(const EwaldTables *ew) { return ew->xcut64; }
 };
 template <> struct ETraits<float> {
-    __device__ static const float *img(int i) { return c_ew.img32[i]; }
-    __device__ static const float *mode(int i) { return c_ew.mode32[i]; }
-    __device__ static float xcut() { return c_ew.xcut32; }
+    __device__ static const float *img(const EwaldTables *ew, int i) { return ew->img32[i]; }
+    __device__ static const float *mode(const EwaldTables *ew, int i) { return ew->mode32[i]; }
+    __device__ static float xcut(const EwaldTables *ew) { return ew->xcut32; }
 };
 
 // g_p(d) for an in-cell difference d; images whose bit is set in `sub`
 // (9-bit mask over (m,n) in {-1,0,1}^2) have their static part
 // phase/(4 pi R) removed.
 template <typename T>
-__device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub) {
-    const T E = T(c_ew.E);
-    const T bb = T(c_ew.bb);
-    const T xc = ETraits<T>::xcut() + T(0.5);
+__device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub, const EwaldTables *__restrict__ ew) {
+    const T E = T(ew->E);
+    const T bb = T(ew->bb);
+    const T xc = ETraits<T>::xcut(ew) + T(0.5);
     cx<T> acc = {T(0), T(0)};
     // spectral series
     const T z = fabs(dz);
     const T ez = exp(-(z * E) * (z * E));
     const T inv2E = T(0.5) / E;
-    for (int i = 0; i < c_ew.n_mode; ++i) {
-        const T *md = ETraits<T>::mode(i);
+    for (int i = 0; i < ew->n_mode; ++i) {
+        const T *md = ETraits<T>::mode(ew, i);
         T s, c;
         sincos(-(md[0] * dx + md[1] * dy), &s, &c);
         cx<T> ph = {c, s};
@@ -176,8 +147,8 @@ __device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub) {
         acc = acc + ph * (br * ig);
     }
     // spatial series
-    for (int i = 0; i < c_ew.n_img; ++i) {
-        const T *im = ETraits<T>::img(i);
+    for (int i = 0; i < ew->n_img; ++i) {
+        const T *im = ETraits<T>::img(ew, i);
         T x = dx + im[0], y = dy + im[1];
         T R2 = x * x + y * y + dz * dz;
         T R = sqrt(R2);
@@ -186,14 +157,14 @@ __device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub) {
         if (sub) {
 #pragma unroll
             for (int k = 0; k < 9; ++k)
-                if (((sub >> k) & 1u) && c_ew.near_img[k] == i) regular = true;
+                if (((sub >> k) & 1u) && ew->near_img[k] == i) regular = true;
         }
         if (regular && R * E < T(1e-6)) {
             // continuous limit at R = 0 of (image term - static term):
             // reg0 = (E/4pi)[2 b erfi(b) - (2/sqrt pi) exp(b^2)]; the table
             // phase carries exp(b^2)/(4 pi), undone here
             cx<T> ph = {im[2], im[3]};
-            T unscale = T(4.0 * CUDART_PI) * exp(-bb * bb) * T(c_ew.reg0_re);
+            T unscale = T(4.0 * CUDART_PI) * exp(-bb * bb) * T(ew->reg0_re);
             acc = acc + unscale * ph;
             continue;
         }
@@ -213,27 +184,27 @@ __device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub) {
 //            cancellation in the first interval
 // stab: [NSPAT][4] cubic coefficients (shared memory); ztab: [n_tab][NZTAB][4] complex
 __device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, unsigned sub, const float *stab,
-                                               const float2 *__restrict__ ztab) {
+                                               const float2 *__restrict__ ztab, const EwaldF32 &ew) {
     cx<float> acc = {0.f, 0.f};
     const float z = fabsf(dz);
-    float zu = fminf(z * c_ew.z_inv_h, float(NZTAB));
+    float zu = fminf(z * ew.z_inv_h, float(NZTAB));
     int iz = min((int)zu, NZTAB - 1);
     const float u = zu - iz;
-    const int P = c_ew.P, Q = c_ew.Q, nq = 2 * Q + 1;
+    const int P = ew.P, Q = ew.Q, nq = 2 * Q + 1;
     float s, c;
-    sincospif(-(c_ew.kx - P * c_ew.step_x) * dx * 0.31830988618f, &s, &c);
+    sincospif(-(ew.kx - P * ew.step_x) * dx * 0.31830988618f, &s, &c);
     cx<float> ex = {c, s};
-    sincospif(-c_ew.step_x * dx * 0.31830988618f, &s, &c);
+    sincospif(-ew.step_x * dx * 0.31830988618f, &s, &c);
     const cx<float> sx = {c, s};
-    sincospif(-(c_ew.ky - Q * c_ew.step_y) * dy * 0.31830988618f, &s, &c);
+    sincospif(-(ew.ky - Q * ew.step_y) * dy * 0.31830988618f, &s, &c);
     cx<float> ey0 = {c, s};
-    sincospif(-c_ew.step_y * dy * 0.31830988618f, &s, &c);
+    sincospif(-ew.step_y * dy * 0.31830988618f, &s, &c);
     const cx<float> sy = {c, s};
     for (int p = 0; p <= 2 * P; ++p) {
         cx<float> inner = {0.f, 0.f};
         cx<float> ey = ey0;
         for (int q = 0; q < nq; ++q) {
-            const int tb = c_ew.rect_tab[p * nq + q];
+            const int tb = ew.rect_tab[p * nq + q];
             if (tb >= 0) {
                 const float2 *cf = ztab + ((size_t)tb * NZTAB + iz) * 4;
                 const float2 c0 = __ldg(cf), c1 = __ldg(cf + 1), c2 = __ldg(cf + 2), c3 = __ldg(cf + 3);
@@ -246,10 +217,10 @@ __device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, uns
         acc = acc + ex * inner;
         ex = ex * sx;
     }
-    const float E = c_ew.Ef;
-    const float xmax = c_ew.xs_max, ih = c_ew.xs_inv_h;
-    for (int i = 0; i < c_ew.n_img; ++i) {
-        const float *im = c_ew.img32[i];
+    const float E = ew.Ef;
+    const float xmax = ew.xs_max, ih = ew.xs_inv_h;
+    for (int i = 0; i < ew.n_img; ++i) {
+        const float *im = ew.img[i];
         const float x = dx + im[0], y = dy + im[1];
         const float R = sqrtf(x * x + y * y + dz * dz);
         const float xr = R * E;
@@ -258,7 +229,7 @@ __device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, uns
         if (sub) {
 #pragma unroll
             for (int k = 0; k < 9; ++k)
-                if (((sub >> k) & 1u) && c_ew.near_img[k] == i) regular = true;
+                if (((sub >> k) & 1u) && ew.near_img[k] == i) regular = true;
         }
         const float xu = xr * ih;
         const int ix = min((int)xu, NSPAT - 1);
@@ -269,7 +240,7 @@ __device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, uns
             if (ix == 0)   // (F(x) - F(0))/R = E (c1 + v (c2 + v c3)) / h
                 val = E * ih * fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]);
             else
-                val = (fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) - c_ew.e_mb2) / R;
+                val = (fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) - ew.e_mb2) / R;
         } else {
             val = fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) / R;
         }

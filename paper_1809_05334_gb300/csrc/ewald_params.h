@@ -1,0 +1,61 @@
+// Ewald parameters of one incidence, shared by host (set-up) and device code.
+#pragma once
+
+namespace vie {
+
+// Ewald parameters of one incidence.  Spatial series (images R_mn):
+//   phase_mn exp(b^2 - R^2 E^2) Re erfcx(R E + j b) / (4 pi R),  b = k/(2E)
+// Spectral series (Floquet modes k_t = k_par + 2 pi (p/a, q/b)):
+//   exp(-j k_t.rho) / (4 a b gamma) [e^{gamma z} erfc(gamma/2E + zE) + e^{-gamma z} erfc(gamma/2E - zE)]
+constexpr int MAX_IMG = 160;
+constexpr int MAX_MODE = 160;
+struct EwaldTables {
+    // per image: (m a, n b, Re, Im) of exp(j k_par.R_mn) exp(b^2)/(4 pi)
+    double img64[MAX_IMG][4];
+    float img32[MAX_IMG][4];
+    // per mode: (k_tx, k_ty, gamma_re, gamma_im, exp(-gamma^2/4E^2), Re, Im of 1/(4ab gamma))
+    double mode64[MAX_MODE][8];
+    float mode32[MAX_MODE][8];
+    int n_img, n_mode;
+    int near_img[9];        // image-table index of (m,n) = (k/3-1, k%3-1)
+    double E, bb, a, b, xcut64;
+    float xcut32;
+    double reg0_re;          // limit R->0 of (image term - static term), without the phase
+    // tabulated FP32 evaluation (see green_tab): spatial kernel F(x) on [0, xs_max],
+    // spectral G_g(z) per distinct gamma on [0, z_max], piecewise cubic Hermite
+    float xs_max, xs_inv_h, z_max, z_inv_h, e_mb2, Ef;
+    float kx, ky, step_x, step_y;   // k_t,pq = (kx + p step_x, ky + q step_y)
+    int P, Q, n_tab;
+    int rect_tab[MAX_MODE];  // table of rectangle entry (p+P)(2Q+1)+(q+Q), -1 outside the cut
+    double tab_gamma[MAX_MODE][2];   // gamma of each table
+    double tab_ig[MAX_MODE][2];      // 1/(4ab gamma) of each table
+    double tab_pre[MAX_MODE];        // exp(-gamma^2/4E^2)
+};
+constexpr int NSPAT = 512;    // spatial intervals
+constexpr int NZTAB = 256;    // spectral intervals
+// EwaldTables lives in device global memory, one copy per request in flight, so
+// independent solves can run concurrently.  The part of it that the FP32
+// tabulated evaluation reads in its inner loops travels as a kernel parameter
+// (EwaldF32 below, ~3.3 KB, __grid_constant__): warp-uniform reads of it are
+// served by the constant cache and every launch carries its own copy.
+struct EwaldF32 {
+    float img[MAX_IMG][4];   // = EwaldTables::img32
+    int rect_tab[MAX_MODE];
+    int near_img[9];
+    int n_img, P, Q;
+    float xs_max, xs_inv_h, z_inv_h, e_mb2, Ef, kx, ky, step_x, step_y;
+};
+inline EwaldF32 make_ewald_f32(const EwaldTables &t) {
+    EwaldF32 f{};
+    for (int i = 0; i < MAX_IMG; ++i)
+        for (int k = 0; k < 4; ++k) f.img[i][k] = t.img32[i][k];
+    for (int i = 0; i < MAX_MODE; ++i) f.rect_tab[i] = t.rect_tab[i];
+    for (int k = 0; k < 9; ++k) f.near_img[k] = t.near_img[k];
+    f.n_img = t.n_img; f.P = t.P; f.Q = t.Q;
+    f.xs_max = t.xs_max; f.xs_inv_h = t.xs_inv_h; f.z_inv_h = t.z_inv_h; f.e_mb2 = t.e_mb2; f.Ef = t.Ef;
+    f.kx = t.kx; f.ky = t.ky; f.step_x = t.step_x; f.step_y = t.step_y;
+    return f;
+}
+
+
+}  // namespace vie

@@ -65,8 +65,8 @@ cudaError_t upload_constants() {
     return cudaMemcpyToSymbol(c_w5tri, w5f, sizeof(w5f));
 }
 
-cudaError_t upload_ewald(const EwaldTables &t, cudaStream_t st) {
-    return cudaMemcpyToSymbolAsync(c_ew, &t, sizeof(t), 0, cudaMemcpyHostToDevice, st);
+cudaError_t upload_ewald(EwaldTables *dev, const EwaldTables &t, cudaStream_t st) {
+    return cudaMemcpyAsync(dev, &t, sizeof(t), cudaMemcpyHostToDevice, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -80,21 +80,21 @@ __device__ void hermite(double f0, double d0, double f1, double d1, double h, do
     c[3] = 2.0 * (f0 - f1) + h * (d0 + d1);
 }
 
-__device__ void spatial_node(double x, double &F, double &dF) {
+__device__ void spatial_node(const EwaldTables *ew, double x, double &F, double &dF) {
     // F(x) = exp(-x^2) Re erfcx(x + j b),  F'(x) = -exp(-x^2) (2 b Im erfcx(x + j b) + 2/sqrt(pi))
-    const double b = c_ew.bb;
+    const double b = ew->bb;
     cx<double> w = erfcx_c<double>(cx<double>{x, b});
     const double g = exp(-x * x);
     F = g * w.re;
     dF = -g * (2.0 * b * w.im + 2.0 * rsqrt_pi<double>());
 }
 
-__device__ void spectral_node(int tb, double z, cx<double> &G, cx<double> &dG) {
+__device__ void spectral_node(const EwaldTables *ew, int tb, double z, cx<double> &G, cx<double> &dG) {
     // G(z) = (t1 + t2)/(4ab gamma), G'(z) = gamma (t1 - t2)/(4ab gamma)
-    const double E = c_ew.E;
-    const cx<double> g = {c_ew.tab_gamma[tb][0], c_ew.tab_gamma[tb][1]};
-    const cx<double> ig = {c_ew.tab_ig[tb][0], c_ew.tab_ig[tb][1]};
-    const double pre = c_ew.tab_pre[tb] * exp(-(z * E) * (z * E));
+    const double E = ew->E;
+    const cx<double> g = {ew->tab_gamma[tb][0], ew->tab_gamma[tb][1]};
+    const cx<double> ig = {ew->tab_ig[tb][0], ew->tab_ig[tb][1]};
+    const double pre = ew->tab_pre[tb] * exp(-(z * E) * (z * E));
     cx<double> t1, t2;
     if (g.im == 0.0) {
         const double gr = g.re;
@@ -113,13 +113,13 @@ __device__ void spectral_node(int tb, double z, cx<double> &G, cx<double> &dG) {
     dG = (g * (t1 - t2)) * ig;
 }
 
-__global__ void k_build_tables(float *stab, float2 *ztab, int n_tab) {
+__global__ void k_build_tables(const EwaldTables *__restrict__ ew, float *stab, float2 *ztab, int n_tab) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < NSPAT) {
-        const double h = double(c_ew.xs_max) / NSPAT;
+        const double h = double(ew->xs_max) / NSPAT;
         double F0, D0, F1, D1, c[4];
-        spatial_node(i * h, F0, D0);
-        spatial_node((i + 1) * h, F1, D1);
+        spatial_node(ew, i * h, F0, D0);
+        spatial_node(ew, (i + 1) * h, F1, D1);
         hermite(F0, D0, F1, D1, h, c);
         for (int k = 0; k < 4; ++k) stab[4 * i + k] = float(c[k]);
         return;
@@ -127,33 +127,34 @@ __global__ void k_build_tables(float *stab, float2 *ztab, int n_tab) {
     const int j = i - NSPAT;
     const int tb = j / NZTAB, iz = j % NZTAB;
     if (tb >= n_tab) return;
-    const double h = double(c_ew.z_max) / NZTAB;
+    const double h = double(ew->z_max) / NZTAB;
     cx<double> G0, D0, G1, D1;
-    spectral_node(tb, iz * h, G0, D0);
-    spectral_node(tb, (iz + 1) * h, G1, D1);
+    spectral_node(ew, tb, iz * h, G0, D0);
+    spectral_node(ew, tb, (iz + 1) * h, G1, D1);
     double cr[4], ci[4];
     hermite(G0.re, D0.re, G1.re, D1.re, h, cr);
     hermite(G0.im, D0.im, G1.im, D1.im, h, ci);
     for (int k = 0; k < 4; ++k) ztab[((size_t)tb * NZTAB + iz) * 4 + k] = make_float2(float(cr[k]), float(ci[k]));
 }
 
-cudaError_t launch_build_tables(float *stab, float2 *ztab, int n_tab, cudaStream_t st) {
+cudaError_t launch_build_tables(const EwaldTables *ew, float *stab, float2 *ztab, int n_tab, cudaStream_t st) {
     const int n = NSPAT + n_tab * NZTAB;
-    k_build_tables<<<(n + 127) / 128, 128, 0, st>>>(stab, ztab, n_tab);
+    k_build_tables<<<(n + 127) / 128, 128, 0, st>>>(ew, stab, ztab, n_tab); ++g_launches;
     return cudaGetLastError();
 }
 
 // g_p for the fill kernels: FP64 by the Ewald series, FP32 from the tables
 template <typename T> struct Green;
 template <> struct Green<double> {
-    __device__ static cx<double> eval(double dx, double dy, double dz, unsigned sub, const float *, const float2 *) {
-        return green_p<double>(dx, dy, dz, sub);
+    __device__ static cx<double> eval(double dx, double dy, double dz, unsigned sub, const float *, const float2 *,
+                                      const EwaldTables *ew, const EwaldF32 &) {
+        return green_p<double>(dx, dy, dz, sub, ew);
     }
 };
 template <> struct Green<float> {
     __device__ static cx<float> eval(float dx, float dy, float dz, unsigned sub, const float *stab,
-                                     const float2 *ztab) {
-        return green_tab(dx, dy, dz, sub, stab, ztab);
+                                     const float2 *ztab, const EwaldTables *, const EwaldF32 &ef) {
+        return green_tab(dx, dy, dz, sub, stab, ztab, ef);
     }
 };
 
@@ -221,7 +222,7 @@ __device__ void scatter_tt(const DevMesh &m, const DevReq &q, T *Z, size_t N, in
 // pair the static part is removed here and integrated by k_pr_tt / k_touch_tt
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) k_far_tt(DevMesh m, DevReq q, T *Z, size_t N) {
+__global__ void __launch_bounds__(128) k_far_tt(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N) {
     extern __shared__ float smem_tab[];
     const float *stab = stage_stab<T>(q, smem_tab);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(128) k_far_tt(DevMesh m, DevReq q, T *Z, size_
         for (int b = 0; b < 4; ++b) {
             const T yb[3] = {fs[3 * b], fs[3 * b + 1], fs[3 * b + 2]};
             const T rb[3] = {yb[0] - fs[12], yb[1] - fs[13], yb[2] - fs[14]};
-            cx<T> g = Green<T>::eval(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab);
+            cx<T> g = Green<T>::eval(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab, q.ew, q.ef);
             g = wgt * g;
             mo.S = mo.S + g;
             for (int d = 0; d < 3; ++d) {
@@ -299,7 +300,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // near image of a pair, elements not touching: degree-5 x degree-5 product
 // rule of exp(j k_par.R)/(4 pi R), one thread per (pair, image)
 template <typename T>
-__global__ void __launch_bounds__(128) k_pr_tt(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list, int n) {
+__global__ void __launch_bounds__(128) k_pr_tt(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N, const NearEntry *list, int n) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const NearEntry en = list[e];
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(128) k_pr_tt(DevMesh m, DevReq q, T *Z, size_t
 // the degree-5 points of the other, both orders averaged, in FP64; one warp per
 // (pair, image), lanes 0..13 order (i), 14..27 order (ii)
 template <typename T>
-__global__ void __launch_bounds__(128) k_touch_tt(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list,
+__global__ void __launch_bounds__(128) k_touch_tt(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N, const NearEntry *list,
                                                   int n) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(128) k_touch_half(DevMesh m, const NearEntry *
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_touch_combine(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list,
+__global__ void __launch_bounds__(128) k_touch_combine(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N, const NearEntry *list,
                                                        const int32_t *partner, const double *half, int n) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
@@ -495,7 +496,7 @@ __device__ __forceinline__ const T *far_el(const DevMesh &m, int e) {
 }
 
 template <typename T, int PK>
-__global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, DevReq q, T *Z, size_t N, int nx, int ny,
+__global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N, int nx, int ny,
                                                     const uint16_t *mk) {
     extern __shared__ float smem_tab[];
     const float *stab = stage_stab<T>(q, smem_tab);
@@ -513,7 +514,7 @@ __global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, DevReq q, T *Z, s
     for (int a = 0; a < qx; ++a)
         for (int b = 0; b < qy; ++b) {
             cx<T> g = Green<T>::eval(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1], fx[3 * a + 2] - fy[3 * b + 2],
-                                     sub, stab, q.ztab);
+                                     sub, stab, q.ztab, q.ew, q.ef);
             S = S + g;
         }
     S = wgt * S;
@@ -540,7 +541,7 @@ __device__ double static_scalar(const double *r5, bool other_tet, const double *
 }
 
 template <typename T, int PK>
-__global__ void __launch_bounds__(128) k_pr_scalar(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list,
+__global__ void __launch_bounds__(128) k_pr_scalar(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N, const NearEntry *list,
                                                    int n) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
@@ -570,7 +571,7 @@ __global__ void __launch_bounds__(128) k_pr_scalar(DevMesh m, DevReq q, T *Z, si
 }
 
 template <typename T, int PK>
-__global__ void __launch_bounds__(128) k_touch_scalar(DevMesh m, DevReq q, T *Z, size_t N, const NearEntry *list,
+__global__ void __launch_bounds__(128) k_touch_scalar(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N, const NearEntry *list,
                                                       int n) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -608,7 +609,7 @@ __global__ void __launch_bounds__(128) k_touch_scalar(DevMesh m, DevReq q, T *Z,
 // local (Gram) term and right-hand side, per tetrahedron
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_gram(DevMesh m, DevReq q, T *Z, size_t N) {
+__global__ void k_gram(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.nt) return;
     const double *P = m.tv + 12 * (size_t)t;
@@ -632,7 +633,7 @@ __global__ void k_gram(DevMesh m, DevReq q, T *Z, size_t N) {
     }
 }
 
-__global__ void k_rhs(DevMesh m, DevReq q, double *b) {
+__global__ void k_rhs(DevMesh m, const __grid_constant__ DevReq q, double *b) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.nt) return;
     const double *P = m.tv + 12 * (size_t)t;
@@ -675,10 +676,11 @@ __global__ void k_erfcx(const double *u, double *out, int n) {
 }
 
 template <typename T>
-__global__ void k_green(const double *d, double *out, int n, const float *stab, const float2 *ztab) {
+__global__ void k_green(const double *d, double *out, int n, const float *stab, const float2 *ztab,
+                        const EwaldTables *ew, const __grid_constant__ EwaldF32 ef) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    cx<T> r = Green<T>::eval(T(d[3 * i]), T(d[3 * i + 1]), T(d[3 * i + 2]), 0u, stab, ztab);
+    cx<T> r = Green<T>::eval(T(d[3 * i]), T(d[3 * i + 1]), T(d[3 * i + 2]), 0u, stab, ztab, ew, ef);
     out[2 * i] = double(r.re);
     out[2 * i + 1] = double(r.im);
 }
@@ -694,33 +696,33 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
     cudaMemsetAsync(Z, 0, sizeof(T) * 2 * ld * (size_t)m.N, st);
     if (b) cudaMemsetAsync(b, 0, sizeof(double) * 4 * (size_t)m.N, st);
     dim3 blk(128);
-    k_gram<T><<<(m.nt + 127) / 128, blk, 0, st>>>(m, q, Z, N);
-    if (b) k_rhs<<<(m.nt + 127) / 128, blk, 0, st>>>(m, q, b);
+    k_gram<T><<<(m.nt + 127) / 128, blk, 0, st>>>(m, q, Z, N); ++g_launches;
+    if (b) { k_rhs<<<(m.nt + 127) / 128, blk, 0, st>>>(m, q, b); ++g_launches; }
     const size_t sm = stab_bytes<T>();
     if (far0) cudaEventRecord(far0, st);
-    k_far_tt<T><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N);
+    k_far_tt<T><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N); ++g_launches;
     if (far1) cudaEventRecord(far1, st);
     auto grid1 = [](int n) { return (unsigned)((n + 127) / 128); };
     auto gridw = [](int n) { return (unsigned)(((size_t)n * 32 + 127) / 128); };
-    if (m.npr[0]) k_pr_tt<T><<<grid1(m.npr[0]), blk, 0, st>>>(m, q, Z, N, m.pr[0], m.npr[0]);
+    if (m.npr[0]) { k_pr_tt<T><<<grid1(m.npr[0]), blk, 0, st>>>(m, q, Z, N, m.pr[0], m.npr[0]); ++g_launches; }
     if (m.nto[0]) {
         k_touch_half<<<(unsigned)(((size_t)(m.nto[0] + 1) / 2 * 32 + 127) / 128), blk, 0, st>>>(m, m.to[0], m.nto[0],
-                                                                                              m.touch_half);
+                                                                                              m.touch_half); ++g_launches;
         k_touch_combine<T><<<grid1(m.nto[0]), blk, 0, st>>>(m, q, Z, N, m.to[0], m.touch_partner, m.touch_half,
-                                                            m.nto[0]);
+                                                            m.nto[0]); ++g_launches;
     }
     if (m.nf) {
-        k_far_scalar<T, PK_TF><<<dim3((m.nf + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N, m.nt, m.nf, m.mk_tf);
-        if (m.npr[1]) k_pr_scalar<T, PK_TF><<<grid1(m.npr[1]), blk, 0, st>>>(m, q, Z, N, m.pr[1], m.npr[1]);
-        if (m.nto[1]) k_touch_scalar<T, PK_TF><<<gridw(m.nto[1]), blk, 0, st>>>(m, q, Z, N, m.to[1], m.nto[1]);
+        k_far_scalar<T, PK_TF><<<dim3((m.nf + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N, m.nt, m.nf, m.mk_tf); ++g_launches;
+        if (m.npr[1]) { k_pr_scalar<T, PK_TF><<<grid1(m.npr[1]), blk, 0, st>>>(m, q, Z, N, m.pr[1], m.npr[1]); ++g_launches; }
+        if (m.nto[1]) { k_touch_scalar<T, PK_TF><<<gridw(m.nto[1]), blk, 0, st>>>(m, q, Z, N, m.to[1], m.nto[1]); ++g_launches; }
     }
     if (m.nh) {
-        k_far_scalar<T, PK_FT><<<dim3((m.nt + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nt, m.mk_ft);
-        if (m.npr[2]) k_pr_scalar<T, PK_FT><<<grid1(m.npr[2]), blk, 0, st>>>(m, q, Z, N, m.pr[2], m.npr[2]);
-        if (m.nto[2]) k_touch_scalar<T, PK_FT><<<gridw(m.nto[2]), blk, 0, st>>>(m, q, Z, N, m.to[2], m.nto[2]);
-        k_far_scalar<T, PK_FF><<<dim3((m.nf + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nf, m.mk_ff);
-        if (m.npr[3]) k_pr_scalar<T, PK_FF><<<grid1(m.npr[3]), blk, 0, st>>>(m, q, Z, N, m.pr[3], m.npr[3]);
-        if (m.nto[3]) k_touch_scalar<T, PK_FF><<<gridw(m.nto[3]), blk, 0, st>>>(m, q, Z, N, m.to[3], m.nto[3]);
+        k_far_scalar<T, PK_FT><<<dim3((m.nt + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nt, m.mk_ft); ++g_launches;
+        if (m.npr[2]) { k_pr_scalar<T, PK_FT><<<grid1(m.npr[2]), blk, 0, st>>>(m, q, Z, N, m.pr[2], m.npr[2]); ++g_launches; }
+        if (m.nto[2]) { k_touch_scalar<T, PK_FT><<<gridw(m.nto[2]), blk, 0, st>>>(m, q, Z, N, m.to[2], m.nto[2]); ++g_launches; }
+        k_far_scalar<T, PK_FF><<<dim3((m.nf + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nf, m.mk_ff); ++g_launches;
+        if (m.npr[3]) { k_pr_scalar<T, PK_FF><<<grid1(m.npr[3]), blk, 0, st>>>(m, q, Z, N, m.pr[3], m.npr[3]); ++g_launches; }
+        if (m.nto[3]) { k_touch_scalar<T, PK_FF><<<gridw(m.nto[3]), blk, 0, st>>>(m, q, Z, N, m.to[3], m.nto[3]); ++g_launches; }
     }
     return cudaGetLastError();
 }
@@ -731,15 +733,15 @@ template cudaError_t launch_fill<double>(const DevMesh &, const DevReq &, double
                                          cudaEvent_t, cudaEvent_t);
 
 cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStream_t st) {
-    if (fp64) k_erfcx<double><<<(n + 127) / 128, 128, 0, st>>>(u, out, n);
-    else k_erfcx<float><<<(n + 127) / 128, 128, 0, st>>>(u, out, n);
+    if (fp64) { k_erfcx<double><<<(n + 127) / 128, 128, 0, st>>>(u, out, n); ++g_launches; }
+    else { k_erfcx<float><<<(n + 127) / 128, 128, 0, st>>>(u, out, n); ++g_launches; }
     return cudaGetLastError();
 }
 
 cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const float *stab, const float2 *ztab,
-                         cudaStream_t st) {
-    if (fp64) k_green<double><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab);
-    else k_green<float><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab);
+                         const EwaldTables *ew, const EwaldF32 &ef, cudaStream_t st) {
+    if (fp64) { k_green<double><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
+    else { k_green<float><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
     return cudaGetLastError();
 }
 
@@ -762,8 +764,10 @@ cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const f
 namespace vie {
 
 constexpr int NOALLOC_MAX_TAB = 96;   // distinct Floquet decay constants the scratch can hold
-constexpr size_t NOALLOC_FLOAT2 = 2 * NSPAT + (size_t)NOALLOC_MAX_TAB * NZTAB * 4;
-// spatial table (4*NSPAT floats) followed by the spectral tables (float2): 786 KB + 8 KB
+constexpr size_t NOALLOC_EW_FLOAT2 = (sizeof(EwaldTables) + sizeof(float2) - 1) / sizeof(float2);
+constexpr size_t NOALLOC_FLOAT2 = NOALLOC_EW_FLOAT2 + 2 * NSPAT + (size_t)NOALLOC_MAX_TAB * NZTAB * 4;
+// Ewald parameter block (~49 KB), spatial table (4*NSPAT floats), spectral tables
+// (float2): about 0.85 MB in total
 static __device__ __align__(256) float2 g_noalloc_scratch[NOALLOC_FLOAT2];
 
 namespace {
@@ -903,10 +907,13 @@ extern "C" int vie_green_noalloc(double lambda_nm, double theta, double phi, dou
     if (rc != VIE_OK) return rc;
     if (precision == VIE_FP32 && tabs.n_tab > NOALLOC_MAX_TAB) return VIE_EINVAL;   // scratch too small
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (upload_ewald(tabs, st) != cudaSuccess) return VIE_ECUDA;
-    float *stab = reinterpret_cast<float *>(g_scratch_ptr[dev]);
-    float2 *ztab = g_scratch_ptr[dev] + 2 * NSPAT;
-    if (precision == VIE_FP32 && launch_build_tables(stab, ztab, tabs.n_tab, st) != cudaSuccess) return VIE_ECUDA;
-    if (launch_green(d_dev, out_dev, n, precision == VIE_FP64, stab, ztab, st) != cudaSuccess) return VIE_ECUDA;
+    EwaldTables *ewd = reinterpret_cast<EwaldTables *>(g_scratch_ptr[dev]);
+    if (upload_ewald(ewd, tabs, st) != cudaSuccess) return VIE_ECUDA;
+    float *stab = reinterpret_cast<float *>(g_scratch_ptr[dev] + NOALLOC_EW_FLOAT2);
+    float2 *ztab = g_scratch_ptr[dev] + NOALLOC_EW_FLOAT2 + 2 * NSPAT;
+    if (precision == VIE_FP32 && launch_build_tables(ewd, stab, ztab, tabs.n_tab, st) != cudaSuccess) return VIE_ECUDA;
+    if (launch_green(d_dev, out_dev, n, precision == VIE_FP64, stab, ztab, ewd, make_ewald_f32(tabs), st) !=
+        cudaSuccess)
+        return VIE_ECUDA;
     return VIE_OK;
 }

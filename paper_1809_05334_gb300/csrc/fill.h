@@ -4,11 +4,10 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "ewald_params.h"
 #include "vie_internal.h"
 
 namespace vie {
-
-struct EwaldTables;
 
 // one near image k (= 3(m+1) + (n+1)) of the element pair (x, y)
 struct NearEntry {
@@ -72,6 +71,8 @@ struct DevReq {
     double img_ph[18];     // exp(j k_par.R_k)/(4 pi) of the near images k = 0..8
     const float *stab;     // FP32 tables of the Ewald series (built per request)
     const float2 *ztab;
+    const EwaldTables *ew; // Ewald parameters of the request (device memory)
+    EwaldF32 ef;           // FP32 inner-loop parameters (kernel parameter space)
 };
 
 // degree-5 rules: barycentric points [14][4] / [7][3] (may be null) and weights
@@ -81,13 +82,13 @@ void tet_rule2(double (*pts)[4], double *w);
 void tri_rule2(double (*pts)[3], double *w);
 
 cudaError_t upload_constants();
-cudaError_t upload_ewald(const EwaldTables &t, cudaStream_t st);
+cudaError_t upload_ewald(EwaldTables *dev, const EwaldTables &t, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, double *b, cudaStream_t st,
                         cudaEvent_t far0 = nullptr, cudaEvent_t far1 = nullptr);
 cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStream_t st);
 cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const float *stab, const float2 *ztab,
-                         cudaStream_t st);
-cudaError_t launch_build_tables(float *stab, float2 *ztab, int n_tab, cudaStream_t st);
+                         const EwaldTables *ew, const EwaldF32 &ef, cudaStream_t st);
+cudaError_t launch_build_tables(const EwaldTables *ew, float *stab, float2 *ztab, int n_tab, cudaStream_t st);
 
 }  // namespace vie

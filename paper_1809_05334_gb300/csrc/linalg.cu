@@ -111,6 +111,7 @@ cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *
         k_matvec<TZ, TX, TA, true><<<grid, MV_WARPS * 32, 0, st>>>(A, ld, rows, cols, x, y, alpha);
     else
         k_matvec<TZ, TX, TA, false><<<grid, MV_WARPS * 32, 0, st>>>(A, ld, rows, cols, x, y, alpha);
+    ++g_launches;
     return cudaGetLastError();
 }
 
@@ -314,13 +315,13 @@ template <typename T>
 cudaError_t gj_invert(T *A, size_t ld, int n, int *status, cudaStream_t st) {
     for (int k0 = 0; k0 < n; k0 += GJ_NB) {
         const int w = (n - k0 < GJ_NB) ? n - k0 : GJ_NB;
-        k_gj_diag<T><<<1, 256, 0, st>>>(A, ld, k0, w, status);
+        k_gj_diag<T><<<1, 256, 0, st>>>(A, ld, k0, w, status); ++g_launches;
         const int m = n - w;
         if (m > 0) {
-            k_gj_row<T><<<(m + 127) / 128, 128, 0, st>>>(A, ld, n, k0, w);
+            k_gj_row<T><<<(m + 127) / 128, 128, 0, st>>>(A, ld, n, k0, w); ++g_launches;
             dim3 g((m + 63) / 64, (m + 63) / 64);
-            k_gj_update<T><<<g, 256, 0, st>>>(A, ld, n, k0, w);
-            k_gj_col<T><<<(m + 127) / 128, 128, 0, st>>>(A, ld, n, k0, w);
+            k_gj_update<T><<<g, 256, 0, st>>>(A, ld, n, k0, w); ++g_launches;
+            k_gj_col<T><<<(m + 127) / 128, 128, 0, st>>>(A, ld, n, k0, w); ++g_launches;
         }
     }
     return cudaGetLastError();
@@ -473,22 +474,22 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t s
     }
     for (int k0 = 0; k0 < n; k0 += GJ_W) {
         const int w = (n - k0 < GJ_W) ? n - k0 : GJ_W;
-        k_gj_diag_w<<<1, 512, dsz, st>>>(A, ld, k0, w, status);
+        k_gj_diag_w<<<1, 512, dsz, st>>>(A, ld, k0, w, status); ++g_launches;
         const int m = n - w;
         if (m > 0) {
             const int nb = (m + GJ_PL - 1) / GJ_PL;
-            k_gj_panel<true><<<nb, 256, psz, st>>>(A, ld, n, k0, w);
+            k_gj_panel<true><<<nb, 256, psz, st>>>(A, ld, n, k0, w); ++g_launches;
             dim3 g((m + TC_TN - 1) / TC_TN, (m + TC_TM - 1) / TC_TM);
             cudaEvent_t e0 = kt ? kt->next() : nullptr, e1 = kt ? kt->next() : nullptr;
             if (e0) cudaEventRecord(e0, st);
-            k_tc_update<<<g, TC_THREADS, TC_SMEM, st>>>(A, ld, m, k0, w, w, status);
+            k_tc_update<<<g, TC_THREADS, TC_SMEM, st>>>(A, ld, m, k0, w, w, status); ++g_launches;
             if (e1) {
                 cudaEventRecord(e1, st);
                 // algorithmic bytes: read-modify-write of the m x m trailing matrix and one
                 // read of the two m x w panels (complex FP32)
                 kt->add(e0, e1, 16.0 * m * (double)m + 16.0 * m * (double)w);
             }
-            k_gj_panel<false><<<nb, 256, psz, st>>>(A, ld, n, k0, w);
+            k_gj_panel<false><<<nb, 256, psz, st>>>(A, ld, n, k0, w); ++g_launches;
         }
     }
     return cudaGetLastError();
@@ -513,7 +514,7 @@ __global__ void k_copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, siz
 template <typename TS, typename TD>
 cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st) {
     size_t tot = (size_t)n * ldb;
-    k_copy_block<TS, TD><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Z, ldz, off, n, B, ldb);
+    k_copy_block<TS, TD><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Z, ldz, off, n, B, ldb); ++g_launches;
     return cudaGetLastError();
 }
 template cudaError_t copy_block<float, float>(const float *, size_t, int, int, float *, size_t, cudaStream_t);
@@ -612,22 +613,22 @@ __global__ void k_combine(const TV *V, size_t vstride, int nv, const double *y, 
 template <typename TV>
 cudaError_t dots(const TV *V, size_t vstride, int nv, const TV *w, int n, double *h, cudaStream_t st) {
     cudaMemsetAsync(h, 0, sizeof(double) * 4 * nv, st);
-    k_dots<TV><<<296, 256, 0, st>>>(V, vstride, nv, w, n, h);
+    k_dots<TV><<<296, 256, 0, st>>>(V, vstride, nv, w, n, h); ++g_launches;
     return cudaGetLastError();
 }
 template <typename TV>
 cudaError_t subtract(const TV *V, size_t vstride, int nv, const double *h, TV *w, int n, cudaStream_t st) {
-    k_subtract<TV><<<(n + 255) / 256, 256, 0, st>>>(V, vstride, nv, h, w, n);
+    k_subtract<TV><<<(n + 255) / 256, 256, 0, st>>>(V, vstride, nv, h, w, n); ++g_launches;
     return cudaGetLastError();
 }
 template <typename TX, typename TY>
 cudaError_t scale(const TX *x, TY *y, int n, const double s[4], cudaStream_t st) {
-    k_scale<TX, TY><<<(n + 255) / 256, 256, 0, st>>>(x, y, n, s[0], s[1], s[2], s[3]);
+    k_scale<TX, TY><<<(n + 255) / 256, 256, 0, st>>>(x, y, n, s[0], s[1], s[2], s[3]); ++g_launches;
     return cudaGetLastError();
 }
 template <typename TV>
 cudaError_t combine(const TV *V, size_t vstride, int nv, const double *y, double *x, int n, cudaStream_t st) {
-    k_combine<TV><<<(n + 255) / 256, 256, 0, st>>>(V, vstride, nv, y, x, n);
+    k_combine<TV><<<(n + 255) / 256, 256, 0, st>>>(V, vstride, nv, y, x, n); ++g_launches;
     return cudaGetLastError();
 }
 template cudaError_t dots<float>(const float *, size_t, int, const float *, int, double *, cudaStream_t);

@@ -5,6 +5,8 @@
 #include <utility>
 #include <vector>
 
+#include "vie_internal.h"
+
 namespace vie {
 
 template <typename TZ, typename TX, typename TA>

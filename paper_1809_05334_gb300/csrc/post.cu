@@ -149,14 +149,14 @@ cudaError_t launch_post(const DevMesh &m, const DevReq &q, const double *x, cons
                         const double *pol_dev, double *acc, double *J, double *rt, cudaStream_t st) {
     cudaMemsetAsync(acc, 0, sizeof(double) * 2 * n_dom, st);
     cudaMemsetAsync(J, 0, sizeof(double) * 24 * n_orders, st);
-    k_absorb<<<(m.nt + 127) / 128, 128, 0, st>>>(m, q, x, dom, acc, n_dom, norm);
-    k_project<<<(m.nt + 127) / 128, 128, 0, st>>>(m, q, x, orders, n_orders, J);
-    k_rt<<<1, 32, 0, st>>>(orders, n_orders, J, q.k0, a, b, kz00, pol_dev, rt);
+    k_absorb<<<(m.nt + 127) / 128, 128, 0, st>>>(m, q, x, dom, acc, n_dom, norm); ++g_launches;
+    k_project<<<(m.nt + 127) / 128, 128, 0, st>>>(m, q, x, orders, n_orders, J); ++g_launches;
+    k_rt<<<1, 32, 0, st>>>(orders, n_orders, J, q.k0, a, b, kz00, pol_dev, rt); ++g_launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpermute(const double *x, const int32_t *perm, int n, double *out, cudaStream_t st) {
-    k_unpermute<<<(n + 255) / 256, 256, 0, st>>>(x, perm, n, out);
+    k_unpermute<<<(n + 255) / 256, 256, 0, st>>>(x, perm, n, out); ++g_launches;
     return cudaGetLastError();
 }
 

@@ -15,6 +15,10 @@ constexpr double NEAR_FACTOR = 1.5;
 // independently of the rounding of the distance
 constexpr double NEAR_MARGIN = 1e-9;
 
+// kernel launches issued by this host thread (every launch site increments it;
+// a solve reports the difference across its own work)
+extern thread_local int64_t g_launches;
+
 enum Kind : int { KIND_INTERIOR = 0, KIND_HALF = 1, KIND_PERIODIC = 2 };
 
 // One near pair: test element x, source element y, bit k of `mask` set when the

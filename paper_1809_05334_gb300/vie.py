@@ -46,7 +46,7 @@ class Result(ctypes.Structure):
                 ("k_matvec_ms", ctypes.c_double), ("k_matvec_n", ctypes.c_int32), ("n_near_pairs", ctypes.c_int32),
                 ("far_pair_evals", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("k_tc_ms", ctypes.c_double), ("k_tc_bytes", ctypes.c_double), ("k_tc_n", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("n_launches", ctypes.c_int32)]
 
 
 _LIB = None
@@ -166,7 +166,7 @@ class Solver:
                     k_factor_ms=res.k_factor_ms, k_matvec_ms=res.k_matvec_ms, k_matvec_n=res.k_matvec_n,
                     n_near_pairs=res.n_near_pairs, far_pair_evals=res.far_pair_evals,
                     h2d_bytes=res.h2d_bytes, d2h_bytes=res.d2h_bytes, k_tc_ms=res.k_tc_ms,
-                    k_tc_bytes=res.k_tc_bytes, k_tc_n=res.k_tc_n, x=out)
+                    k_tc_bytes=res.k_tc_bytes, k_tc_n=res.k_tc_n, n_launches=res.n_launches, x=out)
 
     def solve_device(self, lam, theta, phi, eps, coeffs_dev_ptr, stream=None):
         """Solve writing the unknowns to a caller-owned device buffer [N][2] complex128."""
