@@ -41,6 +41,19 @@ WORKLOADS = {
 }
 
 
+SWEEP_WORKLOAD = ("batched sweep on the plasmonic geometry at sweep density (~8.9k unknowns): lambda 400-800 nm "
+                  "in 5 nm steps (81 values, dispersive Drude/Cauchy eps) with theta cycling 0-80 deg in 10 deg "
+                  "steps, TE+TM per solve")
+
+
+def sweep_requests(k):
+    """The first k (lambda, theta) points of the sweep: lambda_i = 400 + 5 (i mod 81) nm,
+    theta_i = 10 deg x (i mod 9), phi = 0."""
+    lams = [400.0 + 5.0 * (i % 81) for i in range(k)]
+    ths = [np.deg2rad(10.0 * (i % 9)) for i in range(k)]
+    return lams, ths
+
+
 def _cell(name):
     import cellgen
     return getattr(cellgen, WORKLOADS[name][0])()
@@ -137,13 +150,17 @@ def run_ours(args):
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     results = []
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        step_ev[0].record(stream)
+        for k in range(args.steps):
             results.append(solver.solve(LAM, THETA, PHI, eps, stream=sp))
+            step_ev[k + 1].record(stream)
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
+    lat = [step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps)]
     t = torch.tensor([ms], device=dev, dtype=torch.float64)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -189,6 +206,8 @@ def run_ours(args):
         "kernels_ms": {"far_tt": last["k_far_tt_ms"], "fill": last["k_fill_ms"], "factor": last["k_factor_ms"],
                        "tc_update_total": last["k_tc_ms"], "tc_update_n": last["k_tc_n"],
                        "matvec_total": last["k_matvec_ms"], "matvec_n": last["k_matvec_n"]},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "note": "per solve, one solve in flight"},
         "iterations": last["iterations"], "rel_residual": [float(v) for v in last["rel_residual"]],
         "absorbed_active": [float(v) for v in last["A"][:, cell.active_domain]],
         "e2e": {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -243,6 +262,58 @@ def roofline(last, n, peaks, fp32):
     return dict(dom), out
 
 
+def run_sweep(args):
+    """Batched wavelength x angle sweep through vie_solve_batch (several solve
+    slots in flight); a step is one (lambda, theta) solve, TE and TM together."""
+    import torch
+
+    from paper_1809_05334_gb300 import vie
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = vie.VIE_FP32 if args.precision == "fp32" else vie.VIE_FP64
+    cell = _cell("sweep_cell")
+    solver = vie.Solver(device=local, precision=prec, tol=1e-6)
+    n = solver.set_mesh(cell)
+    steps = args.steps
+    lams, ths = sweep_requests(max(steps, args.warmup))
+    eps = [cell.eps(l) for l in lams]
+    phs = [0.0] * len(lams)
+    w = args.warmup
+    solver.solve_batch(lams[:w], ths[:w], phs[:w], eps[:w], max_slots=args.slots)
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        out, used = solver.solve_batch(lams[:steps], ths[:steps], phs[:steps], eps[:steps], max_slots=args.slots)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    lat = [o["t_fill_ms"] + o["t_factor_ms"] + o["t_solve_ms"] + o["t_post_ms"] for o in out]
+    bad = [o["status"] for o in out if o["status"] != 0]
+    res = {
+        "metric": METRIC, "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": w, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64+f64" if prec == vie.VIE_FP32 else "c128", "data": "synthetic",
+        "config": {"workload": SWEEP_WORKLOAD, "n_unknowns": n, "n_tets": cell.n_tets, "precision": args.precision,
+                   "slots": used, "parallelism": "single",
+                   "l2": "inputs larger than L2 (each slot's Z is %.2f GB)"
+                         % (n * n * (8 if prec == vie.VIE_FP32 else 16) / 1e9)},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "note": "per solve, wall time inside the batch with %d slots in flight" % used},
+        "iterations_mean": float(np.mean([sum(o["iterations"]) / 2 for o in out])),
+        "max_rel_residual": float(max(np.max(o["rel_residual"]) for o in out)),
+        "non_ok_status": bad,
+        "absorbed_active_first": [float(v) for v in out[0]["A"][:, cell.active_domain]],
+        "gpu_launches": int(sum(o["n_launches"] for o in out)),
+        "clocks": clk.summary(),
+    }
+    solver.close()
+    print(json.dumps(res))
+
+
 def cpu_baseline(args):
     """The FP64 oracle on a reduced-density sample of the same cell, scaled to the full workload."""
     import cellgen
@@ -291,15 +362,23 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed solves (default 5; 81 with --sweep)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="plasmonic", choices=sorted(WORKLOADS))
+    ap.add_argument("--sweep", action="store_true",
+                    help="batched wavelength x angle sweep on the sweep-density cell (vie_solve_batch)")
+    ap.add_argument("--slots", type=int, default=3, help="solve slots in flight for --sweep")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 81 if args.sweep else 5
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -142,6 +142,23 @@ int32_t vie_num_unknowns(const vie_ctx *ctx);
    returns after the work on it has finished. */
 int vie_solve(vie_ctx *ctx, const vie_request *req, vie_result *res, void *stream);
 
+/* A batch of independent solves on the current mesh (a wavelength x angle
+   sweep): reqs[n] in, res[n] out (caller-owned; res[i] is what vie_solve
+   would return for reqs[i], status included).  Up to max_slots solves run at
+   once, each in its own solve slot: a host thread, a CUDA stream and its own
+   device copy of Z, the block inverses of Eq. (6) and the Krylov state, all
+   reading the one device copy of the mesh.  One request's fill overlaps the
+   block inversion and GMRES of others.  Slots are opened while their device
+   footprint (estimated from reqs[0]) fits in free HBM less 5% and 1 GB; the
+   context keeps them, with their buffers, for later batches until
+   vie_destroy.  *slots_used (may be NULL)
+   receives the number of slots that ran.  The caller's stream is synchronised
+   before the first solve; the call returns when all solves have finished.
+   Returns VIE_OK, the first negative status of a request, or else the first
+   positive one. */
+int vie_solve_batch(vie_ctx *ctx, const vie_request *reqs, vie_result *res, int32_t n,
+                    int32_t max_slots, int32_t *slots_used, void *stream);
+
 /* Parity entry points: the FP64 impedance matrix Z [N][N] (row-major, complex)
    and right-hand side b [N][2] of Eq. (2) in canonical unknown order, copied
    to host buffers owned by the caller.  They run the same fill kernels as

@@ -14,7 +14,11 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <new>
 #include <tuple>
 #include <type_traits>
@@ -66,18 +70,24 @@ cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t st) {
 
 }  // namespace
 
+// One mesh on the device: built by vie_set_mesh, read-only afterwards, shared
+// by the context and its solve slots (concurrent solves read it together).
+struct MeshState {
+    bool have_mesh = false;
+    vie::Topology topo;
+    DevBuf tv, cen, vol, q5, far32, far64, fv, f5, farea, ffar32, ffar64, hf, n32, n64, fn32, fn64, fcen;
+    DevBuf mk[4], pr[4], to[4], tdom, tpart;
+    int npr[4] = {0, 0, 0, 0}, nto[4] = {0, 0, 0, 0};
+};
+
 struct vie_ctx {
     int device = 0;
     vie_options opt{};
     std::string err;
-    bool have_mesh = false;
-    vie::Topology topo;
-    // mesh (device)
-    DevBuf tv, cen, vol, q5, far32, far64, fv, f5, farea, ffar32, ffar64, hf, n32, n64, fn32, fn64, fcen;
-    DevBuf mk[4], pr[4], to[4], tdom, tpart, thalf;
-    int npr[4] = {0, 0, 0, 0}, nto[4] = {0, 0, 0, 0};
+    std::shared_ptr<MeshState> mesh = std::make_shared<MeshState>();
     // request (device)
     DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab, ew;
+    DevBuf thalf;   // per-request scratch of the touching-pair kernels
     double z_extent = 0;
     // solve buffers
     DevBuf Z, b, x, r, u, w, V, h, y, Minv, status, acc, J, rt, cout;
@@ -86,8 +96,14 @@ struct vie_ctx {
     // CUDA events for options.timing
     std::vector<cudaEvent_t> events;
     size_t ev_used = 0;
+    // solve slots of vie_solve_batch: contexts sharing this mesh, each with its
+    // own request and solve buffers and its own stream
+    std::vector<std::unique_ptr<vie_ctx>> slots;
+    cudaStream_t own_stream = nullptr;
     ~vie_ctx() {
+        slots.clear();
         for (auto e : events) cudaEventDestroy(e);
+        if (own_stream) cudaStreamDestroy(own_stream);
     }
     cudaEvent_t event() {   // next event of the pool (nullptr when timing is off)
         if (!opt.timing) return nullptr;
@@ -149,7 +165,7 @@ struct HostReq {
 };
 
 int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
-    const vie::Topology &T = ctx->topo;
+    const vie::Topology &T = ctx->mesh->topo;
     if (!(req->lambda_nm > 0) || !std::isfinite(req->lambda_nm)) return fail(ctx, VIE_EINVAL, "lambda must be > 0");
     if (!(std::fabs(req->theta) < M_PI / 2)) return fail(ctx, VIE_EINVAL, "|theta| must be < pi/2");
     H.k0 = 2.0 * M_PI / req->lambda_nm;
@@ -280,7 +296,7 @@ int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
 
 // upload the per-request arrays and build the device views
 int upload_request(vie_ctx *ctx, const HostReq &H, vie::DevReq &q, cudaStream_t st) {
-    const vie::Topology &T = ctx->topo;
+    const vie::Topology &T = ctx->mesh->topo;
     std::vector<int32_t> row(4 * (size_t)T.nt);
     std::vector<double> coef(4 * (size_t)T.nt), wt(8 * (size_t)T.nt), kap(2 * (size_t)T.nt), ie(2 * (size_t)T.nt);
     for (int t = 0; t < T.nt; ++t) {
@@ -336,7 +352,7 @@ int upload_request(vie_ctx *ctx, const HostReq &H, vie::DevReq &q, cudaStream_t 
     q.ef = vie::make_ewald_f32(H.ew);
     q.k0 = H.k0; q.kx = H.kx; q.ky = H.ky;
     for (int k = 0; k < 9; ++k) {
-        const double phs = H.kx * (k / 3 - 1) * ctx->topo.a + H.ky * (k % 3 - 1) * ctx->topo.b;
+        const double phs = H.kx * (k / 3 - 1) * ctx->mesh->topo.a + H.ky * (k % 3 - 1) * ctx->mesh->topo.b;
         q.img_ph[2 * k] = std::cos(phs) / (4.0 * M_PI);
         q.img_ph[2 * k + 1] = std::sin(phs) / (4.0 * M_PI);
     }
@@ -353,25 +369,25 @@ int upload_request(vie_ctx *ctx, const HostReq &H, vie::DevReq &q, cudaStream_t 
 }
 
 vie::DevMesh dev_mesh(vie_ctx *ctx) {
-    const vie::Topology &T = ctx->topo;
+    const vie::Topology &T = ctx->mesh->topo;
     vie::DevMesh m{};
     m.nt = T.nt; m.N = T.N; m.nf = (int)T.cf.size(); m.nh = (int)T.hf.size();
     m.a = T.a; m.b = T.b;
-    m.tv = ctx->tv.as<double>(); m.cen = ctx->cen.as<double>(); m.vol = ctx->vol.as<double>();
-    m.q5 = ctx->q5.as<double>(); m.far32 = ctx->far32.as<float>(); m.far64 = ctx->far64.as<double>();
-    m.fv = ctx->fv.as<double>(); m.f5 = ctx->f5.as<double>(); m.farea = ctx->farea.as<double>();
-    m.ffar32 = ctx->ffar32.as<float>(); m.ffar64 = ctx->ffar64.as<double>(); m.hf = ctx->hf.as<int32_t>();
-    m.n32 = ctx->n32.as<float>(); m.n64 = ctx->n64.as<double>();
-    m.fn32 = ctx->fn32.as<float>(); m.fn64 = ctx->fn64.as<double>(); m.fcen = ctx->fcen.as<double>();
-    m.mk_tt = ctx->mk[0].as<uint16_t>(); m.mk_tf = ctx->mk[1].as<uint16_t>();
-    m.mk_ft = ctx->mk[2].as<uint16_t>(); m.mk_ff = ctx->mk[3].as<uint16_t>();
-    m.touch_partner = ctx->tpart.as<int32_t>();
+    m.tv = ctx->mesh->tv.as<double>(); m.cen = ctx->mesh->cen.as<double>(); m.vol = ctx->mesh->vol.as<double>();
+    m.q5 = ctx->mesh->q5.as<double>(); m.far32 = ctx->mesh->far32.as<float>(); m.far64 = ctx->mesh->far64.as<double>();
+    m.fv = ctx->mesh->fv.as<double>(); m.f5 = ctx->mesh->f5.as<double>(); m.farea = ctx->mesh->farea.as<double>();
+    m.ffar32 = ctx->mesh->ffar32.as<float>(); m.ffar64 = ctx->mesh->ffar64.as<double>(); m.hf = ctx->mesh->hf.as<int32_t>();
+    m.n32 = ctx->mesh->n32.as<float>(); m.n64 = ctx->mesh->n64.as<double>();
+    m.fn32 = ctx->mesh->fn32.as<float>(); m.fn64 = ctx->mesh->fn64.as<double>(); m.fcen = ctx->mesh->fcen.as<double>();
+    m.mk_tt = ctx->mesh->mk[0].as<uint16_t>(); m.mk_tf = ctx->mesh->mk[1].as<uint16_t>();
+    m.mk_ft = ctx->mesh->mk[2].as<uint16_t>(); m.mk_ff = ctx->mesh->mk[3].as<uint16_t>();
+    m.touch_partner = ctx->mesh->tpart.as<int32_t>();
     m.touch_half = ctx->thalf.as<double>();
     for (int i = 0; i < 4; ++i) {
-        m.pr[i] = ctx->pr[i].as<vie::NearEntry>();
-        m.to[i] = ctx->to[i].as<vie::NearEntry>();
-        m.npr[i] = ctx->npr[i];
-        m.nto[i] = ctx->nto[i];
+        m.pr[i] = ctx->mesh->pr[i].as<vie::NearEntry>();
+        m.to[i] = ctx->mesh->to[i].as<vie::NearEntry>();
+        m.npr[i] = ctx->mesh->npr[i];
+        m.nto[i] = ctx->mesh->nto[i];
     }
     return m;
 }
@@ -385,12 +401,15 @@ struct Timing {
 template <typename TZ>
 int fill(vie_ctx *ctx, const vie::DevMesh &m, const vie::DevReq &q, bool with_rhs, cudaStream_t st,
          Timing *tm = nullptr) {
-    const size_t N = (size_t)ctx->topo.N;
+    const size_t N = (size_t)ctx->mesh->topo.N;
     ctx->ld = (N + 3) / 4 * 4;
     CK(ctx->Z.ensure(sizeof(TZ) * 2 * ctx->ld * N));
     if (with_rhs) CK(ctx->b.ensure(sizeof(double) * 4 * N));
+    CK(ctx->thalf.ensure(sizeof(double) * 8 * std::max(ctx->mesh->nto[0], 1)));
+    vie::DevMesh mm = m;
+    mm.touch_half = ctx->thalf.as<double>();
     if (tm && tm->fill0) CK(cudaEventRecord(tm->fill0, st));
-    CK(vie::launch_fill<TZ>(m, q, ctx->Z.as<TZ>(), ctx->ld, with_rhs ? ctx->b.as<double>() : nullptr, st,
+    CK(vie::launch_fill<TZ>(mm, q, ctx->Z.as<TZ>(), ctx->ld, with_rhs ? ctx->b.as<double>() : nullptr, st,
                             tm ? tm->far0 : nullptr, tm ? tm->far1 : nullptr));
     if (tm && tm->fill1) CK(cudaEventRecord(tm->fill1, st));
     return VIE_OK;
@@ -411,7 +430,7 @@ int precond_apply(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &mof
 template <typename TZ, typename TV>
 int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const std::vector<size_t> &mld,
           vie_result *res, cudaStream_t st, Timing &tm) {
-    const int N = ctx->topo.N;
+    const int N = ctx->mesh->topo.N;
     const int m = std::max(2, ctx->opt.restart);
     const bool pre = ctx->opt.use_precond != 0;
     const double tol = ctx->opt.tol;
@@ -627,26 +646,26 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     if (stat < 0) return stat;
     auto t3 = clk::now();
     // post-processing
-    const int nd = ctx->topo.n_dom;
+    const int nd = ctx->mesh->topo.n_dom;
     const int n_orders = (int)H.orders.size() / 4;
     CK(ctx->acc.ensure(sizeof(double) * 2 * nd));
     CK(ctx->J.ensure(sizeof(double) * 24 * std::max(n_orders, 1)));
     CK(ctx->rt.ensure(sizeof(double) * 4));
-    const double norm = H.k0 / (ctx->topo.a * ctx->topo.b * std::cos(H.theta));
-    CK(vie::launch_post(m, q, ctx->x.as<double>(), ctx->tdom.as<int32_t>(), nd, norm, ctx->orders.as<double>(),
-                        n_orders, ctx->topo.a, ctx->topo.b, H.k0 * std::cos(H.theta), ctx->pol.as<double>(),
+    const double norm = H.k0 / (ctx->mesh->topo.a * ctx->mesh->topo.b * std::cos(H.theta));
+    CK(vie::launch_post(m, q, ctx->x.as<double>(), ctx->mesh->tdom.as<int32_t>(), nd, norm, ctx->orders.as<double>(),
+                        n_orders, ctx->mesh->topo.a, ctx->mesh->topo.b, H.k0 * std::cos(H.theta), ctx->pol.as<double>(),
                         ctx->acc.as<double>(), ctx->J.as<double>(), ctx->rt.as<double>(), st));
     std::vector<double> acc(2 * nd), rt(4);
     CK(cudaMemcpyAsync(acc.data(), ctx->acc.p, sizeof(double) * 2 * nd, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(rt.data(), ctx->rt.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
     ctx->d2h += sizeof(double) * (2 * nd + 4);
     if (req->coeffs_out) {
-        const size_t bytes = sizeof(double) * 4 * (size_t)ctx->topo.N;
+        const size_t bytes = sizeof(double) * 4 * (size_t)ctx->mesh->topo.N;
         if (req->coeffs_on_device) {
-            CK(vie::launch_unpermute(ctx->x.as<double>(), ctx->perm.as<int32_t>(), ctx->topo.N, req->coeffs_out, st));
+            CK(vie::launch_unpermute(ctx->x.as<double>(), ctx->perm.as<int32_t>(), ctx->mesh->topo.N, req->coeffs_out, st));
         } else {
             CK(ctx->cout.ensure(bytes));
-            CK(vie::launch_unpermute(ctx->x.as<double>(), ctx->perm.as<int32_t>(), ctx->topo.N, ctx->cout.as<double>(), st));
+            CK(vie::launch_unpermute(ctx->x.as<double>(), ctx->perm.as<int32_t>(), ctx->mesh->topo.N, ctx->cout.as<double>(), st));
             CK(cudaMemcpyAsync(req->coeffs_out, ctx->cout.p, bytes, cudaMemcpyDeviceToHost, st));
             ctx->d2h += bytes;
         }
@@ -663,11 +682,11 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     res->t_factor_ms = ms(t1, t2);
     res->t_solve_ms = ms(t2, t3);
     res->t_post_ms = ms(t3, t4);
-    res->n_unknowns = ctx->topo.N;
-    res->n_near_pairs = (int32_t)ctx->topo.near_tt.size();
+    res->n_unknowns = ctx->mesh->topo.N;
+    res->n_near_pairs = (int32_t)ctx->mesh->topo.near_tt.size();
     res->h2d_bytes = ctx->h2d;
     res->d2h_bytes = ctx->d2h;
-    res->far_pair_evals = 16 * (int64_t)ctx->topo.nt * ctx->topo.nt;
+    res->far_pair_evals = 16 * (int64_t)ctx->mesh->topo.nt * ctx->mesh->topo.nt;
     res->n_launches = (int32_t)(vie::g_launches - launches0);
     if (ctx->opt.timing) {
         res->k_far_tt_ms = ev_ms(tm.far0, tm.far1);
@@ -688,6 +707,39 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     }
     res->status = stat;
     return stat;
+}
+
+// quadrature weights and Faddeeva coefficients: uploaded once per device, so
+// that creating a context never writes constant memory that running solves read
+cudaError_t upload_device_constants(int device) {
+    static std::mutex mu;
+    static std::vector<char> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((size_t)device < done.size() && done[device]) return cudaSuccess;
+    cudaError_t e = vie::upload_constants();
+    if (e == cudaSuccess) e = vie::upload_post_constants();
+    if (e != cudaSuccess) return e;
+    if (done.size() <= (size_t)device) done.resize(device + 1, 0);
+    done[device] = 1;
+    return cudaSuccess;
+}
+
+// Device bytes one solve slot holds for request `req` on the current mesh:
+// Z, the block inverses, the Krylov basis and vectors, the touching scratch.
+int slot_footprint(vie_ctx *ctx, const vie_request *req, size_t *bytes) {
+    HostReq H;
+    if (int e = prepare(ctx, req, H)) return e;
+    const size_t N = (size_t)ctx->mesh->topo.N, ld = (N + 3) / 4 * 4;
+    const bool fp64 = ctx->opt.precision == VIE_FP64;
+    const size_t sz = fp64 ? 8 : 4;
+    size_t minv = 0;
+    for (int n : H.blk_n) minv += 8 * (((size_t)n + 3) / 4 * 4) * (size_t)n;
+    const size_t m = (size_t)std::max(2, ctx->opt.restart);
+    const size_t vs = 4 * N;
+    size_t b = 2 * sz * ld * N + minv + sz * vs * (m + 3) + 8 * vs * 4 + 64 * (size_t)ctx->mesh->nto[0];
+    b += (size_t)ctx->mesh->topo.nt * 4 * 64 + (16u << 20);   // request arrays, tables, small buffers
+    *bytes = b;
+    return VIE_OK;
 }
 
 void default_opts(vie_options *o) {
@@ -720,7 +772,7 @@ int vie_create(vie_ctx **out, int device, const vie_options *opt) {
     default_opts(&ctx->opt);
     if (opt) ctx->opt = *opt;
     if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return VIE_ECUDA; }
-    if (vie::upload_constants() != cudaSuccess || vie::upload_post_constants() != cudaSuccess) {
+    if (upload_device_constants(device) != cudaSuccess) {
         delete ctx;
         return VIE_ECUDA;
     }
@@ -743,11 +795,12 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
     if (n_domains < 1 || n_domains > VIE_MAX_DOMAINS) return fail(ctx, VIE_EINVAL, "n_domains out of range");
     if (active_domain < 0 || active_domain >= n_domains) return fail(ctx, VIE_EINVAL, "active_domain out of range");
     cudaSetDevice(ctx->device);
-    ctx->have_mesh = false;
+    // a new mesh object: solve slots still holding the previous one keep it alive
+    ctx->mesh = std::make_shared<MeshState>();
     std::string e = vie::build_topology(verts, n_verts, tets, n_tets, tet_domain, n_domains, period_a, period_b,
-                                        active_domain, ctx->topo);
+                                        active_domain, ctx->mesh->topo);
     if (!e.empty()) return fail(ctx, e.find("range") != std::string::npos ? VIE_EINVAL : VIE_BAD_MESH, e);
-    const vie::Topology &T = ctx->topo;
+    const vie::Topology &T = ctx->mesh->topo;
     cudaStream_t st = 0;
     {
         double zlo = 1e300, zhi = -1e300;
@@ -840,58 +893,57 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
     if (hf.empty()) hf.push_back(0);
     std::vector<double> fv = T.fv;
     if (fv.empty()) fv.assign(9, 0.0);
-    CK(upload(ctx->tv, T.tv, st));
-    CK(upload(ctx->cen, T.cen, st));
-    CK(upload(ctx->vol, T.vol, st));
-    CK(upload(ctx->q5, q5, st));
-    CK(upload(ctx->far64, far64, st));
-    CK(upload(ctx->far32, far32, st));
-    CK(upload(ctx->fv, fv, st));
-    CK(upload(ctx->f5, f5, st));
-    CK(upload(ctx->farea, farea, st));
-    CK(upload(ctx->ffar64, ffar64, st));
-    CK(upload(ctx->ffar32, ffar32, st));
-    CK(upload(ctx->hf, hf, st));
-    CK(upload(ctx->n64, n64, st));
-    CK(upload(ctx->n32, n32, st));
-    CK(upload(ctx->fn64, fn64, st));
-    CK(upload(ctx->fn32, fn32, st));
-    CK(upload(ctx->fcen, fcen, st));
-    CK(upload(ctx->tdom, T.dom, st));
+    CK(upload(ctx->mesh->tv, T.tv, st));
+    CK(upload(ctx->mesh->cen, T.cen, st));
+    CK(upload(ctx->mesh->vol, T.vol, st));
+    CK(upload(ctx->mesh->q5, q5, st));
+    CK(upload(ctx->mesh->far64, far64, st));
+    CK(upload(ctx->mesh->far32, far32, st));
+    CK(upload(ctx->mesh->fv, fv, st));
+    CK(upload(ctx->mesh->f5, f5, st));
+    CK(upload(ctx->mesh->farea, farea, st));
+    CK(upload(ctx->mesh->ffar64, ffar64, st));
+    CK(upload(ctx->mesh->ffar32, ffar32, st));
+    CK(upload(ctx->mesh->hf, hf, st));
+    CK(upload(ctx->mesh->n64, n64, st));
+    CK(upload(ctx->mesh->n32, n32, st));
+    CK(upload(ctx->mesh->fn64, fn64, st));
+    CK(upload(ctx->mesh->fn32, fn32, st));
+    CK(upload(ctx->mesh->fcen, fcen, st));
+    CK(upload(ctx->mesh->tdom, T.dom, st));
     const std::vector<vie::NearPair> *lists[4] = {&T.near_tt, &T.near_tf, &T.near_ft, &T.near_ff};
     const size_t dims[4][2] = {{(size_t)T.nt, (size_t)T.nt}, {(size_t)T.nt, (size_t)nf}, {(size_t)nh, (size_t)T.nt},
                                {(size_t)nh, (size_t)nf}};
     for (int i = 0; i < 4; ++i) {
-        CK(upload(ctx->mk[i], masks(*lists[i], dims[i][0], dims[i][1]), st));
+        CK(upload(ctx->mesh->mk[i], masks(*lists[i], dims[i][0], dims[i][1]), st));
         auto p = entries(*lists[i], false), q = entries(*lists[i], true);
-        ctx->npr[i] = (int)p.size();
-        ctx->nto[i] = (int)q.size();
+        ctx->mesh->npr[i] = (int)p.size();
+        ctx->mesh->nto[i] = (int)q.size();
         if (p.empty()) p.push_back({0, 0, 0, 0});
         if (q.empty()) q.push_back({0, 0, 0, 0});
-        CK(upload(ctx->pr[i], p, st));
-        CK(upload(ctx->to[i], q, st));
+        CK(upload(ctx->mesh->pr[i], p, st));
+        CK(upload(ctx->mesh->to[i], q, st));
         if (i == 0) {   // partner (y, x, 8-k) of every touching tetrahedron entry
             std::map<std::tuple<int, int, int>, int> idx;
-            for (int e = 0; e < ctx->nto[0]; ++e) idx[std::make_tuple(q[e].x, q[e].y, q[e].k)] = e;
-            std::vector<int32_t> part(std::max(ctx->nto[0], 1), 0);
-            for (int e = 0; e < ctx->nto[0]; ++e) {
+            for (int e = 0; e < ctx->mesh->nto[0]; ++e) idx[std::make_tuple(q[e].x, q[e].y, q[e].k)] = e;
+            std::vector<int32_t> part(std::max(ctx->mesh->nto[0], 1), 0);
+            for (int e = 0; e < ctx->mesh->nto[0]; ++e) {
                 auto it = idx.find(std::make_tuple(q[e].y, q[e].x, 8 - q[e].k));
                 if (it == idx.end()) return fail(ctx, VIE_BAD_MESH, "near-pair lists are not symmetric");
                 part[e] = it->second;
             }
-            CK(upload(ctx->tpart, part, st));
-            CK(ctx->thalf.ensure(sizeof(double) * 8 * std::max(ctx->nto[0], 1)));
+            CK(upload(ctx->mesh->tpart, part, st));
         }
     }
-    ctx->have_mesh = true;
+    ctx->mesh->have_mesh = true;
     return VIE_OK;
 }
 
-int32_t vie_num_unknowns(const vie_ctx *ctx) { return (ctx && ctx->have_mesh) ? ctx->topo.N : 0; }
+int32_t vie_num_unknowns(const vie_ctx *ctx) { return (ctx && ctx->mesh->have_mesh) ? ctx->mesh->topo.N : 0; }
 
 int vie_solve(vie_ctx *ctx, const vie_request *req, vie_result *res, void *stream) {
     if (!ctx || !req || !res) return VIE_EINVAL;
-    if (!ctx->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
+    if (!ctx->mesh->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
     std::memset(res, 0, sizeof(*res));
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -901,9 +953,69 @@ int vie_solve(vie_ctx *ctx, const vie_request *req, vie_result *res, void *strea
     return r;
 }
 
+int vie_solve_batch(vie_ctx *ctx, const vie_request *reqs, vie_result *res, int32_t n, int32_t max_slots,
+                    int32_t *slots_used, void *stream) {
+    if (slots_used) *slots_used = 0;
+    if (!ctx || (n > 0 && (!reqs || !res)) || n < 0 || max_slots < 1) return VIE_EINVAL;
+    if (!ctx->mesh->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
+    if (n == 0) return VIE_OK;
+    std::memset(res, 0, sizeof(vie_result) * (size_t)n);
+    cudaSetDevice(ctx->device);
+    // work the caller queued on its stream (for example device coefficient
+    // buffers being prepared) completes before any slot starts
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    // admission by HBM footprint: a slot is opened only while its buffers fit
+    // in the free device memory (less 5% and 1 GB of headroom)
+    size_t per = 0;
+    if (int e = slot_footprint(ctx, &reqs[0], &per)) return e;
+    int want = std::min<int>(max_slots, n);
+    std::vector<vie_ctx *> use;
+    use.push_back(ctx);
+    for (int k = 1; k < want; ++k) {
+        if ((size_t)k > ctx->slots.size()) {
+            size_t free_b = 0, total_b = 0;
+            CK(cudaMemGetInfo(&free_b, &total_b));
+            const size_t headroom = total_b / 20 + (1ull << 30);
+            if (free_b < headroom || free_b - headroom < per) break;
+            std::unique_ptr<vie_ctx> c(new (std::nothrow) vie_ctx());
+            if (!c) break;
+            c->device = ctx->device;
+            CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+            ctx->slots.push_back(std::move(c));
+        }
+        vie_ctx *c = ctx->slots[k - 1].get();
+        c->opt = ctx->opt;
+        c->mesh = ctx->mesh;
+        c->z_extent = ctx->z_extent;
+        use.push_back(c);
+    }
+    if (!ctx->own_stream) CK(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+    if (slots_used) *slots_used = (int32_t)use.size();
+    std::atomic<int> next{0};
+    auto worker = [&](vie_ctx *c) {
+        cudaSetDevice(c->device);
+        for (int i = next++; i < n; i = next++) vie_solve(c, &reqs[i], &res[i], c->own_stream);
+    };
+    std::vector<std::thread> th;
+    for (size_t k = 1; k < use.size(); ++k) th.emplace_back(worker, use[k]);
+    worker(ctx);
+    for (auto &t : th) t.join();
+    int worst = VIE_OK;
+    for (int i = 0; i < n; ++i)
+        if (res[i].status < 0) { worst = res[i].status; break; }
+    if (worst < 0) {
+        for (vie_ctx *c : use)
+            if (!c->err.empty()) { ctx->err = c->err; break; }
+        return worst;
+    }
+    for (int i = 0; i < n; ++i)
+        if (res[i].status > 0) return res[i].status;
+    return VIE_OK;
+}
+
 int vie_fill_matrix(vie_ctx *ctx, const vie_request *req, double *Z_host, double *b_host, void *stream) {
     if (!ctx || !req || !Z_host) return VIE_EINVAL;
-    if (!ctx->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
+    if (!ctx->mesh->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     vie_options saved = ctx->opt;
@@ -916,7 +1028,7 @@ int vie_fill_matrix(vie_ctx *ctx, const vie_request *req, double *Z_host, double
     vie::DevReq q{};
     if ((e = upload_request(ctx, H, q, st))) return e;
     if ((e = fill<double>(ctx, m, q, true, st))) return e;
-    const int N = ctx->topo.N;
+    const int N = ctx->mesh->topo.N;
     std::vector<double> Zp((size_t)2 * ctx->ld * N), bp(4 * (size_t)N);
     CK(cudaMemcpyAsync(Zp.data(), ctx->Z.p, sizeof(double) * Zp.size(), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(bp.data(), ctx->b.p, sizeof(double) * bp.size(), cudaMemcpyDeviceToHost, st));
@@ -936,7 +1048,7 @@ int vie_fill_matrix(vie_ctx *ctx, const vie_request *req, double *Z_host, double
 
 int vie_fill_matrix_prec(vie_ctx *ctx, const vie_request *req, double *Z_host, void *stream) {
     if (!ctx || !req || !Z_host) return VIE_EINVAL;
-    if (!ctx->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
+    if (!ctx->mesh->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
     if (ctx->opt.precision == VIE_FP64) return vie_fill_matrix(ctx, req, Z_host, nullptr, stream);
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -947,7 +1059,7 @@ int vie_fill_matrix_prec(vie_ctx *ctx, const vie_request *req, double *Z_host, v
     vie::DevReq q{};
     if ((e = upload_request(ctx, H, q, st))) return e;
     if ((e = fill<float>(ctx, m, q, false, st))) return e;
-    const int N = ctx->topo.N;
+    const int N = ctx->mesh->topo.N;
     std::vector<float> Zp((size_t)2 * ctx->ld * N);
     CK(cudaMemcpyAsync(Zp.data(), ctx->Z.p, sizeof(float) * Zp.size(), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -978,7 +1090,7 @@ int vie_erfcx(vie_ctx *ctx, const double *u, double *out, int32_t n, int32_t pre
 
 int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out, int32_t n, int32_t precision) {
     if (!ctx || !req || !d || !out || n < 0) return VIE_EINVAL;
-    if (!ctx->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set (the period comes from the mesh)");
+    if (!ctx->mesh->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set (the period comes from the mesh)");
     if (n == 0) return VIE_OK;
     cudaSetDevice(ctx->device);
     vie_options saved = ctx->opt;

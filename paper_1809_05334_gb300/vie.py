@@ -21,7 +21,7 @@ STATUS = {0: "VIE_OK", 1: "VIE_NOT_CONVERGED", -1: "VIE_EINVAL", -2: "VIE_ENOMEM
 # every symbol include/vie.h declares
 EXPORTS = ["vie_default_options", "vie_create", "vie_set_options", "vie_set_mesh", "vie_num_unknowns",
            "vie_solve", "vie_fill_matrix", "vie_fill_matrix_prec", "vie_erfcx", "vie_green",
-           "vie_status_str", "vie_last_error", "vie_destroy", "vie_green_noalloc"]
+           "vie_status_str", "vie_last_error", "vie_destroy", "vie_green_noalloc", "vie_solve_batch"]
 
 
 class Options(ctypes.Structure):
@@ -80,6 +80,8 @@ def load():
     lib.vie_destroy.argtypes = [P]
     lib.vie_destroy.restype = None
     lib.vie_green_noalloc.argtypes = [D, D, D, D, D, D, P, P, I, I, P]
+    lib.vie_solve_batch.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(Result), I, I,
+                                    ctypes.POINTER(I), P]
     _LIB = lib
     return lib
 
@@ -156,6 +158,9 @@ class Solver:
         rc = self.lib.vie_solve(self.ctx, ctypes.byref(req), ctypes.byref(res),
                                 ctypes.c_void_p(stream) if stream else None)
         self._check(rc, allow_positive=True)
+        return self._result(res, rc, out)
+
+    def _result(self, res, rc, out=None):
         nd = self.n_domains
         return dict(status=rc, n=res.n_unknowns, iterations=list(res.iterations), refinements=res.refinements,
                     rel_residual=np.array(res.rel_residual[:]),
@@ -167,6 +172,29 @@ class Solver:
                     n_near_pairs=res.n_near_pairs, far_pair_evals=res.far_pair_evals,
                     h2d_bytes=res.h2d_bytes, d2h_bytes=res.d2h_bytes, k_tc_ms=res.k_tc_ms,
                     k_tc_bytes=res.k_tc_bytes, k_tc_n=res.k_tc_n, n_launches=res.n_launches, x=out)
+
+    def solve_batch(self, lams, thetas, phis, eps_list, max_slots=2, coeffs=False, stream=None):
+        """Independent solves of one mesh (vie_solve_batch): lams/thetas/phis/eps_list
+        have one entry per request; returns (list of result dicts, slots used).
+        A request whose status is negative gets its dict with that status; the
+        call raises only for errors of the batch itself."""
+        n = len(lams)
+        reqs = (Request * n)()
+        outs = []
+        for i in range(n):
+            reqs[i] = self.request(lams[i], thetas[i], phis[i], eps_list[i])
+            out = None
+            if coeffs:
+                out = np.zeros((self.num_unknowns(), 2), dtype=np.complex128)
+                reqs[i].coeffs_out = out.ctypes.data
+            outs.append(out)
+        res = (Result * n)()
+        used = ctypes.c_int32(0)
+        rc = self.lib.vie_solve_batch(self.ctx, reqs, res, n, int(max_slots), ctypes.byref(used),
+                                      ctypes.c_void_p(stream) if stream else None)
+        if rc < 0 and not any(res[i].status == rc for i in range(n)):
+            self._check(rc)
+        return [self._result(res[i], res[i].status, outs[i]) for i in range(n)], int(used.value)
 
     def solve_device(self, lam, theta, phi, eps, coeffs_dev_ptr, stream=None):
         """Solve writing the unknowns to a caller-owned device buffer [N][2] complex128."""
