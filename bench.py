@@ -314,6 +314,90 @@ def run_sweep(args):
     print(json.dumps(res))
 
 
+SERVE_WORKLOAD = ("serving stream: Poisson arrivals (mean 200 req/s) of solves on seeded random cells (square "
+                  "period 150-400 nm, 0-4 Ag spheres r 10-40 nm, active and buffer layers 30-150 nm, ~2k-40k "
+                  "unknowns), lambda U[400,800] nm, theta U[0,80] deg, TE+TM per solve")
+
+
+def serve_requests(k, rate=200.0, master_seed=4):
+    """The first k requests of the serving stream: (arrival time s, cell, lambda, theta).
+    A lambda within 1e-3/a of a Rayleigh anomaly (|gamma_pq| a < 1e-3) is moved
+    up in 0.01 nm steps."""
+    import cellgen
+    rng = np.random.default_rng([master_seed, 1 << 20])
+    t = np.cumsum(rng.exponential(1.0 / rate, size=k))
+    out = []
+    for i in range(k):
+        cell, _ = cellgen.serving_cell(i, master_seed)
+        r = np.random.default_rng([master_seed, i, 1])
+        lam, th = float(r.uniform(400.0, 800.0)), float(r.uniform(0.0, np.deg2rad(80.0)))
+        a = cell.period_a
+        while True:
+            k0 = 2 * np.pi / lam
+            p = np.arange(-4, 5)
+            kx = k0 * np.sin(th) + 2 * np.pi * p[:, None] / a
+            ky = 2 * np.pi * p[None, :] / a
+            if np.min(np.abs(np.sqrt((kx ** 2 + ky ** 2 - k0 ** 2).astype(complex)))) * a >= 1e-3:
+                break
+            lam += 0.01
+        out.append((float(t[i]), cell, lam, th))
+    return out
+
+
+def run_serve(args):
+    """Serving stream through the solve server (vie_server_*): requests are
+    submitted at their Poisson arrival times; value = requests / (last completion
+    - first arrival); latency from submission to completion, queueing included."""
+    import torch
+
+    from paper_1809_05334_gb300 import vie
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    prec = vie.VIE_FP32 if args.precision == "fp32" else vie.VIE_FP64
+    reqs = serve_requests(args.steps)
+    srv = vie.Server(device=local, n_slots=args.slots, precision=prec, tol=1e-6)
+    import cellgen
+    warm = cellgen.small_cells()["plasmonic_tiny"]
+    for _ in range(args.warmup):
+        t, _ = srv.submit(warm, 500.0, 0.0, 0.0, warm.eps(500.0))
+        srv.poll(t, wait_ms=-1)
+    torch.cuda.synchronize()
+    tickets = []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for at, cell, lam, th in reqs:
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            tk, fp = srv.submit(cell, lam, th, 0.0, cell.eps(lam))
+            tickets.append((tk, fp, cell))
+        out = [srv.poll(tk, wait_ms=-1) for tk, _, _ in tickets]
+        elapsed = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = [o["t_latency_ms"] for o in out]
+    ns = [o["n"] for o in out]
+    res = {
+        "metric": METRIC, "value": len(out) / elapsed, "unit": UNIT, "n_gpus": 1, "steps": len(out),
+        "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / len(out), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if prec == vie.VIE_FP32 else "c128",
+        "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD, "slots": args.slots, "precision": args.precision,
+                   "unknowns_min_median_max": [int(min(ns)), int(np.median(ns)), int(max(ns))],
+                   "parallelism": "single", "l2": "inputs larger than L2 (Z of 26 MB to 13 GB per request)"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "note": "submission to completion, queueing included"},
+        "server": {k: st[k] for k in ("max_running", "peak_reserved_bytes", "budget_bytes", "completed")},
+        "non_ok_status": [o["status"] for o in out if o["status"] != 0],
+        "max_rel_residual": float(max(np.max(o["rel_residual"]) for o in out)),
+        "gpu_launches": int(sum(o["n_launches"] for o in out)),
+        "timing": "host wall clock (several streams and host threads in flight)",
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(res))
+
+
 def cpu_baseline(args):
     """The FP64 oracle on a reduced-density sample of the same cell, scaled to the full workload."""
     import cellgen
@@ -371,14 +455,18 @@ def main():
     ap.add_argument("--workload", default="plasmonic", choices=sorted(WORKLOADS))
     ap.add_argument("--sweep", action="store_true",
                     help="batched wavelength x angle sweep on the sweep-density cell (vie_solve_batch)")
-    ap.add_argument("--slots", type=int, default=3, help="solve slots in flight for --sweep")
+    ap.add_argument("--slots", type=int, default=3, help="solve slots in flight for --sweep / --serve")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving stream of random cells through the solve server (vie_server_*)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 81 if args.sweep else 5
+        args.steps = 81 if args.sweep else (24 if args.serve else 5)
     if args.impl == "reference":
         run_reference(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

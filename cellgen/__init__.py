@@ -300,6 +300,63 @@ def config_sweep_geometry(seed=3):
     return config_plasmonic(seed=seed, h_coarse=40.0, h_fine=12.0, h_z=30.0)
 
 
+def serving_cell(index, master_seed=4):
+    """One seeded random cell of the serving stream: square period U[150, 400] nm,
+    an active layer and a buffer layer of thicknesses U[30, 150] nm, 0-4 Ag
+    spheres of radius U[10, 40] nm (kept inside the active layer and apart
+    laterally), mesh density aimed at a log-uniform 2k-40k SWG unknowns.
+    Returns (cell, target_unknowns)."""
+    rng = np.random.default_rng([master_seed, index])
+    a = float(rng.uniform(150.0, 400.0))
+    t_act = float(rng.uniform(30.0, 150.0))
+    t_buf = float(rng.uniform(30.0, 150.0))
+    n_sph = int(rng.integers(0, 5))
+    target = float(np.exp(rng.uniform(np.log(2000.0), np.log(40000.0))))
+    spheres = []
+    slots = [(0.25, 0.25), (0.75, 0.75), (0.75, 0.25), (0.25, 0.75)]
+    for k in range(n_sph):
+        r = float(rng.uniform(10.0, 40.0))
+        r = min(r, 0.4 * t_act, 0.2 * a)
+        fx, fy = slots[k]
+        spheres.append((fx * a, fy * a, t_buf + 0.5 * t_act, r, "ag"))
+    # ~2.05 unknowns per tetrahedron, 6 tetrahedra per grid cell; the graded
+    # tensor grid is counted before meshing and its coarse spacing scaled to the
+    # target (cells whose spheres alone need more land above it)
+    zb = [0.0, t_buf, t_buf + t_act]
+    h0 = (a * a * (t_act + t_buf) / (target / 2.05 / 6.0)) ** (1.0 / 3.0)
+    hf0 = min(h0, min(sp[3] for sp in spheres) / 1.2) if spheres else None
+
+    r_min = min(sp[3] for sp in spheres) if spheres else None
+
+    def spacing(sc, coarse_spheres=False):
+        # the coarse spacing scales; spheres keep h_fine <= r / 1.2, or <= r
+        # when that alone would exceed the target
+        hc = h0 * sc
+        hf = min(r_min if coarse_spheres else hf0, hc) if spheres else None
+        pad = 0.5 * (hf or hc)
+        fx = [(sp[0] - sp[3] - pad, sp[0] + sp[3] + pad) for sp in spheres]
+        fy = [(sp[1] - sp[3] - pad, sp[1] + sp[3] + pad) for sp in spheres]
+        fz = [(sp[2] - sp[3] - pad, sp[2] + sp[3] + pad) for sp in spheres]
+        nx = len(grid_1d(0.0, a, (), fx, hf, hc)) - 1
+        ny = len(grid_1d(0.0, a, (), fy, hf, hc)) - 1
+        nz = len(grid_1d(0.0, zb[-1], zb[1:-1], fz, hf, hc)) - 1
+        return 6 * nx * ny * nz, hc, hf
+
+    coarse = spacing(20.0)[0] * 2.05 > 1.2 * target
+    lo, hi = 0.1, 20.0
+    for _ in range(40):                      # bisection on the spacing scale (count decreases with it)
+        mid = math.sqrt(lo * hi)
+        if spacing(mid, coarse)[0] * 2.05 > target:
+            lo = mid
+        else:
+            hi = mid
+    _, hc, hf = spacing(hi, coarse)
+    cell = layered_cell(a, a, [(t_buf, "buffer"), (t_act, "active")], spheres=spheres,
+                        h_coarse=hc, h_fine=hf, h_z=hc, jitter=0.1, seed=int(rng.integers(1 << 30)),
+                        name="serving_%d" % index)
+    return cell, target
+
+
 def small_cells():
     """Small cells the oracle finishes in seconds (parity cases)."""
     return {

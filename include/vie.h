@@ -45,6 +45,7 @@ typedef struct vie_ctx vie_ctx;
 typedef enum {
     VIE_OK = 0,
     VIE_NOT_CONVERGED = 1,      /* result returned, residual above tolerance        */
+    VIE_PENDING = 2,            /* vie_server_poll: the request has not finished     */
     VIE_EINVAL = -1,            /* bad argument                                      */
     VIE_ENOMEM = -2,            /* device allocation failed                          */
     VIE_ECUDA = -3,             /* CUDA runtime / launch error                       */
@@ -110,6 +111,9 @@ typedef struct {
     double  k_tc_ms, k_tc_bytes;
     int32_t k_tc_n;
     int32_t n_launches;                  /* CUDA kernels this call launched          */
+    /* solve server only (0 elsewhere): time from vie_server_submit to the start
+       of the solve, and to its end */
+    double  t_queue_ms, t_latency_ms;
 } vie_result;
 
 /* Fill *opt with defaults (FP32 with refinement, preconditioner on, tol 1e-6). */
@@ -205,6 +209,69 @@ int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out
 int vie_green_noalloc(double lambda_nm, double theta, double phi, double period_a, double period_b,
                       double z_extent, const double *d_dev, double *out_dev, int32_t n,
                       int32_t precision, void *stream);
+
+/* ------------------------------------------------------------------------
+   Solve server: continuous batching of independent solves, each with its own
+   mesh (a stream of (geometry, lambda, theta) requests of different sizes).
+   The paper solves one configuration at a time; this is a deployment layer
+   over vie_set_mesh + vie_solve.
+
+   A server owns n_slots solve slots on one device.  Each slot is a host
+   thread with its own context (mesh, Z, block inverses of Eq. (6), Krylov
+   state, all device resident) and its own CUDA stream, so the solves of
+   different slots overlap on the GPU.  A queued request is admitted to a free
+   slot as soon as its device footprint fits in the HBM budget next to what
+   the other slots hold: requests are taken in arrival order, and a later
+   request that fits may pass one that does not (at most 8 times per waiting
+   request, then the queue waits for it).  All server functions are thread
+   safe. */
+
+typedef struct vie_server vie_server;
+
+typedef struct {                 /* one unit-cell mesh, as in vie_set_mesh    */
+    const double  *verts;        /* [n_verts][3] nm                           */
+    int32_t        n_verts;
+    const int32_t *tets;         /* [n_tets][4]                               */
+    int32_t        n_tets;
+    const int32_t *tet_domain;   /* [n_tets]                                  */
+    int32_t        n_domains;
+    int32_t        active_domain;
+    double         period_a, period_b;
+} vie_mesh;
+
+typedef struct {
+    int64_t submitted, completed, rejected;   /* requests                        */
+    int64_t queued, running, max_running;     /* now, and the most at once       */
+    int64_t budget_bytes;                     /* HBM budget of the slots          */
+    int64_t reserved_bytes, peak_reserved_bytes;
+} vie_server_stats;
+
+/* Start a server on `device` with n_slots slots (1..64) and solver options
+   opt (NULL: defaults).  hbm_budget_bytes bounds the device memory the slots
+   may hold together; 0 means the free memory at creation less 5% and 1 GB. */
+int vie_server_create(vie_server **out, int device, const vie_options *opt, int32_t n_slots,
+                      int64_t hbm_budget_bytes);
+
+/* Queue one request: the mesh and the request are copied (except
+   req->coeffs_out, which must stay valid until the request has finished).
+   *ticket receives its id; *footprint_bytes (may be NULL) the device bytes
+   its slot will hold (an upper bound computed from the mesh: Z, block
+   inverses, Krylov basis, near-pair masks).  Returns VIE_OK, VIE_EINVAL, or
+   VIE_ENOMEM when the footprint exceeds the whole budget (not queued). */
+int vie_server_submit(vie_server *s, const vie_mesh *mesh, const vie_request *req, uint64_t *ticket,
+                      int64_t *footprint_bytes);
+
+/* Wait up to wait_ms (0: do not wait, negative: until done) for a request.
+   Returns VIE_OK with *res filled (res->status is the solve's status, the
+   ticket is then forgotten), VIE_PENDING if it has not finished, VIE_EINVAL
+   for an unknown ticket. */
+int vie_server_poll(vie_server *s, uint64_t ticket, vie_result *res, int32_t wait_ms);
+
+/* Counters of the server (a snapshot). */
+int vie_server_get_stats(vie_server *s, vie_server_stats *out);
+
+/* Finish the solves in progress, drop queued requests, free everything. */
+void vie_server_destroy(vie_server *s);
 
 /* Human-readable name of a status code; never NULL. */
 const char *vie_status_str(int status);

@@ -54,6 +54,11 @@ struct DevBuf {
         return e;
     }
     template <typename T> T *as() const { return static_cast<T *>(p); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
 };
 
 thread_local int64_t *g_h2d_counter = nullptr;   // bytes counter of the solve in progress (host thread local use)
@@ -1123,6 +1128,7 @@ const char *vie_status_str(int s) {
     switch (s) {
         case VIE_OK: return "VIE_OK";
         case VIE_NOT_CONVERGED: return "VIE_NOT_CONVERGED";
+        case VIE_PENDING: return "VIE_PENDING";
         case VIE_EINVAL: return "VIE_EINVAL";
         case VIE_ENOMEM: return "VIE_ENOMEM";
         case VIE_ECUDA: return "VIE_ECUDA";
@@ -1142,3 +1148,21 @@ void vie_destroy(vie_ctx *ctx) {
 }
 
 }  // extern "C"
+
+namespace vie {
+// Free the device memory of a context: its mesh (unless a solve slot shares
+// it), the request arrays and the solve buffers (Z, block inverses, Krylov
+// state).  The context stays usable: the next vie_set_mesh and vie_solve
+// allocate again.  Used by the solve server to give memory back.
+void release_device_memory(vie_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    ctx->slots.clear();
+    ctx->mesh = std::make_shared<MeshState>();
+    DevBuf *bufs[] = {&ctx->row, &ctx->coef, &ctx->wt, &ctx->kap, &ctx->ieps, &ctx->frow, &ctx->qs,
+                      &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->ew, &ctx->thalf,
+                      &ctx->Z, &ctx->b, &ctx->x, &ctx->r, &ctx->u, &ctx->w, &ctx->V, &ctx->h, &ctx->y,
+                      &ctx->Minv, &ctx->status, &ctx->acc, &ctx->J, &ctx->rt, &ctx->cout};
+    for (DevBuf *b : bufs) b->release();
+}
+}  // namespace vie

@@ -221,44 +221,99 @@ std::string build_topology(const double *verts, int nv, const int32_t *tets, int
         T.frad.push_back(r);
     }
 
-    // near-pair lists
+    // near-pair lists: for every x and image R_k, the y whose centroid lies
+    // within NEAR_FACTOR (rho_x + rho_y) of c_x + R_k, found through a uniform
+    // bucket grid over the y centroids (cell size NEAR_FACTOR * 2 max rho_y)
     auto near_list = [&](int nx, const double *cx, const double *rx, const double *vx, int kvx,
                          int ny, const double *cy, const double *ry, const double *vy, int kvy,
                          std::vector<NearPair> &out) {
-        double rymax = 0;
-        for (int j = 0; j < ny; ++j) rymax = std::max(rymax, ry[j]);
+        double rymax = 0, lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int j = 0; j < ny; ++j) {
+            rymax = std::max(rymax, ry[j]);
+            for (int q = 0; q < 3; ++q) {
+                lo[q] = std::min(lo[q], cy[3 * j + q]);
+                hi[q] = std::max(hi[q], cy[3 * j + q]);
+            }
+        }
+        const double hcell = std::max(2.0 * NEAR_FACTOR * rymax, 1e-9);
+        int nc[3];
+        for (int q = 0; q < 3; ++q) nc[q] = std::max(1, std::min(512, (int)std::ceil((hi[q] - lo[q]) / hcell) + 1));
+        auto cell_of = [&](double v, int q) {
+            return std::min(nc[q] - 1, std::max(0, (int)std::floor((v - lo[q]) / hcell)));
+        };
+        // counting sort of the y into cells
+        std::vector<int> start((size_t)nc[0] * nc[1] * nc[2] + 1, 0), items(ny);
+        std::vector<int> cid(ny);
+        for (int j = 0; j < ny; ++j) {
+            cid[j] = (cell_of(cy[3 * j], 0) * nc[1] + cell_of(cy[3 * j + 1], 1)) * nc[2] + cell_of(cy[3 * j + 2], 2);
+            start[cid[j] + 1]++;
+        }
+        for (size_t c = 1; c < start.size(); ++c) start[c] += start[c - 1];
+        {
+            std::vector<int> fill(start.begin(), start.end() - 1);
+            for (int j = 0; j < ny; ++j) items[fill[cid[j]]++] = j;
+        }
+        // per-x lists, concatenated in x order (each sorted by y)
+        std::vector<std::vector<NearPair>> per(nx);
         #pragma omp parallel
         {
-            std::vector<NearPair> local;
+            std::vector<uint16_t> mk(ny, 0), tc(ny, 0);
+            std::vector<int> hit;
             #pragma omp for schedule(dynamic, 16)
             for (int i = 0; i < nx; ++i) {
-                for (int j = 0; j < ny; ++j) {
-                    uint16_t mask = 0, touch = 0;
-                    double lim = NEAR_FACTOR * (rx[i] + ry[j]) * (1.0 + NEAR_MARGIN);
-                    for (int k = 0; k < 9; ++k) {
-                        double R[3] = {(k / 3 - 1) * a, (k % 3 - 1) * b, 0.0};
-                        double d[3];
-                        for (int q = 0; q < 3; ++q) d[q] = cx[3 * i + q] - cy[3 * j + q] + R[q];
-                        if (norm3(d) < lim) {
-                            mask |= (uint16_t)(1u << k);
-                            // shared vertex with the image y - R ?
-                            for (int p = 0; p < kvx && !(touch & (1u << k)); ++p)
-                                for (int s = 0; s < kvy; ++s) {
-                                    double e[3];
-                                    for (int q = 0; q < 3; ++q) e[q] = vx[(size_t)kvx * 3 * i + 3 * p + q] - (vy[(size_t)kvy * 3 * j + 3 * s + q] - R[q]);
-                                    if (norm3(e) < tol) { touch |= (uint16_t)(1u << k); break; }
-                                }
-                        }
+                hit.clear();
+                const double reach = NEAR_FACTOR * (rx[i] + rymax) * (1.0 + NEAR_MARGIN);
+                for (int k = 0; k < 9; ++k) {
+                    const double R[3] = {(k / 3 - 1) * a, (k % 3 - 1) * b, 0.0};
+                    const double p[3] = {cx[3 * i] + R[0], cx[3 * i + 1] + R[1], cx[3 * i + 2]};
+                    int c0[3], c1[3];
+                    bool empty = false;
+                    for (int q = 0; q < 3; ++q) {
+                        if (p[q] + reach < lo[q] - hcell || p[q] - reach > hi[q] + hcell) empty = true;
+                        c0[q] = cell_of(p[q] - reach, q);
+                        c1[q] = cell_of(p[q] + reach, q);
                     }
-                    if (mask) local.push_back({i, j, mask, touch});
+                    if (empty) continue;
+                    for (int u = c0[0]; u <= c1[0]; ++u)
+                        for (int v = c0[1]; v <= c1[1]; ++v)
+                            for (int w = c0[2]; w <= c1[2]; ++w) {
+                                const int c = (u * nc[1] + v) * nc[2] + w;
+                                for (int e = start[c]; e < start[c + 1]; ++e) {
+                                    const int j = items[e];
+                                    const double lim = NEAR_FACTOR * (rx[i] + ry[j]) * (1.0 + NEAR_MARGIN);
+                                    double d[3];
+                                    for (int q = 0; q < 3; ++q) d[q] = cx[3 * i + q] - cy[3 * j + q] + R[q];
+                                    if (!(norm3(d) < lim)) continue;
+                                    if (!mk[j]) hit.push_back(j);
+                                    mk[j] |= (uint16_t)(1u << k);
+                                    // shared vertex with the image y - R ?
+                                    bool t = false;
+                                    for (int pp = 0; pp < kvx && !t; ++pp)
+                                        for (int s2 = 0; s2 < kvy; ++s2) {
+                                            double ev[3];
+                                            for (int q = 0; q < 3; ++q)
+                                                ev[q] = vx[(size_t)kvx * 3 * i + 3 * pp + q] -
+                                                        (vy[(size_t)kvy * 3 * j + 3 * s2 + q] - R[q]);
+                                            if (norm3(ev) < tol) { t = true; break; }
+                                        }
+                                    if (t) tc[j] |= (uint16_t)(1u << k);
+                                }
+                            }
+                }
+                std::sort(hit.begin(), hit.end());
+                per[i].reserve(hit.size());
+                for (int j : hit) {
+                    per[i].push_back({i, j, mk[j], tc[j]});
+                    mk[j] = 0;
+                    tc[j] = 0;
                 }
             }
-            #pragma omp critical
-            out.insert(out.end(), local.begin(), local.end());
         }
-        std::sort(out.begin(), out.end(), [](const NearPair &p, const NearPair &q) {
-            return std::tie(p.x, p.y) < std::tie(q.x, q.y);
-        });
+        size_t tot = 0;
+        for (auto &v : per) tot += v.size();
+        out.clear();
+        out.reserve(tot);
+        for (auto &v : per) out.insert(out.end(), v.begin(), v.end());
     };
     int nf = (int)T.cf.size(), nh = (int)T.hf.size();
     std::vector<double> hcen(3 * (size_t)nh), hrad(nh), hv(9 * (size_t)nh);

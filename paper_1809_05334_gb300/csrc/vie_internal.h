@@ -15,6 +15,11 @@ constexpr double NEAR_FACTOR = 1.5;
 // independently of the rounding of the distance
 constexpr double NEAR_MARGIN = 1e-9;
 
+}  // namespace vie
+struct vie_ctx;
+namespace vie {
+void release_device_memory(vie_ctx *ctx);
+
 // kernel launches issued by this host thread (every launch site increments it;
 // a solve reports the difference across its own work)
 extern thread_local int64_t g_launches;

@@ -15,13 +15,16 @@ LIB_PATH = os.path.join(HERE, "libvie.so")
 MAX_DOMAINS = 8
 
 VIE_FP64, VIE_FP32 = 0, 1
-STATUS = {0: "VIE_OK", 1: "VIE_NOT_CONVERGED", -1: "VIE_EINVAL", -2: "VIE_ENOMEM", -3: "VIE_ECUDA",
+VIE_PENDING = 2
+STATUS = {0: "VIE_OK", 1: "VIE_NOT_CONVERGED", 2: "VIE_PENDING", -1: "VIE_EINVAL", -2: "VIE_ENOMEM", -3: "VIE_ECUDA",
           -4: "VIE_RAYLEIGH_ANOMALY", -6: "VIE_BAD_MESH", -8: "VIE_BREAKDOWN"}
 
 # every symbol include/vie.h declares
 EXPORTS = ["vie_default_options", "vie_create", "vie_set_options", "vie_set_mesh", "vie_num_unknowns",
            "vie_solve", "vie_fill_matrix", "vie_fill_matrix_prec", "vie_erfcx", "vie_green",
-           "vie_status_str", "vie_last_error", "vie_destroy", "vie_green_noalloc", "vie_solve_batch"]
+           "vie_status_str", "vie_last_error", "vie_destroy", "vie_green_noalloc", "vie_solve_batch",
+           "vie_server_create", "vie_server_submit", "vie_server_poll", "vie_server_get_stats",
+           "vie_server_destroy"]
 
 
 class Options(ctypes.Structure):
@@ -46,7 +49,20 @@ class Result(ctypes.Structure):
                 ("k_matvec_ms", ctypes.c_double), ("k_matvec_n", ctypes.c_int32), ("n_near_pairs", ctypes.c_int32),
                 ("far_pair_evals", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("k_tc_ms", ctypes.c_double), ("k_tc_bytes", ctypes.c_double), ("k_tc_n", ctypes.c_int32),
-                ("n_launches", ctypes.c_int32)]
+                ("n_launches", ctypes.c_int32), ("t_queue_ms", ctypes.c_double),
+                ("t_latency_ms", ctypes.c_double)]
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_int32), ("tets", ctypes.c_void_p),
+                ("n_tets", ctypes.c_int32), ("tet_domain", ctypes.c_void_p), ("n_domains", ctypes.c_int32),
+                ("active_domain", ctypes.c_int32), ("period_a", ctypes.c_double), ("period_b", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "rejected", "queued", "running",
+                                              "max_running", "budget_bytes", "reserved_bytes",
+                                              "peak_reserved_bytes")]
 
 
 _LIB = None
@@ -82,6 +98,13 @@ def load():
     lib.vie_green_noalloc.argtypes = [D, D, D, D, D, D, P, P, I, I, P]
     lib.vie_solve_batch.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(Result), I, I,
                                     ctypes.POINTER(I), P]
+    lib.vie_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(Options), I, ctypes.c_int64]
+    lib.vie_server_submit.argtypes = [P, ctypes.POINTER(Mesh), ctypes.POINTER(Request),
+                                      ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64)]
+    lib.vie_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(Result), I]
+    lib.vie_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    lib.vie_server_destroy.argtypes = [P]
+    lib.vie_server_destroy.restype = None
     _LIB = lib
     return lib
 
@@ -171,7 +194,8 @@ class Solver:
                     k_factor_ms=res.k_factor_ms, k_matvec_ms=res.k_matvec_ms, k_matvec_n=res.k_matvec_n,
                     n_near_pairs=res.n_near_pairs, far_pair_evals=res.far_pair_evals,
                     h2d_bytes=res.h2d_bytes, d2h_bytes=res.d2h_bytes, k_tc_ms=res.k_tc_ms,
-                    k_tc_bytes=res.k_tc_bytes, k_tc_n=res.k_tc_n, n_launches=res.n_launches, x=out)
+                    k_tc_bytes=res.k_tc_bytes, k_tc_n=res.k_tc_n, n_launches=res.n_launches,
+                    t_queue_ms=res.t_queue_ms, t_latency_ms=res.t_latency_ms, x=out)
 
     def solve_batch(self, lams, thetas, phis, eps_list, max_slots=2, coeffs=False, stream=None):
         """Independent solves of one mesh (vie_solve_batch): lams/thetas/phis/eps_list
@@ -240,6 +264,81 @@ class Solver:
         if self.ctx:
             self.lib.vie_destroy(self.ctx)
             self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Solve server (vie_server_*): continuous batching of independent solves,
+    each request with its own mesh, in n_slots concurrent slots admitted by
+    HBM footprint."""
+
+    def __init__(self, device=0, n_slots=3, hbm_budget_bytes=0, precision=VIE_FP32, use_precond=True,
+                 restart=60, max_iter=1000, tol=1e-6, inner_tol=1e-4):
+        self.lib = load()
+        opt = Options()
+        self.lib.vie_default_options(ctypes.byref(opt))
+        opt.precision, opt.use_precond = int(precision), int(bool(use_precond))
+        opt.restart, opt.max_iter, opt.tol, opt.inner_tol = int(restart), int(max_iter), float(tol), float(inner_tol)
+        self.s = ctypes.c_void_p()
+        rc = self.lib.vie_server_create(ctypes.byref(self.s), int(device), ctypes.byref(opt), int(n_slots),
+                                        int(hbm_budget_bytes))
+        if rc != 0:
+            raise VIEError(rc, "vie_server_create failed")
+        self._n_dom = {}
+
+    def submit(self, cell, lam, theta=0.0, phi=0.0, eps=()):
+        """Queue one solve; returns (ticket, footprint bytes).  Raises VIEError
+        (VIE_ENOMEM) when the request can never fit in the HBM budget."""
+        v = np.ascontiguousarray(cell.verts, dtype=np.float64)
+        t = np.ascontiguousarray(cell.tets, dtype=np.int32)
+        d = np.ascontiguousarray(cell.tet_domain, dtype=np.int32)
+        m = Mesh(verts=v.ctypes.data, n_verts=len(v), tets=t.ctypes.data, n_tets=len(t), tet_domain=d.ctypes.data,
+                 n_domains=int(cell.n_domains), active_domain=int(cell.active_domain),
+                 period_a=float(cell.period_a), period_b=float(cell.period_b))
+        r = Request()
+        r.lambda_nm, r.theta, r.phi = float(lam), float(theta), float(phi)
+        for k, e in enumerate(np.asarray(eps, dtype=np.complex128)):
+            r.eps[2 * k], r.eps[2 * k + 1] = e.real, e.imag
+        ticket = ctypes.c_uint64(0)
+        fp = ctypes.c_int64(0)
+        rc = self.lib.vie_server_submit(self.s, ctypes.byref(m), ctypes.byref(r), ctypes.byref(ticket),
+                                        ctypes.byref(fp))
+        if rc != 0:
+            raise VIEError(rc, "vie_server_submit failed (footprint %d bytes)" % fp.value)
+        self._n_dom[ticket.value] = int(cell.n_domains)
+        return int(ticket.value), int(fp.value)
+
+    def poll(self, ticket, wait_ms=-1):
+        """The result dict of a finished request, or None if it is still pending."""
+        res = Result()
+        rc = self.lib.vie_server_poll(self.s, ctypes.c_uint64(ticket), ctypes.byref(res), int(wait_ms))
+        if rc == VIE_PENDING:
+            return None
+        if rc != 0:
+            raise VIEError(rc, "vie_server_poll failed")
+        nd = self._n_dom.pop(ticket)
+        return dict(status=res.status, n=res.n_unknowns, iterations=list(res.iterations),
+                    rel_residual=np.array(res.rel_residual[:]),
+                    A=np.array([[res.absorbed[p][k] for k in range(nd)] for p in range(2)]),
+                    R=np.array(res.reflectance[:]), T=np.array(res.transmittance[:]),
+                    t_fill_ms=res.t_fill_ms, t_factor_ms=res.t_factor_ms, t_solve_ms=res.t_solve_ms,
+                    t_post_ms=res.t_post_ms, t_queue_ms=res.t_queue_ms, t_latency_ms=res.t_latency_ms,
+                    n_launches=res.n_launches)
+
+    def stats(self):
+        st = ServerStats()
+        self.lib.vie_server_get_stats(self.s, ctypes.byref(st))
+        return {n: int(getattr(st, n)) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.s:
+            self.lib.vie_server_destroy(self.s)
+            self.s = ctypes.c_void_p()
 
     def __del__(self):
         try:

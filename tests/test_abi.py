@@ -34,6 +34,35 @@ def test_struct_layout_matches_header():
     assert vie.Result.absorbed.offset % 8 == 0
 
 
+def test_struct_layout_compiled_against_header(tmp_path):
+    """sizeof/offsetof of every ABI struct, as the C compiler lays them out from
+    include/vie.h, equal the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    from paper_1809_05334_gb300 import vie
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"vie_options": vie.Options, "vie_request": vie.Request, "vie_result": vie.Result,
+               "vie_mesh": vie.Mesh, "vie_server_stats": vie.ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vie.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
 def test_status_strings_and_no_gpu_error():
     from paper_1809_05334_gb300 import vie
     lib = vie.load()
@@ -44,3 +73,5 @@ def test_status_strings_and_no_gpu_error():
     if not torch.cuda.is_available():
         with pytest.raises(vie.VIEError):
             vie.Solver()
+        with pytest.raises(vie.VIEError):
+            vie.Server()

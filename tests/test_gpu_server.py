@@ -1,0 +1,109 @@
+"""Solve server (vie_server_*): continuous batching with HBM-footprint admission.
+
+Each result in the mix equals the same request solved alone (vie_solve on a
+plain context).  The fill accumulates Z with atomics, so repeated fills agree
+to rounding; FP32 solves stop at relative residual 1e-6 after FP64
+refinement, hence |dA| <= 1e-5 (see test_gpu_batch.py for the reasoning).
+"""
+import numpy as np
+import pytest
+
+import cellgen
+
+pytestmark = pytest.mark.gpu
+
+vie = pytest.importorskip("paper_1809_05334_gb300.vie")
+
+
+def _mix():
+    cells = cellgen.small_cells()
+    out = []
+    for name, lam, th, ph in [("plasmonic_tiny", 450.0, 0.3, 0.1), ("slab_3x3x1", 520.0, 0.0, 0.0),
+                              ("slab_4x3x2_jit", 610.0, 0.9, 0.4), ("plasmonic_tiny", 700.0, 1.2, 0.0),
+                              ("plasmonic_mini", 560.0, 0.5, 0.2), ("slab_3x3x1", 430.0, 0.6, 0.3)]:
+        c = cells[name]
+        out.append((c, lam, th, ph, c.eps(lam)))
+    return out
+
+
+def _alone(mix):
+    s = vie.Solver(precision=vie.VIE_FP32, tol=1e-6)
+    try:
+        res = []
+        for c, lam, th, ph, eps in mix:
+            s.set_mesh(c)
+            res.append(s.solve(lam, th, ph, eps))
+        return res
+    finally:
+        s.close()
+
+
+def test_server_mix_equals_alone():
+    mix = _mix()
+    alone = _alone(mix)
+    srv = vie.Server(n_slots=3)
+    try:
+        tickets = [srv.submit(c, lam, th, ph, eps)[0] for c, lam, th, ph, eps in mix]
+        out = [srv.poll(t, wait_ms=-1) for t in tickets]
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert st["submitted"] == len(mix) and st["completed"] == len(mix)
+    assert st["max_running"] >= 2            # requests overlapped on the device
+    for a, b in zip(alone, out):
+        assert b["status"] == 0
+        assert np.all(b["rel_residual"] <= 1e-6)
+        assert np.max(np.abs(a["A"] - b["A"])) <= 1e-5
+        assert np.max(np.abs(a["R"] - b["R"])) <= 1e-5
+        assert b["t_latency_ms"] >= b["t_queue_ms"] >= 0.0
+
+
+def test_server_budget_admission_and_rejection():
+    """A budget that holds one request at a time serialises the slots; a request
+    larger than the whole budget is rejected at submission."""
+    cells = cellgen.small_cells()
+    c = cells["plasmonic_tiny"]
+    probe = vie.Server(n_slots=1)
+    try:
+        _, fp = probe.submit(c, 500.0, 0.0, 0.0, c.eps(500.0))
+    finally:
+        probe.close()
+    srv = vie.Server(n_slots=3, hbm_budget_bytes=int(1.5 * fp))
+    try:
+        reqs = [(500.0, 0.0), (560.0, 0.4), (620.0, 0.8), (680.0, 0.2)]
+        tickets = [srv.submit(c, lam, th, 0.0, c.eps(lam))[0] for lam, th in reqs]
+        big = cellgen.config_sweep_geometry()       # ~8.9k unknowns: > 1 GB
+        with pytest.raises(vie.VIEError) as e:
+            srv.submit(big, 500.0, 0.0, 0.0, big.eps(500.0))
+        assert e.value.code == -2
+        out = [srv.poll(t, wait_ms=-1) for t in tickets]
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert st["max_running"] == 1
+    assert st["rejected"] == 1
+    assert st["peak_reserved_bytes"] <= st["budget_bytes"]
+    s = vie.Solver(precision=vie.VIE_FP32, tol=1e-6)
+    try:
+        s.set_mesh(c)
+        for (lam, th), o in zip(reqs, out):
+            ref = s.solve(lam, th, 0.0, c.eps(lam))
+            assert o["status"] == 0
+            assert np.max(np.abs(ref["A"] - o["A"])) <= 1e-5
+    finally:
+        s.close()
+
+
+def test_server_poll_pending_and_unknown_ticket():
+    c = cellgen.small_cells()["slab_3x3x1"]
+    srv = vie.Server(n_slots=1)
+    try:
+        t, _ = srv.submit(c, 500.0, 0.0, 0.0, c.eps(500.0))
+        r = srv.poll(t, wait_ms=0)
+        if r is None:
+            r = srv.poll(t, wait_ms=-1)
+        assert r["status"] == 0
+        with pytest.raises(vie.VIEError):
+            srv.poll(t, wait_ms=0)          # a ticket is forgotten once its result is read
+    finally:
+        srv.close()
