@@ -95,7 +95,7 @@ struct vie_ctx {
     DevBuf thalf;   // per-request scratch of the touching-pair kernels
     double z_extent = 0;
     // solve buffers
-    DevBuf Z, b, x, r, u, w, V, h, y, Minv, status, acc, J, rt, cout;
+    DevBuf Z, b, x, r, u, w, V, h, y, Minv, tcpack, status, acc, J, rt, cout;
     size_t ld = 0;
     int64_t h2d = 0, d2h = 0;   // bytes copied by the current solve
     // CUDA events for options.timing
@@ -603,11 +603,14 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
     }
     CK(ctx->Minv.ensure(sizeof(float) * 2 * std::max<size_t>(tot, 1)));
     CK(ctx->status.ensure(sizeof(int)));
+    size_t pk = 1;
+    for (int nb : H.blk_n) pk = std::max(pk, vie::gj_pack_floats(nb));
+    CK(ctx->tcpack.ensure(sizeof(float) * pk));
     CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
     for (size_t k = 0; k < H.blk_n.size(); ++k) {
         float *B = ctx->Minv.as<float>() + 2 * moff[k];
         CK((vie::copy_block<TZ, float>(ctx->Z.as<TZ>(), ctx->ld, H.blk_off[k], H.blk_n[k], B, mld[k], st)));
-        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), st, kt));
+        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), ctx->tcpack.as<float>(), st, kt));
     }
     int stat = 0;
     ctx->d2h += sizeof(int);
@@ -1162,7 +1165,7 @@ void release_device_memory(vie_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->row, &ctx->coef, &ctx->wt, &ctx->kap, &ctx->ieps, &ctx->frow, &ctx->qs,
                       &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->ew, &ctx->thalf,
                       &ctx->Z, &ctx->b, &ctx->x, &ctx->r, &ctx->u, &ctx->w, &ctx->V, &ctx->h, &ctx->y,
-                      &ctx->Minv, &ctx->status, &ctx->acc, &ctx->J, &ctx->rt, &ctx->cout};
+                      &ctx->Minv, &ctx->tcpack, &ctx->status, &ctx->acc, &ctx->J, &ctx->rt, &ctx->cout};
     for (DevBuf *b : bufs) b->release();
 }
 }  // namespace vie

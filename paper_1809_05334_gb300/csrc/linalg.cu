@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <algorithm>
+#include <mutex>
 
 #include "linalg.h"
 #include "tc_gemm.cuh"
@@ -462,15 +464,71 @@ __global__ void __launch_bounds__(256) k_gj_panel(float *A, size_t ld, int n, in
     }
 }
 
-cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t st, KernelTimer *kt) {
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2D FP32 tensor map, 128-byte swizzle: `inner` floats per row, `rows` rows
+// `row_bytes` apart, box of box_in floats x box_rows rows
+bool tensor_map(CUtensorMap *map, const float *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
+                uint32_t box_in, uint32_t box_rows) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_in, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+size_t gj_pack_floats(int n) {
+    const size_t mp = ((size_t)n + TC_TM - 1) / TC_TM * TC_TM;
+    return 3 * mp * TC_PACK_ROW;
+}
+
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, KernelTimer *kt) {
     const int dsz = (2 * GJ_W * GJ_W + 2 * GJ_W + 2) * (int)sizeof(float);
     const int psz = (2 * GJ_W * GJ_W + 2 * GJ_PL * (GJ_W + 1)) * (int)sizeof(float);
+    static_assert(GJ_W == TC_KP, "the packed panels hold one pivot block");
+    int dev = 0, sms = 0;
     {   // opt in to the large dynamic shared memory (per device, cheap to repeat)
         cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_diag_w, cudaFuncAttributeMaxDynamicSharedMemorySize, dsz);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, psz);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_panel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, psz);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
+    }
+    // packed panels (zero padded to 128-row tiles) and the tensor maps of this block
+    const int mpmax = (n + TC_TM - 1) / TC_TM * TC_TM;
+    float *Ap = pack, *Bp = pack + (size_t)mpmax * TC_PACK_ROW;
+    CUtensorMap tmA, tmB, tmC, tmCs;
+    if (n > GJ_W) {
+        if (!tensor_map(&tmA, Ap, TC_PACK_ROW, mpmax, TC_PACK_ROW * 4, 32, TC_TM) ||
+            !tensor_map(&tmB, Bp, TC_PACK_ROW, 2 * (uint64_t)mpmax, TC_PACK_ROW * 4, 32, 2 * TC_TN) ||
+            !tensor_map(&tmC, A, 2 * (uint64_t)ld, n, 8 * ld, 32, TC_TM) ||
+            !tensor_map(&tmCs, A, 2 * (uint64_t)ld, n, 8 * ld, 32, 32))
+            return cudaErrorInvalidValue;
     }
     for (int k0 = 0; k0 < n; k0 += GJ_W) {
         const int w = (n - k0 < GJ_W) ? n - k0 : GJ_W;
@@ -479,10 +537,13 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t s
         if (m > 0) {
             const int nb = (m + GJ_PL - 1) / GJ_PL;
             k_gj_panel<true><<<nb, 256, psz, st>>>(A, ld, n, k0, w); ++g_launches;
-            dim3 g((m + TC_TN - 1) / TC_TN, (m + TC_TM - 1) / TC_TM);
+            const int mp = (m + TC_TM - 1) / TC_TM * TC_TM;
+            const int ntiles = (mp / TC_TM) * (mp / TC_TM);
             cudaEvent_t e0 = kt ? kt->next() : nullptr, e1 = kt ? kt->next() : nullptr;
             if (e0) cudaEventRecord(e0, st);
-            k_tc_update<<<g, TC_THREADS, TC_SMEM, st>>>(A, ld, m, k0, w, w, status); ++g_launches;
+            k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, m, k0, w, mp, Ap); ++g_launches;
+            k_tc_pack_b<<<dim3(mp / 32, TC_KP / 32), 256, 0, st>>>(A, ld, m, k0, w, Bp); ++g_launches;
+            k_tc_update<<<std::min(ntiles, sms), TC_THREADS, TC_SMEM, st>>>(tmA, tmB, tmC, tmCs, m, k0, w, status); ++g_launches;
             if (e1) {
                 cudaEventRecord(e1, st);
                 // algorithmic bytes: read-modify-write of the m x m trailing matrix and one

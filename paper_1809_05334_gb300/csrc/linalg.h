@@ -23,8 +23,11 @@ struct KernelTimer {
     cudaEvent_t next() { return alloc ? alloc(pool) : nullptr; }
     void add(cudaEvent_t a, cudaEvent_t b, double w) { ev.push_back({a, b}); work.push_back(w); }
 };
-// the same inversion with 128-wide pivot blocks and the tcgen05 (TF32) trailing update
-cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, cudaStream_t st, KernelTimer *kt = nullptr);
+// the same inversion with 128-wide pivot blocks and the tcgen05 (TF32) trailing
+// update; `pack` is device scratch of gj_pack_floats(n) floats (the packed panels)
+size_t gj_pack_floats(int n);
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st,
+                         KernelTimer *kt = nullptr);
 template <typename TS, typename TD>
 cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st);
 template <typename TV>

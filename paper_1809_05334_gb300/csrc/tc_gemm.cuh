@@ -1,47 +1,55 @@
-// Complex FP32 GEMM update C -= A B on the 5th-generation tensor cores
-// (tcgen05, kind::tf32, accumulator in tensor memory), for the Gauss-Jordan
-// inversion of the domain blocks of Eq. (6).
+// Complex FP32 trailing update C <- C - A B of the Gauss-Jordan inversion of
+// the domain blocks of Eq. (6), on the 5th-generation tensor cores (tcgen05,
+// kind::tf32, accumulators in tensor memory), with every operand moved by TMA.
 //
 // A complex product is one real product of the real views:
-//   C_rv (M x 2N) = A_rv (M x 2K) * Bt (2K x 2N),  Bt[2k][2n] = Re B, Bt[2k][2n+1] = Im B,
-//   Bt[2k+1][2n] = -Im B, Bt[2k+1][2n+1] = Re B,
-// where the real view of a row-major complex matrix interleaves (re, im).
+//   C_rv (M x 2N) += A_rv (M x 2K) * Bt (2K x 2N)
+// where the real view of a row-major complex matrix interleaves (re, im) and
+// Bt is minus the 2x2 real expansion of B.  Per pivot step a pack kernel writes
+//   Ap [mp][2 KP]    row r: the pivot columns of trailing row r (TF32-rounded)
+//   Bp [2 mp][2 KP]  rows 2j, 2j+1: (-Re B, Im B), (-Im B, -Re B) per pivot k
+// so that both operands are K-major and TMA-loadable (zero padded to 128-row
+// tiles and to KP = 128 pivots).
 //
-// One CTA (256 threads) computes a 128 x 128 complex tile (128 x 256 real,
-// 256 TMEM columns; two CTAs fit one SM) for any K <= TC_KMAX complex.  K is
-// streamed in chunks of 16 complex through two shared-memory stages in the
-// K-major 128-byte-swizzle layout (8-row x 128-byte atoms, 16-byte chunks
-// XOR-ed with the row index); the MMAs (M=128, N=256, K=8) of a chunk are
-// issued by one thread and committed to the stage's mbarrier, which the
-// staging of the chunk two steps later waits on.  The accumulator is read back
-// with tcgen05.ld and subtracted from C.  Every wait has an iteration limit;
-// on timeout the CTA records an error flag, skips its update and still frees
-// its tensor memory.
+// k_tc_update is persistent (one CTA per SM, tiles of 128 x 128 complex taken
+// round-robin) and warp-specialised:
+//   warp 0   TMA producer of the A/B chunks (32 real K each) into a 3-stage ring
+//   warp 1   tensor-memory allocation (512 columns = two 128 x 256 FP32
+//            accumulators) and the MMA issuer (M=128, N=256, K=8)
+//   warp 2   TMA producer of C, in 128-row x 32-float chunks, into a 4-slot ring
+//   warps 4-7  epilogue: tcgen05.ld of the accumulator (lane = row), add to the
+//            staged C chunk, TMA store of each warp's 32 rows
+// so the C traffic of one tile overlaps the MMAs of the next.  Every mbarrier
+// wait has an iteration limit; on timeout the role records an error, stops,
+// waits (bounded) for the copies and MMAs it issued, and the CTA still frees
+// its tensor memory.  Warp-level decisions are made uniform with a vote, and no
+// barrier other than the final __syncthreads spans several warps.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
 namespace vie {
 
-constexpr int TC_TM = 128;            // complex rows per tile
-constexpr int TC_TN = 128;            // complex columns per tile (256 real)
-constexpr int TC_KMAX = 128;          // complex K per launch (pivot block width)
-constexpr int TC_CHUNK = 32;          // real K elements per stage (one 128-byte swizzle row)
-constexpr int TC_A_CHUNK_BYTES = TC_TM * 128;          // 16 KB
-constexpr int TC_B_CHUNK_BYTES = 2 * TC_TN * 128;      // 32 KB
-constexpr int TC_STAGES = 2;
-constexpr int TC_SMEM = TC_STAGES * (TC_A_CHUNK_BYTES + TC_B_CHUNK_BYTES) + 1024 + 64;   // ~97 KB: 2 CTAs/SM
-constexpr uint32_t TC_TMEM_COLS = 256;
-constexpr long long TC_WAIT_LIMIT = 20000000;  // ~ tens of ms of polling
+constexpr int TC_TM = 128;                        // complex rows per tile
+constexpr int TC_TN = 128;                        // complex columns per tile (256 real)
+constexpr int TC_KP = 128;                        // complex pivots per update (zero padded)
+constexpr int TC_CHUNK = 32;                      // real K per stage: one 128-byte swizzle row
+constexpr int TC_NCHUNK = 2 * TC_KP / TC_CHUNK;   // 8
+constexpr int TC_A_BYTES = TC_TM * 128;           // 16 KB
+constexpr int TC_B_BYTES = 2 * TC_TN * 128;       // 32 KB
+constexpr int TC_C_BYTES = TC_TM * 128;           // 16 KB: 128 rows x 32 floats of C
+constexpr int TC_STAGES = 3;
+constexpr int TC_CSLOTS = 4;
+constexpr int TC_BAR_BYTES = 256;
+constexpr int TC_SMEM = 1024 + TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + TC_CSLOTS * TC_C_BYTES + TC_BAR_BYTES;
+constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr long long TC_WAIT_LIMIT = 20000000;     // polls of one wait (tens of ms)
 constexpr int TC_THREADS = 256;
+constexpr int TC_PACK_ROW = 2 * TC_KP;            // floats per packed row (1 KB)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// byte offset of real element (row r, k in [0,32)) inside one swizzled chunk
-__device__ __forceinline__ uint32_t sw128(int r, int k) {
-    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + ((k & 3) << 2));
 }
 
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 1024-byte atom stride
@@ -64,11 +72,6 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-// One Gauss-Jordan trailing update on the tile (blockIdx.y, blockIdx.x):
-// C[r][c] -= sum_k C[r][k0+k] C[k0+k][c] for k < K, over rows and columns
-// outside the pivot block [k0, k0+w): tile row i maps to r = i < k0 ? i : i + w
-// (columns likewise), m = n - w rows and columns are updated.  The pivot rows
-// and columns are only read, so tiles never race.
 // bounded wait on an mbarrier phase; returns false on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
     for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
@@ -85,24 +88,115 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
     return false;
 }
 
-__global__ void __launch_bounds__(TC_THREADS) k_tc_update(float *__restrict__ C, size_t ld, int m, int k0, int w,
-                                                          int K, int *err) {
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(mbar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Pack the pivot column panel of the trailing rows: Ap[r][2k..2k+1] = A[row(r)][k0+k]
+// for r < m, k < w (row(r) = r < k0 ? r : r + w), zero elsewhere up to mp rows.
+__global__ void __launch_bounds__(256) k_tc_pack_a(const float *__restrict__ A, size_t ld, int m, int k0, int w,
+                                                   int mp, float *__restrict__ Ap) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)mp * TC_KP) return;
+    const int r = (int)(e / TC_KP), k = (int)(e % TC_KP);
+    float2 v = make_float2(0.f, 0.f);
+    if (r < m && k < w) {
+        const int gr = r < k0 ? r : r + w;
+        v = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)gr * ld + k0 + k));
+    }
+    *reinterpret_cast<float2 *>(Ap + (size_t)r * TC_PACK_ROW + 2 * k) = make_float2(to_tf32(v.x), to_tf32(v.y));
+}
+
+// Pack minus the real expansion of the pivot row panel, K-major: for trailing
+// column j (col(j) = j < k0 ? j : j + w) and pivot k, with b = A[k0+k][col(j)]:
+//   Bp[2j][2k..] = (-Re b, Im b),  Bp[2j+1][2k..] = (-Im b, -Re b)
+// through a 32 x 32 shared-memory transpose (coalesced on both sides).
+__global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, size_t ld, int m, int k0, int w,
+                                                   float *__restrict__ Bp) {
+    __shared__ float2 t[32][33];
+    const int j0 = blockIdx.x * 32, kb = blockIdx.y * 32;
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+        const int kk = idx / 32, jj = idx % 32;
+        const int j = j0 + jj, k = kb + kk;
+        float2 v = make_float2(0.f, 0.f);
+        if (j < m && k < w) {
+            const int gc = j < k0 ? j : j + w;
+            v = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)(k0 + k) * ld + gc));
+        }
+        t[kk][jj] = v;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+        const int jj = idx / 32, kk = idx % 32;
+        const float2 v = t[kk][jj];
+        const size_t j = (size_t)(j0 + jj), k = (size_t)(kb + kk);
+        *reinterpret_cast<float2 *>(Bp + (2 * j) * TC_PACK_ROW + 2 * k) = make_float2(to_tf32(-v.x), to_tf32(v.y));
+        *reinterpret_cast<float2 *>(Bp + (2 * j + 1) * TC_PACK_ROW + 2 * k) =
+            make_float2(to_tf32(-v.y), to_tf32(-v.x));
+    }
+}
+
+// C <- C + Ap * Bp^T over the m x m trailing matrix (rows and columns outside the
+// pivot block [k0, k0+w); k0 is a multiple of 128 and the update never
+// straddles it).  tmA, tmB: the packed panels (box 32 floats x 128 / 256 rows);
+// tmC: the block [n rows][2 ld floats] (box 32 x 128, loads); tmCs: the same
+// with a 32 x 32 box (stores of one epilogue warp).  All four use SWIZZLE_128B.
+// The maps span whole padded rows (a multiple of 16 bytes), so a box that
+// reaches past column n stays in bounds: there, and on pivot rows or columns
+// that a ragged tile covers, the packed operands are zero and the store writes
+// back the value it loaded.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmCs, int m, int k0,
+                int w, int *err) {
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sA = base;                                         // [stage] 16 KB
-    uint8_t *sB = base + TC_STAGES * TC_A_CHUNK_BYTES;          // [stage] 32 KB
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sB + TC_STAGES * TC_B_CHUNK_BYTES);   // [stage]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + TC_STAGES);
+    uint8_t *sA = base;                                              // [stage] 16 KB
+    uint8_t *sB = sA + TC_STAGES * TC_A_BYTES;                       // [stage] 32 KB
+    uint8_t *sC = sB + TC_STAGES * TC_B_BYTES;                       // [slot] 16 KB
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sC + TC_CSLOTS * TC_C_BYTES);
+    uint64_t *full = bars, *empty = full + TC_STAGES;
+    uint64_t *cfull = empty + TC_STAGES, *cempty = cfull + TC_CSLOTS;
+    uint64_t *accfull = cempty + TC_CSLOTS, *accempty = accfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ti = blockIdx.y * TC_TM, tj = blockIdx.x * TC_TN;
-    const int nch = (2 * K + TC_CHUNK - 1) / TC_CHUNK;   // stages of 16 complex k
+    const int nt = (m + TC_TM - 1) / TC_TM;
+    const int ntiles = nt * nt;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + s)));
+        for (int s = 0; s < TC_STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+        for (int s = 0; s < TC_CSLOTS; ++s) { mbar_init(cfull + s, 1); mbar_init(cempty + s, 4); }
+        for (int b = 0; b < 2; ++b) { mbar_init(accfull + b, 1); mbar_init(accempty + b, 4); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmC)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmCs)) : "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -111,177 +205,149 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float *__restrict__ C,
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    bool ok = true;
 
-    // per-thread registers of one chunk: A items (row, k pair) and B items (column, k pair)
-    constexpr int NA = TC_TM * 8 / TC_THREADS, NB = TC_TN * 8 / TC_THREADS;   // 4 and 4
-    float4 ra[NA];
-    float4 rb[NB];   // (Re B[k], Im B[k], Re B[k+1], Im B[k+1]) of one column
-    auto load_chunk = [&](int c) {
-        const int kc0 = c * (TC_CHUNK / 2);
-        const int kcn = min(TC_CHUNK / 2, K - kc0);
-#pragma unroll
-        for (int u = 0; u < NA; ++u) {
-            const int e = tid + u * TC_THREADS;
-            const int i = e >> 3, f = e & 7;
-            const int ii = ti + i;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (ii < m && 2 * f < kcn) {
-                const int r = ii < k0 ? ii : ii + w;
-                const float *src = C + 2 * ((size_t)r * ld + k0 + kc0 + 2 * f);
-                if (2 * f + 1 < kcn) v = __ldcg(reinterpret_cast<const float4 *>(src));
-                else v = make_float4(__ldcg(src), __ldcg(src + 1), 0.f, 0.f);
+    if (warp == 0 && lane == 0) {
+        // ---- A/B producer -------------------------------------------------------
+        int it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int ty = t / nt, tx = t % nt;
+            for (int kc = 0; kc < TC_NCHUNK; ++kc, ++it) {
+                const int s = it % TC_STAGES;
+                if (it >= TC_STAGES && !mbar_wait(empty + s, (uint32_t)((it / TC_STAGES - 1) & 1))) { ok = false; break; }
+                mbar_expect_tx(full + s, TC_A_BYTES + TC_B_BYTES);
+                tma_load_2d(sA + s * TC_A_BYTES, &tmA, kc * TC_CHUNK, ty * TC_TM, full + s);
+                tma_load_2d(sB + s * TC_B_BYTES, &tmB, kc * TC_CHUNK, 2 * tx * TC_TN, full + s);
             }
-            ra[u] = v;
         }
-#pragma unroll
-        for (int u = 0; u < NB; ++u) {
-            const int e = tid + u * TC_THREADS;
-            const int j = e % TC_TN, kp = e / TC_TN;
-            const int jj = tj + j;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (jj < m && 2 * kp < kcn) {
-                const int cc = jj < k0 ? jj : jj + w;
-                const float2 u0 = __ldcg(reinterpret_cast<const float2 *>(C + 2 * ((size_t)(k0 + kc0 + 2 * kp) * ld + cc)));
-                v.x = u0.x;
-                v.y = u0.y;
-                if (2 * kp + 1 < kcn) {
-                    const float2 u1 =
-                        __ldcg(reinterpret_cast<const float2 *>(C + 2 * ((size_t)(k0 + kc0 + 2 * kp + 1) * ld + cc)));
-                    v.z = u1.x;
-                    v.w = u1.y;
-                }
-            }
-            rb[u] = v;
-        }
-    };
-    auto store_chunk = [&](uint8_t *a_st, uint8_t *b_st) {
-#pragma unroll
-        for (int u = 0; u < NA; ++u) {
-            const int e = tid + u * TC_THREADS;
-            const int i = e >> 3, f = e & 7;
-            const float4 v = ra[u];
-            *reinterpret_cast<float4 *>(a_st + sw128(i, 4 * f)) =
-                make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
-        }
-#pragma unroll
-        for (int u = 0; u < NB; ++u) {
-            const int e = tid + u * TC_THREADS;
-            const int j = e % TC_TN, kp = e / TC_TN;
-            const float4 v = rb[u];
-            // real column 2j (Re C): [Re B, -Im B]; column 2j+1 (Im C): [Im B, Re B]
-            *reinterpret_cast<float4 *>(b_st + sw128(2 * j, 4 * kp)) =
-                make_float4(to_tf32(v.x), to_tf32(-v.y), to_tf32(v.z), to_tf32(-v.w));
-            *reinterpret_cast<float4 *>(b_st + sw128(2 * j + 1, 4 * kp)) =
-                make_float4(to_tf32(v.y), to_tf32(v.x), to_tf32(v.w), to_tf32(v.z));
-        }
-    };
-
-    load_chunk(0);
-    for (int c = 0; c < nch; ++c) {
-        const int st = c % TC_STAGES;
-        uint8_t *a_st = sA + st * TC_A_CHUNK_BYTES;
-        uint8_t *b_st = sB + st * TC_B_CHUNK_BYTES;
-        if (c >= TC_STAGES) {   // the MMAs of chunk c-2 read this stage: wait for them
-            bool done = mbar_wait(mbar + st, (uint32_t)(((c - TC_STAGES) / TC_STAGES) & 1));
-            ok = __syncthreads_and(done) && ok;
-            if (!ok) break;
-        }
-        store_chunk(a_st, b_st);
-        if (c + 1 < nch) load_chunk(c + 1);   // next chunk's loads overlap this chunk's MMAs
-        // make the generic-proxy shared stores visible to the tensor core (async proxy)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            const int kcn = min(TC_CHUNK / 2, K - c * (TC_CHUNK / 2));
-            const int steps = (2 * kcn + 7) / 8;
-            for (int s2 = 0; s2 < steps; ++s2) {
-                const uint64_t da = make_desc(smem_u32(a_st) + s2 * 32), db = make_desc(smem_u32(b_st) + s2 * 32);
-                const uint32_t acc = (c > 0 || s2 > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\t"
-                    "setp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                    ::"r"(tmem), "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc));
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(mbar + st)) : "memory");
-        }
-    }
-    // wait for the last chunk (in-order completion covers the earlier ones)
-    if (ok) {
-        const int last = nch - 1;
-        bool done = mbar_wait(mbar + (last % TC_STAGES), (uint32_t)((last / TC_STAGES) & 1));
-        ok = __syncthreads_and(done);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) {
-        // record the failure and give the MMAs in flight a second bounded wait
-        // before the tensor memory is released; the update is skipped
-        if (tid == 0) atomicExch(err, 2);
+        if (!ok) atomicExch(err, 2);
+        // the loads issued last into each stage have landed before the CTA leaves
         for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_wait(mbar + s, 0);
-            mbar_wait(mbar + s, 1);
+            const int uses = it / TC_STAGES + (s < it % TC_STAGES ? 1 : 0);
+            if (uses > 0) mbar_wait(full + s, (uint32_t)((uses - 1) & 1));
         }
-    } else {
-        // ---- epilogue: TMEM (row = lane) -> registers -> C -= acc ------------------
-        const int i = (warp & 3) * 32 + lane;
-        const int ii = ti + i;
-        const int r = ii < k0 ? ii : ii + w;
-        const int cbase = (warp >> 2) * 128;   // warps 4..7 take real columns 128..255
-        for (int c0 = cbase; c0 < cbase + 128; c0 += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (ii >= m) continue;
-            // 16 complex columns jj = tj + c0/2 + q, as 8 pairs
-            float4 old[8];
-            bool vec[8];
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ---------------------------------------------------------
+        int it = 0, tl = 0;
+        bool ok = true;
+        uint64_t *last_bar = nullptr;
+        uint32_t last_par = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+            const int b = tl & 1;
+            if (tl >= 2 && !mbar_wait(accempty + b, (uint32_t)((tl / 2 - 1) & 1))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dcol = tmem + (uint32_t)(b * 256);
+            for (int kc = 0; kc < TC_NCHUNK; ++kc, ++it) {
+                const int s = it % TC_STAGES;
+                if (!mbar_wait(full + s, (uint32_t)((it / TC_STAGES) & 1))) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(sA + s * TC_A_BYTES), b0 = smem_u32(sB + s * TC_B_BYTES);
 #pragma unroll
-            for (int p2 = 0; p2 < 8; ++p2) {
-                const int jj = tj + c0 / 2 + 2 * p2;
-                const int cc = jj < k0 ? jj : jj + w;
-                vec[p2] = (jj + 1 < m) && !(jj < k0 && jj + 1 >= k0) && (cc & 1) == 0;
-                if (vec[p2]) old[p2] = __ldcs(reinterpret_cast<const float4 *>(C + 2 * ((size_t)r * ld + cc)));
-            }
-#pragma unroll
-            for (int p2 = 0; p2 < 8; ++p2) {
-                const int jj = tj + c0 / 2 + 2 * p2;
-                const float a0 = __uint_as_float(v[4 * p2]), a1 = __uint_as_float(v[4 * p2 + 1]);
-                const float a2 = __uint_as_float(v[4 * p2 + 2]), a3 = __uint_as_float(v[4 * p2 + 3]);
-                if (vec[p2]) {
-                    const int cc = jj < k0 ? jj : jj + w;
-                    float4 o = old[p2];
-                    o.x -= a0; o.y -= a1; o.z -= a2; o.w -= a3;
-                    __stcs(reinterpret_cast<float4 *>(C + 2 * ((size_t)r * ld + cc)), o);   // streaming: keep the panels in L2
-                } else {
-                    for (int h = 0; h < 2; ++h) {
-                        const int j2 = jj + h;
-                        if (j2 >= m) break;
-                        const int c2 = j2 < k0 ? j2 : j2 + w;
-                        float *pp = C + 2 * ((size_t)r * ld + c2);
-                        pp[0] -= h ? a2 : a0;
-                        pp[1] -= h ? a3 : a1;
-                    }
+                for (int q = 0; q < TC_CHUNK / 8; ++q) {
+                    const uint64_t da = make_desc(a0 + q * 32), db = make_desc(b0 + q * 32);
+                    const uint32_t acc = (kc > 0 || q > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                        ::"r"(dcol), "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc));
                 }
+                mma_commit(empty + s);   // frees the stage once these MMAs have read it
+                last_bar = empty + s;
+                last_par = (uint32_t)((it / TC_STAGES) & 1);
+            }
+            if (!ok) break;
+            mma_commit(accfull + b);     // accumulator b complete
+            last_bar = accfull + b;
+            last_par = (uint32_t)((tl / 2) & 1);
+        }
+        if (!ok) atomicExch(err, 2);
+        // the MMAs issued last have finished before the tensor memory is released
+        if (last_bar) mbar_wait(last_bar, last_par);
+    } else if (warp == 2 && lane == 0) {
+        // ---- C producer ---------------------------------------------------------
+        int ci = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int ty = t / nt, tx = t % nt;
+            const int r0 = ty * TC_TM, c0 = tx * TC_TN;
+            const int gr0 = r0 < k0 ? r0 : r0 + w, gc0 = c0 < k0 ? c0 : c0 + w;
+            for (int cc = 0; cc < TC_NCHUNK; ++cc, ++ci) {
+                const int s = ci % TC_CSLOTS;
+                if (ci >= TC_CSLOTS && !mbar_wait(cempty + s, (uint32_t)((ci / TC_CSLOTS - 1) & 1))) { ok = false; break; }
+                mbar_expect_tx(cfull + s, TC_C_BYTES);
+                tma_load_2d(sC + s * TC_C_BYTES, &tmC, 2 * gc0 + cc * 32, gr0, cfull + s);
             }
         }
+        if (!ok) atomicExch(err, 2);
+        for (int s = 0; s < TC_CSLOTS; ++s) {
+            const int uses = ci / TC_CSLOTS + (s < ci % TC_CSLOTS ? 1 : 0);
+            if (uses > 0) mbar_wait(cfull + s, (uint32_t)((uses - 1) & 1));
+        }
+    } else if (warp >= 4) {
+        // ---- epilogue: TMEM lane = row; warp q owns rows 32q..32q+31 of the tile --
+        const int q4 = warp - 4;
+        const int row = q4 * 32 + lane;
+        int ci = 0, tl = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+            const int ty = t / nt, tx = t % nt;
+            const int r0 = ty * TC_TM, c0 = tx * TC_TN;
+            const int gr0 = r0 < k0 ? r0 : r0 + w, gc0 = c0 < k0 ? c0 : c0 + w;
+            const int b = tl & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(accfull + b, (uint32_t)((tl / 2) & 1)))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int cc = 0; cc < TC_NCHUNK; ++cc, ++ci) {
+                const int s = ci % TC_CSLOTS;
+                if (!__all_sync(0xffffffffu, mbar_wait(cfull + s, (uint32_t)((ci / TC_CSLOTS) & 1)))) { ok = false; break; }
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * 256 + cc * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // the chunk's row `row`: 8 swizzled 16-byte pieces (piece q at q ^ (row & 7))
+                uint8_t *rp = sC + s * TC_C_BYTES + row * 128;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float4 *p = reinterpret_cast<float4 *>(rp + ((q ^ (row & 7)) << 4));
+                    float4 c = *p;
+                    c.x += __uint_as_float(v[4 * q]);
+                    c.y += __uint_as_float(v[4 * q + 1]);
+                    c.z += __uint_as_float(v[4 * q + 2]);
+                    c.w += __uint_as_float(v[4 * q + 3]);
+                    *p = c;
+                }
+                // make the generic-proxy writes visible to the bulk copy, then store the warp's rows
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    tma_store_2d(&tmCs, sC + s * TC_C_BYTES + q4 * 32 * 128, 2 * gc0 + cc * 32, gr0 + q4 * 32);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    // the store of the previous chunk has finished reading its slot
+                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    if (ci > 0) mbar_arrive(cempty + (ci - 1) % TC_CSLOTS);
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(accempty + b);
+        }
+        if (!ok && lane == 0) atomicExch(err, 2);
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
     }
