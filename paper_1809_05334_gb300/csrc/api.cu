@@ -446,13 +446,13 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
     CK(ctx->u.ensure(sizeof(TV) * vs));
     CK(ctx->w.ensure(sizeof(TV) * vs));
     CK(ctx->V.ensure(sizeof(TV) * vs * (m + 1)));
-    CK(ctx->h.ensure(sizeof(double) * 4 * (m + 2)));
+    CK(ctx->h.ensure(sizeof(double) * 4 * (2 * m + 4)));
     CK(ctx->y.ensure(sizeof(double) * 4 * (m + 1)));
     double *x = ctx->x.as<double>(), *r = ctx->r.as<double>(), *hd = ctx->h.as<double>();
     TV *u = ctx->u.as<TV>(), *w = ctx->w.as<TV>(), *V = ctx->V.as<TV>();
     const TZ *Z = ctx->Z.as<TZ>();
     CK(cudaMemsetAsync(x, 0, sizeof(double) * vs, st));
-    std::vector<double> hh(4 * (m + 2));
+    std::vector<double> hh(4 * (2 * m + 4));
     auto norms2 = [&](const double *vec, double out[2]) -> int {
         CK(vie::dots<double>(vec, 0, 1, vec, N, hd, st));
         CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
@@ -512,21 +512,20 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
             CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st)));
             if (e1) { CK(cudaEventRecord(e1, st)); tm.mv.push_back({e0, e1}); }
             if (pre) { if (int e = precond_apply<TV>(ctx, H, moff, mld, u, vn, st)) return e; }
-            // classical Gram-Schmidt, twice
-            std::vector<double> hsum(4 * (k + 1), 0.0);
-            for (int pass = 0; pass < 2; ++pass) {
-                CK(vie::dots<TV>(V, vs, k + 1, vn, N, hd, st));
-                CK(vie::subtract<TV>(V, vs, k + 1, hd, vn, N, st));
-                CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4 * (k + 1), cudaMemcpyDeviceToHost, st));
-                ctx->d2h += sizeof(double) * 4 * (k + 1);
-                CK(cudaStreamSynchronize(st));
-                for (int i = 0; i < 4 * (k + 1); ++i) hsum[i] += hh[i];
-            }
-            CK(vie::dots<TV>(vn, 0, 1, vn, N, hd, st));
-            ctx->d2h += sizeof(double) * 4;
-            CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+            // classical Gram-Schmidt, twice; the projections of both passes and
+            // the new norm stay on the device until one copy at the end
+            const size_t nh = 4 * (size_t)(k + 1);
+            CK(vie::dots<TV>(V, vs, k + 1, vn, N, hd, st));
+            CK(vie::subtract<TV>(V, vs, k + 1, hd, vn, N, st));
+            CK(vie::dots<TV>(V, vs, k + 1, vn, N, hd + nh, st));
+            CK(vie::subtract<TV>(V, vs, k + 1, hd + nh, vn, N, st));
+            CK(vie::dots<TV>(vn, 0, 1, vn, N, hd + 2 * nh, st));
+            CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * (2 * nh + 4), cudaMemcpyDeviceToHost, st));
+            ctx->d2h += sizeof(double) * (2 * nh + 4);
             CK(cudaStreamSynchronize(st));
-            double hn[2] = {std::sqrt(std::max(hh[0], 0.0)), std::sqrt(std::max(hh[2], 0.0))};
+            std::vector<double> hsum(nh);
+            for (size_t i = 0; i < nh; ++i) hsum[i] = hh[i] + hh[nh + i];
+            double hn[2] = {std::sqrt(std::max(hh[2 * nh], 0.0)), std::sqrt(std::max(hh[2 * nh + 2], 0.0))};
             double sc[4] = {0, 0, 0, 0};
             for (int p = 0; p < 2; ++p) {
                 if (!inner_active[p]) continue;

@@ -21,84 +21,104 @@ template <> struct V2<float> { using t = float4; };
 template <> struct V2<double> { using t = double2; };
 
 // ---------------------------------------------------------------------------
-// matvec: y[r] = sum_c A[r][c] x[c] for rows [0, rows), two right-hand sides.
-// One warp per MV_ROWS rows; the x tile of MV_TILE columns is staged in shared
-// memory (converted to the accumulation type TA); Z streams with 16-byte loads.
+// matvec: y[r] = alpha sum_c A[r][c] x[c] (+ y[r] if ACCUM) for rows [0, rows),
+// two right-hand sides ([n][2] complex vectors).
+// The grid is one wave (every resident CTA slot of the GPU); CTA b owns the
+// contiguous rows [rows b / G, rows (b+1) / G), so all CTAs stream the same
+// number of bytes.  Its warps split the columns of each group of MV_ROWS rows
+// (equal segments, 16-byte loads of A streamed with evict-first), reduce by
+// shuffles, and combine the warps' partial sums through shared memory (double
+// buffered: one barrier per row group).  x is read through L1/L2 (it is a few
+// hundred KB and every row group reuses it).
 // ---------------------------------------------------------------------------
 constexpr int MV_ROWS = 4;
 constexpr int MV_WARPS = 8;
-template <typename TA> __host__ __device__ constexpr int mv_tile() { return 512; }   // x tile of 512 columns
+
+template <typename TX, typename TA> __device__ __forceinline__ void load_x(const TX *x, int c, TA out[4]);
+template <> __device__ __forceinline__ void load_x<float, float>(const float *x, int c, float out[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(x + 4 * (size_t)c));
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <> __device__ __forceinline__ void load_x<double, double>(const double *x, int c, double out[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(x + 4 * (size_t)c));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(x + 4 * (size_t)c + 2));
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
 
 template <typename TZ, typename TX, typename TA, bool ACCUM>
 __global__ void __launch_bounds__(MV_WARPS * 32)
 k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__restrict__ x,
          TA *__restrict__ y, TA alpha) {
-    constexpr int MV_TILE = mv_tile<TA>();
-    __shared__ TA xs[MV_TILE * 4];
+    __shared__ TA part[2][MV_WARPS][MV_ROWS * 4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = (blockIdx.x * MV_WARPS + warp) * MV_ROWS;
-    TA acc[MV_ROWS][4];
-#pragma unroll
-    for (int i = 0; i < MV_ROWS; ++i)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[i][k] = TA(0);
+    const int rb = (int)((long long)rows * blockIdx.x / gridDim.x);
+    const int re = (int)((long long)rows * (blockIdx.x + 1) / gridDim.x);
     constexpr int VEC = sizeof(TZ) == 4 ? 2 : 1;   // complex entries per 16-byte load
-    for (int c0 = 0; c0 < cols; c0 += MV_TILE) {
-        const int cn = min(MV_TILE, cols - c0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < MV_TILE * 4; i += blockDim.x)
-            xs[i] = (i < cn * 4) ? TA(x[(size_t)c0 * 4 + i]) : TA(0);
-        __syncthreads();
-        const int cend = (cn + VEC - 1) / VEC * VEC;
-        for (int c = lane * VEC; c < cend; c += 32 * VEC) {
+    const int nvec = (cols + VEC - 1) / VEC;
+    const int v0 = (int)((long long)nvec * warp / MV_WARPS), v1 = (int)((long long)nvec * (warp + 1) / MV_WARPS);
+    int buf = 0;
+    for (int r0 = rb; r0 < re; r0 += MV_ROWS, buf ^= 1) {
+        TA acc[MV_ROWS][4];
+#pragma unroll
+        for (int i = 0; i < MV_ROWS; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][k] = TA(0);
+#pragma unroll 2
+        for (int v = v0 + lane; v < v1; v += 32) {
+            const int c = v * VEC;
             typename V2<TZ>::t z[MV_ROWS];
 #pragma unroll
             for (int i = 0; i < MV_ROWS; ++i) {
-                const int r = r0 + i;
-                if (r < rows)
-                    z[i] = __ldcs(reinterpret_cast<const typename V2<TZ>::t *>(A + 2 * ((size_t)r * ld + c0 + c)));
+                if (r0 + i < re)
+                    z[i] = __ldcs(reinterpret_cast<const typename V2<TZ>::t *>(A + 2 * ((size_t)(r0 + i) * ld + c)));
                 else
                     z[i] = {};
             }
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                const TA *xv = xs + 4 * (c + v);
-                const TA x0r = xv[0], x0i = xv[1], x1r = xv[2], x1i = xv[3];
+            for (int u = 0; u < VEC; ++u) {
+                TA xv[4] = {TA(0), TA(0), TA(0), TA(0)};
+                if (c + u < cols) load_x<TX, TA>(x, c + u, xv);
 #pragma unroll
                 for (int i = 0; i < MV_ROWS; ++i) {
                     TA zr, zi;
                     if (VEC == 2) {
                         const float4 f = *reinterpret_cast<const float4 *>(&z[i]);
-                        zr = TA(v == 0 ? f.x : f.z);
-                        zi = TA(v == 0 ? f.y : f.w);
+                        zr = TA(u == 0 ? f.x : f.z);
+                        zi = TA(u == 0 ? f.y : f.w);
                     } else {
                         const double2 d = *reinterpret_cast<const double2 *>(&z[i]);
                         zr = TA(d.x);
                         zi = TA(d.y);
                     }
-                    acc[i][0] = fma(zr, x0r, fma(-zi, x0i, acc[i][0]));
-                    acc[i][1] = fma(zr, x0i, fma(zi, x0r, acc[i][1]));
-                    acc[i][2] = fma(zr, x1r, fma(-zi, x1i, acc[i][2]));
-                    acc[i][3] = fma(zr, x1i, fma(zi, x1r, acc[i][3]));
+                    acc[i][0] = fma(zr, xv[0], fma(-zi, xv[1], acc[i][0]));
+                    acc[i][1] = fma(zr, xv[1], fma(zi, xv[0], acc[i][1]));
+                    acc[i][2] = fma(zr, xv[2], fma(-zi, xv[3], acc[i][2]));
+                    acc[i][3] = fma(zr, xv[3], fma(zi, xv[2], acc[i][3]));
                 }
             }
         }
-    }
 #pragma unroll
-    for (int i = 0; i < MV_ROWS; ++i)
+        for (int i = 0; i < MV_ROWS; ++i)
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[i][k] += __shfl_down_sync(0xffffffffu, acc[i][k], o);
-    if (lane == 0) {
+                for (int o = 16; o > 0; o >>= 1) acc[i][k] += __shfl_down_sync(0xffffffffu, acc[i][k], o);
+        if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < MV_ROWS; ++i) {
+            for (int i = 0; i < MV_ROWS; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) part[buf][warp][4 * i + k] = acc[i][k];
+        }
+        __syncthreads();
+        if (threadIdx.x < MV_ROWS * 4) {
+            const int i = threadIdx.x / 4, k = threadIdx.x % 4;
             const int r = r0 + i;
-            if (r >= rows) continue;
+            if (r < re) {
+                TA s = TA(0);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (ACCUM) y[(size_t)r * 4 + k] += alpha * acc[i][k];
-                else y[(size_t)r * 4 + k] = alpha * acc[i][k];
+                for (int w2 = 0; w2 < MV_WARPS; ++w2) s += part[buf][w2][threadIdx.x];
+                if (ACCUM) y[(size_t)r * 4 + k] += alpha * s;
+                else y[(size_t)r * 4 + k] = alpha * s;
             }
         }
     }
@@ -108,7 +128,17 @@ template <typename TZ, typename TX, typename TA>
 cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *y, TA alpha, bool accumulate,
                    cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
-    const int grid = (rows + MV_WARPS * MV_ROWS - 1) / (MV_WARPS * MV_ROWS);
+    static int slots = 0;   // resident CTAs of the GPU (per instantiation; one device per process)
+    if (slots == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_matvec<TZ, TX, TA, false>, MV_WARPS * 32, 0);
+        if (e != cudaSuccess) return e;
+        slots = std::max(1, sms * per);
+    }
+    const int grid = std::max(1, std::min(slots, (rows + MV_ROWS - 1) / MV_ROWS));
     if (accumulate)
         k_matvec<TZ, TX, TA, true><<<grid, MV_WARPS * 32, 0, st>>>(A, ld, rows, cols, x, y, alpha);
     else
@@ -338,62 +368,67 @@ template cudaError_t gj_invert<double>(double *, size_t, int, int *, cudaStream_
 constexpr int GJ_W = 128;     // pivot block width (the K of the tensor-core update)
 constexpr int GJ_PL = 32;     // panel lines per CTA in the row / column panel kernels
 
-__global__ void __launch_bounds__(512) k_gj_diag_w(float *A, size_t ld, int k0, int w, int *status) {
-    // unblocked in-place Gauss-Jordan inverse of the w x w (w <= GJ_W) pivot block
-    extern __shared__ float dsm[];
-    float *P = dsm;                      // [w][w][2], row stride 2w
-    float *col = dsm + 2 * GJ_W * GJ_W;  // [w][2]
-    float *piv = col + 2 * GJ_W;         // [2]
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i = e / w, j = e % w;
-        P[2 * (i * w + j)] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
-        P[2 * (i * w + j) + 1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
+// In-place Gauss-Jordan inverse of the w x w (w <= GJ_W) pivot block, held in
+// registers: thread t owns column c = t % 128 and rows g + 8q (g = t / 128,
+// q = 0..15).  Per pivot j the owners publish row j and column j through
+// double-buffered shared memory (one barrier per pivot); every thread forms
+// p = 1 / a_jj and updates its 32 entries.
+constexpr int GJ_DG = 8;   // row groups of the pivot-block inverse (1024 threads)
+__global__ void __launch_bounds__(GJ_W * GJ_DG) k_gj_diag_w(float *A, size_t ld, int k0, int w, int *status) {
+    __shared__ float2 rowbuf[2][GJ_W], colbuf[2][GJ_W];
+    const int c = threadIdx.x & (GJ_W - 1), g = threadIdx.x >> 7;
+    float pr[GJ_W / GJ_DG], pi[GJ_W / GJ_DG];
+#pragma unroll
+    for (int q = 0; q < GJ_W / GJ_DG; ++q) {
+        const int i = g + GJ_DG * q;
+        float2 v = make_float2(0.f, 0.f);
+        if (i < w && c < w) v = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)(k0 + i) * ld + k0 + c));
+        pr[q] = v.x;
+        pi[q] = v.y;
     }
-    __syncthreads();
     for (int j = 0; j < w; ++j) {
-        if (threadIdx.x == 0) {
-            float pr = P[2 * (j * w + j)], pi = P[2 * (j * w + j) + 1];
-            float d = pr * pr + pi * pi;
-            if (!(d > 0.f) || !isfinite(d)) atomicExch(status, 1);
-            piv[0] = pr / d;
-            piv[1] = -pi / d;
+        const int b = j & 1;
+        const int qj = j / GJ_DG;
+        if (g == j % GJ_DG) {   // this thread holds row j of column c
+            float xr = 0.f, xi = 0.f;
+#pragma unroll
+            for (int q = 0; q < GJ_W / GJ_DG; ++q)
+                if (q == qj) { xr = pr[q]; xi = pi[q]; }
+            rowbuf[b][c] = make_float2(xr, xi);
         }
-        if (threadIdx.x < w) {
-            col[2 * threadIdx.x] = P[2 * (threadIdx.x * w + j)];
-            col[2 * threadIdx.x + 1] = P[2 * (threadIdx.x * w + j) + 1];
+        if (c == j) {         // this thread holds column j for its rows
+#pragma unroll
+            for (int q = 0; q < GJ_W / GJ_DG; ++q) colbuf[b][g + GJ_DG * q] = make_float2(pr[q], pi[q]);
         }
         __syncthreads();
-        const float qr = piv[0], qi = piv[1];
-        if (threadIdx.x < w) {   // row j <- p * row j, pivot entry <- p
-            const int c = threadIdx.x;
-            if (c == j) {
-                P[2 * (j * w + c)] = qr; P[2 * (j * w + c) + 1] = qi;
+        const float2 pv = rowbuf[b][j];
+        const float d = pv.x * pv.x + pv.y * pv.y;
+        if (threadIdx.x == 0 && (!(d > 0.f) || !isfinite(d))) atomicExch(status, 1);
+        const float qr = pv.x / d, qi = -pv.y / d;            // p = 1 / a_jj
+        const float2 rc = rowbuf[b][c];
+        const float nr = qr * rc.x - qi * rc.y, ni = qr * rc.y + qi * rc.x;   // p a_jc
+#pragma unroll
+        for (int q = 0; q < GJ_W / GJ_DG; ++q) {
+            const int i = g + GJ_DG * q;
+            if (i == j) {                                       // row j <- p row j, a_jj <- p
+                pr[q] = (c == j) ? qr : nr;
+                pi[q] = (c == j) ? qi : ni;
             } else {
-                float ar = P[2 * (j * w + c)], ai = P[2 * (j * w + c) + 1];
-                P[2 * (j * w + c)] = qr * ar - qi * ai;
-                P[2 * (j * w + c) + 1] = qr * ai + qi * ar;
+                const float2 f = colbuf[b][i];
+                if (c == j) {                                   // a_ij <- -f p
+                    pr[q] = -(f.x * qr - f.y * qi);
+                    pi[q] = -(f.x * qi + f.y * qr);
+                } else {                                        // a_ic <- a_ic - f (p a_jc)
+                    pr[q] -= f.x * nr - f.y * ni;
+                    pi[q] -= f.x * ni + f.y * nr;
+                }
             }
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-            const int i = e / w, c = e % w;
-            if (i == j) continue;
-            const float fr = col[2 * i], fi = col[2 * i + 1];
-            if (c == j) {            // a_ij <- -f_i p
-                P[2 * (i * w + c)] = -(fr * qr - fi * qi);
-                P[2 * (i * w + c) + 1] = -(fr * qi + fi * qr);
-            } else {                 // a_ic <- a_ic - f_i a_jc(new)
-                const float br = P[2 * (j * w + c)], bi = P[2 * (j * w + c) + 1];
-                P[2 * (i * w + c)] -= fr * br - fi * bi;
-                P[2 * (i * w + c) + 1] -= fr * bi + fi * br;
-            }
-        }
-        __syncthreads();
     }
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i = e / w, j = e % w;
-        A[2 * ((size_t)(k0 + i) * ld + k0 + j)] = P[2 * (i * w + j)];
-        A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1] = P[2 * (i * w + j) + 1];
+#pragma unroll
+    for (int q = 0; q < GJ_W / GJ_DG; ++q) {
+        const int i = g + GJ_DG * q;
+        if (i < w && c < w) *reinterpret_cast<float2 *>(A + 2 * ((size_t)(k0 + i) * ld + k0 + c)) = make_float2(pr[q], pi[q]);
     }
 }
 
@@ -506,13 +541,12 @@ size_t gj_pack_floats(int n) {
 }
 
 cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, KernelTimer *kt) {
-    const int dsz = (2 * GJ_W * GJ_W + 2 * GJ_W + 2) * (int)sizeof(float);
     const int psz = (2 * GJ_W * GJ_W + 2 * GJ_PL * (GJ_W + 1)) * (int)sizeof(float);
     static_assert(GJ_W == TC_KP, "the packed panels hold one pivot block");
+    static_assert(GJ_W == 128, "k_gj_diag_w maps its threads onto 128 columns");
     int dev = 0, sms = 0;
     {   // opt in to the large dynamic shared memory (per device, cheap to repeat)
         cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_diag_w, cudaFuncAttributeMaxDynamicSharedMemorySize, dsz);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, psz);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_panel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, psz);
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -532,7 +566,7 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
     }
     for (int k0 = 0; k0 < n; k0 += GJ_W) {
         const int w = (n - k0 < GJ_W) ? n - k0 : GJ_W;
-        k_gj_diag_w<<<1, 512, dsz, st>>>(A, ld, k0, w, status); ++g_launches;
+        k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(A, ld, k0, w, status); ++g_launches;
         const int m = n - w;
         if (m > 0) {
             const int nb = (m + GJ_PL - 1) / GJ_PL;
