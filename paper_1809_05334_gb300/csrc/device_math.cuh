@@ -183,9 +183,15 @@ __device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub, const EwaldTables *__re
 //            the regularised near image uses (F(RE) - F(0))/R, formed without
 //            cancellation in the first interval
 // stab: [NSPAT][4] cubic coefficients (shared memory); ztab: [n_tab][NZTAB][4] complex
-__device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, unsigned sub, const float *stab,
-                                               const float2 *__restrict__ ztab, const EwaldF32 &ew) {
-    cx<float> acc = {0.f, 0.f};
+// With PAIR the same pass also returns gm = g_p(-d): the spectral terms of -d
+// carry the conjugate phases, and the spatial term of image -R_mn at -d is the
+// table value of image R_mn at d with the conjugate lattice phase (the image
+// list and the near-image masks are symmetric under (m,n) -> (-m,-n)).
+template <bool PAIR>
+__device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, unsigned sub, const float *stab,
+                                               const float2 *__restrict__ ztab, const EwaldF32 &ew,
+                                               cx<float> &gp, cx<float> &gm) {
+    cx<float> acc = {0.f, 0.f}, acc2 = {0.f, 0.f};
     const float z = fabsf(dz);
     float zu = fminf(z * ew.z_inv_h, float(NZTAB));
     int iz = min((int)zu, NZTAB - 1);
@@ -201,7 +207,7 @@ __device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, uns
     sincospif(-ew.step_y * dy * 0.31830988618f, &s, &c);
     const cx<float> sy = {c, s};
     for (int p = 0; p <= 2 * P; ++p) {
-        cx<float> inner = {0.f, 0.f};
+        cx<float> inner = {0.f, 0.f}, inner2 = {0.f, 0.f};
         cx<float> ey = ey0;
         for (int q = 0; q < nq; ++q) {
             const int tb = ew.rect_tab[p * nq + q];
@@ -211,10 +217,12 @@ __device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, uns
                 cx<float> g = {fmaf(u, fmaf(u, fmaf(u, c3.x, c2.x), c1.x), c0.x),
                                fmaf(u, fmaf(u, fmaf(u, c3.y, c2.y), c1.y), c0.y)};
                 inner = inner + ey * g;
+                if (PAIR) inner2 = inner2 + cconj(ey) * g;
             }
             ey = ey * sy;
         }
         acc = acc + ex * inner;
+        if (PAIR) acc2 = acc2 + cconj(ex) * inner2;
         ex = ex * sx;
     }
     const float E = ew.Ef;
@@ -246,8 +254,20 @@ __device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, uns
         }
         acc.re = fmaf(val, im[2], acc.re);
         acc.im = fmaf(val, im[3], acc.im);
+        if (PAIR) {
+            acc2.re = fmaf(val, im[2], acc2.re);
+            acc2.im = fmaf(-val, im[3], acc2.im);
+        }
     }
-    return acc;
+    gp = acc;
+    gm = acc2;
+}
+
+__device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, unsigned sub, const float *stab,
+                                               const float2 *__restrict__ ztab, const EwaldF32 &ew) {
+    cx<float> g, unused;
+    green_tab_impl<false>(dx, dy, dz, sub, stab, ztab, ew, g, unused);
+    return g;
 }
 
 // ---------------------------------------------------------------------------

@@ -143,18 +143,37 @@ cudaError_t launch_build_tables(const EwaldTables *ew, float *stab, float2 *ztab
     return cudaGetLastError();
 }
 
+// near-image mask of the reversed pair: image (m,n) <-> (-m,-n), i.e. bit k <-> bit 8-k
+__device__ __forceinline__ unsigned mirror_mask(unsigned sub) {
+    unsigned r = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        if ((sub >> k) & 1u) r |= 1u << (8 - k);
+    return r;
+}
+
 // g_p for the fill kernels: FP64 by the Ewald series, FP32 from the tables
 template <typename T> struct Green;
+// eval2 returns g_p(d) and g_p(-d) (the same near-image mask applies to both)
 template <> struct Green<double> {
     __device__ static cx<double> eval(double dx, double dy, double dz, unsigned sub, const float *, const float2 *,
                                       const EwaldTables *ew, const EwaldF32 &) {
         return green_p<double>(dx, dy, dz, sub, ew);
+    }
+    __device__ static void eval2(double dx, double dy, double dz, unsigned sub, const float *, const float2 *,
+                                 const EwaldTables *ew, const EwaldF32 &, cx<double> &gp, cx<double> &gm) {
+        gp = green_p<double>(dx, dy, dz, sub, ew);
+        gm = green_p<double>(-dx, -dy, -dz, mirror_mask(sub), ew);
     }
 };
 template <> struct Green<float> {
     __device__ static cx<float> eval(float dx, float dy, float dz, unsigned sub, const float *stab,
                                      const float2 *ztab, const EwaldTables *, const EwaldF32 &ef) {
         return green_tab(dx, dy, dz, sub, stab, ztab, ef);
+    }
+    __device__ static void eval2(float dx, float dy, float dz, unsigned sub, const float *stab, const float2 *ztab,
+                                 const EwaldTables *, const EwaldF32 &ef, cx<float> &gp, cx<float> &gm) {
+        green_tab_impl<true>(dx, dy, dz, sub, stab, ztab, ef, gp, gm);
     }
 };
 
@@ -221,19 +240,24 @@ __device__ void scatter_tt(const DevMesh &m, const DevReq &q, T *Z, size_t N, in
 // all tetrahedron pairs: degree-2 product rule of g_p; for the near images of a
 // pair the static part is removed here and integrated by k_pr_tt / k_touch_tt
 // ---------------------------------------------------------------------------
+// Each unordered pair {t, s} (s >= t) is evaluated once: one pass over the 16
+// point pairs gives g_p(x_a - y_b) for the block (t, s) and g_p(y_b - x_a) for
+// the block (s, t) (the reversed pair's moments swap the roles of the offsets).
 template <typename T>
 __global__ void __launch_bounds__(128) k_far_tt(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N) {
     extern __shared__ float smem_tab[];
+    const int t = blockIdx.y;
+    if ((int)(blockIdx.x * blockDim.x + blockDim.x) <= t) return;   // the whole block is below the diagonal
     const float *stab = stage_stab<T>(q, smem_tab);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = blockIdx.y;
-    if (s >= m.nt) return;
+    if (s >= m.nt || s < t) return;
     // near images of this pair: their static part is integrated separately
     const unsigned sub = m.mk_tt[(size_t)t * m.nt + s];
     const T *ft = m.far<T>(t);
     const T *fs = m.far<T>(s);
-    Mom<T> mo;
+    Mom<T> mo, mr;   // blocks (t, s) and (s, t)
     mo.zero();
+    mr.zero();
     const T wgt = ft[27] * fs[27];
     for (int a = 0; a < 4; ++a) {
         const T xa[3] = {ft[3 * a], ft[3 * a + 1], ft[3 * a + 2]};
@@ -241,17 +265,25 @@ __global__ void __launch_bounds__(128) k_far_tt(DevMesh m, const __grid_constant
         for (int b = 0; b < 4; ++b) {
             const T yb[3] = {fs[3 * b], fs[3 * b + 1], fs[3 * b + 2]};
             const T rb[3] = {yb[0] - fs[12], yb[1] - fs[13], yb[2] - fs[14]};
-            cx<T> g = Green<T>::eval(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab, q.ew, q.ef);
+            cx<T> g, gr;
+            Green<T>::eval2(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab, q.ew, q.ef, g, gr);
             g = wgt * g;
+            gr = wgt * gr;
+            const T rr = ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2];
             mo.S = mo.S + g;
+            mr.S = mr.S + gr;
             for (int d = 0; d < 3; ++d) {
                 mo.A[d] = mo.A[d] + ra[d] * g;
                 mo.B[d] = mo.B[d] + rb[d] * g;
+                mr.A[d] = mr.A[d] + rb[d] * gr;
+                mr.B[d] = mr.B[d] + ra[d] * gr;
             }
-            mo.C = mo.C + (ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2]) * g;
+            mo.C = mo.C + rr * g;
+            mr.C = mr.C + rr * gr;
         }
     }
     scatter_tt<T>(m, q, Z, N, t, s, mo);
+    if (s != t) scatter_tt<T>(m, q, Z, N, s, t, mr);
 }
 
 // ---------------------------------------------------------------------------
