@@ -366,7 +366,6 @@ template cudaError_t gj_invert<double>(double *, size_t, int, int *, cudaStream_
 // (FP32 matrix, TF32 products with FP32 accumulation).
 // ---------------------------------------------------------------------------
 constexpr int GJ_W = 128;     // pivot block width (the K of the tensor-core update)
-constexpr int GJ_PL = 32;     // panel lines per CTA in the row / column panel kernels
 
 // In-place Gauss-Jordan inverse of the w x w (w <= GJ_W) pivot block, held in
 // registers: thread t owns column c = t % 128 and rows g + 8q (g = t / 128,
@@ -432,73 +431,6 @@ __global__ void __launch_bounds__(GJ_W * GJ_DG) k_gj_diag_w(float *A, size_t ld,
     }
 }
 
-// row panel (ROW): A[k0+i][c] <- sum_q P[i][q] A[k0+q][c]  for GJ_PL columns c per CTA
-// column panel   : A[r][k0+j] <- -sum_q A[r][k0+q] P[q][j] for GJ_PL rows r per CTA
-// (columns / rows outside the pivot block; P = the inverted pivot block)
-template <bool ROW>
-__global__ void __launch_bounds__(256) k_gj_panel(float *A, size_t ld, int n, int k0, int w) {
-    extern __shared__ float pan_smem[];
-    float *P = pan_smem;                          // [w][w][2]
-    float *Tt = pan_smem + 2 * GJ_W * GJ_W;       // [GJ_PL][w + 1][2]: line l, pivot index q
-    const int tw = w + 1;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i = e / w, j = e % w;
-        P[2 * (i * w + j)] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
-        P[2 * (i * w + j) + 1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
-    }
-    const int m = n - w;
-    const int base = blockIdx.x * GJ_PL;
-    for (int e = threadIdx.x; e < GJ_PL * w; e += blockDim.x) {
-        float vr = 0.f, vi = 0.f;
-        int l, q;
-        if (ROW) {   // coalesced along the row of pivot index q
-            q = e / GJ_PL; l = e % GJ_PL;
-            const int jj = base + l;
-            if (jj < m) {
-                const int c = jj < k0 ? jj : jj + w;
-                vr = A[2 * ((size_t)(k0 + q) * ld + c)];
-                vi = A[2 * ((size_t)(k0 + q) * ld + c) + 1];
-            }
-        } else {     // coalesced along the row segment of line l
-            l = e / w; q = e % w;
-            const int jj = base + l;
-            if (jj < m) {
-                const int r = jj < k0 ? jj : jj + w;
-                vr = A[2 * ((size_t)r * ld + k0 + q)];
-                vi = A[2 * ((size_t)r * ld + k0 + q) + 1];
-            }
-        }
-        Tt[2 * (l * tw + q)] = vr;
-        Tt[2 * (l * tw + q) + 1] = vi;
-    }
-    __syncthreads();
-    // thread: line l = tid % GJ_PL, outputs o = tid / GJ_PL + 8 t
-    const int l = threadIdx.x % GJ_PL;
-    const int jj = base + l;
-    for (int o = threadIdx.x / GJ_PL; o < w; o += blockDim.x / GJ_PL) {
-        float sr = 0.f, si = 0.f;
-        for (int q = 0; q < w; ++q) {
-            const float tr = Tt[2 * (l * tw + q)], ti = Tt[2 * (l * tw + q) + 1];
-            // ROW: P[o][q] * T[q];  COL: T[q] * P[q][o]
-            const float pr = ROW ? P[2 * (o * w + q)] : P[2 * (q * w + o)];
-            const float pi = ROW ? P[2 * (o * w + q) + 1] : P[2 * (q * w + o) + 1];
-            sr = fmaf(pr, tr, fmaf(-pi, ti, sr));
-            si = fmaf(pr, ti, fmaf(pi, tr, si));
-        }
-        if (jj < m) {
-            if (ROW) {
-                const int c = jj < k0 ? jj : jj + w;
-                A[2 * ((size_t)(k0 + o) * ld + c)] = sr;
-                A[2 * ((size_t)(k0 + o) * ld + c) + 1] = si;
-            } else {
-                const int r = jj < k0 ? jj : jj + w;
-                A[2 * ((size_t)r * ld + k0 + o)] = -sr;
-                A[2 * ((size_t)r * ld + k0 + o) + 1] = -si;
-            }
-        }
-    }
-}
-
 namespace {
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -540,20 +472,24 @@ size_t gj_pack_floats(int n) {
     return 3 * mp * TC_PACK_ROW;
 }
 
+// One Gauss-Jordan step with pivot block P = A[k0:k0+w, k0:k0+w] (rows and
+// columns outside it: the trailing set T):
+//   1. P <- P^-1                                  (k_gj_diag_w, registers)
+//   2. A[T, P] <- -A[T, P] P^-1                   (product (a): trailing rows x pivot columns, beta 0)
+//   3. A[T, T] <- A[T, T] + A[T, P] A[P, T],  A[P, T] <- P^-1 A[P, T]
+//      as one product over all rows in natural order (the pivot rows' A operand
+//      is P^-1) x the trailing columns, beta 0 on the pivot tile row
+// Products (a) and (3) run on the tensor cores from packed operands.
 cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, KernelTimer *kt) {
-    const int psz = (2 * GJ_W * GJ_W + 2 * GJ_PL * (GJ_W + 1)) * (int)sizeof(float);
-    static_assert(GJ_W == TC_KP, "the packed panels hold one pivot block");
+    static_assert(GJ_W == TC_KP, "the packed operands hold one pivot block");
     static_assert(GJ_W == 128, "k_gj_diag_w maps its threads onto 128 columns");
     int dev = 0, sms = 0;
     {   // opt in to the large dynamic shared memory (per device, cheap to repeat)
         cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, psz);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gj_panel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, psz);
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
     }
-    // packed panels (zero padded to 128-row tiles) and the tensor maps of this block
     const int mpmax = (n + TC_TM - 1) / TC_TM * TC_TM;
     float *Ap = pack, *Bp = pack + (size_t)mpmax * TC_PACK_ROW;
     CUtensorMap tmA, tmB, tmC, tmCs;
@@ -564,27 +500,30 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
             !tensor_map(&tmCs, A, 2 * (uint64_t)ld, n, 8 * ld, 32, 32))
             return cudaErrorInvalidValue;
     }
+    auto tiles = [](int r, int c) { return ((r + TC_TM - 1) / TC_TM) * ((c + TC_TN - 1) / TC_TN); };
     for (int k0 = 0; k0 < n; k0 += GJ_W) {
         const int w = (n - k0 < GJ_W) ? n - k0 : GJ_W;
         k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(A, ld, k0, w, status); ++g_launches;
         const int m = n - w;
-        if (m > 0) {
-            const int nb = (m + GJ_PL - 1) / GJ_PL;
-            k_gj_panel<true><<<nb, 256, psz, st>>>(A, ld, n, k0, w); ++g_launches;
-            const int mp = (m + TC_TM - 1) / TC_TM * TC_TM;
-            const int ntiles = (mp / TC_TM) * (mp / TC_TM);
-            cudaEvent_t e0 = kt ? kt->next() : nullptr, e1 = kt ? kt->next() : nullptr;
-            if (e0) cudaEventRecord(e0, st);
-            k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, m, k0, w, mp, Ap); ++g_launches;
-            k_tc_pack_b<<<dim3(mp / 32, TC_KP / 32), 256, 0, st>>>(A, ld, m, k0, w, Bp); ++g_launches;
-            k_tc_update<<<std::min(ntiles, sms), TC_THREADS, TC_SMEM, st>>>(tmA, tmB, tmC, tmCs, m, k0, w, status); ++g_launches;
-            if (e1) {
-                cudaEventRecord(e1, st);
-                // algorithmic bytes: read-modify-write of the m x m trailing matrix and one
-                // read of the two m x w panels (complex FP32)
-                kt->add(e0, e1, 16.0 * m * (double)m + 16.0 * m * (double)w);
-            }
-            k_gj_panel<false><<<nb, 256, psz, st>>>(A, ld, n, k0, w); ++g_launches;
+        if (m <= 0) continue;
+        const int mp = (m + TC_TM - 1) / TC_TM * TC_TM;
+        cudaEvent_t e0 = kt ? kt->next() : nullptr, e1 = kt ? kt->next() : nullptr;
+        if (e0) cudaEventRecord(e0, st);
+        // (a) column panel: A[T, P] <- A[T, P] (-P^-1)
+        k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, m, k0, w, k0, w, mp, Ap); ++g_launches;
+        k_tc_pack_b<<<dim3(TC_TN / 32, TC_KP / 32), 256, 0, st>>>(A, ld, w, k0, w, 0, k0, -1.f, Bp); ++g_launches;
+        const TcMap ma = {m, w, k0, w, 0, k0, -1, 1};
+        k_tc_update<<<std::min(tiles(m, w), sms), TC_THREADS, TC_SMEM, st>>>(tmA, tmB, tmC, tmCs, ma, status); ++g_launches;
+        // (3) trailing update and row panel in one product over all n rows
+        k_tc_pack_a<<<(unsigned)((size_t)mpmax * TC_KP / 256), 256, 0, st>>>(A, ld, n, k0, w, n, 0, mpmax, Ap); ++g_launches;
+        k_tc_pack_b<<<dim3(mp / 32, TC_KP / 32), 256, 0, st>>>(A, ld, m, k0, w, k0, w, 1.f, Bp); ++g_launches;
+        const TcMap mb = {n, m, n, 0, k0, w, k0 / TC_TM, 0};
+        k_tc_update<<<std::min(tiles(n, m), sms), TC_THREADS, TC_SMEM, st>>>(tmA, tmB, tmC, tmCs, mb, status); ++g_launches;
+        if (e1) {
+            cudaEventRecord(e1, st);
+            // algorithmic bytes: read and write of the n x m updated columns and of the
+            // m x w column panel, one read of the pivot block (complex FP32)
+            kt->add(e0, e1, 16.0 * n * (double)m + 16.0 * m * (double)w + 8.0 * w * (double)w);
         }
     }
     return cudaGetLastError();
@@ -619,36 +558,53 @@ template cudaError_t copy_block<double, double>(const double *, size_t, int, int
 // ---------------------------------------------------------------------------
 // GMRES vector kernels (two right-hand sides, [n][2] complex)
 // ---------------------------------------------------------------------------
-// h[j][r] += sum_i conj(V_j[i][r]) w[i][r]  for j < nv (atomics into FP64)
+// h[j][r] += sum_i conj(V_j[i][r]) w[i][r]  for j < nv (atomics into FP64).
+// Grid (chunks of DOT_CHUNK elements) x (vectors): every CTA streams one chunk
+// of one basis vector with 16-byte loads, reduces in FP64 and adds 4 numbers.
+constexpr int DOT_CHUNK = 2048;
+
+__device__ __forceinline__ void load4(const float *p, double o[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double *p, double o[4]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
 template <typename TV>
-__global__ void k_dots(const TV *V, size_t vstride, int nv, const TV *w, int n, double *h) {
+__global__ void __launch_bounds__(256) k_dots(const TV *V, size_t vstride, int nv, const TV *w, int n, double *h) {
     __shared__ double red[8][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = 0; j < nv; ++j) {
-        const TV *v = V + j * vstride;
-        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-            const double vr0 = v[4 * i], vi0 = v[4 * i + 1], vr1 = v[4 * i + 2], vi1 = v[4 * i + 3];
-            const double wr0 = w[4 * i], wi0 = w[4 * i + 1], wr1 = w[4 * i + 2], wi1 = w[4 * i + 3];
-            a0 += vr0 * wr0 + vi0 * wi0;
-            a1 += vr0 * wi0 - vi0 * wr0;
-            a2 += vr1 * wr1 + vi1 * wi1;
-            a3 += vr1 * wi1 - vi1 * wr1;
+    const int j = blockIdx.y;
+    const TV *v = V + (size_t)j * vstride;
+    const int base = blockIdx.x * DOT_CHUNK;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+    for (int u = 0; u < DOT_CHUNK / 256; ++u) {
+        const int i = base + u * 256 + threadIdx.x;
+        if (i < n) {
+            double x[4], y[4];
+            load4(v + 4 * (size_t)i, x);
+            load4(w + 4 * (size_t)i, y);
+            a0 += x[0] * y[0] + x[1] * y[1];
+            a1 += x[0] * y[1] - x[1] * y[0];
+            a2 += x[2] * y[2] + x[3] * y[3];
+            a3 += x[2] * y[3] - x[3] * y[2];
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_down_sync(0xffffffffu, a0, o);
-            a1 += __shfl_down_sync(0xffffffffu, a1, o);
-            a2 += __shfl_down_sync(0xffffffffu, a2, o);
-            a3 += __shfl_down_sync(0xffffffffu, a3, o);
-        }
-        if (lane == 0) { red[warp][0] = a0; red[warp][1] = a1; red[warp][2] = a2; red[warp][3] = a3; }
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            double s = 0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q][threadIdx.x];
-            atomicAdd(h + 4 * j + threadIdx.x, s);
-        }
-        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_down_sync(0xffffffffu, a0, o);
+        a1 += __shfl_down_sync(0xffffffffu, a1, o);
+        a2 += __shfl_down_sync(0xffffffffu, a2, o);
+        a3 += __shfl_down_sync(0xffffffffu, a3, o);
+    }
+    if (lane == 0) { red[warp][0] = a0; red[warp][1] = a1; red[warp][2] = a2; red[warp][3] = a3; }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s2 = 0;
+        for (int q = 0; q < 8; ++q) s2 += red[q][threadIdx.x];
+        atomicAdd(h + 4 * j + threadIdx.x, s2);
     }
 }
 
@@ -707,8 +663,9 @@ __global__ void k_combine(const TV *V, size_t vstride, int nv, const double *y, 
 
 template <typename TV>
 cudaError_t dots(const TV *V, size_t vstride, int nv, const TV *w, int n, double *h, cudaStream_t st) {
+    if (nv <= 0 || n <= 0) return cudaSuccess;
     cudaMemsetAsync(h, 0, sizeof(double) * 4 * nv, st);
-    k_dots<TV><<<296, 256, 0, st>>>(V, vstride, nv, w, n, h); ++g_launches;
+    k_dots<TV><<<dim3((n + DOT_CHUNK - 1) / DOT_CHUNK, nv), 256, 0, st>>>(V, vstride, nv, w, n, h); ++g_launches;
     return cudaGetLastError();
 }
 template <typename TV>

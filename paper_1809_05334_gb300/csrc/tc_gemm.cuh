@@ -1,15 +1,18 @@
-// Complex FP32 trailing update C <- C - A B of the Gauss-Jordan inversion of
-// the domain blocks of Eq. (6), on the 5th-generation tensor cores (tcgen05,
-// kind::tf32, accumulators in tensor memory), with every operand moved by TMA.
+// Complex FP32 products C <- beta C + A B (K <= 128) of the Gauss-Jordan
+// inversion of the domain blocks of Eq. (6), on the 5th-generation tensor
+// cores (tcgen05, kind::tf32, accumulators in tensor memory), with every
+// operand moved by TMA.
 //
 // A complex product is one real product of the real views:
 //   C_rv (M x 2N) += A_rv (M x 2K) * Bt (2K x 2N)
 // where the real view of a row-major complex matrix interleaves (re, im) and
-// Bt is minus the 2x2 real expansion of B.  Per pivot step a pack kernel writes
-//   Ap [mp][2 KP]    row r: the pivot columns of trailing row r (TF32-rounded)
-//   Bp [2 mp][2 KP]  rows 2j, 2j+1: (-Re B, Im B), (-Im B, -Re B) per pivot k
+// Bt is the 2x2 real expansion of B (times a sign).  Pack kernels write
+//   Ap [mp][2 KP]    row r: K complex entries of the r-th row of A (TF32-rounded)
+//   Bp [2 np][2 KP]  rows 2j, 2j+1: s (Re b, -Im b), s (Im b, Re b), b = B[k][j]
 // so that both operands are K-major and TMA-loadable (zero padded to 128-row
-// tiles and to KP = 128 pivots).
+// tiles and to KP = 128).  Rows and columns of C are addressed through
+// skip maps (index i < at ? i : i + skip), so a product can cover the trailing
+// rows/columns around a pivot block, the pivot columns alone, or all rows.
 //
 // k_tc_update is persistent (one CTA per SM, tiles of 128 x 128 complex taken
 // round-robin) and warp-specialised:
@@ -114,36 +117,37 @@ __device__ __forceinline__ void mma_commit(uint64_t *mbar) {
                  ::"r"(smem_u32(mbar)) : "memory");
 }
 
-// Pack the pivot column panel of the trailing rows: Ap[r][2k..2k+1] = A[row(r)][k0+k]
-// for r < m, k < w (row(r) = r < k0 ? r : r + w), zero elsewhere up to mp rows.
-__global__ void __launch_bounds__(256) k_tc_pack_a(const float *__restrict__ A, size_t ld, int m, int k0, int w,
-                                                   int mp, float *__restrict__ Ap) {
+// Ap[r][2k..2k+1] = A[row(r)][col0 + k] for r < rows, k < w, with
+// row(r) = r < at ? r : r + skip; zero elsewhere up to mp rows.
+__global__ void __launch_bounds__(256) k_tc_pack_a(const float *__restrict__ A, size_t ld, int rows, int col0, int w,
+                                                   int at, int skip, int mp, float *__restrict__ Ap) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)mp * TC_KP) return;
     const int r = (int)(e / TC_KP), k = (int)(e % TC_KP);
     float2 v = make_float2(0.f, 0.f);
-    if (r < m && k < w) {
-        const int gr = r < k0 ? r : r + w;
-        v = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)gr * ld + k0 + k));
+    if (r < rows && k < w) {
+        const int gr = r < at ? r : r + skip;
+        v = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)gr * ld + col0 + k));
     }
     *reinterpret_cast<float2 *>(Ap + (size_t)r * TC_PACK_ROW + 2 * k) = make_float2(to_tf32(v.x), to_tf32(v.y));
 }
 
-// Pack minus the real expansion of the pivot row panel, K-major: for trailing
-// column j (col(j) = j < k0 ? j : j + w) and pivot k, with b = A[k0+k][col(j)]:
-//   Bp[2j][2k..] = (-Re b, Im b),  Bp[2j+1][2k..] = (-Im b, -Re b)
-// through a 32 x 32 shared-memory transpose (coalesced on both sides).
-__global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, size_t ld, int m, int k0, int w,
-                                                   float *__restrict__ Bp) {
+// The sign-scaled real expansion of B[k][j] = A[row0 + k][col(j)] (k < w,
+// j < cols, col(j) = j < at ? j : j + skip), K-major:
+//   Bp[2j][2k..] = sgn (Re b, -Im b),  Bp[2j+1][2k..] = sgn (Im b, Re b)
+// through a 32 x 32 shared-memory transpose (coalesced on both sides); rows up
+// to 2 * 32 * gridDim.x are written (zero beyond cols).
+__global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, size_t ld, int cols, int row0, int w,
+                                                   int at, int skip, float sgn, float *__restrict__ Bp) {
     __shared__ float2 t[32][33];
     const int j0 = blockIdx.x * 32, kb = blockIdx.y * 32;
     for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
         const int kk = idx / 32, jj = idx % 32;
         const int j = j0 + jj, k = kb + kk;
         float2 v = make_float2(0.f, 0.f);
-        if (j < m && k < w) {
-            const int gc = j < k0 ? j : j + w;
-            v = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)(k0 + k) * ld + gc));
+        if (j < cols && k < w) {
+            const int gc = j < at ? j : j + skip;
+            v = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)(row0 + k) * ld + gc));
         }
         t[kk][jj] = v;
     }
@@ -152,15 +156,23 @@ __global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, 
         const int jj = idx / 32, kk = idx % 32;
         const float2 v = t[kk][jj];
         const size_t j = (size_t)(j0 + jj), k = (size_t)(kb + kk);
-        *reinterpret_cast<float2 *>(Bp + (2 * j) * TC_PACK_ROW + 2 * k) = make_float2(to_tf32(-v.x), to_tf32(v.y));
+        *reinterpret_cast<float2 *>(Bp + (2 * j) * TC_PACK_ROW + 2 * k) =
+            make_float2(to_tf32(sgn * v.x), to_tf32(-sgn * v.y));
         *reinterpret_cast<float2 *>(Bp + (2 * j + 1) * TC_PACK_ROW + 2 * k) =
-            make_float2(to_tf32(-v.y), to_tf32(-v.x));
+            make_float2(to_tf32(sgn * v.y), to_tf32(sgn * v.x));
     }
 }
 
-// C <- C + Ap * Bp^T over the m x m trailing matrix (rows and columns outside the
-// pivot block [k0, k0+w); k0 is a multiple of 128 and the update never
-// straddles it).  tmA, tmB: the packed panels (box 32 floats x 128 / 256 rows);
+// Index maps and scaling of one product: C rows r < mrows at row(r) =
+// r < rat ? r : r + rskip, columns c < ncols at col(c) = c < cat ? c : c + cskip
+// (rat, cat multiples of 128 or beyond the extent, so no tile straddles a
+// skip); beta = 0 on every tile if beta0_all, else on tile row beta0_row.
+struct TcMap {
+    int mrows, ncols, rat, rskip, cat, cskip, beta0_row, beta0_all;
+};
+
+// C <- beta C + Ap * Bp^T over the tiles of the map.  tmA, tmB: the packed
+// operands (box 32 floats x 128 / 256 rows);
 // tmC: the block [n rows][2 ld floats] (box 32 x 128, loads); tmCs: the same
 // with a 32 x 32 box (stores of one epilogue warp).  All four use SWIZZLE_128B.
 // The maps span whole padded rows (a multiple of 16 bytes), so a box that
@@ -169,8 +181,8 @@ __global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, 
 // back the value it loaded.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmCs, int m, int k0,
-                int w, int *err) {
+                const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmCs, const TcMap mp,
+                int *err) {
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = base;                                              // [stage] 16 KB
@@ -183,8 +195,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nt = (m + TC_TM - 1) / TC_TM;
-    const int ntiles = nt * nt;
+    const int ntm = (mp.mrows + TC_TM - 1) / TC_TM, nt = (mp.ncols + TC_TN - 1) / TC_TN;
+    const int ntiles = ntm * nt;
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
@@ -271,7 +283,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int ty = t / nt, tx = t % nt;
             const int r0 = ty * TC_TM, c0 = tx * TC_TN;
-            const int gr0 = r0 < k0 ? r0 : r0 + w, gc0 = c0 < k0 ? c0 : c0 + w;
+            const int gr0 = r0 < mp.rat ? r0 : r0 + mp.rskip, gc0 = c0 < mp.cat ? c0 : c0 + mp.cskip;
             for (int cc = 0; cc < TC_NCHUNK; ++cc, ++ci) {
                 const int s = ci % TC_CSLOTS;
                 if (ci >= TC_CSLOTS && !mbar_wait(cempty + s, (uint32_t)((ci / TC_CSLOTS - 1) & 1))) { ok = false; break; }
@@ -293,7 +305,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
             const int ty = t / nt, tx = t % nt;
             const int r0 = ty * TC_TM, c0 = tx * TC_TN;
-            const int gr0 = r0 < k0 ? r0 : r0 + w, gc0 = c0 < k0 ? c0 : c0 + w;
+            const int gr0 = r0 < mp.rat ? r0 : r0 + mp.rskip, gc0 = c0 < mp.cat ? c0 : c0 + mp.cskip;
+            const bool keep = !(mp.beta0_all || ty == mp.beta0_row);   // beta = 1 (else the product alone)
             const int b = tl & 1;
             if (!__all_sync(0xffffffffu, mbar_wait(accfull + b, (uint32_t)((tl / 2) & 1)))) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -318,7 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     float4 *p = reinterpret_cast<float4 *>(rp + ((q ^ (row & 7)) << 4));
-                    float4 c = *p;
+                    float4 c = keep ? *p : make_float4(0.f, 0.f, 0.f, 0.f);
                     c.x += __uint_as_float(v[4 * q]);
                     c.y += __uint_as_float(v[4 * q + 1]);
                     c.z += __uint_as_float(v[4 * q + 2]);
