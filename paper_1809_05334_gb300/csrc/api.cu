@@ -503,6 +503,12 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
         }
         int kused[2] = {0, 0};
         bool inner_active[2] = {active[0] && beta[0] > 0, active[1] && beta[1] > 0};
+        // stop a sweep once the preconditioned residual has dropped by inner_tol,
+        // or once it predicts the outer target: the FP64 residual at the end of the
+        // sweep is expected near (|g| / beta) |r|, and half of tol |b| is aimed for
+        double stop[2];
+        for (int p = 0; p < 2; ++p)
+            stop[p] = std::max(inner_tol, rn[p] > 0 ? 0.5 * tol * bn[p] / rn[p] : 0.0) * beta[p];
         for (int k = 0; k < m; ++k) {
             if (!inner_active[0] && !inner_active[1]) break;
             TV *vk = V + vs * k;
@@ -546,7 +552,7 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
                 g[p][k] = std::conj(cs[p][k]) * g[p][k];
                 kused[p] = k + 1;
                 ++iters[p];
-                if (std::abs(g[p][k + 1]) <= inner_tol * beta[p] || hn[p] <= 1e-300) inner_active[p] = false;
+                if (std::abs(g[p][k + 1]) <= stop[p] || hn[p] <= 1e-300) inner_active[p] = false;
                 if (hn[p] > 0) sc[2 * p] = 1.0 / hn[p];
             }
             ++total;
