@@ -82,6 +82,7 @@ struct MeshState {
     vie::Topology topo;
     DevBuf tv, cen, vol, q5, far32, far64, fv, f5, farea, ffar32, ffar64, hf, n32, n64, fn32, fn64, fcen;
     DevBuf mk[4], pr[4], to[4], tdom, tpart;
+    DevBuf thalf, tsc[4];   // static integrals of the touching near images (per mesh)
     int npr[4] = {0, 0, 0, 0}, nto[4] = {0, 0, 0, 0};
 };
 
@@ -92,7 +93,6 @@ struct vie_ctx {
     std::shared_ptr<MeshState> mesh = std::make_shared<MeshState>();
     // request (device)
     DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab, ew;
-    DevBuf thalf;   // per-request scratch of the touching-pair kernels
     double z_extent = 0;
     // solve buffers
     DevBuf Z, b, x, r, u, w, V, h, y, Minv, tcpack, status, acc, J, rt, cout;
@@ -387,7 +387,8 @@ vie::DevMesh dev_mesh(vie_ctx *ctx) {
     m.mk_tt = ctx->mesh->mk[0].as<uint16_t>(); m.mk_tf = ctx->mesh->mk[1].as<uint16_t>();
     m.mk_ft = ctx->mesh->mk[2].as<uint16_t>(); m.mk_ff = ctx->mesh->mk[3].as<uint16_t>();
     m.touch_partner = ctx->mesh->tpart.as<int32_t>();
-    m.touch_half = ctx->thalf.as<double>();
+    m.touch_half = ctx->mesh->thalf.as<double>();
+    for (int i = 0; i < 4; ++i) m.touch_sc[i] = ctx->mesh->tsc[i].as<double>();
     for (int i = 0; i < 4; ++i) {
         m.pr[i] = ctx->mesh->pr[i].as<vie::NearEntry>();
         m.to[i] = ctx->mesh->to[i].as<vie::NearEntry>();
@@ -410,9 +411,7 @@ int fill(vie_ctx *ctx, const vie::DevMesh &m, const vie::DevReq &q, bool with_rh
     ctx->ld = (N + 3) / 4 * 4;
     CK(ctx->Z.ensure(sizeof(TZ) * 2 * ctx->ld * N));
     if (with_rhs) CK(ctx->b.ensure(sizeof(double) * 4 * N));
-    CK(ctx->thalf.ensure(sizeof(double) * 8 * std::max(ctx->mesh->nto[0], 1)));
-    vie::DevMesh mm = m;
-    mm.touch_half = ctx->thalf.as<double>();
+    const vie::DevMesh &mm = m;
     if (tm && tm->fill0) CK(cudaEventRecord(tm->fill0, st));
     CK(vie::launch_fill<TZ>(mm, q, ctx->Z.as<TZ>(), ctx->ld, with_rhs ? ctx->b.as<double>() : nullptr, st,
                             tm ? tm->far0 : nullptr, tm ? tm->far1 : nullptr));
@@ -948,6 +947,18 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
             CK(upload(ctx->mesh->tpart, part, st));
         }
     }
+    // static integrals of the touching near images: geometry only, once per mesh
+    CK(ctx->mesh->thalf.ensure(sizeof(double) * 8 * std::max(ctx->mesh->nto[0], 1)));
+    double *tsc[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int i = 1; i < 4; ++i) {
+        CK(ctx->mesh->tsc[i].ensure(sizeof(double) * std::max(ctx->mesh->nto[i], 1)));
+        tsc[i] = ctx->mesh->tsc[i].as<double>();
+    }
+    {
+        const vie::DevMesh dm = dev_mesh(ctx);
+        CK(vie::launch_static_cache(dm, ctx->mesh->thalf.as<double>(), tsc, st));
+        CK(cudaStreamSynchronize(st));
+    }
     ctx->mesh->have_mesh = true;
     return VIE_OK;
 }
@@ -1168,7 +1179,7 @@ void release_device_memory(vie_ctx *ctx) {
     ctx->slots.clear();
     ctx->mesh = std::make_shared<MeshState>();
     DevBuf *bufs[] = {&ctx->row, &ctx->coef, &ctx->wt, &ctx->kap, &ctx->ieps, &ctx->frow, &ctx->qs,
-                      &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->ew, &ctx->thalf,
+                      &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->ew,
                       &ctx->Z, &ctx->b, &ctx->x, &ctx->r, &ctx->u, &ctx->w, &ctx->V, &ctx->h, &ctx->y,
                       &ctx->Minv, &ctx->tcpack, &ctx->status, &ctx->acc, &ctx->J, &ctx->rt, &ctx->cout};
     for (DevBuf *b : bufs) b->release();

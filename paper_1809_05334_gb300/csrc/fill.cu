@@ -602,9 +602,11 @@ __global__ void __launch_bounds__(128) k_pr_scalar(DevMesh m, const __grid_const
     scatter_scalar<T, PK>(m, q, Z, N, x, y, s0 * cx<T>{T(q.img_ph[2 * k]), T(q.img_ph[2 * k + 1])});
 }
 
-template <typename T, int PK>
-__global__ void __launch_bounds__(128) k_touch_scalar(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N, const NearEntry *list,
-                                                      int n) {
+// Touching face entries: the static integral, both integration orders
+// averaged, summed over the degree-5 points (phase-free, FP64; one warp per
+// entry, lanes = the points of the two elements).  Request independent.
+template <int PK>
+__global__ void __launch_bounds__(128) k_touch_scalar(DevMesh m, const NearEntry *list, int n, double *out) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= n) return;
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(128) k_touch_scalar(DevMesh m, const __grid_co
     const double *y5 = YT ? m.q5 + (size_t)yf * 42 : m.f5 + (size_t)yf * 21;
     const double mx = XT ? m.vol[xf] : m.farea[xf];
     const double my = YT ? m.vol[yf] : m.farea[yf];
-    cx<double> acc = {0, 0};
+    double acc = 0;
     if (lane < nqx + nqy) {
         const double R[3] = {(k / 3 - 1) * m.a, (k % 3 - 1) * m.b, 0.0};
         const bool oi = lane < nqx;
@@ -630,11 +632,23 @@ __global__ void __launch_bounds__(128) k_touch_scalar(DevMesh m, const __grid_co
         const double w = (oi ? mx : my) * (self_tet ? c_w5tet[qi] : c_w5tri[qi]);
         const double *vo = other_tet ? m.tv + 12 * (size_t)other : m.fv + 9 * (size_t)other;
         const double I = static_scalar<double>(r5, other_tet, vo, R, oi ? -1.0 : 1.0);
-        acc.re = 0.5 * w * q.img_ph[2 * k] * I;
-        acc.im = 0.5 * w * q.img_ph[2 * k + 1] * I;
+        acc = 0.5 * w * I;
     }
-    const double sr = warp_sum(acc.re), si = warp_sum(acc.im);
-    if (lane == 0) scatter_scalar<T, PK>(m, q, Z, N, x, y, cx<T>{T(sr), T(si)});
+    const double sum = warp_sum(acc);
+    if (lane == 0) out[wid] = sum;
+}
+
+// scatter the cached static integral of every touching face entry with the
+// request's image phase exp(j k_par.R)/(4 pi)
+template <typename T, int PK>
+__global__ void __launch_bounds__(128) k_touch_apply(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N,
+                                                     const NearEntry *list, const double *sc, int n) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const NearEntry en = list[e];
+    const double v = sc[e];
+    scatter_scalar<T, PK>(m, q, Z, N, en.x, en.y,
+                          cx<T>{T(v * q.img_ph[2 * en.k]), T(v * q.img_ph[2 * en.k + 1])});
 }
 
 // ---------------------------------------------------------------------------
@@ -735,27 +749,37 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
     k_far_tt<T><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N); ++g_launches;
     if (far1) cudaEventRecord(far1, st);
     auto grid1 = [](int n) { return (unsigned)((n + 127) / 128); };
-    auto gridw = [](int n) { return (unsigned)(((size_t)n * 32 + 127) / 128); };
     if (m.npr[0]) { k_pr_tt<T><<<grid1(m.npr[0]), blk, 0, st>>>(m, q, Z, N, m.pr[0], m.npr[0]); ++g_launches; }
     if (m.nto[0]) {
-        k_touch_half<<<(unsigned)(((size_t)(m.nto[0] + 1) / 2 * 32 + 127) / 128), blk, 0, st>>>(m, m.to[0], m.nto[0],
-                                                                                              m.touch_half); ++g_launches;
         k_touch_combine<T><<<grid1(m.nto[0]), blk, 0, st>>>(m, q, Z, N, m.to[0], m.touch_partner, m.touch_half,
                                                             m.nto[0]); ++g_launches;
     }
     if (m.nf) {
         k_far_scalar<T, PK_TF><<<dim3((m.nf + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N, m.nt, m.nf, m.mk_tf); ++g_launches;
         if (m.npr[1]) { k_pr_scalar<T, PK_TF><<<grid1(m.npr[1]), blk, 0, st>>>(m, q, Z, N, m.pr[1], m.npr[1]); ++g_launches; }
-        if (m.nto[1]) { k_touch_scalar<T, PK_TF><<<gridw(m.nto[1]), blk, 0, st>>>(m, q, Z, N, m.to[1], m.nto[1]); ++g_launches; }
+        if (m.nto[1]) { k_touch_apply<T, PK_TF><<<grid1(m.nto[1]), blk, 0, st>>>(m, q, Z, N, m.to[1], m.touch_sc[1], m.nto[1]); ++g_launches; }
     }
     if (m.nh) {
         k_far_scalar<T, PK_FT><<<dim3((m.nt + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nt, m.mk_ft); ++g_launches;
         if (m.npr[2]) { k_pr_scalar<T, PK_FT><<<grid1(m.npr[2]), blk, 0, st>>>(m, q, Z, N, m.pr[2], m.npr[2]); ++g_launches; }
-        if (m.nto[2]) { k_touch_scalar<T, PK_FT><<<gridw(m.nto[2]), blk, 0, st>>>(m, q, Z, N, m.to[2], m.nto[2]); ++g_launches; }
+        if (m.nto[2]) { k_touch_apply<T, PK_FT><<<grid1(m.nto[2]), blk, 0, st>>>(m, q, Z, N, m.to[2], m.touch_sc[2], m.nto[2]); ++g_launches; }
         k_far_scalar<T, PK_FF><<<dim3((m.nf + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nf, m.mk_ff); ++g_launches;
         if (m.npr[3]) { k_pr_scalar<T, PK_FF><<<grid1(m.npr[3]), blk, 0, st>>>(m, q, Z, N, m.pr[3], m.npr[3]); ++g_launches; }
-        if (m.nto[3]) { k_touch_scalar<T, PK_FF><<<gridw(m.nto[3]), blk, 0, st>>>(m, q, Z, N, m.to[3], m.nto[3]); ++g_launches; }
+        if (m.nto[3]) { k_touch_apply<T, PK_FF><<<grid1(m.nto[3]), blk, 0, st>>>(m, q, Z, N, m.to[3], m.touch_sc[3], m.nto[3]); ++g_launches; }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_static_cache(const DevMesh &m, double *touch_half, double *const touch_sc[4], cudaStream_t st) {
+    const dim3 blk(128);
+    auto gridw = [](int n) { return (unsigned)(((size_t)n * 32 + 127) / 128); };
+    if (m.nto[0]) {
+        k_touch_half<<<(unsigned)(((size_t)(m.nto[0] + 1) / 2 * 32 + 127) / 128), blk, 0, st>>>(m, m.to[0], m.nto[0],
+                                                                                              touch_half); ++g_launches;
+    }
+    if (m.nto[1]) { k_touch_scalar<PK_TF><<<gridw(m.nto[1]), blk, 0, st>>>(m, m.to[1], m.nto[1], touch_sc[1]); ++g_launches; }
+    if (m.nto[2]) { k_touch_scalar<PK_FT><<<gridw(m.nto[2]), blk, 0, st>>>(m, m.to[2], m.nto[2], touch_sc[2]); ++g_launches; }
+    if (m.nto[3]) { k_touch_scalar<PK_FF><<<gridw(m.nto[3]), blk, 0, st>>>(m, m.to[3], m.nto[3], touch_sc[3]); ++g_launches; }
     return cudaGetLastError();
 }
 

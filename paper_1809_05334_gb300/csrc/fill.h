@@ -41,7 +41,10 @@ struct DevMesh {
     const NearEntry *pr[4], *to[4];
     int npr[4], nto[4];
     const int32_t *touch_partner;   // [nto[0]] index of the entry (y, x, 8-k)
-    double *touch_half;             // [nto[0]][8] scratch: one integration order per entry
+    // static (phase-free) integrals of the touching near images, a property of
+    // the mesh alone: computed once by launch_static_cache, read by every fill
+    const double *touch_half;       // [nto[0]][8] one integration order per tetrahedron entry
+    const double *touch_sc[4];      // [nto[i]] (i = 1..3) summed static integral of a face entry
 
     template <typename T> __device__ const T *far(int t) const;
     template <typename T> __device__ const T *ffar(int f) const;
@@ -86,6 +89,9 @@ cudaError_t upload_ewald(EwaldTables *dev, const EwaldTables &t, cudaStream_t st
 template <typename T>
 cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, double *b, cudaStream_t st,
                         cudaEvent_t far0 = nullptr, cudaEvent_t far1 = nullptr);
+// the request-independent static integrals of the touching near images:
+// touch_half [nto[0]][8] and touch_sc[i] [nto[i]] (i = 1..3)
+cudaError_t launch_static_cache(const DevMesh &m, double *touch_half, double *const touch_sc[4], cudaStream_t st);
 cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStream_t st);
 cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const float *stab, const float2 *ztab,
                          const EwaldTables *ew, const EwaldF32 &ef, cudaStream_t st);
