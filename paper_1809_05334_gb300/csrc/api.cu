@@ -105,10 +105,12 @@ struct vie_ctx {
     // own request and solve buffers and its own stream
     std::vector<std::unique_ptr<vie_ctx>> slots;
     cudaStream_t own_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;   // second stream of the block inversion (look-ahead)
     ~vie_ctx() {
         slots.clear();
         for (auto e : events) cudaEventDestroy(e);
         if (own_stream) cudaStreamDestroy(own_stream);
+        if (aux_stream) cudaStreamDestroy(aux_stream);
     }
     cudaEvent_t event() {   // next event of the pool (nullptr when timing is off)
         if (!opt.timing) return nullptr;
@@ -610,11 +612,13 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
     size_t pk = 1;
     for (int nb : H.blk_n) pk = std::max(pk, vie::gj_pack_floats(nb));
     CK(ctx->tcpack.ensure(sizeof(float) * pk));
+    if (!ctx->aux_stream) CK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
     CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
     for (size_t k = 0; k < H.blk_n.size(); ++k) {
         float *B = ctx->Minv.as<float>() + 2 * moff[k];
         CK((vie::copy_block<TZ, float>(ctx->Z.as<TZ>(), ctx->ld, H.blk_off[k], H.blk_n[k], B, mld[k], st)));
-        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), ctx->tcpack.as<float>(), st, kt));
+        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), ctx->tcpack.as<float>(), st,
+                             ctx->aux_stream, kt));
     }
     int stat = 0;
     ctx->d2h += sizeof(int);

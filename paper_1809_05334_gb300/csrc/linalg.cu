@@ -467,9 +467,9 @@ bool tensor_map(CUtensorMap *map, const float *base, uint64_t inner, uint64_t ro
 }
 }  // namespace
 
-size_t gj_pack_floats(int n) {
+size_t gj_pack_floats(int n) {   // two sets (consecutive steps overlap) of Ap [mp] and Bp [2 mp] rows
     const size_t mp = ((size_t)n + TC_TM - 1) / TC_TM * TC_TM;
-    return 3 * mp * TC_PACK_ROW;
+    return 2 * 3 * mp * TC_PACK_ROW;
 }
 
 // One Gauss-Jordan step with pivot block P = A[k0:k0+w, k0:k0+w] (rows and
@@ -480,7 +480,13 @@ size_t gj_pack_floats(int n) {
 //      as one product over all rows in natural order (the pivot rows' A operand
 //      is P^-1) x the trailing columns, beta 0 on the pivot tile row
 // Products (a) and (3) run on the tensor cores from packed operands.
-cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, KernelTimer *kt) {
+// Look-ahead: product (3) is split into the tile column holding the next
+// pivot block (on st) and the rest (on aux, on all SMs but four).  The next
+// step's pivot inverse and column-panel product need only the first part, so
+// they run on st while the rest of (3) streams through HBM; the next row-panel
+// packing waits for it.  Consecutive steps use alternate packing buffers.
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, cudaStream_t aux,
+                         KernelTimer *kt) {
     static_assert(GJ_W == TC_KP, "the packed operands hold one pivot block");
     static_assert(GJ_W == 128, "k_gj_diag_w maps its threads onto 128 columns");
     int dev = 0, sms = 0;
@@ -491,41 +497,79 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
         if (e != cudaSuccess) return e;
     }
     const int mpmax = (n + TC_TM - 1) / TC_TM * TC_TM;
-    float *Ap = pack, *Bp = pack + (size_t)mpmax * TC_PACK_ROW;
-    CUtensorMap tmA, tmB, tmC, tmCs;
+    const size_t set_floats = 3 * (size_t)mpmax * TC_PACK_ROW;
+    float *Ap[2], *Bp[2];
+    CUtensorMap tmA[2], tmB[2], tmC, tmCs;
+    for (int b = 0; b < 2; ++b) {
+        Ap[b] = pack + b * set_floats;
+        Bp[b] = Ap[b] + (size_t)mpmax * TC_PACK_ROW;
+    }
     if (n > GJ_W) {
-        if (!tensor_map(&tmA, Ap, TC_PACK_ROW, mpmax, TC_PACK_ROW * 4, 32, TC_TM) ||
-            !tensor_map(&tmB, Bp, TC_PACK_ROW, 2 * (uint64_t)mpmax, TC_PACK_ROW * 4, 32, 2 * TC_TN) ||
-            !tensor_map(&tmC, A, 2 * (uint64_t)ld, n, 8 * ld, 32, TC_TM) ||
+        for (int b = 0; b < 2; ++b)
+            if (!tensor_map(&tmA[b], Ap[b], TC_PACK_ROW, mpmax, TC_PACK_ROW * 4, 32, TC_TM) ||
+                !tensor_map(&tmB[b], Bp[b], TC_PACK_ROW, 2 * (uint64_t)mpmax, TC_PACK_ROW * 4, 32, 2 * TC_TN))
+                return cudaErrorInvalidValue;
+        if (!tensor_map(&tmC, A, 2 * (uint64_t)ld, n, 8 * ld, 32, TC_TM) ||
             !tensor_map(&tmCs, A, 2 * (uint64_t)ld, n, 8 * ld, 32, 32))
             return cudaErrorInvalidValue;
     }
+    cudaEvent_t evP = nullptr, evB = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&evP, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evB, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
     auto tiles = [](int r, int c) { return ((r + TC_TM - 1) / TC_TM) * ((c + TC_TN - 1) / TC_TN); };
+    // one product on stream s, timed when kt is set; algorithmic bytes: read and
+    // write of the rows x cols block of C, one read of the two operand panels
+    auto product = [&](cudaStream_t s, int b, const TcMap &mp, int grid, double rows, double cols, int w) {
+        cudaEvent_t e0 = kt ? kt->next() : nullptr, e1 = kt ? kt->next() : nullptr;
+        if (e0) cudaEventRecord(e0, s);
+        k_tc_update<<<grid, TC_THREADS, TC_SMEM, s>>>(tmA[b], tmB[b], tmC, tmCs, mp, status); ++g_launches;
+        if (e1) {
+            cudaEventRecord(e1, s);
+            kt->add(e0, e1, 16.0 * rows * cols + 8.0 * (rows + cols) * w);
+        }
+    };
+    bool pending = false;   // the second part of the previous product (3) is running on aux
+    k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(A, ld, 0, std::min(n, GJ_W), status); ++g_launches;
     for (int k0 = 0; k0 < n; k0 += GJ_W) {
         const int w = (n - k0 < GJ_W) ? n - k0 : GJ_W;
-        k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(A, ld, k0, w, status); ++g_launches;
         const int m = n - w;
-        if (m <= 0) continue;
+        if (m <= 0) break;
+        const int cur = (k0 / GJ_W) & 1;
         const int mp = (m + TC_TM - 1) / TC_TM * TC_TM;
-        cudaEvent_t e0 = kt ? kt->next() : nullptr, e1 = kt ? kt->next() : nullptr;
-        if (e0) cudaEventRecord(e0, st);
         // (a) column panel: A[T, P] <- A[T, P] (-P^-1)
-        k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, m, k0, w, k0, w, mp, Ap); ++g_launches;
-        k_tc_pack_b<<<dim3(TC_TN / 32, TC_KP / 32), 256, 0, st>>>(A, ld, w, k0, w, 0, k0, -1.f, Bp); ++g_launches;
-        const TcMap ma = {m, w, k0, w, 0, k0, -1, 1};
-        k_tc_update<<<std::min(tiles(m, w), sms), TC_THREADS, TC_SMEM, st>>>(tmA, tmB, tmC, tmCs, ma, status); ++g_launches;
-        // (3) trailing update and row panel in one product over all n rows
-        k_tc_pack_a<<<(unsigned)((size_t)mpmax * TC_KP / 256), 256, 0, st>>>(A, ld, n, k0, w, n, 0, mpmax, Ap); ++g_launches;
-        k_tc_pack_b<<<dim3(mp / 32, TC_KP / 32), 256, 0, st>>>(A, ld, m, k0, w, k0, w, 1.f, Bp); ++g_launches;
-        const TcMap mb = {n, m, n, 0, k0, w, k0 / TC_TM, 0};
-        k_tc_update<<<std::min(tiles(n, m), sms), TC_THREADS, TC_SMEM, st>>>(tmA, tmB, tmC, tmCs, mb, status); ++g_launches;
-        if (e1) {
-            cudaEventRecord(e1, st);
-            // algorithmic bytes: read and write of the n x m updated columns and of the
-            // m x w column panel, one read of the pivot block (complex FP32)
-            kt->add(e0, e1, 16.0 * n * (double)m + 16.0 * m * (double)w + 8.0 * w * (double)w);
+        k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, m, k0, w, k0, w, mp, Ap[cur]); ++g_launches;
+        k_tc_pack_b<<<dim3(TC_TN / 32, TC_KP / 32), 256, 0, st>>>(A, ld, w, k0, w, 0, k0, -1.f, Bp[cur]); ++g_launches;
+        product(st, cur, TcMap{m, w, k0, w, 0, k0, -1, 1, -1, -1}, std::min(tiles(m, w), sms), m, w, w);
+        // (3) reads this step's row panel, which the previous step's second part wrote
+        if (pending) { cudaStreamWaitEvent(st, evB, 0); pending = false; }
+        k_tc_pack_a<<<(unsigned)((size_t)mpmax * TC_KP / 256), 256, 0, st>>>(A, ld, n, k0, w, n, 0, mpmax, Ap[cur]); ++g_launches;
+        k_tc_pack_b<<<dim3(mp / 32, TC_KP / 32), 256, 0, st>>>(A, ld, m, k0, w, k0, w, 1.f, Bp[cur]); ++g_launches;
+        const TcMap mb = {n, m, n, 0, k0, w, k0 / TC_TM, 0, -1, -1};
+        const int nt = (m + TC_TN - 1) / TC_TN, ntm = (n + TC_TM - 1) / TC_TM;
+        const bool next = k0 + GJ_W < n;
+        if (next && nt > 1) {
+            const int tA = k0 / TC_TN;   // trailing column k0 is global column k0 + w: the next pivot block
+            TcMap ma = mb, mr = mb;
+            ma.tx_only = tA;
+            mr.tx_skip = tA;
+            product(st, cur, ma, std::min(ntm, sms), n, std::min(TC_TN, m - k0), w);
+            cudaEventRecord(evP, st);
+            cudaStreamWaitEvent(aux, evP, 0);
+            product(aux, cur, mr, std::max(1, std::min(ntm * (nt - 1), sms - 4)), n, m - std::min(TC_TN, m - k0), w);
+            cudaEventRecord(evB, aux);
+            pending = true;
+        } else {
+            product(st, cur, mb, std::min(tiles(n, m), sms), n, m, w);
+        }
+        if (next) {
+            const int k1 = k0 + GJ_W;
+            k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(A, ld, k1, std::min(n - k1, GJ_W), status); ++g_launches;
         }
     }
+    if (pending) cudaStreamWaitEvent(st, evB, 0);
+    cudaEventDestroy(evP);
+    cudaEventDestroy(evB);
     return cudaGetLastError();
 }
 

@@ -23,10 +23,12 @@ struct KernelTimer {
     cudaEvent_t next() { return alloc ? alloc(pool) : nullptr; }
     void add(cudaEvent_t a, cudaEvent_t b, double w) { ev.push_back({a, b}); work.push_back(w); }
 };
-// the same inversion with 128-wide pivot blocks and the tcgen05 (TF32) trailing
-// update; `pack` is device scratch of gj_pack_floats(n) floats (the packed panels)
+// the same inversion with 128-wide pivot blocks and the tcgen05 (TF32)
+// products; `pack` is device scratch of gj_pack_floats(n) floats (the packed
+// operands), aux a second stream of the caller (look-ahead); the work is
+// complete on st when the last call returns on it
 size_t gj_pack_floats(int n);
-cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st,
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, cudaStream_t aux,
                          KernelTimer *kt = nullptr);
 template <typename TS, typename TD>
 cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st);

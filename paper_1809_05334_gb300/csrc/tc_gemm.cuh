@@ -167,9 +167,18 @@ __global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, 
 // r < rat ? r : r + rskip, columns c < ncols at col(c) = c < cat ? c : c + cskip
 // (rat, cat multiples of 128 or beyond the extent, so no tile straddles a
 // skip); beta = 0 on every tile if beta0_all, else on tile row beta0_row.
+// tx_only >= 0 restricts the product to that tile column; tx_skip >= 0
+// leaves that tile column out (the two halves of a split product).
 struct TcMap {
-    int mrows, ncols, rat, rskip, cat, cskip, beta0_row, beta0_all;
+    int mrows, ncols, rat, rskip, cat, cskip, beta0_row, beta0_all, tx_only, tx_skip;
 };
+
+// tile t of the product -> (tile row, tile column)
+__device__ __forceinline__ void tc_tile(const TcMap &mp, int ntx, int t, int &ty, int &tx) {
+    ty = t / ntx;
+    const int i = t % ntx;
+    tx = mp.tx_only >= 0 ? mp.tx_only : (mp.tx_skip >= 0 && i >= mp.tx_skip ? i + 1 : i);
+}
 
 // C <- beta C + Ap * Bp^T over the tiles of the map.  tmA, tmB: the packed
 // operands (box 32 floats x 128 / 256 rows);
@@ -196,7 +205,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntm = (mp.mrows + TC_TM - 1) / TC_TM, nt = (mp.ncols + TC_TN - 1) / TC_TN;
-    const int ntiles = ntm * nt;
+    const int ntx = mp.tx_only >= 0 ? 1 : (mp.tx_skip >= 0 ? nt - 1 : nt);   // tile columns covered
+    const int ntiles = ntm * ntx;
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
@@ -223,7 +233,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int it = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const int ty = t / nt, tx = t % nt;
+            int ty, tx;
+            tc_tile(mp, ntx, t, ty, tx);
             for (int kc = 0; kc < TC_NCHUNK; ++kc, ++it) {
                 const int s = it % TC_STAGES;
                 if (it >= TC_STAGES && !mbar_wait(empty + s, (uint32_t)((it / TC_STAGES - 1) & 1))) { ok = false; break; }
@@ -281,7 +292,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int ci = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const int ty = t / nt, tx = t % nt;
+            int ty, tx;
+            tc_tile(mp, ntx, t, ty, tx);
             const int r0 = ty * TC_TM, c0 = tx * TC_TN;
             const int gr0 = r0 < mp.rat ? r0 : r0 + mp.rskip, gc0 = c0 < mp.cat ? c0 : c0 + mp.cskip;
             for (int cc = 0; cc < TC_NCHUNK; ++cc, ++ci) {
@@ -303,7 +315,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int ci = 0, tl = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
-            const int ty = t / nt, tx = t % nt;
+            int ty, tx;
+            tc_tile(mp, ntx, t, ty, tx);
             const int r0 = ty * TC_TM, c0 = tx * TC_TN;
             const int gr0 = r0 < mp.rat ? r0 : r0 + mp.rskip, gc0 = c0 < mp.cat ? c0 : c0 + mp.cskip;
             const bool keep = !(mp.beta0_all || ty == mp.beta0_row);   // beta = 1 (else the product alone)
