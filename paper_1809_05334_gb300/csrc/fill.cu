@@ -244,7 +244,7 @@ __device__ void scatter_tt(const DevMesh &m, const DevReq &q, T *Z, size_t N, in
 // point pairs gives g_p(x_a - y_b) for the block (t, s) and g_p(y_b - x_a) for
 // the block (s, t) (the reversed pair's moments swap the roles of the offsets).
 template <typename T>
-__global__ void __launch_bounds__(128) k_far_tt(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N) {
+__global__ void __launch_bounds__(128, 6) k_far_tt(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N) {
     extern __shared__ float smem_tab[];
     const int t = blockIdx.y;
     if ((int)(blockIdx.x * blockDim.x + blockDim.x) <= t) return;   // the whole block is below the diagonal
