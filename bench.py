@@ -214,7 +214,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": None,
     }
-    res["roofline"], res["rooflines"] = roofline(last, n, peaks, prec == vie.VIE_FP32)
+    res["roofline"], res["rooflines"] = roofline(last, n, peaks, prec == vie.VIE_FP32, cell.n_tets)
     res["clocks"] = clk.summary()
     # kernels launched inside the timed region, counted by the library at each launch site
     res["gpu_launches"] = int(sum(r["n_launches"] for r in results))
@@ -228,18 +228,40 @@ def run_ours(args):
         print(json.dumps(res))
 
 
-def roofline(last, n, peaks, fp32):
+# Executed FP32 operations (2 FFMA + FADD + FMUL, thread level) of the far
+# tetrahedron-pair kernel per g_p value it produces (16 per ordered pair of
+# tetrahedra), counted with ncu on the plasmonic 21k workload at 500 nm (the
+# Ewald series has the same terms per value for every cell of this period and
+# wavelength).
+FAR_FLOPS_PER_VALUE = 1308.0
+SMS, FP32_LANES = 152, 128
+
+
+def roofline(last, n, peaks, fp32, n_tets):
     """Roofline of the dominant kernel (largest device time in the solve), plus the others.
 
-    k_tc_update (block inversion of Eq. (6), tensor cores, TF32): arithmetic
-    intensity 8 m^2 w flop / (16 m^2 + 16 m w) B ~ 64 flop/B at w = 128, below the
-    TF32 ridge (~140 flop/B) -> HBM-bound; algorithmic bytes = read-modify-write of
-    the trailing matrix + one read of the panels, per launch.
-    k_matvec (GMRES): HBM-bound; bytes = N ld 8 B (FP32 Z) + the two vectors.
+    k_far_tt (far tetrahedron pairs of the fill): FP32 CUDA-core bound ("alu");
+    achieved = FAR_FLOPS_PER_VALUE x 16 n_tets^2 values / event time, against
+    152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock.
+    k_tc_update (tensor-core products of the block inversion of Eq. (6), TF32):
+    arithmetic intensity ~ w/2 = 64 flop/B, below the TF32 ridge -> HBM-bound;
+    algorithmic bytes = read and write of the updated block + one read of the
+    two operand panels, per launch.
+    k_matvec (GMRES Z products): HBM-bound; bytes = N ld 8 B (FP32 Z) + the two vectors.
     """
     peak = float(peaks.get("hbm_gbs", 6800.0))
     src = "measured" if "hbm_gbs" in peaks else "fallback"
     out = {}
+    if last.get("k_far_tt_ms") and fp32:
+        t = last["k_far_tt_ms"] / 1e3
+        clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        fpeak = SMS * FP32_LANES * 2 * clk / 1e12
+        ach = FAR_FLOPS_PER_VALUE * 16.0 * n_tets * n_tets / t / 1e12
+        out["k_far_tt"] = {"bound": "alu", "kernel": "k_far_tt", "achieved": ach, "peak": fpeak,
+                           "unit": "TFLOP/s", "frac": ach / fpeak, "traffic": None,
+                           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (clk / 1e6),
+                           "total_ms": last["k_far_tt_ms"], "launches": 1,
+                           "gp_values_per_s": 16.0 * n_tets * n_tets / t}
     if last.get("k_tc_n"):
         t = last["k_tc_ms"] / last["k_tc_n"] / 1e3
         b = last["k_tc_bytes"] / last["k_tc_n"]

@@ -227,10 +227,13 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
     }
     const float E = ew.Ef;
     const float xmax = ew.xs_max, ih = ew.xs_inv_h;
+    const float r2max = (xmax / E) * (xmax / E) * 1.0001f;   // loose: the exact test follows
     for (int i = 0; i < ew.n_img; ++i) {
         const float *im = ew.img[i];
         const float x = dx + im[0], y = dy + im[1];
-        const float R = sqrtf(x * x + y * y + dz * dz);
+        const float R2 = x * x + y * y + dz * dz;
+        if (R2 > r2max) continue;          // outside the cut: skip before the square root
+        const float R = sqrtf(R2);
         const float xr = R * E;
         if (xr > xmax) continue;
         bool regular = false;

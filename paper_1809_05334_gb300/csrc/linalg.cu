@@ -518,10 +518,13 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evB, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
     auto tiles = [](int r, int c) { return ((r + TC_TM - 1) / TC_TM) * ((c + TC_TN - 1) / TC_TN); };
-    // one product on stream s, timed when kt is set; algorithmic bytes: read and
-    // write of the rows x cols block of C, one read of the two operand panels
-    auto product = [&](cudaStream_t s, int b, const TcMap &mp, int grid, double rows, double cols, int w) {
-        cudaEvent_t e0 = kt ? kt->next() : nullptr, e1 = kt ? kt->next() : nullptr;
+    // one product on stream s, timed when kt is set and `timed` (the large
+    // products (3); the column-panel product (a) overlaps them and is left
+    // out); algorithmic bytes: read and write of the rows x cols block of C,
+    // one read of the two operand panels
+    auto product = [&](cudaStream_t s, int b, const TcMap &mp, int grid, double rows, double cols, int w,
+                       bool timed) {
+        cudaEvent_t e0 = (kt && timed) ? kt->next() : nullptr, e1 = (kt && timed) ? kt->next() : nullptr;
         if (e0) cudaEventRecord(e0, s);
         k_tc_update<<<grid, TC_THREADS, TC_SMEM, s>>>(tmA[b], tmB[b], tmC, tmCs, mp, status); ++g_launches;
         if (e1) {
@@ -540,7 +543,7 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
         // (a) column panel: A[T, P] <- A[T, P] (-P^-1)
         k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, m, k0, w, k0, w, mp, Ap[cur]); ++g_launches;
         k_tc_pack_b<<<dim3(TC_TN / 32, TC_KP / 32), 256, 0, st>>>(A, ld, w, k0, w, 0, k0, -1.f, Bp[cur]); ++g_launches;
-        product(st, cur, TcMap{m, w, k0, w, 0, k0, -1, 1, -1, -1}, std::min(tiles(m, w), sms), m, w, w);
+        product(st, cur, TcMap{m, w, k0, w, 0, k0, -1, 1, -1, -1}, std::min(tiles(m, w), sms), m, w, w, false);
         // (3) reads this step's row panel, which the previous step's second part wrote
         if (pending) { cudaStreamWaitEvent(st, evB, 0); pending = false; }
         k_tc_pack_a<<<(unsigned)((size_t)mpmax * TC_KP / 256), 256, 0, st>>>(A, ld, n, k0, w, n, 0, mpmax, Ap[cur]); ++g_launches;
@@ -553,14 +556,15 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
             TcMap ma = mb, mr = mb;
             ma.tx_only = tA;
             mr.tx_skip = tA;
-            product(st, cur, ma, std::min(ntm, sms), n, std::min(TC_TN, m - k0), w);
+            product(st, cur, ma, std::min(ntm, sms), n, std::min(TC_TN, m - k0), w, true);
             cudaEventRecord(evP, st);
             cudaStreamWaitEvent(aux, evP, 0);
-            product(aux, cur, mr, std::max(1, std::min(ntm * (nt - 1), sms - 4)), n, m - std::min(TC_TN, m - k0), w);
+            product(aux, cur, mr, std::max(1, std::min(ntm * (nt - 1), sms - 4)), n, m - std::min(TC_TN, m - k0), w,
+                    true);
             cudaEventRecord(evB, aux);
             pending = true;
         } else {
-            product(st, cur, mb, std::min(tiles(n, m), sms), n, m, w);
+            product(st, cur, mb, std::min(tiles(n, m), sms), n, m, w, true);
         }
         if (next) {
             const int k1 = k0 + GJ_W;
