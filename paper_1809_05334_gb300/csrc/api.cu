@@ -92,7 +92,7 @@ struct vie_ctx {
     std::string err;
     std::shared_ptr<MeshState> mesh = std::make_shared<MeshState>();
     // request (device)
-    DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab, ew;
+    DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab, rtab, ew;
     double z_extent = 0;
     // solve buffers
     DevBuf Z, b, x, r, u, w, V, h, y, Minv, tcpack, status, acc, J, rt, cout;
@@ -294,7 +294,8 @@ int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
                     E.tab_ig[found][0] = ig.real(); E.tab_ig[found][1] = ig.imag();
                     E.tab_pre[found] = std::exp(-g2 / (4 * E.E * E.E));
                 }
-                E.rect_tab[idx] = found;
+                // bit 16 marks a real decay constant (evanescent mode): its G is real
+                E.rect_tab[idx] = found | (g2s[found] > 0 ? vie::TAB_REAL : 0);
             }
         E.n_tab = nt;
     }
@@ -351,10 +352,12 @@ int upload_request(vie_ctx *ctx, const HostReq &H, vie::DevReq &q, cudaStream_t 
     if (g_h2d_counter) *g_h2d_counter += (int64_t)sizeof(vie::EwaldTables);
     CK(ctx->stab.ensure(sizeof(float) * 4 * vie::NSPAT));
     CK(ctx->ztab.ensure(sizeof(float2) * 4 * vie::NZTAB * std::max(H.ew.n_tab, 1)));
+    CK(ctx->rtab.ensure(sizeof(float4) * vie::NZTAB * std::max(H.ew.n_tab, 1)));
     CK(vie::launch_build_tables(ctx->ew.as<vie::EwaldTables>(), ctx->stab.as<float>(), ctx->ztab.as<float2>(),
-                                H.ew.n_tab, st));
+                                H.ew.n_tab, st, ctx->rtab.as<float4>()));
     q.stab = ctx->stab.as<float>();
     q.ztab = ctx->ztab.as<float2>();
+    q.rtab = ctx->rtab.as<float4>();
     q.ew = ctx->ew.as<vie::EwaldTables>();
     q.ef = vie::make_ewald_f32(H.ew);
     q.k0 = H.k0; q.kx = H.kx; q.ky = H.ky;
@@ -1183,7 +1186,7 @@ void release_device_memory(vie_ctx *ctx) {
     ctx->slots.clear();
     ctx->mesh = std::make_shared<MeshState>();
     DevBuf *bufs[] = {&ctx->row, &ctx->coef, &ctx->wt, &ctx->kap, &ctx->ieps, &ctx->frow, &ctx->qs,
-                      &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->ew,
+                      &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->rtab, &ctx->ew,
                       &ctx->Z, &ctx->b, &ctx->x, &ctx->r, &ctx->u, &ctx->w, &ctx->V, &ctx->h, &ctx->y,
                       &ctx->Minv, &ctx->tcpack, &ctx->status, &ctx->acc, &ctx->J, &ctx->rt, &ctx->cout};
     for (DevBuf *b : bufs) b->release();

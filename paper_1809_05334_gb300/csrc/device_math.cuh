@@ -187,10 +187,13 @@ __device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub, const EwaldTables *__re
 // carry the conjugate phases, and the spatial term of image -R_mn at -d is the
 // table value of image R_mn at d with the conjugate lattice phase (the image
 // list and the near-image masks are symmetric under (m,n) -> (-m,-n)).
+// rtab (may be null): the real parts of the tables as one float4 per
+// interval; used for the tables flagged TAB_REAL (their imaginary parts are 0)
 template <bool PAIR>
 __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, unsigned sub, const float *stab,
                                                const float2 *__restrict__ ztab, const EwaldF32 &ew,
-                                               cx<float> &gp, cx<float> &gm) {
+                                               cx<float> &gp, cx<float> &gm,
+                                               const float4 *__restrict__ rtab = nullptr) {
     cx<float> acc = {0.f, 0.f}, acc2 = {0.f, 0.f};
     const float z = fabsf(dz);
     float zu = fminf(z * ew.z_inv_h, float(NZTAB));
@@ -210,14 +213,26 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
         cx<float> inner = {0.f, 0.f}, inner2 = {0.f, 0.f};
         cx<float> ey = ey0;
         for (int q = 0; q < nq; ++q) {
-            const int tb = ew.rect_tab[p * nq + q];
-            if (tb >= 0) {
-                const float2 *cf = ztab + ((size_t)tb * NZTAB + iz) * 4;
-                const float2 c0 = __ldg(cf), c1 = __ldg(cf + 1), c2 = __ldg(cf + 2), c3 = __ldg(cf + 3);
-                cx<float> g = {fmaf(u, fmaf(u, fmaf(u, c3.x, c2.x), c1.x), c0.x),
-                               fmaf(u, fmaf(u, fmaf(u, c3.y, c2.y), c1.y), c0.y)};
-                inner = inner + ey * g;
-                if (PAIR) inner2 = inner2 + cconj(ey) * g;
+            const int code = ew.rect_tab[p * nq + q];
+            if (code >= 0) {
+                const int tb = code & TAB_INDEX;
+                if (rtab && (code & TAB_REAL)) {   // real G: one 16-byte load, real products
+                    const float4 c = __ldg(rtab + (size_t)tb * NZTAB + iz);
+                    const float g = fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+                    inner.re = fmaf(ey.re, g, inner.re);
+                    inner.im = fmaf(ey.im, g, inner.im);
+                    if (PAIR) {
+                        inner2.re = fmaf(ey.re, g, inner2.re);
+                        inner2.im = fmaf(-ey.im, g, inner2.im);
+                    }
+                } else {
+                    const float2 *cf = ztab + ((size_t)tb * NZTAB + iz) * 4;
+                    const float2 c0 = __ldg(cf), c1 = __ldg(cf + 1), c2 = __ldg(cf + 2), c3 = __ldg(cf + 3);
+                    cx<float> g = {fmaf(u, fmaf(u, fmaf(u, c3.x, c2.x), c1.x), c0.x),
+                                   fmaf(u, fmaf(u, fmaf(u, c3.y, c2.y), c1.y), c0.y)};
+                    inner = inner + ey * g;
+                    if (PAIR) inner2 = inner2 + cconj(ey) * g;
+                }
             }
             ey = ey * sy;
         }
@@ -233,7 +248,8 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
         const float x = dx + im[0], y = dy + im[1];
         const float R2 = x * x + y * y + dz * dz;
         if (R2 > r2max) continue;          // outside the cut: skip before the square root
-        const float R = sqrtf(R2);
+        const float rinv = R2 > 0.f ? rsqrtf(R2) : 0.f;   // R = 0 only on a regularised image (no 1/R)
+        const float R = R2 * rinv;
         const float xr = R * E;
         if (xr > xmax) continue;
         bool regular = false;
@@ -251,9 +267,9 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
             if (ix == 0)   // (F(x) - F(0))/R = E (c1 + v (c2 + v c3)) / h
                 val = E * ih * fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]);
             else
-                val = (fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) - ew.e_mb2) / R;
+                val = (fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) - ew.e_mb2) * rinv;
         } else {
-            val = fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) / R;
+            val = fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) * rinv;
         }
         acc.re = fmaf(val, im[2], acc.re);
         acc.im = fmaf(val, im[3], acc.im);

@@ -26,11 +26,14 @@ struct EwaldTables {
     float xs_max, xs_inv_h, z_max, z_inv_h, e_mb2, Ef;
     float kx, ky, step_x, step_y;   // k_t,pq = (kx + p step_x, ky + q step_y)
     int P, Q, n_tab;
-    int rect_tab[MAX_MODE];  // table of rectangle entry (p+P)(2Q+1)+(q+Q), -1 outside the cut
+    int rect_tab[MAX_MODE];  // table of rectangle entry (p+P)(2Q+1)+(q+Q) (| TAB_REAL if its G
+                             // is real), -1 outside the cut
     double tab_gamma[MAX_MODE][2];   // gamma of each table
     double tab_ig[MAX_MODE][2];      // 1/(4ab gamma) of each table
     double tab_pre[MAX_MODE];        // exp(-gamma^2/4E^2)
 };
+constexpr int TAB_REAL = 1 << 16;   // flag in rect_tab: the table's G is real (real decay constant)
+constexpr int TAB_INDEX = TAB_REAL - 1;
 constexpr int NSPAT = 512;    // spatial intervals
 constexpr int NZTAB = 256;    // spectral intervals
 // EwaldTables lives in device global memory, one copy per request in flight, so

@@ -113,7 +113,8 @@ __device__ void spectral_node(const EwaldTables *ew, int tb, double z, cx<double
     dG = (g * (t1 - t2)) * ig;
 }
 
-__global__ void k_build_tables(const EwaldTables *__restrict__ ew, float *stab, float2 *ztab, int n_tab) {
+__global__ void k_build_tables(const EwaldTables *__restrict__ ew, float *stab, float2 *ztab, int n_tab,
+                               float4 *rtab) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < NSPAT) {
         const double h = double(ew->xs_max) / NSPAT;
@@ -135,11 +136,14 @@ __global__ void k_build_tables(const EwaldTables *__restrict__ ew, float *stab, 
     hermite(G0.re, D0.re, G1.re, D1.re, h, cr);
     hermite(G0.im, D0.im, G1.im, D1.im, h, ci);
     for (int k = 0; k < 4; ++k) ztab[((size_t)tb * NZTAB + iz) * 4 + k] = make_float2(float(cr[k]), float(ci[k]));
+    // the real parts again, 16 bytes per interval, for the tables whose G is real
+    if (rtab) rtab[(size_t)tb * NZTAB + iz] = make_float4(float(cr[0]), float(cr[1]), float(cr[2]), float(cr[3]));
 }
 
-cudaError_t launch_build_tables(const EwaldTables *ew, float *stab, float2 *ztab, int n_tab, cudaStream_t st) {
+cudaError_t launch_build_tables(const EwaldTables *ew, float *stab, float2 *ztab, int n_tab, cudaStream_t st,
+                                float4 *rtab) {
     const int n = NSPAT + n_tab * NZTAB;
-    k_build_tables<<<(n + 127) / 128, 128, 0, st>>>(ew, stab, ztab, n_tab); ++g_launches;
+    k_build_tables<<<(n + 127) / 128, 128, 0, st>>>(ew, stab, ztab, n_tab, rtab); ++g_launches;
     return cudaGetLastError();
 }
 
@@ -157,23 +161,28 @@ template <typename T> struct Green;
 // eval2 returns g_p(d) and g_p(-d) (the same near-image mask applies to both)
 template <> struct Green<double> {
     __device__ static cx<double> eval(double dx, double dy, double dz, unsigned sub, const float *, const float2 *,
-                                      const EwaldTables *ew, const EwaldF32 &) {
+                                      const EwaldTables *ew, const EwaldF32 &, const float4 * = nullptr) {
         return green_p<double>(dx, dy, dz, sub, ew);
     }
     __device__ static void eval2(double dx, double dy, double dz, unsigned sub, const float *, const float2 *,
-                                 const EwaldTables *ew, const EwaldF32 &, cx<double> &gp, cx<double> &gm) {
+                                 const EwaldTables *ew, const EwaldF32 &, cx<double> &gp, cx<double> &gm,
+                                 const float4 * = nullptr) {
         gp = green_p<double>(dx, dy, dz, sub, ew);
         gm = green_p<double>(-dx, -dy, -dz, mirror_mask(sub), ew);
     }
 };
 template <> struct Green<float> {
     __device__ static cx<float> eval(float dx, float dy, float dz, unsigned sub, const float *stab,
-                                     const float2 *ztab, const EwaldTables *, const EwaldF32 &ef) {
-        return green_tab(dx, dy, dz, sub, stab, ztab, ef);
+                                     const float2 *ztab, const EwaldTables *, const EwaldF32 &ef,
+                                     const float4 *rtab = nullptr) {
+        cx<float> g, unused;
+        green_tab_impl<false>(dx, dy, dz, sub, stab, ztab, ef, g, unused, rtab);
+        return g;
     }
     __device__ static void eval2(float dx, float dy, float dz, unsigned sub, const float *stab, const float2 *ztab,
-                                 const EwaldTables *, const EwaldF32 &ef, cx<float> &gp, cx<float> &gm) {
-        green_tab_impl<true>(dx, dy, dz, sub, stab, ztab, ef, gp, gm);
+                                 const EwaldTables *, const EwaldF32 &ef, cx<float> &gp, cx<float> &gm,
+                                 const float4 *rtab = nullptr) {
+        green_tab_impl<true>(dx, dy, dz, sub, stab, ztab, ef, gp, gm, rtab);
     }
 };
 
@@ -266,7 +275,8 @@ __global__ void __launch_bounds__(128, 6) k_far_tt(DevMesh m, const __grid_const
             const T yb[3] = {fs[3 * b], fs[3 * b + 1], fs[3 * b + 2]};
             const T rb[3] = {yb[0] - fs[12], yb[1] - fs[13], yb[2] - fs[14]};
             cx<T> g, gr;
-            Green<T>::eval2(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab, q.ew, q.ef, g, gr);
+            Green<T>::eval2(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab, q.ew, q.ef, g, gr,
+                            q.rtab);
             g = wgt * g;
             gr = wgt * gr;
             const T rr = ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2];
@@ -546,7 +556,7 @@ __global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, const __grid_cons
     for (int a = 0; a < qx; ++a)
         for (int b = 0; b < qy; ++b) {
             cx<T> g = Green<T>::eval(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1], fx[3 * a + 2] - fy[3 * b + 2],
-                                     sub, stab, q.ztab, q.ew, q.ef);
+                                     sub, stab, q.ztab, q.ew, q.ef, q.rtab);
             S = S + g;
         }
     S = wgt * S;

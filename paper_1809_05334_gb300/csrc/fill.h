@@ -74,6 +74,7 @@ struct DevReq {
     double img_ph[18];     // exp(j k_par.R_k)/(4 pi) of the near images k = 0..8
     const float *stab;     // FP32 tables of the Ewald series (built per request)
     const float2 *ztab;
+    const float4 *rtab;    // real parts of ztab (16 bytes per interval), read for the real tables
     const EwaldTables *ew; // Ewald parameters of the request (device memory)
     EwaldF32 ef;           // FP32 inner-loop parameters (kernel parameter space)
 };
@@ -95,6 +96,7 @@ cudaError_t launch_static_cache(const DevMesh &m, double *touch_half, double *co
 cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStream_t st);
 cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const float *stab, const float2 *ztab,
                          const EwaldTables *ew, const EwaldF32 &ef, cudaStream_t st);
-cudaError_t launch_build_tables(const EwaldTables *ew, float *stab, float2 *ztab, int n_tab, cudaStream_t st);
+cudaError_t launch_build_tables(const EwaldTables *ew, float *stab, float2 *ztab, int n_tab, cudaStream_t st,
+                                float4 *rtab = nullptr);
 
 }  // namespace vie
