@@ -63,10 +63,11 @@ typedef enum {
 typedef struct {
     int32_t precision;     /* vie_precision                                        */
     int32_t use_precond;   /* 1: diagonal-block preconditioner of Eq. (6); 0: none  */
-    int32_t restart;       /* GMRES restart length (default 60)                    */
+    int32_t restart;       /* GMRES restart length (default 100)                   */
     int32_t max_iter;      /* total GMRES iterations over all restarts (default 1000)*/
     double  tol;           /* target FP64 relative residual ||b - Z x|| / ||b||     */
-    double  inner_tol;     /* FP32 inner GMRES tolerance of each refinement sweep   */
+    double  inner_tol;     /* FP32 inner GMRES tolerance of each refinement sweep
+                              (default 3e-6; never below 1e-6)                   */
     int32_t timing;        /* 1: record CUDA events around the main kernels and
                               report their device times in vie_result.k_* (adds
                               no work, only events on the solve stream)          */
@@ -114,6 +115,11 @@ typedef struct {
     /* solve server only (0 elsewhere): time from vie_server_submit to the start
        of the solve, and to its end */
     double  t_queue_ms, t_latency_ms;
+    /* applications of the preconditioner of Eq. (6) in GMRES (options.timing = 1):
+       total device time of the k_precond_n applications and their algorithmic
+       bytes (one read of every block inverse plus the vectors) */
+    double  k_precond_ms, k_precond_bytes;
+    int32_t k_precond_n, reserved3;
 } vie_result;
 
 /* Fill *opt with defaults (FP32 with refinement, preconditioner on, tol 1e-6). */

@@ -406,6 +406,8 @@ vie::DevMesh dev_mesh(vie_ctx *ctx) {
 struct Timing {
     cudaEvent_t fill0 = nullptr, fill1 = nullptr, far0 = nullptr, far1 = nullptr, fac0 = nullptr, fac1 = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> mv;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pc;   // preconditioner applications
+    double pc_bytes = 0;                                   // their algorithmic bytes
     vie::KernelTimer tc;
 };
 
@@ -432,6 +434,23 @@ int precond_apply(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &mof
         const float *Mi = ctx->Minv.as<float>() + 2 * moff[k];
         CK((vie::matvec<float, TV, TV>(Mi, mld[k], H.blk_n[k], H.blk_n[k], in + 4 * (size_t)H.blk_off[k],
                                         out + 4 * (size_t)H.blk_off[k], TV(1), false, st)));
+    }
+    return VIE_OK;
+}
+
+// one application of M^-1 with CUDA events around it (options.timing); the
+// algorithmic bytes are one read of every block inverse plus the vectors
+template <typename TV>
+int timed_precond(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const std::vector<size_t> &mld,
+                  const TV *in, TV *out, cudaStream_t st, Timing &tm) {
+    cudaEvent_t e0 = ctx->event(), e1 = ctx->event();
+    if (e0) CK(cudaEventRecord(e0, st));
+    if (int e = precond_apply<TV>(ctx, H, moff, mld, in, out, st)) return e;
+    if (e1) {
+        CK(cudaEventRecord(e1, st));
+        tm.pc.push_back({e0, e1});
+        for (size_t k = 0; k < H.blk_n.size(); ++k)
+            tm.pc_bytes += 8.0 * (double)H.blk_n[k] * (double)mld[k] + 2.0 * 2 * 2 * sizeof(TV) * H.blk_n[k];
     }
     return VIE_OK;
 }
@@ -488,7 +507,7 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
         if (!active[0]) s[0] = 0;
         if (!active[1]) s[2] = 0;
         CK((vie::scale<double, TV>(r, u, N, s, st)));
-        if (pre) { if (int e = precond_apply<TV>(ctx, H, moff, mld, u, w, st)) return e; }
+        if (pre) { if (int e = timed_precond<TV>(ctx, H, moff, mld, u, w, st, tm)) return e; }
         else CK(cudaMemcpyAsync(w, u, sizeof(TV) * vs, cudaMemcpyDeviceToDevice, st));
         CK(vie::dots<TV>(w, 0, 1, w, N, hd, st));
         ctx->d2h += sizeof(double) * 4;
@@ -521,7 +540,7 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
             if (e0) CK(cudaEventRecord(e0, st));
             CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st)));
             if (e1) { CK(cudaEventRecord(e1, st)); tm.mv.push_back({e0, e1}); }
-            if (pre) { if (int e = precond_apply<TV>(ctx, H, moff, mld, u, vn, st)) return e; }
+            if (pre) { if (int e = timed_precond<TV>(ctx, H, moff, mld, u, vn, st, tm)) return e; }
             // classical Gram-Schmidt, twice; the projections of both passes and
             // the new norm stay on the device until one copy at the end
             const size_t nh = 4 * (size_t)(k + 1);
@@ -723,6 +742,11 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
         res->k_tc_ms = ts;
         res->k_tc_bytes = tb;
         res->k_tc_n = (int32_t)tm.tc.ev.size();
+        double sp = 0;
+        for (auto &p : tm.pc) sp += ev_ms(p.first, p.second);
+        res->k_precond_ms = sp;
+        res->k_precond_bytes = tm.pc_bytes;
+        res->k_precond_n = (int32_t)tm.pc.size();
     }
     res->status = stat;
     return stat;
@@ -764,10 +788,10 @@ int slot_footprint(vie_ctx *ctx, const vie_request *req, size_t *bytes) {
 void default_opts(vie_options *o) {
     o->precision = VIE_FP32;
     o->use_precond = 1;
-    o->restart = 60;
+    o->restart = 100;
     o->max_iter = 1000;
     o->tol = 1e-6;
-    o->inner_tol = 1e-4;
+    o->inner_tol = 3e-6;
     o->timing = 0;
     o->reserved = 0;
 }

@@ -50,7 +50,9 @@ class Result(ctypes.Structure):
                 ("far_pair_evals", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("k_tc_ms", ctypes.c_double), ("k_tc_bytes", ctypes.c_double), ("k_tc_n", ctypes.c_int32),
                 ("n_launches", ctypes.c_int32), ("t_queue_ms", ctypes.c_double),
-                ("t_latency_ms", ctypes.c_double)]
+                ("t_latency_ms", ctypes.c_double), ("k_precond_ms", ctypes.c_double),
+                ("k_precond_bytes", ctypes.c_double), ("k_precond_n", ctypes.c_int32),
+                ("reserved3", ctypes.c_int32)]
 
 
 class Mesh(ctypes.Structure):
@@ -122,8 +124,8 @@ def _ptr(a):
 class Solver:
     """One library context on one GPU (vie_create ... vie_destroy)."""
 
-    def __init__(self, device=0, precision=VIE_FP32, use_precond=True, restart=60, max_iter=1000,
-                 tol=1e-6, inner_tol=1e-4, timing=False):
+    def __init__(self, device=0, precision=VIE_FP32, use_precond=True, restart=100, max_iter=1000,
+                 tol=1e-6, inner_tol=3e-6, timing=False):
         self.lib = load()
         self.opt = Options()
         self.lib.vie_default_options(ctypes.byref(self.opt))
@@ -195,7 +197,8 @@ class Solver:
                     n_near_pairs=res.n_near_pairs, far_pair_evals=res.far_pair_evals,
                     h2d_bytes=res.h2d_bytes, d2h_bytes=res.d2h_bytes, k_tc_ms=res.k_tc_ms,
                     k_tc_bytes=res.k_tc_bytes, k_tc_n=res.k_tc_n, n_launches=res.n_launches,
-                    t_queue_ms=res.t_queue_ms, t_latency_ms=res.t_latency_ms, x=out)
+                    t_queue_ms=res.t_queue_ms, t_latency_ms=res.t_latency_ms, k_precond_ms=res.k_precond_ms,
+                    k_precond_bytes=res.k_precond_bytes, k_precond_n=res.k_precond_n, x=out)
 
     def solve_batch(self, lams, thetas, phis, eps_list, max_slots=2, coeffs=False, stream=None):
         """Independent solves of one mesh (vie_solve_batch): lams/thetas/phis/eps_list
@@ -278,7 +281,7 @@ class Server:
     HBM footprint."""
 
     def __init__(self, device=0, n_slots=3, hbm_budget_bytes=0, precision=VIE_FP32, use_precond=True,
-                 restart=60, max_iter=1000, tol=1e-6, inner_tol=1e-4):
+                 restart=100, max_iter=1000, tol=1e-6, inner_tol=3e-6):
         self.lib = load()
         opt = Options()
         self.lib.vie_default_options(ctypes.byref(opt))
