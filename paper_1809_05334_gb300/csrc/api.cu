@@ -95,7 +95,8 @@ struct vie_ctx {
     DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab, rtab, ew;
     double z_extent = 0;
     // solve buffers
-    DevBuf Z, b, x, r, u, w, V, h, y, Minv, tcpack, status, acc, J, rt, cout;
+    DevBuf Z, b, x, r, u, w, V, h, y, Minv, MinvH, amax, tcpack, status, acc, J, rt, cout;
+    std::vector<double> pinv;   // per domain block: 1 / (power-of-two scale of its FP16 inverse)
     size_t ld = 0;
     int64_t h2d = 0, d2h = 0;   // bytes copied by the current solve
     // CUDA events for options.timing
@@ -431,15 +432,15 @@ template <typename TV>
 int precond_apply(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const std::vector<size_t> &mld,
                   const TV *in, TV *out, cudaStream_t st) {
     for (size_t k = 0; k < H.blk_off.size(); ++k) {
-        const float *Mi = ctx->Minv.as<float>() + 2 * moff[k];
-        CK((vie::matvec<float, TV, TV>(Mi, mld[k], H.blk_n[k], H.blk_n[k], in + 4 * (size_t)H.blk_off[k],
-                                        out + 4 * (size_t)H.blk_off[k], TV(1), false, st)));
+        const __half *Mi = ctx->MinvH.as<__half>() + 2 * moff[k];
+        CK((vie::matvec<__half, TV, TV>(Mi, mld[k], H.blk_n[k], H.blk_n[k], in + 4 * (size_t)H.blk_off[k],
+                                         out + 4 * (size_t)H.blk_off[k], TV(ctx->pinv[k]), false, st)));
     }
     return VIE_OK;
 }
 
 // one application of M^-1 with CUDA events around it (options.timing); the
-// algorithmic bytes are one read of every block inverse plus the vectors
+// algorithmic bytes are one read of every FP16 block inverse plus the vectors
 template <typename TV>
 int timed_precond(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const std::vector<size_t> &mld,
                   const TV *in, TV *out, cudaStream_t st, Timing &tm) {
@@ -450,7 +451,7 @@ int timed_precond(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &mof
         CK(cudaEventRecord(e1, st));
         tm.pc.push_back({e0, e1});
         for (size_t k = 0; k < H.blk_n.size(); ++k)
-            tm.pc_bytes += 8.0 * (double)H.blk_n[k] * (double)mld[k] + 2.0 * 2 * 2 * sizeof(TV) * H.blk_n[k];
+            tm.pc_bytes += 4.0 * (double)H.blk_n[k] * (double)mld[k] + 2.0 * 2 * 2 * sizeof(TV) * H.blk_n[k];
     }
     return VIE_OK;
 }
@@ -642,11 +643,39 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
         CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), ctx->tcpack.as<float>(), st,
                              ctx->aux_stream, kt));
     }
+    // the applications read FP16 copies of the inverses, each scaled by a power
+    // of two that brings its largest entry to [2^13, 2^14) (the scale is undone
+    // in the product): half the bytes of every GMRES preconditioner application
+    const size_t nblk = H.blk_n.size();
+    CK(ctx->amax.ensure(sizeof(unsigned) * std::max<size_t>(nblk, 1)));
+    CK(cudaMemsetAsync(ctx->amax.p, 0, sizeof(unsigned) * nblk, st));
+    for (size_t k = 0; k < nblk; ++k)
+        CK(vie::absmax(ctx->Minv.as<float>() + 2 * moff[k], 2 * mld[k] * (size_t)H.blk_n[k],
+                       ctx->amax.as<unsigned>() + k, st));
     int stat = 0;
-    ctx->d2h += sizeof(int);
+    std::vector<unsigned> am(nblk);
+    ctx->d2h += sizeof(int) + sizeof(unsigned) * nblk;
     CK(cudaMemcpyAsync(&stat, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(am.data(), ctx->amax.p, sizeof(unsigned) * nblk, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (stat) return fail(ctx, VIE_BREAKDOWN, "zero or non-finite pivot while inverting a domain block");
+    CK(ctx->MinvH.ensure(sizeof(__half) * 2 * std::max<size_t>(tot, 1)));
+    ctx->pinv.assign(nblk, 1.0);
+    for (size_t k = 0; k < nblk; ++k) {
+        float mx;
+        std::memcpy(&mx, &am[k], sizeof(float));
+        double scale = 1.0;
+        if (mx > 0.f && std::isfinite(mx)) {
+            int ex = 0;
+            std::frexp((double)mx, &ex);   // mx in [2^(ex-1), 2^ex)
+            scale = std::ldexp(1.0, 14 - ex);
+        } else if (!(mx == 0.f)) {
+            return fail(ctx, VIE_BREAKDOWN, "non-finite entry in a domain block inverse");
+        }
+        ctx->pinv[k] = 1.0 / scale;
+        CK(vie::to_half(ctx->Minv.as<float>() + 2 * moff[k], 2 * mld[k] * (size_t)H.blk_n[k], (float)scale,
+                        ctx->MinvH.as<__half>() + 2 * moff[k], st));
+    }
     return VIE_OK;
 }
 
@@ -1212,7 +1241,8 @@ void release_device_memory(vie_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->row, &ctx->coef, &ctx->wt, &ctx->kap, &ctx->ieps, &ctx->frow, &ctx->qs,
                       &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->rtab, &ctx->ew,
                       &ctx->Z, &ctx->b, &ctx->x, &ctx->r, &ctx->u, &ctx->w, &ctx->V, &ctx->h, &ctx->y,
-                      &ctx->Minv, &ctx->tcpack, &ctx->status, &ctx->acc, &ctx->J, &ctx->rt, &ctx->cout};
+                      &ctx->Minv, &ctx->MinvH, &ctx->amax, &ctx->tcpack, &ctx->status, &ctx->acc, &ctx->J,
+                      &ctx->rt, &ctx->cout};
     for (DevBuf *b : bufs) b->release();
 }
 }  // namespace vie

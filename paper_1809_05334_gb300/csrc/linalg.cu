@@ -5,6 +5,7 @@
 // Layouts: complex interleaved (re, im).  A matrix is `rows` rows of `ld`
 // complex entries (ld a multiple of 4, zero padded).  Vectors with two
 // right-hand sides are [n][2] complex.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,6 +20,7 @@ namespace vie {
 template <typename T> struct V2;
 template <> struct V2<float> { using t = float4; };
 template <> struct V2<double> { using t = double2; };
+template <> struct V2<__half> { using t = uint4; };   // four complex FP16 entries
 
 // ---------------------------------------------------------------------------
 // matvec: y[r] = alpha sum_c A[r][c] x[c] (+ y[r] if ACCUM) for rows [0, rows),
@@ -53,7 +55,7 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rb = (int)((long long)rows * blockIdx.x / gridDim.x);
     const int re = (int)((long long)rows * (blockIdx.x + 1) / gridDim.x);
-    constexpr int VEC = sizeof(TZ) == 4 ? 2 : 1;   // complex entries per 16-byte load
+    constexpr int VEC = sizeof(TZ) == 4 ? 2 : (sizeof(TZ) == 8 ? 1 : 4);   // complex entries per 16-byte load
     const int nvec = (cols + VEC - 1) / VEC;
     const int v0 = (int)((long long)nvec * warp / MV_WARPS), v1 = (int)((long long)nvec * (warp + 1) / MV_WARPS);
     int buf = 0;
@@ -81,7 +83,12 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
 #pragma unroll
                 for (int i = 0; i < MV_ROWS; ++i) {
                     TA zr, zi;
-                    if (VEC == 2) {
+                    if constexpr (VEC == 4) {
+                        const uint32_t *wv = reinterpret_cast<const uint32_t *>(&z[i]);
+                        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&wv[u]));
+                        zr = TA(f.x);
+                        zi = TA(f.y);
+                    } else if constexpr (VEC == 2) {
                         const float4 f = *reinterpret_cast<const float4 *>(&z[i]);
                         zr = TA(u == 0 ? f.x : f.z);
                         zi = TA(u == 0 ? f.y : f.w);
@@ -148,6 +155,35 @@ cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *
 }
 
 template cudaError_t matvec<float, float, float>(const float *, size_t, int, int, const float *, float *, float, bool, cudaStream_t);
+template cudaError_t matvec<__half, float, float>(const __half *, size_t, int, int, const float *, float *, float, bool, cudaStream_t);
+template cudaError_t matvec<__half, double, double>(const __half *, size_t, int, int, const double *, double *, double, bool,
+                                                    cudaStream_t);
+
+// largest |Re|, |Im| of a block, as the bit pattern of a non-negative float
+// (for those the integer order is the float order, so atomicMax applies)
+__global__ void k_absmax(const float *__restrict__ A, size_t count, unsigned *out) {
+    float m = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(A[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// B = scale A in FP16 (round to nearest), count floats
+__global__ void k_to_half(const float *__restrict__ A, size_t count, float scale, __half *__restrict__ B) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        B[i] = __float2half_rn(A[i] * scale);
+}
+
+cudaError_t absmax(const float *A, size_t count, unsigned *out, cudaStream_t st) {
+    k_absmax<<<1216, 256, 0, st>>>(A, count, out); ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t to_half(const float *A, size_t count, float scale, __half *B, cudaStream_t st) {
+    k_to_half<<<1216, 256, 0, st>>>(A, count, scale, B); ++g_launches;
+    return cudaGetLastError();
+}
 template cudaError_t matvec<float, double, double>(const float *, size_t, int, int, const double *, double *, double, bool, cudaStream_t);
 template cudaError_t matvec<double, double, double>(const double *, size_t, int, int, const double *, double *, double, bool, cudaStream_t);
 

@@ -1,5 +1,6 @@
 // Dense complex linear algebra used by the solve (see linalg.cu).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <utility>
@@ -30,6 +31,10 @@ struct KernelTimer {
 size_t gj_pack_floats(int n);
 cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, cudaStream_t aux,
                          KernelTimer *kt = nullptr);
+// *out (zeroed by the caller) <- max |A[i]| over count floats, as float bits
+cudaError_t absmax(const float *A, size_t count, unsigned *out, cudaStream_t st);
+// B = scale A in FP16, count floats
+cudaError_t to_half(const float *A, size_t count, float scale, __half *B, cudaStream_t st);
 template <typename TS, typename TD>
 cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st);
 template <typename TV>
