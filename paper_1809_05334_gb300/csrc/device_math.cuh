@@ -261,15 +261,15 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
         const float xu = xr * ih;
         const int ix = min((int)xu, NSPAT - 1);
         const float v = xu - ix;
-        const float *cs = stab + 4 * ix;
+        const float4 cs = *reinterpret_cast<const float4 *>(stab + 4 * ix);   // one 16-byte load
         float val;
         if (regular) {
             if (ix == 0)   // (F(x) - F(0))/R = E (c1 + v (c2 + v c3)) / h
-                val = E * ih * fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]);
+                val = E * ih * fmaf(v, fmaf(v, cs.w, cs.z), cs.y);
             else
-                val = (fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) - ew.e_mb2) * rinv;
+                val = (fmaf(v, fmaf(v, fmaf(v, cs.w, cs.z), cs.y), cs.x) - ew.e_mb2) * rinv;
         } else {
-            val = fmaf(v, fmaf(v, fmaf(v, cs[3], cs[2]), cs[1]), cs[0]) * rinv;
+            val = fmaf(v, fmaf(v, fmaf(v, cs.w, cs.z), cs.y), cs.x) * rinv;
         }
         acc.re = fmaf(val, im[2], acc.re);
         acc.im = fmaf(val, im[3], acc.im);

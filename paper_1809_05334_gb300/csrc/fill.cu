@@ -830,7 +830,8 @@ cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const f
 namespace vie {
 
 constexpr int NOALLOC_MAX_TAB = 96;   // distinct Floquet decay constants the scratch can hold
-constexpr size_t NOALLOC_EW_FLOAT2 = (sizeof(EwaldTables) + sizeof(float2) - 1) / sizeof(float2);
+// whole 16-byte units: the spatial table after it is read with 16-byte loads
+constexpr size_t NOALLOC_EW_FLOAT2 = (sizeof(EwaldTables) + 15) / 16 * 2;
 constexpr size_t NOALLOC_FLOAT2 = NOALLOC_EW_FLOAT2 + 2 * NSPAT + (size_t)NOALLOC_MAX_TAB * NZTAB * 4;
 // Ewald parameter block (~49 KB), spatial table (4*NSPAT floats), spectral tables
 // (float2): about 0.85 MB in total
