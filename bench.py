@@ -339,6 +339,25 @@ def run_sweep(args):
         "clocks": clk.summary(),
     }
     solver.close()
+    if args.compare_fp64 and prec == vie.VIE_FP32:
+        # the plain FP64 GPU path (FP64 Z, FP64 Krylov, tolerance 1e-10) on the
+        # first requests of the same sweep, with the same slots: its throughput
+        # and the absorption difference of the mixed-precision results
+        k = min(args.compare_fp64, steps)
+        s64 = vie.Solver(device=local, precision=vie.VIE_FP64, tol=1e-10)
+        s64.set_mesh(cell)
+        s64.solve_batch(lams[:1], ths[:1], phs[:1], eps[:1], max_slots=1)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        o64, used64 = s64.solve_batch(lams[:k], ths[:k], phs[:k], eps[:k], max_slots=args.slots)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        s64.close()
+        dA = max(float(np.max(np.abs(a["A"] - b["A"]))) for a, b in zip(out[:k], o64))
+        res["fp64_gpu_path"] = {"solves": k, "slots": used64, "value": k / dt, "unit": UNIT,
+                                "mixed_over_fp64": (steps / (ms / 1e3)) / (k / dt),
+                                "max_abs_dA_mixed_vs_fp64": dA,
+                                "fp64_max_rel_residual": float(max(np.max(o["rel_residual"]) for o in o64))}
     print(json.dumps(res))
 
 
@@ -484,6 +503,8 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="batched wavelength x angle sweep on the sweep-density cell (vie_solve_batch)")
     ap.add_argument("--slots", type=int, default=3, help="solve slots in flight for --sweep / --serve")
+    ap.add_argument("--compare-fp64", type=int, default=0, metavar="K",
+                    help="with --sweep: also time the FP64 GPU path on the first K requests and compare")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream of random cells through the solve server (vie_server_*)")
     args = ap.parse_args()
