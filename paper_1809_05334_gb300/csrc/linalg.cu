@@ -503,28 +503,85 @@ bool tensor_map(CUtensorMap *map, const float *base, uint64_t inner, uint64_t ro
 }
 }  // namespace
 
-size_t gj_pack_floats(int n) {   // two sets (consecutive steps overlap) of Ap [mp] and Bp [2 mp] rows
+constexpr int GJ_P = 256;   // pivot width of the outer Gauss-Jordan steps (the K of their products)
+static_assert(GJ_P <= TC_KP, "the packed operands hold one outer pivot block");
+static_assert(GJ_W == 128 && GJ_P == 2 * GJ_W, "a pivot block is inverted in two 128-wide steps");
+
+size_t gj_pack_floats(int n) {
+    // two sets (consecutive outer steps overlap) of Ap [mp] and Bp [2 mp] rows,
+    // and one set of 3 GJ_P rows for the inversion of the pivot blocks
     const size_t mp = ((size_t)n + TC_TM - 1) / TC_TM * TC_TM;
-    return 2 * 3 * mp * TC_PACK_ROW;
+    return (2 * 3 * mp + 3 * (size_t)GJ_P) * TC_PACK_ROW;
 }
 
-// One Gauss-Jordan step with pivot block P = A[k0:k0+w, k0:k0+w] (rows and
-// columns outside it: the trailing set T):
-//   1. P <- P^-1                                  (k_gj_diag_w, registers)
+namespace {
+int tiles(int r, int c) { return ((r + TC_TM - 1) / TC_TM) * ((c + TC_TN - 1) / TC_TN); }
+int kchunks(int w) { return (2 * w + TC_CHUNK - 1) / TC_CHUNK; }
+
+// One tensor-core product on stream s with the maps of one operand set; timed
+// (CUDA events, algorithmic bytes: read and write of the rows x cols block of
+// C, one read of the two operand panels of width w) when kt is given.
+void tc_product(cudaStream_t s, const CUtensorMap &tA, const CUtensorMap &tB, const CUtensorMap &tC,
+                const CUtensorMap &tCs, const TcMap &mp, int grid, int *status, KernelTimer *kt, double rows,
+                double cols, int w) {
+    cudaEvent_t e0 = kt ? kt->next() : nullptr, e1 = kt ? kt->next() : nullptr;
+    if (e0) cudaEventRecord(e0, s);
+    k_tc_update<<<grid, TC_THREADS, TC_SMEM, s>>>(tA, tB, tC, tCs, mp, status); ++g_launches;
+    if (e1) {
+        cudaEventRecord(e1, s);
+        kt->add(e0, e1, 16.0 * rows * cols + 8.0 * (rows + cols) * w);
+    }
+}
+
+// In-place inverse of the w x w pivot block at Ab (row stride ld, w <= GJ_P):
+// Gauss-Jordan with 128-wide pivots (register inverse of each 128 block, then
+// its column-panel and trailing/row-panel products, K = 128).  sub: packed
+// operand scratch of 3 GJ_P rows.
+cudaError_t invert_pivot_block(float *Ab, size_t ld, int w, int *status, float *sub, int sms, cudaStream_t st) {
+    k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(Ab, ld, 0, std::min(w, GJ_W), status); ++g_launches;
+    if (w <= GJ_W) return cudaGetLastError();
+    float *Ap = sub, *Bp = sub + (size_t)GJ_P * TC_PACK_ROW;
+    const int wc = (w + 3) / 4 * 4;   // whole 16-byte column groups (padding columns stay zero)
+    CUtensorMap tA, tB, tC, tCs;
+    if (!tensor_map(&tA, Ap, TC_PACK_ROW, GJ_P, TC_PACK_ROW * 4, 32, TC_TM) ||
+        !tensor_map(&tB, Bp, TC_PACK_ROW, 2 * (uint64_t)GJ_P, TC_PACK_ROW * 4, 32, 2 * TC_TN) ||
+        !tensor_map(&tC, Ab, 2 * (uint64_t)wc, w, 8 * ld, 32, TC_TM) ||
+        !tensor_map(&tCs, Ab, 2 * (uint64_t)wc, w, 8 * ld, 32, 32))
+        return cudaErrorInvalidValue;
+    const int wp = (w + TC_TM - 1) / TC_TM * TC_TM;
+    for (int k1 = 0; k1 < w; k1 += GJ_W) {
+        const int wi = std::min(GJ_W, w - k1), m1 = w - wi;
+        if (k1 > 0) { k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(Ab, ld, k1, wi, status); ++g_launches; }
+        const int mp1 = (m1 + TC_TM - 1) / TC_TM * TC_TM;
+        k_tc_pack_a<<<(unsigned)((size_t)mp1 * TC_KP / 256), 256, 0, st>>>(Ab, ld, m1, k1, wi, k1, wi, mp1, Ap); ++g_launches;
+        k_tc_pack_b<<<dim3(TC_TN / 32, TC_KP / 32), 256, 0, st>>>(Ab, ld, wi, k1, wi, 0, k1, -1.f, Bp); ++g_launches;
+        tc_product(st, tA, tB, tC, tCs, TcMap{m1, wi, k1, wi, 0, k1, 0, 0, 1, 0, 0, 0, 0, kchunks(wi)},
+                   std::min(tiles(m1, wi), sms), status, nullptr, 0, 0, 0);
+        k_tc_pack_a<<<(unsigned)((size_t)wp * TC_KP / 256), 256, 0, st>>>(Ab, ld, w, k1, wi, w, 0, wp, Ap); ++g_launches;
+        k_tc_pack_b<<<dim3(mp1 / 32, TC_KP / 32), 256, 0, st>>>(Ab, ld, m1, k1, wi, k1, wi, 1.f, Bp); ++g_launches;
+        tc_product(st, tA, tB, tC, tCs, TcMap{w, m1, w, 0, k1, wi, k1 / TC_TM, 1, 0, 0, 0, 0, 0, kchunks(wi)},
+                   std::min(tiles(w, m1), sms), status, nullptr, 0, 0, 0);
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
+// One outer Gauss-Jordan step with pivot block P = A[k0:k0+w, k0:k0+w]
+// (w = 256; rows and columns outside it: the trailing set T):
+//   1. P <- P^-1                                  (invert_pivot_block)
 //   2. A[T, P] <- -A[T, P] P^-1                   (product (a): trailing rows x pivot columns, beta 0)
 //   3. A[T, T] <- A[T, T] + A[T, P] A[P, T],  A[P, T] <- P^-1 A[P, T]
 //      as one product over all rows in natural order (the pivot rows' A operand
-//      is P^-1) x the trailing columns, beta 0 on the pivot tile row
-// Products (a) and (3) run on the tensor cores from packed operands.
-// Look-ahead: product (3) is split into the tile column holding the next
+//      is P^-1) x the trailing columns, beta 0 on the pivot tile rows
+// Products (a) and (3) run on the tensor cores from packed operands (K = 256:
+// the HBM traffic of the inversion is proportional to n^3 / w).
+// Look-ahead: product (3) is split into the tile columns holding the next
 // pivot block (on st) and the rest (on aux, on all SMs but four).  The next
 // step's pivot inverse and column-panel product need only the first part, so
 // they run on st while the rest of (3) streams through HBM; the next row-panel
 // packing waits for it.  Consecutive steps use alternate packing buffers.
 cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, cudaStream_t aux,
                          KernelTimer *kt) {
-    static_assert(GJ_W == TC_KP, "the packed operands hold one pivot block");
-    static_assert(GJ_W == 128, "k_gj_diag_w maps its threads onto 128 columns");
     int dev = 0, sms = 0;
     {   // opt in to the large dynamic shared memory (per device, cheap to repeat)
         cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
@@ -535,12 +592,13 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
     const int mpmax = (n + TC_TM - 1) / TC_TM * TC_TM;
     const size_t set_floats = 3 * (size_t)mpmax * TC_PACK_ROW;
     float *Ap[2], *Bp[2];
+    float *sub = pack + 2 * set_floats;
     CUtensorMap tmA[2], tmB[2], tmC, tmCs;
     for (int b = 0; b < 2; ++b) {
         Ap[b] = pack + b * set_floats;
         Bp[b] = Ap[b] + (size_t)mpmax * TC_PACK_ROW;
     }
-    if (n > GJ_W) {
+    if (n > GJ_P) {
         for (int b = 0; b < 2; ++b)
             if (!tensor_map(&tmA[b], Ap[b], TC_PACK_ROW, mpmax, TC_PACK_ROW * 4, 32, TC_TM) ||
                 !tensor_map(&tmB[b], Bp[b], TC_PACK_ROW, 2 * (uint64_t)mpmax, TC_PACK_ROW * 4, 32, 2 * TC_TN))
@@ -553,63 +611,54 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
     cudaError_t e = cudaEventCreateWithFlags(&evP, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evB, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
-    auto tiles = [](int r, int c) { return ((r + TC_TM - 1) / TC_TM) * ((c + TC_TN - 1) / TC_TN); };
-    // one product on stream s, timed when kt is set and `timed` (the large
-    // products (3); the column-panel product (a) overlaps them and is left
-    // out); algorithmic bytes: read and write of the rows x cols block of C,
-    // one read of the two operand panels
-    auto product = [&](cudaStream_t s, int b, const TcMap &mp, int grid, double rows, double cols, int w,
-                       bool timed) {
-        cudaEvent_t e0 = (kt && timed) ? kt->next() : nullptr, e1 = (kt && timed) ? kt->next() : nullptr;
-        if (e0) cudaEventRecord(e0, s);
-        k_tc_update<<<grid, TC_THREADS, TC_SMEM, s>>>(tmA[b], tmB[b], tmC, tmCs, mp, status); ++g_launches;
-        if (e1) {
-            cudaEventRecord(e1, s);
-            kt->add(e0, e1, 16.0 * rows * cols + 8.0 * (rows + cols) * w);
-        }
-    };
     bool pending = false;   // the second part of the previous product (3) is running on aux
-    k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(A, ld, 0, std::min(n, GJ_W), status); ++g_launches;
-    for (int k0 = 0; k0 < n; k0 += GJ_W) {
-        const int w = (n - k0 < GJ_W) ? n - k0 : GJ_W;
+    e = invert_pivot_block(A, ld, std::min(n, GJ_P), status, sub, sms, st);
+    for (int k0 = 0; k0 < n && e == cudaSuccess; k0 += GJ_P) {
+        const int w = std::min(GJ_P, n - k0);
         const int m = n - w;
         if (m <= 0) break;
-        const int cur = (k0 / GJ_W) & 1;
+        const int cur = (k0 / GJ_P) & 1;
         const int mp = (m + TC_TM - 1) / TC_TM * TC_TM;
+        const int kc = kchunks(w);
         // (a) column panel: A[T, P] <- A[T, P] (-P^-1)
         k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, m, k0, w, k0, w, mp, Ap[cur]); ++g_launches;
-        k_tc_pack_b<<<dim3(TC_TN / 32, TC_KP / 32), 256, 0, st>>>(A, ld, w, k0, w, 0, k0, -1.f, Bp[cur]); ++g_launches;
-        product(st, cur, TcMap{m, w, k0, w, 0, k0, -1, 1, -1, -1}, std::min(tiles(m, w), sms), m, w, w, false);
+        k_tc_pack_b<<<dim3((w + TC_TN - 1) / TC_TN * TC_TN / 32, TC_KP / 32), 256, 0, st>>>(A, ld, w, k0, w, 0, k0, -1.f,
+                                                                                          Bp[cur]); ++g_launches;
+        tc_product(st, tmA[cur], tmB[cur], tmC, tmCs, TcMap{m, w, k0, w, 0, k0, 0, 0, 1, 0, 0, 0, 0, kc},
+                   std::min(tiles(m, w), sms), status, nullptr, 0, 0, 0);
         // (3) reads this step's row panel, which the previous step's second part wrote
         if (pending) { cudaStreamWaitEvent(st, evB, 0); pending = false; }
         k_tc_pack_a<<<(unsigned)((size_t)mpmax * TC_KP / 256), 256, 0, st>>>(A, ld, n, k0, w, n, 0, mpmax, Ap[cur]); ++g_launches;
         k_tc_pack_b<<<dim3(mp / 32, TC_KP / 32), 256, 0, st>>>(A, ld, m, k0, w, k0, w, 1.f, Bp[cur]); ++g_launches;
-        const TcMap mb = {n, m, n, 0, k0, w, k0 / TC_TM, 0, -1, -1};
-        const int nt = (m + TC_TN - 1) / TC_TN, ntm = (n + TC_TM - 1) / TC_TM;
-        const bool next = k0 + GJ_W < n;
-        if (next && nt > 1) {
-            const int tA = k0 / TC_TN;   // trailing column k0 is global column k0 + w: the next pivot block
+        const int ntm = (n + TC_TM - 1) / TC_TM, nt = (m + TC_TN - 1) / TC_TN;
+        const int prow = k0 / TC_TM, nprow = (w + TC_TM - 1) / TC_TM;   // pivot tile rows: beta 0
+        const TcMap mb = {n, m, n, 0, k0, w, prow, nprow, 0, 0, 0, 0, 0, kc};
+        const bool next = k0 + GJ_P < n;
+        const int tA = k0 / TC_TN, nA = std::min(GJ_P / TC_TN, nt - tA);   // tile columns of the next pivot block
+        if (next && nt > nA) {
             TcMap ma = mb, mr = mb;
-            ma.tx_only = tA;
-            mr.tx_skip = tA;
-            product(st, cur, ma, std::min(ntm, sms), n, std::min(TC_TN, m - k0), w, true);
+            ma.only_lo = tA; ma.only_n = nA;
+            mr.skip_lo = tA; mr.skip_n = nA;
+            const int colsA = std::min(nA * TC_TN, m - k0);
+            tc_product(st, tmA[cur], tmB[cur], tmC, tmCs, ma, std::min(ntm * nA, sms), status, kt, n, colsA, w);
             cudaEventRecord(evP, st);
             cudaStreamWaitEvent(aux, evP, 0);
-            product(aux, cur, mr, std::max(1, std::min(ntm * (nt - 1), sms - 4)), n, m - std::min(TC_TN, m - k0), w,
-                    true);
+            tc_product(aux, tmA[cur], tmB[cur], tmC, tmCs, mr, std::max(1, std::min(ntm * (nt - nA), sms - 4)),
+                       status, kt, n, m - colsA, w);
             cudaEventRecord(evB, aux);
             pending = true;
         } else {
-            product(st, cur, mb, std::min(tiles(n, m), sms), n, m, w, true);
+            tc_product(st, tmA[cur], tmB[cur], tmC, tmCs, mb, std::min(tiles(n, m), sms), status, kt, n, m, w);
         }
         if (next) {
-            const int k1 = k0 + GJ_W;
-            k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(A, ld, k1, std::min(n - k1, GJ_W), status); ++g_launches;
+            const int k1 = k0 + GJ_P;
+            e = invert_pivot_block(A + 2 * ((size_t)k1 * ld + k1), ld, std::min(n - k1, GJ_P), status, sub, sms, st);
         }
     }
     if (pending) cudaStreamWaitEvent(st, evB, 0);
     cudaEventDestroy(evP);
     cudaEventDestroy(evB);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

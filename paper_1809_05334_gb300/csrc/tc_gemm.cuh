@@ -10,7 +10,7 @@
 //   Ap [mp][2 KP]    row r: K complex entries of the r-th row of A (TF32-rounded)
 //   Bp [2 np][2 KP]  rows 2j, 2j+1: s (Re b, -Im b), s (Im b, Re b), b = B[k][j]
 // so that both operands are K-major and TMA-loadable (zero padded to 128-row
-// tiles and to KP = 128).  Rows and columns of C are addressed through
+// tiles and to KP = 256; a product reads the first kchunks x 32 real K).  Rows and columns of C are addressed through
 // skip maps (index i < at ? i : i + skip), so a product can cover the trailing
 // rows/columns around a pivot block, the pivot columns alone, or all rows.
 //
@@ -36,9 +36,9 @@ namespace vie {
 
 constexpr int TC_TM = 128;                        // complex rows per tile
 constexpr int TC_TN = 128;                        // complex columns per tile (256 real)
-constexpr int TC_KP = 128;                        // complex pivots per update (zero padded)
+constexpr int TC_KP = 256;                        // complex K of the packed operands (zero padded)
 constexpr int TC_CHUNK = 32;                      // real K per stage: one 128-byte swizzle row
-constexpr int TC_NCHUNK = 2 * TC_KP / TC_CHUNK;   // 8
+constexpr int TC_CCHUNK = 2 * TC_TN / TC_CHUNK;   // 8 chunks of 32 floats across a C tile
 constexpr int TC_A_BYTES = TC_TM * 128;           // 16 KB
 constexpr int TC_B_BYTES = 2 * TC_TN * 128;       // 32 KB
 constexpr int TC_C_BYTES = TC_TM * 128;           // 16 KB: 128 rows x 32 floats of C
@@ -49,7 +49,7 @@ constexpr int TC_SMEM = 1024 + TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + TC_CSLOTS
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr long long TC_WAIT_LIMIT = 20000000;     // polls of one wait (tens of ms)
 constexpr int TC_THREADS = 256;
-constexpr int TC_PACK_ROW = 2 * TC_KP;            // floats per packed row (1 KB)
+constexpr int TC_PACK_ROW = 2 * TC_KP;            // floats per packed row (2 KB)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -166,18 +166,21 @@ __global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, 
 // Index maps and scaling of one product: C rows r < mrows at row(r) =
 // r < rat ? r : r + rskip, columns c < ncols at col(c) = c < cat ? c : c + cskip
 // (rat, cat multiples of 128 or beyond the extent, so no tile straddles a
-// skip); beta = 0 on every tile if beta0_all, else on tile row beta0_row.
-// tx_only >= 0 restricts the product to that tile column; tx_skip >= 0
-// leaves that tile column out (the two halves of a split product).
+// skip); beta = 0 on every tile if beta0_all, else on the tile rows
+// [beta0_lo, beta0_lo + beta0_n).
+// only_n > 0 restricts the product to the tile columns [only_lo, only_lo +
+// only_n); skip_n > 0 leaves the tile columns [skip_lo, skip_lo + skip_n) out
+// (the two parts of a split product).  kchunks: chunks of 32 real K read.
 struct TcMap {
-    int mrows, ncols, rat, rskip, cat, cskip, beta0_row, beta0_all, tx_only, tx_skip;
+    int mrows, ncols, rat, rskip, cat, cskip, beta0_lo, beta0_n, beta0_all;
+    int only_lo, only_n, skip_lo, skip_n, kchunks;
 };
 
 // tile t of the product -> (tile row, tile column)
 __device__ __forceinline__ void tc_tile(const TcMap &mp, int ntx, int t, int &ty, int &tx) {
     ty = t / ntx;
     const int i = t % ntx;
-    tx = mp.tx_only >= 0 ? mp.tx_only : (mp.tx_skip >= 0 && i >= mp.tx_skip ? i + 1 : i);
+    tx = mp.only_n > 0 ? mp.only_lo + i : (mp.skip_n > 0 && i >= mp.skip_lo ? i + mp.skip_n : i);
 }
 
 // C <- beta C + Ap * Bp^T over the tiles of the map.  tmA, tmB: the packed
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntm = (mp.mrows + TC_TM - 1) / TC_TM, nt = (mp.ncols + TC_TN - 1) / TC_TN;
-    const int ntx = mp.tx_only >= 0 ? 1 : (mp.tx_skip >= 0 ? nt - 1 : nt);   // tile columns covered
+    const int ntx = mp.only_n > 0 ? mp.only_n : (mp.skip_n > 0 ? nt - mp.skip_n : nt);   // tile columns covered
     const int ntiles = ntm * ntx;
 
     if (tid == 0) {
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             int ty, tx;
             tc_tile(mp, ntx, t, ty, tx);
-            for (int kc = 0; kc < TC_NCHUNK; ++kc, ++it) {
+            for (int kc = 0; kc < mp.kchunks; ++kc, ++it) {
                 const int s = it % TC_STAGES;
                 if (it >= TC_STAGES && !mbar_wait(empty + s, (uint32_t)((it / TC_STAGES - 1) & 1))) { ok = false; break; }
                 mbar_expect_tx(full + s, TC_A_BYTES + TC_B_BYTES);
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (tl >= 2 && !mbar_wait(accempty + b, (uint32_t)((tl / 2 - 1) & 1))) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dcol = tmem + (uint32_t)(b * 256);
-            for (int kc = 0; kc < TC_NCHUNK; ++kc, ++it) {
+            for (int kc = 0; kc < mp.kchunks; ++kc, ++it) {
                 const int s = it % TC_STAGES;
                 if (!mbar_wait(full + s, (uint32_t)((it / TC_STAGES) & 1))) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_tile(mp, ntx, t, ty, tx);
             const int r0 = ty * TC_TM, c0 = tx * TC_TN;
             const int gr0 = r0 < mp.rat ? r0 : r0 + mp.rskip, gc0 = c0 < mp.cat ? c0 : c0 + mp.cskip;
-            for (int cc = 0; cc < TC_NCHUNK; ++cc, ++ci) {
+            for (int cc = 0; cc < TC_CCHUNK; ++cc, ++ci) {
                 const int s = ci % TC_CSLOTS;
                 if (ci >= TC_CSLOTS && !mbar_wait(cempty + s, (uint32_t)((ci / TC_CSLOTS - 1) & 1))) { ok = false; break; }
                 mbar_expect_tx(cfull + s, TC_C_BYTES);
@@ -319,11 +322,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_tile(mp, ntx, t, ty, tx);
             const int r0 = ty * TC_TM, c0 = tx * TC_TN;
             const int gr0 = r0 < mp.rat ? r0 : r0 + mp.rskip, gc0 = c0 < mp.cat ? c0 : c0 + mp.cskip;
-            const bool keep = !(mp.beta0_all || ty == mp.beta0_row);   // beta = 1 (else the product alone)
+            const bool keep = !(mp.beta0_all || (ty >= mp.beta0_lo && ty < mp.beta0_lo + mp.beta0_n));   // beta = 1
             const int b = tl & 1;
             if (!__all_sync(0xffffffffu, mbar_wait(accfull + b, (uint32_t)((tl / 2) & 1)))) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int cc = 0; cc < TC_NCHUNK; ++cc, ++ci) {
+            for (int cc = 0; cc < TC_CCHUNK; ++cc, ++ci) {
                 const int s = ci % TC_CSLOTS;
                 if (!__all_sync(0xffffffffu, mbar_wait(cfull + s, (uint32_t)((ci / TC_CSLOTS) & 1)))) { ok = false; break; }
                 uint32_t v[32];
