@@ -265,12 +265,26 @@ def roofline(last, n, peaks, fp32, n_tets):
                            "total_ms": last["k_far_tt_ms"], "launches": 1,
                            "gp_values_per_s": 16.0 * n_tets * n_tets / t}
     if last.get("k_tc_n"):
-        t = last["k_tc_ms"] / last["k_tc_n"] / 1e3
-        b = last["k_tc_bytes"] / last["k_tc_n"]
-        ach = b / t / 1e9
-        out["k_tc_update"] = {"bound": "hbm", "kernel": "k_tc_update", "achieved": ach, "peak": peak, "unit": "GB/s",
-                              "frac": ach / peak, "traffic": None, "peak_source": src,
-                              "total_ms": last["k_tc_ms"], "launches": last["k_tc_n"]}
+        # bound = whichever roof is lower for the algorithmic bytes and flops:
+        # HBM at the measured copy bandwidth, or TF32 tensor cores at the
+        # measured sustained bf16 rate x 1.1/2.25 (the nominal TF32/bf16 ratio)
+        t = last["k_tc_ms"] / 1e3
+        b, f = last["k_tc_bytes"], last.get("k_tc_flops", 0.0)
+        tpeak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * (1.1 / 2.25)
+        t_hbm = b / (peak * 1e9)
+        t_tc = f / (tpeak * 1e12)
+        if t_tc > t_hbm:
+            ach = f / t / 1e12
+            out["k_tc_update"] = {"bound": "tensor", "kernel": "k_tc_update", "achieved": ach, "peak": tpeak,
+                                  "unit": "TFLOP/s", "frac": ach / tpeak, "traffic": None,
+                                  "peak_source": "measured bf16 sustained x 1.1/2.25 (TF32)",
+                                  "hbm_gbs": b / t / 1e9, "hbm_frac": b / t / 1e9 / peak}
+        else:
+            ach = b / t / 1e9
+            out["k_tc_update"] = {"bound": "hbm", "kernel": "k_tc_update", "achieved": ach, "peak": peak,
+                                  "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": src,
+                                  "tf32_tflops": f / t / 1e12}
+        out["k_tc_update"].update({"total_ms": last["k_tc_ms"], "launches": last["k_tc_n"]})
     if last["k_matvec_n"]:
         # the Z products of GMRES and the block-inverse products of the
         # preconditioner applications (the same kernel)

@@ -106,9 +106,10 @@ typedef struct {
     int64_t far_pair_evals;              /* Green's-function evaluations of the
                                             tetrahedron-pair kernel (16 per pair)   */
     int64_t h2d_bytes, d2h_bytes;        /* host<->device bytes this solve copied    */
-    /* tensor-core update of the block inversion (options.timing = 1): total
-       device time of its k_tc_n launches and their algorithmic bytes (the
-       read-modify-write of the trailing matrix plus one read of the panels) */
+    /* tensor-core products of the block inversion (options.timing = 1): total
+       device time of the k_tc_n timed launches (trailing/row-panel products)
+       and their algorithmic bytes (read and write of the updated block plus
+       one read of the two operand panels) */
     double  k_tc_ms, k_tc_bytes;
     int32_t k_tc_n;
     int32_t n_launches;                  /* CUDA kernels this call launched          */
@@ -120,6 +121,7 @@ typedef struct {
        bytes (one read of every block inverse plus the vectors) */
     double  k_precond_ms, k_precond_bytes;
     int32_t k_precond_n, reserved3;
+    double  k_tc_flops;                  /* algorithmic flops of the k_tc_n launches */
 } vie_result;
 
 /* Fill *opt with defaults (FP32 with refinement, preconditioner on, tol 1e-6). */

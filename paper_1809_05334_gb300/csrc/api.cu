@@ -763,11 +763,13 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
         for (auto &p : tm.mv) s += ev_ms(p.first, p.second);
         res->k_matvec_ms = s;
         res->k_matvec_n = (int32_t)tm.mv.size();
-        double ts = 0, tb = 0;
+        double ts = 0, tb = 0, tf = 0;
         for (size_t i = 0; i < tm.tc.ev.size(); ++i) {
             ts += ev_ms(tm.tc.ev[i].first, tm.tc.ev[i].second);
             tb += tm.tc.work[i];
+            tf += tm.tc.flops[i];
         }
+        res->k_tc_flops = tf;
         res->k_tc_ms = ts;
         res->k_tc_bytes = tb;
         res->k_tc_n = (int32_t)tm.tc.ev.size();

@@ -519,8 +519,9 @@ int tiles(int r, int c) { return ((r + TC_TM - 1) / TC_TM) * ((c + TC_TN - 1) / 
 int kchunks(int w) { return (2 * w + TC_CHUNK - 1) / TC_CHUNK; }
 
 // One tensor-core product on stream s with the maps of one operand set; timed
-// (CUDA events, algorithmic bytes: read and write of the rows x cols block of
-// C, one read of the two operand panels of width w) when kt is given.
+// (CUDA events; algorithmic bytes: read and write of the rows x cols block of
+// C, one read of the two operand panels of width w; algorithmic flops
+// 8 rows cols w) when kt is given.
 void tc_product(cudaStream_t s, const CUtensorMap &tA, const CUtensorMap &tB, const CUtensorMap &tC,
                 const CUtensorMap &tCs, const TcMap &mp, int grid, int *status, KernelTimer *kt, double rows,
                 double cols, int w) {
@@ -529,7 +530,8 @@ void tc_product(cudaStream_t s, const CUtensorMap &tA, const CUtensorMap &tB, co
     k_tc_update<<<grid, TC_THREADS, TC_SMEM, s>>>(tA, tB, tC, tCs, mp, status); ++g_launches;
     if (e1) {
         cudaEventRecord(e1, s);
-        kt->add(e0, e1, 16.0 * rows * cols + 8.0 * (rows + cols) * w);
+        // a complex multiply-add is 8 real flops: 8 rows cols w per product
+        kt->add(e0, e1, 16.0 * rows * cols + 8.0 * (rows + cols) * w, 8.0 * rows * cols * w);
     }
 }
 

@@ -20,9 +20,14 @@ struct KernelTimer {
     cudaEvent_t (*alloc)(void *) = nullptr;   // returns the next event of the caller's pool
     void *pool = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-    std::vector<double> work;
+    std::vector<double> work;    // algorithmic bytes of each timed launch
+    std::vector<double> flops;   // and its algorithmic flops
     cudaEvent_t next() { return alloc ? alloc(pool) : nullptr; }
-    void add(cudaEvent_t a, cudaEvent_t b, double w) { ev.push_back({a, b}); work.push_back(w); }
+    void add(cudaEvent_t a, cudaEvent_t b, double w, double f = 0) {
+        ev.push_back({a, b});
+        work.push_back(w);
+        flops.push_back(f);
+    }
 };
 // the same inversion with 128-wide pivot blocks and the tcgen05 (TF32)
 // products; `pack` is device scratch of gj_pack_floats(n) floats (the packed
