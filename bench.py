@@ -243,10 +243,11 @@ def roofline(last, n, peaks, fp32, n_tets):
     k_far_tt (far tetrahedron pairs of the fill): FP32 CUDA-core bound ("alu");
     achieved = FAR_FLOPS_PER_VALUE x 16 n_tets^2 values / event time, against
     152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock.
-    k_tc_update (tensor-core products of the block inversion of Eq. (6), TF32):
-    arithmetic intensity ~ w/2 = 64 flop/B, below the TF32 ridge -> HBM-bound;
-    algorithmic bytes = read and write of the updated block + one read of the
-    two operand panels, per launch.
+    k_tc_update (tensor-core products of the block inversion of Eq. (6), FP16
+    operands, FP32 accumulation): K = 256 complex, ~128 flop per byte of the
+    updated block; algorithmic bytes = read and write of the updated block +
+    one read of the two packed FP16 operand panels, per launch; the roof is
+    whichever of HBM and the FP16 tensor rate binds for those bytes and flops.
     k_matvec (GMRES Z products and block-inverse products): HBM-bound; bytes =
     N ld 8 B (FP32 Z) + the two vectors per Z product, one read of every block
     inverse + the vectors per preconditioner application.
@@ -266,24 +267,24 @@ def roofline(last, n, peaks, fp32, n_tets):
                            "gp_values_per_s": 16.0 * n_tets * n_tets / t}
     if last.get("k_tc_n"):
         # bound = whichever roof is lower for the algorithmic bytes and flops:
-        # HBM at the measured copy bandwidth, or TF32 tensor cores at the
-        # measured sustained bf16 rate x 1.1/2.25 (the nominal TF32/bf16 ratio)
+        # HBM at the measured copy bandwidth, or FP16 tensor cores at the
+        # measured sustained bf16 rate (FP16 and bf16 have the same nominal rate)
         t = last["k_tc_ms"] / 1e3
         b, f = last["k_tc_bytes"], last.get("k_tc_flops", 0.0)
-        tpeak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * (1.1 / 2.25)
+        tpeak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         t_hbm = b / (peak * 1e9)
         t_tc = f / (tpeak * 1e12)
         if t_tc > t_hbm:
             ach = f / t / 1e12
             out["k_tc_update"] = {"bound": "tensor", "kernel": "k_tc_update", "achieved": ach, "peak": tpeak,
                                   "unit": "TFLOP/s", "frac": ach / tpeak, "traffic": None,
-                                  "peak_source": "measured bf16 sustained x 1.1/2.25 (TF32)",
+                                  "peak_source": "measured bf16 sustained (FP16 operands)",
                                   "hbm_gbs": b / t / 1e9, "hbm_frac": b / t / 1e9 / peak}
         else:
             ach = b / t / 1e9
             out["k_tc_update"] = {"bound": "hbm", "kernel": "k_tc_update", "achieved": ach, "peak": peak,
                                   "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": src,
-                                  "tf32_tflops": f / t / 1e12}
+                                  "tensor_tflops": f / t / 1e12, "tensor_frac": f / t / 1e12 / tpeak}
         out["k_tc_update"].update({"total_ms": last["k_tc_ms"], "launches": last["k_tc_n"]})
     if last["k_matvec_n"]:
         # the Z products of GMRES and the block-inverse products of the

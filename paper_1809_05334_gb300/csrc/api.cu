@@ -633,14 +633,14 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
     CK(ctx->Minv.ensure(sizeof(float) * 2 * std::max<size_t>(tot, 1)));
     CK(ctx->status.ensure(sizeof(int)));
     size_t pk = 1;
-    for (int nb : H.blk_n) pk = std::max(pk, vie::gj_pack_floats(nb));
-    CK(ctx->tcpack.ensure(sizeof(float) * pk));
+    for (int nb : H.blk_n) pk = std::max(pk, vie::gj_pack_bytes(nb));
+    CK(ctx->tcpack.ensure(pk));
     if (!ctx->aux_stream) CK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
     CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
     for (size_t k = 0; k < H.blk_n.size(); ++k) {
         float *B = ctx->Minv.as<float>() + 2 * moff[k];
         CK((vie::copy_block<TZ, float>(ctx->Z.as<TZ>(), ctx->ld, H.blk_off[k], H.blk_n[k], B, mld[k], st)));
-        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), ctx->tcpack.as<float>(), st,
+        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), ctx->tcpack.p, st,
                              ctx->aux_stream, kt));
     }
     // the applications read FP16 copies of the inverses, each scaled by a power

@@ -398,8 +398,8 @@ template cudaError_t gj_invert<float>(float *, size_t, int, int *, cudaStream_t)
 template cudaError_t gj_invert<double>(double *, size_t, int, int *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Gauss-Jordan with 64-wide pivot blocks and the tensor-core trailing update
-// (FP32 matrix, TF32 products with FP32 accumulation).
+// Gauss-Jordan with 256-wide outer pivot blocks and tensor-core products
+// (FP32 matrix; FP16 operands scaled by powers of two, FP32 accumulation).
 // ---------------------------------------------------------------------------
 constexpr int GJ_W = 128;     // pivot block width (the K of the tensor-core update)
 
@@ -487,17 +487,18 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// 2D FP32 tensor map, 128-byte swizzle: `inner` floats per row, `rows` rows
-// `row_bytes` apart, box of box_in floats x box_rows rows
-bool tensor_map(CUtensorMap *map, const float *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
-                uint32_t box_in, uint32_t box_rows) {
+// 2D tensor map (FP32 or FP16), 128-byte swizzle: `inner` elements per row,
+// `rows` rows `row_bytes` apart, box of box_in elements x box_rows rows
+bool tensor_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
+                uint32_t box_in, uint32_t box_rows, bool half = false) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
     cuuint64_t dims[2] = {inner, rows};
     cuuint64_t strides[1] = {row_bytes};
     cuuint32_t box[2] = {box_in, box_rows};
     cuuint32_t es[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+    return fn(map, half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base),
+              dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -507,21 +508,40 @@ constexpr int GJ_P = 256;   // pivot width of the outer Gauss-Jordan steps (the 
 static_assert(GJ_P <= TC_KP, "the packed operands hold one outer pivot block");
 static_assert(GJ_W == 128 && GJ_P == 2 * GJ_W, "a pivot block is inverted in two 128-wide steps");
 
-size_t gj_pack_floats(int n) {
-    // two sets (consecutive outer steps overlap) of Ap [mp] and Bp [2 mp] rows,
-    // and one set of 3 GJ_P rows for the inversion of the pivot blocks
+constexpr int GJ_WORDS = 16;   // largest-entry words: 4 per set (products (a), (3)), 2 for the pivot blocks
+
+size_t gj_pack_bytes(int n) {
+    // two sets (consecutive outer steps overlap) of Ap [mp] and Bp [2 mp] FP16
+    // rows, one set of 3 GJ_P rows for the inversion of the pivot blocks, and
+    // the largest-entry words of the packed operands
     const size_t mp = ((size_t)n + TC_TM - 1) / TC_TM * TC_TM;
-    return (2 * 3 * mp + 3 * (size_t)GJ_P) * TC_PACK_ROW;
+    return (2 * 3 * mp + 3 * (size_t)GJ_P) * TC_PACK_ROW * sizeof(__half) + GJ_WORDS * sizeof(unsigned);
 }
 
 namespace {
 int tiles(int r, int c) { return ((r + TC_TM - 1) / TC_TM) * ((c + TC_TN - 1) / TC_TN); }
-int kchunks(int w) { return (2 * w + TC_CHUNK - 1) / TC_CHUNK; }
+int kchunks(int w) { return (2 * w + TC_KCHUNK - 1) / TC_KCHUNK; }
+
+// Packs the operands of one product from A (row stride ld): panel pa into Ap
+// (mp rows, k_tc_pack_a) and panel pb, times sgn, into Bp (2 x 32 x bx rows,
+// k_tc_pack_b), each scaled by the power of two its largest entry (found first
+// into amax[0], amax[1]) selects.
+void tc_pack(cudaStream_t st, const float *A, size_t ld, const TcPanel &pa, int mp, const TcPanel &pb, float sgn,
+             int bx, unsigned *amax, __half *Ap, __half *Bp) {
+    cudaMemsetAsync(amax, 0, 2 * sizeof(unsigned), st);
+    const int big = std::max(pa.n1 * pa.w, pb.n1 * pb.w);
+    const unsigned gx = (unsigned)std::max(1, std::min((big + 2047) / 2048, 2 * 152));
+    k_tc_absmax<<<dim3(gx, 2), 256, 0, st>>>(A, ld, pa, pb, amax); ++g_launches;
+    k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, pa.n1, pa.c0, pa.w, pa.at, pa.skip, mp,
+                                                                       amax, Ap); ++g_launches;
+    k_tc_pack_b<<<dim3(bx, TC_KP / 32), 256, 0, st>>>(A, ld, pb.n1, pb.c0, pb.w, pb.at, pb.skip, sgn, amax + 1, Bp);
+    ++g_launches;
+}
 
 // One tensor-core product on stream s with the maps of one operand set; timed
 // (CUDA events; algorithmic bytes: read and write of the rows x cols block of
-// C, one read of the two operand panels of width w; algorithmic flops
-// 8 rows cols w) when kt is given.
+// C, one read of the two packed FP16 operand panels of width w; algorithmic
+// flops 8 rows cols w) when kt is given.
 void tc_product(cudaStream_t s, const CUtensorMap &tA, const CUtensorMap &tB, const CUtensorMap &tC,
                 const CUtensorMap &tCs, const TcMap &mp, int grid, int *status, KernelTimer *kt, double rows,
                 double cols, int w) {
@@ -531,22 +551,23 @@ void tc_product(cudaStream_t s, const CUtensorMap &tA, const CUtensorMap &tB, co
     if (e1) {
         cudaEventRecord(e1, s);
         // a complex multiply-add is 8 real flops: 8 rows cols w per product
-        kt->add(e0, e1, 16.0 * rows * cols + 8.0 * (rows + cols) * w, 8.0 * rows * cols * w);
+        kt->add(e0, e1, 16.0 * rows * cols + 4.0 * (rows + cols) * w, 8.0 * rows * cols * w);
     }
 }
 
 // In-place inverse of the w x w pivot block at Ab (row stride ld, w <= GJ_P):
 // Gauss-Jordan with 128-wide pivots (register inverse of each 128 block, then
 // its column-panel and trailing/row-panel products, K = 128).  sub: packed
-// operand scratch of 3 GJ_P rows.
-cudaError_t invert_pivot_block(float *Ab, size_t ld, int w, int *status, float *sub, int sms, cudaStream_t st) {
+// operand scratch of 3 GJ_P rows; amax: two largest-entry words.
+cudaError_t invert_pivot_block(float *Ab, size_t ld, int w, int *status, __half *sub, unsigned *amax, int sms,
+                               cudaStream_t st) {
     k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(Ab, ld, 0, std::min(w, GJ_W), status); ++g_launches;
     if (w <= GJ_W) return cudaGetLastError();
-    float *Ap = sub, *Bp = sub + (size_t)GJ_P * TC_PACK_ROW;
+    __half *Ap = sub, *Bp = sub + (size_t)GJ_P * TC_PACK_ROW;
     const int wc = (w + 3) / 4 * 4;   // whole 16-byte column groups (padding columns stay zero)
     CUtensorMap tA, tB, tC, tCs;
-    if (!tensor_map(&tA, Ap, TC_PACK_ROW, GJ_P, TC_PACK_ROW * 4, 32, TC_TM) ||
-        !tensor_map(&tB, Bp, TC_PACK_ROW, 2 * (uint64_t)GJ_P, TC_PACK_ROW * 4, 32, 2 * TC_TN) ||
+    if (!tensor_map(&tA, Ap, TC_PACK_ROW, GJ_P, TC_PACK_ROW * 2, TC_KCHUNK, TC_TM, true) ||
+        !tensor_map(&tB, Bp, TC_PACK_ROW, 2 * (uint64_t)GJ_P, TC_PACK_ROW * 2, TC_KCHUNK, 2 * TC_TN, true) ||
         !tensor_map(&tC, Ab, 2 * (uint64_t)wc, w, 8 * ld, 32, TC_TM) ||
         !tensor_map(&tCs, Ab, 2 * (uint64_t)wc, w, 8 * ld, 32, 32))
         return cudaErrorInvalidValue;
@@ -555,13 +576,11 @@ cudaError_t invert_pivot_block(float *Ab, size_t ld, int w, int *status, float *
         const int wi = std::min(GJ_W, w - k1), m1 = w - wi;
         if (k1 > 0) { k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(Ab, ld, k1, wi, status); ++g_launches; }
         const int mp1 = (m1 + TC_TM - 1) / TC_TM * TC_TM;
-        k_tc_pack_a<<<(unsigned)((size_t)mp1 * TC_KP / 256), 256, 0, st>>>(Ab, ld, m1, k1, wi, k1, wi, mp1, Ap); ++g_launches;
-        k_tc_pack_b<<<dim3(TC_TN / 32, TC_KP / 32), 256, 0, st>>>(Ab, ld, wi, k1, wi, 0, k1, -1.f, Bp); ++g_launches;
-        tc_product(st, tA, tB, tC, tCs, TcMap{m1, wi, k1, wi, 0, k1, 0, 0, 1, 0, 0, 0, 0, kchunks(wi)},
+        tc_pack(st, Ab, ld, TcPanel{m1, k1, wi, k1, wi}, mp1, TcPanel{wi, k1, wi, 0, k1}, -1.f, TC_TN / 32, amax, Ap, Bp);
+        tc_product(st, tA, tB, tC, tCs, TcMap{m1, wi, k1, wi, 0, k1, 0, 0, 1, 0, 0, 0, 0, kchunks(wi), amax},
                    std::min(tiles(m1, wi), sms), status, nullptr, 0, 0, 0);
-        k_tc_pack_a<<<(unsigned)((size_t)wp * TC_KP / 256), 256, 0, st>>>(Ab, ld, w, k1, wi, w, 0, wp, Ap); ++g_launches;
-        k_tc_pack_b<<<dim3(mp1 / 32, TC_KP / 32), 256, 0, st>>>(Ab, ld, m1, k1, wi, k1, wi, 1.f, Bp); ++g_launches;
-        tc_product(st, tA, tB, tC, tCs, TcMap{w, m1, w, 0, k1, wi, k1 / TC_TM, 1, 0, 0, 0, 0, 0, kchunks(wi)},
+        tc_pack(st, Ab, ld, TcPanel{w, k1, wi, w, 0}, wp, TcPanel{m1, k1, wi, k1, wi}, 1.f, mp1 / 32, amax, Ap, Bp);
+        tc_product(st, tA, tB, tC, tCs, TcMap{w, m1, w, 0, k1, wi, k1 / TC_TM, 1, 0, 0, 0, 0, 0, kchunks(wi), amax},
                    std::min(tiles(w, m1), sms), status, nullptr, 0, 0, 0);
     }
     return cudaGetLastError();
@@ -582,7 +601,7 @@ cudaError_t invert_pivot_block(float *Ab, size_t ld, int w, int *status, float *
 // step's pivot inverse and column-panel product need only the first part, so
 // they run on st while the rest of (3) streams through HBM; the next row-panel
 // packing waits for it.  Consecutive steps use alternate packing buffers.
-cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, cudaStream_t aux,
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cudaStream_t st, cudaStream_t aux,
                          KernelTimer *kt) {
     int dev = 0, sms = 0;
     {   // opt in to the large dynamic shared memory (per device, cheap to repeat)
@@ -592,18 +611,21 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
         if (e != cudaSuccess) return e;
     }
     const int mpmax = (n + TC_TM - 1) / TC_TM * TC_TM;
-    const size_t set_floats = 3 * (size_t)mpmax * TC_PACK_ROW;
-    float *Ap[2], *Bp[2];
-    float *sub = pack + 2 * set_floats;
+    const size_t set_halves = 3 * (size_t)mpmax * TC_PACK_ROW;
+    __half *const base = static_cast<__half *>(pack);
+    __half *Ap[2], *Bp[2];
+    __half *sub = base + 2 * set_halves;
+    unsigned *words = reinterpret_cast<unsigned *>(sub + 3 * (size_t)GJ_P * TC_PACK_ROW);   // GJ_WORDS
     CUtensorMap tmA[2], tmB[2], tmC, tmCs;
     for (int b = 0; b < 2; ++b) {
-        Ap[b] = pack + b * set_floats;
+        Ap[b] = base + b * set_halves;
         Bp[b] = Ap[b] + (size_t)mpmax * TC_PACK_ROW;
     }
     if (n > GJ_P) {
         for (int b = 0; b < 2; ++b)
-            if (!tensor_map(&tmA[b], Ap[b], TC_PACK_ROW, mpmax, TC_PACK_ROW * 4, 32, TC_TM) ||
-                !tensor_map(&tmB[b], Bp[b], TC_PACK_ROW, 2 * (uint64_t)mpmax, TC_PACK_ROW * 4, 32, 2 * TC_TN))
+            if (!tensor_map(&tmA[b], Ap[b], TC_PACK_ROW, mpmax, TC_PACK_ROW * 2, TC_KCHUNK, TC_TM, true) ||
+                !tensor_map(&tmB[b], Bp[b], TC_PACK_ROW, 2 * (uint64_t)mpmax, TC_PACK_ROW * 2, TC_KCHUNK, 2 * TC_TN,
+                            true))
                 return cudaErrorInvalidValue;
         if (!tensor_map(&tmC, A, 2 * (uint64_t)ld, n, 8 * ld, 32, TC_TM) ||
             !tensor_map(&tmCs, A, 2 * (uint64_t)ld, n, 8 * ld, 32, 32))
@@ -614,7 +636,7 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evB, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
     bool pending = false;   // the second part of the previous product (3) is running on aux
-    e = invert_pivot_block(A, ld, std::min(n, GJ_P), status, sub, sms, st);
+    e = invert_pivot_block(A, ld, std::min(n, GJ_P), status, sub, words + 8, sms, st);
     for (int k0 = 0; k0 < n && e == cudaSuccess; k0 += GJ_P) {
         const int w = std::min(GJ_P, n - k0);
         const int m = n - w;
@@ -622,19 +644,18 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
         const int cur = (k0 / GJ_P) & 1;
         const int mp = (m + TC_TM - 1) / TC_TM * TC_TM;
         const int kc = kchunks(w);
+        unsigned *wa = words + 4 * cur, *w3 = wa + 2;   // this set's largest-entry words
         // (a) column panel: A[T, P] <- A[T, P] (-P^-1)
-        k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, m, k0, w, k0, w, mp, Ap[cur]); ++g_launches;
-        k_tc_pack_b<<<dim3((w + TC_TN - 1) / TC_TN * TC_TN / 32, TC_KP / 32), 256, 0, st>>>(A, ld, w, k0, w, 0, k0, -1.f,
-                                                                                          Bp[cur]); ++g_launches;
-        tc_product(st, tmA[cur], tmB[cur], tmC, tmCs, TcMap{m, w, k0, w, 0, k0, 0, 0, 1, 0, 0, 0, 0, kc},
+        tc_pack(st, A, ld, TcPanel{m, k0, w, k0, w}, mp, TcPanel{w, k0, w, 0, k0}, -1.f,
+                (w + TC_TN - 1) / TC_TN * TC_TN / 32, wa, Ap[cur], Bp[cur]);
+        tc_product(st, tmA[cur], tmB[cur], tmC, tmCs, TcMap{m, w, k0, w, 0, k0, 0, 0, 1, 0, 0, 0, 0, kc, wa},
                    std::min(tiles(m, w), sms), status, nullptr, 0, 0, 0);
         // (3) reads this step's row panel, which the previous step's second part wrote
         if (pending) { cudaStreamWaitEvent(st, evB, 0); pending = false; }
-        k_tc_pack_a<<<(unsigned)((size_t)mpmax * TC_KP / 256), 256, 0, st>>>(A, ld, n, k0, w, n, 0, mpmax, Ap[cur]); ++g_launches;
-        k_tc_pack_b<<<dim3(mp / 32, TC_KP / 32), 256, 0, st>>>(A, ld, m, k0, w, k0, w, 1.f, Bp[cur]); ++g_launches;
+        tc_pack(st, A, ld, TcPanel{n, k0, w, n, 0}, mpmax, TcPanel{m, k0, w, k0, w}, 1.f, mp / 32, w3, Ap[cur], Bp[cur]);
         const int ntm = (n + TC_TM - 1) / TC_TM, nt = (m + TC_TN - 1) / TC_TN;
         const int prow = k0 / TC_TM, nprow = (w + TC_TM - 1) / TC_TM;   // pivot tile rows: beta 0
-        const TcMap mb = {n, m, n, 0, k0, w, prow, nprow, 0, 0, 0, 0, 0, kc};
+        const TcMap mb = {n, m, n, 0, k0, w, prow, nprow, 0, 0, 0, 0, 0, kc, w3};
         const bool next = k0 + GJ_P < n;
         const int tA = k0 / TC_TN, nA = std::min(GJ_P / TC_TN, nt - tA);   // tile columns of the next pivot block
         if (next && nt > nA) {
@@ -654,7 +675,8 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, c
         }
         if (next) {
             const int k1 = k0 + GJ_P;
-            e = invert_pivot_block(A + 2 * ((size_t)k1 * ld + k1), ld, std::min(n - k1, GJ_P), status, sub, sms, st);
+            e = invert_pivot_block(A + 2 * ((size_t)k1 * ld + k1), ld, std::min(n - k1, GJ_P), status, sub, words + 8,
+                                   sms, st);
         }
     }
     if (pending) cudaStreamWaitEvent(st, evB, 0);

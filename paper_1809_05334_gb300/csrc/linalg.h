@@ -29,12 +29,13 @@ struct KernelTimer {
         flops.push_back(f);
     }
 };
-// the same inversion with 128-wide pivot blocks and the tcgen05 (TF32)
-// products; `pack` is device scratch of gj_pack_floats(n) floats (the packed
-// operands), aux a second stream of the caller (look-ahead); the work is
-// complete on st when the last call returns on it
-size_t gj_pack_floats(int n);
-cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, float *pack, cudaStream_t st, cudaStream_t aux,
+// the same inversion with 256-wide outer pivot blocks and the tcgen05
+// products (FP16 operands with power-of-two scales, FP32 accumulation);
+// `pack` is device scratch of gj_pack_bytes(n) bytes (the packed operands and
+// their scale words), aux a second stream of the caller (look-ahead); the work
+// is complete on st when the last call returns on it
+size_t gj_pack_bytes(int n);
+cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cudaStream_t st, cudaStream_t aux,
                          KernelTimer *kt = nullptr);
 // *out (zeroed by the caller) <- max |A[i]| over count floats, as float bits
 cudaError_t absmax(const float *A, size_t count, unsigned *out, cudaStream_t st);

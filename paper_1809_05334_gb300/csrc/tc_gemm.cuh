@@ -1,24 +1,27 @@
-// Complex FP32 products C <- beta C + A B (K <= 128) of the Gauss-Jordan
+// Complex FP32 products C <- beta C + A B (K <= 256) of the Gauss-Jordan
 // inversion of the domain blocks of Eq. (6), on the 5th-generation tensor
-// cores (tcgen05, kind::tf32, accumulators in tensor memory), with every
-// operand moved by TMA.
+// cores (tcgen05, kind::f16 with FP16 operands and FP32 accumulators in tensor
+// memory), with every operand moved by TMA.  FP16 keeps the 10-bit mantissa
+// of TF32 at half the operand bytes and twice the rate; its range is handled
+// by a power-of-two scale per packed operand (its largest entry brought to
+// [2^13, 2^14)), undone in the epilogue.
 //
 // A complex product is one real product of the real views:
 //   C_rv (M x 2N) += A_rv (M x 2K) * Bt (2K x 2N)
 // where the real view of a row-major complex matrix interleaves (re, im) and
-// Bt is the 2x2 real expansion of B (times a sign).  Pack kernels write
-//   Ap [mp][2 KP]    row r: K complex entries of the r-th row of A (TF32-rounded)
+// Bt is the 2x2 real expansion of B (times a sign).  Pack kernels write (FP16)
+//   Ap [mp][2 KP]    row r: K complex entries of the r-th row of A
 //   Bp [2 np][2 KP]  rows 2j, 2j+1: s (Re b, -Im b), s (Im b, Re b), b = B[k][j]
 // so that both operands are K-major and TMA-loadable (zero padded to 128-row
-// tiles and to KP = 256; a product reads the first kchunks x 32 real K).  Rows and columns of C are addressed through
+// tiles and to KP = 256; a product reads the first kchunks x 64 real K).  Rows and columns of C are addressed through
 // skip maps (index i < at ? i : i + skip), so a product can cover the trailing
 // rows/columns around a pivot block, the pivot columns alone, or all rows.
 //
 // k_tc_update is persistent (one CTA per SM, tiles of 128 x 128 complex taken
 // round-robin) and warp-specialised:
-//   warp 0   TMA producer of the A/B chunks (32 real K each) into a 3-stage ring
+//   warp 0   TMA producer of the A/B chunks (64 real K each) into a 3-stage ring
 //   warp 1   tensor-memory allocation (512 columns = two 128 x 256 FP32
-//            accumulators) and the MMA issuer (M=128, N=256, K=8)
+//            accumulators) and the MMA issuer (M=128, N=256, K=16)
 //   warp 2   TMA producer of C, in 128-row x 32-float chunks, into a 4-slot ring
 //   warps 4-7  epilogue: tcgen05.ld of the accumulator (lane = row), add to the
 //            staged C chunk, TMA store of each warp's 32 rows
@@ -29,6 +32,7 @@
 // barrier other than the final __syncthreads spans several warps.
 #pragma once
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -37,8 +41,8 @@ namespace vie {
 constexpr int TC_TM = 128;                        // complex rows per tile
 constexpr int TC_TN = 128;                        // complex columns per tile (256 real)
 constexpr int TC_KP = 256;                        // complex K of the packed operands (zero padded)
-constexpr int TC_CHUNK = 32;                      // real K per stage: one 128-byte swizzle row
-constexpr int TC_CCHUNK = 2 * TC_TN / TC_CHUNK;   // 8 chunks of 32 floats across a C tile
+constexpr int TC_KCHUNK = 64;                     // real K (FP16) per stage: one 128-byte swizzle row
+constexpr int TC_CCHUNK = 2 * TC_TN / 32;         // 8 chunks of 32 floats across a C tile
 constexpr int TC_A_BYTES = TC_TM * 128;           // 16 KB
 constexpr int TC_B_BYTES = 2 * TC_TN * 128;       // 32 KB
 constexpr int TC_C_BYTES = TC_TM * 128;           // 16 KB: 128 rows x 32 floats of C
@@ -49,7 +53,7 @@ constexpr int TC_SMEM = 1024 + TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + TC_CSLOTS
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr long long TC_WAIT_LIMIT = 20000000;     // polls of one wait (tens of ms)
 constexpr int TC_THREADS = 256;
-constexpr int TC_PACK_ROW = 2 * TC_KP;            // floats per packed row (2 KB)
+constexpr int TC_PACK_ROW = 2 * TC_KP;            // FP16 entries per packed row (1 KB)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -66,14 +70,21 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;
 }
 
-// instruction descriptor: D f32, A/B tf32, K-major, N = 256, M = 128
-constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor: D f32, A and B f16, K-major, N = 256, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+// Exponent x of the power-of-two scale 2^x that brings a packed operand's
+// largest entry (given as the bits of a non-negative float) into [2^13, 2^14):
+// x = 13 - e for amax = 1.f.. x 2^e, read from the exponent field; 0 for a zero
+// or non-finite amax; clamped to [-120, 120] (subnormal amax take 120).
+__device__ __forceinline__ int tc_shift(unsigned amax_bits) {
+    const int be = (int)((amax_bits >> 23) & 0xffu);
+    if (amax_bits == 0u || be == 0xff) return 0;
+    const int x = 13 - (be - 127);
+    return x < -120 ? -120 : (x > 120 ? 120 : x);
 }
+__device__ __forceinline__ float tc_pow2(int x) { return __int_as_float((127 + x) << 23); }   // |x| <= 126
+
 
 // bounded wait on an mbarrier phase; returns false on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
@@ -117,10 +128,42 @@ __device__ __forceinline__ void mma_commit(uint64_t *mbar) {
                  ::"r"(smem_u32(mbar)) : "memory");
 }
 
-// Ap[r][2k..2k+1] = A[row(r)][col0 + k] for r < rows, k < w, with
-// row(r) = r < at ? r : r + skip; zero elsewhere up to mp rows.
+// One operand panel of a product, as the pack kernels read it: mode A (k_tc_pack_a)
+// rows r < n1 at row(r) = r < at ? r : r + skip, columns c0 .. c0 + w; mode B
+// (k_tc_pack_b) rows c0 .. c0 + w, columns j < n1 at col(j) = j < at ? j : j + skip.
+struct TcPanel {
+    int n1, c0, w, at, skip;
+};
+
+// Largest |Re|, |Im| of panel pa (blockIdx.y = 0, mode A) and pb (1, mode B),
+// atomicMax-ed as float bits into out[blockIdx.y] (zeroed by the caller).
+__global__ void __launch_bounds__(256) k_tc_absmax(const float *__restrict__ A, size_t ld, TcPanel pa, TcPanel pb,
+                                                   unsigned *out) {
+    const bool mb = blockIdx.y != 0;
+    const TcPanel p = mb ? pb : pa;
+    const int tot = p.n1 * p.w;
+    float mx = 0.f;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+        size_t idx;
+        if (!mb) {   // row r (mapped), column c0 + k: consecutive e along a row
+            const int r = e / p.w, k = e - r * p.w;
+            idx = (size_t)(r < p.at ? r : r + p.skip) * ld + p.c0 + k;
+        } else {     // row c0 + k, column j (mapped): consecutive e along a row
+            const int k = e / p.n1, j = e - k * p.n1;
+            idx = (size_t)(p.c0 + k) * ld + (j < p.at ? j : j + p.skip);
+        }
+        const float2 v = *reinterpret_cast<const float2 *>(A + 2 * idx);
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, __float_as_uint(mx));
+}
+
+// Ap[r][2k..2k+1] = s A[row(r)][col0 + k] for r < rows, k < w, with
+// row(r) = r < at ? r : r + skip; zero elsewhere up to mp rows; s from *amax.
 __global__ void __launch_bounds__(256) k_tc_pack_a(const float *__restrict__ A, size_t ld, int rows, int col0, int w,
-                                                   int at, int skip, int mp, float *__restrict__ Ap) {
+                                                   int at, int skip, int mp, const unsigned *__restrict__ amax,
+                                                   __half *__restrict__ Ap) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)mp * TC_KP) return;
     const int r = (int)(e / TC_KP), k = (int)(e % TC_KP);
@@ -129,16 +172,18 @@ __global__ void __launch_bounds__(256) k_tc_pack_a(const float *__restrict__ A, 
         const int gr = r < at ? r : r + skip;
         v = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)gr * ld + col0 + k));
     }
-    *reinterpret_cast<float2 *>(Ap + (size_t)r * TC_PACK_ROW + 2 * k) = make_float2(to_tf32(v.x), to_tf32(v.y));
+    const float s = tc_pow2(tc_shift(*amax));
+    *reinterpret_cast<__half2 *>(Ap + (size_t)r * TC_PACK_ROW + 2 * k) = __floats2half2_rn(s * v.x, s * v.y);
 }
 
-// The sign-scaled real expansion of B[k][j] = A[row0 + k][col(j)] (k < w,
-// j < cols, col(j) = j < at ? j : j + skip), K-major:
-//   Bp[2j][2k..] = sgn (Re b, -Im b),  Bp[2j+1][2k..] = sgn (Im b, Re b)
+// The sign- and power-of-two-scaled real expansion of B[k][j] = A[row0 + k][col(j)]
+// (k < w, j < cols, col(j) = j < at ? j : j + skip), K-major:
+//   Bp[2j][2k..] = sgn s (Re b, -Im b),  Bp[2j+1][2k..] = sgn s (Im b, Re b)
 // through a 32 x 32 shared-memory transpose (coalesced on both sides); rows up
 // to 2 * 32 * gridDim.x are written (zero beyond cols).
 __global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, size_t ld, int cols, int row0, int w,
-                                                   int at, int skip, float sgn, float *__restrict__ Bp) {
+                                                   int at, int skip, float sgn, const unsigned *__restrict__ amax,
+                                                   __half *__restrict__ Bp) {
     __shared__ float2 t[32][33];
     const int j0 = blockIdx.x * 32, kb = blockIdx.y * 32;
     for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
@@ -152,14 +197,13 @@ __global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, 
         t[kk][jj] = v;
     }
     __syncthreads();
+    const float g = sgn * tc_pow2(tc_shift(*amax));
     for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
         const int jj = idx / 32, kk = idx % 32;
         const float2 v = t[kk][jj];
         const size_t j = (size_t)(j0 + jj), k = (size_t)(kb + kk);
-        *reinterpret_cast<float2 *>(Bp + (2 * j) * TC_PACK_ROW + 2 * k) =
-            make_float2(to_tf32(sgn * v.x), to_tf32(-sgn * v.y));
-        *reinterpret_cast<float2 *>(Bp + (2 * j + 1) * TC_PACK_ROW + 2 * k) =
-            make_float2(to_tf32(sgn * v.y), to_tf32(sgn * v.x));
+        *reinterpret_cast<__half2 *>(Bp + (2 * j) * TC_PACK_ROW + 2 * k) = __floats2half2_rn(g * v.x, -g * v.y);
+        *reinterpret_cast<__half2 *>(Bp + (2 * j + 1) * TC_PACK_ROW + 2 * k) = __floats2half2_rn(g * v.y, g * v.x);
     }
 }
 
@@ -170,10 +214,11 @@ __global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, 
 // [beta0_lo, beta0_lo + beta0_n).
 // only_n > 0 restricts the product to the tile columns [only_lo, only_lo +
 // only_n); skip_n > 0 leaves the tile columns [skip_lo, skip_lo + skip_n) out
-// (the two parts of a split product).  kchunks: chunks of 32 real K read.
+// (the two parts of a split product).  kchunks: chunks of 64 real K read.
 struct TcMap {
     int mrows, ncols, rat, rskip, cat, cskip, beta0_lo, beta0_n, beta0_all;
     int only_lo, only_n, skip_lo, skip_n, kchunks;
+    const unsigned *amax;   // [2]: the float bits of the largest entries packed into A and B
 };
 
 // tile t of the product -> (tile row, tile column)
@@ -242,8 +287,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int s = it % TC_STAGES;
                 if (it >= TC_STAGES && !mbar_wait(empty + s, (uint32_t)((it / TC_STAGES - 1) & 1))) { ok = false; break; }
                 mbar_expect_tx(full + s, TC_A_BYTES + TC_B_BYTES);
-                tma_load_2d(sA + s * TC_A_BYTES, &tmA, kc * TC_CHUNK, ty * TC_TM, full + s);
-                tma_load_2d(sB + s * TC_B_BYTES, &tmB, kc * TC_CHUNK, 2 * tx * TC_TN, full + s);
+                tma_load_2d(sA + s * TC_A_BYTES, &tmA, kc * TC_KCHUNK, ty * TC_TM, full + s);
+                tma_load_2d(sB + s * TC_B_BYTES, &tmB, kc * TC_KCHUNK, 2 * tx * TC_TN, full + s);
             }
         }
         if (!ok) atomicExch(err, 2);
@@ -269,13 +314,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t a0 = smem_u32(sA + s * TC_A_BYTES), b0 = smem_u32(sB + s * TC_B_BYTES);
 #pragma unroll
-                for (int q = 0; q < TC_CHUNK / 8; ++q) {
+                for (int q = 0; q < TC_KCHUNK / 16; ++q) {   // K = 16 per MMA, 32 bytes along the row
                     const uint64_t da = make_desc(a0 + q * 32), db = make_desc(b0 + q * 32);
                     const uint32_t acc = (kc > 0 || q > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "setp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                         ::"r"(dcol), "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc));
                 }
                 mma_commit(empty + s);   // frees the stage once these MMAs have read it
@@ -315,6 +360,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---- epilogue: TMEM lane = row; warp q owns rows 32q..32q+31 of the tile --
         const int q4 = warp - 4;
         const int row = q4 * 32 + lane;
+        const float unscale = tc_pow2(-tc_shift(mp.amax[0])) * tc_pow2(-tc_shift(mp.amax[1]));   // exact: powers of two
         int ci = 0, tl = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
@@ -348,10 +394,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int q = 0; q < 8; ++q) {
                     float4 *p = reinterpret_cast<float4 *>(rp + ((q ^ (row & 7)) << 4));
                     float4 c = keep ? *p : make_float4(0.f, 0.f, 0.f, 0.f);
-                    c.x += __uint_as_float(v[4 * q]);
-                    c.y += __uint_as_float(v[4 * q + 1]);
-                    c.z += __uint_as_float(v[4 * q + 2]);
-                    c.w += __uint_as_float(v[4 * q + 3]);
+                    c.x = fmaf(unscale, __uint_as_float(v[4 * q]), c.x);
+                    c.y = fmaf(unscale, __uint_as_float(v[4 * q + 1]), c.y);
+                    c.z = fmaf(unscale, __uint_as_float(v[4 * q + 2]), c.z);
+                    c.w = fmaf(unscale, __uint_as_float(v[4 * q + 3]), c.w);
                     *p = c;
                 }
                 // make the generic-proxy writes visible to the bulk copy, then store the warp's rows
