@@ -270,15 +270,13 @@ int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
         E.Ef = (float)E.E;
         E.kx = (float)H.kx; E.ky = (float)H.ky;
         E.step_x = (float)(2 * M_PI / a); E.step_y = (float)(2 * M_PI / b);
-        const int P = (int)std::ceil((2.0 * E.E * xc32 + std::fabs(H.kx)) * a / (2 * M_PI)) + 1;
-        const int Q = (int)std::ceil((2.0 * E.E * xc32 + std::fabs(H.ky)) * b / (2 * M_PI)) + 1;
-        if ((2 * P + 1) * (2 * Q + 1) > vie::MAX_MODE) return fail(ctx, VIE_EINVAL, "too many Floquet modes for the table");
-        E.P = P; E.Q = Q;
+        if (!vie::mode_rect(H.kx, H.ky, a, b, 2.0 * E.E * xc32 + k0, E.p0, E.np, E.q0, E.nq))
+            return fail(ctx, VIE_EINVAL, "too many Floquet modes for the table");
         int nt = 0;
         std::vector<double> g2s;
-        for (int p = -P; p <= P; ++p)
-            for (int q = -Q; q <= Q; ++q) {
-                const int idx = (p + P) * (2 * Q + 1) + (q + Q);
+        for (int p = E.p0; p < E.p0 + E.np; ++p)
+            for (int q = E.q0; q < E.q0 + E.nq; ++q) {
+                const int idx = (p - E.p0) * E.nq + (q - E.q0);
                 const double ktx = H.kx + 2 * M_PI * p / a, kty = H.ky + 2 * M_PI * q / b;
                 const double kt2 = ktx * ktx + kty * kty;
                 if (std::sqrt(kt2) > 2.0 * E.E * xc32 + k0) { E.rect_tab[idx] = -1; continue; }

@@ -193,23 +193,24 @@ template <bool PAIR>
 __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, unsigned sub, const float *stab,
                                                const float2 *__restrict__ ztab, const EwaldF32 &ew,
                                                cx<float> &gp, cx<float> &gm,
-                                               const float4 *__restrict__ rtab = nullptr) {
+                                               const float4 *__restrict__ rtab = nullptr,
+                                               unsigned long long imask = ~0ull) {
     cx<float> acc = {0.f, 0.f}, acc2 = {0.f, 0.f};
     const float z = fabsf(dz);
     float zu = fminf(z * ew.z_inv_h, float(NZTAB));
     int iz = min((int)zu, NZTAB - 1);
     const float u = zu - iz;
-    const int P = ew.P, Q = ew.Q, nq = 2 * Q + 1;
+    const int np = ew.np, nq = ew.nq;
     float s, c;
-    sincospif(-(ew.kx - P * ew.step_x) * dx * 0.31830988618f, &s, &c);
+    sincospif(-(ew.kx + ew.p0 * ew.step_x) * dx * 0.31830988618f, &s, &c);
     cx<float> ex = {c, s};
     sincospif(-ew.step_x * dx * 0.31830988618f, &s, &c);
     const cx<float> sx = {c, s};
-    sincospif(-(ew.ky - Q * ew.step_y) * dy * 0.31830988618f, &s, &c);
+    sincospif(-(ew.ky + ew.q0 * ew.step_y) * dy * 0.31830988618f, &s, &c);
     cx<float> ey0 = {c, s};
     sincospif(-ew.step_y * dy * 0.31830988618f, &s, &c);
     const cx<float> sy = {c, s};
-    for (int p = 0; p <= 2 * P; ++p) {
+    for (int p = 0; p < np; ++p) {
         cx<float> inner = {0.f, 0.f}, inner2 = {0.f, 0.f};
         cx<float> ey = ey0;
         for (int q = 0; q < nq; ++q) {
@@ -243,15 +244,15 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
     const float E = ew.Ef;
     const float xmax = ew.xs_max, ih = ew.xs_inv_h;
     const float r2max = (xmax / E) * (xmax / E) * 1.0001f;   // loose: the exact test follows
-    for (int i = 0; i < ew.n_img; ++i) {
+    auto image = [&](int i) {
         const float *im = ew.img[i];
         const float x = dx + im[0], y = dy + im[1];
         const float R2 = x * x + y * y + dz * dz;
-        if (R2 > r2max) continue;          // outside the cut: skip before the square root
+        if (R2 > r2max) return;            // outside the cut: skip before the square root
         const float rinv = R2 > 0.f ? rsqrtf(R2) : 0.f;   // R = 0 only on a regularised image (no 1/R)
         const float R = R2 * rinv;
         const float xr = R * E;
-        if (xr > xmax) continue;
+        if (xr > xmax) return;
         bool regular = false;
         if (sub) {
 #pragma unroll
@@ -277,9 +278,30 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
             acc2.re = fmaf(val, im[2], acc2.re);
             acc2.im = fmaf(-val, im[3], acc2.im);
         }
-    }
+    };
+    // images 0..63 as the caller's mask selects them (it leaves out only images
+    // beyond the cut), the rest one by one
+    if (ew.n_img < 64) imask &= (1ull << ew.n_img) - 1ull;
+    for (unsigned long long mk = imask; mk; mk &= mk - 1ull) image(__ffsll((long long)mk) - 1);
+    for (int i = 64; i < ew.n_img; ++i) image(i);
     gp = acc;
     gm = acc2;
+}
+
+// Images (of the first 64) that can lie inside the spatial cut for some
+// displacement within `rad` of (cx, cy, cz): every image whose shifted centre
+// distance exceeds the cut radius + rad is left out.
+__device__ __forceinline__ unsigned long long image_mask(const EwaldF32 &ew, float cx, float cy, float cz,
+                                                         float rad) {
+    const float rc = ew.xs_max / ew.Ef * 1.0001f + rad * 1.0001f + 1e-6f * (fabsf(cx) + fabsf(cy) + fabsf(cz));
+    const float rc2 = rc * rc;
+    const int n = min(ew.n_img, 64);
+    unsigned long long m = 0ull;
+    for (int i = 0; i < n; ++i) {
+        const float x = cx + ew.img[i][0], y = cy + ew.img[i][1];
+        if (x * x + y * y + cz * cz <= rc2) m |= 1ull << i;
+    }
+    return m;
 }
 
 __device__ __forceinline__ cx<float> green_tab(float dx, float dy, float dz, unsigned sub, const float *stab,

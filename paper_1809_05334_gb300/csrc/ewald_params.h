@@ -25,8 +25,9 @@ struct EwaldTables {
     // spectral G_g(z) per distinct gamma on [0, z_max], piecewise cubic Hermite
     float xs_max, xs_inv_h, z_max, z_inv_h, e_mb2, Ef;
     float kx, ky, step_x, step_y;   // k_t,pq = (kx + p step_x, ky + q step_y)
-    int P, Q, n_tab;
-    int rect_tab[MAX_MODE];  // table of rectangle entry (p+P)(2Q+1)+(q+Q) (| TAB_REAL if its G
+    int p0, np, q0, nq, n_tab;       // the smallest rectangle p0 <= p < p0 + np, q0 <= q < q0 + nq
+                                     // holding every mode inside the cut
+    int rect_tab[MAX_MODE];  // table of rectangle entry (p-p0) nq + (q-q0) (| TAB_REAL if its G
                              // is real), -1 outside the cut
     double tab_gamma[MAX_MODE][2];   // gamma of each table
     double tab_ig[MAX_MODE][2];      // 1/(4ab gamma) of each table
@@ -45,16 +46,36 @@ struct EwaldF32 {
     float img[MAX_IMG][4];   // = EwaldTables::img32
     int rect_tab[MAX_MODE];
     int near_img[9];
-    int n_img, P, Q;
+    int n_img, p0, np, q0, nq;
     float xs_max, xs_inv_h, z_inv_h, e_mb2, Ef, kx, ky, step_x, step_y;
 };
+// The smallest rectangle of Floquet orders (p, q) holding every mode with
+// |k_t,pq| <= kmax, k_t,pq = (kx + 2 pi p / a, ky + 2 pi q / b); np = nq = 0
+// when there is none.  False when the rectangle has more than MAX_MODE entries.
+inline bool mode_rect(double kx, double ky, double a, double b, double kmax, int &p0, int &np, int &q0, int &nq) {
+    const double tp = 6.283185307179586;
+    const int P = (int)((kmax + (kx < 0 ? -kx : kx)) * a / tp) + 2;
+    const int Q = (int)((kmax + (ky < 0 ? -ky : ky)) * b / tp) + 2;
+    int plo = P + 1, phi = -P - 1, qlo = Q + 1, qhi = -Q - 1;
+    for (int p = -P; p <= P; ++p)
+        for (int q = -Q; q <= Q; ++q) {
+            const double ktx = kx + tp * p / a, kty = ky + tp * q / b;
+            if (ktx * ktx + kty * kty > kmax * kmax * (1.0 + 1e-12)) continue;   // loose: callers test each mode
+            plo = p < plo ? p : plo; phi = p > phi ? p : phi;
+            qlo = q < qlo ? q : qlo; qhi = q > qhi ? q : qhi;
+        }
+    if (phi < plo) { p0 = q0 = np = nq = 0; return true; }
+    p0 = plo; np = phi - plo + 1; q0 = qlo; nq = qhi - qlo + 1;
+    return np * nq <= MAX_MODE;
+}
+
 inline EwaldF32 make_ewald_f32(const EwaldTables &t) {
     EwaldF32 f{};
     for (int i = 0; i < MAX_IMG; ++i)
         for (int k = 0; k < 4; ++k) f.img[i][k] = t.img32[i][k];
     for (int i = 0; i < MAX_MODE; ++i) f.rect_tab[i] = t.rect_tab[i];
     for (int k = 0; k < 9; ++k) f.near_img[k] = t.near_img[k];
-    f.n_img = t.n_img; f.P = t.P; f.Q = t.Q;
+    f.n_img = t.n_img; f.p0 = t.p0; f.np = t.np; f.q0 = t.q0; f.nq = t.nq;
     f.xs_max = t.xs_max; f.xs_inv_h = t.xs_inv_h; f.z_inv_h = t.z_inv_h; f.e_mb2 = t.e_mb2; f.Ef = t.Ef;
     f.kx = t.kx; f.ky = t.ky; f.step_x = t.step_x; f.step_y = t.step_y;
     return f;

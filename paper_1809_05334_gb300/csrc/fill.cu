@@ -166,7 +166,7 @@ template <> struct Green<double> {
     }
     __device__ static void eval2(double dx, double dy, double dz, unsigned sub, const float *, const float2 *,
                                  const EwaldTables *ew, const EwaldF32 &, cx<double> &gp, cx<double> &gm,
-                                 const float4 * = nullptr) {
+                                 const float4 * = nullptr, unsigned long long = ~0ull) {
         gp = green_p<double>(dx, dy, dz, sub, ew);
         gm = green_p<double>(-dx, -dy, -dz, mirror_mask(sub), ew);
     }
@@ -181,8 +181,8 @@ template <> struct Green<float> {
     }
     __device__ static void eval2(float dx, float dy, float dz, unsigned sub, const float *stab, const float2 *ztab,
                                  const EwaldTables *, const EwaldF32 &ef, cx<float> &gp, cx<float> &gm,
-                                 const float4 *rtab = nullptr) {
-        green_tab_impl<true>(dx, dy, dz, sub, stab, ztab, ef, gp, gm, rtab);
+                                 const float4 *rtab = nullptr, unsigned long long imask = ~0ull) {
+        green_tab_impl<true>(dx, dy, dz, sub, stab, ztab, ef, gp, gm, rtab, imask);
     }
 };
 
@@ -268,6 +268,20 @@ __global__ void __launch_bounds__(128, 6) k_far_tt(DevMesh m, const __grid_const
     mo.zero();
     mr.zero();
     const T wgt = ft[27] * fs[27];
+    // images that can reach the cut from some point pair of {t, s}, decided once
+    // for the 16 point pairs (FP32 tables only): every point pair lies within
+    // rt + rs of the centroid offset
+    unsigned long long imask = ~0ull;
+    if (sizeof(T) == 4) {
+        float rt = 0.f, rs = 0.f;
+        for (int a = 0; a < 4; ++a) {
+            const float ux = float(ft[3 * a] - ft[12]), uy = float(ft[3 * a + 1] - ft[13]), uz = float(ft[3 * a + 2] - ft[14]);
+            const float vx = float(fs[3 * a] - fs[12]), vy = float(fs[3 * a + 1] - fs[13]), vz = float(fs[3 * a + 2] - fs[14]);
+            rt = fmaxf(rt, sqrtf(ux * ux + uy * uy + uz * uz));
+            rs = fmaxf(rs, sqrtf(vx * vx + vy * vy + vz * vz));
+        }
+        imask = image_mask(q.ef, float(ft[12] - fs[12]), float(ft[13] - fs[13]), float(ft[14] - fs[14]), rt + rs);
+    }
     for (int a = 0; a < 4; ++a) {
         const T xa[3] = {ft[3 * a], ft[3 * a + 1], ft[3 * a + 2]};
         const T ra[3] = {xa[0] - ft[12], xa[1] - ft[13], xa[2] - ft[14]};
@@ -276,7 +290,7 @@ __global__ void __launch_bounds__(128, 6) k_far_tt(DevMesh m, const __grid_const
             const T rb[3] = {yb[0] - fs[12], yb[1] - fs[13], yb[2] - fs[14]};
             cx<T> g, gr;
             Green<T>::eval2(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab, q.ew, q.ef, g, gr,
-                            q.rtab);
+                            q.rtab, imask);
             g = wgt * g;
             gr = wgt * gr;
             const T rr = ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2];
@@ -912,16 +926,12 @@ int noalloc_tables(double lambda, double theta, double phi, double a, double b, 
     E.ky = (float)ky;
     E.step_x = (float)(2 * M_PI / a);
     E.step_y = (float)(2 * M_PI / b);
-    const int P = (int)std::ceil((2.0 * E.E * xc32 + std::fabs(kx)) * a / (2 * M_PI)) + 1;
-    const int Q = (int)std::ceil((2.0 * E.E * xc32 + std::fabs(ky)) * b / (2 * M_PI)) + 1;
-    if ((2 * P + 1) * (2 * Q + 1) > MAX_MODE) return VIE_EINVAL;
-    E.P = P;
-    E.Q = Q;
+    if (!mode_rect(kx, ky, a, b, 2.0 * E.E * xc32 + k0, E.p0, E.np, E.q0, E.nq)) return VIE_EINVAL;
     int nt = 0;
     double g2s[MAX_MODE];
-    for (int p = -P; p <= P; ++p)
-        for (int q = -Q; q <= Q; ++q) {
-            const int idx = (p + P) * (2 * Q + 1) + (q + Q);
+    for (int p = E.p0; p < E.p0 + E.np; ++p)
+        for (int q = E.q0; q < E.q0 + E.nq; ++q) {
+            const int idx = (p - E.p0) * E.nq + (q - E.q0);
             const double ktx = kx + 2 * M_PI * p / a, kty = ky + 2 * M_PI * q / b;
             const double kt2 = ktx * ktx + kty * kty;
             if (std::sqrt(kt2) > 2.0 * E.E * xc32 + k0) { E.rect_tab[idx] = -1; continue; }
