@@ -272,6 +272,7 @@ int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
         E.step_x = (float)(2 * M_PI / a); E.step_y = (float)(2 * M_PI / b);
         if (!vie::mode_rect(H.kx, H.ky, a, b, 2.0 * E.E * xc32 + k0, E.p0, E.np, E.q0, E.nq))
             return fail(ctx, VIE_EINVAL, "too many Floquet modes for the table");
+        E.sym = (H.kx == 0.0 && H.ky == 0.0 && 2 * E.p0 + E.np == 1 && 2 * E.q0 + E.nq == 1) ? 1 : 0;
         int nt = 0;
         std::vector<double> g2s;
         for (int p = E.p0; p < E.p0 + E.np; ++p)

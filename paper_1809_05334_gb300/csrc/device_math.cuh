@@ -189,7 +189,10 @@ __device__ cx<T> green_p(T dx, T dy, T dz, unsigned sub, const EwaldTables *__re
 // list and the near-image masks are symmetric under (m,n) -> (-m,-n)).
 // rtab (may be null): the real parts of the tables as one float4 per
 // interval; used for the tables flagged TAB_REAL (their imaginary parts are 0)
-template <bool PAIR>
+// SYM (normal incidence, k_par = 0, mode rectangle symmetric about (0, 0)):
+// G_pq = G_-p-q, so the orders pair up into 2 G_pq cos(k_t,pq . rho) over the
+// half plane p > 0 or (p = 0, q > 0), plus G_00; g_p is even in d, so gm = gp.
+template <bool PAIR, bool SYM = false>
 __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, unsigned sub, const float *stab,
                                                const float2 *__restrict__ ztab, const EwaldF32 &ew,
                                                cx<float> &gp, cx<float> &gm,
@@ -200,46 +203,102 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
     float zu = fminf(z * ew.z_inv_h, float(NZTAB));
     int iz = min((int)zu, NZTAB - 1);
     const float u = zu - iz;
+    // G of the mode table `code` at |z| (real tables: one 16-byte load)
+    auto table = [&](int code, float &gr, float &gi) {
+        const int tb = code & TAB_INDEX;
+        if (rtab && (code & TAB_REAL)) {
+            const float4 c = __ldg(rtab + (size_t)tb * NZTAB + iz);
+            gr = fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+            gi = 0.f;
+            return true;
+        }
+        const float2 *cf = ztab + ((size_t)tb * NZTAB + iz) * 4;
+        const float2 c0 = __ldg(cf), c1 = __ldg(cf + 1), c2 = __ldg(cf + 2), c3 = __ldg(cf + 3);
+        gr = fmaf(u, fmaf(u, fmaf(u, c3.x, c2.x), c1.x), c0.x);
+        gi = fmaf(u, fmaf(u, fmaf(u, c3.y, c2.y), c1.y), c0.y);
+        return false;
+    };
     const int np = ew.np, nq = ew.nq;
     float s, c;
-    sincospif(-(ew.kx + ew.p0 * ew.step_x) * dx * 0.31830988618f, &s, &c);
-    cx<float> ex = {c, s};
-    sincospif(-ew.step_x * dx * 0.31830988618f, &s, &c);
-    const cx<float> sx = {c, s};
-    sincospif(-(ew.ky + ew.q0 * ew.step_y) * dy * 0.31830988618f, &s, &c);
-    cx<float> ey0 = {c, s};
-    sincospif(-ew.step_y * dy * 0.31830988618f, &s, &c);
-    const cx<float> sy = {c, s};
-    for (int p = 0; p < np; ++p) {
-        cx<float> inner = {0.f, 0.f}, inner2 = {0.f, 0.f};
-        cx<float> ey = ey0;
-        for (int q = 0; q < nq; ++q) {
-            const int code = ew.rect_tab[p * nq + q];
-            if (code >= 0) {
-                const int tb = code & TAB_INDEX;
-                if (rtab && (code & TAB_REAL)) {   // real G: one 16-byte load, real products
-                    const float4 c = __ldg(rtab + (size_t)tb * NZTAB + iz);
-                    const float g = fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
-                    inner.re = fmaf(ey.re, g, inner.re);
-                    inner.im = fmaf(ey.im, g, inner.im);
-                    if (PAIR) {
-                        inner2.re = fmaf(ey.re, g, inner2.re);
-                        inner2.im = fmaf(-ey.im, g, inner2.im);
+    if constexpr (SYM) {
+        if (np > 0) {
+            const int P = (np - 1) / 2, Q = (nq - 1) / 2;
+            sincospif(-ew.step_x * dx * 0.31830988618f, &s, &c);
+            const cx<float> sx = {c, s};
+            sincospif(-ew.step_y * dy * 0.31830988618f, &s, &c);
+            const cx<float> sy = {c, s};
+            sincospif(Q * ew.step_y * dy * 0.31830988618f, &s, &c);
+            const cx<float> ey0 = {c, s};   // exp(-j k_y,-Q dy)
+            cx<float> h = {0.f, 0.f};       // sum over the half plane of G cos(k_t . rho)
+            {   // row p = 0: G_00 once, q = 1..Q paired
+                const int row = P * nq + Q;
+                float gr, gi;
+                const int c00 = ew.rect_tab[row];
+                if (c00 >= 0) { table(c00, gr, gi); acc.re = gr; acc.im = gi; }
+                cx<float> ey = sy;
+                for (int q = 1; q <= Q; ++q) {
+                    const int code = ew.rect_tab[row + q];
+                    if (code >= 0) {
+                        if (table(code, gr, gi)) h.re = fmaf(gr, ey.re, h.re);
+                        else { h.re = fmaf(gr, ey.re, h.re); h.im = fmaf(gi, ey.re, h.im); }
                     }
-                } else {
-                    const float2 *cf = ztab + ((size_t)tb * NZTAB + iz) * 4;
-                    const float2 c0 = __ldg(cf), c1 = __ldg(cf + 1), c2 = __ldg(cf + 2), c3 = __ldg(cf + 3);
-                    cx<float> g = {fmaf(u, fmaf(u, fmaf(u, c3.x, c2.x), c1.x), c0.x),
-                                   fmaf(u, fmaf(u, fmaf(u, c3.y, c2.y), c1.y), c0.y)};
-                    inner = inner + ey * g;
-                    if (PAIR) inner2 = inner2 + cconj(ey) * g;
+                    ey = ey * sy;
                 }
             }
-            ey = ey * sy;
+            cx<float> ex = sx;
+            for (int p = 1; p <= P; ++p) {   // rows p = 1..P, all q
+                const int row = (P + p) * nq;
+                cx<float> ey = ey0;
+                for (int q = 0; q < nq; ++q) {
+                    const int code = ew.rect_tab[row + q];
+                    if (code >= 0) {
+                        const float cs = fmaf(ex.re, ey.re, -ex.im * ey.im);   // cos(k_t . rho)
+                        float gr, gi;
+                        if (table(code, gr, gi)) h.re = fmaf(gr, cs, h.re);
+                        else { h.re = fmaf(gr, cs, h.re); h.im = fmaf(gi, cs, h.im); }
+                    }
+                    ey = ey * sy;
+                }
+                ex = ex * sx;
+            }
+            acc.re = fmaf(2.f, h.re, acc.re);
+            acc.im = fmaf(2.f, h.im, acc.im);
         }
-        acc = acc + ex * inner;
-        if (PAIR) acc2 = acc2 + cconj(ex) * inner2;
-        ex = ex * sx;
+    } else {
+        sincospif(-(ew.kx + ew.p0 * ew.step_x) * dx * 0.31830988618f, &s, &c);
+        cx<float> ex = {c, s};
+        sincospif(-ew.step_x * dx * 0.31830988618f, &s, &c);
+        const cx<float> sx = {c, s};
+        sincospif(-(ew.ky + ew.q0 * ew.step_y) * dy * 0.31830988618f, &s, &c);
+        const cx<float> ey0 = {c, s};
+        sincospif(-ew.step_y * dy * 0.31830988618f, &s, &c);
+        const cx<float> sy = {c, s};
+        for (int p = 0; p < np; ++p) {
+            cx<float> inner = {0.f, 0.f}, inner2 = {0.f, 0.f};
+            cx<float> ey = ey0;
+            for (int q = 0; q < nq; ++q) {
+                const int code = ew.rect_tab[p * nq + q];
+                if (code >= 0) {
+                    float gr, gi;
+                    if (table(code, gr, gi)) {   // real G: real products
+                        inner.re = fmaf(ey.re, gr, inner.re);
+                        inner.im = fmaf(ey.im, gr, inner.im);
+                        if (PAIR) {
+                            inner2.re = fmaf(ey.re, gr, inner2.re);
+                            inner2.im = fmaf(-ey.im, gr, inner2.im);
+                        }
+                    } else {
+                        const cx<float> g = {gr, gi};
+                        inner = inner + ey * g;
+                        if (PAIR) inner2 = inner2 + cconj(ey) * g;
+                    }
+                }
+                ey = ey * sy;
+            }
+            acc = acc + ex * inner;
+            if (PAIR) acc2 = acc2 + cconj(ex) * inner2;
+            ex = ex * sx;
+        }
     }
     const float E = ew.Ef;
     const float xmax = ew.xs_max, ih = ew.xs_inv_h;
@@ -274,7 +333,7 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
         }
         acc.re = fmaf(val, im[2], acc.re);
         acc.im = fmaf(val, im[3], acc.im);
-        if (PAIR) {
+        if (PAIR && !SYM) {
             acc2.re = fmaf(val, im[2], acc2.re);
             acc2.im = fmaf(-val, im[3], acc2.im);
         }
@@ -285,7 +344,7 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
     for (unsigned long long mk = imask; mk; mk &= mk - 1ull) image(__ffsll((long long)mk) - 1);
     for (int i = 64; i < ew.n_img; ++i) image(i);
     gp = acc;
-    gm = acc2;
+    gm = SYM ? acc : acc2;
 }
 
 // Images (of the first 64) that can lie inside the spatial cut for some

@@ -27,6 +27,7 @@ struct EwaldTables {
     float kx, ky, step_x, step_y;   // k_t,pq = (kx + p step_x, ky + q step_y)
     int p0, np, q0, nq, n_tab;       // the smallest rectangle p0 <= p < p0 + np, q0 <= q < q0 + nq
                                      // holding every mode inside the cut
+    int sym;                         // 1: k_par = 0 and the rectangle is symmetric about (0, 0)
     int rect_tab[MAX_MODE];  // table of rectangle entry (p-p0) nq + (q-q0) (| TAB_REAL if its G
                              // is real), -1 outside the cut
     double tab_gamma[MAX_MODE][2];   // gamma of each table
@@ -46,7 +47,7 @@ struct EwaldF32 {
     float img[MAX_IMG][4];   // = EwaldTables::img32
     int rect_tab[MAX_MODE];
     int near_img[9];
-    int n_img, p0, np, q0, nq;
+    int n_img, p0, np, q0, nq, sym;
     float xs_max, xs_inv_h, z_inv_h, e_mb2, Ef, kx, ky, step_x, step_y;
 };
 // The smallest rectangle of Floquet orders (p, q) holding every mode with
@@ -75,7 +76,7 @@ inline EwaldF32 make_ewald_f32(const EwaldTables &t) {
         for (int k = 0; k < 4; ++k) f.img[i][k] = t.img32[i][k];
     for (int i = 0; i < MAX_MODE; ++i) f.rect_tab[i] = t.rect_tab[i];
     for (int k = 0; k < 9; ++k) f.near_img[k] = t.near_img[k];
-    f.n_img = t.n_img; f.p0 = t.p0; f.np = t.np; f.q0 = t.q0; f.nq = t.nq;
+    f.n_img = t.n_img; f.p0 = t.p0; f.np = t.np; f.q0 = t.q0; f.nq = t.nq; f.sym = t.sym;
     f.xs_max = t.xs_max; f.xs_inv_h = t.xs_inv_h; f.z_inv_h = t.z_inv_h; f.e_mb2 = t.e_mb2; f.Ef = t.Ef;
     f.kx = t.kx; f.ky = t.ky; f.step_x = t.step_x; f.step_y = t.step_y;
     return f;

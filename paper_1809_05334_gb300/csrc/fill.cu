@@ -160,10 +160,13 @@ __device__ __forceinline__ unsigned mirror_mask(unsigned sub) {
 template <typename T> struct Green;
 // eval2 returns g_p(d) and g_p(-d) (the same near-image mask applies to both)
 template <> struct Green<double> {
+    template <bool SYM = false>
     __device__ static cx<double> eval(double dx, double dy, double dz, unsigned sub, const float *, const float2 *,
-                                      const EwaldTables *ew, const EwaldF32 &, const float4 * = nullptr) {
+                                      const EwaldTables *ew, const EwaldF32 &, const float4 * = nullptr,
+                                      unsigned long long = ~0ull) {
         return green_p<double>(dx, dy, dz, sub, ew);
     }
+    template <bool SYM = false>
     __device__ static void eval2(double dx, double dy, double dz, unsigned sub, const float *, const float2 *,
                                  const EwaldTables *ew, const EwaldF32 &, cx<double> &gp, cx<double> &gm,
                                  const float4 * = nullptr, unsigned long long = ~0ull) {
@@ -172,17 +175,19 @@ template <> struct Green<double> {
     }
 };
 template <> struct Green<float> {
+    template <bool SYM = false>
     __device__ static cx<float> eval(float dx, float dy, float dz, unsigned sub, const float *stab,
                                      const float2 *ztab, const EwaldTables *, const EwaldF32 &ef,
-                                     const float4 *rtab = nullptr) {
+                                     const float4 *rtab = nullptr, unsigned long long imask = ~0ull) {
         cx<float> g, unused;
-        green_tab_impl<false>(dx, dy, dz, sub, stab, ztab, ef, g, unused, rtab);
+        green_tab_impl<false, SYM>(dx, dy, dz, sub, stab, ztab, ef, g, unused, rtab, imask);
         return g;
     }
+    template <bool SYM = false>
     __device__ static void eval2(float dx, float dy, float dz, unsigned sub, const float *stab, const float2 *ztab,
                                  const EwaldTables *, const EwaldF32 &ef, cx<float> &gp, cx<float> &gm,
                                  const float4 *rtab = nullptr, unsigned long long imask = ~0ull) {
-        green_tab_impl<true>(dx, dy, dz, sub, stab, ztab, ef, gp, gm, rtab, imask);
+        green_tab_impl<true, SYM>(dx, dy, dz, sub, stab, ztab, ef, gp, gm, rtab, imask);
     }
 };
 
@@ -252,7 +257,8 @@ __device__ void scatter_tt(const DevMesh &m, const DevReq &q, T *Z, size_t N, in
 // Each unordered pair {t, s} (s >= t) is evaluated once: one pass over the 16
 // point pairs gives g_p(x_a - y_b) for the block (t, s) and g_p(y_b - x_a) for
 // the block (s, t) (the reversed pair's moments swap the roles of the offsets).
-template <typename T>
+// SYM: normal incidence (the tabulated path's symmetric mode sum, gm = gp).
+template <typename T, bool SYM>
 __global__ void __launch_bounds__(128, 6) k_far_tt(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N) {
     extern __shared__ float smem_tab[];
     const int t = blockIdx.y;
@@ -289,8 +295,8 @@ __global__ void __launch_bounds__(128, 6) k_far_tt(DevMesh m, const __grid_const
             const T yb[3] = {fs[3 * b], fs[3 * b + 1], fs[3 * b + 2]};
             const T rb[3] = {yb[0] - fs[12], yb[1] - fs[13], yb[2] - fs[14]};
             cx<T> g, gr;
-            Green<T>::eval2(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab, q.ew, q.ef, g, gr,
-                            q.rtab, imask);
+            Green<T>::template eval2<SYM>(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab, q.ew,
+                                          q.ef, g, gr, q.rtab, imask);
             g = wgt * g;
             gr = wgt * gr;
             const T rr = ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2];
@@ -551,7 +557,8 @@ __device__ __forceinline__ const T *far_el(const DevMesh &m, int e) {
     return TET ? m.far<T>(e) : m.ffar<T>(e);
 }
 
-template <typename T, int PK>
+// SYM: normal incidence (the tabulated path's symmetric mode sum).
+template <typename T, int PK, bool SYM>
 __global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N, int nx, int ny,
                                                     const uint16_t *mk) {
     extern __shared__ float smem_tab[];
@@ -566,11 +573,32 @@ __global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, const __grid_cons
     const T *fy = far_el<T, YT>(m, y);
     const int qx = XT ? 4 : 3, qy = YT ? 4 : 3;
     const T wgt = fx[XT ? 27 : 9] * fy[YT ? 27 : 9];
+    // images that can reach the cut from some point pair, decided once per
+    // element pair (FP32 tables only): centres and radii of the two point sets
+    unsigned long long imask = ~0ull;
+    if (sizeof(T) == 4) {
+        float c1[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < qx; ++a)
+            for (int d = 0; d < 3; ++d) c1[d] += float(fx[3 * a + d]) / qx;
+        for (int b = 0; b < qy; ++b)
+            for (int d = 0; d < 3; ++d) c2[d] += float(fy[3 * b + d]) / qy;
+        float r1 = 0.f, r2 = 0.f;
+        for (int a = 0; a < qx; ++a) {
+            const float ux = float(fx[3 * a]) - c1[0], uy = float(fx[3 * a + 1]) - c1[1], uz = float(fx[3 * a + 2]) - c1[2];
+            r1 = fmaxf(r1, sqrtf(ux * ux + uy * uy + uz * uz));
+        }
+        for (int b = 0; b < qy; ++b) {
+            const float ux = float(fy[3 * b]) - c2[0], uy = float(fy[3 * b + 1]) - c2[1], uz = float(fy[3 * b + 2]) - c2[2];
+            r2 = fmaxf(r2, sqrtf(ux * ux + uy * uy + uz * uz));
+        }
+        imask = image_mask(q.ef, c1[0] - c2[0], c1[1] - c2[1], c1[2] - c2[2], r1 + r2);
+    }
     cx<T> S = {0, 0};
     for (int a = 0; a < qx; ++a)
         for (int b = 0; b < qy; ++b) {
-            cx<T> g = Green<T>::eval(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1], fx[3 * a + 2] - fy[3 * b + 2],
-                                     sub, stab, q.ztab, q.ew, q.ef, q.rtab);
+            cx<T> g = Green<T>::template eval<SYM>(fx[3 * a] - fy[3 * b], fx[3 * a + 1] - fy[3 * b + 1],
+                                                   fx[3 * a + 2] - fy[3 * b + 2], sub, stab, q.ztab, q.ew, q.ef,
+                                                   q.rtab, imask);
             S = S + g;
         }
     S = wgt * S;
@@ -745,12 +773,12 @@ __global__ void k_erfcx(const double *u, double *out, int n) {
     out[2 * i + 1] = double(r.im);
 }
 
-template <typename T>
+template <typename T, bool SYM = false>
 __global__ void k_green(const double *d, double *out, int n, const float *stab, const float2 *ztab,
                         const EwaldTables *ew, const __grid_constant__ EwaldF32 ef) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    cx<T> r = Green<T>::eval(T(d[3 * i]), T(d[3 * i + 1]), T(d[3 * i + 2]), 0u, stab, ztab, ew, ef);
+    cx<T> r = Green<T>::template eval<SYM>(T(d[3 * i]), T(d[3 * i + 1]), T(d[3 * i + 2]), 0u, stab, ztab, ew, ef);
     out[2 * i] = double(r.re);
     out[2 * i + 1] = double(r.im);
 }
@@ -758,6 +786,18 @@ __global__ void k_green(const double *d, double *out, int n, const float *stab, 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+template <typename T, int PK>
+void far_scalar(bool sym, dim3 grid, size_t sm, cudaStream_t st, const DevMesh &m, const DevReq &q, T *Z, size_t N,
+                int nx, int ny, const uint16_t *mk) {
+    if constexpr (sizeof(T) == 4) {
+        if (sym) k_far_scalar<T, PK, true><<<grid, 128, sm, st>>>(m, q, Z, N, nx, ny, mk);
+        else k_far_scalar<T, PK, false><<<grid, 128, sm, st>>>(m, q, Z, N, nx, ny, mk);
+    } else {
+        k_far_scalar<T, PK, false><<<grid, 128, sm, st>>>(m, q, Z, N, nx, ny, mk);
+    }
+    ++g_launches;
+}
+
 template <typename T>
 cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, double *b, cudaStream_t st,
                         cudaEvent_t far0, cudaEvent_t far1) {
@@ -770,7 +810,14 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
     if (b) { k_rhs<<<(m.nt + 127) / 128, blk, 0, st>>>(m, q, b); ++g_launches; }
     const size_t sm = stab_bytes<T>();
     if (far0) cudaEventRecord(far0, st);
-    k_far_tt<T><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N); ++g_launches;
+    const bool sym = sizeof(T) == 4 && q.ef.sym;   // normal incidence: the symmetric tabulated path
+    if constexpr (sizeof(T) == 4) {
+        if (sym) k_far_tt<T, true><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N);
+        else k_far_tt<T, false><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N);
+    } else {
+        k_far_tt<T, false><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N);
+    }
+    ++g_launches;
     if (far1) cudaEventRecord(far1, st);
     auto grid1 = [](int n) { return (unsigned)((n + 127) / 128); };
     if (m.npr[0]) { k_pr_tt<T><<<grid1(m.npr[0]), blk, 0, st>>>(m, q, Z, N, m.pr[0], m.npr[0]); ++g_launches; }
@@ -779,15 +826,15 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
                                                             m.nto[0]); ++g_launches;
     }
     if (m.nf) {
-        k_far_scalar<T, PK_TF><<<dim3((m.nf + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N, m.nt, m.nf, m.mk_tf); ++g_launches;
+        far_scalar<T, PK_TF>(sym, dim3((m.nf + 127) / 128, m.nt), sm, st, m, q, Z, N, m.nt, m.nf, m.mk_tf);
         if (m.npr[1]) { k_pr_scalar<T, PK_TF><<<grid1(m.npr[1]), blk, 0, st>>>(m, q, Z, N, m.pr[1], m.npr[1]); ++g_launches; }
         if (m.nto[1]) { k_touch_apply<T, PK_TF><<<grid1(m.nto[1]), blk, 0, st>>>(m, q, Z, N, m.to[1], m.touch_sc[1], m.nto[1]); ++g_launches; }
     }
     if (m.nh) {
-        k_far_scalar<T, PK_FT><<<dim3((m.nt + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nt, m.mk_ft); ++g_launches;
+        far_scalar<T, PK_FT>(sym, dim3((m.nt + 127) / 128, m.nh), sm, st, m, q, Z, N, m.nh, m.nt, m.mk_ft);
         if (m.npr[2]) { k_pr_scalar<T, PK_FT><<<grid1(m.npr[2]), blk, 0, st>>>(m, q, Z, N, m.pr[2], m.npr[2]); ++g_launches; }
         if (m.nto[2]) { k_touch_apply<T, PK_FT><<<grid1(m.nto[2]), blk, 0, st>>>(m, q, Z, N, m.to[2], m.touch_sc[2], m.nto[2]); ++g_launches; }
-        k_far_scalar<T, PK_FF><<<dim3((m.nf + 127) / 128, m.nh), blk, sm, st>>>(m, q, Z, N, m.nh, m.nf, m.mk_ff); ++g_launches;
+        far_scalar<T, PK_FF>(sym, dim3((m.nf + 127) / 128, m.nh), sm, st, m, q, Z, N, m.nh, m.nf, m.mk_ff);
         if (m.npr[3]) { k_pr_scalar<T, PK_FF><<<grid1(m.npr[3]), blk, 0, st>>>(m, q, Z, N, m.pr[3], m.npr[3]); ++g_launches; }
         if (m.nto[3]) { k_touch_apply<T, PK_FF><<<grid1(m.nto[3]), blk, 0, st>>>(m, q, Z, N, m.to[3], m.touch_sc[3], m.nto[3]); ++g_launches; }
     }
@@ -821,6 +868,7 @@ cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStr
 cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const float *stab, const float2 *ztab,
                          const EwaldTables *ew, const EwaldF32 &ef, cudaStream_t st) {
     if (fp64) { k_green<double><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
+    else if (ef.sym) { k_green<float, true><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
     else { k_green<float><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
     return cudaGetLastError();
 }
@@ -927,6 +975,7 @@ int noalloc_tables(double lambda, double theta, double phi, double a, double b, 
     E.step_x = (float)(2 * M_PI / a);
     E.step_y = (float)(2 * M_PI / b);
     if (!mode_rect(kx, ky, a, b, 2.0 * E.E * xc32 + k0, E.p0, E.np, E.q0, E.nq)) return VIE_EINVAL;
+    E.sym = (kx == 0.0 && ky == 0.0 && 2 * E.p0 + E.np == 1 && 2 * E.q0 + E.nq == 1) ? 1 : 0;
     int nt = 0;
     double g2s[MAX_MODE];
     for (int p = E.p0; p < E.p0 + E.np; ++p)
