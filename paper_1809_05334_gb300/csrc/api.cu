@@ -213,12 +213,12 @@ int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
     vie::EwaldTables &E = H.ew;
     std::memset(&E, 0, sizeof(E));
     const double a = T.a, b = T.b, k0 = H.k0;
-    E.E = std::max(std::sqrt(M_PI / (a * b)), k0 / 6.0);
+    const bool fp64 = ctx->opt.precision == VIE_FP64;
+    E.E = vie::ewald_split(a, b, k0, !fp64 && H.kx == 0.0 && H.ky == 0.0);
     E.bb = k0 / (2.0 * E.E);
     E.a = a; E.b = b;
     E.xcut64 = FP64_XCUT;
     E.xcut32 = FP32_XCUT;
-    const bool fp64 = ctx->opt.precision == VIE_FP64;
     const double xc = fp64 ? FP64_XCUT : FP32_XCUT;
     const int mm = (int)std::ceil(xc / (E.E * a)) + 2, nn = (int)std::ceil(xc / (E.E * b)) + 2;
     int ni = 0;

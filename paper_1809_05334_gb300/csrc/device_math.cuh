@@ -303,6 +303,7 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
     const float E = ew.Ef;
     const float xmax = ew.xs_max, ih = ew.xs_inv_h;
     const float r2max = (xmax / E) * (xmax / E) * 1.0001f;   // loose: the exact test follows
+    float sv = 0.f;   // SYM: the sum of the image values before their common factor
     auto image = [&](int i) {
         const float *im = ew.img[i];
         const float x = dx + im[0], y = dy + im[1];
@@ -331,9 +332,13 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
         } else {
             val = fmaf(v, fmaf(v, fmaf(v, cs.w, cs.z), cs.y), cs.x) * rinv;
         }
+        if (SYM) {   // k_par = 0: every image carries the same real phase factor
+            sv += val;
+            return;
+        }
         acc.re = fmaf(val, im[2], acc.re);
         acc.im = fmaf(val, im[3], acc.im);
-        if (PAIR && !SYM) {
+        if (PAIR) {
             acc2.re = fmaf(val, im[2], acc2.re);
             acc2.im = fmaf(-val, im[3], acc2.im);
         }
@@ -343,6 +348,7 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
     if (ew.n_img < 64) imask &= (1ull << ew.n_img) - 1ull;
     for (unsigned long long mk = imask; mk; mk &= mk - 1ull) image(__ffsll((long long)mk) - 1);
     for (int i = 64; i < ew.n_img; ++i) image(i);
+    if (SYM) acc.re = fmaf(ew.img[0][2], sv, acc.re);
     gp = acc;
     gm = SYM ? acc : acc2;
 }

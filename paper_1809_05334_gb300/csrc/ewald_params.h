@@ -1,5 +1,7 @@
 // Ewald parameters of one incidence, shared by host (set-up) and device code.
 #pragma once
+#include <algorithm>
+#include <cmath>
 
 namespace vie {
 
@@ -50,6 +52,16 @@ struct EwaldF32 {
     int n_img, p0, np, q0, nq, sym;
     float xs_max, xs_inv_h, z_inv_h, e_mb2, Ef, kx, ky, step_x, step_y;
 };
+// Ewald splitting parameter: sqrt(pi / ab) balances the spatial and spectral
+// series, bounded below by k0/6 (b = k0 / 2E <= 3 keeps exp(b^2) moderate).  The
+// tabulated FP32 path at normal incidence pairs the Floquet orders (half the
+// spectral terms, each cheaper), which moves the balance to a larger E: there
+// E is 1.5 times as large (fewer lattice images inside the same erfc cut).
+inline double ewald_split(double a, double b, double k0, bool fp32_normal) {
+    const double e = std::max(std::sqrt(3.141592653589793 / (a * b)), k0 / 6.0);
+    return fp32_normal ? 1.5 * e : e;
+}
+
 // The smallest rectangle of Floquet orders (p, q) holding every mode with
 // |k_t,pq| <= kmax, k_t,pq = (kx + 2 pi p / a, ky + 2 pi q / b); np = nq = 0
 // when there is none.  False when the rectangle has more than MAX_MODE entries.

@@ -912,7 +912,7 @@ int noalloc_tables(double lambda, double theta, double phi, double a, double b, 
     const double k0 = 2.0 * M_PI / lambda;
     const double kx = k0 * std::sin(theta) * std::cos(phi), ky = k0 * std::sin(theta) * std::sin(phi);
     std::memset(&E, 0, sizeof(E));
-    E.E = std::max(std::sqrt(M_PI / (a * b)), k0 / 6.0);
+    E.E = ewald_split(a, b, k0, !fp64 && kx == 0.0 && ky == 0.0);
     E.bb = k0 / (2.0 * E.E);
     E.a = a;
     E.b = b;
