@@ -205,7 +205,9 @@ def run_ours(args):
                       "post": last["t_post_ms"]},
         "kernels_ms": {"far_tt": last["k_far_tt_ms"], "fill": last["k_fill_ms"], "factor": last["k_factor_ms"],
                        "tc_update_total": last["k_tc_ms"], "tc_update_n": last["k_tc_n"],
-                       "matvec_total": last["k_matvec_ms"], "matvec_n": last["k_matvec_n"]},
+                       "matvec_total": last["k_matvec_ms"], "matvec_n": last["k_matvec_n"],
+                       "precond_total": last["k_precond_ms"], "precond_n": last["k_precond_n"],
+                       "ortho_total": last["k_ortho_ms"]},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "note": "per solve, one solve in flight"},
         "iterations": last["iterations"], "rel_residual": [float(v) for v in last["rel_residual"]],

@@ -122,6 +122,10 @@ typedef struct {
     double  k_precond_ms, k_precond_bytes;
     int32_t k_precond_n, reserved3;
     double  k_tc_flops;                  /* algorithmic flops of the k_tc_n launches */
+    /* GMRES orthogonalisation (options.timing = 1): total device time of the
+       classical Gram-Schmidt passes (both projections, both updates and the
+       norm of the new vector) over all iterations */
+    double  k_ortho_ms;
 } vie_result;
 
 /* Fill *opt with defaults (FP32 with refinement, preconditioner on, tol 1e-6). */

@@ -407,6 +407,7 @@ struct Timing {
     cudaEvent_t fill0 = nullptr, fill1 = nullptr, far0 = nullptr, far1 = nullptr, fac0 = nullptr, fac1 = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> mv;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pc;   // preconditioner applications
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ot;   // Gram-Schmidt passes
     double pc_bytes = 0;                                   // their algorithmic bytes
     vie::KernelTimer tc;
 };
@@ -544,11 +545,14 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
             // classical Gram-Schmidt, twice; the projections of both passes and
             // the new norm stay on the device until one copy at the end
             const size_t nh = 4 * (size_t)(k + 1);
+            cudaEvent_t o0 = ctx->event(), o1 = ctx->event();
+            if (o0) CK(cudaEventRecord(o0, st));
             CK(vie::dots<TV>(V, vs, k + 1, vn, N, hd, st));
             CK(vie::subtract<TV>(V, vs, k + 1, hd, vn, N, st));
             CK(vie::dots<TV>(V, vs, k + 1, vn, N, hd + nh, st));
             CK(vie::subtract<TV>(V, vs, k + 1, hd + nh, vn, N, st));
             CK(vie::dots<TV>(vn, 0, 1, vn, N, hd + 2 * nh, st));
+            if (o1) { CK(cudaEventRecord(o1, st)); tm.ot.push_back({o0, o1}); }
             CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * (2 * nh + 4), cudaMemcpyDeviceToHost, st));
             ctx->d2h += sizeof(double) * (2 * nh + 4);
             CK(cudaStreamSynchronize(st));
@@ -777,6 +781,9 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
         res->k_precond_ms = sp;
         res->k_precond_bytes = tm.pc_bytes;
         res->k_precond_n = (int32_t)tm.pc.size();
+        double so = 0;
+        for (auto &p : tm.ot) so += ev_ms(p.first, p.second);
+        res->k_ortho_ms = so;
     }
     res->status = stat;
     return stat;

@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "linalg.h"
+#include <type_traits>
 #include "tc_gemm.cuh"
 
 namespace vie {
@@ -731,32 +732,45 @@ __device__ __forceinline__ void load4(const double *p, double o[4]) {
 
 template <typename TV>
 __global__ void __launch_bounds__(256) k_dots(const TV *V, size_t vstride, int nv, const TV *w, int n, double *h) {
+    // FP32 vectors: FP32 products summed over a thread's 8 rows, FP64 from the
+    // warp reduction on (the FP64 pipe is narrow); FP64 vectors: FP64 throughout
+    using A = typename std::conditional<sizeof(TV) == 4, float, double>::type;
     __shared__ double red[8][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j = blockIdx.y;
     const TV *v = V + (size_t)j * vstride;
     const int base = blockIdx.x * DOT_CHUNK;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    A a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll
     for (int u = 0; u < DOT_CHUNK / 256; ++u) {
         const int i = base + u * 256 + threadIdx.x;
         if (i < n) {
-            double x[4], y[4];
-            load4(v + 4 * (size_t)i, x);
-            load4(w + 4 * (size_t)i, y);
+            A x[4], y[4];
+            if constexpr (sizeof(TV) == 4) {
+                const float4 p = *reinterpret_cast<const float4 *>(v + 4 * (size_t)i);
+                const float4 q = *reinterpret_cast<const float4 *>(w + 4 * (size_t)i);
+                x[0] = p.x; x[1] = p.y; x[2] = p.z; x[3] = p.w;
+                y[0] = q.x; y[1] = q.y; y[2] = q.z; y[3] = q.w;
+            } else {
+                double xd[4], yd[4];
+                load4(v + 4 * (size_t)i, xd);
+                load4(w + 4 * (size_t)i, yd);
+                for (int c = 0; c < 4; ++c) { x[c] = xd[c]; y[c] = yd[c]; }
+            }
             a0 += x[0] * y[0] + x[1] * y[1];
             a1 += x[0] * y[1] - x[1] * y[0];
             a2 += x[2] * y[2] + x[3] * y[3];
             a3 += x[2] * y[3] - x[3] * y[2];
         }
     }
+    double d0 = a0, d1 = a1, d2 = a2, d3 = a3;
     for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_down_sync(0xffffffffu, a0, o);
-        a1 += __shfl_down_sync(0xffffffffu, a1, o);
-        a2 += __shfl_down_sync(0xffffffffu, a2, o);
-        a3 += __shfl_down_sync(0xffffffffu, a3, o);
+        d0 += __shfl_down_sync(0xffffffffu, d0, o);
+        d1 += __shfl_down_sync(0xffffffffu, d1, o);
+        d2 += __shfl_down_sync(0xffffffffu, d2, o);
+        d3 += __shfl_down_sync(0xffffffffu, d3, o);
     }
-    if (lane == 0) { red[warp][0] = a0; red[warp][1] = a1; red[warp][2] = a2; red[warp][3] = a3; }
+    if (lane == 0) { red[warp][0] = d0; red[warp][1] = d1; red[warp][2] = d2; red[warp][3] = d3; }
     __syncthreads();
     if (threadIdx.x < 4) {
         double s2 = 0;
@@ -766,6 +780,43 @@ __global__ void __launch_bounds__(256) k_dots(const TV *V, size_t vstride, int n
 }
 
 // w[i][r] -= sum_j V_j[i][r] h[j][r]   (h on the device, FP64)
+// FP32 vectors: a CTA owns 32 rows (one per lane) and its 8 warps split the
+// basis vectors; 16-byte loads, FP32 products and sums, the 8 partial sums
+// combined through shared memory.  FP64 vectors: one thread per row.
+__global__ void __launch_bounds__(256) k_subtract_f32(const float *V, size_t vstride, int nv, const double *h,
+                                                      float *w, int n) {
+    __shared__ float4 part[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    float s0r = 0.f, s0i = 0.f, s1r = 0.f, s1i = 0.f;
+    if (i < n) {
+#pragma unroll 2
+        for (int j = warp; j < nv; j += 8) {
+            const float4 v = *reinterpret_cast<const float4 *>(V + (size_t)j * vstride + 4 * (size_t)i);
+            const double2 ha = __ldg(reinterpret_cast<const double2 *>(h + 4 * j));
+            const double2 hb = __ldg(reinterpret_cast<const double2 *>(h + 4 * j + 2));
+            const float h0 = (float)ha.x, h1 = (float)ha.y, h2 = (float)hb.x, h3 = (float)hb.y;
+            s0r = fmaf(v.x, h0, fmaf(-v.y, h1, s0r));
+            s0i = fmaf(v.x, h1, fmaf(v.y, h0, s0i));
+            s1r = fmaf(v.z, h2, fmaf(-v.w, h3, s1r));
+            s1i = fmaf(v.z, h3, fmaf(v.w, h2, s1i));
+        }
+    }
+    part[warp][lane] = make_float4(s0r, s0i, s1r, s1i);
+    __syncthreads();
+    if (warp == 0 && i < n) {
+        float4 t = part[0][lane];
+        for (int q = 1; q < 8; ++q) {
+            const float4 u = part[q][lane];
+            t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+        }
+        float4 *o = reinterpret_cast<float4 *>(w + 4 * (size_t)i);
+        float4 c = *o;
+        c.x -= t.x; c.y -= t.y; c.z -= t.z; c.w -= t.w;
+        *o = c;
+    }
+}
+
 template <typename TV>
 __global__ void k_subtract(const TV *V, size_t vstride, int nv, const double *h, TV *w, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -827,7 +878,12 @@ cudaError_t dots(const TV *V, size_t vstride, int nv, const TV *w, int n, double
 }
 template <typename TV>
 cudaError_t subtract(const TV *V, size_t vstride, int nv, const double *h, TV *w, int n, cudaStream_t st) {
-    k_subtract<TV><<<(n + 255) / 256, 256, 0, st>>>(V, vstride, nv, h, w, n); ++g_launches;
+    if constexpr (sizeof(TV) == 4) {
+        k_subtract_f32<<<(n + 31) / 32, 256, 0, st>>>(V, vstride, nv, h, w, n);
+    } else {
+        k_subtract<TV><<<(n + 255) / 256, 256, 0, st>>>(V, vstride, nv, h, w, n);
+    }
+    ++g_launches;
     return cudaGetLastError();
 }
 template <typename TX, typename TY>

@@ -52,7 +52,8 @@ class Result(ctypes.Structure):
                 ("n_launches", ctypes.c_int32), ("t_queue_ms", ctypes.c_double),
                 ("t_latency_ms", ctypes.c_double), ("k_precond_ms", ctypes.c_double),
                 ("k_precond_bytes", ctypes.c_double), ("k_precond_n", ctypes.c_int32),
-                ("reserved3", ctypes.c_int32), ("k_tc_flops", ctypes.c_double)]
+                ("reserved3", ctypes.c_int32), ("k_tc_flops", ctypes.c_double),
+                ("k_ortho_ms", ctypes.c_double)]
 
 
 class Mesh(ctypes.Structure):
@@ -199,7 +200,7 @@ class Solver:
                     k_tc_bytes=res.k_tc_bytes, k_tc_n=res.k_tc_n, n_launches=res.n_launches,
                     t_queue_ms=res.t_queue_ms, t_latency_ms=res.t_latency_ms, k_precond_ms=res.k_precond_ms,
                     k_precond_bytes=res.k_precond_bytes, k_precond_n=res.k_precond_n, k_tc_flops=res.k_tc_flops,
-                    x=out)
+                    k_ortho_ms=res.k_ortho_ms, x=out)
 
     def solve_batch(self, lams, thetas, phis, eps_list, max_slots=2, coeffs=False, stream=None):
         """Independent solves of one mesh (vie_solve_batch): lams/thetas/phis/eps_list
