@@ -95,7 +95,7 @@ struct vie_ctx {
     DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab, rtab, ew;
     double z_extent = 0;
     // solve buffers
-    DevBuf Z, b, x, r, u, w, V, h, y, Minv, MinvH, amax, tcpack, status, acc, J, rt, cout;
+    DevBuf Z, b, x, r, u, w, V, h, y, Minv, MinvH, amax, tcpack, status, acc, J, rt, cout, xs;
     std::vector<double> pinv;   // per domain block: 1 / (power-of-two scale of its FP16 inverse)
     size_t ld = 0;
     int64_t h2d = 0, d2h = 0;   // bytes copied by the current solve
@@ -488,16 +488,24 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
     };
     double bn[2];
     if (int e = norms2(ctx->b.as<double>(), bn)) return e;
+    const double b_raw[2] = {bn[0], bn[1]};
     for (int p = 0; p < 2; ++p) if (!(bn[p] > 0)) bn[p] = 1.0;
     int iters[2] = {0, 0};
     int total = 0, sweeps = 0;
     double rel[2] = {1, 1};
+    bool x_zero = true;   // the first sweep starts from x = 0: r = b
+    if (std::is_same<TZ, float>::value) CK(ctx->xs.ensure(sizeof(float) * 8 * (size_t)N));
     while (true) {
-        // FP64 residual r = b - Z x
+        // FP64 residual r = b - Z x (FP32 Z: double-length product from FP32 arithmetic)
         CK(cudaMemcpyAsync(r, ctx->b.p, sizeof(double) * vs, cudaMemcpyDeviceToDevice, st));
-        CK((vie::matvec<TZ, double, double>(Z, ctx->ld, N, N, x, r, -1.0, true, st)));
-        double rn[2];
-        if (int e = norms2(r, rn)) return e;
+        double rn[2] = {b_raw[0], b_raw[1]};
+        if (!x_zero) {
+            if constexpr (std::is_same<TZ, float>::value)
+                CK(vie::matvec_ds(Z, ctx->ld, N, N, x, ctx->xs.as<float>(), r, -1.0, true, st));
+            else
+                CK((vie::matvec<TZ, double, double>(Z, ctx->ld, N, N, x, r, -1.0, true, st)));
+            if (int e = norms2(r, rn)) return e;
+        }
         rel[0] = rn[0] / bn[0];
         rel[1] = rn[1] / bn[1];
         bool active[2] = {rel[0] > tol, rel[1] > tol};
@@ -608,6 +616,7 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
             ctx->h2d += sizeof(double) * 4 * kmax;
             CK(vie::combine<TV>(V, vs, kmax, ctx->y.as<double>(), x, N, st));
             CK(cudaStreamSynchronize(st));
+            x_zero = false;
         }
         if (kmax == 0) break;
     }
@@ -1249,7 +1258,7 @@ void release_device_memory(vie_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->row, &ctx->coef, &ctx->wt, &ctx->kap, &ctx->ieps, &ctx->frow, &ctx->qs,
                       &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->rtab, &ctx->ew,
                       &ctx->Z, &ctx->b, &ctx->x, &ctx->r, &ctx->u, &ctx->w, &ctx->V, &ctx->h, &ctx->y,
-                      &ctx->Minv, &ctx->MinvH, &ctx->amax, &ctx->tcpack, &ctx->status, &ctx->acc, &ctx->J,
+                      &ctx->Minv, &ctx->MinvH, &ctx->amax, &ctx->tcpack, &ctx->status, &ctx->acc, &ctx->J, &ctx->xs,
                       &ctx->rt, &ctx->cout};
     for (DevBuf *b : bufs) b->release();
 }

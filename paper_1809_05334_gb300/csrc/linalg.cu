@@ -186,6 +186,152 @@ cudaError_t to_half(const float *A, size_t count, float scale, __half *B, cudaSt
     return cudaGetLastError();
 }
 template cudaError_t matvec<float, double, double>(const float *, size_t, int, int, const double *, double *, double, bool, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Residual product of the FP64 refinement, y <- y + alpha Z x, Z in FP32 and
+// x, y in FP64, without FP64 arithmetic in the inner loop (the FP64 pipe is a
+// small fraction of the FP32 one): x is split once into x = xh + xl (two FP32
+// parts, 48 significant bits), every product Z xh is formed exactly as p + e
+// (p = Z xh rounded, e = fma(Z, xh, -p)), the p are summed with TwoSum into a
+// running (S, C) pair per output value, and e and the small Z xl terms go into
+// C.  The result carries the error of a double-length sum (~2^-44 of the sum
+// of |terms|), far below the FP32 rounding of Z itself.  Same row and column
+// split as k_matvec.
+// ---------------------------------------------------------------------------
+__global__ void k_split_x(const double *__restrict__ x, float *__restrict__ xs, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * n) return;
+    const double v = x[i];
+    const float h = (float)v;
+    const float l = (float)(v - (double)h);
+    const int r = i / 4, k = i % 4;
+    xs[8 * (size_t)r + k] = h;
+    xs[8 * (size_t)r + 4 + k] = l;
+}
+
+struct DS {   // unevaluated sum S + C
+    float s, c;
+};
+__device__ __forceinline__ void ds_add(DS &a, float p) {   // a += p (TwoSum on the leading part)
+    const float t = __fadd_rn(a.s, p);
+    const float bp = __fsub_rn(t, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    a.s = t;
+    a.c = __fadd_rn(a.c, err);
+}
+// a += z * xh + z * xl, the first product exact (p + e)
+__device__ __forceinline__ void ds_fma(DS &a, float z, float xh, float xl) {
+    const float p = __fmul_rn(z, xh);
+    const float e = __fmaf_rn(z, xh, -p);
+    ds_add(a, p);
+    a.c = __fmaf_rn(z, xl, __fadd_rn(a.c, e));
+}
+__device__ __forceinline__ DS ds_sum(DS a, DS b) {
+    DS r = a;
+    ds_add(r, b.s);
+    r.c = __fadd_rn(r.c, b.c);
+    return r;
+}
+
+template <bool ACCUM>
+__global__ void __launch_bounds__(MV_WARPS * 32)
+k_matvec_ds(const float *__restrict__ A, size_t ld, int rows, int cols, const float *__restrict__ xs,
+            double *__restrict__ y, double alpha) {
+    __shared__ double part[2][MV_WARPS][MV_ROWS * 4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rb = (int)((long long)rows * blockIdx.x / gridDim.x);
+    const int re = (int)((long long)rows * (blockIdx.x + 1) / gridDim.x);
+    const int nvec = (cols + 1) / 2;   // two complex FP32 entries per 16-byte load
+    const int v0 = (int)((long long)nvec * warp / MV_WARPS), v1 = (int)((long long)nvec * (warp + 1) / MV_WARPS);
+    int buf = 0;
+    for (int r0 = rb; r0 < re; r0 += MV_ROWS, buf ^= 1) {
+        DS acc[MV_ROWS][4];
+#pragma unroll
+        for (int i = 0; i < MV_ROWS; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][k] = {0.f, 0.f};
+        for (int v = v0 + lane; v < v1; v += 32) {
+            const int c = 2 * v;
+            float4 z[MV_ROWS];
+#pragma unroll
+            for (int i = 0; i < MV_ROWS; ++i) {
+                if (r0 + i < re) z[i] = __ldcs(reinterpret_cast<const float4 *>(A + 2 * ((size_t)(r0 + i) * ld + c)));
+                else z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+                if (c + u < cols) {
+                    h = __ldg(reinterpret_cast<const float4 *>(xs + 8 * (size_t)(c + u)));
+                    l = __ldg(reinterpret_cast<const float4 *>(xs + 8 * (size_t)(c + u) + 4));
+                }
+#pragma unroll
+                for (int i = 0; i < MV_ROWS; ++i) {
+                    const float zr = u == 0 ? z[i].x : z[i].z, zi = u == 0 ? z[i].y : z[i].w;
+                    // (zr + j zi)(xr + j xi) for the two right-hand sides
+                    ds_fma(acc[i][0], zr, h.x, l.x);
+                    ds_fma(acc[i][0], -zi, h.y, l.y);
+                    ds_fma(acc[i][1], zr, h.y, l.y);
+                    ds_fma(acc[i][1], zi, h.x, l.x);
+                    ds_fma(acc[i][2], zr, h.z, l.z);
+                    ds_fma(acc[i][2], -zi, h.w, l.w);
+                    ds_fma(acc[i][3], zr, h.w, l.w);
+                    ds_fma(acc[i][3], zi, h.z, l.z);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < MV_ROWS; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    DS b;
+                    b.s = __shfl_down_sync(0xffffffffu, acc[i][k].s, o);
+                    b.c = __shfl_down_sync(0xffffffffu, acc[i][k].c, o);
+                    acc[i][k] = ds_sum(acc[i][k], b);
+                }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < MV_ROWS; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) part[buf][warp][4 * i + k] = (double)acc[i][k].s + (double)acc[i][k].c;
+        }
+        __syncthreads();
+        if (threadIdx.x < MV_ROWS * 4) {
+            const int i = threadIdx.x / 4, k = threadIdx.x % 4;
+            const int r = r0 + i;
+            if (r < re) {
+                double s = 0.0;
+#pragma unroll
+                for (int w2 = 0; w2 < MV_WARPS; ++w2) s += part[buf][w2][threadIdx.x];
+                if (ACCUM) y[(size_t)r * 4 + k] += alpha * s;
+                else y[(size_t)r * 4 + k] = alpha * s;
+            }
+        }
+    }
+}
+
+cudaError_t matvec_ds(const float *A, size_t ld, int rows, int cols, const double *x, float *xs, double *y,
+                      double alpha, bool accumulate, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    static int slots = 0;   // resident CTAs of the GPU (one device per process)
+    if (slots == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_matvec_ds<false>, MV_WARPS * 32, 0);
+        if (e != cudaSuccess) return e;
+        slots = std::max(1, sms * per);
+    }
+    k_split_x<<<(4 * cols + 255) / 256, 256, 0, st>>>(x, xs, cols); ++g_launches;
+    const int grid = std::max(1, std::min(slots, (rows + MV_ROWS - 1) / MV_ROWS));
+    if (accumulate) k_matvec_ds<true><<<grid, MV_WARPS * 32, 0, st>>>(A, ld, rows, cols, xs, y, alpha);
+    else k_matvec_ds<false><<<grid, MV_WARPS * 32, 0, st>>>(A, ld, rows, cols, xs, y, alpha);
+    ++g_launches;
+    return cudaGetLastError();
+}
 template cudaError_t matvec<double, double, double>(const double *, size_t, int, int, const double *, double *, double, bool, cudaStream_t);
 
 // ---------------------------------------------------------------------------

@@ -10,6 +10,11 @@
 
 namespace vie {
 
+// y <- alpha Z x (+ y if accumulate) for FP32 Z and FP64 x, y, at double-length
+// accuracy from FP32 arithmetic (x split into two FP32 parts, exact products,
+// compensated sums); xs is device scratch of 8 cols floats
+cudaError_t matvec_ds(const float *A, size_t ld, int rows, int cols, const double *x, float *xs, double *y,
+                      double alpha, bool accumulate, cudaStream_t st);
 template <typename TZ, typename TX, typename TA>
 cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *y, TA alpha, bool accumulate,
                    cudaStream_t st);
