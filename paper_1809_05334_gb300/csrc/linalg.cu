@@ -545,72 +545,98 @@ template cudaError_t gj_invert<float>(float *, size_t, int, int *, cudaStream_t)
 template cudaError_t gj_invert<double>(double *, size_t, int, int *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Gauss-Jordan with 256-wide outer pivot blocks and tensor-core products
+// Gauss-Jordan with 512-wide outer pivot blocks and tensor-core products
 // (FP32 matrix; FP16 operands scaled by powers of two, FP32 accumulation).
 // ---------------------------------------------------------------------------
 constexpr int GJ_W = 128;     // pivot block width (the K of the tensor-core update)
 
 // In-place Gauss-Jordan inverse of the w x w (w <= GJ_W) pivot block, held in
-// registers: thread t owns column c = t % 128 and rows g + 8q (g = t / 128,
-// q = 0..15).  Per pivot j the owners publish row j and column j through
-// double-buffered shared memory (one barrier per pivot); every thread forms
-// p = 1 / a_jj and updates its 32 entries.
-constexpr int GJ_DG = 8;   // row groups of the pivot-block inverse (1024 threads)
+// registers: 512 threads, thread t owns column c = t % 128 and the rows
+// g + 4q (g = t / 128, q = 0..31).  Pivot j (p = 1 / a_jj, m_c = p a_jc off
+// the pivot column, m_j = p) is one update of every entry,
+//   a_ic <- a_ic - f_i m_c,   f_i = a_ij for i != j,  f_j = a_jj - 1,
+// with the pivot-column owner starting from the unit vector e_j: this gives
+// p a_jc on row j, p at (j, j), -a_ij p on column j and a_ic - a_ij p a_jc
+// elsewhere.  Row j and the factors f travel through double-buffered shared
+// memory; the owners of row j+1 and column j+1 publish them right after their
+// update of pivot j, so one barrier per pivot suffices.
+constexpr int GJ_DG = 4;               // row groups of the pivot-block inverse (512 threads)
+constexpr int GJ_RQ = GJ_W / GJ_DG;    // rows per thread
 __global__ void __launch_bounds__(GJ_W * GJ_DG) k_gj_diag_w(float *A, size_t ld, int k0, int w, int *status) {
-    __shared__ float2 rowbuf[2][GJ_W], colbuf[2][GJ_W];
+    __shared__ float2 rowbuf[2][GJ_W];
+    __shared__ __align__(16) float2 colbuf[2][GJ_DG][GJ_RQ];   // factors f of pivot j: row g + 4q at [g][q]
     const int c = threadIdx.x & (GJ_W - 1), g = threadIdx.x >> 7;
-    float pr[GJ_W / GJ_DG], pi[GJ_W / GJ_DG];
+    float2 a[GJ_RQ];
 #pragma unroll
-    for (int q = 0; q < GJ_W / GJ_DG; ++q) {
+    for (int q = 0; q < GJ_RQ; ++q) {
         const int i = g + GJ_DG * q;
-        float2 v = make_float2(0.f, 0.f);
-        if (i < w && c < w) v = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)(k0 + i) * ld + k0 + c));
-        pr[q] = v.x;
-        pi[q] = v.y;
+        a[q] = make_float2(0.f, 0.f);
+        if (i < w && c < w) a[q] = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)(k0 + i) * ld + k0 + c));
+    }
+    // pivot 0: row 0 (group 0) and the factors of column 0 (diagonal one minus one)
+    if (g == 0) rowbuf[0][c] = a[0];
+    if (c == 0) {
+#pragma unroll
+        for (int q = 0; q < GJ_RQ; ++q) colbuf[0][g][q] = a[q];
+        if (g == 0) colbuf[0][0][0] = make_float2(a[0].x - 1.f, a[0].y);
     }
     for (int j = 0; j < w; ++j) {
-        const int b = j & 1;
-        const int qj = j / GJ_DG;
-        if (g == j % GJ_DG) {   // this thread holds row j of column c
-            float xr = 0.f, xi = 0.f;
-#pragma unroll
-            for (int q = 0; q < GJ_W / GJ_DG; ++q)
-                if (q == qj) { xr = pr[q]; xi = pi[q]; }
-            rowbuf[b][c] = make_float2(xr, xi);
-        }
-        if (c == j) {         // this thread holds column j for its rows
-#pragma unroll
-            for (int q = 0; q < GJ_W / GJ_DG; ++q) colbuf[b][g + GJ_DG * q] = make_float2(pr[q], pi[q]);
-        }
+        const int b = j & 1, nb = b ^ 1, jn = j + 1;
         __syncthreads();
         const float2 pv = rowbuf[b][j];
         const float d = pv.x * pv.x + pv.y * pv.y;
         if (threadIdx.x == 0 && (!(d > 0.f) || !isfinite(d))) atomicExch(status, 1);
-        const float qr = pv.x / d, qi = -pv.y / d;            // p = 1 / a_jj
+        const float rd = __frcp_rn(d);
+        const float qr = pv.x * rd, qi = -pv.y * rd;   // p = 1 / a_jj
         const float2 rc = rowbuf[b][c];
-        const float nr = qr * rc.x - qi * rc.y, ni = qr * rc.y + qi * rc.x;   // p a_jc
+        float mr = qr * rc.x - qi * rc.y, mi = qr * rc.y + qi * rc.x;
+        if (c == j) {   // the pivot column: m = p, entries from e_j
+            mr = qr;
+            mi = qi;
 #pragma unroll
-        for (int q = 0; q < GJ_W / GJ_DG; ++q) {
-            const int i = g + GJ_DG * q;
-            if (i == j) {                                       // row j <- p row j, a_jj <- p
-                pr[q] = (c == j) ? qr : nr;
-                pi[q] = (c == j) ? qi : ni;
-            } else {
-                const float2 f = colbuf[b][i];
-                if (c == j) {                                   // a_ij <- -f p
-                    pr[q] = -(f.x * qr - f.y * qi);
-                    pi[q] = -(f.x * qi + f.y * qr);
-                } else {                                        // a_ic <- a_ic - f (p a_jc)
-                    pr[q] -= f.x * nr - f.y * ni;
-                    pi[q] -= f.x * ni + f.y * nr;
-                }
+            for (int q = 0; q < GJ_RQ; ++q) a[q] = make_float2(g + GJ_DG * q == j ? 1.f : 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < GJ_RQ; q2 += 2) {
+            const float4 ff = *reinterpret_cast<const float4 *>(&colbuf[b][g][q2]);
+            a[q2].x = fmaf(-ff.x, mr, fmaf(ff.y, mi, a[q2].x));
+            a[q2].y = fmaf(-ff.x, mi, fmaf(-ff.y, mr, a[q2].y));
+            a[q2 + 1].x = fmaf(-ff.z, mr, fmaf(ff.w, mi, a[q2 + 1].x));
+            a[q2 + 1].y = fmaf(-ff.z, mi, fmaf(-ff.w, mr, a[q2 + 1].y));
+        }
+        // publish row j + 1: its owners (group jn % 4, slot jn / 4; a warp-uniform
+        // branch) store their entry, the slot picked by a jump over static indices
+        const int qn = ((jn - g) & (GJ_DG - 1)) == 0 ? (jn - g) / GJ_DG : -1;
+        if (qn >= 0) {
+            switch (qn) {
+#define GJ_ROW_CASE(k) case k: rowbuf[nb][c] = a[k]; break;
+                GJ_ROW_CASE(0) GJ_ROW_CASE(1) GJ_ROW_CASE(2) GJ_ROW_CASE(3) GJ_ROW_CASE(4) GJ_ROW_CASE(5)
+                GJ_ROW_CASE(6) GJ_ROW_CASE(7) GJ_ROW_CASE(8) GJ_ROW_CASE(9) GJ_ROW_CASE(10) GJ_ROW_CASE(11)
+                GJ_ROW_CASE(12) GJ_ROW_CASE(13) GJ_ROW_CASE(14) GJ_ROW_CASE(15) GJ_ROW_CASE(16) GJ_ROW_CASE(17)
+                GJ_ROW_CASE(18) GJ_ROW_CASE(19) GJ_ROW_CASE(20) GJ_ROW_CASE(21) GJ_ROW_CASE(22) GJ_ROW_CASE(23)
+                GJ_ROW_CASE(24) GJ_ROW_CASE(25) GJ_ROW_CASE(26) GJ_ROW_CASE(27) GJ_ROW_CASE(28) GJ_ROW_CASE(29)
+                GJ_ROW_CASE(30) GJ_ROW_CASE(31)
+#undef GJ_ROW_CASE
+                default: break;
+            }
+        }
+        if (c == jn) {   // publish the factors of column j + 1, the diagonal one minus one
+#pragma unroll
+            for (int q = 0; q < GJ_RQ; ++q) colbuf[nb][g][q] = a[q];
+            if (qn >= 0) {
+                const float2 dj = rowbuf[nb][jn];
+                colbuf[nb][g][qn] = make_float2(dj.x - 1.f, dj.y);
             }
         }
     }
+    // store through an opaque copy of A: the addresses are formed here, not
+    // kept live across the pivot loop from the loads above
+    float *Ao;
+    asm volatile("mov.b64 %0, %1;" : "=l"(Ao) : "l"(A));
 #pragma unroll
-    for (int q = 0; q < GJ_W / GJ_DG; ++q) {
+    for (int q = 0; q < GJ_RQ; ++q) {
         const int i = g + GJ_DG * q;
-        if (i < w && c < w) *reinterpret_cast<float2 *>(A + 2 * ((size_t)(k0 + i) * ld + k0 + c)) = make_float2(pr[q], pi[q]);
+        if (i < w && c < w) *reinterpret_cast<float2 *>(Ao + 2 * ((size_t)(k0 + i) * ld + k0 + c)) = a[q];
     }
 }
 
@@ -651,9 +677,10 @@ bool tensor_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t row
 }
 }  // namespace
 
-constexpr int GJ_P = 256;   // pivot width of the outer Gauss-Jordan steps (the K of their products)
+constexpr int GJ_P = 512;   // pivot width of the outer Gauss-Jordan steps (the K of their products)
 static_assert(GJ_P <= TC_KP, "the packed operands hold one outer pivot block");
-static_assert(GJ_W == 128 && GJ_P == 2 * GJ_W, "a pivot block is inverted in two 128-wide steps");
+static_assert(GJ_RQ == 32, "the row-publish jump covers 32 slots");
+static_assert(GJ_W == 128 && GJ_P % GJ_W == 0, "a pivot block is inverted in 128-wide steps");
 
 constexpr int GJ_WORDS = 16;   // largest-entry words: 4 per set (products (a), (3)), 2 for the pivot blocks
 
@@ -735,14 +762,16 @@ cudaError_t invert_pivot_block(float *Ab, size_t ld, int w, int *status, __half 
 }  // namespace
 
 // One outer Gauss-Jordan step with pivot block P = A[k0:k0+w, k0:k0+w]
-// (w = 256; rows and columns outside it: the trailing set T):
+// (w = 512; rows and columns outside it: the trailing set T):
 //   1. P <- P^-1                                  (invert_pivot_block)
 //   2. A[T, P] <- -A[T, P] P^-1                   (product (a): trailing rows x pivot columns, beta 0)
 //   3. A[T, T] <- A[T, T] + A[T, P] A[P, T],  A[P, T] <- P^-1 A[P, T]
 //      as one product over all rows in natural order (the pivot rows' A operand
 //      is P^-1) x the trailing columns, beta 0 on the pivot tile rows
-// Products (a) and (3) run on the tensor cores from packed operands (K = 256:
-// the HBM traffic of the inversion is proportional to n^3 / w).
+// Products (a) and (3) run on the tensor cores from packed operands (K = 512:
+// every step streams the whole n x (n - w) matrix, so the HBM traffic of the
+// inversion is 16 n^3 / w bytes; at w = 512 the products sit near the ridge of
+// the FP16 tensor rate and the HBM bandwidth).
 // Look-ahead: product (3) is split into the tile columns holding the next
 // pivot block (on st) and the rest (on aux, on all SMs but four).  The next
 // step's pivot inverse and column-panel product need only the first part, so
