@@ -66,7 +66,7 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
         for (int i = 0; i < MV_ROWS; ++i)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[i][k] = TA(0);
-#pragma unroll 2
+#pragma unroll 8
         for (int v = v0 + lane; v < v1; v += 32) {
             const int c = v * VEC;
             typename V2<TZ>::t z[MV_ROWS];
