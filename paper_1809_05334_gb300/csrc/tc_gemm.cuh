@@ -222,9 +222,13 @@ struct TcMap {
 };
 
 // tile t of the product -> (tile row, tile column)
+// Tiles run column by column (t -> tile row t % ntm of tile column t / ntm): a
+// wave of CTAs shares one B tile (the larger, 2x expanded operand) and sweeps
+// the A panel, which stays in L2 beside the C column streaming through.
 __device__ __forceinline__ void tc_tile(const TcMap &mp, int ntx, int t, int &ty, int &tx) {
-    ty = t / ntx;
-    const int i = t % ntx;
+    const int ntm = (mp.mrows + TC_TM - 1) / TC_TM;
+    ty = t % ntm;
+    const int i = t / ntm;
     tx = mp.only_n > 0 ? mp.only_lo + i : (mp.skip_n > 0 && i >= mp.skip_lo ? i + mp.skip_n : i);
 }
 
