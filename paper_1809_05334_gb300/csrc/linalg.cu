@@ -551,86 +551,100 @@ template cudaError_t gj_invert<double>(double *, size_t, int, int *, cudaStream_
 constexpr int GJ_W = 128;     // pivot block width (the K of the tensor-core update)
 
 // In-place Gauss-Jordan inverse of the w x w (w <= GJ_W) pivot block, held in
-// registers: 512 threads, thread t owns column c = t % 128 and the rows
-// g + 4q (g = t / 128, q = 0..31).  Pivot j (p = 1 / a_jj, m_c = p a_jc off
-// the pivot column, m_j = p) is one update of every entry,
-//   a_ic <- a_ic - f_i m_c,   f_i = a_ij for i != j,  f_j = a_jj - 1,
-// with the pivot-column owner starting from the unit vector e_j: this gives
-// p a_jc on row j, p at (j, j), -a_ij p on column j and a_ic - a_ij p a_jc
-// elsewhere.  Row j and the factors f travel through double-buffered shared
-// memory; the owners of row j+1 and column j+1 publish them right after their
-// update of pivot j, so one barrier per pivot suffices.
+// registers, two pivots per step: 512 threads, thread t owns column c = t % 128
+// and the rows g + 4q (g = t / 128, q = 0..31); the block is padded with the
+// identity up to an even width.  Step (j, j+1) with the 2 x 2 pivot block P
+// and rows R = A[j:j+2, :] is one update of every entry,
+//   a_ic <- a_ic - f_i0 m_0c - f_i1 m_1c,
+// m_c = P^-1 R[:, c] off the pivot columns and the matching column of P^-1 on
+// them; f_i = (a_ij, a_i,j+1) off the pivot rows and the rows of P - I on them;
+// the owners of the pivot columns start from the unit vectors.  This gives
+// P^-1 R on the pivot rows, P^-1 on the pivot block, -F P^-1 on the pivot
+// columns and A - F P^-1 R elsewhere.  The pivot rows and the factors travel
+// through double-buffered shared memory; the owners of the next pair publish
+// them right after their update, so one barrier per two pivots suffices.
 constexpr int GJ_DG = 4;               // row groups of the pivot-block inverse (512 threads)
 constexpr int GJ_RQ = GJ_W / GJ_DG;    // rows per thread
 __global__ void __launch_bounds__(GJ_W * GJ_DG) k_gj_diag_w(float *A, size_t ld, int k0, int w, int *status) {
-    __shared__ float2 rowbuf[2][GJ_W];
-    __shared__ __align__(16) float2 colbuf[2][GJ_DG][GJ_RQ];   // factors f of pivot j: row g + 4q at [g][q]
+    __shared__ float2 rowbuf[2][2][GJ_W];
+    __shared__ __align__(16) float2 colbuf[2][GJ_DG][GJ_RQ][2];   // factors (f0, f1) of the pivot pair, row g + 4q
     const int c = threadIdx.x & (GJ_W - 1), g = threadIdx.x >> 7;
     float2 a[GJ_RQ];
 #pragma unroll
     for (int q = 0; q < GJ_RQ; ++q) {
         const int i = g + GJ_DG * q;
-        a[q] = make_float2(0.f, 0.f);
+        a[q] = make_float2(i == c && (i >= w || c >= w) ? 1.f : 0.f, 0.f);   // identity on the padding
         if (i < w && c < w) a[q] = *reinterpret_cast<const float2 *>(A + 2 * ((size_t)(k0 + i) * ld + k0 + c));
     }
-    // pivot 0: row 0 (group 0) and the factors of column 0 (diagonal one minus one)
-    if (g == 0) rowbuf[0][c] = a[0];
-    if (c == 0) {
+    const int wr = (w + 1) & ~1;
+    // pair 0: rows 0, 1 (groups 0, 1, slot 0), columns 0, 1, the diagonal factors minus one
+    if (g < 2) rowbuf[0][g][c] = a[0];
+    if (c < 2) {
 #pragma unroll
-        for (int q = 0; q < GJ_RQ; ++q) colbuf[0][g][q] = a[q];
-        if (g == 0) colbuf[0][0][0] = make_float2(a[0].x - 1.f, a[0].y);
+        for (int q = 0; q < GJ_RQ; ++q) colbuf[0][g][q][c] = a[q];
+        if (g == c) colbuf[0][g][0][c] = make_float2(a[0].x - 1.f, a[0].y);
     }
-    for (int j = 0; j < w; ++j) {
-        const int b = j & 1, nb = b ^ 1, jn = j + 1;
+    for (int j = 0; j < wr; j += 2) {
+        const int b = (j >> 1) & 1, nb = b ^ 1, jn = j + 2;
         __syncthreads();
-        const float2 pv = rowbuf[b][j];
-        const float d = pv.x * pv.x + pv.y * pv.y;
-        if (threadIdx.x == 0 && (!(d > 0.f) || !isfinite(d))) atomicExch(status, 1);
-        const float rd = __frcp_rn(d);
-        const float qr = pv.x * rd, qi = -pv.y * rd;   // p = 1 / a_jj
-        const float2 rc = rowbuf[b][c];
-        float mr = qr * rc.x - qi * rc.y, mi = qr * rc.y + qi * rc.x;
-        if (c == j) {   // the pivot column: m = p, entries from e_j
-            mr = qr;
-            mi = qi;
+        const float2 p00 = rowbuf[b][0][j], p01 = rowbuf[b][0][j + 1], p10 = rowbuf[b][1][j], p11 = rowbuf[b][1][j + 1];
+        const float dr = (p00.x * p11.x - p00.y * p11.y) - (p01.x * p10.x - p01.y * p10.y);
+        const float di = (p00.x * p11.y + p00.y * p11.x) - (p01.x * p10.y + p01.y * p10.x);
+        const float dd = dr * dr + di * di;
+        if (threadIdx.x == 0 && (!(dd > 0.f) || !isfinite(dd))) atomicExch(status, 1);
+        const float rd = __frcp_rn(dd);
+        const float er = dr * rd, ei = -di * rd;   // 1 / det
+        auto cm = [](float ar, float ai, float br, float bi) { return make_float2(ar * br - ai * bi, ar * bi + ai * br); };
+        const float2 q00 = cm(p11.x, p11.y, er, ei), q01 = cm(-p01.x, -p01.y, er, ei);
+        const float2 q10 = cm(-p10.x, -p10.y, er, ei), q11 = cm(p00.x, p00.y, er, ei);   // P^-1
+        float2 m0, m1;
+        if (c == j || c == j + 1) {   // a pivot column: m = column of P^-1, entries from the unit vector
+            m0 = c == j ? q00 : q01;
+            m1 = c == j ? q10 : q11;
 #pragma unroll
-            for (int q = 0; q < GJ_RQ; ++q) a[q] = make_float2(g + GJ_DG * q == j ? 1.f : 0.f, 0.f);
+            for (int q = 0; q < GJ_RQ; ++q) a[q] = make_float2(g + GJ_DG * q == c ? 1.f : 0.f, 0.f);
+        } else {
+            const float2 r0 = rowbuf[b][0][c], r1 = rowbuf[b][1][c];
+            m0 = make_float2(q00.x * r0.x - q00.y * r0.y + q01.x * r1.x - q01.y * r1.y,
+                             q00.x * r0.y + q00.y * r0.x + q01.x * r1.y + q01.y * r1.x);
+            m1 = make_float2(q10.x * r0.x - q10.y * r0.y + q11.x * r1.x - q11.y * r1.y,
+                             q10.x * r0.y + q10.y * r0.x + q11.x * r1.y + q11.y * r1.x);
         }
 #pragma unroll
-        for (int q2 = 0; q2 < GJ_RQ; q2 += 2) {
-            const float4 ff = *reinterpret_cast<const float4 *>(&colbuf[b][g][q2]);
-            a[q2].x = fmaf(-ff.x, mr, fmaf(ff.y, mi, a[q2].x));
-            a[q2].y = fmaf(-ff.x, mi, fmaf(-ff.y, mr, a[q2].y));
-            a[q2 + 1].x = fmaf(-ff.z, mr, fmaf(ff.w, mi, a[q2 + 1].x));
-            a[q2 + 1].y = fmaf(-ff.z, mi, fmaf(-ff.w, mr, a[q2 + 1].y));
+        for (int q = 0; q < GJ_RQ; ++q) {
+            const float4 ff = *reinterpret_cast<const float4 *>(&colbuf[b][g][q][0]);
+            a[q].x = fmaf(-ff.x, m0.x, fmaf(ff.y, m0.y, fmaf(-ff.z, m1.x, fmaf(ff.w, m1.y, a[q].x))));
+            a[q].y = fmaf(-ff.x, m0.y, fmaf(-ff.y, m0.x, fmaf(-ff.z, m1.y, fmaf(-ff.w, m1.x, a[q].y))));
         }
-        // publish row j + 1: its owners (group jn % 4, slot jn / 4; a warp-uniform
-        // branch) store their entry, the slot picked by a jump over static indices
-        const int qn = ((jn - g) & (GJ_DG - 1)) == 0 ? (jn - g) / GJ_DG : -1;
-        if (qn >= 0) {
-            switch (qn) {
-#define GJ_ROW_CASE(k) case k: rowbuf[nb][c] = a[k]; break;
-                GJ_ROW_CASE(0) GJ_ROW_CASE(1) GJ_ROW_CASE(2) GJ_ROW_CASE(3) GJ_ROW_CASE(4) GJ_ROW_CASE(5)
-                GJ_ROW_CASE(6) GJ_ROW_CASE(7) GJ_ROW_CASE(8) GJ_ROW_CASE(9) GJ_ROW_CASE(10) GJ_ROW_CASE(11)
-                GJ_ROW_CASE(12) GJ_ROW_CASE(13) GJ_ROW_CASE(14) GJ_ROW_CASE(15) GJ_ROW_CASE(16) GJ_ROW_CASE(17)
-                GJ_ROW_CASE(18) GJ_ROW_CASE(19) GJ_ROW_CASE(20) GJ_ROW_CASE(21) GJ_ROW_CASE(22) GJ_ROW_CASE(23)
-                GJ_ROW_CASE(24) GJ_ROW_CASE(25) GJ_ROW_CASE(26) GJ_ROW_CASE(27) GJ_ROW_CASE(28) GJ_ROW_CASE(29)
-                GJ_ROW_CASE(30) GJ_ROW_CASE(31)
+        if (jn < wr) {
+            // rows jn, jn + 1: groups jn % 4 and jn % 4 + 1, slot jn / 4
+            const int gj = jn & (GJ_DG - 1), qn = jn / GJ_DG;
+            if (g == gj || g == gj + 1) {
+                float2 r = make_float2(0.f, 0.f);
+                switch (qn) {
+#define GJ_ROW_CASE(k) case k: r = a[k]; break;
+                    GJ_ROW_CASE(0) GJ_ROW_CASE(1) GJ_ROW_CASE(2) GJ_ROW_CASE(3) GJ_ROW_CASE(4) GJ_ROW_CASE(5)
+                    GJ_ROW_CASE(6) GJ_ROW_CASE(7) GJ_ROW_CASE(8) GJ_ROW_CASE(9) GJ_ROW_CASE(10) GJ_ROW_CASE(11)
+                    GJ_ROW_CASE(12) GJ_ROW_CASE(13) GJ_ROW_CASE(14) GJ_ROW_CASE(15) GJ_ROW_CASE(16) GJ_ROW_CASE(17)
+                    GJ_ROW_CASE(18) GJ_ROW_CASE(19) GJ_ROW_CASE(20) GJ_ROW_CASE(21) GJ_ROW_CASE(22) GJ_ROW_CASE(23)
+                    GJ_ROW_CASE(24) GJ_ROW_CASE(25) GJ_ROW_CASE(26) GJ_ROW_CASE(27) GJ_ROW_CASE(28) GJ_ROW_CASE(29)
+                    GJ_ROW_CASE(30) GJ_ROW_CASE(31)
 #undef GJ_ROW_CASE
-                default: break;
+                    default: break;
+                }
+                rowbuf[nb][g - gj][c] = r;
             }
-        }
-        if (c == jn) {   // publish the factors of column j + 1, the diagonal one minus one
+            if (c == jn || c == jn + 1) {   // columns jn, jn + 1: the factors, diagonal ones minus one
+                const int h = c - jn;
 #pragma unroll
-            for (int q = 0; q < GJ_RQ; ++q) colbuf[nb][g][q] = a[q];
-            if (qn >= 0) {
-                const float2 dj = rowbuf[nb][jn];
-                colbuf[nb][g][qn] = make_float2(dj.x - 1.f, dj.y);
+                for (int q = 0; q < GJ_RQ; ++q) colbuf[nb][g][q][h] = a[q];
+                if (g == gj + h) {
+                    const float2 dj = rowbuf[nb][h][c];
+                    colbuf[nb][g][qn][h] = make_float2(dj.x - 1.f, dj.y);
+                }
             }
         }
     }
-    // store through an opaque copy of A: the addresses are formed here, not
-    // kept live across the pivot loop from the loads above
     float *Ao;
     asm volatile("mov.b64 %0, %1;" : "=l"(Ao) : "l"(A));
 #pragma unroll
