@@ -237,6 +237,7 @@ def run_ours(args):
 FAR_FLOPS_PER_VALUE = 429.5
 FAR_WINST_PER_VALUE = 32.44
 SMS, FP32_LANES, SCHEDULERS = 152, 128, 4
+MATVEC_Z_TRAFFIC = 3.5527e9   # DRAM read + write per FP32 Z product, 21,024 unknowns (ncu)
 
 
 def roofline(last, n, peaks, fp32, n_tets):
@@ -305,8 +306,13 @@ def roofline(last, n, peaks, fp32, n_tets):
         tot_ms = last["k_matvec_ms"] + last.get("k_precond_ms", 0.0)
         tot_b = bytes_z + last.get("k_precond_bytes", 0.0)
         ach = tot_b / (tot_ms / 1e3) / 1e9
+        # DRAM bytes per Z product from one ncu capture of this workload
+        # (profiles/k_matvec_plasmonic_21k.md); other workloads: not captured
+        traffic = MATVEC_Z_TRAFFIC if (n == 21024 and fp32) else None
         out["k_matvec"] = {"bound": "hbm", "kernel": "k_matvec", "achieved": ach, "peak": peak, "unit": "GB/s",
-                           "frac": ach / peak, "traffic": None, "peak_source": src, "total_ms": tot_ms,
+                           "frac": ach / peak, "traffic": traffic, "traffic_unit": "bytes per Z product",
+                           "algorithmic_bytes_per_z_product": n * ld * zb + n * 2 * (8 if fp32 else 16) * 2,
+                           "peak_source": src, "total_ms": tot_ms,
                            "launches": last["k_matvec_n"], "precond_applications": last.get("k_precond_n", 0),
                            "z_products_gbs": bytes_z / (last["k_matvec_ms"] / 1e3) / 1e9}
     if not out:
