@@ -95,7 +95,7 @@ struct vie_ctx {
     DevBuf row, coef, wt, kap, ieps, frow, qs, perm, pol, orders, stab, ztab, rtab, ew;
     double z_extent = 0;
     // solve buffers
-    DevBuf Z, b, x, r, u, w, V, h, y, Minv, MinvH, amax, tcpack, status, acc, J, rt, cout, xs;
+    DevBuf Z, b, x, r, u, w, V, h, y, Minv, MinvH, amax, tcpack, tcpack2, status, acc, J, rt, cout, xs;
     std::vector<double> pinv;   // per domain block: 1 / (power-of-two scale of its FP16 inverse)
     size_t ld = 0;
     int64_t h2d = 0, d2h = 0;   // bytes copied by the current solve
@@ -106,12 +106,17 @@ struct vie_ctx {
     // own request and solve buffers and its own stream
     std::vector<std::unique_ptr<vie_ctx>> slots;
     cudaStream_t own_stream = nullptr;
-    cudaStream_t aux_stream = nullptr;   // second stream of the block inversion (look-ahead)
+    cudaStream_t aux_stream = nullptr;    // second stream of the block inversion (look-ahead)
+    cudaStream_t side_stream = nullptr;   // the smaller domain blocks' inversions, beside the largest
+    cudaEvent_t side_go = nullptr, side_done = nullptr;
     ~vie_ctx() {
         slots.clear();
         for (auto e : events) cudaEventDestroy(e);
+        if (side_go) cudaEventDestroy(side_go);
+        if (side_done) cudaEventDestroy(side_done);
         if (own_stream) cudaStreamDestroy(own_stream);
         if (aux_stream) cudaStreamDestroy(aux_stream);
+        if (side_stream) cudaStreamDestroy(side_stream);
     }
     cudaEvent_t event() {   // next event of the pool (nullptr when timing is off)
         if (!opt.timing) return nullptr;
@@ -644,16 +649,40 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
     }
     CK(ctx->Minv.ensure(sizeof(float) * 2 * std::max<size_t>(tot, 1)));
     CK(ctx->status.ensure(sizeof(int)));
-    size_t pk = 1;
-    for (int nb : H.blk_n) pk = std::max(pk, vie::gj_pack_bytes(nb));
-    CK(ctx->tcpack.ensure(pk));
+    // the largest block is inverted on st with the look-ahead stream; the others,
+    // one after another, on a side stream at the same time (their kernels fill
+    // the SMs that the largest block's pivot chain leaves idle)
+    size_t kbig = 0;
+    for (size_t k = 1; k < H.blk_n.size(); ++k)
+        if (H.blk_n[k] > H.blk_n[kbig]) kbig = k;
+    size_t pk2 = 1;
+    for (size_t k = 0; k < H.blk_n.size(); ++k)
+        if (k != kbig) pk2 = std::max(pk2, vie::gj_pack_bytes(H.blk_n[k]));
+    CK(ctx->tcpack.ensure(vie::gj_pack_bytes(H.blk_n[kbig])));
+    if (H.blk_n.size() > 1) CK(ctx->tcpack2.ensure(pk2));
     if (!ctx->aux_stream) CK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+    if (!ctx->side_stream) {
+        CK(cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->side_go, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->side_done, cudaEventDisableTiming));
+    }
     CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
+    const bool side = H.blk_n.size() > 1;
+    if (side) {
+        CK(cudaEventRecord(ctx->side_go, st));
+        CK(cudaStreamWaitEvent(ctx->side_stream, ctx->side_go, 0));
+    }
     for (size_t k = 0; k < H.blk_n.size(); ++k) {
+        const bool big = k == kbig;
+        cudaStream_t sk = big ? st : ctx->side_stream;
         float *B = ctx->Minv.as<float>() + 2 * moff[k];
-        CK((vie::copy_block<TZ, float>(ctx->Z.as<TZ>(), ctx->ld, H.blk_off[k], H.blk_n[k], B, mld[k], st)));
-        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), ctx->tcpack.p, st,
-                             ctx->aux_stream, kt));
+        CK((vie::copy_block<TZ, float>(ctx->Z.as<TZ>(), ctx->ld, H.blk_off[k], H.blk_n[k], B, mld[k], sk)));
+        CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), big ? ctx->tcpack.p : ctx->tcpack2.p, sk,
+                             big ? ctx->aux_stream : ctx->side_stream, kt));
+    }
+    if (side) {
+        CK(cudaEventRecord(ctx->side_done, ctx->side_stream));
+        CK(cudaStreamWaitEvent(st, ctx->side_done, 0));
     }
     // the applications read FP16 copies of the inverses, each scaled by a power
     // of two that brings its largest entry to [2^13, 2^14) (the scale is undone
@@ -821,8 +850,13 @@ int slot_footprint(vie_ctx *ctx, const vie_request *req, size_t *bytes) {
     const size_t N = (size_t)ctx->mesh->topo.N, ld = (N + 3) / 4 * 4;
     const bool fp64 = ctx->opt.precision == VIE_FP64;
     const size_t sz = fp64 ? 8 : 4;
-    size_t minv = 0;
-    for (int n : H.blk_n) minv += 8 * (((size_t)n + 3) / 4 * 4) * (size_t)n;
+    size_t minv = 0, pk1 = 0, pk2 = 0;   // block inverses; packing scratch of the largest block and of the others
+    for (int n : H.blk_n) {
+        minv += 8 * (((size_t)n + 3) / 4 * 4) * (size_t)n;
+        const size_t pk = vie::gj_pack_bytes(n);
+        if (pk > pk1) { pk2 = pk1; pk1 = pk; } else if (pk > pk2) pk2 = pk;
+    }
+    minv += pk1 + pk2;
     const size_t m = (size_t)std::max(2, ctx->opt.restart);
     const size_t vs = 4 * N;
     size_t b = 2 * sz * ld * N + minv + sz * vs * (m + 3) + 8 * vs * 4 + 64 * (size_t)ctx->mesh->nto[0];
@@ -1258,7 +1292,8 @@ void release_device_memory(vie_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->row, &ctx->coef, &ctx->wt, &ctx->kap, &ctx->ieps, &ctx->frow, &ctx->qs,
                       &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->rtab, &ctx->ew,
                       &ctx->Z, &ctx->b, &ctx->x, &ctx->r, &ctx->u, &ctx->w, &ctx->V, &ctx->h, &ctx->y,
-                      &ctx->Minv, &ctx->MinvH, &ctx->amax, &ctx->tcpack, &ctx->status, &ctx->acc, &ctx->J, &ctx->xs,
+                      &ctx->Minv, &ctx->MinvH, &ctx->amax, &ctx->tcpack, &ctx->tcpack2, &ctx->status, &ctx->acc,
+                      &ctx->J, &ctx->xs,
                       &ctx->rt, &ctx->cout};
     for (DevBuf *b : bufs) b->release();
 }

@@ -28,6 +28,10 @@
 #include "../../include/vie.h"
 #include "vie_internal.h"
 
+namespace vie {
+size_t gj_pack_bytes(int n);   // packing scratch of the block inversion (linalg.cu)
+}
+
 namespace {
 
 using clk = std::chrono::steady_clock;
@@ -84,6 +88,7 @@ size_t mesh_footprint(const vie_mesh &m, const vie_options &opt) {
     const size_t mres = (size_t)std::max(2, opt.restart);
     size_t b = 2 * sz * ld * N;                          // Z
     b += 8 * ld * N;                                     // block inverses (FP32 complex), bounded by N^2
+    b += 2 * vie::gj_pack_bytes((int)N);                 // packing scratch of the inversion (two blocks at once)
     b += sz * 4 * N * (mres + 3) + 8 * 4 * N * 4;        // Krylov basis and vectors, x, r, b, coefficients
     b += 2 * (nt * nt + nt * nf + nh * nt + nh * nf);    // near-image masks
     b += nt * 4096 + ((size_t)64 << 20);                 // per-element arrays, lists, tables, small buffers
