@@ -107,7 +107,7 @@ struct vie_ctx {
     std::vector<std::unique_ptr<vie_ctx>> slots;
     cudaStream_t own_stream = nullptr;
     cudaStream_t aux_stream = nullptr;    // second stream of the block inversion (look-ahead)
-    cudaStream_t side_stream = nullptr;   // the smaller domain blocks' inversions, beside the largest
+    cudaStream_t side_stream = nullptr;   // the smaller domain blocks' inversions and products, beside the largest
     cudaEvent_t side_go = nullptr, side_done = nullptr;
     ~vie_ctx() {
         slots.clear();
@@ -432,14 +432,29 @@ int fill(vie_ctx *ctx, const vie::DevMesh &m, const vie::DevReq &q, bool with_rh
     return VIE_OK;
 }
 
-// M^-1 applied block by block: out[blk] = Minv_d in[blk]
+// M^-1 applied block by block: out[blk] = Minv_d in[blk].  The largest block's
+// product runs on st, the smaller (latency-bound) ones beside it on the side
+// stream, joined before the application returns on st.
 template <typename TV>
 int precond_apply(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const std::vector<size_t> &mld,
                   const TV *in, TV *out, cudaStream_t st) {
+    size_t kbig = 0;
+    for (size_t k = 1; k < H.blk_n.size(); ++k)
+        if (H.blk_n[k] > H.blk_n[kbig]) kbig = k;
+    const bool side = H.blk_n.size() > 1 && ctx->side_stream;
+    if (side) {
+        CK(cudaEventRecord(ctx->side_go, st));
+        CK(cudaStreamWaitEvent(ctx->side_stream, ctx->side_go, 0));
+    }
     for (size_t k = 0; k < H.blk_off.size(); ++k) {
         const __half *Mi = ctx->MinvH.as<__half>() + 2 * moff[k];
         CK((vie::matvec<__half, TV, TV>(Mi, mld[k], H.blk_n[k], H.blk_n[k], in + 4 * (size_t)H.blk_off[k],
-                                         out + 4 * (size_t)H.blk_off[k], TV(ctx->pinv[k]), false, st)));
+                                         out + 4 * (size_t)H.blk_off[k], TV(ctx->pinv[k]), false,
+                                         side && k != kbig ? ctx->side_stream : st)));
+    }
+    if (side) {
+        CK(cudaEventRecord(ctx->side_done, ctx->side_stream));
+        CK(cudaStreamWaitEvent(st, ctx->side_done, 0));
     }
     return VIE_OK;
 }
