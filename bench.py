@@ -248,8 +248,8 @@ def roofline(last, n, peaks, fp32, n_tets):
     152 SMs x 4 schedulers x 1 warp instruction per clock x the maximum SM
     clock; the FP32 rate (FAR_FLOPS_PER_VALUE) is reported beside it.
     k_tc_update (tensor-core products of the block inversion of Eq. (6), FP16
-    operands, FP32 accumulation): K = 256 complex, ~128 flop per byte of the
-    updated block; algorithmic bytes = read and write of the updated block +
+    operands, FP32 accumulation): K = 512 complex, ~256 flop per byte of the
+    updated block (near the ridge); algorithmic bytes = read and write of the updated block +
     one read of the two packed FP16 operand panels, per launch; the roof is
     whichever of HBM and the FP16 tensor rate binds for those bytes and flops.
     k_matvec (GMRES Z products and block-inverse products): HBM-bound; bytes =

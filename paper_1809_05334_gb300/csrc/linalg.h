@@ -34,7 +34,7 @@ struct KernelTimer {
         flops.push_back(f);
     }
 };
-// the same inversion with 256-wide outer pivot blocks and the tcgen05
+// the same inversion with 512-wide outer pivot blocks and the tcgen05
 // products (FP16 operands with power-of-two scales, FP32 accumulation);
 // `pack` is device scratch of gj_pack_bytes(n) bytes (the packed operands and
 // their scale words), aux a second stream of the caller (look-ahead); the work

@@ -18,7 +18,7 @@
 // rows/columns around a pivot block, the pivot columns alone, or all rows.
 //
 // k_tc_update is persistent (one CTA per SM, tiles of 128 x 128 complex taken
-// round-robin) and warp-specialised:
+// round-robin in column-by-column order) and warp-specialised:
 //   warp 0   TMA producer of the A/B chunks (64 real K each) into a 3-stage ring
 //   warp 1   tensor-memory allocation (512 columns = two 128 x 256 FP32
 //            accumulators) and the MMA issuer (M=128, N=256, K=16)
