@@ -159,6 +159,24 @@ def test_ewald_independent_of_splitting():
         assert np.max(np.abs(alt - ref) / np.abs(ref)) < 1e-12
 
 
+def test_ewald_even_at_normal_incidence():
+    """k_par = 0: g_p(-d) = g_p(d) (the image lattice is symmetric and every
+    image carries the phase 1), the property the FP32 path's paired Floquet sum
+    G_00 + 2 sum over a half plane of G_pq cos(k_t.rho) rests on; the split
+    parameter that path uses there (1.5 sqrt(pi/ab)) gives the same sum.  At
+    oblique incidence g_p is not even."""
+    _, _, a, b, d = _pgf_case()
+    d = np.concatenate([d, d * [1.0, 1.0, 0.0]])   # include z = 0
+    g = PeriodicGreen(K0, 0.0, 0.0, a, b)
+    ref = g(d)
+    assert np.max(np.abs(g(-d) - ref) / np.abs(ref)) < 1e-12
+    alt = PeriodicGreen(K0, 0.0, 0.0, a, b, E=1.5 * g.E)(d)
+    assert np.max(np.abs(alt - ref) / np.abs(ref)) < 1e-12
+    kx, ky, _, _, _ = _pgf_case()
+    go = PeriodicGreen(K0, kx, ky, a, b)
+    assert np.max(np.abs(go(-d) - go(d)) / np.abs(go(d))) > 1e-3
+
+
 def test_ewald_vs_floquet_series():
     kx, ky, a, b, d = _pgf_case()
     d[:, 2] = np.sign(d[:, 2]) * np.linspace(25, 90, len(d))
