@@ -306,8 +306,8 @@ def roofline(last, n, peaks, fp32, n_tets):
         tot_ms = last["k_matvec_ms"] + last.get("k_precond_ms", 0.0)
         tot_b = bytes_z + last.get("k_precond_bytes", 0.0)
         ach = tot_b / (tot_ms / 1e3) / 1e9
-        # DRAM bytes per Z product from one ncu capture of this workload
-        # (profiles/k_matvec_plasmonic_21k.md); other workloads: not captured
+        # DRAM bytes per Z product from one ncu capture of this workload (its
+        # summary is under profiles/); other workloads: not captured
         traffic = MATVEC_Z_TRAFFIC if (n == 21024 and fp32) else None
         out["k_matvec"] = {"bound": "hbm", "kernel": "k_matvec", "achieved": ach, "peak": peak, "unit": "GB/s",
                            "frac": ach / peak, "traffic": traffic, "traffic_unit": "bytes per Z product",

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
 
-Tolerances (derived in the design doc from the arithmetic of each path):
+Tolerances (each derived from the arithmetic of its path):
   FP64 Faddeeva           |rel| <= 1e-13      (Weideman N=40 error ~3e-14)
   FP32 Faddeeva           |rel| <= 2e-6       (N=20 expansion in FP32)
   FP64 g_p                |rel| <= 1e-11      (Ewald truncation, rounding)
