@@ -294,6 +294,45 @@ def test_planted_surface_charge_sign_fails(monkeypatch):
     assert abs(bad["T"][1] - T0) > 0.2
 
 
+def _sphere_mean_field(out, cell, eps):
+    """Volume-weighted mean total field E = D/eps_r inside a lone sphere for
+    TE and TM, and the quasi-static field 3/(eps_r + 2) E^i(centre) (the SWG
+    function of face i is s a/(3V) (r - v_i) in its tetrahedron)."""
+    topo, prob = out["topo"], out["prob"]
+    P = topo["tet_verts"]
+    cent = P.mean(axis=1)
+    vol = topo["vol"]
+    coef = topo["sign"] * topo["area"] / (3.0 * vol[:, None])
+    epsi = np.conj(eps)                               # exp(j w t) internally
+    c0 = cent.T @ vol / vol.sum()
+    kin = prob.k_inc()
+    got, want = [], []
+    for p, pol in enumerate(prob.pol_vectors()):
+        D = np.einsum("ti,tid->td", out["x"][:, p][topo["basis"]] * coef, cent[:, None, :] - P)
+        got.append((D / epsi).T @ vol / vol.sum())
+        want.append(3.0 / (epsi + 2.0) * pol * np.exp(-1j * kin @ c0))
+    return np.array(got), np.array(want), vol.sum()
+
+
+def test_small_sphere_quasistatic_limit():
+    """A lone lossy dielectric sphere (eps_r = 4 + 1i, k0 r = 0.075, 1.3% of a
+    sparse lattice cell): the mean internal field is the quasi-static
+    3/(eps_r + 2) E^i, and the absorbed fraction of Eq. (7) is
+    k0 Im(eps_r) |3/(eps_r + 2)|^2 V / (a b) (V the mesh volume).  On this
+    coarse mesh (r/h = 2.4) the field is within 5% and the absorption within
+    12% (measured 2.6% and 6.8%)."""
+    a, r, h, lam = 120.0, 12.0, 5.0, 1000.0
+    k0 = 2 * np.pi / lam
+    eps = 4.0 + 1.0j
+    cell = cellgen.sphere_cell(a, r, h, "const:4.0,1.0")
+    out = solve_cell(cell, lam, 0.0, 0.0)
+    got, want, V = _sphere_mean_field(out, cell, eps)
+    rel = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+    assert np.all(rel < 0.05), rel
+    a_qs = k0 * eps.imag * 9.0 / abs(eps + 2.0) ** 2 * V / (a * a)
+    assert np.all(np.abs(out["A"][:, 0] / a_qs - 1.0) < 0.12), (out["A"][:, 0], a_qs)
+
+
 def test_reciprocity_single_material():
     """Z(k_par) = Z(-k_par)^T for one material, exact to rounding.
 
