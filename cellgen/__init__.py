@@ -30,7 +30,7 @@ __all__ = [
     "Cell", "grid_1d", "kuhn_mesh", "slab_cell", "layered_cell",
     "eps_ag_drude", "eps_active", "eps_buffer",
     "config_slab", "config_plasmonic", "config_plasmonic_sample", "config_sweep_geometry", "small_cells",
-    "sphere_cell",
+    "ball_cell",
 ]
 
 
@@ -358,23 +358,22 @@ def serving_cell(index, master_seed=4):
     return cell, target
 
 
-def sphere_cell(period, radius, h, material="const:4.0,1.0", snap=0.4):
-    """A lone sphere centred in a period x period cell, in vacuum: the
-    tetrahedra of a layered cell's sphere domain (grid spacing h around it,
-    surface nodes snapped radially), with the vacuum tetrahedra left out, so
-    its outer faces carry the body's boundary functions and none touches the
-    lateral faces."""
-    c = layered_cell(period, period, [(period, "const:1.0,0.0")],
-                     spheres=[(period / 2, period / 2, period / 2, radius, material)],
-                     h_coarse=2 * h, h_fine=h, jitter=0.0, snap=snap, name="sphere")
-    tets = c.tets[c.tet_domain == 1]
-    used = np.unique(tets)
-    remap = -np.ones(len(c.verts), dtype=np.int64)
-    remap[used] = np.arange(len(used))
-    return Cell(verts=c.verts[used], tets=remap[tets].astype(np.int32),
-                tet_domain=np.zeros(len(tets), dtype=np.int32), n_domains=1,
-                period_a=float(period), period_b=float(period), active_domain=0,
-                domain_names=(material,), name="sphere")
+def ball_cell(period, radius, n, material="const:4.0,1.0"):
+    """A lone sphere centred in a period x period cell, in vacuum, meshed as a
+    Kuhn-split n x n x n cube mapped radially onto the ball (each cube shell
+    max|p| = s goes to the sphere of radius s r): a smooth surface without the
+    slivers and steps of a snapped grid.  Its outer faces carry the body's
+    boundary functions and none touches the lateral faces."""
+    g = np.linspace(-1.0, 1.0, n + 1)
+    verts, tets = kuhn_mesh(g, g, g)
+    shell = np.abs(verts).max(axis=1)
+    norm = np.linalg.norm(verts, axis=1)
+    scale = np.where(norm > 0, shell / np.where(norm > 0, norm, 1.0), 0.0)
+    verts = verts * scale[:, None] * radius + 0.5 * np.array([period, period, period])
+    tets = _orient(verts, tets)
+    return Cell(verts=verts, tets=tets.astype(np.int32), tet_domain=np.zeros(len(tets), dtype=np.int32),
+                n_domains=1, period_a=float(period), period_b=float(period), active_domain=0,
+                domain_names=(material,), name="ball")
 
 
 def small_cells():
