@@ -15,6 +15,7 @@ import pytest
 from scipy.special import wofz
 
 import cellgen
+import golden_data
 from oracle import solve_cell
 from oracle.fill import Problem, assemble
 from oracle.greens import PeriodicGreen
@@ -164,10 +165,14 @@ def test_preconditioner_does_not_change_solution(solver64):
     finally:
         solver64.set_options(use_precond=1)
     # Eq. (8): relative difference of the current coefficients; both solves stop
-    # at relative residual 1e-10, so they agree to ~cond(Z) x 1e-10 (the paper
-    # reports < 12% at its own, looser, tolerance)
+    # at relative residual 1e-10, so they agree to ~cond(Z) x 1e-10; the paper
+    # reports < 12% per unknown at its own, looser, tolerance (golden fixture;
+    # checked here on the coefficients above 1e-3 of the largest)
     rel = np.linalg.norm(a["x"] - b["x"]) / np.linalg.norm(b["x"])
     assert rel < 1e-5
+    per_unknown = np.abs(a["x"] - b["x"]) / np.maximum(np.abs(b["x"]), 1e-300)
+    big = np.abs(b["x"]) > 1e-3 * np.max(np.abs(b["x"]))
+    assert np.all(per_unknown[big] < golden_data.load("paper_eq8_preconditioner.txt")["eq8_relative_error_max"])
     assert a["iterations"][0] <= b["iterations"][0]
 
 

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import cellgen
+import golden_data
 from closed_forms import tmm_rt
 from oracle import quadrature as qr
 from oracle.fill import Problem, assemble
@@ -332,6 +333,16 @@ def test_small_sphere_quasistatic_limit(mat, eps, tol_e, tol_a):
     assert np.all(rel < tol_e), rel
     a_qs = k0 * eps.imag * 9.0 / abs(eps + 2.0) ** 2 * V / (a * a)
     assert np.all(np.abs(out["A"][:, 0] / a_qs - 1.0) < tol_a), (out["A"][:, 0], a_qs)
+
+
+def test_golden_fixture_of_the_paper():
+    """The fixture of the paper's preconditioner experiment (Sec. 3, Fig. 2-3,
+    Eq. (8)) reads as the printed values; the GPU parity test checks the
+    Eq. (8) bound against it."""
+    g = golden_data.load("paper_eq8_preconditioner.txt")
+    assert g["eq8_relative_error_max"] == 0.12
+    assert (g["cube_side_nm"], g["period_nm"], g["wavelength_nm"]) == (20.0, 40.0, 400.0)
+    assert (g["spacer_thickness_nm"], g["active_thickness_nm"]) == (20.0, 60.0)
 
 
 def test_reciprocity_single_material():
