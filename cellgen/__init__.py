@@ -164,7 +164,7 @@ def _orient(verts, tets):
 
 def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=None,
                  h_z=None, jitter=0.1, seed=0, snap=0.4, name="", active_domain=None,
-                 lateral_fine=True):
+                 lateral_fine=True, particles="snap"):
     """Layered unit cell with optional spheres.
 
     layers:  list of (thickness_nm, material_name) from bottom (z=0) to top.
@@ -173,18 +173,43 @@ def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=N
     The grid is graded to spacing h_fine inside the bounding box of each sphere
     (plus half a fine cell), h_coarse elsewhere laterally, h_z (default
     h_coarse) vertically outside fine zones.
+    particles: "snap" moves the grid nodes near each sphere surface radially
+             onto it; "ball" maps the grid inside a cube of half-width r onto
+             the ball and blends a shell of two fine cells out to the
+             surrounding grid (a smooth particle surface without slivers or
+             steps, conformal with the layers; the box of half-width r + 2
+             h_fine must lie inside one layer and inside the cell).
     """
+    if particles not in ("snap", "ball"):
+        raise ValueError("particles must be 'snap' or 'ball'")
     rng = np.random.default_rng(seed)
     zb = np.concatenate([[0.0], np.cumsum([t for t, _ in layers])])
     fine_x, fine_y, fine_z = [], [], []
+    brk_x, brk_y, brk_z = [], [], list(zb[1:-1])
+    boxes = []   # "ball" particles: (centre, r, half-width of the blended box)
     for cx, cy, cz, r, _ in spheres:
+        if particles == "ball":
+            hb = h_fine or h_coarse
+            L = r + 2.0 * hb
+            if not (L < cx < period_a - L and L < cy < period_b - L):
+                raise ValueError("a ball particle's box must lie inside the cell")
+            if not any(z0 < cz - L and cz + L < z1 for z0, z1 in zip(zb[:-1], zb[1:])):
+                raise ValueError("a ball particle's box must lie inside one layer")
+            boxes.append((np.array([cx, cy, cz]), float(r), float(L)))
+            fine_x.append((cx - L, cx + L))
+            fine_y.append((cy - L, cy + L))
+            fine_z.append((cz - L, cz + L))
+            brk_x += [cx - L, cx - r, cx + r, cx + L]
+            brk_y += [cy - L, cy - r, cy + r, cy + L]
+            brk_z += [cz - L, cz - r, cz + r, cz + L]
+            continue
         pad = 0.5 * (h_fine or h_coarse)
         fine_x.append((cx - r - pad, cx + r + pad))
         fine_y.append((cy - r - pad, cy + r + pad))
         fine_z.append((cz - r - pad, cz + r + pad))
-    xs = grid_1d(0.0, period_a, (), fine_x if lateral_fine else (), h_fine, h_coarse)
-    ys = grid_1d(0.0, period_b, (), fine_y if lateral_fine else (), h_fine, h_coarse)
-    zs = grid_1d(0.0, zb[-1], zb[1:-1], fine_z, h_fine, h_z or h_coarse)
+    xs = grid_1d(0.0, period_a, brk_x, fine_x if (lateral_fine or boxes) else (), h_fine, h_coarse)
+    ys = grid_1d(0.0, period_b, brk_y, fine_y if (lateral_fine or boxes) else (), h_fine, h_coarse)
+    zs = grid_1d(0.0, zb[-1], brk_z, fine_z, h_fine, h_z or h_coarse)
     verts, tets = kuhn_mesh(xs, ys, zs)
     v0 = verts.copy()
     nxv, nyv, nzv = len(xs), len(ys), len(zs)
@@ -201,7 +226,22 @@ def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=N
     hloc = np.minimum(np.minimum(_loc(xs, ii), _loc(ys, jj)), _loc(zs, kk))
 
     snapped = np.zeros(len(verts), dtype=bool)
-    for cx, cy, cz, r, _ in spheres:
+    inbox = np.zeros(len(verts), dtype=bool)
+    for c, r, L in boxes:
+        # inner cube (max-norm <= r) onto the ball of radius r; the shell out to
+        # the box blends the ball surface (t = 0) into the grid (t = 1)
+        d = verts - c
+        sinf = np.abs(d).max(axis=1)
+        nrm = np.linalg.norm(d, axis=1)
+        sel = sinf <= L * (1.0 + 1e-9)
+        unit = np.where(nrm[:, None] > 0, d / np.where(nrm > 0, nrm, 1.0)[:, None], 0.0)
+        inner = sel & (sinf <= r * (1.0 + 1e-9))
+        verts[inner] = c + unit[inner] * sinf[inner, None]
+        shell = sel & ~inner
+        t = ((sinf - r) / (L - r))[shell, None]
+        verts[shell] = (1.0 - t) * (c + unit[shell] * r) + t * verts[shell]
+        inbox |= sel
+    for cx, cy, cz, r, _ in (spheres if particles == "snap" else ()):
         d = verts - np.array([cx, cy, cz])
         dist = np.linalg.norm(d, axis=1)
         near = (np.abs(dist - r) < snap * hloc) & ~lateral & ~on_plane & (dist > 0)
@@ -209,7 +249,7 @@ def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=N
         snapped |= near
     # seeded jitter: free interior nodes in 3D, interface/top/bottom nodes in-plane
     if jitter > 0:
-        free = ~lateral & ~snapped
+        free = ~lateral & ~snapped & ~inbox
         dj = rng.uniform(-jitter, jitter, size=verts.shape) * hloc[:, None]
         dj[on_plane, 2] = 0.0
         # keep jittered nodes clear of sphere surfaces (no accidental straddling)
@@ -227,6 +267,9 @@ def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=N
         if not bad.any():
             break
         nodes = np.unique(tets[bad])
+        nodes = nodes[~inbox[nodes]]   # the ball mapping stays
+        if not len(nodes):
+            break
         verts[nodes] = v0[nodes]
     vol = _signed_volumes(verts, tets)
     assert (vol > 0).all(), "mesh generation produced an inverted tetrahedron"
@@ -235,8 +278,12 @@ def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=N
     dom = np.searchsorted(zb, cent[:, 2], side="right") - 1
     dom = np.clip(dom, 0, len(layers) - 1).astype(np.int32)
     names = [m for _, m in layers]
+    cent0 = v0[tets].mean(axis=1)
     for s, (cx, cy, cz, r, m) in enumerate(spheres):
-        inside = np.linalg.norm(cent - np.array([cx, cy, cz]), axis=1) < r
+        if particles == "ball":   # the tetrahedra of the mapped inner cube
+            inside = np.abs(cent0 - np.array([cx, cy, cz])).max(axis=1) < r
+        else:
+            inside = np.linalg.norm(cent - np.array([cx, cy, cz]), axis=1) < r
         dom[inside] = len(layers) + s
         names.append(m)
     if active_domain is None:

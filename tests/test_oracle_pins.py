@@ -247,6 +247,32 @@ def test_swg_topology_counts_and_flux():
             assert abs(topo["area"][tm, im] - topo["area"][tp, ip]) < 1e-9
 
 
+def test_ball_particles_conformal_and_smooth():
+    """particles="ball": the particle is a mapped cube whose surface nodes lie on
+    the sphere, every tetrahedron is positive, and the mesh stays conformal with
+    the layers (the only unpaired faces are the cell's top and bottom)."""
+    r, c0 = 15.0, np.array([60.0, 60.0, 80.0])
+    cell = cellgen.layered_cell(120.0, 120.0, [(40.0, "buffer"), (80.0, "active")],
+                                spheres=[(60.0, 60.0, 80.0, r, "ag")], h_coarse=30.0, h_fine=6.0,
+                                h_z=20.0, jitter=0.1, seed=3, particles="ball")
+    v = cell.verts[cell.tets]
+    vol = np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), v[:, 3] - v[:, 0]) / 6.0
+    assert np.all(vol > 0)
+    sph = cell.tet_domain == 2
+    inside = np.unique(cell.tets[sph])
+    outside = np.unique(cell.tets[~sph])
+    surface = np.intersect1d(inside, outside)
+    rad = np.linalg.norm(cell.verts - c0, axis=1)
+    assert np.all(rad[inside] <= r * (1 + 1e-12))
+    assert np.all(np.abs(rad[surface] - r) < 1e-9 * r)
+    assert 0.9 < vol[sph].sum() / (4.0 / 3.0 * np.pi * r ** 3) < 1.0
+    topo = build_topology(cell)
+    half = topo["kind"] == KIND_HALF
+    P = topo["tet_verts"]
+    zf = np.array([P[t, [j for j in range(4) if j != i], 2] for t, i in zip(topo["tp"][half], topo["ip"][half])])
+    assert np.all((np.abs(zf) < 1e-9).all(axis=1) | (np.abs(zf - 120.0) < 1e-9).all(axis=1))
+
+
 # --------------------------------------------------------------------------- physics pins
 @pytest.fixture(scope="module")
 def slab_runs():
