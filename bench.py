@@ -35,6 +35,10 @@ WORKLOADS = {
     "plasmonic": ("config_plasmonic",
                   "plasmonic cell 200 nm period, Ag sphere r=20 nm in 100 nm active over 40 nm buffer, "
                   "~21k unknowns, lambda=500 nm, theta=0, TE+TM"),
+    # the same cell with the Ag sphere meshed as a mapped cube (smooth particle surface)
+    "plasmonic_ball": ("config_plasmonic_ball",
+                       "plasmonic cell 200 nm period, Ag sphere r=20 nm (mapped-cube mesh) in 100 nm active over "
+                       "40 nm buffer, ~35.6k unknowns, lambda=500 nm, theta=0, TE+TM"),
     # the same geometry at the sweep density (~8.9k unknowns): a smaller case for profiling
     "sweep_cell": ("config_sweep_geometry",
                    "plasmonic cell 200 nm period at sweep density (~8.9k unknowns), lambda=500 nm, theta=0, TE+TM"),
@@ -481,7 +485,7 @@ def cpu_baseline(args):
     import cellgen
     from oracle import solve_cell
     sample = cellgen.config_plasmonic_sample()
-    full = cellgen.config_plasmonic()
+    full = _cell(args.workload)                          # scaled to the workload being timed
     t0 = time.perf_counter()
     solve_cell(sample, LAM, THETA, PHI)
     dt = time.perf_counter() - t0
@@ -499,7 +503,7 @@ def run_reference(args):
     import cellgen
     from oracle import solve_cell
     sample = cellgen.config_plasmonic_sample()
-    full = cellgen.config_plasmonic()
+    full = _cell(args.workload)                          # scaled to the workload being timed
     scale = (full.n_tets / sample.n_tets) ** 2
     for _ in range(args.warmup):
         solve_cell(sample, LAM, THETA, PHI)

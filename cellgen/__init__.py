@@ -30,7 +30,7 @@ __all__ = [
     "Cell", "grid_1d", "kuhn_mesh", "slab_cell", "layered_cell",
     "eps_ag_drude", "eps_active", "eps_buffer",
     "config_slab", "config_plasmonic", "config_plasmonic_sample", "config_sweep_geometry", "small_cells",
-    "ball_cell",
+    "ball_cell", "config_plasmonic_ball",
 ]
 
 
@@ -324,13 +324,21 @@ def config_slab():
     return slab_cell(6, 6, 2, 200.0, 200.0, 40.0, (4.0, 0.5))
 
 
-def config_plasmonic(seed=2, h_coarse=28.0, h_fine=9.5, h_z=25.0):
+def config_plasmonic(seed=2, h_coarse=28.0, h_fine=9.5, h_z=25.0, particles="snap"):
     """Plasmonic cell: period 200 nm, Ag sphere r=20 nm centred in a 100 nm active
-    layer over a 40 nm buffer (three material domains)."""
+    layer over a 40 nm buffer (three material domains).  particles="ball" meshes
+    the sphere as a mapped cube (see layered_cell)."""
     return layered_cell(200.0, 200.0, [(40.0, "buffer"), (100.0, "active")],
                         spheres=[(100.0, 100.0, 90.0, 20.0, "ag")],
                         h_coarse=h_coarse, h_fine=h_fine, h_z=h_z, jitter=0.1, seed=seed,
-                        name="plasmonic_200nm_r20")
+                        name="plasmonic_200nm_r20" + ("_ball" if particles == "ball" else ""),
+                        particles=particles)
+
+
+def config_plasmonic_ball(seed=2):
+    """The plasmonic cell with its Ag sphere meshed as a mapped cube (smooth,
+    sliver-free particle surface)."""
+    return config_plasmonic(seed=seed, particles="ball")
 
 
 def config_plasmonic_sample(seed=2):

@@ -273,6 +273,17 @@ def test_ball_particles_conformal_and_smooth():
     assert np.all((np.abs(zf) < 1e-9).all(axis=1) | (np.abs(zf - 120.0) < 1e-9).all(axis=1))
 
 
+def test_plasmonic_ball_workload_builds():
+    """The bench's ball-particle variant of the plasmonic cell: valid mesh,
+    three domains, the Ag sphere a 750-tetrahedron mapped cube."""
+    cell = cellgen.config_plasmonic_ball()
+    v = cell.verts[cell.tets]
+    vol = np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), v[:, 3] - v[:, 0]) / 6.0
+    assert np.all(vol > 0) and cell.n_domains == 3
+    assert int(np.sum(cell.tet_domain == 2)) == 750
+    assert build_topology(cell)["n"] == 35550
+
+
 # --------------------------------------------------------------------------- physics pins
 @pytest.fixture(scope="module")
 def slab_runs():
