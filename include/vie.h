@@ -155,7 +155,11 @@ int32_t vie_num_unknowns(const vie_ctx *ctx);
    Ewald-summed g_p (Eq. (3)-(4)), factor the domain blocks (Eq. (6)), run
    GMRES, compute Eq. (7) absorption per domain plus R and T.
    stream: a cudaStream_t (may be NULL for the legacy default stream); the call
-   returns after the work on it has finished. */
+   returns after the work on it has finished.  The block inversion and the
+   preconditioner applications also use two non-blocking streams that the
+   context owns (look-ahead, and the smaller domain blocks beside the
+   largest); their work is ordered after, and joined back into, `stream` by
+   events, so nothing of the solve is left running when the call returns. */
 int vie_solve(vie_ctx *ctx, const vie_request *req, vie_result *res, void *stream);
 
 /* A batch of independent solves on the current mesh (a wavelength x angle
