@@ -30,7 +30,7 @@ __all__ = [
     "Cell", "grid_1d", "kuhn_mesh", "slab_cell", "layered_cell",
     "eps_ag_drude", "eps_active", "eps_buffer",
     "config_slab", "config_plasmonic", "config_plasmonic_sample", "config_sweep_geometry", "small_cells",
-    "ball_cell", "config_plasmonic_ball",
+    "ball_cell", "config_plasmonic_ball", "cube_cell", "paper_cube_cell", "two_layer_cell",
 ]
 
 
@@ -429,6 +429,58 @@ def ball_cell(period, radius, n, material="const:4.0,1.0"):
     return Cell(verts=verts, tets=tets.astype(np.int32), tet_domain=np.zeros(len(tets), dtype=np.int32),
                 n_domains=1, period_a=float(period), period_b=float(period), active_domain=0,
                 domain_names=(material,), name="ball")
+
+
+def cube_cell(period, d_spacer, d_active, side, h_fine, h_coarse=None, particle=True, name=""):
+    """The unit cell of the paper's Sec. 3 experiments (Fig. 1): a spacer layer
+    (z in [0, D1], the synthetic "buffer" material) under the active layer
+    (z in [D1, D1 + D2]) with one metal cube of side W centred in the active
+    layer and in the period x period cell.  The tensor grid has planes on the
+    layer interface and on the six cube faces (spacing <= h_fine across the
+    cube, <= h_coarse elsewhere), so the cube is exactly W^3; no jitter.
+    Domains: 0 spacer, 1 active, 2 the cube.  particle=False keeps the same
+    mesh and domains but fills the cube with the active material (the cell
+    "without NPs" of the paper's enhancement: A(with) / A(without), both
+    integrated over the active material only)."""
+    c, half = 0.5 * period, 0.5 * side
+    zc = d_spacer + 0.5 * d_active
+    if not (half < c and d_spacer < zc - half and zc + half < d_spacer + d_active):
+        raise ValueError("the cube must lie inside the active layer and the cell")
+    hc = h_coarse or h_fine
+    xs = grid_1d(0.0, period, (c - half, c + half), [(c - half, c + half)], h_fine, hc)
+    zs = grid_1d(0.0, d_spacer + d_active, (d_spacer, zc - half, zc + half), [(zc - half, zc + half)], h_fine, hc)
+    verts, tets = kuhn_mesh(xs, xs, zs)
+    cent = verts[tets].mean(axis=1)
+    dom = (cent[:, 2] > d_spacer).astype(np.int32)
+    inside = ((np.abs(cent[:, 0] - c) < half) & (np.abs(cent[:, 1] - c) < half) & (np.abs(cent[:, 2] - zc) < half))
+    dom[inside] = 2
+    names = ("buffer", "active", "ag" if particle else "active")
+    return Cell(verts=verts, tets=tets.astype(np.int32), tet_domain=dom, n_domains=3, period_a=float(period),
+                period_b=float(period), active_domain=1, domain_names=names,
+                name=name or "cube_W%g_a%g%s" % (side, period, "" if particle else "_noNP"))
+
+
+def paper_cube_cell(h_fine=5.0, h_coarse=10.0, particle=True, geometry=None):
+    """The paper's preconditioner experiment (Sec. 3, Fig. 2-3): Ag cubes W = 20 nm
+    on a square lattice a = b = 40 nm, 20 nm spacer, 60 nm active layer.
+    `geometry` (a dict with cube_side_nm, period_nm, spacer_thickness_nm,
+    active_thickness_nm) overrides those values."""
+    g = geometry or {"cube_side_nm": 20.0, "period_nm": 40.0, "spacer_thickness_nm": 20.0,
+                     "active_thickness_nm": 60.0}
+    return cube_cell(g["period_nm"], g["spacer_thickness_nm"], g["active_thickness_nm"], g["cube_side_nm"],
+                     h_fine, h_coarse, particle=particle, name="paper_fig2_cube")
+
+
+def two_layer_cell(period, d_buffer, d_active, nxy, h_z, eps_buffer=None, eps_active=None):
+    """A laterally homogeneous two-layer stack (buffer below, active on top, no
+    particles) on a uniform nxy x nxy lateral grid: a case with a closed form
+    (transfer matrix).  eps_* = None uses the synthetic dispersive models,
+    else a constant complex permittivity."""
+    def mat(e, named):
+        return named if e is None else "const:%r,%r" % (float(np.real(e)), float(np.imag(e)))
+    return layered_cell(period, period, [(d_buffer, mat(eps_buffer, "buffer")), (d_active, mat(eps_active, "active"))],
+                        h_coarse=period / nxy, h_z=h_z, jitter=0.0, seed=0, active_domain=1,
+                        name="two_layer_%dx%d_hz%g" % (nxy, nxy, h_z))
 
 
 def small_cells():

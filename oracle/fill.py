@@ -53,6 +53,14 @@ SURFACE_CHARGE_SIGN = 1.0
 NEAR_IMAGES = [(m, n) for m in (-1, 0, 1) for n in (-1, 0, 1)]
 
 
+def surface_charge(kappa_plus, kappa_minus, half):
+    """Surface part of q_n = div'(kappa f_n) on face n, per unit normal flux:
+    kappa(T-) - kappa(T+), where kappa(T-) = 0 for a half function (the outside
+    of the body is vacuum).  Charge conservation fixes the sign; the paper's
+    Eq. (2) prints the kappa-gradient terms with the opposite one."""
+    return SURFACE_CHARGE_SIGN * (np.where(half, 0.0, kappa_minus) - kappa_plus)
+
+
 class Problem:
     """One (lambda, theta, phi) incidence on a meshed cell, with per-domain eps (physics sign)."""
 
@@ -156,9 +164,12 @@ def tet_tet_moments(prob, chunk=48):
     B = np.zeros((nt, nt, 3), np.complex128)
     C = np.zeros((nt, nt), np.complex128)
     near = _near_images(cent, rad, cent, rad, topo["a"], topo["b"])
+    # all pairs by the degree-2 product rule; near images with their static part
+    # removed (the near pass below recomputes those pairs and adds it back), so
+    # that no term is evaluated at coincident points
     for i0 in range(0, nt, chunk):
         sl = slice(i0, min(nt, i0 + chunk))
-        s, a_, b_, c_ = _pair_moments(green, X2[sl], W2[sl], cent[sl], X2, W2, cent)
+        s, a_, b_, c_ = _pair_moments(green, X2[sl], W2[sl], cent[sl], X2, W2, cent, sub=_sub_mask(green, near[sl]))
         S[sl], A[sl], B[sl], C[sl] = s, a_, b_, c_
     # near pairs: closed-form static part + remainder
     ti, tj = np.nonzero(near.any(axis=-1))
@@ -245,10 +256,11 @@ def _scalar_moments(prob, X_el, X_cent, X_rad, X_kind, Y_el, Y_cent, Y_rad, Y_ki
     out = np.zeros((nx, ny), np.complex128)
     if nx == 0 or ny == 0:
         return out
-    for i0 in range(0, nx, chunk):
-        sl = slice(i0, min(nx, i0 + chunk))
-        out[sl] = _pair_moments(green, X2[sl], WX[sl], X_cent[sl], Y2, WY, Y_cent, vector=False)
     near = _near_images(X_cent, X_rad, Y_cent, Y_rad, topo["a"], topo["b"])
+    for i0 in range(0, nx, chunk):   # static part of near images removed, as in tet_tet_moments
+        sl = slice(i0, min(nx, i0 + chunk))
+        out[sl] = _pair_moments(green, X2[sl], WX[sl], X_cent[sl], Y2, WY, Y_cent, sub=_sub_mask(green, near[sl]),
+                                vector=False)
     I, J = np.nonzero(near.any(axis=-1))
     b5, w5 = rules5[X_kind]
     X5, W5 = qr.map_points(b5, X_el), mX[:, None] * w5
@@ -335,8 +347,8 @@ def assemble(prob, with_rhs=True):
     if len(cf):
         kind = topo["kind"][cf]
         kp = prob.kappa[dom[topo["tp"][cf]]]
-        km = np.where(kind == KIND_HALF, 0.0, prob.kappa[dom[np.maximum(topo["tm"][cf], 0)]])
-        qs = SURFACE_CHARGE_SIGN * (km - kp)              # surface charge of basis n on its face
+        km = prob.kappa[dom[np.maximum(topo["tm"][cf], 0)]]
+        qs = surface_charge(kp, km, kind == KIND_HALF)    # surface charge of basis n on its face
         ts = np.where(kind == KIND_HALF, -1.0, 0.0)       # surface part of div f_m
         I_tf = _scalar_moments(prob, P, cent, rad, "tet", F, cent_f, rad_f, "tri")
         val = (wT * div)[:, :, None] * (qs[None, :] * I_tf)[:, None, :]
@@ -350,6 +362,8 @@ def assemble(prob, with_rhs=True):
             val = ts[hf][:, None] * qs[None, :] * I_ff
             scatter(np.broadcast_to(cf[hf][:, None], val.shape), np.broadcast_to(cf[None, :], val.shape), val)
 
+    # every singular term was integrated in closed form: a non-finite entry is a bug
+    assert np.all(np.isfinite(Z)), "non-finite impedance matrix entry"
     if not with_rhs:
         return Z, None
     return Z, rhs(prob)

@@ -116,11 +116,14 @@ class PeriodicGreen:
         ph = np.exp(1j * (self.kx * m * self.a + self.ky * n * self.b))
         # real k: erfcx(RE - jb) = conj(erfcx(RE + jb)), so the bracket is 2 Re erfcx(RE + jb);
         # terms with R E beyond the cut are below exp(-X_CUT^2) and are skipped
+        # R = 0 (coincident points) is singular: such a term must be replaced by
+        # its regular part (subtract mask); NaN marks it if it is not
         val = np.zeros(R.shape, dtype=np.float64)
-        live = R * E <= X_CUT + 0.5
+        live = (R * E <= X_CUT + 0.5) & (R > 0)
         if np.any(live):
             Rl = R[live]
             val[live] = np.exp(bb * bb - (Rl * E) ** 2) * np.real(erfcx(Rl * E + 1j * bb)) / (4 * np.pi * Rl)
+        val[R == 0] = np.nan
         return ph * val, R, ph
 
     def spatial_regular(self, d, m, n):
@@ -176,14 +179,11 @@ class PeriodicGreen:
     def _eval(self, d, subtract=None):
         acc = self.spectral(d)
         for idx, (m, n) in enumerate(self.images):
-            if subtract is not None:
-                sub = subtract[..., idx]
-                if np.any(sub):
-                    reg = self.spatial_regular(d, m, n)
-                    full, _, _ = self.spatial_terms(d, m, n)
-                    acc += np.where(sub, reg, full)
-                    continue
             full, _, _ = self.spatial_terms(d, m, n)
+            if subtract is not None:
+                sub = np.broadcast_to(subtract[..., idx], full.shape)
+                if np.any(sub):   # flagged entries: the regular part only
+                    full[sub] = self.spatial_regular(d[sub], m, n)
             acc += full
         return acc
 

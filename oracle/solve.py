@@ -84,16 +84,18 @@ def gmres(Z, b, M=None, tol=1e-8, restart=100, maxiter=2000):
             H[k + 1, k] = np.linalg.norm(w)
             if H[k + 1, k] != 0:
                 V[:, k + 1] = w / H[k + 1, k]
+            # Givens rotations: G_j = [[conj(c_j), conj(s_j)], [-s_j, c_j]] (unitary),
+            # c = h_kk / den, s = h_(k+1)k / den zero the subdiagonal of column k
             for j in range(k):                     # apply previous rotations
-                t = cs[j] * H[j, k] + sn[j] * H[j + 1, k]
-                H[j + 1, k] = -np.conj(sn[j]) * H[j, k] + np.conj(cs[j]) * H[j + 1, k]
+                t = np.conj(cs[j]) * H[j, k] + np.conj(sn[j]) * H[j + 1, k]
+                H[j + 1, k] = -sn[j] * H[j, k] + cs[j] * H[j + 1, k]
                 H[j, k] = t
             den = np.hypot(abs(H[k, k]), abs(H[k + 1, k]))
             cs[k] = H[k, k] / den if den else 1.0
             sn[k] = H[k + 1, k] / den if den else 0.0
             H[k, k] = den
             H[k + 1, k] = 0.0
-            g[k + 1] = -np.conj(sn[k]) * g[k]
+            g[k + 1] = -sn[k] * g[k]
             g[k] = np.conj(cs[k]) * g[k]
             it += 1
             k_used = k + 1

@@ -1,7 +1,5 @@
 import os
 import sys
-import warnings
-
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -13,4 +11,3 @@ for p in (ROOT, os.path.join(ROOT, "tests")):
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built extension")
     config.addinivalue_line("markers", "slow: long-running CPU test")
-    warnings.filterwarnings("ignore", category=RuntimeWarning)

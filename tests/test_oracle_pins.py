@@ -5,8 +5,12 @@ share code with: polynomial exactness of the quadrature rules, brute-force
 Duffy cubature of the 1/R potentials, independence of the Ewald sum from its
 splitting parameter plus agreement with the plain Floquet and windowed lattice
 sums of Eq. (3), transfer-matrix reflectance/transmittance/absorption of a
-homogeneous slab, reciprocity Z(k) = Z(-k)^T, the energy balance, and a planted
-sign error that must fail the slab test.
+homogeneous slab and of a two-layer stack (whose interface carries the
+two-material surface charge of Eq. (2)), reciprocity Z(k) = Z(-k)^T, the
+energy balance, the domain-block preconditioner of Eq. (6) and the restarted
+GMRES against dense LU, the paper's preconditioner experiment (Sec. 3,
+Fig. 2-3, Eq. (8)) on its own geometry, and planted errors (surface-charge
+signs, a dropped interface charge) that must fail.
 """
 import math
 
@@ -22,6 +26,7 @@ from oracle.greens import PeriodicGreen, spectral_direct, windowed_direct
 from oracle.potentials import tet_integrals, tri_integrals
 from oracle.topology import build_topology, KIND_HALF, KIND_PERIODIC
 from oracle import solve_cell
+from oracle.solve import block_preconditioner, gmres, unknown_domains
 
 
 # --------------------------------------------------------------------------- quadrature
@@ -372,16 +377,6 @@ def test_small_sphere_quasistatic_limit(mat, eps, tol_e, tol_a):
     assert np.all(np.abs(out["A"][:, 0] / a_qs - 1.0) < tol_a), (out["A"][:, 0], a_qs)
 
 
-def test_golden_fixture_of_the_paper():
-    """The fixture of the paper's preconditioner experiment (Sec. 3, Fig. 2-3,
-    Eq. (8)) reads as the printed values; the GPU parity test checks the
-    Eq. (8) bound against it."""
-    g = golden_data.load("paper_eq8_preconditioner.txt")
-    assert g["eq8_relative_error_max"] == 0.12
-    assert (g["cube_side_nm"], g["period_nm"], g["wavelength_nm"]) == (20.0, 40.0, 400.0)
-    assert (g["spacer_thickness_nm"], g["active_thickness_nm"]) == (20.0, 60.0)
-
-
 def test_reciprocity_single_material():
     """Z(k_par) = Z(-k_par)^T for one material, exact to rounding.
 
@@ -396,3 +391,168 @@ def test_reciprocity_single_material():
     scale = np.max(np.abs(Zp))
     assert np.max(np.abs(Zp - Zm.T)) < 1e-12 * scale
     assert np.max(np.abs(Zp - Zp.T)) > 1e-2 * scale          # oblique: not symmetric by itself
+
+
+# --------------------------------------------------------------------------- two-layer stack
+# The stack of the plasmonic cell without its particle: 100 nm active
+# (3.9+0.6i) over 40 nm buffer (2.4+0.05i), lit from the active side.  On the
+# interface between them kappa jumps between two non-vacuum values, so the
+# surface-charge terms of Eq. (2) there are (kappa- - kappa+) with both kappas
+# non-zero: a face type no single-material case contains.  At normal incidence
+# D is tangential to the interface (no interface charge); at oblique TM it has
+# a normal component and the interface charge acts.
+EPS_ACT, EPS_BUF = 3.9 + 0.6j, 2.4 + 0.05j
+TWO_LAYER = {"coarse": (2, 20.0), "fine": (2, 10.0)}   # lateral cells per 100 nm period, vertical spacing
+
+
+def _two_layer(level):
+    nxy, hz = TWO_LAYER[level]
+    return cellgen.two_layer_cell(100.0, 40.0, 100.0, nxy, hz, eps_buffer=EPS_BUF, eps_active=EPS_ACT)
+
+
+@pytest.fixture(scope="module")
+def two_layer_runs():
+    return {(lv, th): solve_cell(_two_layer(lv), 500.0, th, 0.0, keep_matrix=(lv == "coarse" and th > 0))
+            for lv in TWO_LAYER for th in (0.0, np.pi / 4)}
+
+
+def _stack_err(run, th):
+    """|dR|, |dT|, |dA| (A summed over both layers) against the transfer matrix, TE and TM."""
+    out = []
+    for p, pol in enumerate(("TE", "TM")):
+        R0, T0, A0 = tmm_rt([EPS_ACT, EPS_BUF], [100.0, 40.0], 500.0, th, pol)
+        out.append((abs(run["R"][p] - R0), abs(run["T"][p] - T0), abs(run["A"][p].sum() - A0)))
+    return np.array(out)
+
+
+def test_two_layer_stack_normal_incidence(two_layer_runs):
+    """Normal incidence: R 0.03118, T 0.64965, A 0.31916 (transfer matrix);
+    the error falls under 2x vertical refinement."""
+    R0, T0, A0 = tmm_rt([EPS_ACT, EPS_BUF], [100.0, 40.0], 500.0, 0.0, "TE")
+    assert abs(R0 - 0.03118) < 1e-5 and abs(T0 - 0.64965) < 1e-5 and abs(A0 - 0.31916) < 1e-5
+    coarse = _stack_err(two_layer_runs[("coarse", 0.0)], 0.0)
+    fine = _stack_err(two_layer_runs[("fine", 0.0)], 0.0)
+    assert np.all(fine[:, 2] < 0.003) and np.all(fine[:, :2] < 0.002), fine
+    assert np.all(fine < coarse), (fine, coarse)
+    for run in (two_layer_runs[("coarse", 0.0)], two_layer_runs[("fine", 0.0)]):
+        assert run["residual"].max() < 1e-12
+        assert np.all(np.abs(run["A"].sum(axis=1) + run["R"] + run["T"] - 1) < 1e-5)
+
+
+def test_two_layer_stack_oblique_te_tm(two_layer_runs):
+    """theta = 45 deg, TE and TM: both converge to the transfer matrix (the TM
+    case exercises the interface charge); the energy balance closes to the
+    discretisation error."""
+    th = np.pi / 4
+    coarse = _stack_err(two_layer_runs[("coarse", th)], th)
+    fine = _stack_err(two_layer_runs[("fine", th)], th)
+    assert np.all(fine[:, 2] < 0.005) and np.all(fine[:, :2] < 0.006), fine
+    assert np.all(fine[:, [0, 2]] < coarse[:, [0, 2]]), (fine, coarse)    # R and A
+    run = two_layer_runs[("fine", th)]
+    bal = run["A"].sum(axis=1) + run["R"] + run["T"] - 1
+    assert abs(bal[0]) < 1e-5 and abs(bal[1]) < 1.5e-3, bal
+
+
+@pytest.mark.parametrize("plant", ["interface_sign", "interface_dropped"])
+def test_planted_interface_charge_error_fails(monkeypatch, two_layer_runs, plant):
+    """A sign error (or a dropped term) on the two-material interface faces
+    only, with the outer boundary faces right, moves oblique-TM T by > 0.05;
+    the correct oracle is within 0.003 on the same mesh."""
+    from oracle import fill
+    th = np.pi / 4
+    R0, T0, A0 = tmm_rt([EPS_ACT, EPS_BUF], [100.0, 40.0], 500.0, th, "TM")
+    assert abs(two_layer_runs[("coarse", th)]["T"][1] - T0) < 0.003
+    right = fill.surface_charge
+    if plant == "interface_sign":
+        wrong = lambda kp, km, half: np.where(half, right(kp, km, half), -right(kp, km, half))  # noqa: E731
+    else:
+        wrong = lambda kp, km, half: np.where(half, right(kp, km, half), 0.0)  # noqa: E731
+    monkeypatch.setattr(fill, "surface_charge", wrong)
+    bad = solve_cell(_two_layer("coarse"), 500.0, th, 0.0)
+    assert abs(bad["T"][1] - T0) > 0.05
+
+
+# --------------------------------------------------------------------------- preconditioner and GMRES
+@pytest.fixture(scope="module")
+def tiny_run():
+    cell = cellgen.small_cells()["plasmonic_tiny"]
+    return cell, solve_cell(cell, 520.0, 0.35, 0.2, keep_matrix=True)
+
+
+def test_unknown_domains_rule(tiny_run):
+    """Eq. (5) grouping: a face inside one domain belongs to it; a face between
+    two domains to the one with the larger |eps| (the metal); a half function to
+    its tetrahedron's domain."""
+    cell, out = tiny_run
+    topo = out["topo"]
+    eps = cell.eps(520.0)
+    ud = unknown_domains(topo, eps)
+    dp = topo["domain"][topo["tp"]]
+    half = topo["kind"] == KIND_HALF
+    dm = np.where(half, dp, topo["domain"][np.maximum(topo["tm"], 0)])
+    same = dp == dm
+    assert np.all(ud[same] == dp[same])
+    ag = list(cell.domain_names).index("ag")
+    touches_ag = (dp == ag) | (dm == ag)
+    assert np.all(ud[touches_ag] == ag) and np.any(touches_ag & ~same)
+    act, buf = list(cell.domain_names).index("active"), list(cell.domain_names).index("buffer")
+    act_buf = ((dp == act) & (dm == buf)) | ((dp == buf) & (dm == act))
+    assert abs(eps[act]) > abs(eps[buf]) and np.all(ud[act_buf] == act) and np.any(act_buf)
+
+
+def test_block_preconditioner_inverts_the_domain_blocks(tiny_run):
+    """M applied to blockdiag(Z_dd) v returns v (Eq. (6)): the LU factors are
+    those of the diagonal blocks of the domain grouping."""
+    cell, out = tiny_run
+    Z = out["Z"]
+    ud = unknown_domains(out["topo"], cell.eps(520.0))
+    M = block_preconditioner(Z, ud)
+    P = np.where(ud[:, None] == ud[None, :], Z, 0.0)
+    rng = np.random.default_rng(9)
+    v = rng.normal(size=len(Z)) + 1j * rng.normal(size=len(Z))
+    assert np.linalg.norm(M(P @ v) - v) < 1e-12 * np.linalg.norm(v)
+    assert np.linalg.norm(M(Z @ v) - v) > 1e-3 * np.linalg.norm(v)     # Z itself is not block diagonal
+
+
+def test_gmres_reaches_the_lu_solution(tiny_run):
+    """Restarted GMRES, with and without the Eq. (6) preconditioner, reaches the
+    dense-LU x to tol x cond(Z) (both right-hand sides), and the preconditioner
+    cuts the iterations (Fig. 2's claim: measured 35 against 476 here)."""
+    cell, out = tiny_run
+    Z, b, x = out["Z"], out["b"], out["x"]
+    M = block_preconditioner(Z, unknown_domains(out["topo"], cell.eps(520.0)))
+    tol = 1e-10
+    bound = 10 * tol * np.linalg.cond(Z)
+    for p in range(2):
+        xp, ip, hp = gmres(Z, b[:, p], M, tol=tol)
+        xn, i_n, hn = gmres(Z, b[:, p], None, tol=tol)
+        for xg, h in ((xp, hp), (xn, hn)):
+            assert h[-1] <= tol
+            assert np.linalg.norm(xg - x[:, p]) <= bound * np.linalg.norm(x[:, p])
+        assert 3 * ip < i_n, (ip, i_n)
+
+
+def test_paper_preconditioner_experiment():
+    """Sec. 3, Fig. 2-3: the cell is built from the golden fixture (Ag cubes
+    W = 20 nm, a = b = 40 nm, 20 nm spacer, 60 nm active layer, lambda = 400 nm).
+    Solved with and without the Eq. (6) preconditioner at a GMRES tolerance of
+    1e-4 (the paper gives none; this reading reproduces its printed result), the
+    current coefficients of every unknown differ by less than the fixture's
+    12% (Fig. 3), and the preconditioned solve needs fewer iterations (Fig. 2)."""
+    g = golden_data.load("paper_eq8_preconditioner.txt")
+    cell = cellgen.paper_cube_cell(h_fine=20.0, h_coarse=20.0, geometry=g)
+    v = cell.verts[cell.tets]
+    vol = np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), v[:, 3] - v[:, 0]) / 6.0
+    a, W = g["period_nm"], g["cube_side_nm"]
+    assert abs(vol[cell.tet_domain == 2].sum() - W ** 3) < 1e-6 * W ** 3
+    assert abs(vol[cell.tet_domain == 0].sum() - a * a * g["spacer_thickness_nm"]) < 1e-6 * a * a * 20
+    assert abs(vol[cell.tet_domain == 1].sum() - (a * a * g["active_thickness_nm"] - W ** 3)) < 1e-3
+    lam = g["wavelength_nm"]
+    out = solve_cell(cell, lam, 0.0, 0.0, keep_matrix=True)
+    Z, b = out["Z"], out["b"]
+    M = block_preconditioner(Z, unknown_domains(out["topo"], cell.eps(lam)))
+    xp, ip, _ = gmres(Z, b[:, 0], M, tol=1e-4)
+    xn, i_n, _ = gmres(Z, b[:, 0], None, tol=1e-4)
+    per_unknown = np.abs(xp - xn) / np.abs(xn)
+    assert np.max(per_unknown) < g["eq8_relative_error_max"], np.max(per_unknown)
+    assert ip < i_n, (ip, i_n)
