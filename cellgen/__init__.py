@@ -30,7 +30,8 @@ __all__ = [
     "Cell", "grid_1d", "kuhn_mesh", "slab_cell", "layered_cell",
     "eps_ag_drude", "eps_active", "eps_buffer",
     "config_slab", "config_plasmonic", "config_plasmonic_sample", "config_sweep_geometry", "small_cells",
-    "ball_cell", "config_plasmonic_ball", "cube_cell", "paper_cube_cell", "two_layer_cell",
+    "ball_cell", "config_plasmonic_snap", "config_plasmonic_fine", "cube_cell", "config_large",
+    "config_large_reduced", "paper_cube_cell", "two_layer_cell",
 ]
 
 
@@ -164,7 +165,7 @@ def _orient(verts, tets):
 
 def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=None,
                  h_z=None, jitter=0.1, seed=0, snap=0.4, name="", active_domain=None,
-                 lateral_fine=True, particles="snap"):
+                 lateral_fine=True, particles="snap", ridges=None):
     """Layered unit cell with optional spheres.
 
     layers:  list of (thickness_nm, material_name) from bottom (z=0) to top.
@@ -179,6 +180,10 @@ def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=N
              surrounding grid (a smooth particle surface without slivers or
              steps, conformal with the layers; the box of half-width r + 2
              h_fine must lie inside one layer and inside the cell).
+    ridges:  optional (layer_index, [(x0, x1), ...], material_name): a grating
+             in that layer, ridges along y occupying x in [x0, x1] (one domain,
+             numbered after the spheres); the grid has planes at the ridge walls
+             and jitter keeps their nodes on them.
     """
     if particles not in ("snap", "ball"):
         raise ValueError("particles must be 'snap' or 'ball'")
@@ -207,6 +212,8 @@ def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=N
         fine_x.append((cx - r - pad, cx + r + pad))
         fine_y.append((cy - r - pad, cy + r + pad))
         fine_z.append((cz - r - pad, cz + r + pad))
+    walls = sorted({float(x) for x0x1 in (ridges[1] if ridges else ()) for x in x0x1})
+    brk_x = list(brk_x) + walls
     xs = grid_1d(0.0, period_a, brk_x, fine_x if (lateral_fine or boxes) else (), h_fine, h_coarse)
     ys = grid_1d(0.0, period_b, brk_y, fine_y if (lateral_fine or boxes) else (), h_fine, h_coarse)
     zs = grid_1d(0.0, zb[-1], brk_z, fine_z, h_fine, h_z or h_coarse)
@@ -252,6 +259,8 @@ def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=N
         free = ~lateral & ~snapped & ~inbox
         dj = rng.uniform(-jitter, jitter, size=verts.shape) * hloc[:, None]
         dj[on_plane, 2] = 0.0
+        if walls:   # ridge walls stay planar
+            dj[np.isin(np.round(verts[:, 0], 9), np.round(walls, 9)), 0] = 0.0
         # keep jittered nodes clear of sphere surfaces (no accidental straddling)
         cand = verts + dj
         for cx, cy, cz, r, _ in spheres:
@@ -285,6 +294,14 @@ def layered_cell(period_a, period_b, layers, spheres=(), h_coarse=20.0, h_fine=N
         else:
             inside = np.linalg.norm(cent - np.array([cx, cy, cz]), axis=1) < r
         dom[inside] = len(layers) + s
+        names.append(m)
+    if ridges:
+        li, spans, m = ridges
+        in_layer = dom == li
+        on_ridge = np.zeros(len(dom), dtype=bool)
+        for x0, x1 in spans:
+            on_ridge |= (cent[:, 0] > x0) & (cent[:, 0] < x1)
+        dom[in_layer & on_ridge] = len(names)
         names.append(m)
     if active_domain is None:
         active_domain = names.index("active") if "active" in names else 0
@@ -324,21 +341,30 @@ def config_slab():
     return slab_cell(6, 6, 2, 200.0, 200.0, 40.0, (4.0, 0.5))
 
 
-def config_plasmonic(seed=2, h_coarse=28.0, h_fine=9.5, h_z=25.0, particles="snap"):
+def config_plasmonic(seed=2, h_coarse=30.0, h_fine=10.0, h_z=25.0, particles="ball"):
     """Plasmonic cell: period 200 nm, Ag sphere r=20 nm centred in a 100 nm active
-    layer over a 40 nm buffer (three material domains).  particles="ball" meshes
-    the sphere as a mapped cube (see layered_cell)."""
+    layer over a 40 nm buffer (three material domains), 10,368 tetrahedra and
+    21,024 SWG unknowns.  The sphere is meshed as a mapped cube (384
+    tetrahedra, smooth surface, particles="ball", see layered_cell);
+    particles="snap" snaps the grid nodes near its surface instead."""
     return layered_cell(200.0, 200.0, [(40.0, "buffer"), (100.0, "active")],
                         spheres=[(100.0, 100.0, 90.0, 20.0, "ag")],
                         h_coarse=h_coarse, h_fine=h_fine, h_z=h_z, jitter=0.1, seed=seed,
-                        name="plasmonic_200nm_r20" + ("_ball" if particles == "ball" else ""),
+                        name="plasmonic_200nm_r20" + ("_ball" if particles == "ball" else "_snap"),
                         particles=particles)
 
 
-def config_plasmonic_ball(seed=2):
-    """The plasmonic cell with its Ag sphere meshed as a mapped cube (smooth,
-    sliver-free particle surface)."""
-    return config_plasmonic(seed=seed, particles="ball")
+def config_plasmonic_snap(seed=2):
+    """The plasmonic cell with the grid nodes near the sphere snapped onto it
+    (10,368 tetrahedra, 21,024 unknowns, 1,098 of them in the sphere): a
+    faceted particle surface on which the metal's absorption is not reliable."""
+    return config_plasmonic(seed=seed, h_coarse=28.0, h_fine=9.5, particles="snap")
+
+
+def config_plasmonic_fine(seed=2):
+    """The plasmonic cell with a finer mapped-cube sphere (750 tetrahedra;
+    17,550 tetrahedra, 35,550 unknowns in all)."""
+    return config_plasmonic(seed=seed, h_coarse=28.0, h_fine=9.5, particles="ball")
 
 
 def config_plasmonic_sample(seed=2):
@@ -352,8 +378,8 @@ def config_plasmonic_sample(seed=2):
 
 def config_sweep_geometry(seed=3):
     """The plasmonic geometry at the coarser density used for wavelength x angle
-    sweeps: 4374 tets, 8910 SWG unknowns (150 tets in the sphere)."""
-    return config_plasmonic(seed=seed, h_coarse=40.0, h_fine=12.0, h_z=30.0)
+    sweeps: 4,860 tets, 9,882 SWG unknowns (a 162-tetrahedron mapped-cube sphere)."""
+    return config_plasmonic(seed=seed, h_coarse=60.0, h_fine=14.5, h_z=40.0)
 
 
 def serving_cell(index, master_seed=4):
@@ -429,6 +455,29 @@ def ball_cell(period, radius, n, material="const:4.0,1.0"):
     return Cell(verts=verts, tets=tets.astype(np.int32), tet_domain=np.zeros(len(tets), dtype=np.int32),
                 n_domains=1, period_a=float(period), period_b=float(period), active_domain=0,
                 domain_names=(material,), name="ball")
+
+
+def config_large(h_coarse=24.0, h_fine=12.0, h_z=20.0, particles="snap", seed=5, lateral_fine=True,
+                 name="large_400nm_2x2"):
+    """The large cell: period 400 nm, a 2 x 2 array of Ag spheres (r = 35 nm)
+    centred in a 120 nm active layer, over a 40 nm periodic Ag back grating
+    (ridges 40 nm wide along y, two per period, the gaps filled with the
+    buffer material).  Domains: 0 grating gaps (buffer), 1 active, 2-5 the
+    spheres, 6 the ridges.  The default density gives 44,550 tetrahedra and
+    about 91k SWG unknowns (the dense FP32 Z is ~66 GB).  The spheres are
+    snapped (a mapped-cube ball of r = 35 nm needs h_fine <= 12.5 nm inside the
+    120 nm layer, which alone would exceed this size)."""
+    spheres = [(x, y, 100.0, 35.0, "ag") for y in (100.0, 300.0) for x in (100.0, 300.0)]
+    return layered_cell(400.0, 400.0, [(40.0, "buffer"), (120.0, "active")], spheres=spheres,
+                        h_coarse=h_coarse, h_fine=h_fine, h_z=h_z, jitter=0.1, seed=seed, name=name,
+                        particles=particles, lateral_fine=lateral_fine,
+                        ridges=(0, [(80.0, 120.0), (280.0, 320.0)], "ag"))
+
+
+def config_large_reduced(seed=5):
+    """The large cell's geometry at a density the FP64 oracle solves in under a
+    minute: 720 tetrahedra, 1,500 unknowns, every domain present."""
+    return config_large(h_coarse=80.0, h_fine=50.0, h_z=40.0, seed=seed, lateral_fine=False, name="large_reduced")
 
 
 def cube_cell(period, d_spacer, d_active, side, h_fine, h_coarse=None, particle=True, name=""):

@@ -50,14 +50,27 @@ typedef enum {
     VIE_ENOMEM = -2,            /* device allocation failed                          */
     VIE_ECUDA = -3,             /* CUDA runtime / launch error                       */
     VIE_RAYLEIGH_ANOMALY = -4,  /* a Floquet mode is at grazing: g_p is singular     */
+    VIE_DEVICE_TIMEOUT = -5,    /* a bounded wait inside a device kernel ran out (the
+                                   kernel gave up and returned; the context stays
+                                   usable, the solve has no result)                 */
     VIE_BAD_MESH = -6,          /* inverted tetrahedron or unmatched periodic walls  */
-    VIE_BREAKDOWN = -8          /* zero or non-finite pivot in a preconditioner block*/
+    VIE_CANCELLED = -7,         /* the request was cancelled (vie_server_cancel)     */
+    VIE_BREAKDOWN = -8          /* zero or non-finite pivot while inverting a domain
+                                   block of Eq. (6) (no pivoting): the preconditioner
+                                   does not exist, the solve has no result; rerun
+                                   with use_precond = 0                              */
 } vie_status;
 
 typedef enum {
     VIE_FP64 = 0,   /* Z, Krylov vectors and products in FP64                        */
-    VIE_FP32 = 1    /* Z stored in FP32 (near-singular integrals in FP64), FP32
+    VIE_FP32 = 1,   /* Z stored in FP32 (near-singular integrals in FP64), FP32
                        GMRES inside FP64-residual iterative refinement           */
+    VIE_FP16 = 2,   /* as VIE_FP32, and the GMRES products of every refinement
+                       sweep read a second copy of Z in FP16 (one power-of-two
+                       scale for the matrix, FP32 accumulation); the FP64
+                       residual of each sweep still reads the FP32 Z, so the
+                       converged answer is that of the FP32 Z                   */
+    VIE_BF16 = 3    /* as VIE_FP16 with the second copy in BF16 (no scale)        */
 } vie_precision;
 
 typedef struct {
@@ -71,7 +84,16 @@ typedef struct {
     int32_t timing;        /* 1: record CUDA events around the main kernels and
                               report their device times in vie_result.k_* (adds
                               no work, only events on the solve stream)          */
-    int32_t reserved;
+    int32_t precond_block_max;  /* 0 (default): one block per material domain,
+                              the preconditioner of Eq. (6).  > 0: sub-block
+                              variant (not in the paper): a domain with more
+                              unknowns than this is cut into spatially compact
+                              sub-blocks of at most this many (recursive
+                              coordinate bisection of the unknowns' positions),
+                              each inverted and applied as its own diagonal
+                              block; inversion work drops by about the square of
+                              the number of pieces, GMRES may need more
+                              iterations                                         */
 } vie_options;
 
 typedef struct {
@@ -83,6 +105,13 @@ typedef struct {
                                            solved unknowns in canonical order; host
                                            pointer, or device if coeffs_on_device */
     int32_t coeffs_on_device;
+    int32_t density_on_device;          /* density_out is a device pointer          */
+    double *density_out;                /* optional [2 pol][n_tets]: the absorbed
+                                           fraction of Eq. (7) contributed by each
+                                           tetrahedron, k0 |Im eps_r| int_t |E|^2 dV
+                                           / (|E0|^2 a b cos theta) (the absorption
+                                           profile of Fig. 5); the sum over the
+                                           tetrahedra of a domain is absorbed[p][d]  */
 } vie_request;
 
 typedef struct {
@@ -185,9 +214,31 @@ int vie_solve_batch(vie_ctx *ctx, const vie_request *reqs, vie_result *res, int3
    vie_solve in FP64. */
 int vie_fill_matrix(vie_ctx *ctx, const vie_request *req, double *Z_host, double *b_host, void *stream);
 
-/* Parity entry point: the matrix in the precision of the current options
-   (FP32 entries widened to double), canonical order. */
+/* Parity entry point: the matrix in the precision of the current options,
+   widened to double, canonical order: the FP32 Z (VIE_FP32), or the 16-bit
+   copy the GMRES products read with its scale undone (VIE_FP16, VIE_BF16). */
 int vie_fill_matrix_prec(vie_ctx *ctx, const vie_request *req, double *Z_host, void *stream);
+
+/* Parity entry point for the preconditioner of Eq. (5)-(6): fills Z for the
+   request in the precision of the current options, inverts every domain block
+   as vie_solve does, and returns block `block` (0-based, in increasing domain
+   order over the non-empty domains, unknowns grouped by the Eq. (5) rule; with
+   options.precond_block_max > 0 the sub-blocks of each domain in turn):
+   *n_out its size n; unknowns [n] (may be NULL) the canonical index of its
+   row/column i; Zdd [n][n] complex (may be NULL) the block A_dd as stored
+   (FP32 or FP64 entries widened); Minv [n][n] complex (may be NULL) the
+   computed inverse (FP32, before its FP16 copy).  With all three NULL only
+   *n_out is set (no fill).  VIE_EINVAL for a block index out of range. */
+int vie_domain_block(vie_ctx *ctx, const vie_request *req, int32_t block, int32_t *n_out, int32_t *unknowns,
+                     double *Zdd, double *Minv, void *stream);
+
+/* Measured peak of the FP32 (precision VIE_FP32) or FP64 (VIE_FP64) fused
+   multiply-add pipes of `device`, in TFLOP/s, from a kernel of independent FMA
+   chains on every SM (the best of three launches of at least 100 ms each):
+   the denominator of the roofline of the CUDA-core fill kernels.  The paper
+   has no counterpart; a measurement entry point.  Allocates nothing; uses a
+   stream and two events of its own.  Returns VIE_OK, VIE_EINVAL or VIE_ECUDA. */
+int vie_fma_peak(int device, int32_t precision, double *tflops);
 
 /* Complex erfcx(u) = exp(u^2) erfc(u) = w(j u) on the device for n host
    arguments (Re u >= 0), in FP64 (precision VIE_FP64) or FP32 (VIE_FP32).
@@ -213,15 +264,21 @@ int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out
    stream a cudaStream_t (NULL: legacy default stream).  Needs no context.
    Scratch: the Ewald parameter block and the FP32 interpolation tables live
    in a file-scope device array of about 0.85 MB that every GPU loading this
-   library keeps until the process exits; requests needing more than 96 distinct Floquet decay constants are
-   rejected with VIE_EINVAL.  The tables are rebuilt completely by each call,
-   so nothing has to start at zero.  All calls share that array and the
-   library's constant tables: calls whose work overlaps on the GPU race.
-   The first call on a device does a one-time set-up (constant upload and the
-   device address of the array); make that first call before any stream
-   capture.  The call only enqueues work: out_dev is valid once the stream has
-   completed it.  Calls no cudaMalloc, cudaFree or allocating library routine.
-   Returns VIE_OK, VIE_EINVAL, VIE_RAYLEIGH_ANOMALY or VIE_ECUDA. */
+   library keeps until the process exits; requests needing more than 96
+   distinct Floquet decay constants are rejected with VIE_EINVAL.  The tables
+   are rebuilt completely by each call, so nothing has to start at zero.  All
+   calls share that array: calls whose work overlaps on the GPU race.
+   The first call on a device (the current device) does a one-time set-up,
+   under a lock shared by all host threads: the library's constant tables (the
+   same once-per-device upload vie_create does; a device that already has them
+   is not written again) and the device address of the array.  Make that first
+   call before any stream capture.  Each call copies the Ewald parameter block
+   (~49 KB) from host memory of the calling thread to the array on `stream`
+   (a pageable copy: the call can wait for it to be staged); the table build
+   and the evaluation are then enqueued on `stream`, and out_dev is valid once
+   the stream has completed them.  Calls no cudaMalloc, cudaFree or allocating
+   library routine.  Returns VIE_OK, VIE_EINVAL, VIE_RAYLEIGH_ANOMALY or
+   VIE_ECUDA. */
 int vie_green_noalloc(double lambda_nm, double theta, double phi, double period_a, double period_b,
                       double z_extent, const double *d_dev, double *out_dev, int32_t n,
                       int32_t precision, void *stream);
@@ -260,6 +317,7 @@ typedef struct {
     int64_t queued, running, max_running;     /* now, and the most at once       */
     int64_t budget_bytes;                     /* HBM budget of the slots          */
     int64_t reserved_bytes, peak_reserved_bytes;
+    int64_t cancelled;                        /* requests that ended VIE_CANCELLED */
 } vie_server_stats;
 
 /* Start a server on `device` with n_slots slots (1..64) and solver options
@@ -282,6 +340,13 @@ int vie_server_submit(vie_server *s, const vie_mesh *mesh, const vie_request *re
    ticket is then forgotten), VIE_PENDING if it has not finished, VIE_EINVAL
    for an unknown ticket. */
 int vie_server_poll(vie_server *s, uint64_t ticket, vie_result *res, int32_t wait_ms);
+
+/* Cancel a request: a queued request is dropped, a running one stops at its
+   next GMRES iteration (or before its next phase); either way the ticket then
+   polls as finished with res->status = VIE_CANCELLED.  A request that had
+   already finished keeps its result.  Returns VIE_OK, or VIE_EINVAL for an
+   unknown ticket. */
+int vie_server_cancel(vie_server *s, uint64_t ticket);
 
 /* Counters of the server (a snapshot). */
 int vie_server_get_stats(vie_server *s, vie_server_stats *out);

@@ -6,6 +6,7 @@
 //   solve  GMRES on diag(A_dd^-1) Z x = diag(A_dd^-1) b, restarted; every restart
 //          recomputes the FP64 residual b - Z x (iterative refinement)
 //   post   absorbed fraction per domain (Eq. (7)), reflectance, transmittance
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -96,6 +97,12 @@ struct vie_ctx {
     double z_extent = 0;
     // solve buffers
     DevBuf Z, b, x, r, u, w, V, h, y, Minv, MinvH, amax, tcpack, tcpack2, status, acc, J, rt, cout, xs;
+    DevBuf Zh;     // 16-bit copy of Z read by the GMRES products (VIE_FP16 / VIE_BF16)
+    DevBuf dens;   // per-tetrahedron absorbed fractions [2][nt] (request density_out)
+    double zh_alpha = 1.0;   // 1 / (power-of-two scale of the FP16 copy)
+    // set by the solve server when the request is cancelled: a solve checks it
+    // between phases and at every GMRES iteration (the stream is idle there)
+    const std::atomic<int> *cancel = nullptr;
     std::vector<double> pinv;   // per domain block: 1 / (power-of-two scale of its FP16 inverse)
     size_t ld = 0;
     int64_t h2d = 0, d2h = 0;   // bytes copied by the current solve
@@ -152,21 +159,6 @@ int fail(vie_ctx *c, int code, const std::string &msg) {
                         std::string(#expr) + ": " + cudaGetErrorString(e_));                 \
     } while (0)
 
-constexpr double FP64_XCUT = 6.0;   // Ewald truncation: exp(-36) ~ 2e-16
-constexpr float FP32_XCUT = 4.2f;   // exp(-17.6) ~ 2e-8
-
-double erfi_series(double x) {
-    // erfi(x) = 2/sqrt(pi) sum x^(2n+1) / (n! (2n+1))
-    double term = x, sum = x;
-    for (int n = 1; n < 200; ++n) {
-        term *= x * x / n;
-        double add = term / (2 * n + 1);
-        sum += add;
-        if (std::fabs(add) < 1e-18 * std::fabs(sum)) break;
-    }
-    return 2.0 / std::sqrt(M_PI) * sum;
-}
-
 struct HostReq {
     double k0, kx, ky, theta;
     std::vector<cplx> eps, kap;          // per domain, exp(j w t) convention
@@ -176,6 +168,37 @@ struct HostReq {
     std::vector<double> orders;          // [n][4]: k_tx, k_ty, k_z, is (0,0)
     double pol[6], kinc[3];
 };
+
+// Recursive coordinate bisection of ids[lo, hi) (unknowns, positioned at the
+// centroid of their T+ tetrahedron) into pieces of at most bmax: split at the
+// median along the axis of largest extent (ties by unknown id, so the order is
+// deterministic); the pieces are appended as [begin, end) ranges of ids, which
+// is reordered in place.
+void split_rcb(const vie::Topology &T, std::vector<int> &ids, int lo, int hi, int bmax,
+               std::vector<std::pair<int, int>> &pieces) {
+    if (hi - lo <= bmax) {
+        std::sort(ids.begin() + lo, ids.begin() + hi);
+        pieces.push_back({lo, hi});
+        return;
+    }
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int i = lo; i < hi; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const double c = T.cen[3 * (size_t)T.tp[ids[i]] + k];
+            mn[k] = std::min(mn[k], c);
+            mx[k] = std::max(mx[k], c);
+        }
+    int ax = 0;
+    for (int k = 1; k < 3; ++k)
+        if (mx[k] - mn[k] > mx[ax] - mn[ax]) ax = k;
+    const int mid = lo + (hi - lo) / 2;
+    std::nth_element(ids.begin() + lo, ids.begin() + mid, ids.begin() + hi, [&](int a, int b) {
+        const double ca = T.cen[3 * (size_t)T.tp[a] + ax], cb = T.cen[3 * (size_t)T.tp[b] + ax];
+        return ca < cb || (ca == cb && a < b);
+    });
+    split_rcb(T, ids, lo, mid, bmax, pieces);
+    split_rcb(T, ids, mid, hi, bmax, pieces);
+}
 
 int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
     const vie::Topology &T = ctx->mesh->topo;
@@ -208,102 +231,34 @@ int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
     }
     H.perm.assign(T.N, 0);
     int next = 0;
+    const int bmax = ctx->opt.precond_block_max;
     for (int d = 0; d < T.n_dom; ++d) {
-        int off = next;
+        std::vector<int> ids;
         for (int n = 0; n < T.N; ++n)
-            if (udom[n] == d) H.perm[n] = next++;
-        if (next > off) { H.blk_off.push_back(off); H.blk_n.push_back(next - off); }
-    }
-    // Ewald tables
-    vie::EwaldTables &E = H.ew;
-    std::memset(&E, 0, sizeof(E));
-    const double a = T.a, b = T.b, k0 = H.k0;
-    const bool fp64 = ctx->opt.precision == VIE_FP64;
-    E.E = vie::ewald_split(a, b, k0, !fp64 && H.kx == 0.0 && H.ky == 0.0);
-    E.bb = k0 / (2.0 * E.E);
-    E.a = a; E.b = b;
-    E.xcut64 = FP64_XCUT;
-    E.xcut32 = FP32_XCUT;
-    const double xc = fp64 ? FP64_XCUT : FP32_XCUT;
-    const int mm = (int)std::ceil(xc / (E.E * a)) + 2, nn = (int)std::ceil(xc / (E.E * b)) + 2;
-    int ni = 0;
-    for (int m = -mm; m <= mm; ++m)
-        for (int n = -nn; n <= nn; ++n) {
-            double dmin = std::hypot(std::max(std::abs(m) - 1, 0) * a, std::max(std::abs(n) - 1, 0) * b);
-            bool nearimg = std::abs(m) <= 1 && std::abs(n) <= 1;
-            if (dmin * E.E > xc && !nearimg) continue;
-            if (ni >= vie::MAX_IMG) return fail(ctx, VIE_EINVAL, "period too small for the image table");
-            double phs = H.kx * m * a + H.ky * n * b;
-            double f = std::exp(E.bb * E.bb) / (4.0 * M_PI);
-            double v[4] = {m * a, n * b, f * std::cos(phs), f * std::sin(phs)};
-            for (int q = 0; q < 4; ++q) { E.img64[ni][q] = v[q]; E.img32[ni][q] = (float)v[q]; }
-            if (nearimg) E.near_img[(m + 1) * 3 + (n + 1)] = ni;
-            ++ni;
-        }
-    E.n_img = ni;
-    const int pm = (int)std::ceil((2.0 * E.E * xc + std::fabs(H.kx)) * a / (2 * M_PI)) + 1;
-    const int qm = (int)std::ceil((2.0 * E.E * xc + std::fabs(H.ky)) * b / (2 * M_PI)) + 1;
-    int nm = 0;
-    H.orders.clear();
-    for (int p = -pm; p <= pm; ++p)
-        for (int q = -qm; q <= qm; ++q) {
-            double ktx = H.kx + 2 * M_PI * p / a, kty = H.ky + 2 * M_PI * q / b;
-            double kt2 = ktx * ktx + kty * kty;
-            double g2 = kt2 - k0 * k0;
-            if (std::fabs(g2) * std::max(a, b) * std::max(a, b) < 1e-10)
-                return fail(ctx, VIE_RAYLEIGH_ANOMALY, "a Floquet order is at grazing (Rayleigh anomaly)");
-            if (g2 < 0) H.orders.insert(H.orders.end(), {ktx, kty, std::sqrt(-g2), (p == 0 && q == 0) ? 1.0 : 0.0});
-            if (std::sqrt(kt2) > 2.0 * E.E * xc + k0) continue;
-            if (nm >= vie::MAX_MODE) return fail(ctx, VIE_EINVAL, "too many Floquet modes for the table");
-            cplx g = g2 >= 0 ? cplx(std::sqrt(g2), 0) : cplx(0, std::sqrt(-g2));
-            cplx ig = 1.0 / (4.0 * a * b * g);
-            double v[8] = {ktx, kty, g.real(), g.imag(), std::exp(-g2 / (4 * E.E * E.E)), ig.real(), ig.imag(), 0};
-            for (int c = 0; c < 8; ++c) { E.mode64[nm][c] = v[c]; E.mode32[nm][c] = (float)v[c]; }
-            ++nm;
-        }
-    E.n_mode = nm;
-    E.reg0_re = (E.E / (4 * M_PI)) * (2 * E.bb * erfi_series(E.bb) - 2.0 / std::sqrt(M_PI) * std::exp(E.bb * E.bb));
-    // tabulated FP32 path: same truncation as the FP32 series
-    {
-        const double xc32 = FP32_XCUT;
-        E.xs_max = (float)(xc32 + 0.5);
-        E.xs_inv_h = (float)(vie::NSPAT / (xc32 + 0.5));
-        const double zr = std::max(ctx->z_extent, 1e-6) * (1.0 + 1e-6);
-        E.z_max = (float)zr;
-        E.z_inv_h = (float)(vie::NZTAB / zr);
-        E.e_mb2 = (float)std::exp(-E.bb * E.bb);
-        E.Ef = (float)E.E;
-        E.kx = (float)H.kx; E.ky = (float)H.ky;
-        E.step_x = (float)(2 * M_PI / a); E.step_y = (float)(2 * M_PI / b);
-        if (!vie::mode_rect(H.kx, H.ky, a, b, 2.0 * E.E * xc32 + k0, E.p0, E.np, E.q0, E.nq))
-            return fail(ctx, VIE_EINVAL, "too many Floquet modes for the table");
-        E.sym = (H.kx == 0.0 && H.ky == 0.0 && 2 * E.p0 + E.np == 1 && 2 * E.q0 + E.nq == 1) ? 1 : 0;
-        int nt = 0;
-        std::vector<double> g2s;
-        for (int p = E.p0; p < E.p0 + E.np; ++p)
-            for (int q = E.q0; q < E.q0 + E.nq; ++q) {
-                const int idx = (p - E.p0) * E.nq + (q - E.q0);
-                const double ktx = H.kx + 2 * M_PI * p / a, kty = H.ky + 2 * M_PI * q / b;
-                const double kt2 = ktx * ktx + kty * kty;
-                if (std::sqrt(kt2) > 2.0 * E.E * xc32 + k0) { E.rect_tab[idx] = -1; continue; }
-                const double g2 = kt2 - k0 * k0;
-                int found = -1;
-                for (int j = 0; j < nt; ++j)
-                    if (std::fabs(g2s[j] - g2) <= 1e-12 * std::max(1e-6, std::fabs(g2))) { found = j; break; }
-                if (found < 0) {
-                    found = nt++;
-                    g2s.push_back(g2);
-                    cplx g = g2 >= 0 ? cplx(std::sqrt(g2), 0) : cplx(0, std::sqrt(-g2));
-                    cplx ig = 1.0 / (4.0 * a * b * g);
-                    E.tab_gamma[found][0] = g.real(); E.tab_gamma[found][1] = g.imag();
-                    E.tab_ig[found][0] = ig.real(); E.tab_ig[found][1] = ig.imag();
-                    E.tab_pre[found] = std::exp(-g2 / (4 * E.E * E.E));
-                }
-                // bit 16 marks a real decay constant (evanescent mode): its G is real
-                E.rect_tab[idx] = found | (g2s[found] > 0 ? vie::TAB_REAL : 0);
+            if (udom[n] == d) ids.push_back(n);
+        if (ids.empty()) continue;
+        if (bmax > 0 && (int)ids.size() > bmax) {
+            // sub-block variant: the domain's unknowns cut into spatially compact
+            // pieces of at most bmax by recursive coordinate bisection (median
+            // split along the longest extent of the T+ tetrahedron centroids)
+            std::vector<std::pair<int, int>> pieces;
+            split_rcb(T, ids, 0, (int)ids.size(), bmax, pieces);
+            for (auto &pc : pieces) {
+                H.blk_off.push_back(next);
+                H.blk_n.push_back(pc.second - pc.first);
+                for (int i = pc.first; i < pc.second; ++i) H.perm[ids[i]] = next++;
             }
-        E.n_tab = nt;
+        } else {
+            H.blk_off.push_back(next);
+            H.blk_n.push_back((int)ids.size());
+            for (int n : ids) H.perm[n] = next++;
+        }
     }
+    // Ewald parameters and tables (Sec. 2.2) and the propagating Floquet orders
+    const char *why = "";
+    const bool fp64 = ctx->opt.precision == VIE_FP64;
+    if (int rc = vie::build_ewald_tables(T.a, T.b, H.k0, H.kx, H.ky, ctx->z_extent, fp64, H.ew, &H.orders, &why))
+        return fail(ctx, rc, why);
     return VIE_OK;
 }
 
@@ -476,6 +431,20 @@ int timed_precond(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &mof
     return VIE_OK;
 }
 
+bool cancelled(const vie_ctx *ctx) { return ctx->cancel && ctx->cancel->load(std::memory_order_relaxed) != 0; }
+
+// Inner-sweep tolerance floors of the 16-bit copies of Z: a sweep whose
+// products read Z rounded to 2^-11 (FP16) or 2^-8 (BF16) relative cannot
+// reduce the FP64 residual of the FP32 Z much further than about that, so the
+// sweep stops there and the next refinement step continues.
+constexpr double INNER_TOL_FP16 = 1e-3;
+constexpr double INNER_TOL_BF16 = 8e-3;
+
+// Left-preconditioned GMRES(m) on diag(A_dd^-1) Z x = diag(A_dd^-1) b for TE
+// and TM together (every product reads Z once for both), inside FP64-residual
+// iterative refinement: each sweep starts from r = b - Z x formed in FP64 (FP32
+// Z: at double length from FP32 arithmetic).  The sweep's products read Z
+// itself, or its 16-bit copy ctx->Zh for VIE_FP16 / VIE_BF16.
 template <typename TZ, typename TV>
 int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const std::vector<size_t> &mld,
           vie_result *res, cudaStream_t st, Timing &tm) {
@@ -483,7 +452,9 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
     const int m = std::max(2, ctx->opt.restart);
     const bool pre = ctx->opt.use_precond != 0;
     const double tol = ctx->opt.tol;
-    const double inner_tol = std::is_same<TV, float>::value ? std::max(ctx->opt.inner_tol, 1e-6) : tol * 0.1;
+    const int zin = std::is_same<TV, float>::value ? (ctx->opt.precision == VIE_FP16 ? 1 : ctx->opt.precision == VIE_BF16 ? 2 : 0) : 0;
+    const double inner_floor = zin == 1 ? INNER_TOL_FP16 : zin == 2 ? INNER_TOL_BF16 : 1e-6;
+    const double inner_tol = std::is_same<TV, float>::value ? std::max(ctx->opt.inner_tol, inner_floor) : tol * 0.1;
     const size_t vs = 4 * (size_t)N;     // stride of one basis vector (two rhs)
     CK(ctx->x.ensure(sizeof(double) * vs));
     CK(ctx->r.ensure(sizeof(double) * vs));
@@ -565,9 +536,21 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
             if (!inner_active[0] && !inner_active[1]) break;
             TV *vk = V + vs * k;
             TV *vn = V + vs * (k + 1);
+            if (cancelled(ctx)) return fail(ctx, VIE_CANCELLED, "cancelled");
             cudaEvent_t e0 = ctx->event(), e1 = ctx->event();
             if (e0) CK(cudaEventRecord(e0, st));
-            CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st)));
+            if constexpr (std::is_same<TV, float>::value) {
+                if (zin == 1)
+                    CK((vie::matvec<__half, TV, TV>(ctx->Zh.as<__half>(), ctx->ld, N, N, vk, pre ? u : vn,
+                                                    TV(ctx->zh_alpha), false, st)));
+                else if (zin == 2)
+                    CK((vie::matvec<__nv_bfloat16, TV, TV>(ctx->Zh.as<__nv_bfloat16>(), ctx->ld, N, N, vk,
+                                                           pre ? u : vn, TV(1), false, st)));
+                else
+                    CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st)));
+            } else {
+                CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st)));
+            }
             if (e1) { CK(cudaEventRecord(e1, st)); tm.mv.push_back({e0, e1}); }
             if (pre) { if (int e = timed_precond<TV>(ctx, H, moff, mld, u, vn, st, tm)) return e; }
             // classical Gram-Schmidt, twice; the projections of both passes and
@@ -714,6 +697,7 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
     CK(cudaMemcpyAsync(&stat, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(am.data(), ctx->amax.p, sizeof(unsigned) * nblk, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (stat & 2) return fail(ctx, VIE_DEVICE_TIMEOUT, "a bounded wait of the tensor-core block inversion ran out");
     if (stat) return fail(ctx, VIE_BREAKDOWN, "zero or non-finite pivot while inverting a domain block");
     CK(ctx->MinvH.ensure(sizeof(__half) * 2 * std::max<size_t>(tot, 1)));
     ctx->pinv.assign(nblk, 1.0);
@@ -732,6 +716,35 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
         CK(vie::to_half(ctx->Minv.as<float>() + 2 * moff[k], 2 * mld[k] * (size_t)H.blk_n[k], (float)scale,
                         ctx->MinvH.as<__half>() + 2 * moff[k], st));
     }
+    return VIE_OK;
+}
+
+// The 16-bit copy of the FP32 Z that the GMRES products read (VIE_FP16:
+// scaled by the power of two that brings the largest |Re|, |Im| to
+// [2^13, 2^14), undone in the product; VIE_BF16: unscaled)
+int make_z16(vie_ctx *ctx, cudaStream_t st) {
+    const size_t count = 2 * ctx->ld * (size_t)ctx->mesh->topo.N;
+    CK(ctx->Zh.ensure(sizeof(uint16_t) * count));
+    if (ctx->opt.precision == VIE_BF16) {
+        ctx->zh_alpha = 1.0;
+        CK(vie::to_bf16(ctx->Z.as<float>(), count, ctx->Zh.as<__nv_bfloat16>(), st));
+        return VIE_OK;
+    }
+    CK(ctx->amax.ensure(sizeof(unsigned)));
+    CK(cudaMemsetAsync(ctx->amax.p, 0, sizeof(unsigned), st));
+    CK(vie::absmax(ctx->Z.as<float>(), count, ctx->amax.as<unsigned>(), st));
+    unsigned bits = 0;
+    CK(cudaMemcpyAsync(&bits, ctx->amax.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    ctx->d2h += sizeof(unsigned);
+    CK(cudaStreamSynchronize(st));
+    float mx;
+    std::memcpy(&mx, &bits, sizeof(float));
+    if (!(mx > 0.f) || !std::isfinite(mx)) return fail(ctx, VIE_EINVAL, "impedance matrix is zero or not finite");
+    int ex = 0;
+    std::frexp((double)mx, &ex);   // mx in [2^(ex-1), 2^ex)
+    const double scale = std::ldexp(1.0, 14 - ex);
+    ctx->zh_alpha = 1.0 / scale;
+    CK(vie::to_half(ctx->Z.as<float>(), count, (float)scale, ctx->Zh.as<__half>(), st));
     return VIE_OK;
 }
 
@@ -755,8 +768,13 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     tm.fac0 = ctx->event(); tm.fac1 = ctx->event();
     auto t0 = clk::now();
     if (int e = fill<TZ>(ctx, m, q, true, st, &tm)) return e;
+    if constexpr (std::is_same<TZ, float>::value) {
+        if (ctx->opt.precision == VIE_FP16 || ctx->opt.precision == VIE_BF16)
+            if (int e = make_z16(ctx, st)) return e;
+    }
     CK(cudaStreamSynchronize(st));
     auto t1 = clk::now();
+    if (cancelled(ctx)) return fail(ctx, VIE_CANCELLED, "cancelled");
     std::vector<size_t> moff, mld;
     if (ctx->opt.use_precond) {
         if (tm.fac0) CK(cudaEventRecord(tm.fac0, st));
@@ -765,6 +783,7 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
         if (tm.fac1) { CK(cudaEventRecord(tm.fac1, st)); CK(cudaStreamSynchronize(st)); }
     }
     auto t2 = clk::now();
+    if (cancelled(ctx)) return fail(ctx, VIE_CANCELLED, "cancelled");
     int stat = gmres<TZ, TV>(ctx, H, moff, mld, res, st, tm);
     if (stat < 0) return stat;
     auto t3 = clk::now();
@@ -775,9 +794,23 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     CK(ctx->J.ensure(sizeof(double) * 24 * std::max(n_orders, 1)));
     CK(ctx->rt.ensure(sizeof(double) * 4));
     const double norm = H.k0 / (ctx->mesh->topo.a * ctx->mesh->topo.b * std::cos(H.theta));
+    const int ntet = ctx->mesh->topo.nt;
+    double *dens = nullptr;   // per-tetrahedron absorbed fractions [2][nt]
+    if (req->density_out) {
+        if (req->density_on_device) {
+            dens = req->density_out;
+        } else {
+            CK(ctx->dens.ensure(sizeof(double) * 2 * (size_t)ntet));
+            dens = ctx->dens.as<double>();
+        }
+    }
     CK(vie::launch_post(m, q, ctx->x.as<double>(), ctx->mesh->tdom.as<int32_t>(), nd, norm, ctx->orders.as<double>(),
                         n_orders, ctx->mesh->topo.a, ctx->mesh->topo.b, H.k0 * std::cos(H.theta), ctx->pol.as<double>(),
-                        ctx->acc.as<double>(), ctx->J.as<double>(), ctx->rt.as<double>(), st));
+                        ctx->acc.as<double>(), ctx->J.as<double>(), ctx->rt.as<double>(), dens, st));
+    if (req->density_out && !req->density_on_device) {
+        CK(cudaMemcpyAsync(req->density_out, dens, sizeof(double) * 2 * (size_t)ntet, cudaMemcpyDeviceToHost, st));
+        ctx->d2h += sizeof(double) * 2 * (size_t)ntet;
+    }
     std::vector<double> acc(2 * nd), rt(4);
     CK(cudaMemcpyAsync(acc.data(), ctx->acc.p, sizeof(double) * 2 * nd, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(rt.data(), ctx->rt.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
@@ -842,21 +875,6 @@ int solve_impl(vie_ctx *ctx, const vie_request *req, vie_result *res, cudaStream
     return stat;
 }
 
-// quadrature weights and Faddeeva coefficients: uploaded once per device, so
-// that creating a context never writes constant memory that running solves read
-cudaError_t upload_device_constants(int device) {
-    static std::mutex mu;
-    static std::vector<char> done;
-    std::lock_guard<std::mutex> lock(mu);
-    if ((size_t)device < done.size() && done[device]) return cudaSuccess;
-    cudaError_t e = vie::upload_constants();
-    if (e == cudaSuccess) e = vie::upload_post_constants();
-    if (e != cudaSuccess) return e;
-    if (done.size() <= (size_t)device) done.resize(device + 1, 0);
-    done[device] = 1;
-    return cudaSuccess;
-}
-
 // Device bytes one solve slot holds for request `req` on the current mesh:
 // Z, the block inverses, the Krylov basis and vectors, the touching scratch.
 int slot_footprint(vie_ctx *ctx, const vie_request *req, size_t *bytes) {
@@ -875,6 +893,7 @@ int slot_footprint(vie_ctx *ctx, const vie_request *req, size_t *bytes) {
     const size_t m = (size_t)std::max(2, ctx->opt.restart);
     const size_t vs = 4 * N;
     size_t b = 2 * sz * ld * N + minv + sz * vs * (m + 3) + 8 * vs * 4 + 64 * (size_t)ctx->mesh->nto[0];
+    if (ctx->opt.precision == VIE_FP16 || ctx->opt.precision == VIE_BF16) b += 2 * 2 * ld * N;   // 16-bit copy of Z
     b += (size_t)ctx->mesh->topo.nt * 4 * 64 + (16u << 20);   // request arrays, tables, small buffers
     *bytes = b;
     return VIE_OK;
@@ -888,10 +907,25 @@ void default_opts(vie_options *o) {
     o->tol = 1e-6;
     o->inner_tol = 3e-6;
     o->timing = 0;
-    o->reserved = 0;
+    o->precond_block_max = 0;
 }
 
 }  // namespace
+
+// quadrature weights and Faddeeva coefficients: uploaded once per device, so
+// that creating a context never writes constant memory that running solves read
+cudaError_t vie::upload_device_constants(int device) {
+    static std::mutex mu;
+    static std::vector<char> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((size_t)device < done.size() && done[device]) return cudaSuccess;
+    cudaError_t e = vie::upload_constants();
+    if (e == cudaSuccess) e = vie::upload_post_constants();
+    if (e != cudaSuccess) return e;
+    if (done.size() <= (size_t)device) done.resize(device + 1, 0);
+    done[device] = 1;
+    return cudaSuccess;
+}
 
 extern "C" {
 
@@ -909,8 +943,9 @@ int vie_create(vie_ctx **out, int device, const vie_options *opt) {
     ctx->device = device;
     default_opts(&ctx->opt);
     if (opt) ctx->opt = *opt;
+    if (ctx->opt.precision < VIE_FP64 || ctx->opt.precision > VIE_BF16) { delete ctx; return VIE_EINVAL; }
     if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return VIE_ECUDA; }
-    if (upload_device_constants(device) != cudaSuccess) {
+    if (vie::upload_device_constants(device) != cudaSuccess) {
         delete ctx;
         return VIE_ECUDA;
     }
@@ -920,8 +955,9 @@ int vie_create(vie_ctx **out, int device, const vie_options *opt) {
 
 int vie_set_options(vie_ctx *ctx, const vie_options *opt) {
     if (!ctx || !opt) return VIE_EINVAL;
-    if (opt->precision != VIE_FP64 && opt->precision != VIE_FP32) return fail(ctx, VIE_EINVAL, "unknown precision");
-    if (opt->restart < 2 || opt->max_iter < 1 || !(opt->tol > 0)) return fail(ctx, VIE_EINVAL, "bad solver options");
+    if (opt->precision < VIE_FP64 || opt->precision > VIE_BF16) return fail(ctx, VIE_EINVAL, "unknown precision");
+    if (opt->restart < 2 || opt->max_iter < 1 || !(opt->tol > 0) || opt->precond_block_max < 0)
+        return fail(ctx, VIE_EINVAL, "bad solver options");
     ctx->opt = *opt;
     return VIE_OK;
 }
@@ -1211,8 +1247,27 @@ int vie_fill_matrix_prec(vie_ctx *ctx, const vie_request *req, double *Z_host, v
     if ((e = fill<float>(ctx, m, q, false, st))) return e;
     const int N = ctx->mesh->topo.N;
     std::vector<float> Zp((size_t)2 * ctx->ld * N);
-    CK(cudaMemcpyAsync(Zp.data(), ctx->Z.p, sizeof(float) * Zp.size(), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    if (ctx->opt.precision == VIE_FP16 || ctx->opt.precision == VIE_BF16) {
+        // the 16-bit copy the GMRES products read, widened, its scale undone
+        if ((e = make_z16(ctx, st))) return e;
+        std::vector<uint16_t> Zb(Zp.size());
+        CK(cudaMemcpyAsync(Zb.data(), ctx->Zh.p, sizeof(uint16_t) * Zb.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < Zb.size(); ++i) {
+            if (ctx->opt.precision == VIE_FP16) {
+                __half_raw r;
+                r.x = Zb[i];
+                Zp[i] = (float)((double)__half2float(__half(r)) * ctx->zh_alpha);
+            } else {
+                __nv_bfloat16_raw r;
+                r.x = Zb[i];
+                Zp[i] = __bfloat162float(__nv_bfloat16(r));
+            }
+        }
+    } else {
+        CK(cudaMemcpyAsync(Zp.data(), ctx->Z.p, sizeof(float) * Zp.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
     for (int i = 0; i < N; ++i) {
         size_t ri = H.perm[i];
         for (int j = 0; j < N; ++j) {
@@ -1222,6 +1277,89 @@ int vie_fill_matrix_prec(vie_ctx *ctx, const vie_request *req, double *Z_host, v
         }
     }
     return VIE_OK;
+}
+
+int vie_domain_block(vie_ctx *ctx, const vie_request *req, int32_t block, int32_t *n_out, int32_t *unknowns,
+                     double *Zdd_host, double *Minv_host, void *stream) {
+    if (!ctx || !req || !n_out || block < 0) return VIE_EINVAL;
+    if (!ctx->mesh->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    HostReq H;
+    int e = prepare(ctx, req, H);
+    if (e) return e;
+    if (block >= (int)H.blk_n.size()) return fail(ctx, VIE_EINVAL, "block index out of range");
+    const int n = H.blk_n[block], off = H.blk_off[block];
+    *n_out = n;
+    if (!unknowns && !Zdd_host && !Minv_host) return VIE_OK;
+    vie::DevMesh m = dev_mesh(ctx);
+    vie::DevReq q{};
+    if ((e = upload_request(ctx, H, q, st))) return e;
+    std::vector<size_t> moff, mld;
+    const size_t ldz = ((size_t)ctx->mesh->topo.N + 3) / 4 * 4;
+    if (ctx->opt.precision == VIE_FP64) {
+        if ((e = fill<double>(ctx, m, q, false, st))) return e;
+        if ((e = factor<double>(ctx, H, moff, mld, st, nullptr))) return e;
+    } else {
+        if ((e = fill<float>(ctx, m, q, false, st))) return e;
+        if ((e = factor<float>(ctx, H, moff, mld, st, nullptr))) return e;
+    }
+    if (unknowns)
+        for (int i = 0; i < ctx->mesh->topo.N; ++i)
+            if (H.perm[i] >= off && H.perm[i] < off + n) unknowns[H.perm[i] - off] = i;
+    if (Zdd_host) {
+        const size_t sz = ctx->opt.precision == VIE_FP64 ? 8 : 4;
+        std::vector<char> row(2 * sz * (size_t)n);
+        for (int i = 0; i < n; ++i) {
+            const char *src = static_cast<const char *>(ctx->Z.p) + 2 * sz * ((size_t)(off + i) * ldz + off);
+            CK(cudaMemcpyAsync(row.data(), src, row.size(), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (size_t k = 0; k < 2 * (size_t)n; ++k)
+                Zdd_host[2 * (size_t)i * n + k] = sz == 8 ? reinterpret_cast<const double *>(row.data())[k]
+                                                          : reinterpret_cast<const float *>(row.data())[k];
+        }
+    }
+    if (Minv_host) {
+        std::vector<float> B(2 * mld[block] * (size_t)n);
+        CK(cudaMemcpyAsync(B.data(), ctx->Minv.as<float>() + 2 * moff[block], sizeof(float) * B.size(),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < 2 * n; ++k) Minv_host[2 * (size_t)i * n + k] = B[2 * (size_t)i * mld[block] + k];
+    }
+    return VIE_OK;
+}
+
+int vie_fma_peak(int device, int32_t precision, double *tflops) {
+    if (!tflops || (precision != VIE_FP64 && precision != VIE_FP32)) return VIE_EINVAL;
+    *tflops = 0;
+    if (cudaSetDevice(device) != cudaSuccess) return VIE_ECUDA;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return VIE_ECUDA;
+    int rc = VIE_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = VIE_ECUDA;
+    // launches of growing length until one runs for at least 100 ms (the short
+    // ones warm the clocks up), then three at that length: the best rate counts
+    const bool fp64 = precision == VIE_FP64;
+    int iters = fp64 ? 16 : 256, timed = 0;
+    double best = 0, flops = 0;
+    for (int k = 0; rc == VIE_OK && k < 24 && timed < 3; ++k) {
+        float ms = 0;
+        if (vie::fma_peak(fp64, iters, st, e0, e1, &flops) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = VIE_ECUDA;
+            break;
+        }
+        if (ms < 100.f) { iters *= 2; continue; }
+        best = std::max(best, flops / (ms * 1e-3) / 1e12);
+        ++timed;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    *tflops = best;
+    return rc;
 }
 
 int vie_erfcx(vie_ctx *ctx, const double *u, double *out, int32_t n, int32_t precision) {
@@ -1278,7 +1416,9 @@ const char *vie_status_str(int s) {
         case VIE_ENOMEM: return "VIE_ENOMEM";
         case VIE_ECUDA: return "VIE_ECUDA";
         case VIE_RAYLEIGH_ANOMALY: return "VIE_RAYLEIGH_ANOMALY";
+        case VIE_DEVICE_TIMEOUT: return "VIE_DEVICE_TIMEOUT";
         case VIE_BAD_MESH: return "VIE_BAD_MESH";
+        case VIE_CANCELLED: return "VIE_CANCELLED";
         case VIE_BREAKDOWN: return "VIE_BREAKDOWN";
         default: return "VIE_UNKNOWN";
     }
@@ -1295,6 +1435,10 @@ void vie_destroy(vie_ctx *ctx) {
 }  // extern "C"
 
 namespace vie {
+void set_cancel_flag(vie_ctx *ctx, const std::atomic<int> *flag) {
+    if (ctx) ctx->cancel = flag;
+}
+
 // Free the device memory of a context: its mesh (unless a solve slot shares
 // it), the request arrays and the solve buffers (Z, block inverses, Krylov
 // state).  The context stays usable: the next vie_set_mesh and vie_solve
@@ -1308,7 +1452,7 @@ void release_device_memory(vie_ctx *ctx) {
                       &ctx->perm, &ctx->pol, &ctx->orders, &ctx->stab, &ctx->ztab, &ctx->rtab, &ctx->ew,
                       &ctx->Z, &ctx->b, &ctx->x, &ctx->r, &ctx->u, &ctx->w, &ctx->V, &ctx->h, &ctx->y,
                       &ctx->Minv, &ctx->MinvH, &ctx->amax, &ctx->tcpack, &ctx->tcpack2, &ctx->status, &ctx->acc,
-                      &ctx->J, &ctx->xs,
+                      &ctx->J, &ctx->xs, &ctx->Zh, &ctx->dens,
                       &ctx->rt, &ctx->cout};
     for (DevBuf *b : bufs) b->release();
 }

@@ -38,6 +38,8 @@ struct EwaldTables {
 };
 constexpr int TAB_REAL = 1 << 16;   // flag in rect_tab: the table's G is real (real decay constant)
 constexpr int TAB_INDEX = TAB_REAL - 1;
+constexpr double FP64_XCUT = 6.0;   // Ewald truncation of the FP64 series: exp(-36) ~ 2e-16
+constexpr float FP32_XCUT = 4.2f;   // of the FP32 series and tables: exp(-17.6) ~ 2e-8
 constexpr int NSPAT = 512;    // spatial intervals
 constexpr int NZTAB = 256;    // spectral intervals
 // EwaldTables lives in device global memory, one copy per request in flight, so

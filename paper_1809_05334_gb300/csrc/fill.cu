@@ -887,38 +887,33 @@ cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const f
 // the Ewald series -- lives in the file-scope array below, which every GPU
 // that loads this library holds until the process exits.
 // ===========================================================================
+#include <mutex>
+#include <vector>
+
 #include "../../include/vie.h"
 
 namespace vie {
 
-constexpr int NOALLOC_MAX_TAB = 96;   // distinct Floquet decay constants the scratch can hold
-// whole 16-byte units: the spatial table after it is read with 16-byte loads
-constexpr size_t NOALLOC_EW_FLOAT2 = (sizeof(EwaldTables) + 15) / 16 * 2;
-constexpr size_t NOALLOC_FLOAT2 = NOALLOC_EW_FLOAT2 + 2 * NSPAT + (size_t)NOALLOC_MAX_TAB * NZTAB * 4;
-// Ewald parameter block (~49 KB), spatial table (4*NSPAT floats), spectral tables
-// (float2): about 0.85 MB in total
-static __device__ __align__(256) float2 g_noalloc_scratch[NOALLOC_FLOAT2];
-
-namespace {
-
-constexpr int NOALLOC_MAX_DEVICES = 64;
-float2 *g_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
-bool g_ready[NOALLOC_MAX_DEVICES] = {};
-
-// Ewald parameters and tables of one incidence (FP64 and tabulated FP32 paths),
-// the same series and truncations as the solver's.
-int noalloc_tables(double lambda, double theta, double phi, double a, double b, double z_extent, bool fp64,
-                   EwaldTables &E) {
-    const double k0 = 2.0 * M_PI / lambda;
-    const double kx = k0 * std::sin(theta) * std::cos(phi), ky = k0 * std::sin(theta) * std::sin(phi);
+// Ewald parameters and tables of one incidence (Sec. 2.2, Eq. (3)-(4)): the
+// splitting parameter, the lattice images and Floquet modes inside the cut of
+// the FP64 (fp64) or FP32 series, the limit of the regularised image term, the
+// rectangle of Floquet orders and the distinct decay constants of the FP32
+// tables (z_extent = the largest |dz| they must cover).  `orders` (may be null)
+// receives the propagating orders [n][4] (k_tx, k_ty, k_z, 1 for (0,0)).  The
+// solver and the allocation-free entry point both build their tables here.
+// Returns VIE_OK, VIE_RAYLEIGH_ANOMALY (a Floquet order at grazing) or
+// VIE_EINVAL (a table would overflow), with *why set.
+int build_ewald_tables(double a, double b, double k0, double kx, double ky, double z_extent, bool fp64,
+                       EwaldTables &E, std::vector<double> *orders, const char **why) {
     std::memset(&E, 0, sizeof(E));
+    if (orders) orders->clear();
     E.E = ewald_split(a, b, k0, !fp64 && kx == 0.0 && ky == 0.0);
     E.bb = k0 / (2.0 * E.E);
     E.a = a;
     E.b = b;
-    E.xcut64 = 6.0;
-    E.xcut32 = 4.2f;
-    const double xc = fp64 ? 6.0 : 4.2;
+    E.xcut64 = FP64_XCUT;
+    E.xcut32 = FP32_XCUT;
+    const double xc = fp64 ? FP64_XCUT : (double)FP32_XCUT;
     const int mm = (int)std::ceil(xc / (E.E * a)) + 2, nn = (int)std::ceil(xc / (E.E * b)) + 2;
     int ni = 0;
     for (int m = -mm; m <= mm; ++m)
@@ -926,7 +921,7 @@ int noalloc_tables(double lambda, double theta, double phi, double a, double b, 
             const double dmin = std::hypot(std::max(std::abs(m) - 1, 0) * a, std::max(std::abs(n) - 1, 0) * b);
             const bool nearimg = std::abs(m) <= 1 && std::abs(n) <= 1;
             if (dmin * E.E > xc && !nearimg) continue;
-            if (ni >= MAX_IMG) return VIE_EINVAL;
+            if (ni >= MAX_IMG) { *why = "period too small for the image table"; return VIE_EINVAL; }
             const double phs = kx * m * a + ky * n * b, f = std::exp(E.bb * E.bb) / (4.0 * M_PI);
             const double v[4] = {m * a, n * b, f * std::cos(phs), f * std::sin(phs)};
             for (int q = 0; q < 4; ++q) { E.img64[ni][q] = v[q]; E.img32[ni][q] = (float)v[q]; }
@@ -941,18 +936,22 @@ int noalloc_tables(double lambda, double theta, double phi, double a, double b, 
         for (int q = -qm; q <= qm; ++q) {
             const double ktx = kx + 2 * M_PI * p / a, kty = ky + 2 * M_PI * q / b;
             const double kt2 = ktx * ktx + kty * kty, g2 = kt2 - k0 * k0;
-            if (std::fabs(g2) * std::max(a, b) * std::max(a, b) < 1e-10) return VIE_RAYLEIGH_ANOMALY;
+            if (std::fabs(g2) * std::max(a, b) * std::max(a, b) < 1e-10) {
+                *why = "a Floquet order is at grazing (Rayleigh anomaly)";
+                return VIE_RAYLEIGH_ANOMALY;
+            }
+            if (g2 < 0 && orders) orders->insert(orders->end(), {ktx, kty, std::sqrt(-g2), (p == 0 && q == 0) ? 1.0 : 0.0});
             if (std::sqrt(kt2) > 2.0 * E.E * xc + k0) continue;
-            if (nm >= MAX_MODE) return VIE_EINVAL;
+            if (nm >= MAX_MODE) { *why = "too many Floquet modes for the table"; return VIE_EINVAL; }
+            // gamma = sqrt(g2) (evanescent) or j sqrt(-g2) (propagating); 1/(4 a b gamma)
             const double gr = g2 >= 0 ? std::sqrt(g2) : 0.0, gi = g2 >= 0 ? 0.0 : std::sqrt(-g2);
-            // 1/(4 a b gamma)
             const double ir = gr / (4.0 * a * b * (gr * gr + gi * gi)), ii = -gi / (4.0 * a * b * (gr * gr + gi * gi));
             const double w8[8] = {ktx, kty, gr, gi, std::exp(-g2 / (4 * E.E * E.E)), ir, ii, 0};
             for (int c = 0; c < 8; ++c) { E.mode64[nm][c] = w8[c]; E.mode32[nm][c] = (float)w8[c]; }
             ++nm;
         }
     E.n_mode = nm;
-    {   // erfi(b) by its series, for the limit of the regularised image term
+    {   // erfi(b) by its series, for the limit R -> 0 of the regularised image term
         double term = E.bb, sum = E.bb;
         for (int n = 1; n < 200; ++n) {
             term *= E.bb * E.bb / n;
@@ -963,7 +962,8 @@ int noalloc_tables(double lambda, double theta, double phi, double a, double b, 
         const double erfi = 2.0 / std::sqrt(M_PI) * sum;
         E.reg0_re = (E.E / (4 * M_PI)) * (2 * E.bb * erfi - 2.0 / std::sqrt(M_PI) * std::exp(E.bb * E.bb));
     }
-    const double xc32 = 4.2, zr = std::max(z_extent, 1e-6) * (1.0 + 1e-6);
+    // tabulated FP32 path: the truncation of the FP32 series
+    const double xc32 = FP32_XCUT, zr = std::max(z_extent, 1e-6) * (1.0 + 1e-6);
     E.xs_max = (float)(xc32 + 0.5);
     E.xs_inv_h = (float)(NSPAT / (xc32 + 0.5));
     E.z_max = (float)zr;
@@ -974,7 +974,10 @@ int noalloc_tables(double lambda, double theta, double phi, double a, double b, 
     E.ky = (float)ky;
     E.step_x = (float)(2 * M_PI / a);
     E.step_y = (float)(2 * M_PI / b);
-    if (!mode_rect(kx, ky, a, b, 2.0 * E.E * xc32 + k0, E.p0, E.np, E.q0, E.nq)) return VIE_EINVAL;
+    if (!mode_rect(kx, ky, a, b, 2.0 * E.E * xc32 + k0, E.p0, E.np, E.q0, E.nq)) {
+        *why = "too many Floquet modes for the table";
+        return VIE_EINVAL;
+    }
     E.sym = (kx == 0.0 && ky == 0.0 && 2 * E.p0 + E.np == 1 && 2 * E.q0 + E.nq == 1) ? 1 : 0;
     int nt = 0;
     double g2s[MAX_MODE];
@@ -998,11 +1001,26 @@ int noalloc_tables(double lambda, double theta, double phi, double a, double b, 
                 E.tab_ig[found][1] = -gi / (4.0 * a * b * (gr * gr + gi * gi));
                 E.tab_pre[found] = std::exp(-g2 / (4 * E.E * E.E));
             }
-            E.rect_tab[idx] = found;
+            // bit 16 marks a real decay constant (evanescent mode): its G is real
+            E.rect_tab[idx] = found | (g2s[found] > 0 ? TAB_REAL : 0);
         }
     E.n_tab = nt;
     return VIE_OK;
 }
+
+constexpr int NOALLOC_MAX_TAB = 96;   // distinct Floquet decay constants the scratch can hold
+// whole 16-byte units: the spatial table after it is read with 16-byte loads
+constexpr size_t NOALLOC_EW_FLOAT2 = (sizeof(EwaldTables) + 15) / 16 * 2;
+constexpr size_t NOALLOC_FLOAT2 = NOALLOC_EW_FLOAT2 + 2 * NSPAT + (size_t)NOALLOC_MAX_TAB * NZTAB * 4;
+// Ewald parameter block (~49 KB), spatial table (4*NSPAT floats), spectral tables
+// (float2): about 0.85 MB in total
+static __device__ __align__(256) float2 g_noalloc_scratch[NOALLOC_FLOAT2];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;                                   // guards the per-device set-up below
+float2 *g_scratch_ptr[NOALLOC_MAX_DEVICES] = {};           // device address of the array, per device
 
 }  // namespace
 }  // namespace vie
@@ -1018,25 +1036,35 @@ extern "C" int vie_green_noalloc(double lambda_nm, double theta, double phi, dou
     if (precision != VIE_FP64 && precision != VIE_FP32) return VIE_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return VIE_ECUDA;
-    if (!g_ready[dev]) {
-        // one-time set-up on this device (the device is current): Weideman
-        // constants and the device address of the scratch array
-        if (upload_constants() != cudaSuccess) return VIE_ECUDA;
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VIE_ECUDA;
-        g_scratch_ptr[dev] = static_cast<float2 *>(p);
-        g_ready[dev] = true;
+    float2 *base = nullptr;
+    {
+        // one-time set-up per device, with the device current, under one lock
+        // across threads: the library's constant tables (the same once-per-device
+        // upload that vie_create does, so a device whose solves are running is
+        // never written again) and the device address of the scratch array
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_scratch_ptr[dev]) {
+            if (upload_device_constants(dev) != cudaSuccess) return VIE_ECUDA;
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VIE_ECUDA;
+            g_scratch_ptr[dev] = static_cast<float2 *>(p);
+        }
+        base = g_scratch_ptr[dev];
     }
     if (n == 0) return VIE_OK;
     static thread_local EwaldTables tabs;
-    const int rc = noalloc_tables(lambda_nm, theta, phi, period_a, period_b, z_extent, precision == VIE_FP64, tabs);
+    const double k0 = 2.0 * M_PI / lambda_nm;
+    const char *why = "";
+    const int rc = build_ewald_tables(period_a, period_b, k0, k0 * std::sin(theta) * std::cos(phi),
+                                      k0 * std::sin(theta) * std::sin(phi), z_extent, precision == VIE_FP64, tabs,
+                                      nullptr, &why);
     if (rc != VIE_OK) return rc;
     if (precision == VIE_FP32 && tabs.n_tab > NOALLOC_MAX_TAB) return VIE_EINVAL;   // scratch too small
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    EwaldTables *ewd = reinterpret_cast<EwaldTables *>(g_scratch_ptr[dev]);
+    EwaldTables *ewd = reinterpret_cast<EwaldTables *>(base);
     if (upload_ewald(ewd, tabs, st) != cudaSuccess) return VIE_ECUDA;
-    float *stab = reinterpret_cast<float *>(g_scratch_ptr[dev] + NOALLOC_EW_FLOAT2);
-    float2 *ztab = g_scratch_ptr[dev] + NOALLOC_EW_FLOAT2 + 2 * NSPAT;
+    float *stab = reinterpret_cast<float *>(base + NOALLOC_EW_FLOAT2);
+    float2 *ztab = base + NOALLOC_EW_FLOAT2 + 2 * NSPAT;
     if (precision == VIE_FP32 && launch_build_tables(ewd, stab, ztab, tabs.n_tab, st) != cudaSuccess) return VIE_ECUDA;
     if (launch_green(d_dev, out_dev, n, precision == VIE_FP64, stab, ztab, ewd, make_ewald_f32(tabs), st) !=
         cudaSuccess)

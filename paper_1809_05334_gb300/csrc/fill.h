@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 #include "ewald_params.h"
 #include "vie_internal.h"
@@ -86,6 +87,14 @@ void tet_rule2(double (*pts)[4], double *w);
 void tri_rule2(double (*pts)[3], double *w);
 
 cudaError_t upload_constants();
+// The library's constant tables (quadrature weights, Faddeeva coefficients)
+// written to `device` (the current device) once per process under a lock:
+// later calls return at once, so constant memory that running solves read is
+// never written again.  Returns the CUDA error of the first upload, if any.
+cudaError_t upload_device_constants(int device);
+// Ewald parameters and tables of one incidence (fill.cu); status as vie_status
+int build_ewald_tables(double a, double b, double k0, double kx, double ky, double z_extent, bool fp64,
+                       EwaldTables &E, std::vector<double> *orders, const char **why);
 cudaError_t upload_ewald(EwaldTables *dev, const EwaldTables &t, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, double *b, cudaStream_t st,

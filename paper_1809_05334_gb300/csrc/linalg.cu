@@ -5,6 +5,7 @@
 // Layouts: complex interleaved (re, im).  A matrix is `rows` rows of `ld`
 // complex entries (ld a multiple of 4, zero padded).  Vectors with two
 // right-hand sides are [n][2] complex.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -22,6 +23,16 @@ template <typename T> struct V2;
 template <> struct V2<float> { using t = float4; };
 template <> struct V2<double> { using t = double2; };
 template <> struct V2<__half> { using t = uint4; };   // four complex FP16 entries
+template <> struct V2<__nv_bfloat16> { using t = uint4; };   // four complex BF16 entries
+
+// one complex 16-bit entry (two halves of a 32-bit word) widened to FP32
+template <typename T> __device__ __forceinline__ float2 widen2(uint32_t w);
+template <> __device__ __forceinline__ float2 widen2<__half>(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+template <> __device__ __forceinline__ float2 widen2<__nv_bfloat16>(uint32_t w) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+}
 
 // ---------------------------------------------------------------------------
 // matvec: y[r] = alpha sum_c A[r][c] x[c] (+ y[r] if ACCUM) for rows [0, rows),
@@ -86,7 +97,7 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
                     TA zr, zi;
                     if constexpr (VEC == 4) {
                         const uint32_t *wv = reinterpret_cast<const uint32_t *>(&z[i]);
-                        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&wv[u]));
+                        const float2 f = widen2<TZ>(wv[u]);
                         zr = TA(f.x);
                         zi = TA(f.y);
                     } else if constexpr (VEC == 2) {
@@ -159,6 +170,8 @@ template cudaError_t matvec<float, float, float>(const float *, size_t, int, int
 template cudaError_t matvec<__half, float, float>(const __half *, size_t, int, int, const float *, float *, float, bool, cudaStream_t);
 template cudaError_t matvec<__half, double, double>(const __half *, size_t, int, int, const double *, double *, double, bool,
                                                     cudaStream_t);
+template cudaError_t matvec<__nv_bfloat16, float, float>(const __nv_bfloat16 *, size_t, int, int, const float *, float *,
+                                                         float, bool, cudaStream_t);
 
 // largest |Re|, |Im| of a block, as the bit pattern of a non-negative float
 // (for those the integer order is the float order, so atomicMax applies)
@@ -174,6 +187,17 @@ __global__ void k_absmax(const float *__restrict__ A, size_t count, unsigned *ou
 __global__ void k_to_half(const float *__restrict__ A, size_t count, float scale, __half *__restrict__ B) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
         B[i] = __float2half_rn(A[i] * scale);
+}
+
+// B = A in BF16 (round to nearest), count floats (BF16 has the FP32 range: no scale)
+__global__ void k_to_bf16(const float *__restrict__ A, size_t count, __nv_bfloat16 *__restrict__ B) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        B[i] = __float2bfloat16_rn(A[i]);
+}
+
+cudaError_t to_bf16(const float *A, size_t count, __nv_bfloat16 *B, cudaStream_t st) {
+    k_to_bf16<<<1216, 256, 0, st>>>(A, count, B); ++g_launches;
+    return cudaGetLastError();
 }
 
 cudaError_t absmax(const float *A, size_t count, unsigned *out, cudaStream_t st) {
@@ -335,214 +359,48 @@ cudaError_t matvec_ds(const float *A, size_t ld, int rows, int cols, const doubl
 template cudaError_t matvec<double, double, double>(const double *, size_t, int, int, const double *, double *, double, bool, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Blocked Gauss-Jordan inversion in place, no pivoting (step k, block width w):
-//   P = A_kk^-1; A_kj <- P A_kj (j != k); A_ij <- A_ij - A_ik A_kj (i, j != k);
-//   A_ik <- -A_ik P (i != k); A_kk <- P.
+// Peak of the FP32 / FP64 FMA pipes, for the roofline of the CUDA-core
+// kernels: every thread runs FMA_CHAINS independent dependent chains of
+// fma(a, x, b) for `iters` steps (2 flops each); the chains hide the pipe
+// latency and the result is stored only if it is impossible, so nothing is
+// optimised away.
 // ---------------------------------------------------------------------------
-constexpr int GJ_NB = 32;
+constexpr int FMA_CHAINS = 8;
 
 template <typename T>
-__global__ void k_gj_diag(T *A, size_t ld, int k0, int w, int *status) {
-    // unblocked in-place Gauss-Jordan inverse of the w x w pivot block
-    __shared__ T P[GJ_NB][GJ_NB][2];
-    __shared__ T col[GJ_NB][2];
-    __shared__ T piv[2];
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i = e / w, j = e % w;
-        P[i][j][0] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
-        P[i][j][1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
+__global__ void __launch_bounds__(256) k_fma_peak(T a, T b, int iters, T *sink) {
+    T x[FMA_CHAINS];
+#pragma unroll
+    for (int c = 0; c < FMA_CHAINS; ++c) x[c] = T(threadIdx.x + c) * T(1e-3);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+#pragma unroll
+            for (int c = 0; c < FMA_CHAINS; ++c) x[c] = fma(a, x[c], b);
     }
-    __syncthreads();
-    for (int j = 0; j < w; ++j) {
-        if (threadIdx.x == 0) {
-            T pr = P[j][j][0], pi = P[j][j][1];
-            T d = pr * pr + pi * pi;
-            if (!(d > T(0)) || !isfinite(d)) atomicExch(status, 1);
-            piv[0] = pr / d;
-            piv[1] = -pi / d;
-        }
-        if (threadIdx.x < w) {   // column j before the step: f_i = a_ij
-            col[threadIdx.x][0] = P[threadIdx.x][j][0];
-            col[threadIdx.x][1] = P[threadIdx.x][j][1];
-        }
-        __syncthreads();
-        const T qr = piv[0], qi = piv[1];
-        if (threadIdx.x < w) {   // row j <- p * row j, pivot entry <- p
-            const int c = threadIdx.x;
-            if (c == j) {
-                P[j][c][0] = qr; P[j][c][1] = qi;
-            } else {
-                T ar = P[j][c][0], ai = P[j][c][1];
-                P[j][c][0] = qr * ar - qi * ai;
-                P[j][c][1] = qr * ai + qi * ar;
-            }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-            const int i = e / w, c = e % w;
-            if (i == j) continue;
-            const T fr = col[i][0], fi = col[i][1];
-            if (c == j) {            // a_ij <- -f_i p
-                P[i][c][0] = -(fr * qr - fi * qi);
-                P[i][c][1] = -(fr * qi + fi * qr);
-            } else {                 // a_ic <- a_ic - f_i a_jc(new)
-                const T br = P[j][c][0], bi = P[j][c][1];
-                P[i][c][0] -= fr * br - fi * bi;
-                P[i][c][1] -= fr * bi + fi * br;
-            }
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i = e / w, j = e % w;
-        A[2 * ((size_t)(k0 + i) * ld + k0 + j)] = P[i][j][0];
-        A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1] = P[i][j][1];
-    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < FMA_CHAINS; ++c) s += x[c];
+    if (s == T(-1.2345e-29)) sink[blockIdx.x] = s;
 }
 
-// row panel: A_kj <- P A_kj for columns j outside the pivot block (thread per column)
-template <typename T>
-__global__ void k_gj_row(T *A, size_t ld, int n, int k0, int w) {
-    __shared__ T P[GJ_NB][GJ_NB][2];
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i = e / w, j = e % w;
-        P[i][j][0] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
-        P[i][j][1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
-    }
-    __syncthreads();
-    int jj = blockIdx.x * blockDim.x + threadIdx.x;
-    if (jj >= n - w) return;
-    const int j = jj < k0 ? jj : jj + w;
-    T cr[GJ_NB], ci[GJ_NB];
-    for (int i = 0; i < w; ++i) {
-        cr[i] = A[2 * ((size_t)(k0 + i) * ld + j)];
-        ci[i] = A[2 * ((size_t)(k0 + i) * ld + j) + 1];
-    }
-    for (int i = 0; i < w; ++i) {
-        T sr = 0, si = 0;
-        for (int c = 0; c < w; ++c) {
-            sr += P[i][c][0] * cr[c] - P[i][c][1] * ci[c];
-            si += P[i][c][0] * ci[c] + P[i][c][1] * cr[c];
-        }
-        A[2 * ((size_t)(k0 + i) * ld + j)] = sr;
-        A[2 * ((size_t)(k0 + i) * ld + j) + 1] = si;
-    }
-}
-
-// trailing update A_ij -= A_ik A_kj for i, j outside the pivot block.
-// 64 x 64 output tile per CTA, 256 threads, 4 x 4 complex outputs per thread.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gj_update(T *A, size_t ld, int n, int k0, int w) {
-    __shared__ T Ls[64][GJ_NB + 1][2];   // A_ik tile: 64 rows x w
-    __shared__ T Us[GJ_NB][64 + 1][2];   // A_kj tile: w x 64 cols
-    const int m = n - w;
-    const int ti = blockIdx.y * 64, tj = blockIdx.x * 64;
-    for (int e = threadIdx.x; e < 64 * w; e += 256) {
-        int i = e / w, c = e % w;
-        int ii = ti + i;
-        T vr = 0, vi = 0;
-        if (ii < m) {
-            int r = ii < k0 ? ii : ii + w;
-            vr = A[2 * ((size_t)r * ld + k0 + c)];
-            vi = A[2 * ((size_t)r * ld + k0 + c) + 1];
-        }
-        Ls[i][c][0] = vr; Ls[i][c][1] = vi;
-    }
-    for (int e = threadIdx.x; e < 64 * w; e += 256) {
-        int c = e / 64, j = e % 64;
-        int jj = tj + j;
-        T vr = 0, vi = 0;
-        if (jj < m) {
-            int col = jj < k0 ? jj : jj + w;
-            vr = A[2 * ((size_t)(k0 + c) * ld + col)];
-            vi = A[2 * ((size_t)(k0 + c) * ld + col) + 1];
-        }
-        Us[c][j][0] = vr; Us[c][j][1] = vi;
-    }
-    __syncthreads();
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    T ar[4][4], ai[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) { ar[a][b] = 0; ai[a][b] = 0; }
-    for (int c = 0; c < w; ++c) {
-        T lr[4], li[4], ur[4], ui[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) { lr[a] = Ls[ty + 16 * a][c][0]; li[a] = Ls[ty + 16 * a][c][1]; }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) { ur[b] = Us[c][tx + 16 * b][0]; ui[b] = Us[c][tx + 16 * b][1]; }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                ar[a][b] = fma(lr[a], ur[b], fma(-li[a], ui[b], ar[a][b]));
-                ai[a][b] = fma(lr[a], ui[b], fma(li[a], ur[b], ai[a][b]));
-            }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        int ii = ti + ty + 16 * a;
-        if (ii >= m) continue;
-        int r = ii < k0 ? ii : ii + w;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            int jj = tj + tx + 16 * b;
-            if (jj >= m) continue;
-            int col = jj < k0 ? jj : jj + w;
-            size_t o = 2 * ((size_t)r * ld + col);
-            A[o] -= ar[a][b];
-            A[o + 1] -= ai[a][b];
-        }
-    }
-}
-
-// column panel: A_ik <- -A_ik P for rows i outside the pivot block (thread per row)
-template <typename T>
-__global__ void k_gj_col(T *A, size_t ld, int n, int k0, int w) {
-    __shared__ T P[GJ_NB][GJ_NB][2];
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i = e / w, j = e % w;
-        P[i][j][0] = A[2 * ((size_t)(k0 + i) * ld + k0 + j)];
-        P[i][j][1] = A[2 * ((size_t)(k0 + i) * ld + k0 + j) + 1];
-    }
-    __syncthreads();
-    int ii = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ii >= n - w) return;
-    const int r = ii < k0 ? ii : ii + w;
-    T vr[GJ_NB], vi[GJ_NB];
-    for (int c = 0; c < w; ++c) {
-        vr[c] = A[2 * ((size_t)r * ld + k0 + c)];
-        vi[c] = A[2 * ((size_t)r * ld + k0 + c) + 1];
-    }
-    for (int j = 0; j < w; ++j) {
-        T sr = 0, si = 0;
-        for (int c = 0; c < w; ++c) {
-            sr += vr[c] * P[c][j][0] - vi[c] * P[c][j][1];
-            si += vr[c] * P[c][j][1] + vi[c] * P[c][j][0];
-        }
-        A[2 * ((size_t)r * ld + k0 + j)] = -sr;
-        A[2 * ((size_t)r * ld + k0 + j) + 1] = -si;
-    }
-}
-
-template <typename T>
-cudaError_t gj_invert(T *A, size_t ld, int n, int *status, cudaStream_t st) {
-    for (int k0 = 0; k0 < n; k0 += GJ_NB) {
-        const int w = (n - k0 < GJ_NB) ? n - k0 : GJ_NB;
-        k_gj_diag<T><<<1, 256, 0, st>>>(A, ld, k0, w, status); ++g_launches;
-        const int m = n - w;
-        if (m > 0) {
-            k_gj_row<T><<<(m + 127) / 128, 128, 0, st>>>(A, ld, n, k0, w); ++g_launches;
-            dim3 g((m + 63) / 64, (m + 63) / 64);
-            k_gj_update<T><<<g, 256, 0, st>>>(A, ld, n, k0, w); ++g_launches;
-            k_gj_col<T><<<(m + 127) / 128, 128, 0, st>>>(A, ld, n, k0, w); ++g_launches;
-        }
-    }
+cudaError_t fma_peak(bool fp64, int iters, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, double *flops) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fma_peak<double>, 256, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fma_peak<float>, 256, 0);
+    if (e != cudaSuccess) return e;
+    const int grid = sms * std::max(per, 1);
+    *flops = 2.0 * grid * 256.0 * iters * 16.0 * FMA_CHAINS;
+    cudaEventRecord(e0, st);
+    if (fp64) k_fma_peak<double><<<grid, 256, 0, st>>>(0.999999, 1e-7, iters, nullptr);
+    else k_fma_peak<float><<<grid, 256, 0, st>>>(0.9999f, 1e-4f, iters, nullptr);
+    ++g_launches;
+    cudaEventRecord(e1, st);
     return cudaGetLastError();
 }
-template cudaError_t gj_invert<float>(float *, size_t, int, int *, cudaStream_t);
-template cudaError_t gj_invert<double>(double *, size_t, int, int *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Gauss-Jordan with 512-wide outer pivot blocks and tensor-core products
@@ -591,7 +449,7 @@ __global__ void __launch_bounds__(GJ_W * GJ_DG) k_gj_diag_w(float *A, size_t ld,
         const float dr = (p00.x * p11.x - p00.y * p11.y) - (p01.x * p10.x - p01.y * p10.y);
         const float di = (p00.x * p11.y + p00.y * p11.x) - (p01.x * p10.y + p01.y * p10.x);
         const float dd = dr * dr + di * di;
-        if (threadIdx.x == 0 && (!(dd > 0.f) || !isfinite(dd))) atomicExch(status, 1);
+        if (threadIdx.x == 0 && (!(dd > 0.f) || !isfinite(dd))) atomicOr(status, 1);
         const float rd = __frcp_rn(dd);
         const float er = dr * rd, ei = -di * rd;   // 1 / det
         auto cm = [](float ar, float ai, float br, float bi) { return make_float2(ar * br - ai * bi, ar * bi + ai * br); };

@@ -1,5 +1,6 @@
 // Dense complex linear algebra used by the solve (see linalg.cu).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
@@ -18,8 +19,6 @@ cudaError_t matvec_ds(const float *A, size_t ld, int rows, int cols, const doubl
 template <typename TZ, typename TX, typename TA>
 cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *y, TA alpha, bool accumulate,
                    cudaStream_t st);
-template <typename T>
-cudaError_t gj_invert(T *A, size_t ld, int n, int *status, cudaStream_t st);
 // CUDA-event timing of selected launches (optional)
 struct KernelTimer {
     cudaEvent_t (*alloc)(void *) = nullptr;   // returns the next event of the caller's pool
@@ -34,18 +33,26 @@ struct KernelTimer {
         flops.push_back(f);
     }
 };
-// the same inversion with 512-wide outer pivot blocks and the tcgen05
-// products (FP16 operands with power-of-two scales, FP32 accumulation);
+// In-place inversion of an n x n complex FP32 block (no pivoting) by blocked
+// Gauss-Jordan with 512-wide outer pivot blocks and the tcgen05 products
+// (FP16 operands with power-of-two scales, FP32 accumulation); *status gets
+// bit 0 for a zero or non-finite pivot and bit 1 for a bounded device wait
+// that ran out;
 // `pack` is device scratch of gj_pack_bytes(n) bytes (the packed operands and
 // their scale words), aux a second stream of the caller (look-ahead); the work
 // is complete on st when the last call returns on it
 size_t gj_pack_bytes(int n);
 cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cudaStream_t st, cudaStream_t aux,
                          KernelTimer *kt = nullptr);
+// one launch of the FMA-loop peak kernel (FP32 or FP64), events e0/e1 around
+// it on st; *flops = its floating-point operations
+cudaError_t fma_peak(bool fp64, int iters, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, double *flops);
 // *out (zeroed by the caller) <- max |A[i]| over count floats, as float bits
 cudaError_t absmax(const float *A, size_t count, unsigned *out, cudaStream_t st);
 // B = scale A in FP16, count floats
 cudaError_t to_half(const float *A, size_t count, float scale, __half *B, cudaStream_t st);
+// B = A in BF16, count floats
+cudaError_t to_bf16(const float *A, size_t count, __nv_bfloat16 *B, cudaStream_t st);
 template <typename TS, typename TD>
 cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st);
 template <typename TV>

@@ -36,8 +36,10 @@ __device__ void tet_beta(const DevMesh &m, const DevReq &q, const double *x, int
     }
 }
 
+// absorbed fraction of tetrahedron t (Eq. (7), normalised), summed per domain
+// into acc[p][domain]; also stored per tetrahedron in dens[p][t] if dens is set
 __global__ void k_absorb(DevMesh m, DevReq q, const double *x, const int32_t *dom, double *acc,
-                         int n_dom, double norm) {
+                         int n_dom, double norm, double *dens) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.nt) return;
     cx<double> beta[2][4];
@@ -63,7 +65,9 @@ __global__ void k_absorb(DevMesh m, DevReq q, const double *x, const int32_t *do
                 cx<double> bi = ie * beta[p][i], bj = ie * beta[p][j];
                 e2 += G * (bi.re * bj.re + bi.im * bj.im);
             }
-        atomicAdd(acc + p * n_dom + dom[t], norm * imeps * e2);
+        const double a_t = norm * imeps * e2;
+        atomicAdd(acc + p * n_dom + dom[t], a_t);
+        if (dens) dens[(size_t)p * m.nt + t] = a_t;
     }
 }
 
@@ -146,10 +150,10 @@ __global__ void k_unpermute(const double *x, const int32_t *perm, int n, double 
 
 cudaError_t launch_post(const DevMesh &m, const DevReq &q, const double *x, const int32_t *dom, int n_dom,
                         double norm, const double *orders, int n_orders, double a, double b, double kz00,
-                        const double *pol_dev, double *acc, double *J, double *rt, cudaStream_t st) {
+                        const double *pol_dev, double *acc, double *J, double *rt, double *dens, cudaStream_t st) {
     cudaMemsetAsync(acc, 0, sizeof(double) * 2 * n_dom, st);
     cudaMemsetAsync(J, 0, sizeof(double) * 24 * n_orders, st);
-    k_absorb<<<(m.nt + 127) / 128, 128, 0, st>>>(m, q, x, dom, acc, n_dom, norm); ++g_launches;
+    k_absorb<<<(m.nt + 127) / 128, 128, 0, st>>>(m, q, x, dom, acc, n_dom, norm, dens); ++g_launches;
     k_project<<<(m.nt + 127) / 128, 128, 0, st>>>(m, q, x, orders, n_orders, J); ++g_launches;
     k_rt<<<1, 32, 0, st>>>(orders, n_orders, J, q.k0, a, b, kz00, pol_dev, rt); ++g_launches;
     return cudaGetLastError();

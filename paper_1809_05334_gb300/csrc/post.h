@@ -10,7 +10,7 @@ namespace vie {
 cudaError_t upload_post_constants();
 cudaError_t launch_post(const DevMesh &m, const DevReq &q, const double *x, const int32_t *dom, int n_dom,
                         double norm, const double *orders, int n_orders, double a, double b, double kz00,
-                        const double *pol_dev, double *acc, double *J, double *rt, cudaStream_t st);
+                        const double *pol_dev, double *acc, double *J, double *rt, double *dens, cudaStream_t st);
 cudaError_t launch_unpermute(const double *x, const int32_t *perm, int n, double *out, cudaStream_t st);
 
 }  // namespace vie

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -46,6 +47,7 @@ struct Job {
     size_t footprint = 0;
     int passed = 0;          // times a later request was admitted before this one
     bool done = false;
+    std::atomic<int> cancel{0};   // set by vie_server_cancel while the request runs
     vie_result res{};
     clk::time_point t_submit, t_start, t_end;
 };
@@ -87,6 +89,7 @@ size_t mesh_footprint(const vie_mesh &m, const vie_options &opt) {
     const size_t sz = opt.precision == VIE_FP64 ? 8 : 4;
     const size_t mres = (size_t)std::max(2, opt.restart);
     size_t b = 2 * sz * ld * N;                          // Z
+    if (opt.precision == VIE_FP16 || opt.precision == VIE_BF16) b += 2 * 2 * ld * N;   // its 16-bit copy
     b += 8 * ld * N;                                     // block inverses (FP32 complex), bounded by N^2
     b += 2 * vie::gj_pack_bytes((int)N);                 // packing scratch of the inversion (two blocks at once)
     b += sz * 4 * N * (mres + 3) + 8 * 4 * N * 4;        // Krylov basis and vectors, x, r, b, coefficients
@@ -109,7 +112,7 @@ struct vie_server {
     std::vector<size_t> held;   // bytes each slot holds or has reserved
     size_t reserved = 0, peak_reserved = 0;
     uint64_t next_ticket = 1;
-    int64_t submitted = 0, completed = 0, rejected = 0, running = 0, max_running = 0;
+    int64_t submitted = 0, completed = 0, rejected = 0, running = 0, max_running = 0, cancelled = 0;
     bool stop = false;
 
     // index in the queue of the request slot k may take now, or -1
@@ -173,7 +176,11 @@ struct vie_server {
                 rc = vie_set_mesh(ctx, j->mesh.verts, j->mesh.n_verts, j->mesh.tets, j->mesh.n_tets,
                                   j->mesh.tet_domain, j->mesh.n_domains, j->mesh.period_a, j->mesh.period_b,
                                   j->mesh.active_domain);
-            if (rc == VIE_OK) rc = vie_solve(ctx, &j->req, &res, st);
+            if (rc == VIE_OK) {
+                vie::set_cancel_flag(ctx, &j->cancel);
+                rc = vie_solve(ctx, &j->req, &res, st);
+                vie::set_cancel_flag(ctx, nullptr);
+            }
             res.status = rc;
             {
                 std::lock_guard<std::mutex> lock(mu);
@@ -191,6 +198,7 @@ struct vie_server {
                 std::vector<int32_t>().swap(j->dom);
                 running--;
                 completed++;
+                if (rc == VIE_CANCELLED) cancelled++;
             }
             cv_done.notify_all();
             cv_work.notify_all();   // memory may have been released for a waiting request
@@ -277,6 +285,30 @@ int vie_server_poll(vie_server *s, uint64_t ticket, vie_result *res, int32_t wai
     return VIE_OK;
 }
 
+int vie_server_cancel(vie_server *s, uint64_t ticket) {
+    if (!s) return VIE_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return VIE_EINVAL;
+    Job *j = it->second.get();
+    if (j->done) return VIE_OK;   // finished first: it keeps its result
+    auto q = std::find(s->queue.begin(), s->queue.end(), j);
+    if (q != s->queue.end()) {    // still queued: never runs
+        s->queue.erase(q);
+        j->t_start = j->t_end = clk::now();
+        j->res = vie_result{};
+        j->res.status = VIE_CANCELLED;
+        j->res.t_latency_ms = std::chrono::duration<double, std::milli>(j->t_end - j->t_submit).count();
+        j->done = true;
+        s->cancelled++;
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+        return VIE_OK;
+    }
+    j->cancel.store(1);           // running: the solve stops at its next check
+    return VIE_OK;
+}
+
 int vie_server_get_stats(vie_server *s, vie_server_stats *out) {
     if (!s || !out) return VIE_EINVAL;
     std::lock_guard<std::mutex> lock(s->mu);
@@ -289,6 +321,7 @@ int vie_server_get_stats(vie_server *s, vie_server_stats *out) {
     out->budget_bytes = (int64_t)s->budget;
     out->reserved_bytes = (int64_t)s->reserved;
     out->peak_reserved_bytes = (int64_t)s->peak_reserved;
+    out->cancelled = s->cancelled;
     return VIE_OK;
 }
 

@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tma_load_2d(sB + s * TC_B_BYTES, &tmB, kc * TC_KCHUNK, 2 * tx * TC_TN, full + s);
             }
         }
-        if (!ok) atomicExch(err, 2);
+        if (!ok) atomicOr(err, 2);
         // the loads issued last into each stage have landed before the CTA leaves
         for (int s = 0; s < TC_STAGES; ++s) {
             const int uses = it / TC_STAGES + (s < it % TC_STAGES ? 1 : 0);
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             last_bar = accfull + b;
             last_par = (uint32_t)((tl / 2) & 1);
         }
-        if (!ok) atomicExch(err, 2);
+        if (!ok) atomicOr(err, 2);
         // the MMAs issued last have finished before the tensor memory is released
         if (last_bar) mbar_wait(last_bar, last_par);
     } else if (warp == 2 && lane == 0) {
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tma_load_2d(sC + s * TC_C_BYTES, &tmC, 2 * gc0 + cc * 32, gr0, cfull + s);
             }
         }
-        if (!ok) atomicExch(err, 2);
+        if (!ok) atomicOr(err, 2);
         for (int s = 0; s < TC_CSLOTS; ++s) {
             const int uses = ci / TC_CSLOTS + (s < ci % TC_CSLOTS ? 1 : 0);
             if (uses > 0) mbar_wait(cfull + s, (uint32_t)((uses - 1) & 1));
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(accempty + b);
         }
-        if (!ok && lane == 0) atomicExch(err, 2);
+        if (!ok && lane == 0) atomicOr(err, 2);
         if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

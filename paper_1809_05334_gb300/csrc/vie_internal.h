@@ -1,5 +1,6 @@
 // Internal host/device declarations of the periodic SWG VIE library.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -19,6 +20,9 @@ constexpr double NEAR_MARGIN = 1e-9;
 struct vie_ctx;
 namespace vie {
 void release_device_memory(vie_ctx *ctx);
+// A flag the solves of ctx poll between phases and at every GMRES iteration;
+// once it is non-zero the solve returns VIE_CANCELLED (nullptr: none)
+void set_cancel_flag(vie_ctx *ctx, const std::atomic<int> *flag);
 
 // kernel launches issued by this host thread (every launch site increments it;
 // a solve reports the difference across its own work)

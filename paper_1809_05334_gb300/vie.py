@@ -14,29 +14,32 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvie.so")
 MAX_DOMAINS = 8
 
-VIE_FP64, VIE_FP32 = 0, 1
+VIE_FP64, VIE_FP32, VIE_FP16, VIE_BF16 = 0, 1, 2, 3
 VIE_PENDING = 2
+VIE_CANCELLED = -7
 STATUS = {0: "VIE_OK", 1: "VIE_NOT_CONVERGED", 2: "VIE_PENDING", -1: "VIE_EINVAL", -2: "VIE_ENOMEM", -3: "VIE_ECUDA",
-          -4: "VIE_RAYLEIGH_ANOMALY", -6: "VIE_BAD_MESH", -8: "VIE_BREAKDOWN"}
+          -4: "VIE_RAYLEIGH_ANOMALY", -5: "VIE_DEVICE_TIMEOUT", -6: "VIE_BAD_MESH", -7: "VIE_CANCELLED",
+          -8: "VIE_BREAKDOWN"}
 
 # every symbol include/vie.h declares
 EXPORTS = ["vie_default_options", "vie_create", "vie_set_options", "vie_set_mesh", "vie_num_unknowns",
            "vie_solve", "vie_fill_matrix", "vie_fill_matrix_prec", "vie_erfcx", "vie_green",
            "vie_status_str", "vie_last_error", "vie_destroy", "vie_green_noalloc", "vie_solve_batch",
            "vie_server_create", "vie_server_submit", "vie_server_poll", "vie_server_get_stats",
-           "vie_server_destroy"]
+           "vie_server_destroy", "vie_server_cancel", "vie_domain_block", "vie_fma_peak"]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("use_precond", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("precond_block_max", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
     _fields_ = [("lambda_nm", ctypes.c_double), ("theta", ctypes.c_double), ("phi", ctypes.c_double),
                 ("eps", ctypes.c_double * (2 * MAX_DOMAINS)), ("coeffs_out", ctypes.c_void_p),
-                ("coeffs_on_device", ctypes.c_int32)]
+                ("coeffs_on_device", ctypes.c_int32), ("density_on_device", ctypes.c_int32),
+                ("density_out", ctypes.c_void_p)]
 
 
 class Result(ctypes.Structure):
@@ -65,7 +68,7 @@ class Mesh(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "rejected", "queued", "running",
                                               "max_running", "budget_bytes", "reserved_bytes",
-                                              "peak_reserved_bytes")]
+                                              "peak_reserved_bytes", "cancelled")]
 
 
 _LIB = None
@@ -108,8 +111,21 @@ def load():
     lib.vie_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
     lib.vie_server_destroy.argtypes = [P]
     lib.vie_server_destroy.restype = None
+    lib.vie_server_cancel.argtypes = [P, ctypes.c_uint64]
+    lib.vie_domain_block.argtypes = [P, ctypes.POINTER(Request), I, ctypes.POINTER(I), P, P, P, P]
+    lib.vie_fma_peak.argtypes = [ctypes.c_int, I, ctypes.POINTER(D)]
     _LIB = lib
     return lib
+
+
+def fma_peak(device=0, precision=VIE_FP32):
+    """Measured FP32 / FP64 FMA peak of the device in TFLOP/s (vie_fma_peak)."""
+    lib = load()
+    out = ctypes.c_double(0.0)
+    rc = lib.vie_fma_peak(int(device), int(precision), ctypes.byref(out))
+    if rc != 0:
+        raise VIEError(rc, "vie_fma_peak failed")
+    return float(out.value)
 
 
 class VIEError(RuntimeError):
@@ -126,7 +142,7 @@ class Solver:
     """One library context on one GPU (vie_create ... vie_destroy)."""
 
     def __init__(self, device=0, precision=VIE_FP32, use_precond=True, restart=100, max_iter=1000,
-                 tol=1e-6, inner_tol=3e-6, timing=False):
+                 tol=1e-6, inner_tol=3e-6, timing=False, precond_block_max=0):
         self.lib = load()
         self.opt = Options()
         self.lib.vie_default_options(ctypes.byref(self.opt))
@@ -134,11 +150,13 @@ class Solver:
         self.opt.restart, self.opt.max_iter = int(restart), int(max_iter)
         self.opt.tol, self.opt.inner_tol = float(tol), float(inner_tol)
         self.opt.timing = int(bool(timing))
+        self.opt.precond_block_max = int(precond_block_max)
         self.ctx = ctypes.c_void_p()
         rc = self.lib.vie_create(ctypes.byref(self.ctx), int(device), ctypes.byref(self.opt))
         if rc != 0:
             raise VIEError(rc, "vie_create failed (is a CUDA GPU present?)")
         self.n_domains = 0
+        self.n_tets = 0
 
     def _check(self, rc, allow_positive=False):
         if rc < 0 or (rc > 0 and not allow_positive):
@@ -155,6 +173,7 @@ class Solver:
         self._tets = np.ascontiguousarray(cell.tets, dtype=np.int32)
         self._dom = np.ascontiguousarray(cell.tet_domain, dtype=np.int32)
         self.n_domains = int(cell.n_domains)
+        self.n_tets = len(self._tets)
         self._check(self.lib.vie_set_mesh(self.ctx, _ptr(self._verts), len(self._verts), _ptr(self._tets),
                                           len(self._tets), _ptr(self._dom), self.n_domains,
                                           float(cell.period_a), float(cell.period_b), int(cell.active_domain)))
@@ -170,8 +189,9 @@ class Solver:
             r.eps[2 * d], r.eps[2 * d + 1] = e.real, e.imag
         return r
 
-    def solve(self, lam, theta=0.0, phi=0.0, eps=(), coeffs=False, stream=None):
-        """Solve at one incidence; returns a dict of absorbed fractions, R, T, residuals, timings."""
+    def solve(self, lam, theta=0.0, phi=0.0, eps=(), coeffs=False, stream=None, density=False):
+        """Solve at one incidence; returns a dict of absorbed fractions, R, T, residuals, timings
+        (and, with density=True, the per-tetrahedron absorbed fractions [2, n_tets] as "density")."""
         req = self.request(lam, theta, phi, eps)
         out = None
         if coeffs is not False and coeffs is not None:
@@ -180,11 +200,18 @@ class Solver:
             else:
                 out = np.zeros((self.num_unknowns(), 2), dtype=np.complex128)
             req.coeffs_out = out.ctypes.data
+        dens = None
+        if density:
+            dens = np.zeros((2, self.n_tets), dtype=np.float64)
+            req.density_out = dens.ctypes.data
         res = Result()
         rc = self.lib.vie_solve(self.ctx, ctypes.byref(req), ctypes.byref(res),
                                 ctypes.c_void_p(stream) if stream else None)
         self._check(rc, allow_positive=True)
-        return self._result(res, rc, out)
+        r = self._result(res, rc, out)
+        if density:
+            r["density"] = dens
+        return r
 
     def _result(self, res, rc, out=None):
         nd = self.n_domains
@@ -251,6 +278,28 @@ class Solver:
         req = self.request(lam, theta, phi, eps)
         self._check(self.lib.vie_fill_matrix_prec(self.ctx, ctypes.byref(req), _ptr(Z), None))
         return Z
+
+    def block_size(self, lam, theta=0.0, phi=0.0, eps=(), block=0):
+        """Size of domain block `block` of Eq. (5) for this request (no fill)."""
+        req = self.request(lam, theta, phi, eps)
+        n = ctypes.c_int32(0)
+        self._check(self.lib.vie_domain_block(self.ctx, ctypes.byref(req), int(block), ctypes.byref(n),
+                                              None, None, None, None))
+        return int(n.value)
+
+    def domain_block(self, lam, theta=0.0, phi=0.0, eps=(), block=0):
+        """(unknowns [n], Z_dd [n,n], computed inverse [n,n]) of domain block `block`
+        of Eq. (5)-(6), as vie_solve inverts it (vie_domain_block)."""
+        req = self.request(lam, theta, phi, eps)
+        n = ctypes.c_int32(0)
+        self._check(self.lib.vie_domain_block(self.ctx, ctypes.byref(req), int(block), ctypes.byref(n),
+                                              None, None, None, None))
+        idx = np.zeros(n.value, dtype=np.int32)
+        Z = np.zeros((n.value, n.value), dtype=np.complex128)
+        M = np.zeros((n.value, n.value), dtype=np.complex128)
+        self._check(self.lib.vie_domain_block(self.ctx, ctypes.byref(req), int(block), ctypes.byref(n),
+                                              _ptr(idx), _ptr(Z), _ptr(M), None))
+        return idx, Z, M
 
     def erfcx(self, u, precision=VIE_FP64):
         u = np.ascontiguousarray(u, dtype=np.complex128)
@@ -334,6 +383,13 @@ class Server:
                     t_fill_ms=res.t_fill_ms, t_factor_ms=res.t_factor_ms, t_solve_ms=res.t_solve_ms,
                     t_post_ms=res.t_post_ms, t_queue_ms=res.t_queue_ms, t_latency_ms=res.t_latency_ms,
                     n_launches=res.n_launches)
+
+    def cancel(self, ticket):
+        """Cancel a queued or running request (vie_server_cancel); it then polls
+        with status VIE_CANCELLED unless it had already finished."""
+        rc = self.lib.vie_server_cancel(self.s, ctypes.c_uint64(ticket))
+        if rc != 0:
+            raise VIEError(rc, "vie_server_cancel failed")
 
     def stats(self):
         st = ServerStats()

@@ -29,8 +29,8 @@ def test_struct_layout_matches_header():
     from paper_1809_05334_gb300 import vie
     # vie_options: 4 int32 + 2 double + 2 int32
     assert ctypes.sizeof(vie.Options) == 4 * 4 + 2 * 8 + 2 * 4
-    # vie_request: 3 double + 16 double + pointer + int32 (+ padding)
-    assert ctypes.sizeof(vie.Request) == 3 * 8 + 16 * 8 + 8 + 8
+    # vie_request: 3 double + 16 double + pointer + 2 int32 + pointer
+    assert ctypes.sizeof(vie.Request) == 3 * 8 + 16 * 8 + 8 + 8 + 8
     assert vie.Result.absorbed.offset % 8 == 0
 
 
@@ -67,6 +67,8 @@ def test_status_strings_and_no_gpu_error():
     from paper_1809_05334_gb300 import vie
     lib = vie.load()
     assert lib.vie_status_str(-4) == b"VIE_RAYLEIGH_ANOMALY"
+    for code, name in vie.STATUS.items():
+        assert lib.vie_status_str(code).decode() == name
     assert lib.vie_status_str(12345) == b"VIE_UNKNOWN"
     assert lib.vie_last_error(None) == b""
     import torch

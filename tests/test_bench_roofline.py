@@ -18,16 +18,16 @@ def _last(far_ms=65.0, tc_ms=40.0, mv_ms=50.0, pc_ms=23.7):
 
 
 def test_dominant_kernel_is_the_largest_device_time():
-    dom, allr = bench.roofline(_last(), N, PEAKS, True, N_TETS)
+    dom, allr = bench.roofline(_last(), N, PEAKS, 1, N_TETS)
     assert set(allr) == {"k_far_tt", "k_tc_update", "k_matvec"}
     assert dom["kernel"] == "k_matvec"               # 50 + 23.7 ms > 65 ms > 40 ms
     assert math.isclose(dom["total_ms"], 73.7)
-    dom2, _ = bench.roofline(_last(far_ms=90.0), N, PEAKS, True, N_TETS)
+    dom2, _ = bench.roofline(_last(far_ms=90.0), N, PEAKS, 1, N_TETS)
     assert dom2["kernel"] == "k_far_tt"
 
 
 def test_matvec_bytes_and_fraction():
-    _, allr = bench.roofline(_last(), N, PEAKS, True, N_TETS)
+    _, allr = bench.roofline(_last(), N, PEAKS, 1, N_TETS)
     m = allr["k_matvec"]
     ld = (N + 3) // 4 * 4
     per_z = N * ld * 8 + N * 2 * 8 * 2            # FP32 Z and the two complex vectors
@@ -37,12 +37,12 @@ def test_matvec_bytes_and_fraction():
     assert math.isclose(m["frac"], ach / 6794.5, rel_tol=1e-12)
     assert m["bound"] == "hbm" and m["unit"] == "GB/s"
     assert m["traffic"] == bench.MATVEC_Z_TRAFFIC   # captured on this workload only
-    _, other = bench.roofline(_last(), 8910, PEAKS, True, 4374)
+    _, other = bench.roofline(_last(), 8910, PEAKS, 1, 4374)
     assert other["k_matvec"]["traffic"] is None
 
 
 def test_far_kernel_against_the_issue_rate():
-    _, allr = bench.roofline(_last(), N, PEAKS, True, N_TETS)
+    _, allr = bench.roofline(_last(), N, PEAKS, 1, N_TETS)
     f = allr["k_far_tt"]
     vals = 16.0 * N_TETS * N_TETS
     peak = 152 * 4 * 2070e6 / 1e9                   # G warp instructions / s
@@ -53,7 +53,7 @@ def test_far_kernel_against_the_issue_rate():
 
 
 def test_products_take_the_binding_roof():
-    _, allr = bench.roofline(_last(), N, PEAKS, True, N_TETS)
+    _, allr = bench.roofline(_last(), N, PEAKS, 1, N_TETS)
     t = allr["k_tc_update"]
     t_hbm = 1.49e11 / 6794.5e9
     t_tc = 3.7e13 / 1719.1e12
@@ -61,7 +61,18 @@ def test_products_take_the_binding_roof():
     # a flop-heavier record binds on the tensor rate
     last = _last()
     last["k_tc_flops"] = 3.0e14
-    _, allr2 = bench.roofline(last, N, PEAKS, True, N_TETS)
+    _, allr2 = bench.roofline(last, N, PEAKS, 1, N_TETS)
     t2 = allr2["k_tc_update"]
     assert t2["bound"] == "tensor" and t2["unit"] == "TFLOP/s"
     assert math.isclose(t2["frac"], 3.0e14 / 40e-3 / 1e12 / 1719.1, rel_tol=1e-12)
+
+
+def test_matvec_bytes_follow_the_precision_of_the_products():
+    """FP16 / BF16 Z: the GMRES products read 4 bytes per complex entry, FP32 8, FP64 16."""
+    import bench
+    got = {}
+    for prec in (0, 1, 2, 3):
+        _, allr = bench.roofline(_last(), N, PEAKS, prec, N_TETS)
+        got[prec] = allr["k_matvec"]["algorithmic_bytes_per_z_product"]
+    ld = (N + 3) // 4 * 4
+    assert got[1] - got[2] == N * ld * 4 and got[2] == got[3] and got[0] - got[1] > N * ld * 8 - 1

@@ -107,3 +107,36 @@ def test_server_poll_pending_and_unknown_ticket():
             srv.poll(t, wait_ms=0)          # a ticket is forgotten once its result is read
     finally:
         srv.close()
+
+
+def test_server_cancel_queued_and_running():
+    """vie_server_cancel: with one slot, a request queued behind a running one
+    never runs and polls as VIE_CANCELLED; the running one, cancelled while it
+    runs, stops at its next check (VIE_CANCELLED) unless it finished first;
+    a finished request keeps its result; an unknown ticket is an error."""
+    import time
+    big = cellgen.config_sweep_geometry()
+    small = cellgen.small_cells()["slab_3x3x1"]
+    srv = vie.Server(n_slots=1, precision=vie.VIE_FP32, tol=1e-6)
+    try:
+        t_run, _ = srv.submit(big, 500.0, 0.2, 0.0, big.eps(500.0))
+        t_queued, _ = srv.submit(small, 520.0, 0.0, 0.0, small.eps(520.0))
+        t_done, _ = srv.submit(small, 520.0, 0.0, 0.0, small.eps(520.0))
+        for _ in range(2000):                       # wait until the first request runs
+            if srv.stats()["running"] == 1:
+                break
+            time.sleep(0.005)
+        srv.cancel(t_queued)
+        srv.cancel(t_run)
+        r_run = srv.poll(t_run, wait_ms=-1)
+        r_queued = srv.poll(t_queued, wait_ms=-1)
+        r_done = srv.poll(t_done, wait_ms=-1)
+        assert r_queued["status"] == vie.VIE_CANCELLED
+        assert r_run["status"] in (vie.VIE_CANCELLED, 0)
+        assert r_done["status"] == 0
+        with pytest.raises(vie.VIEError):
+            srv.cancel(123456789)
+        st = srv.stats()
+        assert st["cancelled"] >= 1 and st["queued"] == 0 and st["running"] == 0
+    finally:
+        srv.close()

@@ -34,27 +34,37 @@ def test_green_noalloc_matches_allocating_entry(precision, rtol):
         pytest.skip("needs a GPU")
     a, b, thick = 180.0, 150.0, 60.0
     cell = cellgen.slab_cell(2, 2, 1, a, b, thick, (2.0, 0.1))
+    incidences = ((520.0, 0.0, 0.0), (430.0, 0.6, 0.3))
     s = vie.Solver(precision=vie.VIE_FP32)
+    d = _points(a, b, thick)
     try:
         s.set_mesh(cell)
-        lib = vie.load()
-        for lam, th, ph in ((520.0, 0.0, 0.0), (430.0, 0.6, 0.3)):
-            d = _points(a, b, thick)
-            ref = s.green(d, lam, th, ph, precision)
-            # the allocating entry covers |dz| up to max(mesh thickness, max|dz|)
-            z_ext = max(thick, float(np.max(np.abs(d[:, 2]))))
-            d_dev = torch.from_numpy(np.ascontiguousarray(d)).cuda()
-            out_dev = torch.zeros(2 * len(d), dtype=torch.float64, device="cuda")
-            stream = torch.cuda.current_stream()
-            rc = lib.vie_green_noalloc(lam, th, ph, a, b, z_ext, ctypes.c_void_p(d_dev.data_ptr()),
-                                       ctypes.c_void_p(out_dev.data_ptr()), len(d), precision,
-                                       ctypes.c_void_p(stream.cuda_stream))
-            assert rc == 0
-            torch.cuda.synchronize()
-            got = out_dev.cpu().numpy().view(np.complex128)
-            assert np.max(np.abs(got - ref) / np.abs(ref)) < rtol
+        refs = [s.green(d, lam, th, ph, precision) for lam, th, ph in incidences]
     finally:
         s.close()
+    lib = vie.load()
+    # the allocating entry covers |dz| up to max(mesh thickness, max|dz|)
+    z_ext = max(thick, float(np.max(np.abs(d[:, 2]))))
+    d_dev = torch.from_numpy(np.ascontiguousarray(d)).cuda()
+    out_dev = torch.zeros(2 * len(d), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def call(lam, th, ph):
+        rc = lib.vie_green_noalloc(lam, th, ph, a, b, z_ext, ctypes.c_void_p(d_dev.data_ptr()),
+                                   ctypes.c_void_p(out_dev.data_ptr()), len(d), precision,
+                                   ctypes.c_void_p(stream.cuda_stream))
+        torch.cuda.synchronize()
+        return rc
+
+    assert call(*incidences[1]) == 0          # first call: the one-time set-up on this device
+    free0 = torch.cuda.mem_get_info()[0]
+    for (lam, th, ph), ref in zip(incidences, refs):   # two calls in a row, different incidences
+        out_dev.zero_()
+        assert call(lam, th, ph) == 0
+        got = out_dev.cpu().numpy().view(np.complex128)
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < rtol
+    # no device memory was taken by the calls
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_green_noalloc_rejects_bad_arguments():
