@@ -79,8 +79,10 @@ typedef struct {
     int32_t restart;       /* GMRES restart length (default 100)                   */
     int32_t max_iter;      /* total GMRES iterations over all restarts (default 1000)*/
     double  tol;           /* target FP64 relative residual ||b - Z x|| / ||b||     */
-    double  inner_tol;     /* FP32 inner GMRES tolerance of each refinement sweep
-                              (default 3e-6; never below 1e-6)                   */
+    double  inner_tol;     /* relative reduction of the preconditioned residual at
+                              which a refinement sweep's inner GMRES stops (never
+                              below 1e-6); 0 (default): 3e-6 for VIE_FP32, 1e-3
+                              for VIE_FP16, 8e-3 for VIE_BF16                     */
     int32_t timing;        /* 1: record CUDA events around the main kernels and
                               report their device times in vie_result.k_* (adds
                               no work, only events on the solve stream)          */
@@ -157,7 +159,8 @@ typedef struct {
     double  k_ortho_ms;
 } vie_result;
 
-/* Fill *opt with defaults (FP32 with refinement, preconditioner on, tol 1e-6). */
+/* Fill *opt with defaults (FP32 with refinement, preconditioner on, tol 1e-6,
+   restart 100, max_iter 1000, inner_tol 0 = per precision). */
 void vie_default_options(vie_options *opt);
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).

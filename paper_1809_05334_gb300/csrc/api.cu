@@ -433,10 +433,12 @@ int timed_precond(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &mof
 
 bool cancelled(const vie_ctx *ctx) { return ctx->cancel && ctx->cancel->load(std::memory_order_relaxed) != 0; }
 
-// Inner-sweep tolerance floors of the 16-bit copies of Z: a sweep whose
-// products read Z rounded to 2^-11 (FP16) or 2^-8 (BF16) relative cannot
-// reduce the FP64 residual of the FP32 Z much further than about that, so the
-// sweep stops there and the next refinement step continues.
+// Default inner-sweep tolerances (options.inner_tol = 0): FP32 products
+// 3e-6; the 16-bit copies of Z, rounded to 2^-11 (FP16) or 2^-8 (BF16)
+// relative, cannot reduce the FP64 residual of the FP32 Z much further than
+// about that in one sweep, so their sweeps stop there and the next refinement
+// step continues.
+constexpr double INNER_TOL_FP32 = 3e-6;
 constexpr double INNER_TOL_FP16 = 1e-3;
 constexpr double INNER_TOL_BF16 = 8e-3;
 
@@ -453,8 +455,10 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
     const bool pre = ctx->opt.use_precond != 0;
     const double tol = ctx->opt.tol;
     const int zin = std::is_same<TV, float>::value ? (ctx->opt.precision == VIE_FP16 ? 1 : ctx->opt.precision == VIE_BF16 ? 2 : 0) : 0;
-    const double inner_floor = zin == 1 ? INNER_TOL_FP16 : zin == 2 ? INNER_TOL_BF16 : 1e-6;
-    const double inner_tol = std::is_same<TV, float>::value ? std::max(ctx->opt.inner_tol, inner_floor) : tol * 0.1;
+    const double inner_def = zin == 1 ? INNER_TOL_FP16 : zin == 2 ? INNER_TOL_BF16 : INNER_TOL_FP32;
+    const double inner_tol = std::is_same<TV, float>::value
+                                 ? std::max(ctx->opt.inner_tol > 0 ? ctx->opt.inner_tol : inner_def, 1e-6)
+                                 : tol * 0.1;
     const size_t vs = 4 * (size_t)N;     // stride of one basis vector (two rhs)
     CK(ctx->x.ensure(sizeof(double) * vs));
     CK(ctx->r.ensure(sizeof(double) * vs));
@@ -905,7 +909,7 @@ void default_opts(vie_options *o) {
     o->restart = 100;
     o->max_iter = 1000;
     o->tol = 1e-6;
-    o->inner_tol = 3e-6;
+    o->inner_tol = 0;   // per precision (3e-6 FP32, 1e-3 FP16, 8e-3 BF16)
     o->timing = 0;
     o->precond_block_max = 0;
 }
@@ -956,7 +960,8 @@ int vie_create(vie_ctx **out, int device, const vie_options *opt) {
 int vie_set_options(vie_ctx *ctx, const vie_options *opt) {
     if (!ctx || !opt) return VIE_EINVAL;
     if (opt->precision < VIE_FP64 || opt->precision > VIE_BF16) return fail(ctx, VIE_EINVAL, "unknown precision");
-    if (opt->restart < 2 || opt->max_iter < 1 || !(opt->tol > 0) || opt->precond_block_max < 0)
+    if (opt->restart < 2 || opt->max_iter < 1 || !(opt->tol > 0) || opt->precond_block_max < 0 ||
+        !(opt->inner_tol >= 0))
         return fail(ctx, VIE_EINVAL, "bad solver options");
     ctx->opt = *opt;
     return VIE_OK;

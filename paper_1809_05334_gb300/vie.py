@@ -142,7 +142,7 @@ class Solver:
     """One library context on one GPU (vie_create ... vie_destroy)."""
 
     def __init__(self, device=0, precision=VIE_FP32, use_precond=True, restart=100, max_iter=1000,
-                 tol=1e-6, inner_tol=3e-6, timing=False, precond_block_max=0):
+                 tol=1e-6, inner_tol=0.0, timing=False, precond_block_max=0):
         self.lib = load()
         self.opt = Options()
         self.lib.vie_default_options(ctypes.byref(self.opt))
@@ -332,7 +332,7 @@ class Server:
     HBM footprint."""
 
     def __init__(self, device=0, n_slots=3, hbm_budget_bytes=0, precision=VIE_FP32, use_precond=True,
-                 restart=100, max_iter=1000, tol=1e-6, inner_tol=3e-6):
+                 restart=100, max_iter=1000, tol=1e-6, inner_tol=0.0):
         self.lib = load()
         opt = Options()
         self.lib.vie_default_options(ctypes.byref(opt))
