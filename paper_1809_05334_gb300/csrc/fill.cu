@@ -258,14 +258,18 @@ __device__ void scatter_tt(const DevMesh &m, const DevReq &q, T *Z, size_t N, in
 // point pairs gives g_p(x_a - y_b) for the block (t, s) and g_p(y_b - x_a) for
 // the block (s, t) (the reversed pair's moments swap the roles of the offsets).
 // SYM: normal incidence (the tabulated path's symmetric mode sum, gm = gp).
+// Eight CTAs per SM for the FP32 tables (64 registers; the kernel is
+// issue-bound and its fixed-latency waits need the extra warps), six for FP64.
 template <typename T, bool SYM>
-__global__ void __launch_bounds__(128, 6) k_far_tt(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 6)
+    k_far_tt(DevMesh m, const __grid_constant__ DevReq q, T *Z, size_t N) {
     extern __shared__ float smem_tab[];
     const int t = blockIdx.y;
     if ((int)(blockIdx.x * blockDim.x + blockDim.x) <= t) return;   // the whole block is below the diagonal
     const float *stab = stage_stab<T>(q, smem_tab);
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= m.nt || s < t) return;
+    const int s0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = s0 < m.nt && s0 >= t;   // lanes off the pair range stay until the warp's image mask is formed
+    const int s = live ? s0 : t;
     // near images of this pair: their static part is integrated separately
     const unsigned sub = m.mk_tt[(size_t)t * m.nt + s];
     const T *ft = m.far<T>(t);
@@ -287,7 +291,15 @@ __global__ void __launch_bounds__(128, 6) k_far_tt(DevMesh m, const __grid_const
             rs = fmaxf(rs, sqrtf(vx * vx + vy * vy + vz * vz));
         }
         imask = image_mask(q.ef, float(ft[12] - fs[12]), float(ft[13] - fs[13]), float(ft[14] - fs[14]), rt + rs);
+        // one image list for the whole warp (the union of its pairs' lists): the
+        // image index is warp-uniform, so the image loop runs on the uniform
+        // datapath and its table entries are broadcast loads
+        if (!live) imask = 0ull;
+        const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)imask);
+        const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(imask >> 32));
+        imask = ((unsigned long long)hi << 32) | lo;
     }
+    if (!live) return;
     for (int a = 0; a < 4; ++a) {
         const T xa[3] = {ft[3 * a], ft[3 * a + 1], ft[3 * a + 2]};
         const T ra[3] = {xa[0] - ft[12], xa[1] - ft[13], xa[2] - ft[14]};
@@ -298,19 +310,28 @@ __global__ void __launch_bounds__(128, 6) k_far_tt(DevMesh m, const __grid_const
             Green<T>::template eval2<SYM>(xa[0] - yb[0], xa[1] - yb[1], xa[2] - yb[2], sub, stab, q.ztab, q.ew,
                                           q.ef, g, gr, q.rtab, imask);
             g = wgt * g;
-            gr = wgt * gr;
             const T rr = ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2];
             mo.S = mo.S + g;
-            mr.S = mr.S + gr;
             for (int d = 0; d < 3; ++d) {
                 mo.A[d] = mo.A[d] + ra[d] * g;
                 mo.B[d] = mo.B[d] + rb[d] * g;
-                mr.A[d] = mr.A[d] + rb[d] * gr;
-                mr.B[d] = mr.B[d] + ra[d] * gr;
             }
             mo.C = mo.C + rr * g;
-            mr.C = mr.C + rr * gr;
+            if (!SYM) {
+                gr = wgt * gr;
+                mr.S = mr.S + gr;
+                for (int d = 0; d < 3; ++d) {
+                    mr.A[d] = mr.A[d] + rb[d] * gr;
+                    mr.B[d] = mr.B[d] + ra[d] * gr;
+                }
+                mr.C = mr.C + rr * gr;
+            }
         }
+    }
+    if (SYM) {   // g_p(-d) = g_p(d): the reversed pair's moments swap A and B
+        mr.S = mo.S;
+        mr.C = mo.C;
+        for (int d = 0; d < 3; ++d) { mr.A[d] = mo.B[d]; mr.B[d] = mo.A[d]; }
     }
     scatter_tt<T>(m, q, Z, N, t, s, mo);
     if (s != t) scatter_tt<T>(m, q, Z, N, s, t, mr);
