@@ -235,6 +235,15 @@ int vie_fill_matrix_prec(vie_ctx *ctx, const vie_request *req, double *Z_host, v
 int vie_domain_block(vie_ctx *ctx, const vie_request *req, int32_t block, int32_t *n_out, int32_t *unknowns,
                      double *Zdd, double *Minv, void *stream);
 
+/* Check of the failure path of the device's bounded waits (the paper has no
+   counterpart): one thread waits, with the bounded mbarrier wait the
+   tensor-core block inversion uses, on a barrier that gets its arrival
+   (arrive = 1) or never does (arrive = 0), for at most `polls` polls
+   (1..1000000).  Returns VIE_OK when the wait completed, VIE_DEVICE_TIMEOUT
+   when it ran out (the kernel gave up and returned; the device stays usable),
+   VIE_EINVAL or VIE_ECUDA. */
+int vie_check_device_wait(int device, int32_t arrive, int32_t polls);
+
 /* Measured peak of the FP32 (precision VIE_FP32) or FP64 (VIE_FP64) fused
    multiply-add pipes of `device`, in TFLOP/s, from a kernel of independent FMA
    chains on every SM (the best of three launches of at least 100 ms each):

@@ -1335,6 +1335,20 @@ int vie_domain_block(vie_ctx *ctx, const vie_request *req, int32_t block, int32_
     return VIE_OK;
 }
 
+int vie_check_device_wait(int device, int32_t arrive, int32_t polls) {
+    if (polls < 1 || polls > 1000000) return VIE_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return VIE_ECUDA;
+    int *status = nullptr;
+    if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return VIE_ENOMEM;
+    int host = 0, rc = VIE_OK;
+    if (cudaMemset(status, 0, sizeof(int)) != cudaSuccess || vie::wait_check(arrive != 0, polls, status, 0) != cudaSuccess ||
+        cudaMemcpy(&host, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = VIE_ECUDA;
+    cudaFree(status);
+    if (rc != VIE_OK) return rc;
+    return (host & 2) ? VIE_DEVICE_TIMEOUT : VIE_OK;
+}
+
 int vie_fma_peak(int device, int32_t precision, double *tflops) {
     if (!tflops || (precision != VIE_FP64 && precision != VIE_FP32)) return VIE_EINVAL;
     *tflops = 0;

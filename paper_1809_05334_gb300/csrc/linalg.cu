@@ -403,6 +403,26 @@ cudaError_t fma_peak(bool fp64, int iters, cudaStream_t st, cudaEvent_t e0, cuda
 }
 
 // ---------------------------------------------------------------------------
+// Check of the bounded mbarrier wait the tensor-core products use: one thread
+// initialises an mbarrier for one arrival, arrives on it or not, and waits on
+// its phase 0 with the same bounded wait (at most `polls` polls); a wait that
+// runs out sets bit 1 of *status, as a stalled product does.
+// ---------------------------------------------------------------------------
+__global__ void k_wait_check(int arrive, long long polls, int *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (arrive) mbar_arrive(&bar);
+    if (!mbar_wait(&bar, 0, polls)) atomicOr(status, 2);
+}
+
+cudaError_t wait_check(bool arrive, long long polls, int *status, cudaStream_t st) {
+    k_wait_check<<<1, 32, 0, st>>>(arrive ? 1 : 0, polls, status); ++g_launches;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Gauss-Jordan with 512-wide outer pivot blocks and tensor-core products
 // (FP32 matrix; FP16 operands scaled by powers of two, FP32 accumulation).
 // ---------------------------------------------------------------------------

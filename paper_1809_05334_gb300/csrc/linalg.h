@@ -44,6 +44,9 @@ struct KernelTimer {
 size_t gj_pack_bytes(int n);
 cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cudaStream_t st, cudaStream_t aux,
                          KernelTimer *kt = nullptr);
+// one bounded mbarrier wait of at most `polls` polls on a barrier that gets its
+// arrival (arrive) or never does: bit 1 of *status (device) when it runs out
+cudaError_t wait_check(bool arrive, long long polls, int *status, cudaStream_t st);
 // one launch of the FMA-loop peak kernel (FP32 or FP64), events e0/e1 around
 // it on st; *flops = its floating-point operations
 cudaError_t fma_peak(bool fp64, int iters, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, double *flops);

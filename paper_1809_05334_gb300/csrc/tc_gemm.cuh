@@ -87,8 +87,8 @@ __device__ __forceinline__ float tc_pow2(int x) { return __int_as_float((127 + x
 
 
 // bounded wait on an mbarrier phase; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
-    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long long limit = TC_WAIT_LIMIT) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

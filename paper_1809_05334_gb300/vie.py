@@ -26,7 +26,8 @@ EXPORTS = ["vie_default_options", "vie_create", "vie_set_options", "vie_set_mesh
            "vie_solve", "vie_fill_matrix", "vie_fill_matrix_prec", "vie_erfcx", "vie_green",
            "vie_status_str", "vie_last_error", "vie_destroy", "vie_green_noalloc", "vie_solve_batch",
            "vie_server_create", "vie_server_submit", "vie_server_poll", "vie_server_get_stats",
-           "vie_server_destroy", "vie_server_cancel", "vie_domain_block", "vie_fma_peak"]
+           "vie_server_destroy", "vie_server_cancel", "vie_domain_block", "vie_fma_peak",
+           "vie_check_device_wait"]
 
 
 class Options(ctypes.Structure):
@@ -114,6 +115,7 @@ def load():
     lib.vie_server_cancel.argtypes = [P, ctypes.c_uint64]
     lib.vie_domain_block.argtypes = [P, ctypes.POINTER(Request), I, ctypes.POINTER(I), P, P, P, P]
     lib.vie_fma_peak.argtypes = [ctypes.c_int, I, ctypes.POINTER(D)]
+    lib.vie_check_device_wait.argtypes = [ctypes.c_int, I, I]
     _LIB = lib
     return lib
 
@@ -126,6 +128,12 @@ def fma_peak(device=0, precision=VIE_FP32):
     if rc != 0:
         raise VIEError(rc, "vie_fma_peak failed")
     return float(out.value)
+
+
+def check_device_wait(device=0, arrive=False, polls=1000):
+    """Status of one bounded device wait on a barrier that gets its arrival or
+    never does (vie_check_device_wait): 0 (VIE_OK) or -5 (VIE_DEVICE_TIMEOUT)."""
+    return int(load().vie_check_device_wait(int(device), int(bool(arrive)), int(polls)))
 
 
 class VIEError(RuntimeError):

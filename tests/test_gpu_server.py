@@ -140,3 +140,20 @@ def test_server_cancel_queued_and_running():
         assert st["cancelled"] >= 1 and st["queued"] == 0 and st["running"] == 0
     finally:
         srv.close()
+
+
+def test_bounded_device_wait_reports_timeout_and_device_stays_usable():
+    """The failure path of the bounded device waits: a wait on a barrier that
+    nobody arrives on runs out after its poll limit and comes back as
+    VIE_DEVICE_TIMEOUT (no fault, no hang); the same wait with its arrival
+    completes; a solve afterwards still works."""
+    assert vie.check_device_wait(0, arrive=False, polls=1000) == -5
+    assert vie.check_device_wait(0, arrive=True, polls=1000) == 0
+    cell = cellgen.small_cells()["slab_3x3x1"]
+    s = vie.Solver(precision=vie.VIE_FP32, tol=1e-6)
+    try:
+        s.set_mesh(cell)
+        out = s.solve(500.0, 0.0, 0.0, cell.eps(500.0))
+    finally:
+        s.close()
+    assert out["status"] == 0
