@@ -285,3 +285,42 @@ def test_subblock_preconditioner_variant():
         assert np.max(np.abs(out["A"] - ref["A"])) <= 1e-4
     finally:
         s.close()
+
+
+# --------------------------------------------------------------------------- error paths and empty inputs
+def test_invalid_requests_are_rejected(solvers):
+    """Bad arguments come back as VIE_EINVAL (no result, no fault) and leave
+    the context usable; empty inputs are no-ops."""
+    import ctypes
+    cell = cellgen.small_cells()["slab_3x3x1"]
+    s = solvers[vie.VIE_FP32]
+    s.set_mesh(cell)
+    eps = cell.eps(500.0)
+    for lam, th, e in ((0.0, 0.0, eps), (-5.0, 0.0, eps), (500.0, np.pi / 2, eps), (500.0, 0.0, [0.0 + 0.0j])):
+        with pytest.raises(vie.VIEError) as err:
+            s.solve(lam, th, 0.0, e)
+        assert err.value.code == -1, (lam, th)
+    with pytest.raises(vie.VIEError) as err:
+        s.block_size(500.0, 0.0, 0.0, eps, block=5)
+    assert err.value.code == -1
+    with pytest.raises(vie.VIEError) as err:
+        s.set_options(precision=7)
+    assert err.value.code == -1
+    s.set_options(precision=vie.VIE_FP32)
+    assert s.solve(500.0, 0.0, 0.0, eps)["status"] == 0          # still usable
+    assert len(s.green(np.zeros((0, 3)), 500.0)) == 0              # empty evaluation
+    out, used = s.solve_batch([], [], [], [], max_slots=2)          # empty batch
+    assert out == [] and used == 0
+    fresh = vie.Solver(precision=vie.VIE_FP32)
+    try:
+        req = fresh.request(500.0, 0.0, 0.0, eps)
+        res = vie.Result()
+        assert fresh.lib.vie_solve(fresh.ctx, ctypes.byref(req), ctypes.byref(res), None) == -1   # no mesh yet
+        bad = cellgen.Cell(verts=cell.verts, tets=cell.tets, tet_domain=cell.tet_domain, n_domains=9,
+                           period_a=cell.period_a, period_b=cell.period_b, active_domain=0,
+                           domain_names=cell.domain_names * 9)
+        with pytest.raises(vie.VIEError) as err:
+            fresh.set_mesh(bad)
+        assert err.value.code == -1
+    finally:
+        fresh.close()
