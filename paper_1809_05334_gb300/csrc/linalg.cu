@@ -43,7 +43,10 @@ template <> __device__ __forceinline__ float2 widen2<__nv_bfloat16>(uint32_t w) 
 // (equal segments, 16-byte loads of A streamed with evict-first), reduce by
 // shuffles, and combine the warps' partial sums through shared memory (double
 // buffered: one barrier per row group).  x is read through L1/L2 (it is a few
-// hundred KB and every row group reuses it).
+// hundred KB and every row group reuses it).  16-bit entries carry twice the
+// products per byte, so their loop keeps the next column step's loads in
+// flight while it multiplies the current ones (80 registers, three CTAs per
+// SM); FP32 and FP64 entries rely on the unrolled loop alone.
 // ---------------------------------------------------------------------------
 constexpr int MV_ROWS = 4;
 constexpr int MV_WARPS = 8;
@@ -77,10 +80,8 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
         for (int i = 0; i < MV_ROWS; ++i)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[i][k] = TA(0);
-#pragma unroll 8
-        for (int v = v0 + lane; v < v1; v += 32) {
+        auto zload = [&](int v, typename V2<TZ>::t *z) {
             const int c = v * VEC;
-            typename V2<TZ>::t z[MV_ROWS];
 #pragma unroll
             for (int i = 0; i < MV_ROWS; ++i) {
                 if (r0 + i < re)
@@ -88,6 +89,9 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
                 else
                     z[i] = {};
             }
+        };
+        auto zuse = [&](int v, const typename V2<TZ>::t *z) {
+            const int c = v * VEC;
 #pragma unroll
             for (int u = 0; u < VEC; ++u) {
                 TA xv[4] = {TA(0), TA(0), TA(0), TA(0)};
@@ -114,6 +118,29 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
                     acc[i][2] = fma(zr, xv[2], fma(-zi, xv[3], acc[i][2]));
                     acc[i][3] = fma(zr, xv[3], fma(zi, xv[2], acc[i][3]));
                 }
+            }
+        };
+        if constexpr (VEC == 4) {   // 16-bit entries: the next column step's loads in flight during this one's products
+            typename V2<TZ>::t zc[MV_ROWS], zn[MV_ROWS];
+            int v = v0 + lane;
+            if (v < v1) zload(v, zc);
+#pragma unroll 2
+            for (; v < v1; v += 32) {
+                if (v + 32 < v1) zload(v + 32, zn);
+                else {
+#pragma unroll
+                    for (int i = 0; i < MV_ROWS; ++i) zn[i] = {};
+                }
+                zuse(v, zc);
+#pragma unroll
+                for (int i = 0; i < MV_ROWS; ++i) zc[i] = zn[i];
+            }
+        } else {
+#pragma unroll 8
+            for (int v = v0 + lane; v < v1; v += 32) {
+                typename V2<TZ>::t z[MV_ROWS];
+                zload(v, z);
+                zuse(v, z);
             }
         }
 #pragma unroll
