@@ -456,9 +456,11 @@ cudaError_t wait_check(bool arrive, long long polls, int *status, cudaStream_t s
 constexpr int GJ_W = 128;     // pivot block width (the K of the tensor-core update)
 
 // In-place Gauss-Jordan inverse of the w x w (w <= GJ_W) pivot block, held in
-// registers, two pivots per step: 512 threads, thread t owns column c = t % 128
-// and the rows g + 4q (g = t / 128, q = 0..31); the block is padded with the
-// identity up to an even width.  Step (j, j+1) with the 2 x 2 pivot block P
+// registers, two pivots per step: 512 threads; warp v owns the columns
+// c = 32 (v / 4) + lane and the rows g + 4q (g = v % 4, q = 0..31), so the four
+// warps that own a column (the pivot columns' owners do the extra work of a
+// step) sit on the four schedulers; the block is padded with the identity up
+// to an even width.  Step (j, j+1) with the 2 x 2 pivot block P
 // and rows R = A[j:j+2, :] is one update of every entry,
 //   a_ic <- a_ic - f_i0 m_0c - f_i1 m_1c,
 // m_c = P^-1 R[:, c] off the pivot columns and the matching column of P^-1 on
@@ -473,7 +475,8 @@ constexpr int GJ_RQ = GJ_W / GJ_DG;    // rows per thread
 __global__ void __launch_bounds__(GJ_W * GJ_DG) k_gj_diag_w(float *A, size_t ld, int k0, int w, int *status) {
     __shared__ float2 rowbuf[2][2][GJ_W];
     __shared__ __align__(16) float2 colbuf[2][GJ_DG][GJ_RQ][2];   // factors (f0, f1) of the pivot pair, row g + 4q
-    const int c = threadIdx.x & (GJ_W - 1), g = threadIdx.x >> 7;
+    const int wv = threadIdx.x >> 5;
+    const int c = 32 * (wv >> 2) + (threadIdx.x & 31), g = wv & (GJ_DG - 1);
     float2 a[GJ_RQ];
 #pragma unroll
     for (int q = 0; q < GJ_RQ; ++q) {
@@ -625,9 +628,11 @@ void tc_pack(cudaStream_t st, const float *A, size_t ld, const TcPanel &pa, int 
     const int big = std::max(pa.n1 * pa.w, pb.n1 * pb.w);
     const unsigned gx = (unsigned)std::max(1, std::min((big + 2047) / 2048, 2 * 152));
     k_tc_absmax<<<dim3(gx, 2), 256, 0, st>>>(A, ld, pa, pb, amax); ++g_launches;
-    k_tc_pack_a<<<(unsigned)((size_t)mp * TC_KP / 256), 256, 0, st>>>(A, ld, pa.n1, pa.c0, pa.w, pa.at, pa.skip, mp,
-                                                                       amax, Ap); ++g_launches;
-    k_tc_pack_b<<<dim3(bx, TC_KP / 32), 256, 0, st>>>(A, ld, pb.n1, pb.c0, pb.w, pb.at, pb.skip, sgn, amax + 1, Bp);
+    // only the K chunks the product reads: 32 complex K per chunk of 64 FP16
+    const int kp = std::min(TC_KP, (std::max(pa.w, pb.w) + 31) / 32 * 32);
+    k_tc_pack_a<<<(unsigned)(((size_t)mp * kp + 255) / 256), 256, 0, st>>>(A, ld, pa.n1, pa.c0, pa.w, pa.at, pa.skip,
+                                                                          mp, kp, amax, Ap); ++g_launches;
+    k_tc_pack_b<<<dim3(bx, kp / 32), 256, 0, st>>>(A, ld, pb.n1, pb.c0, pb.w, pb.at, pb.skip, sgn, amax + 1, Bp);
     ++g_launches;
 }
 

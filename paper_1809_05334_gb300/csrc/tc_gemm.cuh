@@ -160,13 +160,14 @@ __global__ void __launch_bounds__(256) k_tc_absmax(const float *__restrict__ A, 
 }
 
 // Ap[r][2k..2k+1] = s A[row(r)][col0 + k] for r < rows, k < w, with
-// row(r) = r < at ? r : r + skip; zero elsewhere up to mp rows; s from *amax.
+// row(r) = r < at ? r : r + skip; zero elsewhere up to mp rows and kp columns
+// (the K chunks a product reads); s from *amax.
 __global__ void __launch_bounds__(256) k_tc_pack_a(const float *__restrict__ A, size_t ld, int rows, int col0, int w,
-                                                   int at, int skip, int mp, const unsigned *__restrict__ amax,
+                                                   int at, int skip, int mp, int kp, const unsigned *__restrict__ amax,
                                                    __half *__restrict__ Ap) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (size_t)mp * TC_KP) return;
-    const int r = (int)(e / TC_KP), k = (int)(e % TC_KP);
+    if (e >= (size_t)mp * kp) return;
+    const int r = (int)(e / kp), k = (int)(e % kp);
     float2 v = make_float2(0.f, 0.f);
     if (r < rows && k < w) {
         const int gr = r < at ? r : r + skip;
@@ -180,7 +181,8 @@ __global__ void __launch_bounds__(256) k_tc_pack_a(const float *__restrict__ A, 
 // (k < w, j < cols, col(j) = j < at ? j : j + skip), K-major:
 //   Bp[2j][2k..] = sgn s (Re b, -Im b),  Bp[2j+1][2k..] = sgn s (Im b, Re b)
 // through a 32 x 32 shared-memory transpose (coalesced on both sides); rows up
-// to 2 * 32 * gridDim.x are written (zero beyond cols).
+// to 2 * 32 * gridDim.x and K up to 32 * gridDim.y are written (zero beyond
+// cols and w).
 __global__ void __launch_bounds__(256) k_tc_pack_b(const float *__restrict__ A, size_t ld, int cols, int row0, int w,
                                                    int at, int skip, float sgn, const unsigned *__restrict__ amax,
                                                    __half *__restrict__ Bp) {
