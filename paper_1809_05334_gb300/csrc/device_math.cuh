@@ -222,47 +222,39 @@ __device__ __forceinline__ void green_tab_impl(float dx, float dy, float dz, uns
     float s, c;
     if constexpr (SYM) {
         if (np > 0) {
+            // G_pq depends on |k_t,pq| alone, so it is even in p and in q separately:
+            // sum_pq G_pq exp(-j k_t,pq . rho) = sum_{p,q >= 0} w_p w_q G_pq cos(k_p x) cos(k_q y)
+            // (w_0 = 1, w_>0 = 2; the sine products cancel), one table evaluation per
+            // order of the quadrant; D_q = 2 cos(k_q y) and D_p by Chebyshev recurrence
             const int P = (np - 1) / 2, Q = (nq - 1) / 2;
-            sincospif(-ew.step_x * dx * 0.31830988618f, &s, &c);
-            const cx<float> sx = {c, s};
-            sincospif(-ew.step_y * dy * 0.31830988618f, &s, &c);
-            const cx<float> sy = {c, s};
-            sincospif(Q * ew.step_y * dy * 0.31830988618f, &s, &c);
-            const cx<float> ey0 = {c, s};   // exp(-j k_y,-Q dy)
-            cx<float> h = {0.f, 0.f};       // sum over the half plane of G cos(k_t . rho)
-            {   // row p = 0: G_00 once, q = 1..Q paired
-                const int row = P * nq + Q;
-                float gr, gi;
-                const int c00 = ew.rect_tab[row];
-                if (c00 >= 0) { table(c00, gr, gi); acc.re = gr; acc.im = gi; }
-                cx<float> ey = sy;
+            const float d1x = 2.f * cospif(ew.step_x * dx * 0.31830988618f);
+            const float d1y = 2.f * cospif(ew.step_y * dy * 0.31830988618f);
+            float dp_prev = 2.f, dp = d1x;   // D_0, D_1 in x
+            for (int p = 0; p <= P; ++p) {
+                const int row = (P + p) * nq + Q;
+                float rr = 0.f, ri = 0.f, gr, gi;
+                const int c0 = ew.rect_tab[row];
+                if (c0 >= 0) { table(c0, rr, ri); }
+                float dq_prev = 2.f, dq = d1y;   // D_0, D_1 in y
                 for (int q = 1; q <= Q; ++q) {
                     const int code = ew.rect_tab[row + q];
                     if (code >= 0) {
-                        if (table(code, gr, gi)) h.re = fmaf(gr, ey.re, h.re);
-                        else { h.re = fmaf(gr, ey.re, h.re); h.im = fmaf(gi, ey.re, h.im); }
+                        if (table(code, gr, gi)) rr = fmaf(dq, gr, rr);
+                        else { rr = fmaf(dq, gr, rr); ri = fmaf(dq, gi, ri); }
                     }
-                    ey = ey * sy;
+                    const float dn = fmaf(d1y, dq, -dq_prev);
+                    dq_prev = dq;
+                    dq = dn;
+                }
+                const float wp = p == 0 ? 1.f : dp;
+                acc.re = fmaf(wp, rr, acc.re);
+                acc.im = fmaf(wp, ri, acc.im);
+                if (p >= 1) {   // D_{p+1} = d1x D_p - D_{p-1}
+                    const float dn = fmaf(d1x, dp, -dp_prev);
+                    dp_prev = dp;
+                    dp = dn;
                 }
             }
-            cx<float> ex = sx;
-            for (int p = 1; p <= P; ++p) {   // rows p = 1..P, all q
-                const int row = (P + p) * nq;
-                cx<float> ey = ey0;
-                for (int q = 0; q < nq; ++q) {
-                    const int code = ew.rect_tab[row + q];
-                    if (code >= 0) {
-                        const float cs = fmaf(ex.re, ey.re, -ex.im * ey.im);   // cos(k_t . rho)
-                        float gr, gi;
-                        if (table(code, gr, gi)) h.re = fmaf(gr, cs, h.re);
-                        else { h.re = fmaf(gr, cs, h.re); h.im = fmaf(gi, cs, h.im); }
-                    }
-                    ey = ey * sy;
-                }
-                ex = ex * sx;
-            }
-            acc.re = fmaf(2.f, h.re, acc.re);
-            acc.im = fmaf(2.f, h.im, acc.im);
         }
     } else {
         sincospif(-(ew.kx + ew.p0 * ew.step_x) * dx * 0.31830988618f, &s, &c);
