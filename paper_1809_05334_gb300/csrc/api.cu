@@ -312,7 +312,7 @@ int upload_request(vie_ctx *ctx, const HostReq &H, vie::DevReq &q, cudaStream_t 
     if (g_h2d_counter) *g_h2d_counter += (int64_t)sizeof(vie::EwaldTables);
     CK(ctx->stab.ensure(sizeof(float) * 4 * vie::NSPAT));
     CK(ctx->ztab.ensure(sizeof(float2) * 4 * vie::NZTAB * std::max(H.ew.n_tab, 1)));
-    CK(ctx->rtab.ensure(sizeof(float4) * vie::NZTAB * std::max(H.ew.n_tab, 1)));
+    CK(ctx->rtab.ensure(sizeof(float4) * vie::NZTAB * (2 * (size_t)H.ew.n_tab + 1)));   // real, zero, imaginary
     CK(vie::launch_build_tables(ctx->ew.as<vie::EwaldTables>(), ctx->stab.as<float>(), ctx->ztab.as<float2>(),
                                 H.ew.n_tab, st, ctx->rtab.as<float4>()));
     q.stab = ctx->stab.as<float>();
@@ -1414,14 +1414,16 @@ int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out
     CK(vie::upload_ewald(ctx->ew.as<vie::EwaldTables>(), H.ew, st));
     CK(ctx->stab.ensure(sizeof(float) * 4 * vie::NSPAT));
     CK(ctx->ztab.ensure(sizeof(float2) * 4 * vie::NZTAB * std::max(H.ew.n_tab, 1)));
+    CK(ctx->rtab.ensure(sizeof(float4) * vie::NZTAB * (2 * (size_t)H.ew.n_tab + 1)));   // real, zero, imaginary
     CK(vie::launch_build_tables(ctx->ew.as<vie::EwaldTables>(), ctx->stab.as<float>(), ctx->ztab.as<float2>(),
-                                H.ew.n_tab, st));
+                                H.ew.n_tab, st, ctx->rtab.as<float4>()));
     DevBuf dd, dout;
     CK(dd.ensure(sizeof(double) * 3 * n));
     CK(dout.ensure(sizeof(double) * 2 * n));
     CK(cudaMemcpy(dd.p, d, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
     CK(vie::launch_green(dd.as<double>(), dout.as<double>(), n, precision == VIE_FP64, ctx->stab.as<float>(),
-                         ctx->ztab.as<float2>(), ctx->ew.as<vie::EwaldTables>(), vie::make_ewald_f32(H.ew), st));
+                         ctx->ztab.as<float2>(), ctx->ew.as<vie::EwaldTables>(), vie::make_ewald_f32(H.ew), st,
+                         ctx->rtab.as<float4>()));
     CK(cudaMemcpy(out, dout.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
     return VIE_OK;
 }

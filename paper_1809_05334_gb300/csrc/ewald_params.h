@@ -42,6 +42,14 @@ constexpr double FP64_XCUT = 6.0;   // Ewald truncation of the FP64 series: exp(
 constexpr float FP32_XCUT = 4.2f;   // of the FP32 series and tables: exp(-17.6) ~ 2e-8
 constexpr int NSPAT = 512;    // spatial intervals
 constexpr int NZTAB = 256;    // spectral intervals
+// Normal incidence short form (k_par = 0, at most 32 lattice images, every
+// Floquet order of the cut within |p|, |q| <= SQ_MAX, (0, 0) the only
+// propagating order): the order quadrant p, q >= 0 unrolled at compile time,
+// each entry naming its real spectral table (orders outside the cut name a
+// table of zeros), and the imaginary part of the (0, 0) table beside it.  The
+// real-part buffer `rtab` holds n_tab real tables, the zero table, then the
+// n_tab imaginary tables, NZTAB float4 each.
+constexpr int SQ_MAX = 4;
 // EwaldTables lives in device global memory, one copy per request in flight, so
 // independent solves can run concurrently.  The part of it that the FP32
 // tabulated evaluation reads in its inner loops travels as a kernel parameter
@@ -53,6 +61,10 @@ struct EwaldF32 {
     int near_img[9];
     int n_img, p0, np, q0, nq, sym;
     float xs_max, xs_inv_h, z_inv_h, e_mb2, Ef, kx, ky, step_x, step_y;
+    float Eih;                            // E * xs_inv_h: table abscissa per unit distance
+    int sq_pq;                            // max(P, Q) >= 1 of the short form; 0 where it does not apply
+    int sq_off[SQ_MAX + 1][SQ_MAX + 1];   // order (p, q): offset of its real table in rtab (float4 units)
+    int sq_im;                            // offset of the (0, 0) order's imaginary table in rtab
 };
 // Ewald splitting parameter: sqrt(pi / ab) balances the spatial and spectral
 // series, bounded below by k0/6 (b = k0 / 2E <= 3 keeps exp(b^2) moderate).  The
@@ -93,6 +105,29 @@ inline EwaldF32 make_ewald_f32(const EwaldTables &t) {
     f.n_img = t.n_img; f.p0 = t.p0; f.np = t.np; f.q0 = t.q0; f.nq = t.nq; f.sym = t.sym;
     f.xs_max = t.xs_max; f.xs_inv_h = t.xs_inv_h; f.z_inv_h = t.z_inv_h; f.e_mb2 = t.e_mb2; f.Ef = t.Ef;
     f.kx = t.kx; f.ky = t.ky; f.step_x = t.step_x; f.step_y = t.step_y;
+    f.Eih = t.Ef * t.xs_inv_h;
+    f.sq_pq = 0;
+    const int zero = t.n_tab * NZTAB;   // the zero table
+    for (int p = 0; p <= SQ_MAX; ++p)
+        for (int q = 0; q <= SQ_MAX; ++q) f.sq_off[p][q] = zero;
+    f.sq_im = zero;
+    // the rectangle of a symmetric request is -P..P x -Q..Q; its quadrant p, q >= 0
+    if (t.sym && t.np > 0 && t.nq > 0 && t.n_img <= 32) {
+        const int P = (t.np - 1) / 2, Q = (t.nq - 1) / 2;
+        bool ok = P <= SQ_MAX && Q <= SQ_MAX;
+        for (int p = 0; ok && p <= P; ++p)
+            for (int q = 0; ok && q <= Q; ++q) {
+                const int code = t.rect_tab[(P + p) * t.nq + (Q + q)];
+                if (code < 0) continue;
+                const int tb = code & TAB_INDEX;
+                f.sq_off[p][q] = tb * NZTAB;
+                if (!(code & TAB_REAL)) {
+                    if (p == 0 && q == 0) f.sq_im = (t.n_tab + 1 + tb) * NZTAB;
+                    else ok = false;   // another propagating order: the general form
+                }
+            }
+        if (ok) f.sq_pq = P > Q ? (P > 1 ? P : 1) : (Q > 1 ? Q : 1);
+    }
     return f;
 }
 

@@ -127,6 +127,10 @@ __global__ void k_build_tables(const EwaldTables *__restrict__ ew, float *stab, 
     }
     const int j = i - NSPAT;
     const int tb = j / NZTAB, iz = j % NZTAB;
+    if (rtab && tb == n_tab) {   // the zero table after the real tables
+        rtab[(size_t)n_tab * NZTAB + iz] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     if (tb >= n_tab) return;
     const double h = double(ew->z_max) / NZTAB;
     cx<double> G0, D0, G1, D1;
@@ -136,13 +140,16 @@ __global__ void k_build_tables(const EwaldTables *__restrict__ ew, float *stab, 
     hermite(G0.re, D0.re, G1.re, D1.re, h, cr);
     hermite(G0.im, D0.im, G1.im, D1.im, h, ci);
     for (int k = 0; k < 4; ++k) ztab[((size_t)tb * NZTAB + iz) * 4 + k] = make_float2(float(cr[k]), float(ci[k]));
-    // the real parts again, 16 bytes per interval, for the tables whose G is real
-    if (rtab) rtab[(size_t)tb * NZTAB + iz] = make_float4(float(cr[0]), float(cr[1]), float(cr[2]), float(cr[3]));
+    // the real and the imaginary parts apart, 16 bytes per interval each
+    if (rtab) {
+        rtab[(size_t)tb * NZTAB + iz] = make_float4(float(cr[0]), float(cr[1]), float(cr[2]), float(cr[3]));
+        rtab[(size_t)(n_tab + 1 + tb) * NZTAB + iz] = make_float4(float(ci[0]), float(ci[1]), float(ci[2]), float(ci[3]));
+    }
 }
 
 cudaError_t launch_build_tables(const EwaldTables *ew, float *stab, float2 *ztab, int n_tab, cudaStream_t st,
                                 float4 *rtab) {
-    const int n = NSPAT + n_tab * NZTAB;
+    const int n = NSPAT + (n_tab + (rtab ? 1 : 0)) * NZTAB;
     k_build_tables<<<(n + 127) / 128, 128, 0, st>>>(ew, stab, ztab, n_tab, rtab); ++g_launches;
     return cudaGetLastError();
 }
@@ -338,6 +345,212 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 6)
 }
 
 // ---------------------------------------------------------------------------
+// Normal incidence (k_par = 0), short form of the tabulated evaluation.  The
+// same sum as green_tab_impl's symmetric form,
+//   g_p = sum_{p,q >= 0} w_p w_q G_pq(|z|) cos(p th_x) cos(q th_y)
+//         + exp(b^2)/(4 pi) sum_i F(R_i E) / R_i,   th = 2 pi (dx / a, dy / b),
+// (w_0 = 1, w_k = 2; the static part 1/R removed on the images in regm), with
+// the order quadrant unrolled at compile time (every order of the cut has
+// |p|, |q| <= PQ; entries outside the cut are skipped on a uniform branch), the
+// images from a 32-bit warp-uniform mask, and d1 = (2 cos th_x, 2 cos th_y)
+// supplied by the caller; D_k = 2 cos(k th) by the Chebyshev recurrence
+// D_k = d1 D_{k-1} - D_{k-2}, D_0 = 2.  REG: some lane of the warp has images
+// whose static part is removed (else R > 0 on every image of every lane).
+// ---------------------------------------------------------------------------
+template <int PQ, bool REG>
+__device__ __forceinline__ float image_term(int i, float dx, float dy, float dz2, unsigned regm, const float4 *stab4,
+                                            const EwaldF32 &ef) {
+    const float x = dx + ef.img[i][0], y = dy + ef.img[i][1];
+    const float R2 = fmaf(x, x, fmaf(y, y, dz2));
+    float rinv = rsqrtf(R2);
+    if (REG) rinv = R2 > 0.f ? rinv : 0.f;   // R = 0 only on an image whose static part is removed
+    const float xu = R2 * rinv * ef.Eih;
+    const int ix = min((int)xu, NSPAT - 1);
+    const float v = xu - (float)ix;
+    const float4 c = stab4[ix];
+    const float q1 = fmaf(v, fmaf(v, c.w, c.z), c.y);
+    float val = fmaf(v, q1, c.x) * rinv;
+    if (REG && ((regm >> i) & 1u))   // (F(x) - F(0)) / R; near R = 0 from the first interval's slope
+        val = ix == 0 ? ef.Eih * q1 : fmaf(-ef.e_mb2, rinv, val);
+    return xu <= float(NSPAT) ? val : 0.f;   // beyond the table: outside the cut
+}
+
+template <int PQ, bool REG>
+__device__ __forceinline__ cx<float> green_sym_short(float dx, float dy, float dz, float2 d1, unsigned imask,
+                                                     unsigned regm, const float4 *stab4,
+                                                     const float4 *__restrict__ rtab, const EwaldF32 &ef) {
+    float Dx[PQ + 1], Dy[PQ + 1];
+    Dx[0] = 1.f;
+    Dy[0] = 1.f;
+    Dx[1] = d1.x;
+    Dy[1] = d1.y;
+#pragma unroll
+    for (int k = 2; k <= PQ; ++k) {
+        Dx[k] = fmaf(d1.x, Dx[k - 1], k == 2 ? -2.f : -Dx[k - 2]);
+        Dy[k] = fmaf(d1.y, Dy[k - 1], k == 2 ? -2.f : -Dy[k - 2]);
+    }
+    const float zu = fminf(fabsf(dz) * ef.z_inv_h, float(NZTAB));
+    const int iz = min((int)zu, NZTAB - 1);
+    const float u = zu - (float)iz;
+    const float4 *rt = rtab + iz;
+    // every entry of the quadrant, no branch: orders outside the cut read zeros
+    float ar = 0.f;
+#pragma unroll
+    for (int p = 0; p <= PQ; ++p) {
+        float rr = 0.f;
+#pragma unroll
+        for (int q = 0; q <= PQ; ++q) {
+            const float4 c = __ldg(rt + ef.sq_off[p][q]);
+            const float g = fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+            rr = q == 0 ? g : fmaf(Dy[q], g, rr);
+        }
+        ar = p == 0 ? rr : fmaf(Dx[p], rr, ar);
+    }
+    const float4 ci = __ldg(rt + ef.sq_im);
+    const float ai = fmaf(u, fmaf(u, fmaf(u, ci.w, ci.z), ci.y), ci.x);
+    // lattice images, two at a time (the mask is warp-uniform)
+    const float dz2 = dz * dz;
+    float sv = 0.f;
+    for (unsigned mk = imask; mk;) {
+        const int i0 = __ffs((int)mk) - 1;
+        mk &= mk - 1u;
+        if (mk) {
+            const int i1 = __ffs((int)mk) - 1;
+            mk &= mk - 1u;
+            const float v0 = image_term<PQ, REG>(i0, dx, dy, dz2, regm, stab4, ef);
+            const float v1 = image_term<PQ, REG>(i1, dx, dy, dz2, regm, stab4, ef);
+            sv += v0 + v1;
+        } else {
+            sv += image_term<PQ, REG>(i0, dx, dy, dz2, regm, stab4, ef);
+        }
+    }
+    ar = fmaf(ef.img[0][2], sv, ar);
+    return {ar, ai};
+}
+
+// Images (32-bit mask) that can lie inside the cut for some displacement within
+// `rad` of (cx, cy, cz); n_img <= 32.
+__device__ __forceinline__ unsigned image_mask32(const EwaldF32 &ew, float cx, float cy, float cz, float rad) {
+    const float rc = ew.xs_max / ew.Ef * 1.0001f + rad * 1.0001f + 1e-6f * (fabsf(cx) + fabsf(cy) + fabsf(cz));
+    const float rc2 = rc * rc;
+    const int n = ew.n_img;
+    unsigned m = 0u;
+    for (int i = 0; i < n; ++i) {
+        const float x = cx + ew.img[i][0], y = cy + ew.img[i][1];
+        if (x * x + y * y + cz * cz <= rc2) m |= 1u << i;
+    }
+    return m;
+}
+
+// 4 x 4 point pairs of one tetrahedron pair in the short form.  tpt: the test
+// tetrahedron's points [a] = (x_a, x_a - c) and phases (2 cos, 2 cos, 2 sin,
+// 2 sin) of 2 pi (x / a, y / b); sph (stride 128): the source points' (cos,
+// cos, sin, sin).  The moments are accumulated without the weight.
+template <int PQ, bool REG>
+__device__ __forceinline__ void far_tt_short(const float *__restrict__ fs, const float4 (*tpt)[3],
+                                             const float4 *sph, unsigned imask, unsigned regm,
+                                             const float4 *stab4, const DevReq &q, Mom<float> &mo) {
+#pragma unroll 1
+    for (int b = 0; b < 4; ++b) {
+        const float yb0 = fs[3 * b], yb1 = fs[3 * b + 1], yb2 = fs[3 * b + 2];
+        const float rb[3] = {yb0 - fs[12], yb1 - fs[13], yb2 - fs[14]};
+        const float4 pb = sph[128 * b];
+#pragma unroll 1
+        for (int a = 0; a < 4; ++a) {
+            const float4 xa = tpt[a][0], ra = tpt[a][1], pa = tpt[a][2];
+            // 2 cos(k (x_a - y_b)) = 2 cos(k x_a) cos(k y_b) + 2 sin(k x_a) sin(k y_b)
+            const float2 d1 = {fmaf(pa.x, pb.x, pa.z * pb.z), fmaf(pa.y, pb.y, pa.w * pb.w)};
+            const cx<float> g = green_sym_short<PQ, REG>(xa.x - yb0, xa.y - yb1, xa.z - yb2, d1, imask, regm,
+                                                         stab4, q.rtab, q.ef);
+            const float rr = ra.x * rb[0] + ra.y * rb[1] + ra.z * rb[2];
+            mo.S = mo.S + g;
+            cfma(mo.A[0], ra.x, g);
+            cfma(mo.A[1], ra.y, g);
+            cfma(mo.A[2], ra.z, g);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cfma(mo.B[d], rb[d], g);
+            cfma(mo.C, rr, g);
+        }
+    }
+}
+
+// Far tetrahedron pairs at normal incidence in the short form: one thread per
+// unordered pair {t, s} (s >= t) as in k_far_tt, the reversed pair's moments
+// taken from the pair's own (g_p(-d) = g_p(d)).
+#ifndef VIE_FAR_N_MINB
+#define VIE_FAR_N_MINB 6   // CTAs per SM of the normal-incidence far kernels (85 registers at 6)
+#endif
+template <int PQ>
+__global__ void __launch_bounds__(128, VIE_FAR_N_MINB) k_far_tt_n(DevMesh m, const __grid_constant__ DevReq q, float *Z, size_t N) {
+    __shared__ float4 s_tab[NSPAT];   // spatial table
+    __shared__ float4 s_sph[4 * 128];  // per thread: its source points' phases, [b][thread]
+    __shared__ float4 s_tpt[4][3];     // the test tetrahedron's points, relative points, phases times 2
+    const int t = blockIdx.y;
+    if ((int)(blockIdx.x * blockDim.x + blockDim.x) <= t) return;   // the whole block is below the diagonal
+    const EwaldF32 &ef = q.ef;
+    const float4 *gtab = reinterpret_cast<const float4 *>(q.stab);
+    for (int i = threadIdx.x; i < NSPAT; i += blockDim.x) s_tab[i] = gtab[i];
+    const float *ft = m.far<float>(t);
+    const float sx = ef.step_x * 0.31830988618f, sy = ef.step_y * 0.31830988618f;   // 2/a, 2/b
+    if (threadIdx.x < 4) {
+        const int a = threadIdx.x;
+        float sn_x, cs_x, sn_y, cs_y;
+        sincospif(sx * ft[3 * a], &sn_x, &cs_x);
+        sincospif(sy * ft[3 * a + 1], &sn_y, &cs_y);
+        s_tpt[a][0] = make_float4(ft[3 * a], ft[3 * a + 1], ft[3 * a + 2], 0.f);
+        s_tpt[a][1] = make_float4(ft[3 * a] - ft[12], ft[3 * a + 1] - ft[13], ft[3 * a + 2] - ft[14], 0.f);
+        s_tpt[a][2] = make_float4(2.f * cs_x, 2.f * cs_y, 2.f * sn_x, 2.f * sn_y);
+    }
+    const int s0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = s0 < m.nt && s0 >= t;   // lanes off the pair range stay until the warp's masks are formed
+    const int s = live ? s0 : t;
+    const float *fs = m.far<float>(s);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float sn_x, cs_x, sn_y, cs_y;
+        sincospif(sx * fs[3 * b], &sn_x, &cs_x);
+        sincospif(sy * fs[3 * b + 1], &sn_y, &cs_y);
+        s_sph[128 * b + threadIdx.x] = make_float4(cs_x, cs_y, sn_x, sn_y);
+    }
+    // images that can reach the cut from some point pair of {t, s}: every point
+    // pair lies within rt + rs of the centroid offset; one list for the warp
+    float rt = 0.f, rs = 0.f;
+    for (int a = 0; a < 4; ++a) {
+        const float ux = ft[3 * a] - ft[12], uy = ft[3 * a + 1] - ft[13], uz = ft[3 * a + 2] - ft[14];
+        const float vx = fs[3 * a] - fs[12], vy = fs[3 * a + 1] - fs[13], vz = fs[3 * a + 2] - fs[14];
+        rt = fmaxf(rt, sqrtf(ux * ux + uy * uy + uz * uz));
+        rs = fmaxf(rs, sqrtf(vx * vx + vy * vy + vz * vz));
+    }
+    unsigned imask = live ? image_mask32(ef, ft[12] - fs[12], ft[13] - fs[13], ft[14] - fs[14], rt + rs) : 0u;
+    imask = __reduce_or_sync(0xffffffffu, imask);
+    // near images of this pair: their static part is integrated separately
+    const unsigned sub = live ? (unsigned)m.mk_tt[(size_t)t * m.nt + s] : 0u;
+    unsigned regm = 0u;
+    if (sub) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if ((sub >> k) & 1u) regm |= 1u << ef.near_img[k];
+    }
+    const bool reg = __any_sync(0xffffffffu, regm != 0u);
+    __syncthreads();
+    if (!live) return;
+    Mom<float> mo, mr;
+    mo.zero();
+    if (reg) far_tt_short<PQ, true>(fs, s_tpt, s_sph + threadIdx.x, imask, regm, s_tab, q, mo);
+    else far_tt_short<PQ, false>(fs, s_tpt, s_sph + threadIdx.x, imask, regm, s_tab, q, mo);
+    const float wgt = ft[27] * fs[27];
+    mo.S = wgt * mo.S;
+    mo.C = wgt * mo.C;
+    for (int d = 0; d < 3; ++d) { mo.A[d] = wgt * mo.A[d]; mo.B[d] = wgt * mo.B[d]; }
+    // g_p(-d) = g_p(d): the reversed pair's moments swap A and B
+    mr.S = mo.S;
+    mr.C = mo.C;
+    for (int d = 0; d < 3; ++d) { mr.A[d] = mo.B[d]; mr.B[d] = mo.A[d]; }
+    scatter_tt<float>(m, q, Z, N, t, s, mo);
+    if (s != t) scatter_tt<float>(m, q, Z, N, s, t, mr);
+}
+
+// ---------------------------------------------------------------------------
 // near tetrahedron pairs: one warp per pair
 // ---------------------------------------------------------------------------
 template <typename U>
@@ -399,7 +612,7 @@ __global__ void __launch_bounds__(128) k_pr_tt(DevMesh m, const __grid_constant_
         for (int b = 0; b < 14; ++b) {
             const T *yb = ny + 4 * b;
             const T dx = xa[0] - yb[0] + dc[0], dy = xa[1] - yb[1] + dc[1], dz = xa[2] - yb[2] + dc[2];
-            const T f = yb[3] / sqrt(dx * dx + dy * dy + dz * dz);
+            const T f = yb[3] * rsqrt(dx * dx + dy * dy + dz * dz);
             f0 += f;
             fb[0] += f * yb[0];
             fb[1] += f * yb[1];
@@ -626,6 +839,92 @@ __global__ void __launch_bounds__(128) k_far_scalar(DevMesh m, const __grid_cons
     scatter_scalar<T, PK>(m, q, Z, N, x, y, S);
 }
 
+// Far scalar pairs (charge faces) at normal incidence in the short form: one
+// thread per element pair as in k_far_scalar; the x element's points and their
+// phases (times 2) staged once per block, each thread's y points' phases in
+// shared memory [b][thread].
+template <int PQ, int PK>
+__global__ void __launch_bounds__(128, VIE_FAR_N_MINB)
+    k_far_scalar_n(DevMesh m, const __grid_constant__ DevReq q, float *Z, size_t N, int nx, int ny,
+                   const uint16_t *mk) {
+    __shared__ float4 s_tab[NSPAT];
+    __shared__ float4 s_yph[4 * 128];
+    __shared__ float4 s_xpt[4][2];
+    constexpr bool XT = PKTraits<PK>::xtet, YT = PKTraits<PK>::ytet;
+    constexpr int qx = XT ? 4 : 3, qy = YT ? 4 : 3;
+    const EwaldF32 &ef = q.ef;
+    const int x = blockIdx.y;
+    const float4 *gtab = reinterpret_cast<const float4 *>(q.stab);
+    for (int i = threadIdx.x; i < NSPAT; i += blockDim.x) s_tab[i] = gtab[i];
+    // a test face is addressed by its half-function index; geometry by charge-face index
+    const float *fx = far_el<float, XT>(m, XT ? x : m.hf[x]);
+    const float sx = ef.step_x * 0.31830988618f, sy = ef.step_y * 0.31830988618f;
+    if (threadIdx.x < qx) {
+        const int a = threadIdx.x;
+        float sn_x, cs_x, sn_y, cs_y;
+        sincospif(sx * fx[3 * a], &sn_x, &cs_x);
+        sincospif(sy * fx[3 * a + 1], &sn_y, &cs_y);
+        s_xpt[a][0] = make_float4(fx[3 * a], fx[3 * a + 1], fx[3 * a + 2], 0.f);
+        s_xpt[a][1] = make_float4(2.f * cs_x, 2.f * cs_y, 2.f * sn_x, 2.f * sn_y);
+    }
+    const int y0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = y0 < ny;
+    const int y = live ? y0 : ny - 1;
+    const float *fy = far_el<float, YT>(m, y);
+#pragma unroll
+    for (int b = 0; b < qy; ++b) {
+        float sn_x, cs_x, sn_y, cs_y;
+        sincospif(sx * fy[3 * b], &sn_x, &cs_x);
+        sincospif(sy * fy[3 * b + 1], &sn_y, &cs_y);
+        s_yph[128 * b + threadIdx.x] = make_float4(cs_x, cs_y, sn_x, sn_y);
+    }
+    // images that can reach the cut from some point pair: centres and radii of the point sets
+    float c1[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < qx; ++a)
+        for (int d = 0; d < 3; ++d) c1[d] += fx[3 * a + d] / qx;
+    for (int b = 0; b < qy; ++b)
+        for (int d = 0; d < 3; ++d) c2[d] += fy[3 * b + d] / qy;
+    float r1 = 0.f, r2 = 0.f;
+    for (int a = 0; a < qx; ++a) {
+        const float ux = fx[3 * a] - c1[0], uy = fx[3 * a + 1] - c1[1], uz = fx[3 * a + 2] - c1[2];
+        r1 = fmaxf(r1, sqrtf(ux * ux + uy * uy + uz * uz));
+    }
+    for (int b = 0; b < qy; ++b) {
+        const float ux = fy[3 * b] - c2[0], uy = fy[3 * b + 1] - c2[1], uz = fy[3 * b + 2] - c2[2];
+        r2 = fmaxf(r2, sqrtf(ux * ux + uy * uy + uz * uz));
+    }
+    unsigned imask = live ? image_mask32(ef, c1[0] - c2[0], c1[1] - c2[1], c1[2] - c2[2], r1 + r2) : 0u;
+    imask = __reduce_or_sync(0xffffffffu, imask);
+    const unsigned sub = live ? (unsigned)mk[(size_t)x * ny + y] : 0u;
+    unsigned regm = 0u;
+    if (sub) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if ((sub >> k) & 1u) regm |= 1u << ef.near_img[k];
+    }
+    const bool reg = __any_sync(0xffffffffu, regm != 0u);
+    __syncthreads();
+    if (!live) return;
+    cx<float> S = {0.f, 0.f};
+#pragma unroll 1
+    for (int b = 0; b < qy; ++b) {
+        const float yb0 = fy[3 * b], yb1 = fy[3 * b + 1], yb2 = fy[3 * b + 2];
+        const float4 pb = s_yph[128 * b + threadIdx.x];
+#pragma unroll 1
+        for (int a = 0; a < qx; ++a) {
+            const float4 xa = s_xpt[a][0], pa = s_xpt[a][1];
+            const float2 d1 = {fmaf(pa.x, pb.x, pa.z * pb.z), fmaf(pa.y, pb.y, pa.w * pb.w)};
+            const cx<float> g = reg ? green_sym_short<PQ, true>(xa.x - yb0, xa.y - yb1, xa.z - yb2, d1, imask, regm,
+                                                                s_tab, q.rtab, ef)
+                                    : green_sym_short<PQ, false>(xa.x - yb0, xa.y - yb1, xa.z - yb2, d1, imask, 0u,
+                                                                 s_tab, q.rtab, ef);
+            S = S + g;
+        }
+    }
+    S = (fx[XT ? 27 : 9] * fy[YT ? 27 : 9]) * S;
+    scatter_scalar<float, PK>(m, q, Z, N, x, y, S);
+}
+
 template <typename U>
 __device__ double static_scalar(const double *r5, bool other_tet, const double *verts_other, const double *R,
                                 double sgnR) {
@@ -668,7 +967,7 @@ __global__ void __launch_bounds__(128) k_pr_scalar(DevMesh m, const __grid_const
         for (int b = 0; b < nqy; ++b) {
             const T *yb = ny + 4 * b;
             const T dx = xa[0] - yb[0] + dc[0], dy = xa[1] - yb[1] + dc[1], dz = xa[2] - yb[2] + dc[2];
-            f0 += yb[3] / sqrt(dx * dx + dy * dy + dz * dz);
+            f0 += yb[3] * rsqrt(dx * dx + dy * dy + dz * dz);
         }
         s0 += xa[3] * f0;
     }
@@ -804,6 +1103,23 @@ __global__ void k_green(const double *d, double *out, int n, const float *stab, 
     out[2 * i + 1] = double(r.im);
 }
 
+// the short normal-incidence form at single displacements (every image visited)
+template <int PQ>
+__global__ void k_green_short(const double *d, double *out, int n, const float *stab, const float2 *ztab,
+                              const float4 *rtab, const __grid_constant__ EwaldF32 ef) {
+    __shared__ float4 s_tab[NSPAT];
+    for (int i = threadIdx.x; i < NSPAT; i += blockDim.x) s_tab[i] = reinterpret_cast<const float4 *>(stab)[i];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float dx = float(d[3 * i]), dy = float(d[3 * i + 1]), dz = float(d[3 * i + 2]);
+    const float2 d1 = {2.f * cospif(ef.step_x * dx * 0.31830988618f), 2.f * cospif(ef.step_y * dy * 0.31830988618f)};
+    const unsigned all = ef.n_img >= 32 ? 0xffffffffu : (1u << ef.n_img) - 1u;
+    cx<float> r = green_sym_short<PQ, true>(dx, dy, dz, d1, all, 0u, s_tab, rtab, ef);
+    out[2 * i] = double(r.re);
+    out[2 * i + 1] = double(r.im);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -811,7 +1127,14 @@ template <typename T, int PK>
 void far_scalar(bool sym, dim3 grid, size_t sm, cudaStream_t st, const DevMesh &m, const DevReq &q, T *Z, size_t N,
                 int nx, int ny, const uint16_t *mk) {
     if constexpr (sizeof(T) == 4) {
-        if (sym) k_far_scalar<T, PK, true><<<grid, 128, sm, st>>>(m, q, Z, N, nx, ny, mk);
+        if (sym && q.ef.sq_pq > 0) {   // normal incidence, short form
+            switch (q.ef.sq_pq) {
+                case 1: k_far_scalar_n<1, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+                case 2: k_far_scalar_n<2, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+                case 3: k_far_scalar_n<3, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+                default: k_far_scalar_n<4, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+            }
+        } else if (sym) k_far_scalar<T, PK, true><<<grid, 128, sm, st>>>(m, q, Z, N, nx, ny, mk);
         else k_far_scalar<T, PK, false><<<grid, 128, sm, st>>>(m, q, Z, N, nx, ny, mk);
     } else {
         k_far_scalar<T, PK, false><<<grid, 128, sm, st>>>(m, q, Z, N, nx, ny, mk);
@@ -833,8 +1156,16 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
     if (far0) cudaEventRecord(far0, st);
     const bool sym = sizeof(T) == 4 && q.ef.sym;   // normal incidence: the symmetric tabulated path
     if constexpr (sizeof(T) == 4) {
-        if (sym) k_far_tt<T, true><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N);
-        else k_far_tt<T, false><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N);
+        const dim3 gtt((m.nt + 127) / 128, m.nt);
+        if (sym && q.ef.sq_pq > 0) {   // normal incidence, short form
+            switch (q.ef.sq_pq) {
+                case 1: k_far_tt_n<1><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+                case 2: k_far_tt_n<2><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+                case 3: k_far_tt_n<3><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+                default: k_far_tt_n<4><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+            }
+        } else if (sym) k_far_tt<T, true><<<gtt, blk, sm, st>>>(m, q, Z, N);
+        else k_far_tt<T, false><<<gtt, blk, sm, st>>>(m, q, Z, N);
     } else {
         k_far_tt<T, false><<<dim3((m.nt + 127) / 128, m.nt), blk, sm, st>>>(m, q, Z, N);
     }
@@ -887,8 +1218,18 @@ cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStr
 }
 
 cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const float *stab, const float2 *ztab,
-                         const EwaldTables *ew, const EwaldF32 &ef, cudaStream_t st) {
+                         const EwaldTables *ew, const EwaldF32 &ef, cudaStream_t st, const float4 *rtab) {
+    const unsigned gb = (unsigned)((n + 127) / 128);
     if (fp64) { k_green<double><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
+    else if (ef.sym && ef.sq_pq > 0 && rtab) {   // the fill's normal-incidence form
+        switch (ef.sq_pq) {
+            case 1: k_green_short<1><<<gb, 128, 0, st>>>(d, out, n, stab, ztab, rtab, ef); break;
+            case 2: k_green_short<2><<<gb, 128, 0, st>>>(d, out, n, stab, ztab, rtab, ef); break;
+            case 3: k_green_short<3><<<gb, 128, 0, st>>>(d, out, n, stab, ztab, rtab, ef); break;
+            default: k_green_short<4><<<gb, 128, 0, st>>>(d, out, n, stab, ztab, rtab, ef); break;
+        }
+        ++g_launches;
+    }
     else if (ef.sym) { k_green<float, true><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
     else { k_green<float><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
     return cudaGetLastError();

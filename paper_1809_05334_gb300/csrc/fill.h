@@ -103,8 +103,9 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
 // touch_half [nto[0]][8] and touch_sc[i] [nto[i]] (i = 1..3)
 cudaError_t launch_static_cache(const DevMesh &m, double *touch_half, double *const touch_sc[4], cudaStream_t st);
 cudaError_t launch_erfcx(const double *u, double *out, int n, bool fp64, cudaStream_t st);
+// rtab (optional): the real spectral tables; with it, normal incidence takes the fill's short form
 cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const float *stab, const float2 *ztab,
-                         const EwaldTables *ew, const EwaldF32 &ef, cudaStream_t st);
+                         const EwaldTables *ew, const EwaldF32 &ef, cudaStream_t st, const float4 *rtab = nullptr);
 cudaError_t launch_build_tables(const EwaldTables *ew, float *stab, float2 *ztab, int n_tab, cudaStream_t st,
                                 float4 *rtab = nullptr);
 
