@@ -476,6 +476,7 @@ def run_ours(args):
         "dtype": {"fp32": "c64+f64", "fp16": "c32(fp16)+c64+f64", "bf16": "c32(bf16)+c64+f64"}.get(args.precision, "c128"),
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][1], "n_unknowns": n, "n_tets": cell.n_tets, "precision": args.precision,
+                   "theta_deg": args.theta_deg,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (Z is %.1f GB)" % (n * n * (8 if prec == vie.VIE_FP32 else 16) / 1e9)},
         "phases_ms": {"fill": last["t_fill_ms"], "factor": last["t_factor_ms"], "solve": last["t_solve_ms"],
@@ -939,7 +940,12 @@ def main():
     ap.add_argument("--fp64-tol", type=float, default=1e-8, help="FP64 residual tolerance of the FP64 leg")
     ap.add_argument("--sweep-points", type=int, default=27, help="sweep points of the default run's sweep leg")
     ap.add_argument("--serve-requests", type=int, default=12, help="requests of the default run's serving leg")
+    ap.add_argument("--theta-deg", type=float, default=0.0,
+                    help="incidence angle of the main workload (default 0: the bench configuration)")
     args = ap.parse_args()
+    if args.theta_deg != 0.0:
+        global THETA
+        THETA = float(np.deg2rad(args.theta_deg))
     if args.steps is None:
         args.steps = 81 if args.sweep else (24 if args.serve else 5)
     if args.impl == "reference":

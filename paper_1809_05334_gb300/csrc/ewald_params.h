@@ -50,6 +50,11 @@ constexpr int NZTAB = 256;    // spectral intervals
 // real-part buffer `rtab` holds n_tab real tables, the zero table, then the
 // n_tab imaginary tables, NZTAB float4 each.
 constexpr int SQ_MAX = 4;
+// Oblique incidence short form (at most 64 lattice images, an order rectangle
+// of at most OB_MAX x OB_MAX): the rectangle unrolled at compile time, each
+// entry naming its real table (a zero table outside the cut) and, for a
+// propagating order, its imaginary table.
+constexpr int OB_MAX = 8;
 // EwaldTables lives in device global memory, one copy per request in flight, so
 // independent solves can run concurrently.  The part of it that the FP32
 // tabulated evaluation reads in its inner loops travels as a kernel parameter
@@ -65,15 +70,27 @@ struct EwaldF32 {
     int sq_pq;                            // max(P, Q) >= 1 of the short form; 0 where it does not apply
     int sq_off[SQ_MAX + 1][SQ_MAX + 1];   // order (p, q): offset of its real table in rtab (float4 units)
     int sq_im;                            // offset of the (0, 0) order's imaginary table in rtab
+    int ob_nr;                            // rectangle side (4, 6 or 8) of the oblique short form; 0: not used
+    int ob_nq1;                           // k_y = 0 (orders even in q): q = 0 .. ob_nq1 - 1 (3 or 5) kept; 0: all q
+    float ob_kx0, ob_ky0;                 // k_par + 2 pi (p0 / a, q0 / b): the rectangle's first order
+    int ob_off[OB_MAX][OB_MAX];           // rectangle entry (i, j): offset of its real table in rtab
+    int ob_im[OB_MAX][OB_MAX];            // offset of its imaginary table (propagating order), else -1
 };
 // Ewald splitting parameter: sqrt(pi / ab) balances the spatial and spectral
 // series, bounded below by k0/6 (b = k0 / 2E <= 3 keeps exp(b^2) moderate).  The
-// tabulated FP32 path at normal incidence pairs the Floquet orders (half the
-// spectral terms, each cheaper), which moves the balance to a larger E: there
-// E is 1.5 times as large (fewer lattice images inside the same erfc cut).
-inline double ewald_split(double a, double b, double k0, bool fp32_normal) {
+// tabulated FP32 path makes the spectral terms cheaper than the images (table
+// lookups against square roots and table interpolation per image), which
+// moves the balance to a larger E: fewer lattice images inside the same erfc
+// cut.  The FP64 series keeps the balanced value.
+#ifndef VIE_SPLIT_NORMAL
+#define VIE_SPLIT_NORMAL 1.5    // FP32 tables, normal incidence
+#endif
+#ifndef VIE_SPLIT_OBLIQUE
+#define VIE_SPLIT_OBLIQUE 1.0   // FP32 tables, oblique incidence
+#endif
+inline double ewald_split(double a, double b, double k0, bool fp32, bool normal) {
     const double e = std::max(std::sqrt(3.141592653589793 / (a * b)), k0 / 6.0);
-    return fp32_normal ? 1.5 * e : e;
+    return fp32 ? (normal ? VIE_SPLIT_NORMAL : VIE_SPLIT_OBLIQUE) * e : e;
 }
 
 // The smallest rectangle of Floquet orders (p, q) holding every mode with
@@ -127,6 +144,39 @@ inline EwaldF32 make_ewald_f32(const EwaldTables &t) {
                 }
             }
         if (ok) f.sq_pq = P > Q ? (P > 1 ? P : 1) : (Q > 1 ? Q : 1);
+    }
+    f.ob_nr = 0;
+    f.ob_nq1 = 0;
+    f.ob_kx0 = (float)(t.kx + t.p0 * (double)t.step_x);
+    f.ob_ky0 = (float)(t.ky + t.q0 * (double)t.step_y);
+    for (int i = 0; i < OB_MAX; ++i)
+        for (int j = 0; j < OB_MAX; ++j) { f.ob_off[i][j] = zero; f.ob_im[i][j] = -1; }
+    // k_y = 0 and the rectangle symmetric in q: G_pq = G_p,-q, so the q sum folds
+    // onto q >= 0 with the weights 1, 2 cos(q s_y dy)
+    const int Qh = (t.nq - 1) / 2;
+    if (!t.sym && t.ky == 0.f && t.np > 0 && t.nq > 0 && 2 * t.q0 + t.nq == 1 && t.np <= OB_MAX && Qh + 1 <= 5 &&
+        t.n_img <= 64) {
+        for (int i = 0; i < t.np; ++i)
+            for (int q = 0; q <= Qh; ++q) {
+                const int code = t.rect_tab[i * t.nq + (Qh + q)];
+                if (code < 0) continue;
+                const int tb = code & TAB_INDEX;
+                f.ob_off[i][q] = tb * NZTAB;
+                if (!(code & TAB_REAL)) f.ob_im[i][q] = (t.n_tab + 1 + tb) * NZTAB;
+            }
+        f.ob_nr = t.np <= 6 ? 6 : 8;
+        f.ob_nq1 = Qh + 1 <= 3 ? 3 : 5;
+    } else if (!t.sym && t.np > 0 && t.nq > 0 && t.np <= OB_MAX && t.nq <= OB_MAX && t.n_img <= 64) {
+        for (int i = 0; i < t.np; ++i)
+            for (int j = 0; j < t.nq; ++j) {
+                const int code = t.rect_tab[i * t.nq + j];
+                if (code < 0) continue;
+                const int tb = code & TAB_INDEX;
+                f.ob_off[i][j] = tb * NZTAB;
+                if (!(code & TAB_REAL)) f.ob_im[i][j] = (t.n_tab + 1 + tb) * NZTAB;
+            }
+        const int nr = t.np > t.nq ? t.np : t.nq;
+        f.ob_nr = nr <= 4 ? 4 : (nr <= 6 ? 6 : 8);
     }
     return f;
 }

@@ -551,6 +551,317 @@ __global__ void __launch_bounds__(128, VIE_FAR_N_MINB) k_far_tt_n(DevMesh m, con
 }
 
 // ---------------------------------------------------------------------------
+// Oblique incidence, short form of the tabulated evaluation.  With
+// X_i = exp(-j (k_x0 + i s_x) dx), Y_j = exp(-j (k_y0 + j s_y) dy) (k_x0, k_y0
+// the first order of the rectangle, s = 2 pi / period) and the spectral table
+// G_ij(|z|) = Re G + j Im G of rectangle entry (i, j):
+//   S = sum_ij X_i Y_j Re G_ij,   T = sum_ij X_i Y_j Im G_ij (propagating orders only),
+//   g_p(d) = S + j T + sum_i F(R_i E)/R_i ph_i      (ph_i: image phase exp(j k_par.R_i) exp(b^2)/(4 pi)).
+// Re G is real, so the spectral part of g_p(-d) = sum G conj(X Y) is
+// conj(S) + j conj(T), and the image part is the conjugate of the image part
+// of g_p(d): g_p(-d) = conj(g_p(d)) + 2 j conj(T).  The returned T carries
+// that correction.  X0, SX, Y0, SY: X_0, exp(-j s_x dx), Y_0, exp(-j s_y dy).
+// ---------------------------------------------------------------------------
+template <bool REG>
+__device__ __forceinline__ float image_term64(int i, float dx, float dy, float dz2, unsigned long long regm,
+                                              const float4 *stab4, const EwaldF32 &ef) {
+    const float x = dx + ef.img[i][0], y = dy + ef.img[i][1];
+    const float R2 = fmaf(x, x, fmaf(y, y, dz2));
+    float rinv = rsqrtf(R2);
+    if (REG) rinv = R2 > 0.f ? rinv : 0.f;   // R = 0 only on an image whose static part is removed
+    const float xu = R2 * rinv * ef.Eih;
+    const int ix = min((int)xu, NSPAT - 1);
+    const float v = xu - (float)ix;
+    const float4 c = stab4[ix];
+    const float q1 = fmaf(v, fmaf(v, c.w, c.z), c.y);
+    float val = fmaf(v, q1, c.x) * rinv;
+    if (REG && ((regm >> i) & 1ull))   // (F(x) - F(0)) / R; near R = 0 from the first interval's slope
+        val = ix == 0 ? ef.Eih * q1 : fmaf(-ef.e_mb2, rinv, val);
+    return xu <= float(NSPAT) ? val : 0.f;   // beyond the table: outside the cut
+}
+
+template <int NR, bool REG>
+__device__ __forceinline__ cx<float> green_obl_short(float dx, float dy, float dz, cx<float> X0, cx<float> SX,
+                                                     cx<float> Y0, cx<float> SY, unsigned long long imask,
+                                                     unsigned long long regm, const float4 *stab4,
+                                                     const float4 *__restrict__ rtab, const EwaldF32 &ef,
+                                                     cx<float> &T) {
+    cx<float> Y[NR];
+    Y[0] = Y0;
+#pragma unroll
+    for (int j = 1; j < NR; ++j) Y[j] = Y[j - 1] * SY;
+    const float zu = fminf(fabsf(dz) * ef.z_inv_h, float(NZTAB));
+    const int iz = min((int)zu, NZTAB - 1);
+    const float u = zu - (float)iz;
+    const float4 *rt = rtab + iz;
+    cx<float> S = {0.f, 0.f}, X = X0;
+    T = {0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        cx<float> inr = {0.f, 0.f}, ini = {0.f, 0.f};
+        bool cplx = false;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const float4 c = __ldg(rt + ef.ob_off[i][j]);   // entries outside the cut read zeros
+            const float g = fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+            cfma(inr, g, Y[j]);
+            const int im = ef.ob_im[i][j];
+            if (im >= 0) {   // propagating order (uniform branch)
+                const float4 ci = __ldg(rt + im);
+                cfma(ini, fmaf(u, fmaf(u, fmaf(u, ci.w, ci.z), ci.y), ci.x), Y[j]);
+                cplx = true;
+            }
+        }
+        S = S + X * inr;
+        if (cplx) T = T + X * ini;
+        if (i + 1 < NR) X = X * SX;
+    }
+    // lattice images, two at a time (the mask is warp-uniform)
+    const float dz2 = dz * dz;
+    cx<float> acc = {S.re - T.im, S.im + T.re};
+    for (unsigned long long mk = imask; mk;) {
+        const int i0 = __ffsll((long long)mk) - 1;
+        mk &= mk - 1ull;
+        const float v0 = image_term64<REG>(i0, dx, dy, dz2, regm, stab4, ef);
+        acc.re = fmaf(v0, ef.img[i0][2], acc.re);
+        acc.im = fmaf(v0, ef.img[i0][3], acc.im);
+        if (mk) {
+            const int i1 = __ffsll((long long)mk) - 1;
+            mk &= mk - 1ull;
+            const float v1 = image_term64<REG>(i1, dx, dy, dz2, regm, stab4, ef);
+            acc.re = fmaf(v1, ef.img[i1][2], acc.re);
+            acc.im = fmaf(v1, ef.img[i1][3], acc.im);
+        }
+    }
+    return acc;
+}
+
+// The same at k_y = 0 with the order rectangle symmetric in q: G_pq = G_p,-q,
+// so sum_q Y_q G_pq = sum_{q >= 0} w_q cos(q s_y dy) G_pq (w_0 = 1, w_q = 2),
+// a real weight D_q = 2 cos(q s_y dy) (D_0 -> 1) by the Chebyshev recurrence
+// from d1y = 2 cos(s_y dy); entry (i, q) of the tables is order (p0 + i, q).
+template <int NP, int NQ1, bool REG>
+__device__ __forceinline__ cx<float> green_obl_ky0(float dx, float dy, float dz, cx<float> X0, cx<float> SX,
+                                                   float d1y, unsigned long long imask, unsigned long long regm,
+                                                   const float4 *stab4, const float4 *__restrict__ rtab,
+                                                   const EwaldF32 &ef, cx<float> &T) {
+    float Dy[NQ1];
+    Dy[0] = 1.f;
+    Dy[1] = d1y;
+#pragma unroll
+    for (int k = 2; k < NQ1; ++k) Dy[k] = fmaf(d1y, Dy[k - 1], k == 2 ? -2.f : -Dy[k - 2]);
+    const float zu = fminf(fabsf(dz) * ef.z_inv_h, float(NZTAB));
+    const int iz = min((int)zu, NZTAB - 1);
+    const float u = zu - (float)iz;
+    const float4 *rt = rtab + iz;
+    cx<float> S = {0.f, 0.f}, X = X0;
+    T = {0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        float inr = 0.f, ini = 0.f;
+        bool cplx = false;
+#pragma unroll
+        for (int q = 0; q < NQ1; ++q) {
+            const float4 c = __ldg(rt + ef.ob_off[i][q]);   // entries outside the cut read zeros
+            const float g = fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+            inr = q == 0 ? g : fmaf(Dy[q], g, inr);
+            const int im = ef.ob_im[i][q];
+            if (im >= 0) {   // propagating order (uniform branch)
+                const float4 ci = __ldg(rt + im);
+                const float gi = fmaf(u, fmaf(u, fmaf(u, ci.w, ci.z), ci.y), ci.x);
+                ini = q == 0 ? ini + gi : fmaf(Dy[q], gi, ini);
+                cplx = true;
+            }
+        }
+        S.re = fmaf(X.re, inr, S.re);
+        S.im = fmaf(X.im, inr, S.im);
+        if (cplx) {
+            T.re = fmaf(X.re, ini, T.re);
+            T.im = fmaf(X.im, ini, T.im);
+        }
+        if (i + 1 < NP) X = X * SX;
+    }
+    const float dz2 = dz * dz;
+    cx<float> acc = {S.re - T.im, S.im + T.re};
+    for (unsigned long long mk = imask; mk;) {
+        const int i0 = __ffsll((long long)mk) - 1;
+        mk &= mk - 1ull;
+        const float v0 = image_term64<REG>(i0, dx, dy, dz2, regm, stab4, ef);
+        acc.re = fmaf(v0, ef.img[i0][2], acc.re);
+        acc.im = fmaf(v0, ef.img[i0][3], acc.im);
+        if (mk) {
+            const int i1 = __ffsll((long long)mk) - 1;
+            mk &= mk - 1ull;
+            const float v1 = image_term64<REG>(i1, dx, dy, dz2, regm, stab4, ef);
+            acc.re = fmaf(v1, ef.img[i1][2], acc.re);
+            acc.im = fmaf(v1, ef.img[i1][3], acc.im);
+        }
+    }
+    return acc;
+}
+
+// the oblique evaluation of one point pair: NQ1 = 0 the full rectangle (NR x NR),
+// else the k_y = 0 fold (NR x NQ1); sa, sb carry (cos, sin) of s_x x and s_y y
+template <int NR, int NQ1, bool REG>
+__device__ __forceinline__ cx<float> green_obl(float dx, float dy, float dz, float4 pa, float4 sa, float4 pb,
+                                               float4 sb, unsigned long long imask, unsigned long long regm,
+                                               const float4 *stab4, const float4 *__restrict__ rtab,
+                                               const EwaldF32 &ef, cx<float> &T);
+
+// e^{-j th_a} conj(e^{-j th_b}) = e^{-j (th_a - th_b)} from (cos, sin) of th_a and th_b
+__device__ __forceinline__ cx<float> phase_diff(float ca, float sa, float cb, float sb) {
+    return {fmaf(ca, cb, sa * sb), fmaf(ca, sb, -sa * cb)};
+}
+
+template <int NR, int NQ1, bool REG>
+__device__ __forceinline__ cx<float> green_obl(float dx, float dy, float dz, float4 pa, float4 sa, float4 pb,
+                                               float4 sb, unsigned long long imask, unsigned long long regm,
+                                               const float4 *stab4, const float4 *__restrict__ rtab,
+                                               const EwaldF32 &ef, cx<float> &T) {
+    const cx<float> X0 = phase_diff(pa.x, pa.y, pb.x, pb.y), SX = phase_diff(sa.x, sa.y, sb.x, sb.y);
+    if constexpr (NQ1 > 0) {
+        const float d1y = 2.f * fmaf(sa.z, sb.z, sa.w * sb.w);   // 2 cos(s_y (y_a - y_b))
+        return green_obl_ky0<NR, NQ1, REG>(dx, dy, dz, X0, SX, d1y, imask, regm, stab4, rtab, ef, T);
+    } else {
+        const cx<float> Y0 = phase_diff(pa.z, pa.w, pb.z, pb.w), SY = phase_diff(sa.z, sa.w, sb.z, sb.w);
+        return green_obl_short<NR, REG>(dx, dy, dz, X0, SX, Y0, SY, imask, regm, stab4, rtab, ef, T);
+    }
+}
+
+// 4 x 4 point pairs of one tetrahedron pair in the oblique short form.  tpt:
+// the test points [a] = (x_a, x_a - c, (cos, sin) of k_x0 x and k_y0 y,
+// (cos, sin) of s_x x and s_y y); sph (stride 128, two float4 per point): the
+// same phases of the source points.  mo: moments of g_p(x_a - y_b); mc: the
+// correction 2 j conj(T) of g_p(y_b - x_a) with the reversed pair's roles.
+template <int NR, int NQ1, bool REG>
+__device__ __forceinline__ void far_tt_obl(const float *__restrict__ fs, const float4 (*tpt)[4], const float4 *sph,
+                                           unsigned long long imask, unsigned long long regm, const float4 *stab4,
+                                           const DevReq &q, Mom<float> &mo, Mom<float> &mc) {
+#pragma unroll 1
+    for (int b = 0; b < 4; ++b) {
+        const float yb0 = fs[3 * b], yb1 = fs[3 * b + 1], yb2 = fs[3 * b + 2];
+        const float rb[3] = {yb0 - fs[12], yb1 - fs[13], yb2 - fs[14]};
+        const float4 pb = sph[256 * b], sb = sph[256 * b + 128];
+#pragma unroll 1
+        for (int a = 0; a < 4; ++a) {
+            const float4 xa = tpt[a][0], ra = tpt[a][1], pa = tpt[a][2], sa = tpt[a][3];
+            cx<float> T;
+            const cx<float> g = green_obl<NR, NQ1, REG>(xa.x - yb0, xa.y - yb1, xa.z - yb2, pa, sa, pb, sb, imask,
+                                                        regm, stab4, q.rtab, q.ef, T);
+            const cx<float> c = {2.f * T.im, 2.f * T.re};   // 2 j conj(T)
+            const float rr = ra.x * rb[0] + ra.y * rb[1] + ra.z * rb[2];
+            mo.S = mo.S + g;
+            cfma(mo.A[0], ra.x, g);
+            cfma(mo.A[1], ra.y, g);
+            cfma(mo.A[2], ra.z, g);
+            mc.S = mc.S + c;
+            cfma(mc.B[0], ra.x, c);
+            cfma(mc.B[1], ra.y, c);
+            cfma(mc.B[2], ra.z, c);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                cfma(mo.B[d], rb[d], g);
+                cfma(mc.A[d], rb[d], c);
+            }
+            cfma(mo.C, rr, g);
+            cfma(mc.C, rr, c);
+        }
+    }
+}
+
+// (cos, sin) of k_x0 x, k_y0 y and of s_x x, s_y y of one point
+__device__ __forceinline__ void obl_point_phases(const EwaldF32 &ef, float x, float y, float4 &p, float4 &st) {
+    float s0, c0, s1, c1, s2, c2, s3, c3;
+    sincospif(ef.ob_kx0 * 0.31830988618f * x, &s0, &c0);
+    sincospif(ef.ob_ky0 * 0.31830988618f * y, &s1, &c1);
+    sincospif(ef.step_x * 0.31830988618f * x, &s2, &c2);
+    sincospif(ef.step_y * 0.31830988618f * y, &s3, &c3);
+    p = make_float4(c0, s0, c1, s1);
+    st = make_float4(c2, s2, c3, s3);
+}
+
+#ifndef VIE_FAR_O_MINB
+#define VIE_FAR_O_MINB 5   // CTAs per SM of the oblique-incidence far kernels
+#endif
+// Far tetrahedron pairs at oblique incidence in the short form: one thread per
+// unordered pair {t, s} (s >= t); the reversed pair's moments are the
+// conjugates of the pair's own, exchanged, plus the propagating-order correction.
+template <int NR, int NQ1>
+__global__ void __launch_bounds__(128, VIE_FAR_O_MINB) k_far_tt_o(DevMesh m, const __grid_constant__ DevReq q, float *Z,
+                                                                  size_t N) {
+    __shared__ float4 s_tab[NSPAT];
+    __shared__ float4 s_sph[4 * 2 * 128];   // [b][phase pair][thread]
+    __shared__ float4 s_tpt[4][4];
+    const int t = blockIdx.y;
+    if ((int)(blockIdx.x * blockDim.x + blockDim.x) <= t) return;   // the whole block is below the diagonal
+    const EwaldF32 &ef = q.ef;
+    const float4 *gtab = reinterpret_cast<const float4 *>(q.stab);
+    for (int i = threadIdx.x; i < NSPAT; i += blockDim.x) s_tab[i] = gtab[i];
+    const float *ft = m.far<float>(t);
+    if (threadIdx.x < 4) {
+        const int a = threadIdx.x;
+        float4 p, st;
+        obl_point_phases(ef, ft[3 * a], ft[3 * a + 1], p, st);
+        s_tpt[a][0] = make_float4(ft[3 * a], ft[3 * a + 1], ft[3 * a + 2], 0.f);
+        s_tpt[a][1] = make_float4(ft[3 * a] - ft[12], ft[3 * a + 1] - ft[13], ft[3 * a + 2] - ft[14], 0.f);
+        s_tpt[a][2] = p;
+        s_tpt[a][3] = st;
+    }
+    const int s0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = s0 < m.nt && s0 >= t;
+    const int s = live ? s0 : t;
+    const float *fs = m.far<float>(s);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float4 p, st;
+        obl_point_phases(ef, fs[3 * b], fs[3 * b + 1], p, st);
+        s_sph[256 * b + threadIdx.x] = p;
+        s_sph[256 * b + 128 + threadIdx.x] = st;
+    }
+    float rt = 0.f, rs = 0.f;
+    for (int a = 0; a < 4; ++a) {
+        const float ux = ft[3 * a] - ft[12], uy = ft[3 * a + 1] - ft[13], uz = ft[3 * a + 2] - ft[14];
+        const float vx = fs[3 * a] - fs[12], vy = fs[3 * a + 1] - fs[13], vz = fs[3 * a + 2] - fs[14];
+        rt = fmaxf(rt, sqrtf(ux * ux + uy * uy + uz * uz));
+        rs = fmaxf(rs, sqrtf(vx * vx + vy * vy + vz * vz));
+    }
+    unsigned long long imask = live ? image_mask(ef, ft[12] - fs[12], ft[13] - fs[13], ft[14] - fs[14], rt + rs) : 0ull;
+    {
+        const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)imask);
+        const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(imask >> 32));
+        imask = ((unsigned long long)hi << 32) | lo;
+    }
+    const unsigned sub = live ? (unsigned)m.mk_tt[(size_t)t * m.nt + s] : 0u;
+    unsigned long long regm = 0ull;
+    if (sub) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if ((sub >> k) & 1u) regm |= 1ull << ef.near_img[k];
+    }
+    const bool reg = __any_sync(0xffffffffu, regm != 0ull);
+    __syncthreads();
+    if (!live) return;
+    Mom<float> mo, mc;
+    mo.zero();
+    mc.zero();
+    if (reg) far_tt_obl<NR, NQ1, true>(fs, s_tpt, s_sph + threadIdx.x, imask, regm, s_tab, q, mo, mc);
+    else far_tt_obl<NR, NQ1, false>(fs, s_tpt, s_sph + threadIdx.x, imask, regm, s_tab, q, mo, mc);
+    const float wgt = ft[27] * fs[27];
+    Mom<float> mr;
+    mr.S = wgt * (cconj(mo.S) + mc.S);
+    mr.C = wgt * (cconj(mo.C) + mc.C);
+    for (int d = 0; d < 3; ++d) {
+        mr.A[d] = wgt * (cconj(mo.B[d]) + mc.A[d]);
+        mr.B[d] = wgt * (cconj(mo.A[d]) + mc.B[d]);
+    }
+    mo.S = wgt * mo.S;
+    mo.C = wgt * mo.C;
+    for (int d = 0; d < 3; ++d) { mo.A[d] = wgt * mo.A[d]; mo.B[d] = wgt * mo.B[d]; }
+    scatter_tt<float>(m, q, Z, N, t, s, mo);
+    if (s != t) scatter_tt<float>(m, q, Z, N, s, t, mr);
+}
+
+// ---------------------------------------------------------------------------
 // near tetrahedron pairs: one warp per pair
 // ---------------------------------------------------------------------------
 template <typename U>
@@ -925,6 +1236,90 @@ __global__ void __launch_bounds__(128, VIE_FAR_N_MINB)
     scatter_scalar<float, PK>(m, q, Z, N, x, y, S);
 }
 
+// Far scalar pairs (charge faces) at oblique incidence in the short form.
+template <int NR, int NQ1, int PK>
+__global__ void __launch_bounds__(128, VIE_FAR_O_MINB)
+    k_far_scalar_o(DevMesh m, const __grid_constant__ DevReq q, float *Z, size_t N, int nx, int ny,
+                   const uint16_t *mk) {
+    __shared__ float4 s_tab[NSPAT];
+    __shared__ float4 s_yph[4 * 2 * 128];
+    __shared__ float4 s_xpt[4][3];
+    constexpr bool XT = PKTraits<PK>::xtet, YT = PKTraits<PK>::ytet;
+    constexpr int qx = XT ? 4 : 3, qy = YT ? 4 : 3;
+    const EwaldF32 &ef = q.ef;
+    const int x = blockIdx.y;
+    const float4 *gtab = reinterpret_cast<const float4 *>(q.stab);
+    for (int i = threadIdx.x; i < NSPAT; i += blockDim.x) s_tab[i] = gtab[i];
+    const float *fx = far_el<float, XT>(m, XT ? x : m.hf[x]);
+    if (threadIdx.x < qx) {
+        const int a = threadIdx.x;
+        float4 p, st;
+        obl_point_phases(ef, fx[3 * a], fx[3 * a + 1], p, st);
+        s_xpt[a][0] = make_float4(fx[3 * a], fx[3 * a + 1], fx[3 * a + 2], 0.f);
+        s_xpt[a][1] = p;
+        s_xpt[a][2] = st;
+    }
+    const int y0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = y0 < ny;
+    const int y = live ? y0 : ny - 1;
+    const float *fy = far_el<float, YT>(m, y);
+#pragma unroll
+    for (int b = 0; b < qy; ++b) {
+        float4 p, st;
+        obl_point_phases(ef, fy[3 * b], fy[3 * b + 1], p, st);
+        s_yph[256 * b + threadIdx.x] = p;
+        s_yph[256 * b + 128 + threadIdx.x] = st;
+    }
+    float c1[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < qx; ++a)
+        for (int d = 0; d < 3; ++d) c1[d] += fx[3 * a + d] / qx;
+    for (int b = 0; b < qy; ++b)
+        for (int d = 0; d < 3; ++d) c2[d] += fy[3 * b + d] / qy;
+    float r1 = 0.f, r2 = 0.f;
+    for (int a = 0; a < qx; ++a) {
+        const float ux = fx[3 * a] - c1[0], uy = fx[3 * a + 1] - c1[1], uz = fx[3 * a + 2] - c1[2];
+        r1 = fmaxf(r1, sqrtf(ux * ux + uy * uy + uz * uz));
+    }
+    for (int b = 0; b < qy; ++b) {
+        const float ux = fy[3 * b] - c2[0], uy = fy[3 * b + 1] - c2[1], uz = fy[3 * b + 2] - c2[2];
+        r2 = fmaxf(r2, sqrtf(ux * ux + uy * uy + uz * uz));
+    }
+    unsigned long long imask = live ? image_mask(ef, c1[0] - c2[0], c1[1] - c2[1], c1[2] - c2[2], r1 + r2) : 0ull;
+    {
+        const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)imask);
+        const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(imask >> 32));
+        imask = ((unsigned long long)hi << 32) | lo;
+    }
+    const unsigned sub = live ? (unsigned)mk[(size_t)x * ny + y] : 0u;
+    unsigned long long regm = 0ull;
+    if (sub) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if ((sub >> k) & 1u) regm |= 1ull << ef.near_img[k];
+    }
+    const bool reg = __any_sync(0xffffffffu, regm != 0ull);
+    __syncthreads();
+    if (!live) return;
+    cx<float> S = {0.f, 0.f};
+#pragma unroll 1
+    for (int b = 0; b < qy; ++b) {
+        const float yb0 = fy[3 * b], yb1 = fy[3 * b + 1], yb2 = fy[3 * b + 2];
+        const float4 pb = s_yph[256 * b + threadIdx.x], sb = s_yph[256 * b + 128 + threadIdx.x];
+#pragma unroll 1
+        for (int a = 0; a < qx; ++a) {
+            const float4 xa = s_xpt[a][0], pa = s_xpt[a][1], sa = s_xpt[a][2];
+            cx<float> T;
+            const cx<float> g = reg ? green_obl<NR, NQ1, true>(xa.x - yb0, xa.y - yb1, xa.z - yb2, pa, sa, pb, sb,
+                                                               imask, regm, s_tab, q.rtab, ef, T)
+                                    : green_obl<NR, NQ1, false>(xa.x - yb0, xa.y - yb1, xa.z - yb2, pa, sa, pb, sb,
+                                                                imask, 0ull, s_tab, q.rtab, ef, T);
+            S = S + g;
+        }
+    }
+    S = (fx[XT ? 27 : 9] * fy[YT ? 27 : 9]) * S;
+    scatter_scalar<float, PK>(m, q, Z, N, x, y, S);
+}
+
 template <typename U>
 __device__ double static_scalar(const double *r5, bool other_tet, const double *verts_other, const double *R,
                                 double sgnR) {
@@ -1120,9 +1515,41 @@ __global__ void k_green_short(const double *d, double *out, int n, const float *
     out[2 * i + 1] = double(r.im);
 }
 
+// the oblique short form at single displacements (every image visited)
+template <int NR, int NQ1>
+__global__ void k_green_obl(const double *d, double *out, int n, const float *stab, const float4 *rtab,
+                            const __grid_constant__ EwaldF32 ef) {
+    __shared__ float4 s_tab[NSPAT];
+    for (int i = threadIdx.x; i < NSPAT; i += blockDim.x) s_tab[i] = reinterpret_cast<const float4 *>(stab)[i];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float dx = float(d[3 * i]), dy = float(d[3 * i + 1]), dz = float(d[3 * i + 2]);
+    float s0, c0, s1, c1, s2, c2, s3, c3;
+    sincospif(ef.ob_kx0 * 0.31830988618f * dx, &s0, &c0);
+    sincospif(ef.ob_ky0 * 0.31830988618f * dy, &s1, &c1);
+    sincospif(ef.step_x * 0.31830988618f * dx, &s2, &c2);
+    sincospif(ef.step_y * 0.31830988618f * dy, &s3, &c3);
+    const unsigned long long all = ef.n_img >= 64 ? ~0ull : (1ull << ef.n_img) - 1ull;
+    cx<float> T;
+    // point a at d, point b at the origin: (cos, sin) of the phases of d
+    const float4 pa = make_float4(c0, s0, c1, s1), sa = make_float4(c2, s2, c3, s3);
+    const float4 pb = make_float4(1.f, 0.f, 1.f, 0.f), sb = make_float4(1.f, 0.f, 1.f, 0.f);
+    cx<float> r = green_obl<NR, NQ1, true>(dx, dy, dz, pa, sa, pb, sb, all, 0ull, s_tab, rtab, ef, T);
+    out[2 * i] = double(r.re);
+    out[2 * i + 1] = double(r.im);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// template variant of the oblique short form: 0-2 the full rectangle of side
+// 4, 6, 8; 3-5 the k_y = 0 fold (6 x 3, 8 x 3, 8 x 5)
+inline int obl_variant(const EwaldF32 &ef) {
+    if (ef.ob_nq1 == 0) return ef.ob_nr == 4 ? 0 : (ef.ob_nr == 6 ? 1 : 2);
+    return ef.ob_nq1 == 3 ? (ef.ob_nr == 6 ? 3 : 4) : 5;
+}
+
 template <typename T, int PK>
 void far_scalar(bool sym, dim3 grid, size_t sm, cudaStream_t st, const DevMesh &m, const DevReq &q, T *Z, size_t N,
                 int nx, int ny, const uint16_t *mk) {
@@ -1133,6 +1560,15 @@ void far_scalar(bool sym, dim3 grid, size_t sm, cudaStream_t st, const DevMesh &
                 case 2: k_far_scalar_n<2, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
                 case 3: k_far_scalar_n<3, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
                 default: k_far_scalar_n<4, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+            }
+        } else if (!sym && q.ef.ob_nr > 0) {   // oblique incidence, short form
+            switch (obl_variant(q.ef)) {
+                case 0: k_far_scalar_o<4, 0, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+                case 1: k_far_scalar_o<6, 0, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+                case 2: k_far_scalar_o<8, 0, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+                case 3: k_far_scalar_o<6, 3, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+                case 4: k_far_scalar_o<8, 3, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
+                default: k_far_scalar_o<8, 5, PK><<<grid, 128, 0, st>>>(m, q, Z, N, nx, ny, mk); break;
             }
         } else if (sym) k_far_scalar<T, PK, true><<<grid, 128, sm, st>>>(m, q, Z, N, nx, ny, mk);
         else k_far_scalar<T, PK, false><<<grid, 128, sm, st>>>(m, q, Z, N, nx, ny, mk);
@@ -1163,6 +1599,15 @@ cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, doub
                 case 2: k_far_tt_n<2><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
                 case 3: k_far_tt_n<3><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
                 default: k_far_tt_n<4><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+            }
+        } else if (!sym && q.ef.ob_nr > 0) {   // oblique incidence, short form
+            switch (obl_variant(q.ef)) {
+                case 0: k_far_tt_o<4, 0><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+                case 1: k_far_tt_o<6, 0><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+                case 2: k_far_tt_o<8, 0><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+                case 3: k_far_tt_o<6, 3><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+                case 4: k_far_tt_o<8, 3><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
+                default: k_far_tt_o<8, 5><<<gtt, blk, 0, st>>>(m, q, Z, N); break;
             }
         } else if (sym) k_far_tt<T, true><<<gtt, blk, sm, st>>>(m, q, Z, N);
         else k_far_tt<T, false><<<gtt, blk, sm, st>>>(m, q, Z, N);
@@ -1230,6 +1675,17 @@ cudaError_t launch_green(const double *d, double *out, int n, bool fp64, const f
         }
         ++g_launches;
     }
+    else if (!ef.sym && ef.ob_nr > 0 && rtab) {   // the fill's oblique form
+        switch (obl_variant(ef)) {
+            case 0: k_green_obl<4, 0><<<gb, 128, 0, st>>>(d, out, n, stab, rtab, ef); break;
+            case 1: k_green_obl<6, 0><<<gb, 128, 0, st>>>(d, out, n, stab, rtab, ef); break;
+            case 2: k_green_obl<8, 0><<<gb, 128, 0, st>>>(d, out, n, stab, rtab, ef); break;
+            case 3: k_green_obl<6, 3><<<gb, 128, 0, st>>>(d, out, n, stab, rtab, ef); break;
+            case 4: k_green_obl<8, 3><<<gb, 128, 0, st>>>(d, out, n, stab, rtab, ef); break;
+            default: k_green_obl<8, 5><<<gb, 128, 0, st>>>(d, out, n, stab, rtab, ef); break;
+        }
+        ++g_launches;
+    }
     else if (ef.sym) { k_green<float, true><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
     else { k_green<float><<<(n + 127) / 128, 128, 0, st>>>(d, out, n, stab, ztab, ew, ef); ++g_launches; }
     return cudaGetLastError();
@@ -1269,7 +1725,7 @@ int build_ewald_tables(double a, double b, double k0, double kx, double ky, doub
                        EwaldTables &E, std::vector<double> *orders, const char **why) {
     std::memset(&E, 0, sizeof(E));
     if (orders) orders->clear();
-    E.E = ewald_split(a, b, k0, !fp64 && kx == 0.0 && ky == 0.0);
+    E.E = ewald_split(a, b, k0, !fp64, kx == 0.0 && ky == 0.0);
     E.bb = k0 / (2.0 * E.E);
     E.a = a;
     E.b = b;

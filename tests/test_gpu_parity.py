@@ -51,7 +51,7 @@ def oracle_run(name, cell, lam, th, ph):
 
 
 CASES = [("slab_3x3x1", 500.0, 0.0, 0.0), ("slab_4x3x2_jit", 470.0, 0.5, 0.3),
-         ("plasmonic_tiny", 520.0, 0.35, 0.2)]
+         ("plasmonic_tiny", 520.0, 0.35, 0.2), ("plasmonic_tiny", 560.0, 0.6, 0.0)]
 
 
 # --------------------------------------------------------------------------- special functions
@@ -68,7 +68,9 @@ def test_faddeeva_fp64_and_fp32(solver64):
 
 
 @pytest.mark.parametrize("a,b,lam,th,ph", [(200.0, 200.0, 500.0, 0.0, 0.0), (180.0, 150.0, 430.0, 0.6, 0.3),
-                                           (400.0, 400.0, 650.0, 0.9, 1.1), (60.0, 54.0, 520.0, 0.35, 0.2)])
+                                           (400.0, 400.0, 650.0, 0.9, 1.1), (60.0, 54.0, 520.0, 0.35, 0.2),
+                                           (200.0, 200.0, 500.0, 0.5, 0.0), (400.0, 400.0, 650.0, 0.9, 0.0),
+                                           (300.0, 240.0, 420.0, 1.2, 0.0)])
 def test_periodic_green_vs_oracle(solver64, a, b, lam, th, ph):
     cell = cellgen.slab_cell(2, 2, 1, a, b, 20.0, (2.0, 0.1))
     solver64.set_mesh(cell)
