@@ -529,13 +529,16 @@ def run_ours(args):
         print(json.dumps(res))
 
 
-# Per g_p value of the far tetrahedron-pair kernel (16 values per ordered pair
-# of tetrahedra), counted with ncu on the plasmonic 21k workload (smooth Ag sphere) at 500 nm,
-# normal incidence (the Ewald series has the same terms per value for every
-# cell of this period, wavelength and incidence): executed FP32 operations
-# (2 FFMA + FADD + FMUL, thread level) and executed warp instructions.
-FAR_FLOPS_PER_VALUE = 416.75
-FAR_WINST_PER_VALUE = 32.06
+# Per g_p value of the far tetrahedron-pair kernel at normal incidence (the
+# short form, k_far_tt_n; 16 values per ordered pair of tetrahedra), counted
+# with ncu on the plasmonic geometry at sweep density (4860 tets) at 500 nm:
+# the Ewald series has the same terms per value for every cell of this
+# period, wavelength and incidence.  Executed FP32 operations (2 FFMA + FADD +
+# FMUL, thread level) and executed warp instructions.  Oblique incidence runs
+# another kernel (k_far_tt_o), whose counts were not taken: its issue-rate
+# figures are left out.
+FAR_FLOPS_PER_VALUE = 266.8
+FAR_WINST_PER_VALUE = 13.03
 SMS, FP32_LANES, SCHEDULERS = 152, 128, 4
 MATVEC_Z_TRAFFIC = 3.5527e9   # DRAM read + write per FP32 Z product, 21,024 unknowns (ncu)
 
@@ -563,7 +566,7 @@ def roofline(last, n, peaks, prec, n_tets):
     src = "measured" if "hbm_gbs" in peaks else "fallback"
     out = {}
     fp32 = prec != 0          # the FP32 fill kernels (every precision but FP64)
-    if last.get("k_far_tt_ms") and fp32:
+    if last.get("k_far_tt_ms") and fp32 and THETA == 0.0:
         # instruction-issue bound (a mix of FP32, integer and load instructions):
         # warp instructions per value x values / event time, against 152 SMs x 4
         # schedulers x 1 warp instruction per clock x the maximum SM clock

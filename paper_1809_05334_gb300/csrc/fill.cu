@@ -344,6 +344,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 6)
     if (s != t) scatter_tt<T>(m, q, Z, N, s, t, mr);
 }
 
+// Interval min(floor(x), n - 1) of a table of n intervals and the offset v in
+// it (v in [0, 1]; x >= 0 clamped to n first, so x = n gives interval n - 1 at
+// v = 1), without float <-> int conversions (they run on the quarter-rate
+// pipe): x + 2^23 rounded down holds floor(x) in its low mantissa bits.
+// Callers test the unclamped x against the table's range where it can exceed it.
+__device__ __forceinline__ int table_index(float x, int n, float &v) {
+    const float xc = fminf(x, float(n));
+    const float t = __fadd_rd(xc, 8388608.f);
+    v = xc - fminf(t - 8388608.f, float(n - 1));
+    return min(__float_as_int(t) - 0x4B000000, n - 1);
+}
+
 // ---------------------------------------------------------------------------
 // Normal incidence (k_par = 0), short form of the tabulated evaluation.  The
 // same sum as green_tab_impl's symmetric form,
@@ -365,8 +377,8 @@ __device__ __forceinline__ float image_term(int i, float dx, float dy, float dz2
     float rinv = rsqrtf(R2);
     if (REG) rinv = R2 > 0.f ? rinv : 0.f;   // R = 0 only on an image whose static part is removed
     const float xu = R2 * rinv * ef.Eih;
-    const int ix = min((int)xu, NSPAT - 1);
-    const float v = xu - (float)ix;
+    float v;
+    const int ix = table_index(xu, NSPAT, v);
     const float4 c = stab4[ix];
     const float q1 = fmaf(v, fmaf(v, c.w, c.z), c.y);
     float val = fmaf(v, q1, c.x) * rinv;
@@ -389,9 +401,8 @@ __device__ __forceinline__ cx<float> green_sym_short(float dx, float dy, float d
         Dx[k] = fmaf(d1.x, Dx[k - 1], k == 2 ? -2.f : -Dx[k - 2]);
         Dy[k] = fmaf(d1.y, Dy[k - 1], k == 2 ? -2.f : -Dy[k - 2]);
     }
-    const float zu = fminf(fabsf(dz) * ef.z_inv_h, float(NZTAB));
-    const int iz = min((int)zu, NZTAB - 1);
-    const float u = zu - (float)iz;
+    float u;
+    const int iz = table_index(fabsf(dz) * ef.z_inv_h, NZTAB, u);
     const float4 *rt = rtab + iz;
     // every entry of the quadrant, no branch: orders outside the cut read zeros
     float ar = 0.f;
@@ -570,8 +581,8 @@ __device__ __forceinline__ float image_term64(int i, float dx, float dy, float d
     float rinv = rsqrtf(R2);
     if (REG) rinv = R2 > 0.f ? rinv : 0.f;   // R = 0 only on an image whose static part is removed
     const float xu = R2 * rinv * ef.Eih;
-    const int ix = min((int)xu, NSPAT - 1);
-    const float v = xu - (float)ix;
+    float v;
+    const int ix = table_index(xu, NSPAT, v);
     const float4 c = stab4[ix];
     const float q1 = fmaf(v, fmaf(v, c.w, c.z), c.y);
     float val = fmaf(v, q1, c.x) * rinv;
@@ -590,9 +601,8 @@ __device__ __forceinline__ cx<float> green_obl_short(float dx, float dy, float d
     Y[0] = Y0;
 #pragma unroll
     for (int j = 1; j < NR; ++j) Y[j] = Y[j - 1] * SY;
-    const float zu = fminf(fabsf(dz) * ef.z_inv_h, float(NZTAB));
-    const int iz = min((int)zu, NZTAB - 1);
-    const float u = zu - (float)iz;
+    float u;
+    const int iz = table_index(fabsf(dz) * ef.z_inv_h, NZTAB, u);
     const float4 *rt = rtab + iz;
     cx<float> S = {0.f, 0.f}, X = X0;
     T = {0.f, 0.f};
@@ -650,9 +660,8 @@ __device__ __forceinline__ cx<float> green_obl_ky0(float dx, float dy, float dz,
     Dy[1] = d1y;
 #pragma unroll
     for (int k = 2; k < NQ1; ++k) Dy[k] = fmaf(d1y, Dy[k - 1], k == 2 ? -2.f : -Dy[k - 2]);
-    const float zu = fminf(fabsf(dz) * ef.z_inv_h, float(NZTAB));
-    const int iz = min((int)zu, NZTAB - 1);
-    const float u = zu - (float)iz;
+    float u;
+    const int iz = table_index(fabsf(dz) * ef.z_inv_h, NZTAB, u);
     const float4 *rt = rtab + iz;
     cx<float> S = {0.f, 0.f}, X = X0;
     T = {0.f, 0.f};
