@@ -203,10 +203,11 @@ def leg_sweep(vie, torch, local, k, slots):
     out = {"workload": SWEEP_WORKLOAD + " (first %d points)" % k, "n_unknowns": None}
     res = {}
     for name in ("fp32", "fp16"):
-        s = vie.Solver(device=local, precision=PRECISIONS[name], tol=1e-6)
+        s = vie.Solver(device=local, precision=PRECISIONS[name], tol=1e-6, autotune=True)
         try:
             out["n_unknowns"] = s.set_mesh(cell)
-            s.solve_batch(lams[:slots], ths[:slots], phs[:slots], eps[:slots], max_slots=slots)   # warm-up
+            # warm-up; its normal and oblique requests autotune the schedule (untimed)
+            s.solve_batch(lams[:slots], ths[:slots], phs[:slots], eps[:slots], max_slots=slots)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             r, used = s.solve_batch(lams, ths, phs, eps, max_slots=slots)
@@ -422,6 +423,10 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # schedule autotuning on this mesh and incidence (set-up, untimed)
+    tune = solver.tune(LAM, THETA, PHI, eps, stream=sp)
+    global FAR_SPLIT_CHOSEN
+    FAR_SPLIT_CHOSEN = tune["split_chosen"]
     for _ in range(args.warmup):
         out = solver.solve(LAM, THETA, PHI, eps, stream=sp)
     barrier()
@@ -479,6 +484,7 @@ def run_ours(args):
                    "theta_deg": args.theta_deg,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (Z is %.1f GB)" % (n * n * (8 if prec == vie.VIE_FP32 else 16) / 1e9)},
+        "autotune": tune,
         "phases_ms": {"fill": last["t_fill_ms"], "factor": last["t_factor_ms"], "solve": last["t_solve_ms"],
                       "post": last["t_post_ms"]},
         "kernels_ms": {"far_tt": last["k_far_tt_ms"], "fill": last["k_fill_ms"], "factor": last["k_factor_ms"],
@@ -529,16 +535,17 @@ def run_ours(args):
         print(json.dumps(res))
 
 
-# Per g_p value of the far tetrahedron-pair kernel at normal incidence (the
-# short form, k_far_tt_n; 16 values per ordered pair of tetrahedra), counted
-# with ncu on the plasmonic geometry at sweep density (4860 tets) at 500 nm:
-# the Ewald series has the same terms per value for every cell of this
-# period, wavelength and incidence.  Executed FP32 operations (2 FFMA + FADD +
-# FMUL, thread level) and executed warp instructions.  Oblique incidence runs
-# another kernel (k_far_tt_o), whose counts were not taken: its issue-rate
-# figures are left out.
-FAR_FLOPS_PER_VALUE = 266.8
-FAR_WINST_PER_VALUE = 13.03
+# Per g_p value of the far tetrahedron-pair kernels (16 values per ordered pair
+# of tetrahedra), counted with ncu on the plasmonic geometry at sweep density
+# (4860 tets), lambda = 500 nm, at the default Ewald split (the series has the
+# same terms per value for every cell of this period, wavelength and incidence
+# class): executed warp instructions and FP32 operations (2 FFMA + FADD + FMUL,
+# thread level).  Normal incidence: k_far_tt_n (split 1.5); oblique incidence
+# at theta = 0.3 rad, phi = 0: k_far_tt_o, the k_y = 0 fold (split 1.0).  With
+# another split (the autotuner's choice) the counts do not apply and the
+# issue-rate figures are left out.
+FAR_COUNTS = {"normal": (13.61, 279.2, 1.5), "oblique": (34.09, 512.2, 1.0)}
+FAR_SPLIT_CHOSEN = None   # set by the main leg from its autotune report
 SMS, FP32_LANES, SCHEDULERS = 152, 128, 4
 MATVEC_Z_TRAFFIC = 3.5527e9   # DRAM read + write per FP32 Z product, 21,024 unknowns (ncu)
 
@@ -550,9 +557,9 @@ def roofline(last, n, peaks, prec, n_tets):
     """Roofline of the dominant kernel (largest device time in the solve), plus the others.
 
     k_far_tt (far tetrahedron pairs of the fill): instruction-issue bound ("alu");
-    achieved = FAR_WINST_PER_VALUE x 16 n_tets^2 values / event time, against
+    achieved = warp instructions per value (FAR_COUNTS) x 16 n_tets^2 values / event time, against
     152 SMs x 4 schedulers x 1 warp instruction per clock x the maximum SM
-    clock; the FP32 rate (FAR_FLOPS_PER_VALUE) is reported beside it.
+    clock; the FP32 rate (FAR_COUNTS) is reported beside it.
     k_tc_update (tensor-core products of the block inversion of Eq. (6), FP16
     operands, FP32 accumulation): K = 512 complex, ~256 flop per byte of the
     updated block (near the ridge); algorithmic bytes = read and write of the updated block +
@@ -566,7 +573,10 @@ def roofline(last, n, peaks, prec, n_tets):
     src = "measured" if "hbm_gbs" in peaks else "fallback"
     out = {}
     fp32 = prec != 0          # the FP32 fill kernels (every precision but FP64)
-    if last.get("k_far_tt_ms") and fp32 and THETA == 0.0:
+    cls = "normal" if THETA == 0.0 else "oblique"
+    winst, flops, split0 = FAR_COUNTS[cls]
+    counted = (FAR_SPLIT_CHOSEN in (None, split0)) and (THETA == 0.0 or abs(THETA - 0.3) < 1e-6) and PHI == 0.0
+    if last.get("k_far_tt_ms") and fp32 and counted:
         # instruction-issue bound (a mix of FP32, integer and load instructions):
         # warp instructions per value x values / event time, against 152 SMs x 4
         # schedulers x 1 warp instruction per clock x the maximum SM clock
@@ -574,14 +584,14 @@ def roofline(last, n, peaks, prec, n_tets):
         clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         vals = 16.0 * n_tets * n_tets
         ipeak = SMS * SCHEDULERS * clk / 1e9
-        ach = FAR_WINST_PER_VALUE * vals / t / 1e9
+        ach = winst * vals / t / 1e9
         fpeak = float(peaks.get("fp32_fma_tflops") or SMS * FP32_LANES * 2 * clk / 1e12)
         out["k_far_tt"] = {"bound": "alu", "kernel": "k_far_tt", "achieved": ach, "peak": ipeak,
                            "unit": "Gwarp-inst/s", "frac": ach / ipeak, "traffic": None,
                            "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp instruction/clock x %.0f MHz"
                                           % (clk / 1e6),
-                           "fp32_tflops": FAR_FLOPS_PER_VALUE * vals / t / 1e12,
-                           "fp32_frac": FAR_FLOPS_PER_VALUE * vals / t / 1e12 / fpeak,
+                           "fp32_tflops": flops * vals / t / 1e12,
+                           "fp32_frac": flops * vals / t / 1e12 / fpeak,
                            "fp32_peak_tflops": fpeak,
                            "fp32_peak_source": "measured FMA loop (vie_fma_peak)" if peaks.get("fp32_fma_tflops")
                                                else "derived: 152 x 128 lanes x 2 x max clock",
@@ -643,7 +653,7 @@ def run_sweep(args):
     dev = torch.device("cuda", local)
     prec = PRECISIONS[args.precision]
     cell = _cell("sweep_cell")
-    solver = vie.Solver(device=local, precision=prec, tol=1e-6)
+    solver = vie.Solver(device=local, precision=prec, tol=1e-6, autotune=True)   # tuned in the warm-up
     n = solver.set_mesh(cell)
     steps = args.steps
     lams, ths = sweep_requests(max(steps, args.warmup))

@@ -96,6 +96,11 @@ typedef struct {
                               block; inversion work drops by about the square of
                               the number of pieces, GMRES may need more
                               iterations                                         */
+    int32_t autotune;      /* 1: the first solve of each incidence class (normal,
+                              oblique) on a mesh first runs vie_tune on its own
+                              request (vie_solve_batch: before its slots start),
+                              and the mesh's later solves use the choices; 0
+                              (default): the built-in schedule                   */
 } vie_options;
 
 typedef struct {
@@ -210,6 +215,36 @@ int vie_solve(vie_ctx *ctx, const vie_request *req, vie_result *res, void *strea
    positive one. */
 int vie_solve_batch(vie_ctx *ctx, const vie_request *reqs, vie_result *res, int32_t n,
                     int32_t max_slots, int32_t *slots_used, void *stream);
+
+/* Autotuner (not in the paper; the schedule of this implementation): times
+   candidate schedules of the two hot parts on the context's mesh and on `req`
+   with CUDA events on `stream`, and keeps the fastest for the mesh (every later
+   vie_solve / vie_solve_batch of this context uses them; vie_set_mesh resets
+   them).  Tuned, per incidence class of req (normal: theta = 0, or oblique):
+   - the fill: the Ewald split multiplier E / sqrt(pi / ab) of the FP32 tables
+     (normal 1.25, 1.5, 1.75; oblique 1.0, 1.25, 1.5): it moves work between
+     the lattice images and the Floquet orders, the value of the matrix does not
+     change (the series is split, not truncated differently); each candidate
+     is timed over a whole fill (best of two); VIE_FP64 keeps its own split;
+   - the GMRES products: 1, 2 or 4 row ranges per resident CTA (mean of five
+     products of the matrix the products read).
+   It fills Z (the request's matrix; the next solve fills it again) and
+   allocates two vectors.  report (optional, caller-owned) receives every
+   candidate's time and the choices.  Errors as vie_solve (a candidate whose
+   tables do not fit is skipped and reported with fill_ms = -1). */
+typedef struct {
+    int32_t incidence_class;   /* 0: normal incidence, 1: oblique                   */
+    int32_t n_split;           /* candidates of the split timed (0 for VIE_FP64)    */
+    double  split[4];          /* multiplier of sqrt(pi / ab)                        */
+    double  fill_ms[4];        /* device time of the whole fill with it (-1: skipped)*/
+    double  split_chosen;
+    int32_t n_mv;
+    int32_t mv_grid[4];        /* row ranges per resident CTA of the GMRES products  */
+    double  mv_ms[4];          /* device time of one product with it                 */
+    int32_t mv_chosen;
+    double  tune_ms;           /* host wall time of the tuning                       */
+} vie_tune_report;
+int vie_tune(vie_ctx *ctx, const vie_request *req, vie_tune_report *report, void *stream);
 
 /* Parity entry points: the FP64 impedance matrix Z [N][N] (row-major, complex)
    and right-hand side b [N][2] of Eq. (2) in canonical unknown order, copied

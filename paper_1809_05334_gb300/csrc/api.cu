@@ -104,6 +104,12 @@ struct vie_ctx {
     // between phases and at every GMRES iteration (the stream is idle there)
     const std::atomic<int> *cancel = nullptr;
     std::vector<double> pinv;   // per domain block: 1 / (power-of-two scale of its FP16 inverse)
+    // autotuner choices for this mesh (0: the defaults): the FP32 tables' Ewald
+    // split multiplier per incidence class (0 normal, 1 oblique), and the row
+    // ranges per resident CTA of the GMRES products; tuned[c]: class c was tuned
+    double tune_split[2] = {0.0, 0.0};
+    int tune_mv = 0;
+    bool tuned[2] = {false, false};
     size_t ld = 0;
     int64_t h2d = 0, d2h = 0;   // bytes copied by the current solve
     // CUDA events for options.timing
@@ -257,7 +263,9 @@ int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
     // Ewald parameters and tables (Sec. 2.2) and the propagating Floquet orders
     const char *why = "";
     const bool fp64 = ctx->opt.precision == VIE_FP64;
-    if (int rc = vie::build_ewald_tables(T.a, T.b, H.k0, H.kx, H.ky, ctx->z_extent, fp64, H.ew, &H.orders, &why))
+    const double split = ctx->tune_split[(H.kx == 0.0 && H.ky == 0.0) ? 0 : 1];
+    if (int rc = vie::build_ewald_tables(T.a, T.b, H.k0, H.kx, H.ky, ctx->z_extent, fp64, H.ew, &H.orders, &why,
+                                         split))
         return fail(ctx, rc, why);
     return VIE_OK;
 }
@@ -460,6 +468,7 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
                                  ? std::max(ctx->opt.inner_tol > 0 ? ctx->opt.inner_tol : inner_def, 1e-6)
                                  : tol * 0.1;
     const size_t vs = 4 * (size_t)N;     // stride of one basis vector (two rhs)
+    const int mvg = ctx->tune_mv > 0 ? ctx->tune_mv : 1;   // launch shape of the Z products
     CK(ctx->x.ensure(sizeof(double) * vs));
     CK(ctx->r.ensure(sizeof(double) * vs));
     CK(ctx->u.ensure(sizeof(TV) * vs));
@@ -546,14 +555,14 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
             if constexpr (std::is_same<TV, float>::value) {
                 if (zin == 1)
                     CK((vie::matvec<__half, TV, TV>(ctx->Zh.as<__half>(), ctx->ld, N, N, vk, pre ? u : vn,
-                                                    TV(ctx->zh_alpha), false, st)));
+                                                    TV(ctx->zh_alpha), false, st, mvg)));
                 else if (zin == 2)
                     CK((vie::matvec<__nv_bfloat16, TV, TV>(ctx->Zh.as<__nv_bfloat16>(), ctx->ld, N, N, vk,
-                                                           pre ? u : vn, TV(1), false, st)));
+                                                           pre ? u : vn, TV(1), false, st, mvg)));
                 else
-                    CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st)));
+                    CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st, mvg)));
             } else {
-                CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st)));
+                CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st, mvg)));
             }
             if (e1) { CK(cudaEventRecord(e1, st)); tm.mv.push_back({e0, e1}); }
             if (pre) { if (int e = timed_precond<TV>(ctx, H, moff, mld, u, vn, st, tm)) return e; }
@@ -912,6 +921,7 @@ void default_opts(vie_options *o) {
     o->inner_tol = 0;   // per precision (3e-6 FP32, 1e-3 FP16, 8e-3 BF16)
     o->timing = 0;
     o->precond_block_max = 0;
+    o->autotune = 0;
 }
 
 }  // namespace
@@ -930,6 +940,128 @@ cudaError_t vie::upload_device_constants(int device) {
     done[device] = 1;
     return cudaSuccess;
 }
+
+// ---------------------------------------------------------------------------
+// Autotuner: the fill schedule (the FP32 tables' Ewald split multiplier, which
+// moves work between the lattice images and the Floquet orders) per incidence
+// class, and the launch shape of the GMRES products (row ranges per resident
+// CTA), each timed with CUDA events on the caller's mesh and request; the
+// fastest is kept in the context for the mesh.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr double TUNE_SPLIT_NORMAL[3] = {1.25, 1.5, 1.75};
+constexpr double TUNE_SPLIT_OBLIQUE[3] = {1.0, 1.25, 1.5};
+constexpr int TUNE_MV[3] = {1, 2, 4};
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+int incidence_class(const vie_request *req) { return std::sin(req->theta) == 0.0 ? 0 : 1; }
+
+template <typename TZ, typename TV>
+int tune_impl(vie_ctx *ctx, const vie_request *req, vie_tune_report *out, cudaStream_t st) {
+    using clk = std::chrono::steady_clock;
+    const auto w0 = clk::now();
+    const int cls = incidence_class(req);
+    vie_tune_report r{};
+    r.incidence_class = cls;
+    EventPair ev;
+    CK(cudaEventCreate(&ev.a));
+    CK(cudaEventCreate(&ev.b));
+    auto elapsed = [&](double &ms) -> int {
+        float f = 0.f;
+        CK(cudaEventSynchronize(ev.b));
+        CK(cudaEventElapsedTime(&f, ev.a, ev.b));
+        ms = f;
+        return VIE_OK;
+    };
+    const vie::DevMesh m = dev_mesh(ctx);
+    const bool fp32 = ctx->opt.precision != VIE_FP64;
+    const double keep = ctx->tune_split[cls];
+    double best = 1e300, best_split = 0.0;
+    const int n_split = fp32 ? 3 : 1;   // FP64: the series' own split, one fill for the product timing
+    for (int c = 0; c < n_split; ++c) {
+        const double cand = fp32 ? (cls == 0 ? TUNE_SPLIT_NORMAL[c] : TUNE_SPLIT_OBLIQUE[c]) : 0.0;
+        ctx->tune_split[cls] = cand;
+        HostReq H;
+        vie::DevReq q{};
+        int e = prepare(ctx, req, H);
+        if (e == VIE_OK) e = upload_request(ctx, H, q, st);
+        if (e != VIE_OK) {
+            // a candidate whose tables do not fit is skipped; an error of the
+            // request itself fails every candidate and is returned
+            if (fp32) { r.split[c] = cand; r.fill_ms[c] = -1.0; }
+            if (c + 1 == n_split && best_split == 0.0 && fp32) { ctx->tune_split[cls] = keep; return e; }
+            if (!fp32) { ctx->tune_split[cls] = keep; return e; }
+            continue;
+        }
+        double ms = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaEventRecord(ev.a, st));
+            if (int fe = fill<TZ>(ctx, m, q, false, st)) { ctx->tune_split[cls] = keep; return fe; }
+            CK(cudaEventRecord(ev.b, st));
+            double t;
+            if (int te = elapsed(t)) return te;
+            ms = std::min(ms, t);
+        }
+        if (fp32) {
+            r.split[c] = cand;
+            r.fill_ms[c] = ms;
+            ++r.n_split;
+            if (ms < best) { best = ms; best_split = cand; }
+        }
+    }
+    ctx->tune_split[cls] = fp32 ? best_split : keep;
+    r.split_chosen = fp32 ? best_split : 0.0;
+    // the GMRES products on the matrix they read (FP16 / BF16: the 16-bit copy)
+    const int N = ctx->mesh->topo.N;
+    if constexpr (std::is_same<TZ, float>::value) {
+        if (ctx->opt.precision == VIE_FP16 || ctx->opt.precision == VIE_BF16)
+            if (int e = make_z16(ctx, st)) return e;
+    }
+    DevBuf xv, yv;
+    CK(xv.ensure(sizeof(TV) * 4 * (size_t)N));
+    CK(yv.ensure(sizeof(TV) * 4 * (size_t)N));
+    CK(cudaMemsetAsync(xv.p, 0, sizeof(TV) * 4 * (size_t)N, st));
+    auto product = [&](int g) -> cudaError_t {
+        if constexpr (std::is_same<TV, float>::value) {
+            if (ctx->opt.precision == VIE_FP16)
+                return vie::matvec<__half, TV, TV>(ctx->Zh.as<__half>(), ctx->ld, N, N, xv.as<TV>(), yv.as<TV>(),
+                                                   TV(ctx->zh_alpha), false, st, g);
+            if (ctx->opt.precision == VIE_BF16)
+                return vie::matvec<__nv_bfloat16, TV, TV>(ctx->Zh.as<__nv_bfloat16>(), ctx->ld, N, N, xv.as<TV>(),
+                                                          yv.as<TV>(), TV(1), false, st, g);
+        }
+        return vie::matvec<TZ, TV, TV>(ctx->Z.as<TZ>(), ctx->ld, N, N, xv.as<TV>(), yv.as<TV>(), TV(1), false, st, g);
+    };
+    double bmv = 1e300;
+    int bg = 1;
+    for (int c = 0; c < 3; ++c) {
+        const int g = TUNE_MV[c];
+        CK(product(g));   // warm-up
+        CK(cudaEventRecord(ev.a, st));
+        for (int rep = 0; rep < 5; ++rep) CK(product(g));
+        CK(cudaEventRecord(ev.b, st));
+        double t;
+        if (int te = elapsed(t)) return te;
+        r.mv_grid[c] = g;
+        r.mv_ms[c] = t / 5.0;
+        if (t < bmv) { bmv = t; bg = g; }
+    }
+    r.n_mv = 3;
+    r.mv_chosen = bg;
+    ctx->tune_mv = bg;
+    ctx->tuned[cls] = true;
+    r.tune_ms = std::chrono::duration<double, std::milli>(clk::now() - w0).count();
+    if (out) *out = r;
+    return VIE_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -976,6 +1108,9 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
     cudaSetDevice(ctx->device);
     // a new mesh object: solve slots still holding the previous one keep it alive
     ctx->mesh = std::make_shared<MeshState>();
+    ctx->tune_split[0] = ctx->tune_split[1] = 0.0;   // tuned choices belong to a mesh
+    ctx->tune_mv = 0;
+    ctx->tuned[0] = ctx->tuned[1] = false;
     std::string e = vie::build_topology(verts, n_verts, tets, n_tets, tet_domain, n_domains, period_a, period_b,
                                         active_domain, ctx->mesh->topo);
     if (!e.empty()) return fail(ctx, e.find("range") != std::string::npos ? VIE_EINVAL : VIE_BAD_MESH, e);
@@ -1132,12 +1267,24 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
 
 int32_t vie_num_unknowns(const vie_ctx *ctx) { return (ctx && ctx->mesh->have_mesh) ? ctx->mesh->topo.N : 0; }
 
+int vie_tune(vie_ctx *ctx, const vie_request *req, vie_tune_report *report, void *stream) {
+    if (!ctx || !req) return VIE_EINVAL;
+    if (!ctx->mesh->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    return ctx->opt.precision == VIE_FP64 ? tune_impl<double, double>(ctx, req, report, st)
+                                          : tune_impl<float, float>(ctx, req, report, st);
+}
+
 int vie_solve(vie_ctx *ctx, const vie_request *req, vie_result *res, void *stream) {
     if (!ctx || !req || !res) return VIE_EINVAL;
     if (!ctx->mesh->have_mesh) return fail(ctx, VIE_EINVAL, "no mesh set");
     std::memset(res, 0, sizeof(*res));
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->opt.autotune && !ctx->tuned[incidence_class(req)]) {   // first solve of this class on the mesh
+        if (int e = vie_tune(ctx, req, nullptr, stream)) { res->status = e; return e; }
+    }
     int r = ctx->opt.precision == VIE_FP64 ? solve_impl<double, double>(ctx, req, res, st)
                                            : solve_impl<float, float>(ctx, req, res, st);
     res->status = r;
@@ -1157,6 +1304,12 @@ int vie_solve_batch(vie_ctx *ctx, const vie_request *reqs, vie_result *res, int3
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     // admission by HBM footprint: a slot is opened only while its buffers fit
     // in the free device memory (less 5% and 1 GB of headroom)
+    // autotune: each incidence class of the batch once, here, before the slots start
+    if (ctx->opt.autotune) {
+        for (int i = 0; i < n; ++i)
+            if (!ctx->tuned[incidence_class(&reqs[i])])
+                if (int e = vie_tune(ctx, &reqs[i], nullptr, stream)) return e;
+    }
     size_t per = 0;
     if (int e = slot_footprint(ctx, &reqs[0], &per)) return e;
     int want = std::min<int>(max_slots, n);
@@ -1177,6 +1330,8 @@ int vie_solve_batch(vie_ctx *ctx, const vie_request *reqs, vie_result *res, int3
         vie_ctx *c = ctx->slots[k - 1].get();
         c->opt = ctx->opt;
         c->mesh = ctx->mesh;
+        for (int k2 = 0; k2 < 2; ++k2) { c->tune_split[k2] = ctx->tune_split[k2]; c->tuned[k2] = ctx->tuned[k2]; }
+        c->tune_mv = ctx->tune_mv;
         c->z_extent = ctx->z_extent;
         use.push_back(c);
     }

@@ -88,9 +88,11 @@ struct EwaldF32 {
 #ifndef VIE_SPLIT_OBLIQUE
 #define VIE_SPLIT_OBLIQUE 1.0   // FP32 tables, oblique incidence
 #endif
-inline double ewald_split(double a, double b, double k0, bool fp32, bool normal) {
+// mult > 0 replaces the FP32 multiplier (the autotuner's candidates).
+inline double ewald_split(double a, double b, double k0, bool fp32, bool normal, double mult = 0.0) {
     const double e = std::max(std::sqrt(3.141592653589793 / (a * b)), k0 / 6.0);
-    return fp32 ? (normal ? VIE_SPLIT_NORMAL : VIE_SPLIT_OBLIQUE) * e : e;
+    if (!fp32) return e;
+    return (mult > 0.0 ? mult : (normal ? VIE_SPLIT_NORMAL : VIE_SPLIT_OBLIQUE)) * e;
 }
 
 // The smallest rectangle of Floquet orders (p, q) holding every mode with

@@ -1731,10 +1731,10 @@ namespace vie {
 // Returns VIE_OK, VIE_RAYLEIGH_ANOMALY (a Floquet order at grazing) or
 // VIE_EINVAL (a table would overflow), with *why set.
 int build_ewald_tables(double a, double b, double k0, double kx, double ky, double z_extent, bool fp64,
-                       EwaldTables &E, std::vector<double> *orders, const char **why) {
+                       EwaldTables &E, std::vector<double> *orders, const char **why, double split_mult) {
     std::memset(&E, 0, sizeof(E));
     if (orders) orders->clear();
-    E.E = ewald_split(a, b, k0, !fp64, kx == 0.0 && ky == 0.0);
+    E.E = ewald_split(a, b, k0, !fp64, kx == 0.0 && ky == 0.0, split_mult);
     E.bb = k0 / (2.0 * E.E);
     E.a = a;
     E.b = b;

@@ -172,7 +172,7 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
 
 template <typename TZ, typename TX, typename TA>
 cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *y, TA alpha, bool accumulate,
-                   cudaStream_t st) {
+                   cudaStream_t st, int grid_mult) {
     if (rows <= 0) return cudaSuccess;
     static int slots = 0;   // resident CTAs of the GPU (per instantiation; one device per process)
     if (slots == 0) {
@@ -184,7 +184,8 @@ cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *
         if (e != cudaSuccess) return e;
         slots = std::max(1, sms * per);
     }
-    const int grid = std::max(1, std::min(slots, (rows + MV_ROWS - 1) / MV_ROWS));
+    // grid_mult > 1: that many row ranges per resident CTA (finer ranges, a shorter tail)
+    const int grid = std::max(1, std::min(slots * std::max(1, grid_mult), (rows + MV_ROWS - 1) / MV_ROWS));
     if (accumulate)
         k_matvec<TZ, TX, TA, true><<<grid, MV_WARPS * 32, 0, st>>>(A, ld, rows, cols, x, y, alpha);
     else
@@ -193,12 +194,12 @@ cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *
     return cudaGetLastError();
 }
 
-template cudaError_t matvec<float, float, float>(const float *, size_t, int, int, const float *, float *, float, bool, cudaStream_t);
-template cudaError_t matvec<__half, float, float>(const __half *, size_t, int, int, const float *, float *, float, bool, cudaStream_t);
+template cudaError_t matvec<float, float, float>(const float *, size_t, int, int, const float *, float *, float, bool, cudaStream_t, int);
+template cudaError_t matvec<__half, float, float>(const __half *, size_t, int, int, const float *, float *, float, bool, cudaStream_t, int);
 template cudaError_t matvec<__half, double, double>(const __half *, size_t, int, int, const double *, double *, double, bool,
-                                                    cudaStream_t);
+                                                    cudaStream_t, int);
 template cudaError_t matvec<__nv_bfloat16, float, float>(const __nv_bfloat16 *, size_t, int, int, const float *, float *,
-                                                         float, bool, cudaStream_t);
+                                                         float, bool, cudaStream_t, int);
 
 // largest |Re|, |Im| of a block, as the bit pattern of a non-negative float
 // (for those the integer order is the float order, so atomicMax applies)
@@ -236,7 +237,7 @@ cudaError_t to_half(const float *A, size_t count, float scale, __half *B, cudaSt
     k_to_half<<<1216, 256, 0, st>>>(A, count, scale, B); ++g_launches;
     return cudaGetLastError();
 }
-template cudaError_t matvec<float, double, double>(const float *, size_t, int, int, const double *, double *, double, bool, cudaStream_t);
+template cudaError_t matvec<float, double, double>(const float *, size_t, int, int, const double *, double *, double, bool, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // Residual product of the FP64 refinement, y <- y + alpha Z x, Z in FP32 and
@@ -383,7 +384,7 @@ cudaError_t matvec_ds(const float *A, size_t ld, int rows, int cols, const doubl
     ++g_launches;
     return cudaGetLastError();
 }
-template cudaError_t matvec<double, double, double>(const double *, size_t, int, int, const double *, double *, double, bool, cudaStream_t);
+template cudaError_t matvec<double, double, double>(const double *, size_t, int, int, const double *, double *, double, bool, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // Peak of the FP32 / FP64 FMA pipes, for the roofline of the CUDA-core

@@ -16,9 +16,11 @@ namespace vie {
 // compensated sums); xs is device scratch of 8 cols floats
 cudaError_t matvec_ds(const float *A, size_t ld, int rows, int cols, const double *x, float *xs, double *y,
                       double alpha, bool accumulate, cudaStream_t st);
+// y <- alpha A x (+ y if accumulate) for two right-hand sides; grid_mult: row
+// ranges per resident CTA (1: one; the autotuner may pick more)
 template <typename TZ, typename TX, typename TA>
 cudaError_t matvec(const TZ *A, size_t ld, int rows, int cols, const TX *x, TA *y, TA alpha, bool accumulate,
-                   cudaStream_t st);
+                   cudaStream_t st, int grid_mult = 1);
 // CUDA-event timing of selected launches (optional)
 struct KernelTimer {
     cudaEvent_t (*alloc)(void *) = nullptr;   // returns the next event of the caller's pool

@@ -27,13 +27,20 @@ EXPORTS = ["vie_default_options", "vie_create", "vie_set_options", "vie_set_mesh
            "vie_status_str", "vie_last_error", "vie_destroy", "vie_green_noalloc", "vie_solve_batch",
            "vie_server_create", "vie_server_submit", "vie_server_poll", "vie_server_get_stats",
            "vie_server_destroy", "vie_server_cancel", "vie_domain_block", "vie_fma_peak",
-           "vie_check_device_wait"]
+           "vie_check_device_wait", "vie_tune"]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("use_precond", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("timing", ctypes.c_int32), ("precond_block_max", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("precond_block_max", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("incidence_class", ctypes.c_int32), ("n_split", ctypes.c_int32), ("split", ctypes.c_double * 4),
+                ("fill_ms", ctypes.c_double * 4), ("split_chosen", ctypes.c_double), ("n_mv", ctypes.c_int32),
+                ("mv_grid", ctypes.c_int32 * 4), ("mv_ms", ctypes.c_double * 4), ("mv_chosen", ctypes.c_int32),
+                ("tune_ms", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -116,6 +123,7 @@ def load():
     lib.vie_domain_block.argtypes = [P, ctypes.POINTER(Request), I, ctypes.POINTER(I), P, P, P, P]
     lib.vie_fma_peak.argtypes = [ctypes.c_int, I, ctypes.POINTER(D)]
     lib.vie_check_device_wait.argtypes = [ctypes.c_int, I, I]
+    lib.vie_tune.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(TuneReport), P]
     _LIB = lib
     return lib
 
@@ -150,7 +158,7 @@ class Solver:
     """One library context on one GPU (vie_create ... vie_destroy)."""
 
     def __init__(self, device=0, precision=VIE_FP32, use_precond=True, restart=100, max_iter=1000,
-                 tol=1e-6, inner_tol=0.0, timing=False, precond_block_max=0):
+                 tol=1e-6, inner_tol=0.0, timing=False, precond_block_max=0, autotune=False):
         self.lib = load()
         self.opt = Options()
         self.lib.vie_default_options(ctypes.byref(self.opt))
@@ -159,6 +167,7 @@ class Solver:
         self.opt.tol, self.opt.inner_tol = float(tol), float(inner_tol)
         self.opt.timing = int(bool(timing))
         self.opt.precond_block_max = int(precond_block_max)
+        self.opt.autotune = int(bool(autotune))
         self.ctx = ctypes.c_void_p()
         rc = self.lib.vie_create(ctypes.byref(self.ctx), int(device), ctypes.byref(self.opt))
         if rc != 0:
@@ -236,6 +245,19 @@ class Solver:
                     t_queue_ms=res.t_queue_ms, t_latency_ms=res.t_latency_ms, k_precond_ms=res.k_precond_ms,
                     k_precond_bytes=res.k_precond_bytes, k_precond_n=res.k_precond_n, k_tc_flops=res.k_tc_flops,
                     k_ortho_ms=res.k_ortho_ms, x=out)
+
+    def tune(self, lam, theta=0.0, phi=0.0, eps=(), stream=None):
+        """Autotune the schedule for this mesh and incidence class (vie_tune); returns
+        the report as a dict: candidate split multipliers with their fill times,
+        candidate product launch shapes with their times, and the choices."""
+        req = self.request(lam, theta, phi, eps)
+        rep = TuneReport()
+        self._check(self.lib.vie_tune(self.ctx, ctypes.byref(req), ctypes.byref(rep),
+                                      ctypes.c_void_p(stream) if stream else None))
+        return dict(incidence_class=rep.incidence_class, split=list(rep.split[:rep.n_split]),
+                    fill_ms=list(rep.fill_ms[:rep.n_split]), split_chosen=rep.split_chosen,
+                    mv_grid=list(rep.mv_grid[:rep.n_mv]), mv_ms=list(rep.mv_ms[:rep.n_mv]),
+                    mv_chosen=rep.mv_chosen, tune_ms=rep.tune_ms)
 
     def solve_batch(self, lams, thetas, phis, eps_list, max_slots=2, coeffs=False, stream=None):
         """Independent solves of one mesh (vie_solve_batch): lams/thetas/phis/eps_list

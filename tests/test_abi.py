@@ -27,8 +27,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layout_matches_header():
     from paper_1809_05334_gb300 import vie
-    # vie_options: 4 int32 + 2 double + 2 int32
-    assert ctypes.sizeof(vie.Options) == 4 * 4 + 2 * 8 + 2 * 4
+    # vie_options: 4 int32 + 2 double + 3 int32 (+ 4 bytes of tail padding to the double alignment)
+    assert ctypes.sizeof(vie.Options) == 4 * 4 + 2 * 8 + 3 * 4 + 4
     # vie_request: 3 double + 16 double + pointer + 2 int32 + pointer
     assert ctypes.sizeof(vie.Request) == 3 * 8 + 16 * 8 + 8 + 8 + 8
     assert vie.Result.absorbed.offset % 8 == 0
@@ -44,7 +44,7 @@ def test_struct_layout_compiled_against_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"vie_options": vie.Options, "vie_request": vie.Request, "vie_result": vie.Result,
-               "vie_mesh": vie.Mesh, "vie_server_stats": vie.ServerStats}
+               "vie_mesh": vie.Mesh, "vie_server_stats": vie.ServerStats, "vie_tune_report": vie.TuneReport}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vie.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))

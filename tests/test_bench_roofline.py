@@ -47,9 +47,16 @@ def test_far_kernel_against_the_issue_rate():
     vals = 16.0 * N_TETS * N_TETS
     peak = 152 * 4 * 2070e6 / 1e9                   # G warp instructions / s
     assert f["bound"] == "alu" and math.isclose(f["peak"], peak)
-    assert math.isclose(f["achieved"], bench.FAR_WINST_PER_VALUE * vals / 65e-3 / 1e9, rel_tol=1e-12)
+    winst, flops, _ = bench.FAR_COUNTS["normal"]
+    assert math.isclose(f["achieved"], winst * vals / 65e-3 / 1e9, rel_tol=1e-12)
     assert 0.0 < f["frac"] < 1.0
-    assert math.isclose(f["fp32_tflops"], bench.FAR_FLOPS_PER_VALUE * vals / 65e-3 / 1e12, rel_tol=1e-12)
+    assert math.isclose(f["fp32_tflops"], flops * vals / 65e-3 / 1e12, rel_tol=1e-12)
+
+
+def test_far_kernel_counts_left_out_for_another_split(monkeypatch):
+    monkeypatch.setattr(bench, "FAR_SPLIT_CHOSEN", 1.75)
+    _, allr = bench.roofline(_last(), N, PEAKS, 1, N_TETS)
+    assert "k_far_tt" not in allr
 
 
 def test_products_take_the_binding_roof():

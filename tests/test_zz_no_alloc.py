@@ -28,8 +28,13 @@ def _points(a, b, zmax, n=300, seed=5):
     return d
 
 
-@pytest.mark.parametrize("precision,rtol", [(0, 1e-12), (1, 1e-6)])
-def test_green_noalloc_matches_allocating_entry(precision, rtol):
+# FP64: the same series on both sides (relative 1e-12).  FP32: the entry
+# without allocations evaluates the general tabulated form, the allocating
+# entry the fill's short form (another summation order of the same tables);
+# each is within 2e-6 max|g| of the FP64 oracle (the FP32 g_p bar of
+# test_gpu_parity), so they agree to 4e-6 max|g|.
+@pytest.mark.parametrize("precision,rtol,atol", [(0, 1e-12, 0.0), (1, 0.0, 4e-6)])
+def test_green_noalloc_matches_allocating_entry(precision, rtol, atol):
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
     a, b, thick = 180.0, 150.0, 60.0
@@ -62,7 +67,10 @@ def test_green_noalloc_matches_allocating_entry(precision, rtol):
         out_dev.zero_()
         assert call(lam, th, ph) == 0
         got = out_dev.cpu().numpy().view(np.complex128)
-        assert np.max(np.abs(got - ref) / np.abs(ref)) < rtol
+        if rtol > 0:
+            assert np.max(np.abs(got - ref) / np.abs(ref)) < rtol
+        else:
+            assert np.max(np.abs(got - ref)) < atol * np.max(np.abs(ref))
     # no device memory was taken by the calls
     assert torch.cuda.mem_get_info()[0] == free0
 
