@@ -98,6 +98,9 @@ struct vie_ctx {
     // solve buffers
     DevBuf Z, b, x, r, u, w, V, h, y, Minv, MinvH, amax, tcpack, tcpack2, status, acc, J, rt, cout, xs;
     DevBuf Zh;     // 16-bit copy of Z read by the GMRES products (VIE_FP16 / VIE_BF16)
+    size_t ld16 = 0;   // its row stride (column-interleaved layout, vie::ld16)
+    // the FP16 block inverses the preconditioner reads (interleaved): offsets and row strides
+    std::vector<size_t> moff16, mld16;
     DevBuf dens;   // per-tetrahedron absorbed fractions [2][nt] (request density_out)
     double zh_alpha = 1.0;   // 1 / (power-of-two scale of the FP16 copy)
     // set by the solve server when the request is cancelled: a solve checks it
@@ -410,8 +413,8 @@ int precond_apply(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &mof
         CK(cudaStreamWaitEvent(ctx->side_stream, ctx->side_go, 0));
     }
     for (size_t k = 0; k < H.blk_off.size(); ++k) {
-        const __half *Mi = ctx->MinvH.as<__half>() + 2 * moff[k];
-        CK((vie::matvec<__half, TV, TV>(Mi, mld[k], H.blk_n[k], H.blk_n[k], in + 4 * (size_t)H.blk_off[k],
+        const __half *Mi = ctx->MinvH.as<__half>() + 2 * ctx->moff16[k];
+        CK((vie::matvec<__half, TV, TV>(Mi, ctx->mld16[k], H.blk_n[k], H.blk_n[k], in + 4 * (size_t)H.blk_off[k],
                                          out + 4 * (size_t)H.blk_off[k], TV(ctx->pinv[k]), false,
                                          side && k != kbig ? ctx->side_stream : st)));
     }
@@ -554,10 +557,10 @@ int gmres(vie_ctx *ctx, const HostReq &H, const std::vector<size_t> &moff, const
             if (e0) CK(cudaEventRecord(e0, st));
             if constexpr (std::is_same<TV, float>::value) {
                 if (zin == 1)
-                    CK((vie::matvec<__half, TV, TV>(ctx->Zh.as<__half>(), ctx->ld, N, N, vk, pre ? u : vn,
+                    CK((vie::matvec<__half, TV, TV>(ctx->Zh.as<__half>(), ctx->ld16, N, N, vk, pre ? u : vn,
                                                     TV(ctx->zh_alpha), false, st, mvg)));
                 else if (zin == 2)
-                    CK((vie::matvec<__nv_bfloat16, TV, TV>(ctx->Zh.as<__nv_bfloat16>(), ctx->ld, N, N, vk,
+                    CK((vie::matvec<__nv_bfloat16, TV, TV>(ctx->Zh.as<__nv_bfloat16>(), ctx->ld16, N, N, vk,
                                                            pre ? u : vn, TV(1), false, st, mvg)));
                 else
                     CK((vie::matvec<TZ, TV, TV>(Z, ctx->ld, N, N, vk, pre ? u : vn, TV(1), false, st, mvg)));
@@ -712,7 +715,15 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
     CK(cudaStreamSynchronize(st));
     if (stat & 2) return fail(ctx, VIE_DEVICE_TIMEOUT, "a bounded wait of the tensor-core block inversion ran out");
     if (stat) return fail(ctx, VIE_BREAKDOWN, "zero or non-finite pivot while inverting a domain block");
-    CK(ctx->MinvH.ensure(sizeof(__half) * 2 * std::max<size_t>(tot, 1)));
+    ctx->moff16.assign(nblk, 0);
+    ctx->mld16.assign(nblk, 0);
+    size_t tot16 = 0;
+    for (size_t k = 0; k < nblk; ++k) {
+        ctx->moff16[k] = tot16;
+        ctx->mld16[k] = vie::ld16(H.blk_n[k]);
+        tot16 += ctx->mld16[k] * (size_t)H.blk_n[k];
+    }
+    CK(ctx->MinvH.ensure(sizeof(__half) * 2 * std::max<size_t>(tot16, 1)));
     ctx->pinv.assign(nblk, 1.0);
     for (size_t k = 0; k < nblk; ++k) {
         float mx;
@@ -726,8 +737,8 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
             return fail(ctx, VIE_BREAKDOWN, "non-finite entry in a domain block inverse");
         }
         ctx->pinv[k] = 1.0 / scale;
-        CK(vie::to_half(ctx->Minv.as<float>() + 2 * moff[k], 2 * mld[k] * (size_t)H.blk_n[k], (float)scale,
-                        ctx->MinvH.as<__half>() + 2 * moff[k], st));
+        CK(vie::to_half_il(ctx->Minv.as<float>() + 2 * moff[k], mld[k], H.blk_n[k], H.blk_n[k], (float)scale,
+                           ctx->MinvH.as<__half>() + 2 * ctx->moff16[k], st));
     }
     return VIE_OK;
 }
@@ -736,11 +747,13 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
 // scaled by the power of two that brings the largest |Re|, |Im| to
 // [2^13, 2^14), undone in the product; VIE_BF16: unscaled)
 int make_z16(vie_ctx *ctx, cudaStream_t st) {
-    const size_t count = 2 * ctx->ld * (size_t)ctx->mesh->topo.N;
-    CK(ctx->Zh.ensure(sizeof(uint16_t) * count));
+    const int N = ctx->mesh->topo.N;
+    const size_t count = 2 * ctx->ld * (size_t)N;
+    ctx->ld16 = vie::ld16(N);
+    CK(ctx->Zh.ensure(sizeof(uint16_t) * 2 * ctx->ld16 * (size_t)N));
     if (ctx->opt.precision == VIE_BF16) {
         ctx->zh_alpha = 1.0;
-        CK(vie::to_bf16(ctx->Z.as<float>(), count, ctx->Zh.as<__nv_bfloat16>(), st));
+        CK(vie::to_bf16_il(ctx->Z.as<float>(), ctx->ld, N, N, ctx->Zh.as<__nv_bfloat16>(), st));
         return VIE_OK;
     }
     CK(ctx->amax.ensure(sizeof(unsigned)));
@@ -757,7 +770,7 @@ int make_z16(vie_ctx *ctx, cudaStream_t st) {
     std::frexp((double)mx, &ex);   // mx in [2^(ex-1), 2^ex)
     const double scale = std::ldexp(1.0, 14 - ex);
     ctx->zh_alpha = 1.0 / scale;
-    CK(vie::to_half(ctx->Z.as<float>(), count, (float)scale, ctx->Zh.as<__half>(), st));
+    CK(vie::to_half_il(ctx->Z.as<float>(), ctx->ld, N, N, (float)scale, ctx->Zh.as<__half>(), st));
     return VIE_OK;
 }
 
@@ -898,7 +911,7 @@ int slot_footprint(vie_ctx *ctx, const vie_request *req, size_t *bytes) {
     const size_t sz = fp64 ? 8 : 4;
     size_t minv = 0, pk1 = 0, pk2 = 0;   // block inverses; packing scratch of the largest block and of the others
     for (int n : H.blk_n) {
-        minv += 8 * (((size_t)n + 3) / 4 * 4) * (size_t)n;
+        minv += 8 * (((size_t)n + 3) / 4 * 4) * (size_t)n + 4 * vie::ld16(n) * (size_t)n;   // FP32 and FP16 copies
         const size_t pk = vie::gj_pack_bytes(n);
         if (pk > pk1) { pk2 = pk1; pk1 = pk; } else if (pk > pk2) pk2 = pk;
     }
@@ -906,7 +919,7 @@ int slot_footprint(vie_ctx *ctx, const vie_request *req, size_t *bytes) {
     const size_t m = (size_t)std::max(2, ctx->opt.restart);
     const size_t vs = 4 * N;
     size_t b = 2 * sz * ld * N + minv + sz * vs * (m + 3) + 8 * vs * 4 + 64 * (size_t)ctx->mesh->nto[0];
-    if (ctx->opt.precision == VIE_FP16 || ctx->opt.precision == VIE_BF16) b += 2 * 2 * ld * N;   // 16-bit copy of Z
+    if (ctx->opt.precision == VIE_FP16 || ctx->opt.precision == VIE_BF16) b += 2 * 2 * vie::ld16((int)N) * N;   // 16-bit copy of Z
     b += (size_t)ctx->mesh->topo.nt * 4 * 64 + (16u << 20);   // request arrays, tables, small buffers
     *bytes = b;
     return VIE_OK;
@@ -1031,10 +1044,10 @@ int tune_impl(vie_ctx *ctx, const vie_request *req, vie_tune_report *out, cudaSt
     auto product = [&](int g) -> cudaError_t {
         if constexpr (std::is_same<TV, float>::value) {
             if (ctx->opt.precision == VIE_FP16)
-                return vie::matvec<__half, TV, TV>(ctx->Zh.as<__half>(), ctx->ld, N, N, xv.as<TV>(), yv.as<TV>(),
+                return vie::matvec<__half, TV, TV>(ctx->Zh.as<__half>(), ctx->ld16, N, N, xv.as<TV>(), yv.as<TV>(),
                                                    TV(ctx->zh_alpha), false, st, g);
             if (ctx->opt.precision == VIE_BF16)
-                return vie::matvec<__nv_bfloat16, TV, TV>(ctx->Zh.as<__nv_bfloat16>(), ctx->ld, N, N, xv.as<TV>(),
+                return vie::matvec<__nv_bfloat16, TV, TV>(ctx->Zh.as<__nv_bfloat16>(), ctx->ld16, N, N, xv.as<TV>(),
                                                           yv.as<TV>(), TV(1), false, st, g);
         }
         return vie::matvec<TZ, TV, TV>(ctx->Z.as<TZ>(), ctx->ld, N, N, xv.as<TV>(), yv.as<TV>(), TV(1), false, st, g);
@@ -1410,20 +1423,26 @@ int vie_fill_matrix_prec(vie_ctx *ctx, const vie_request *req, double *Z_host, v
     if (ctx->opt.precision == VIE_FP16 || ctx->opt.precision == VIE_BF16) {
         // the 16-bit copy the GMRES products read, widened, its scale undone
         if ((e = make_z16(ctx, st))) return e;
-        std::vector<uint16_t> Zb(Zp.size());
+        std::vector<uint16_t> Zb(2 * ctx->ld16 * (size_t)N);
         CK(cudaMemcpyAsync(Zb.data(), ctx->Zh.p, sizeof(uint16_t) * Zb.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        for (size_t i = 0; i < Zb.size(); ++i) {
-            if (ctx->opt.precision == VIE_FP16) {
-                __half_raw r;
-                r.x = Zb[i];
-                Zp[i] = (float)((double)__half2float(__half(r)) * ctx->zh_alpha);
-            } else {
-                __nv_bfloat16_raw r;
-                r.x = Zb[i];
-                Zp[i] = __bfloat162float(__nv_bfloat16(r));
-            }
-        }
+        // back from the column-interleaved layout to rows of ld entries
+        for (int r = 0; r < N; ++r)
+            for (int c = 0; c < N; ++c)
+                for (int k = 0; k < 2; ++k) {
+                    const uint16_t bits = Zb[2 * ((size_t)r * ctx->ld16 + vie::il_pos((size_t)c)) + k];
+                    float v;
+                    if (ctx->opt.precision == VIE_FP16) {
+                        __half_raw h;
+                        h.x = bits;
+                        v = (float)((double)__half2float(__half(h)) * ctx->zh_alpha);
+                    } else {
+                        __nv_bfloat16_raw h;
+                        h.x = bits;
+                        v = __bfloat162float(__nv_bfloat16(h));
+                    }
+                    Zp[2 * ((size_t)r * ctx->ld + c) + k] = v;
+                }
     } else {
         CK(cudaMemcpyAsync(Zp.data(), ctx->Z.p, sizeof(float) * Zp.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

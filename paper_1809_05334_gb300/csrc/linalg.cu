@@ -12,9 +12,9 @@
 #include <cstdint>
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "linalg.h"
-#include <type_traits>
 #include "tc_gemm.cuh"
 
 namespace vie {
@@ -71,8 +71,15 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
     const int rb = (int)((long long)rows * blockIdx.x / gridDim.x);
     const int re = (int)((long long)rows * (blockIdx.x + 1) / gridDim.x);
     constexpr int VEC = sizeof(TZ) == 4 ? 2 : (sizeof(TZ) == 8 ? 1 : 4);   // complex entries per 16-byte load
-    const int nvec = (cols + VEC - 1) / VEC;
-    const int v0 = (int)((long long)nvec * warp / MV_WARPS), v1 = (int)((long long)nvec * (warp + 1) / MV_WARPS);
+    // 16-bit entries: the column-interleaved layout (ld16 columns per row, load
+    // v holds columns 128 (v / 32) + v % 32 + 32 u); warp segments start on a
+    // chunk, so a warp's x loads of one step are contiguous
+    const int nvec = VEC == 4 ? (cols + 127) / 128 * 32 : (cols + VEC - 1) / VEC;
+    int v0 = (int)((long long)nvec * warp / MV_WARPS), v1 = (int)((long long)nvec * (warp + 1) / MV_WARPS);
+    if (VEC == 4) {
+        v0 &= ~31;
+        v1 = warp + 1 == MV_WARPS ? nvec : (v1 & ~31);
+    }
     int buf = 0;
     for (int r0 = rb; r0 < re; r0 += MV_ROWS, buf ^= 1) {
         TA acc[MV_ROWS][4];
@@ -95,7 +102,8 @@ k_matvec(const TZ *__restrict__ A, size_t ld, int rows, int cols, const TX *__re
 #pragma unroll
             for (int u = 0; u < VEC; ++u) {
                 TA xv[4] = {TA(0), TA(0), TA(0), TA(0)};
-                if (c + u < cols) load_x<TX, TA>(x, c + u, xv);
+                const int cu = VEC == 4 ? (v >> 5) * 128 + (v & 31) + 32 * u : c + u;   // the entry's column
+                if (cu < cols) load_x<TX, TA>(x, cu, xv);
 #pragma unroll
                 for (int i = 0; i < MV_ROWS; ++i) {
                     TA zr, zi;
@@ -211,20 +219,36 @@ __global__ void k_absmax(const float *__restrict__ A, size_t count, unsigned *ou
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-// B = scale A in FP16 (round to nearest), count floats
-__global__ void k_to_half(const float *__restrict__ A, size_t count, float scale, __half *__restrict__ B) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-        B[i] = __float2half_rn(A[i] * scale);
+// B = scale A in 16 bits (round to nearest), column-interleaved: one thread per
+// complex entry of B (rows x ld16(cols)); position p of a row holds column
+// chunk + (p % 4) * 32 + (p % 128) / 4, zero past cols
+template <typename T>
+__global__ void k_to16_il(const float *__restrict__ A, size_t lda, int rows, int cols, float scale, T *__restrict__ B) {
+    const size_t ldb = ((size_t)cols + 127) / 128 * 128;
+    const size_t total = (size_t)rows * ldb;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / ldb, p = i - r * ldb;
+        const size_t pp = p & 127;
+        const size_t c = (p - pp) + (pp & 3) * 32 + (pp >> 2);
+        float2 v = make_float2(0.f, 0.f);
+        if (c < (size_t)cols) v = *reinterpret_cast<const float2 *>(A + 2 * (r * lda + c));
+        if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value) {
+            B[2 * i] = __float2half_rn(v.x * scale);
+            B[2 * i + 1] = __float2half_rn(v.y * scale);
+        } else {
+            B[2 * i] = __float2bfloat16_rn(v.x);
+            B[2 * i + 1] = __float2bfloat16_rn(v.y);
+        }
+    }
 }
 
-// B = A in BF16 (round to nearest), count floats (BF16 has the FP32 range: no scale)
-__global__ void k_to_bf16(const float *__restrict__ A, size_t count, __nv_bfloat16 *__restrict__ B) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-        B[i] = __float2bfloat16_rn(A[i]);
+cudaError_t to_bf16_il(const float *A, size_t lda, int rows, int cols, __nv_bfloat16 *B, cudaStream_t st) {
+    k_to16_il<__nv_bfloat16><<<1216, 256, 0, st>>>(A, lda, rows, cols, 1.f, B); ++g_launches;
+    return cudaGetLastError();
 }
 
-cudaError_t to_bf16(const float *A, size_t count, __nv_bfloat16 *B, cudaStream_t st) {
-    k_to_bf16<<<1216, 256, 0, st>>>(A, count, B); ++g_launches;
+cudaError_t to_half_il(const float *A, size_t lda, int rows, int cols, float scale, __half *B, cudaStream_t st) {
+    k_to16_il<__half><<<1216, 256, 0, st>>>(A, lda, rows, cols, scale, B); ++g_launches;
     return cudaGetLastError();
 }
 
@@ -233,10 +257,6 @@ cudaError_t absmax(const float *A, size_t count, unsigned *out, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t to_half(const float *A, size_t count, float scale, __half *B, cudaStream_t st) {
-    k_to_half<<<1216, 256, 0, st>>>(A, count, scale, B); ++g_launches;
-    return cudaGetLastError();
-}
 template cudaError_t matvec<float, double, double>(const float *, size_t, int, int, const double *, double *, double, bool, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------

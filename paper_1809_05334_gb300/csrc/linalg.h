@@ -54,10 +54,21 @@ cudaError_t wait_check(bool arrive, long long polls, int *status, cudaStream_t s
 cudaError_t fma_peak(bool fp64, int iters, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, double *flops);
 // *out (zeroed by the caller) <- max |A[i]| over count floats, as float bits
 cudaError_t absmax(const float *A, size_t count, unsigned *out, cudaStream_t st);
-// B = scale A in FP16, count floats
-cudaError_t to_half(const float *A, size_t count, float scale, __half *B, cudaStream_t st);
-// B = A in BF16, count floats
-cudaError_t to_bf16(const float *A, size_t count, __nv_bfloat16 *B, cudaStream_t st);
+// 16-bit copies of complex FP32 matrices in the column-interleaved layout the
+// 16-bit products read: rows of ld16(cols) complex entries; inside each chunk
+// of 128 columns, position p holds column (p % 4) * 32 + p / 4 of the chunk
+// (zero past cols), so the four entries of one 16-byte load are columns
+// j, j + 32, j + 64, j + 96 and the product's x loads are contiguous across a
+// warp.  il_pos(c): the position of column c.
+inline size_t ld16(int cols) { return ((size_t)cols + 127) / 128 * 128; }
+__host__ __device__ inline size_t il_pos(size_t c) {
+    const size_t j = c & 127;
+    return (c - j) + (j & 31) * 4 + (j >> 5);
+}
+// B = scale A in FP16 (interleaved; A: rows x cols complex, row stride lda complex)
+cudaError_t to_half_il(const float *A, size_t lda, int rows, int cols, float scale, __half *B, cudaStream_t st);
+// B = A in BF16 (interleaved)
+cudaError_t to_bf16_il(const float *A, size_t lda, int rows, int cols, __nv_bfloat16 *B, cudaStream_t st);
 template <typename TS, typename TD>
 cudaError_t copy_block(const TS *Z, size_t ldz, int off, int n, TD *B, size_t ldb, cudaStream_t st);
 template <typename TV>

@@ -89,8 +89,9 @@ size_t mesh_footprint(const vie_mesh &m, const vie_options &opt) {
     const size_t sz = opt.precision == VIE_FP64 ? 8 : 4;
     const size_t mres = (size_t)std::max(2, opt.restart);
     size_t b = 2 * sz * ld * N;                          // Z
-    if (opt.precision == VIE_FP16 || opt.precision == VIE_BF16) b += 2 * 2 * ld * N;   // its 16-bit copy
-    b += 8 * ld * N;                                     // block inverses (FP32 complex), bounded by N^2
+    const size_t l16 = (N + 127) / 128 * 128;            // row stride of the 16-bit (interleaved) copies
+    if (opt.precision == VIE_FP16 || opt.precision == VIE_BF16) b += 2 * 2 * l16 * N;   // its 16-bit copy
+    b += 8 * ld * N + 4 * l16 * N;                       // block inverses (FP32 and FP16), bounded by N^2
     b += 2 * vie::gj_pack_bytes((int)N);                 // packing scratch of the inversion (two blocks at once)
     b += sz * 4 * N * (mres + 3) + 8 * 4 * N * 4;        // Krylov basis and vectors, x, r, b, coefficients
     b += 2 * (nt * nt + nt * nf + nh * nt + nh * nf);    // near-image masks
