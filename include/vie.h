@@ -294,11 +294,16 @@ int vie_erfcx(vie_ctx *ctx, const double *u, double *out, int32_t n, int32_t pre
 
 /* The Ewald-summed periodic Green's function g_p(d), Eq. (3), on the device
    for n in-cell difference vectors d [n][3] (|dx| < a, |dy| < b, d != 0) at
-   the request's wavelength and incidence; out [n] complex. */
+   the request's wavelength and incidence; out [n] complex.  VIE_FP32 takes the
+   evaluation form the fill kernels take for that incidence (the short normal
+   or oblique form where it applies, else the general tabulated form), so it
+   checks the fill's own arithmetic. */
 int vie_green(vie_ctx *ctx, const vie_request *req, const double *d, double *out,
               int32_t n, int32_t precision);
 
-/* Allocation-free g_p(d): the same Ewald evaluation as vie_green, for callers
+/* Allocation-free g_p(d): the same Ewald series as vie_green (in FP32 the
+   general tabulated form, where vie_green takes the fill's short form: the two
+   agree to the FP32 accuracy of the tables, 2e-6 max|g| each), for callers
    that cannot allocate device memory while they run (a host framework that
    owns all of HBM through its own pool and forbids cudaMalloc/cudaFree after
    start-up, or code that must not let an allocation synchronise the device).
