@@ -96,6 +96,9 @@ typedef struct {
                               block; inversion work drops by about the square of
                               the number of pieces, GMRES may need more
                               iterations                                         */
+    int32_t precond_pivot; /* outer pivot width of the block inversion: 512 or
+                              1024 sets it; 0 (default): 512, or the width
+                              vie_tune chose for the mesh                        */
     int32_t autotune;      /* 1: the first solve of each incidence class (normal,
                               oblique) on a mesh first runs vie_tune on its own
                               request (vie_solve_batch: before its slots start),
@@ -227,7 +230,11 @@ int vie_solve_batch(vie_ctx *ctx, const vie_request *reqs, vie_result *res, int3
      change (the series is split, not truncated differently); each candidate
      is timed over a whole fill (best of two); VIE_FP64 keeps its own split;
    - the GMRES products: 1, 2 or 4 row ranges per resident CTA (mean of five
-     products of the matrix the products read).
+     products of the matrix the products read);
+   - once per mesh, where a domain block has more than 1024 unknowns: the outer
+     pivot width of the block inversion of Eq. (6), 512 or 1024 (half the
+     passes over the block against a longer chain of pivot-block inverses),
+     each over a whole inversion (best of two).
    It fills Z (the request's matrix; the next solve fills it again) and
    allocates two vectors.  report (optional, caller-owned) receives every
    candidate's time and the choices.  Errors as vie_solve (a candidate whose
@@ -242,6 +249,12 @@ typedef struct {
     int32_t mv_grid[4];        /* row ranges per resident CTA of the GMRES products  */
     double  mv_ms[4];          /* device time of one product with it                 */
     int32_t mv_chosen;
+    int32_t n_pivot;           /* 0: pivot width not timed (already tuned for the
+                                  mesh, no block wider than 1024, or no
+                                  preconditioner)                                   */
+    int32_t pivot[2];          /* outer pivot width of the block inversion           */
+    double  factor_ms[2];      /* device time of the whole block inversion with it   */
+    int32_t pivot_chosen;      /* the width the mesh's solves use                    */
     double  tune_ms;           /* host wall time of the tuning                       */
 } vie_tune_report;
 int vie_tune(vie_ctx *ctx, const vie_request *req, vie_tune_report *report, void *stream);

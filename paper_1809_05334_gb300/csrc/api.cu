@@ -112,6 +112,7 @@ struct vie_ctx {
     // ranges per resident CTA of the GMRES products; tuned[c]: class c was tuned
     double tune_split[2] = {0.0, 0.0};
     int tune_mv = 0;
+    int tune_pivot = 0;   // outer pivot width of the block inversion (0: 512)
     bool tuned[2] = {false, false};
     size_t ld = 0;
     int64_t h2d = 0, d2h = 0;   // bytes copied by the current solve
@@ -692,7 +693,9 @@ int factor(vie_ctx *ctx, const HostReq &H, std::vector<size_t> &moff, std::vecto
         float *B = ctx->Minv.as<float>() + 2 * moff[k];
         CK((vie::copy_block<TZ, float>(ctx->Z.as<TZ>(), ctx->ld, H.blk_off[k], H.blk_n[k], B, mld[k], sk)));
         CK(vie::gj_invert_tc(B, mld[k], H.blk_n[k], ctx->status.as<int>(), big ? ctx->tcpack.p : ctx->tcpack2.p, sk,
-                             big ? ctx->aux_stream : ctx->side_stream, kt));
+                             big ? ctx->aux_stream : ctx->side_stream, kt,
+                             ctx->opt.precond_pivot > 0 ? ctx->opt.precond_pivot
+                                                        : (ctx->tune_pivot > 0 ? ctx->tune_pivot : 512)));
     }
     if (side) {
         CK(cudaEventRecord(ctx->side_done, ctx->side_stream));
@@ -934,6 +937,7 @@ void default_opts(vie_options *o) {
     o->inner_tol = 0;   // per precision (3e-6 FP32, 1e-3 FP16, 8e-3 BF16)
     o->timing = 0;
     o->precond_block_max = 0;
+    o->precond_pivot = 0;
     o->autotune = 0;
 }
 
@@ -997,6 +1001,7 @@ int tune_impl(vie_ctx *ctx, const vie_request *req, vie_tune_report *out, cudaSt
     const bool fp32 = ctx->opt.precision != VIE_FP64;
     const double keep = ctx->tune_split[cls];
     double best = 1e300, best_split = 0.0;
+    HostReq Hk;   // the request as the last filled candidate prepared it (block structure)
     const int n_split = fp32 ? 3 : 1;   // FP64: the series' own split, one fill for the product timing
     for (int c = 0; c < n_split; ++c) {
         const double cand = fp32 ? (cls == 0 ? TUNE_SPLIT_NORMAL[c] : TUNE_SPLIT_OBLIQUE[c]) : 0.0;
@@ -1013,6 +1018,7 @@ int tune_impl(vie_ctx *ctx, const vie_request *req, vie_tune_report *out, cudaSt
             if (!fp32) { ctx->tune_split[cls] = keep; return e; }
             continue;
         }
+        Hk = H;
         double ms = 1e300;
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaEventRecord(ev.a, st));
@@ -1069,6 +1075,34 @@ int tune_impl(vie_ctx *ctx, const vie_request *req, vie_tune_report *out, cudaSt
     r.n_mv = 3;
     r.mv_chosen = bg;
     ctx->tune_mv = bg;
+    // the block inversion's outer pivot width (a property of the mesh's blocks:
+    // tuned once per mesh, only where a block is wider than the larger width)
+    int nbig = 0;
+    for (int nb : Hk.blk_n) nbig = std::max(nbig, nb);
+    if (ctx->opt.use_precond && ctx->opt.precond_pivot == 0 && ctx->tune_pivot == 0 && nbig > 1024) {
+        const int cand[2] = {512, 1024};
+        double bf = 1e300;
+        int bp = 512;
+        for (int c = 0; c < 2; ++c) {
+            ctx->tune_pivot = cand[c];
+            std::vector<size_t> moff, mld;
+            double ms = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {
+                CK(cudaEventRecord(ev.a, st));
+                if (int fe = factor<TZ>(ctx, Hk, moff, mld, st, nullptr)) { ctx->tune_pivot = 0; return fe; }
+                CK(cudaEventRecord(ev.b, st));
+                double t;
+                if (int te = elapsed(t)) return te;
+                ms = std::min(ms, t);
+            }
+            r.pivot[c] = cand[c];
+            r.factor_ms[c] = ms;
+            if (ms < bf) { bf = ms; bp = cand[c]; }
+        }
+        r.n_pivot = 2;
+        ctx->tune_pivot = bp;
+    }
+    r.pivot_chosen = ctx->opt.precond_pivot > 0 ? ctx->opt.precond_pivot : (ctx->tune_pivot > 0 ? ctx->tune_pivot : 512);
     ctx->tuned[cls] = true;
     r.tune_ms = std::chrono::duration<double, std::milli>(clk::now() - w0).count();
     if (out) *out = r;
@@ -1093,6 +1127,10 @@ int vie_create(vie_ctx **out, int device, const vie_options *opt) {
     default_opts(&ctx->opt);
     if (opt) ctx->opt = *opt;
     if (ctx->opt.precision < VIE_FP64 || ctx->opt.precision > VIE_BF16) { delete ctx; return VIE_EINVAL; }
+    if (ctx->opt.precond_pivot != 0 && ctx->opt.precond_pivot != 512 && ctx->opt.precond_pivot != 1024) {
+        delete ctx;
+        return VIE_EINVAL;
+    }
     if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return VIE_ECUDA; }
     if (vie::upload_device_constants(device) != cudaSuccess) {
         delete ctx;
@@ -1106,7 +1144,7 @@ int vie_set_options(vie_ctx *ctx, const vie_options *opt) {
     if (!ctx || !opt) return VIE_EINVAL;
     if (opt->precision < VIE_FP64 || opt->precision > VIE_BF16) return fail(ctx, VIE_EINVAL, "unknown precision");
     if (opt->restart < 2 || opt->max_iter < 1 || !(opt->tol > 0) || opt->precond_block_max < 0 ||
-        !(opt->inner_tol >= 0))
+        !(opt->inner_tol >= 0) || (opt->precond_pivot != 0 && opt->precond_pivot != 512 && opt->precond_pivot != 1024))
         return fail(ctx, VIE_EINVAL, "bad solver options");
     ctx->opt = *opt;
     return VIE_OK;
@@ -1123,6 +1161,7 @@ int vie_set_mesh(vie_ctx *ctx, const double *verts, int32_t n_verts, const int32
     ctx->mesh = std::make_shared<MeshState>();
     ctx->tune_split[0] = ctx->tune_split[1] = 0.0;   // tuned choices belong to a mesh
     ctx->tune_mv = 0;
+    ctx->tune_pivot = 0;
     ctx->tuned[0] = ctx->tuned[1] = false;
     std::string e = vie::build_topology(verts, n_verts, tets, n_tets, tet_domain, n_domains, period_a, period_b,
                                         active_domain, ctx->mesh->topo);
@@ -1345,6 +1384,7 @@ int vie_solve_batch(vie_ctx *ctx, const vie_request *reqs, vie_result *res, int3
         c->mesh = ctx->mesh;
         for (int k2 = 0; k2 < 2; ++k2) { c->tune_split[k2] = ctx->tune_split[k2]; c->tuned[k2] = ctx->tuned[k2]; }
         c->tune_mv = ctx->tune_mv;
+        c->tune_pivot = ctx->tune_pivot;
         c->z_extent = ctx->z_extent;
         use.push_back(c);
     }

@@ -620,19 +620,22 @@ bool tensor_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t row
 }
 }  // namespace
 
-constexpr int GJ_P = 512;   // pivot width of the outer Gauss-Jordan steps (the K of their products)
-static_assert(GJ_P <= TC_KP, "the packed operands hold one outer pivot block");
+// pivot width of the outer Gauss-Jordan steps (the K of their products): 512
+// by default, up to GJ_PMAX (a schedule choice of the autotuner)
+constexpr int GJ_P = 512;
+constexpr int GJ_PMAX = 1024;
+static_assert(GJ_PMAX <= TC_KP, "the packed operands hold one outer pivot block");
 static_assert(GJ_RQ == 32, "the row-publish jump covers 32 slots");
-static_assert(GJ_W == 128 && GJ_P % GJ_W == 0, "a pivot block is inverted in 128-wide steps");
+static_assert(GJ_W == 128 && GJ_P % GJ_W == 0 && GJ_PMAX % GJ_W == 0, "a pivot block is inverted in 128-wide steps");
 
 constexpr int GJ_WORDS = 16;   // largest-entry words: 4 per set (products (a), (3)), 2 for the pivot blocks
 
 size_t gj_pack_bytes(int n) {
     // two sets (consecutive outer steps overlap) of Ap [mp] and Bp [2 mp] FP16
-    // rows, one set of 3 GJ_P rows for the inversion of the pivot blocks, and
+    // rows, one set of 3 GJ_PMAX rows for the inversion of the pivot blocks, and
     // the largest-entry words of the packed operands
     const size_t mp = ((size_t)n + TC_TM - 1) / TC_TM * TC_TM;
-    return (2 * 3 * mp + 3 * (size_t)GJ_P) * TC_PACK_ROW * sizeof(__half) + GJ_WORDS * sizeof(unsigned);
+    return (2 * 3 * mp + 3 * (size_t)GJ_PMAX) * TC_PACK_ROW * sizeof(__half) + GJ_WORDS * sizeof(unsigned);
 }
 
 namespace {
@@ -674,19 +677,19 @@ void tc_product(cudaStream_t s, const CUtensorMap &tA, const CUtensorMap &tB, co
     }
 }
 
-// In-place inverse of the w x w pivot block at Ab (row stride ld, w <= GJ_P):
+// In-place inverse of the w x w pivot block at Ab (row stride ld, w <= GJ_PMAX):
 // Gauss-Jordan with 128-wide pivots (register inverse of each 128 block, then
 // its column-panel and trailing/row-panel products, K = 128).  sub: packed
-// operand scratch of 3 GJ_P rows; amax: two largest-entry words.
+// operand scratch of 3 GJ_PMAX rows; amax: two largest-entry words.
 cudaError_t invert_pivot_block(float *Ab, size_t ld, int w, int *status, __half *sub, unsigned *amax, int sms,
                                cudaStream_t st) {
     k_gj_diag_w<<<1, GJ_W * GJ_DG, 0, st>>>(Ab, ld, 0, std::min(w, GJ_W), status); ++g_launches;
     if (w <= GJ_W) return cudaGetLastError();
-    __half *Ap = sub, *Bp = sub + (size_t)GJ_P * TC_PACK_ROW;
+    __half *Ap = sub, *Bp = sub + (size_t)GJ_PMAX * TC_PACK_ROW;
     const int wc = (w + 3) / 4 * 4;   // whole 16-byte column groups (padding columns stay zero)
     CUtensorMap tA, tB, tC, tCs;
-    if (!tensor_map(&tA, Ap, TC_PACK_ROW, GJ_P, TC_PACK_ROW * 2, TC_KCHUNK, TC_TM, true) ||
-        !tensor_map(&tB, Bp, TC_PACK_ROW, 2 * (uint64_t)GJ_P, TC_PACK_ROW * 2, TC_KCHUNK, 2 * TC_TN, true) ||
+    if (!tensor_map(&tA, Ap, TC_PACK_ROW, GJ_PMAX, TC_PACK_ROW * 2, TC_KCHUNK, TC_TM, true) ||
+        !tensor_map(&tB, Bp, TC_PACK_ROW, 2 * (uint64_t)GJ_PMAX, TC_PACK_ROW * 2, TC_KCHUNK, 2 * TC_TN, true) ||
         !tensor_map(&tC, Ab, 2 * (uint64_t)wc, w, 8 * ld, 32, TC_TM) ||
         !tensor_map(&tCs, Ab, 2 * (uint64_t)wc, w, 8 * ld, 32, 32))
         return cudaErrorInvalidValue;
@@ -723,7 +726,8 @@ cudaError_t invert_pivot_block(float *Ab, size_t ld, int w, int *status, __half 
 // they run on st while the rest of (3) streams through HBM; the next row-panel
 // packing waits for it.  Consecutive steps use alternate packing buffers.
 cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cudaStream_t st, cudaStream_t aux,
-                         KernelTimer *kt) {
+                         KernelTimer *kt, int pivot) {
+    const int P = (pivot == GJ_PMAX) ? GJ_PMAX : GJ_P;   // outer pivot width
     int dev = 0, sms = 0;
     {   // opt in to the large dynamic shared memory (per device, cheap to repeat)
         cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
@@ -736,13 +740,13 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cu
     __half *const base = static_cast<__half *>(pack);
     __half *Ap[2], *Bp[2];
     __half *sub = base + 2 * set_halves;
-    unsigned *words = reinterpret_cast<unsigned *>(sub + 3 * (size_t)GJ_P * TC_PACK_ROW);   // GJ_WORDS
+    unsigned *words = reinterpret_cast<unsigned *>(sub + 3 * (size_t)GJ_PMAX * TC_PACK_ROW);   // GJ_WORDS
     CUtensorMap tmA[2], tmB[2], tmC, tmCs;
     for (int b = 0; b < 2; ++b) {
         Ap[b] = base + b * set_halves;
         Bp[b] = Ap[b] + (size_t)mpmax * TC_PACK_ROW;
     }
-    if (n > GJ_P) {
+    if (n > P) {
         for (int b = 0; b < 2; ++b)
             if (!tensor_map(&tmA[b], Ap[b], TC_PACK_ROW, mpmax, TC_PACK_ROW * 2, TC_KCHUNK, TC_TM, true) ||
                 !tensor_map(&tmB[b], Bp[b], TC_PACK_ROW, 2 * (uint64_t)mpmax, TC_PACK_ROW * 2, TC_KCHUNK, 2 * TC_TN,
@@ -757,12 +761,12 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cu
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evB, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
     bool pending = false;   // the second part of the previous product (3) is running on aux
-    e = invert_pivot_block(A, ld, std::min(n, GJ_P), status, sub, words + 8, sms, st);
-    for (int k0 = 0; k0 < n && e == cudaSuccess; k0 += GJ_P) {
-        const int w = std::min(GJ_P, n - k0);
+    e = invert_pivot_block(A, ld, std::min(n, P), status, sub, words + 8, sms, st);
+    for (int k0 = 0; k0 < n && e == cudaSuccess; k0 += P) {
+        const int w = std::min(P, n - k0);
         const int m = n - w;
         if (m <= 0) break;
-        const int cur = (k0 / GJ_P) & 1;
+        const int cur = (k0 / P) & 1;
         const int mp = (m + TC_TM - 1) / TC_TM * TC_TM;
         const int kc = kchunks(w);
         unsigned *wa = words + 4 * cur, *w3 = wa + 2;   // this set's largest-entry words
@@ -777,8 +781,8 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cu
         const int ntm = (n + TC_TM - 1) / TC_TM, nt = (m + TC_TN - 1) / TC_TN;
         const int prow = k0 / TC_TM, nprow = (w + TC_TM - 1) / TC_TM;   // pivot tile rows: beta 0
         const TcMap mb = {n, m, n, 0, k0, w, prow, nprow, 0, 0, 0, 0, 0, kc, w3};
-        const bool next = k0 + GJ_P < n;
-        const int tA = k0 / TC_TN, nA = std::min(GJ_P / TC_TN, nt - tA);   // tile columns of the next pivot block
+        const bool next = k0 + P < n;
+        const int tA = k0 / TC_TN, nA = std::min(P / TC_TN, nt - tA);   // tile columns of the next pivot block
         if (next && nt > nA) {
             TcMap ma = mb, mr = mb;
             ma.only_lo = tA; ma.only_n = nA;
@@ -795,8 +799,8 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cu
             tc_product(st, tmA[cur], tmB[cur], tmC, tmCs, mb, std::min(tiles(n, m), sms), status, kt, n, m, w);
         }
         if (next) {
-            const int k1 = k0 + GJ_P;
-            e = invert_pivot_block(A + 2 * ((size_t)k1 * ld + k1), ld, std::min(n - k1, GJ_P), status, sub, words + 8,
+            const int k1 = k0 + P;
+            e = invert_pivot_block(A + 2 * ((size_t)k1 * ld + k1), ld, std::min(n - k1, P), status, sub, words + 8,
                                    sms, st);
         }
     }

@@ -44,8 +44,10 @@ struct KernelTimer {
 // their scale words), aux a second stream of the caller (look-ahead); the work
 // is complete on st when the last call returns on it
 size_t gj_pack_bytes(int n);
+// pivot: width of the outer pivot blocks, 512 (default) or 1024 (half the
+// passes over the block, a longer chain of pivot-block inverses)
 cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cudaStream_t st, cudaStream_t aux,
-                         KernelTimer *kt = nullptr);
+                         KernelTimer *kt = nullptr, int pivot = 512);
 // one bounded mbarrier wait of at most `polls` polls on a barrier that gets its
 // arrival (arrive) or never does: bit 1 of *status (device) when it runs out
 cudaError_t wait_check(bool arrive, long long polls, int *status, cudaStream_t st);

@@ -13,7 +13,7 @@
 //   Ap [mp][2 KP]    row r: K complex entries of the r-th row of A
 //   Bp [2 np][2 KP]  rows 2j, 2j+1: s (Re b, -Im b), s (Im b, Re b), b = B[k][j]
 // so that both operands are K-major and TMA-loadable (zero padded to 128-row
-// tiles and to KP = 512; a product reads the first kchunks x 64 real K).  Rows and columns of C are addressed through
+// tiles and to KP = 1024; a product reads the first kchunks x 64 real K).  Rows and columns of C are addressed through
 // skip maps (index i < at ? i : i + skip), so a product can cover the trailing
 // rows/columns around a pivot block, the pivot columns alone, or all rows.
 //
@@ -40,7 +40,7 @@ namespace vie {
 
 constexpr int TC_TM = 128;                        // complex rows per tile
 constexpr int TC_TN = 128;                        // complex columns per tile (256 real)
-constexpr int TC_KP = 512;                        // complex K of the packed operands (zero padded)
+constexpr int TC_KP = 1024;                       // complex K of the packed operands (zero padded)
 constexpr int TC_KCHUNK = 64;                     // real K (FP16) per stage: one 128-byte swizzle row
 constexpr int TC_CCHUNK = 2 * TC_TN / 32;         // 8 chunks of 32 floats across a C tile
 constexpr int TC_A_BYTES = TC_TM * 128;           // 16 KB
@@ -53,7 +53,7 @@ constexpr int TC_SMEM = 1024 + TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + TC_CSLOTS
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr long long TC_WAIT_LIMIT = 20000000;     // polls of one wait (tens of ms)
 constexpr int TC_THREADS = 256;
-constexpr int TC_PACK_ROW = 2 * TC_KP;            // FP16 entries per packed row (2 KB)
+constexpr int TC_PACK_ROW = 2 * TC_KP;            // FP16 entries per packed row (4 KB)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

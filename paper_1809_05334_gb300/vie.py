@@ -33,14 +33,16 @@ EXPORTS = ["vie_default_options", "vie_create", "vie_set_options", "vie_set_mesh
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("use_precond", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("timing", ctypes.c_int32), ("precond_block_max", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("precond_block_max", ctypes.c_int32), ("precond_pivot", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("incidence_class", ctypes.c_int32), ("n_split", ctypes.c_int32), ("split", ctypes.c_double * 4),
                 ("fill_ms", ctypes.c_double * 4), ("split_chosen", ctypes.c_double), ("n_mv", ctypes.c_int32),
                 ("mv_grid", ctypes.c_int32 * 4), ("mv_ms", ctypes.c_double * 4), ("mv_chosen", ctypes.c_int32),
-                ("tune_ms", ctypes.c_double)]
+                ("n_pivot", ctypes.c_int32), ("pivot", ctypes.c_int32 * 2), ("factor_ms", ctypes.c_double * 2),
+                ("pivot_chosen", ctypes.c_int32), ("tune_ms", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -158,7 +160,7 @@ class Solver:
     """One library context on one GPU (vie_create ... vie_destroy)."""
 
     def __init__(self, device=0, precision=VIE_FP32, use_precond=True, restart=100, max_iter=1000,
-                 tol=1e-6, inner_tol=0.0, timing=False, precond_block_max=0, autotune=False):
+                 tol=1e-6, inner_tol=0.0, timing=False, precond_block_max=0, autotune=False, precond_pivot=0):
         self.lib = load()
         self.opt = Options()
         self.lib.vie_default_options(ctypes.byref(self.opt))
@@ -168,6 +170,7 @@ class Solver:
         self.opt.timing = int(bool(timing))
         self.opt.precond_block_max = int(precond_block_max)
         self.opt.autotune = int(bool(autotune))
+        self.opt.precond_pivot = int(precond_pivot)
         self.ctx = ctypes.c_void_p()
         rc = self.lib.vie_create(ctypes.byref(self.ctx), int(device), ctypes.byref(self.opt))
         if rc != 0:
@@ -257,7 +260,8 @@ class Solver:
         return dict(incidence_class=rep.incidence_class, split=list(rep.split[:rep.n_split]),
                     fill_ms=list(rep.fill_ms[:rep.n_split]), split_chosen=rep.split_chosen,
                     mv_grid=list(rep.mv_grid[:rep.n_mv]), mv_ms=list(rep.mv_ms[:rep.n_mv]),
-                    mv_chosen=rep.mv_chosen, tune_ms=rep.tune_ms)
+                    mv_chosen=rep.mv_chosen, pivot=list(rep.pivot[:rep.n_pivot]),
+                    factor_ms=list(rep.factor_ms[:rep.n_pivot]), pivot_chosen=rep.pivot_chosen, tune_ms=rep.tune_ms)
 
     def solve_batch(self, lams, thetas, phis, eps_list, max_slots=2, coeffs=False, stream=None):
         """Independent solves of one mesh (vie_solve_batch): lams/thetas/phis/eps_list

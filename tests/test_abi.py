@@ -27,8 +27,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layout_matches_header():
     from paper_1809_05334_gb300 import vie
-    # vie_options: 4 int32 + 2 double + 3 int32 (+ 4 bytes of tail padding to the double alignment)
-    assert ctypes.sizeof(vie.Options) == 4 * 4 + 2 * 8 + 3 * 4 + 4
+    # vie_options: 4 int32 + 2 double + 4 int32
+    assert ctypes.sizeof(vie.Options) == 4 * 4 + 2 * 8 + 4 * 4
     # vie_request: 3 double + 16 double + pointer + 2 int32 + pointer
     assert ctypes.sizeof(vie.Request) == 3 * 8 + 16 * 8 + 8 + 8 + 8
     assert vie.Result.absorbed.offset % 8 == 0

@@ -168,6 +168,25 @@ def test_block_inverses_of_plasmonic_mini(solvers):
     _check_blocks(s, cell, 500.0, 0.0, range(3))
 
 
+def test_block_inverses_with_1024_wide_pivots():
+    """The same blocks inverted with 1024-wide outer pivot blocks (the width the
+    autotuner may choose): K = 1024 products, eight 128-wide steps per pivot
+    block, the same bound on Z_dd M - I."""
+    cell = cellgen.small_cells()["plasmonic_mini"]
+    s = vie.Solver(precision=vie.VIE_FP32, tol=1e-6, precond_pivot=1024)
+    try:
+        s.set_mesh(cell)
+        sizes = [s.block_size(500.0, 0.0, 0.0, cell.eps(500.0), block=k) for k in range(3)]
+        assert max(sizes) > 1024          # one full 1024-wide step and a ragged one on the largest block
+        _check_blocks(s, cell, 500.0, 0.0, range(3))
+        ref = oracle_run("plasmonic_mini", cell, 500.0, 0.0, 0.0)
+        out = s.solve(500.0, 0.0, 0.0, cell.eps(500.0))
+        assert out["status"] == 0 and np.all(out["rel_residual"] <= 1e-6)
+        assert np.max(np.abs(out["A"] - ref["A"])) <= 1e-4
+    finally:
+        s.close()
+
+
 def test_block_inverse_of_the_bench_cell_metal_block(solvers):
     """The 3,456-unknown buffer block of the snapped bench cell (seven 512-wide
     outer steps, multi-tile products) and its 778-unknown Ag block (the

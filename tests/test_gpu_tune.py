@@ -48,6 +48,26 @@ def test_tune_report_and_parity(cell, lam, th, ph):
     assert np.max(np.abs(out["A"] - base["A"])) <= 1e-5
 
 
+def test_pivot_width_tuned_once_per_mesh():
+    """A mesh with a domain block wider than 1024 unknowns: the first tuning
+    times the inversion at both widths and keeps the faster; the next class's
+    tuning reuses it; solves meet the bar with it."""
+    mini = cellgen.small_cells()["plasmonic_mini"]
+    s = vie.Solver(precision=vie.VIE_FP32, tol=1e-6)
+    try:
+        s.set_mesh(mini)
+        r0 = s.tune(500.0, 0.0, 0.0, mini.eps(500.0))
+        assert r0["pivot"] == [512, 1024] and all(t > 0 for t in r0["factor_ms"])
+        assert r0["pivot_chosen"] == r0["pivot"][int(np.argmin(r0["factor_ms"]))]
+        r1 = s.tune(500.0, 0.4, 0.0, mini.eps(500.0))
+        assert r1["pivot"] == [] and r1["pivot_chosen"] == r0["pivot_chosen"]
+        ref = solve_cell(mini, 500.0, 0.4, 0.0)
+        out = s.solve(500.0, 0.4, 0.0, mini.eps(500.0))
+    finally:
+        s.close()
+    assert out["status"] == 0 and np.max(np.abs(out["A"] - ref["A"])) <= 1e-4
+
+
 def test_autotune_batch_equals_alone(cell):
     lams = [480.0, 520.0, 560.0, 600.0]
     ths = [0.0, 0.3, 0.0, 0.6]
