@@ -624,6 +624,16 @@ bool tensor_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t row
 // by default, up to GJ_PMAX (a schedule choice of the autotuner)
 constexpr int GJ_P = 512;
 constexpr int GJ_PMAX = 1024;
+// SMs the second part of each product (3) leaves free for the next pivot
+// block's inverse, at pivot width 512 and 1024 (measured on the 21k cell's
+// 16,790 block: at 1024, 8 / 12 / 16 / 24 / 32 / 48 SMs gave 47.0 / 46.0 /
+// 44.9 / 44.2 / 43.6 / 46.6 ms per inversion; at 512, 4 / 16 gave 48.1 / 47.1)
+#ifndef VIE_GJ_RESERVE_WIDE
+#define VIE_GJ_RESERVE_WIDE 32
+#endif
+#ifndef VIE_GJ_RESERVE
+#define VIE_GJ_RESERVE 16
+#endif
 static_assert(GJ_PMAX <= TC_KP, "the packed operands hold one outer pivot block");
 static_assert(GJ_RQ == 32, "the row-publish jump covers 32 slots");
 static_assert(GJ_W == 128 && GJ_P % GJ_W == 0 && GJ_PMAX % GJ_W == 0, "a pivot block is inverted in 128-wide steps");
@@ -721,13 +731,16 @@ cudaError_t invert_pivot_block(float *Ab, size_t ld, int w, int *status, __half 
 // inversion is 16 n^3 / w bytes; at w = 512 the products sit near the ridge of
 // the FP16 tensor rate and the HBM bandwidth).
 // Look-ahead: product (3) is split into the tile columns holding the next
-// pivot block (on st) and the rest (on aux, on all SMs but four).  The next
+// pivot block (on st) and the rest (on aux, on all SMs but a reserve).  The next
 // step's pivot inverse and column-panel product need only the first part, so
 // they run on st while the rest of (3) streams through HBM; the next row-panel
 // packing waits for it.  Consecutive steps use alternate packing buffers.
 cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cudaStream_t st, cudaStream_t aux,
                          KernelTimer *kt, int pivot) {
     const int P = (pivot == GJ_PMAX) ? GJ_PMAX : GJ_P;   // outer pivot width
+    // SMs the rest of each product leaves to the next pivot block's inverse
+    // (its K = 128 products; a 1024-wide block has eight 128-wide steps)
+    const int reserve = P > GJ_P ? VIE_GJ_RESERVE_WIDE : VIE_GJ_RESERVE;
     int dev = 0, sms = 0;
     {   // opt in to the large dynamic shared memory (per device, cheap to repeat)
         cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
@@ -791,7 +804,7 @@ cudaError_t gj_invert_tc(float *A, size_t ld, int n, int *status, void *pack, cu
             tc_product(st, tmA[cur], tmB[cur], tmC, tmCs, ma, std::min(ntm * nA, sms), status, kt, n, colsA, w);
             cudaEventRecord(evP, st);
             cudaStreamWaitEvent(aux, evP, 0);
-            tc_product(aux, tmA[cur], tmB[cur], tmC, tmCs, mr, std::max(1, std::min(ntm * (nt - nA), sms - 4)),
+            tc_product(aux, tmA[cur], tmB[cur], tmC, tmCs, mr, std::max(1, std::min(ntm * (nt - nA), sms - reserve)),
                        status, kt, n, m - colsA, w);
             cudaEventRecord(evB, aux);
             pending = true;
