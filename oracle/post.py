@@ -8,7 +8,9 @@ fraction of the incident power absorbed in domain d of one cell is
 
 from P_abs = (w eps0/2) int |Im eps_r||E|^2 and P_inc = |E0|^2 a b cos(theta)/(2 eta0),
 with w eps0 eta0 = k0.  E = d/eps_r is linear in each tetrahedron, so the
-integral of |E|^2 is exact with the tetrahedron's second moments.
+integral of |E|^2 is exact with the tetrahedron's second moments.  The same
+integrand per tetrahedron is the absorption profile (Fig. 5); its layer sums on
+a slab are pinned against the slab's closed-form standing wave.
 
 R and T (not in the paper; they close the energy balance R + T + sum A_d = 1)
 come from the Floquet expansion of the scattered field of J = j w kappa D: for
