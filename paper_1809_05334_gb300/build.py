@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libvie.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "fill.cu", "linalg.cu", "post.cu", "topology.cpp", "rules.cpp", "server.cpp"]
+SOURCES = ["api.cu", "fill.cu", "linalg.cu", "post.cu", "topology.cpp", "rules.cpp", "server.cpp",
+           "ewald_tables.cpp"]
 
 
 def _nvcc():

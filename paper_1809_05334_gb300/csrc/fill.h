@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "ewald_params.h"
+#include "ewald_tables.h"
 #include "vie_internal.h"
 
 namespace vie {
@@ -92,11 +93,7 @@ cudaError_t upload_constants();
 // later calls return at once, so constant memory that running solves read is
 // never written again.  Returns the CUDA error of the first upload, if any.
 cudaError_t upload_device_constants(int device);
-// Ewald parameters and tables of one incidence (fill.cu); status as vie_status;
-// split_mult > 0: the FP32 tables' Ewald split multiplier (else the default)
-int build_ewald_tables(double a, double b, double k0, double kx, double ky, double z_extent, bool fp64,
-                       EwaldTables &E, std::vector<double> *orders, const char **why,
-                       double split_mult = 0.0);
+// build_ewald_tables: ewald_tables.h
 cudaError_t upload_ewald(EwaldTables *dev, const EwaldTables &t, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fill(const DevMesh &m, const DevReq &q, T *Z, size_t ld, double *b, cudaStream_t st,
