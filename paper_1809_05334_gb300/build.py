@@ -3,6 +3,12 @@
 Usage: python -m paper_1809_05334_gb300.build [--force]
 The translation units are compiled in parallel; the library is linked with
 OpenMP (host topology build).  Nothing is installed outside this directory.
+VIE_NVCC_DEFINES (optional, space-separated -D flags) overrides the schedule
+constants that have a compile-time default, for sweeps, e.g.
+    VIE_NVCC_DEFINES="-DVIE_GJ_RESERVE_WIDE=24" python -m paper_1809_05334_gb300.build --force
+(VIE_SPLIT_NORMAL, VIE_SPLIT_OBLIQUE, VIE_FAR_N_MINB, VIE_FAR_O_MINB,
+VIE_GJ_RESERVE, VIE_GJ_RESERVE_WIDE).  The defines are part of the staleness
+check: a build with other defines rebuilds.
 """
 import concurrent.futures
 import os
@@ -26,8 +32,22 @@ def _nvcc():
     return path
 
 
+def _defines():
+    flags = os.environ.get("VIE_NVCC_DEFINES", "").split()
+    for f in flags:
+        if not f.startswith("-DVIE_"):
+            raise RuntimeError("VIE_NVCC_DEFINES takes -DVIE_... flags only, got %r" % f)
+    return flags
+
+
+STAMP = os.path.join(HERE, "_build", "defines.txt")
+
+
 def _stale():
     if not os.path.exists(OUT):
+        return True
+    old = open(STAMP).read() if os.path.exists(STAMP) else ""
+    if old != " ".join(_defines()):
         return True
     t = os.path.getmtime(OUT)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
@@ -40,7 +60,7 @@ def build(force=False, verbose=False):
         return OUT
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp", "-lineinfo"]
+    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp", "-lineinfo"] + _defines()
 
     def compile_one(src):
         obj = os.path.join(BUILD, src + ".o")
@@ -64,6 +84,8 @@ def build(force=False, verbose=False):
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stderr[-6000:])
     os.replace(tmp, OUT)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(_defines()))
     return OUT
 
 
