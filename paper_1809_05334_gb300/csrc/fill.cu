@@ -489,7 +489,10 @@ __device__ __forceinline__ void far_tt_short(const float *__restrict__ fs, const
 // unordered pair {t, s} (s >= t) as in k_far_tt, the reversed pair's moments
 // taken from the pair's own (g_p(-d) = g_p(d)).
 #ifndef VIE_FAR_N_MINB
-#define VIE_FAR_N_MINB 6   // CTAs per SM of the normal-incidence far kernels (85 registers at 6)
+// CTAs per SM of the normal-incidence far kernels: the short form waits on its
+// table loads, so registers (85 at six) pay more than warps (bench cell: 39.8 /
+// 37.5 / 37.0 ms at eight / seven / six, eight spilling at 64 registers)
+#define VIE_FAR_N_MINB 6
 #endif
 template <int PQ>
 __global__ void __launch_bounds__(128, VIE_FAR_N_MINB) k_far_tt_n(DevMesh m, const __grid_constant__ DevReq q, float *Z, size_t N) {
@@ -790,7 +793,9 @@ __device__ __forceinline__ void obl_point_phases(const EwaldF32 &ef, float x, fl
 }
 
 #ifndef VIE_FAR_O_MINB
-#define VIE_FAR_O_MINB 5   // CTAs per SM of the oblique-incidence far kernels
+// CTAs per SM of the oblique-incidence far kernels (bench cell at theta = 0.3,
+// the general order rectangle: 81.6 / 78.3 / 82.3 ms at six / five / four)
+#define VIE_FAR_O_MINB 5
 #endif
 // Far tetrahedron pairs at oblique incidence in the short form: one thread per
 // unordered pair {t, s} (s >= t); the reversed pair's moments are the
