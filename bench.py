@@ -263,13 +263,17 @@ LARGE_WORKLOAD = ("large cell: period 400 nm, 2 x 2 Ag spheres r = 35 nm in a 12
                   "Ag back grating (40 nm ridges), 44550 tets, 90450 unknowns (FP32 Z 65 GB)")
 
 
-def leg_large(vie, torch, local, prec, stream, lam=600.0, theta=0.0):
+def leg_large(vie, torch, local, prec, stream, lam=600.0, theta=0.0, pivot=1024):
     """One solve of the large cell (mixed precision only: an FP64 Z would not
     leave room for the block inverses): set-up time, solve time and phases,
-    iterations, FP64 residual, and the GMRES products' HBM rate at this size."""
+    iterations, FP64 residual, and the GMRES products' HBM rate at this size.
+    pivot: the block inversion's outer pivot width (0: the library default).
+    The cell is not autotuned (that would time four inversions of seconds);
+    1024 is the width measured faster on it (factor 3.32 -> 2.97 s at 600 nm,
+    the same iterations)."""
     import cellgen
     cell = cellgen.config_large()
-    s = vie.Solver(device=local, precision=prec, tol=1e-6, timing=True)
+    s = vie.Solver(device=local, precision=prec, tol=1e-6, timing=True, precond_pivot=pivot)
     try:
         t0 = time.perf_counter()
         n = s.set_mesh(cell)
@@ -281,7 +285,7 @@ def leg_large(vie, torch, local, prec, stream, lam=600.0, theta=0.0):
     zb = Z_BYTES[prec]
     mv = out["k_matvec_ms"]
     return {"workload": LARGE_WORKLOAD, "n_unknowns": n, "lambda_nm": lam, "theta_deg": float(np.rad2deg(theta)),
-            "precision": {v: k for k, v in PRECISIONS.items()}[prec], "set_mesh_s": t1 - t0,
+            "precision": {v: k for k, v in PRECISIONS.items()}[prec], "set_mesh_s": t1 - t0, "precond_pivot": pivot or 512,
             "value": 1e3 / ms, "unit": UNIT, "ms_per_solve": ms, "warmed_up": False,
             "phases_ms": {k: out["t_" + k + "_ms"] for k in ("fill", "factor", "solve", "post")},
             "iterations": out["iterations"], "refinements": out["refinements"],
@@ -305,7 +309,7 @@ def run_large(args):
     cell = cellgen.config_large()
     pts = [(400.0 + 20.0 * i, th) for th in (0.0, np.pi / 4) for i in range(21)][:args.steps]
     pts = [(l + 0.01 if (abs(l - 400.0) < 1e-9 and th == 0.0) else l, th) for l, th in pts]
-    s = vie.Solver(device=local, precision=prec, tol=1e-6)
+    s = vie.Solver(device=local, precision=prec, tol=1e-6, precond_pivot=1024)   # as leg_large
     try:
         t0 = time.perf_counter()
         n = s.set_mesh(cell)
