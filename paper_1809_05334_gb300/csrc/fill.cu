@@ -369,7 +369,7 @@ __device__ __forceinline__ int table_index(float x, int n, float &v) {
 // D_k = d1 D_{k-1} - D_{k-2}, D_0 = 2.  REG: some lane of the warp has images
 // whose static part is removed (else R > 0 on every image of every lane).
 // ---------------------------------------------------------------------------
-template <int PQ, bool REG>
+template <bool REG>
 __device__ __forceinline__ float image_term(int i, float dx, float dy, float dz2, unsigned regm, const float4 *stab4,
                                             const EwaldF32 &ef) {
     const float x = dx + ef.img[i][0], y = dy + ef.img[i][1];
@@ -428,11 +428,11 @@ __device__ __forceinline__ cx<float> green_sym_short(float dx, float dy, float d
         if (mk) {
             const int i1 = __ffs((int)mk) - 1;
             mk &= mk - 1u;
-            const float v0 = image_term<PQ, REG>(i0, dx, dy, dz2, regm, stab4, ef);
-            const float v1 = image_term<PQ, REG>(i1, dx, dy, dz2, regm, stab4, ef);
+            const float v0 = image_term<REG>(i0, dx, dy, dz2, regm, stab4, ef);
+            const float v1 = image_term<REG>(i1, dx, dy, dz2, regm, stab4, ef);
             sv += v0 + v1;
         } else {
-            sv += image_term<PQ, REG>(i0, dx, dy, dz2, regm, stab4, ef);
+            sv += image_term<REG>(i0, dx, dy, dz2, regm, stab4, ef);
         }
     }
     ar = fmaf(ef.img[0][2], sv, ar);
