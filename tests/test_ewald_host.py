@@ -181,3 +181,19 @@ def test_a_planted_fold_error_fails(harness):
             S += X * (1.0 if q == 0 else np.cos(q * t["sy"] * dy)) * _re(t, G, oo[i, q])
     ref = _full(t, G.real.astype(complex), dx, dy)
     assert abs(S - ref) > 1e-3 * np.sum(np.abs(G))
+
+
+def _rc(exe, case):
+    out = subprocess.run([exe] + ["%r" % v for v in case], check=True, capture_output=True, text=True).stdout
+    return json.loads(out)["rc"]
+
+
+@pytest.mark.parametrize("case,moved", [((400.0, 400.0, 400.0, 0.0, 0.0), (400.0, 400.0, 400.01, 0.0, 0.0)),
+                                        # order (-1, 0) grazing: sin(theta) = lambda / a - 1
+                                        ((200.0, 200.0, 300.0, float(np.arcsin(0.5)), 0.0),
+                                         (200.0, 200.0, 300.01, float(np.arcsin(0.5)), 0.0))])
+def test_rayleigh_anomaly_is_detected(harness, case, moved):
+    """A Floquet order exactly at grazing (gamma_pq = 0: the spectral series is
+    singular) returns VIE_RAYLEIGH_ANOMALY (-4); 0.01 nm away the tables build."""
+    assert _rc(harness, case) == -4
+    assert _rc(harness, moved) == 0
