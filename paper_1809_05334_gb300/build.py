@@ -22,7 +22,7 @@ OUT = os.path.join(HERE, "libvie.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "fill.cu", "linalg.cu", "post.cu", "topology.cpp", "rules.cpp", "server.cpp",
-           "ewald_tables.cpp"]
+           "ewald_tables.cpp", "blocks.cpp"]
 
 
 def _nvcc():

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/vie.h"
+#include "blocks.h"
 #include "device_math.cuh"
 #include "fill.h"
 #include "linalg.h"
@@ -179,37 +180,6 @@ struct HostReq {
     double pol[6], kinc[3];
 };
 
-// Recursive coordinate bisection of ids[lo, hi) (unknowns, positioned at the
-// centroid of their T+ tetrahedron) into pieces of at most bmax: split at the
-// median along the axis of largest extent (ties by unknown id, so the order is
-// deterministic); the pieces are appended as [begin, end) ranges of ids, which
-// is reordered in place.
-void split_rcb(const vie::Topology &T, std::vector<int> &ids, int lo, int hi, int bmax,
-               std::vector<std::pair<int, int>> &pieces) {
-    if (hi - lo <= bmax) {
-        std::sort(ids.begin() + lo, ids.begin() + hi);
-        pieces.push_back({lo, hi});
-        return;
-    }
-    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
-    for (int i = lo; i < hi; ++i)
-        for (int k = 0; k < 3; ++k) {
-            const double c = T.cen[3 * (size_t)T.tp[ids[i]] + k];
-            mn[k] = std::min(mn[k], c);
-            mx[k] = std::max(mx[k], c);
-        }
-    int ax = 0;
-    for (int k = 1; k < 3; ++k)
-        if (mx[k] - mn[k] > mx[ax] - mn[ax]) ax = k;
-    const int mid = lo + (hi - lo) / 2;
-    std::nth_element(ids.begin() + lo, ids.begin() + mid, ids.begin() + hi, [&](int a, int b) {
-        const double ca = T.cen[3 * (size_t)T.tp[a] + ax], cb = T.cen[3 * (size_t)T.tp[b] + ax];
-        return ca < cb || (ca == cb && a < b);
-    });
-    split_rcb(T, ids, lo, mid, bmax, pieces);
-    split_rcb(T, ids, mid, hi, bmax, pieces);
-}
-
 int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
     const vie::Topology &T = ctx->mesh->topo;
     if (!(req->lambda_nm > 0) || !std::isfinite(req->lambda_nm)) return fail(ctx, VIE_EINVAL, "lambda must be > 0");
@@ -231,39 +201,10 @@ int prepare(vie_ctx *ctx, const vie_request *req, HostReq &H) {
         H.eps[d] = e;
         H.kap[d] = 1.0 - 1.0 / e;
     }
-    // domain of every unknown (interface faces: larger |eps|, ties to lower id), blocked order
-    std::vector<int> udom(T.N);
-    for (int n = 0; n < T.N; ++n) {
-        int dp = T.dom[T.tp[n]];
-        int dm = T.kind[n] == vie::KIND_HALF ? dp : T.dom[T.tm[n]];
-        double mp = std::abs(H.eps[dp]), mm = std::abs(H.eps[dm]);
-        udom[n] = (mm > mp || (mm == mp && dm < dp)) ? dm : dp;
-    }
-    H.perm.assign(T.N, 0);
-    int next = 0;
-    const int bmax = ctx->opt.precond_block_max;
-    for (int d = 0; d < T.n_dom; ++d) {
-        std::vector<int> ids;
-        for (int n = 0; n < T.N; ++n)
-            if (udom[n] == d) ids.push_back(n);
-        if (ids.empty()) continue;
-        if (bmax > 0 && (int)ids.size() > bmax) {
-            // sub-block variant: the domain's unknowns cut into spatially compact
-            // pieces of at most bmax by recursive coordinate bisection (median
-            // split along the longest extent of the T+ tetrahedron centroids)
-            std::vector<std::pair<int, int>> pieces;
-            split_rcb(T, ids, 0, (int)ids.size(), bmax, pieces);
-            for (auto &pc : pieces) {
-                H.blk_off.push_back(next);
-                H.blk_n.push_back(pc.second - pc.first);
-                for (int i = pc.first; i < pc.second; ++i) H.perm[ids[i]] = next++;
-            }
-        } else {
-            H.blk_off.push_back(next);
-            H.blk_n.push_back((int)ids.size());
-            for (int n : ids) H.perm[n] = next++;
-        }
-    }
+    // Eq. (5): the unknowns grouped by material domain into contiguous blocks
+    std::vector<double> eps_abs(T.n_dom);
+    for (int d = 0; d < T.n_dom; ++d) eps_abs[d] = std::abs(H.eps[d]);
+    vie::domain_blocks(T, eps_abs, ctx->opt.precond_block_max, H.perm, H.blk_off, H.blk_n);
     // Ewald parameters and tables (Sec. 2.2) and the propagating Floquet orders
     const char *why = "";
     const bool fp64 = ctx->opt.precision == VIE_FP64;
